@@ -1,0 +1,211 @@
+/*
+ * brahmap.h — C-ABI of the GB300 GLS map-making library.
+ *
+ * The library solves the generalized-least-squares map-making problem of
+ * BrahMap (Anand & Puglisi, arXiv 2501.16122, Sec. II):
+ *
+ *     d = P s + n                      (Eq. 3)
+ *     A x = b,  A = P^T N^-1 P,  b = P^T N^-1 d     (Eq. 5-6)
+ *     M = (P^T diag(N)^-1 P)^-1        (Eq. 7, the block-diagonal preconditioner)
+ *
+ * where P (Eq. 8) has, for every time sample t, the entries
+ * [1, cos 2psi_t, sin 2psi_t] in the columns (I, Q, U) of the pixel p_t hit
+ * at time t (QU solves use [cos 2psi, sin 2psi], I solves [1]).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers marked "device" are CUDA device pointers on the context's device;
+ *    pointers marked "host" are ordinary host memory.  The caller allocates and
+ *    frees every user array (the ownership rule the paper's Python layer
+ *    adopts, Sec. III-A item 3); handles own the device copies they make, so a
+ *    caller may free its inputs as soon as a *_create call returns.
+ *  - Time samples are laid out detector by detector: samples of detector d
+ *    are [det_offsets[d], det_offsets[d+1]).  Maps are pixel-major with the
+ *    Stokes components interleaved, [npix][ncomp] (Eq. 8's sky vector), FP64.
+ *  - Pixel indices are int32 in [0, npix); -1 marks a flagged sample, which
+ *    contributes nothing (its row of P is zero).
+ *  - Every call is stream-ordered on the context's stream and returns after
+ *    the work it enqueued has completed, unless documented otherwise.
+ *  - Errors: every call returns a bm_status; no exception crosses the ABI.
+ *    bm_last_error() returns a thread-local message for the last failure on
+ *    the calling thread.  On failure, outputs are unspecified and no memory
+ *    is leaked.  An out-of-range argument (size, enum, NULL pointer) returns
+ *    BM_ERR_INVALID before any device work is enqueued.
+ *  - A handle is used by one host thread at a time; the server (bm_serve_*)
+ *    is thread-safe.
+ */
+#ifndef BRAHMAP_H
+#define BRAHMAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BM_OK = 0,
+    BM_ERR_INVALID = 1,        /* bad argument */
+    BM_ERR_OOM = 2,            /* device allocation failed (nothing leaked) */
+    BM_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+    BM_ERR_NOT_CONVERGED = 4,  /* maxiter reached before tol */
+    BM_ERR_BREAKDOWN = 5,      /* p^T A p <= 0 or a non-finite CG scalar */
+    BM_ERR_TIMEOUT = 6,        /* a bounded wait expired */
+    BM_ERR_BUSY = 7,           /* server admission refused (budget or slots) */
+    BM_ERR_NOT_FOUND = 8       /* unknown server ticket */
+} bm_status;
+
+typedef enum { BM_SOLVER_I = 1, BM_SOLVER_QU = 2, BM_SOLVER_IQU = 3 } bm_solver_type;
+typedef enum { BM_F32 = 0, BM_F64 = 1 } bm_dtype;
+
+/* BM_PREC_FP64: every per-sample product and sum in FP64 (the plain path).
+ * BM_PREC_MIXED: FP32 per-sample products inside an FP64 iterative
+ * refinement loop whose residual r = b - A x uses the FP64 operator. */
+typedef enum { BM_PREC_FP64 = 0, BM_PREC_MIXED = 1 } bm_precision;
+
+typedef struct bm_context bm_context;
+typedef struct bm_pointing bm_pointing;
+typedef struct bm_inv_noise bm_inv_noise;
+typedef struct bm_precond bm_precond;
+
+/* Per right-hand-side outcome of bm_pcg_solve. */
+typedef struct {
+    int32_t status;            /* bm_status of this RHS */
+    int32_t iterations;        /* PCG iterations (inner iterations summed in mixed mode) */
+    int32_t outer_iterations;  /* refinement steps (mixed mode; 0 for FP64) */
+    int32_t reserved;
+    double rel_residual;       /* ||b - A x||_2 / ||b||_2, recomputed with the FP64 operator */
+} bm_solve_info;
+
+/* ---------------------------------------------------------------- errors */
+
+/* Static text of a status code. */
+const char* bm_status_string(bm_status s);
+/* Message of the last failed call on this thread ("" if none). */
+const char* bm_last_error(void);
+/* Library version string. */
+const char* bm_version(void);
+
+/* --------------------------------------------------------------- context */
+
+/* Bind the library to CUDA device `device` and stream `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  The stream is
+ * borrowed: the caller keeps it alive until bm_context_destroy. */
+bm_status bm_context_create(int device, void* cuda_stream, bm_context** out);
+void bm_context_destroy(bm_context* ctx);
+
+/* Kernel timing: when enabled, the library brackets its main kernels with
+ * CUDA events on the context stream and accumulates per-kernel device time.
+ * bm_context_kernel_time returns the accumulated milliseconds and launch
+ * count of the kernel family `name` ("matvec_white_f32", "matvec_white_f64",
+ * "toeplitz_f32", "toeplitz_f64", "rhs", "ingest", "blocks") and resets it. */
+bm_status bm_context_set_timing(bm_context* ctx, int enable);
+bm_status bm_context_kernel_time(bm_context* ctx, const char* name, double* total_ms,
+                                 int64_t* launches);
+
+/* ------------------------------------------------------------- pixelisation */
+
+/* HEALPix RING index of n directions (Gorski et al. 2005; the paper's "sky
+ * pixel", Sec. II): z = cos(theta) in [-1, 1], phi in [0, 2 pi), both device
+ * FP64 [n]; pix device int32 [n].  Computed with correctly rounded FP64
+ * operations in a fixed order (no fused multiply-add), so the integers match
+ * any other implementation of the same steps bit for bit.  nside in
+ * [1, 8192]. */
+bm_status bm_ang2pix_ring(bm_context* ctx, int64_t nside, int64_t n, const double* z,
+                          const double* phi, int32_t* pix);
+
+/* -------------------------------------------------------------- pointing */
+
+/* Pointing matrix P (Eq. 8) and its precomputed elements (the paper's
+ * ProcessTimeSamples, Sec. III-A item 1): pix device int32 [nsamples]
+ * (-1 = flagged), psi device [nsamples] of dtype psi_dtype (the polarisation
+ * angle theta of Eq. 2, radians).  The handle keeps the pixel-sorted sample
+ * permutation, CSR offsets, hit counts and cos/sin 2psi stored as FP32
+ * (hi, lo) pairs whose sum carries the FP64 value to 2^-48.
+ * Requires 1 <= npix <= 2^28, 1 <= nsamples < 2^32.  A pixel index outside
+ * [-1, npix) returns BM_ERR_INVALID. */
+bm_status bm_pointing_create(bm_context* ctx, int64_t npix, int64_t nsamples, const int32_t* pix,
+                             const void* psi, bm_dtype psi_dtype, bm_solver_type solver,
+                             bm_pointing** out);
+void bm_pointing_destroy(bm_pointing* p);
+/* hits device int32 [npix]: samples per pixel (flagged samples excluded). */
+bm_status bm_pointing_get_hits(const bm_pointing* p, int32_t* hits);
+/* y = P x (the paper's PointingLO): x device FP64 [npix][ncomp], y device
+ * FP64 [nsamples]; every non-flagged sample, no mask.  FP64 arithmetic. */
+bm_status bm_pointing_apply(bm_pointing* p, const double* x, double* y);
+/* x = P^T y (PointingLO.T): y device FP64 [nsamples], x device FP64
+ * [npix][ncomp].  Deterministic (pixel-sorted segmented sums, no atomics). */
+bm_status bm_pointing_apply_transpose(bm_pointing* p, const double* y, double* x);
+
+/* ---------------------------------------------------------- inverse noise */
+
+/* Diagonal white N^-1 (the paper's InvNoiseCovUnCorr): inv_var host FP64
+ * [ndet] = 1/sigma_d^2 > 0, det_offsets host int64 [ndet+1], increasing,
+ * det_offsets[0] = 0. */
+bm_status bm_inv_noise_create_diag(bm_context* ctx, int32_t ndet, const int64_t* det_offsets,
+                                   const double* inv_var, bm_inv_noise** out);
+/* Banded symmetric Toeplitz N^-1 applied chunk by chunk: each detector's
+ * samples are cut into chunks of chunk_len (the last one may be shorter) and
+ *   z_t = c_0 y_t + sum_{k=1}^{nlags-1} c_k (y_{t-k} + y_{t+k}),
+ * with y = 0 outside the chunk.  coeffs host FP64 [ndet][nlags];
+ * white_inv_var host FP64 [ndet] is diag(N)^-1 of Eq. 7 for the
+ * preconditioner.  1 <= nlags <= 1024, chunk_len >= 1. */
+bm_status bm_inv_noise_create_toeplitz(bm_context* ctx, int32_t ndet, const int64_t* det_offsets,
+                                       int64_t chunk_len, int32_t nlags, const double* coeffs,
+                                       const double* white_inv_var, bm_inv_noise** out);
+void bm_inv_noise_destroy(bm_inv_noise* n);
+/* z = N^-1 y in FP64: y, z device FP64 [nsamples]. */
+bm_status bm_inv_noise_apply(bm_inv_noise* n, const double* y, double* z);
+
+/* --------------------------------------------------------- preconditioner */
+
+/* Block-diagonal preconditioner of Eq. 7 with the pixel mask: the blocks
+ * B_p = sum_{t in p} w_d(t) v_t v_t^T (w = the noise's white level) are
+ * accumulated in FP64; a pixel is masked when hits < min_hits, or, for QU
+ * and IQU, when lambda_min(B_p) <= 0 or lambda_max/lambda_min > max_cond
+ * (strict); M_p = B_p^-1 on kept pixels.  Masked pixels leave the solve.
+ * p and n must describe the same samples (same context). */
+bm_status bm_blockdiag_precond_create(bm_pointing* p, bm_inv_noise* n, int32_t min_hits,
+                                      double max_cond, bm_precond** out);
+void bm_precond_destroy(bm_precond* pc);
+/* mask device uint8 [npix] (1 = masked), hits device int32 [npix]; either may be NULL. */
+bm_status bm_precond_get_mask(const bm_precond* pc, uint8_t* mask, int32_t* hits);
+/* blocks device FP64 [npix][ncomp][ncomp]: B_p (not inverted); cond device
+ * FP64 [npix] (inf where lambda_min <= 0, 0 for empty pixels).  Either may be NULL. */
+bm_status bm_precond_get_blocks(const bm_precond* pc, double* blocks, double* cond);
+/* z = M r per pixel (zero on masked pixels): r, z device FP64 [npix][ncomp]. */
+bm_status bm_precond_apply(bm_precond* pc, const double* r, double* z);
+
+/* ------------------------------------------------------------ the system */
+
+/* b = P^T N^-1 d_m (Eq. 6) where d_m is d with the samples of flagged or
+ * masked pixels set to 0: tod device [nrhs][nsamples] of dtype tod_dtype,
+ * b device FP64 [nrhs][npix][ncomp].  FP64 arithmetic, deterministic. */
+bm_status bm_rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod,
+                 bm_dtype tod_dtype, int32_t nrhs, double* b);
+
+/* q = A x = P^T N^-1 P x on kept pixels (zero on masked ones): x, q device
+ * FP64 [npix][ncomp].  BM_PREC_FP64: FP64 products and sums.  BM_PREC_MIXED:
+ * FP32 per-sample products and filter, FP64 per-pixel accumulation (the
+ * operator the inner solve of the mixed path uses).  White noise streams the
+ * samples in pixel-sorted order; Toeplitz noise gathers in time order,
+ * filters each chunk, and reduces in pixel-sorted order.  Deterministic. */
+bm_status bm_matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, double* q,
+                    bm_precision prec);
+
+/* GLS maps by block-preconditioned CG (Eq. 5-7): tod device [nrhs][nsamples]
+ * (tod_dtype), map_out device FP64 [nrhs][npix][ncomp] (NaN on masked
+ * pixels).  x0 = 0; stops when ||b - A x||_2 <= tol ||b||_2 (per RHS) or
+ * after maxiter PCG iterations (maxiter counts inner iterations in mixed
+ * mode).  info host [nrhs] (may be NULL).  Returns BM_OK when every RHS
+ * converged, otherwise the first non-OK per-RHS status. */
+bm_status bm_pcg_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod,
+                       bm_dtype tod_dtype, int32_t nrhs, double* map_out, double tol,
+                       int32_t maxiter, bm_precision prec, bm_solve_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BRAHMAP_H */

@@ -1,0 +1,284 @@
+"""ctypes binding of ``libbrahmap.so`` (include/brahmap.h), same names as the C-ABI.
+
+Argument marshalling only: device arrays are passed as torch CUDA tensors
+(their ``data_ptr()``), host arrays as numpy arrays, and a non-OK status is
+raised as :class:`BrahmapError` carrying ``bm_last_error()``.  Every step of
+the computation runs in the library's CUDA kernels; there is no Python or
+CPU fallback, and importing this module fails if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbrahmap.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "brahmap.h")
+
+BM_OK, BM_ERR_INVALID, BM_ERR_OOM, BM_ERR_CUDA = 0, 1, 2, 3
+BM_ERR_NOT_CONVERGED, BM_ERR_BREAKDOWN, BM_ERR_TIMEOUT, BM_ERR_BUSY, BM_ERR_NOT_FOUND = 4, 5, 6, 7, 8
+BM_SOLVER_I, BM_SOLVER_QU, BM_SOLVER_IQU = 1, 2, 3
+BM_F32, BM_F64 = 0, 1
+BM_PREC_FP64, BM_PREC_MIXED = 0, 1
+
+
+class BrahmapError(RuntimeError):
+    def __init__(self, status: int, func: str, msg: str):
+        super().__init__(f"{func}: {status_string(status)} ({status}): {msg}")
+        self.status = status
+
+
+class bm_solve_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("outer_iterations", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("rel_residual", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_2501_16122_gb300.build.build()")
+lib = ctypes.CDLL(LIB_PATH)
+
+_P = ctypes.c_void_p
+_PP = ctypes.POINTER(ctypes.c_void_p)
+_i32, _i64, _f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+
+_SIGS = {
+    "bm_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "bm_last_error": ([], ctypes.c_char_p),
+    "bm_version": ([], ctypes.c_char_p),
+    "bm_context_create": ([ctypes.c_int, _P, _PP], ctypes.c_int),
+    "bm_context_destroy": ([_P], None),
+    "bm_context_set_timing": ([_P, ctypes.c_int], ctypes.c_int),
+    "bm_context_kernel_time": ([_P, ctypes.c_char_p, ctypes.POINTER(_f64), ctypes.POINTER(_i64)], ctypes.c_int),
+    "bm_ang2pix_ring": ([_P, _i64, _i64, _P, _P, _P], ctypes.c_int),
+    "bm_pointing_create": ([_P, _i64, _i64, _P, _P, ctypes.c_int, ctypes.c_int, _PP], ctypes.c_int),
+    "bm_pointing_destroy": ([_P], None),
+    "bm_pointing_get_hits": ([_P, _P], ctypes.c_int),
+    "bm_pointing_apply": ([_P, _P, _P], ctypes.c_int),
+    "bm_pointing_apply_transpose": ([_P, _P, _P], ctypes.c_int),
+    "bm_inv_noise_create_diag": ([_P, _i32, _P, _P, _PP], ctypes.c_int),
+    "bm_inv_noise_create_toeplitz": ([_P, _i32, _P, _i64, _i32, _P, _P, _PP], ctypes.c_int),
+    "bm_inv_noise_destroy": ([_P], None),
+    "bm_inv_noise_apply": ([_P, _P, _P], ctypes.c_int),
+    "bm_blockdiag_precond_create": ([_P, _P, _i32, _f64, _PP], ctypes.c_int),
+    "bm_precond_destroy": ([_P], None),
+    "bm_precond_get_mask": ([_P, _P, _P], ctypes.c_int),
+    "bm_precond_get_blocks": ([_P, _P, _P], ctypes.c_int),
+    "bm_precond_apply": ([_P, _P, _P], ctypes.c_int),
+    "bm_rhs": ([_P, _P, _P, _P, ctypes.c_int, _i32, _P], ctypes.c_int),
+    "bm_matvec": ([_P, _P, _P, _P, _P, ctypes.c_int], ctypes.c_int),
+    "bm_pcg_solve": ([_P, _P, _P, _P, ctypes.c_int, _i32, _P, _f64, _i32, ctypes.c_int,
+                      ctypes.POINTER(bm_solve_info)], ctypes.c_int),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/brahmap.h."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bm_[a-z0-9_]+)\s*\(", text)))
+
+
+def status_string(s: int) -> str:
+    return lib.bm_status_string(int(s)).decode()
+
+
+def bm_last_error() -> str:
+    return lib.bm_last_error().decode()
+
+
+def bm_version() -> str:
+    return lib.bm_version().decode()
+
+
+def _check(status: int, func: str):
+    if status != BM_OK:
+        raise BrahmapError(status, func, bm_last_error())
+
+
+def _dev(t, dtype=None, name="array"):
+    """Device pointer of a contiguous CUDA tensor (optionally of a given dtype)."""
+    if t is None:
+        return None
+    if not getattr(t, "is_cuda", False):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.float32:
+        return BM_F32
+    if t.dtype == torch.float64:
+        return BM_F64
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+# ---------------------------------------------------------------- context
+def bm_context_create(device: int = 0, stream=None):
+    """stream: a torch.cuda.Stream (default: the current stream of `device`)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    out = ctypes.c_void_p()
+    _check(lib.bm_context_create(int(device), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(out)),
+           "bm_context_create")
+    return out
+
+
+def bm_context_destroy(ctx):
+    lib.bm_context_destroy(ctx)
+
+
+def bm_context_set_timing(ctx, enable: bool):
+    _check(lib.bm_context_set_timing(ctx, int(bool(enable))), "bm_context_set_timing")
+
+
+def bm_context_kernel_time(ctx, name: str):
+    ms, n = _f64(), _i64()
+    _check(lib.bm_context_kernel_time(ctx, name.encode(), ctypes.byref(ms), ctypes.byref(n)),
+           "bm_context_kernel_time")
+    return ms.value, n.value
+
+
+# ------------------------------------------------------------ pixelisation
+def bm_ang2pix_ring(ctx, nside: int, z, phi, pix):
+    import torch
+    _check(lib.bm_ang2pix_ring(ctx, int(nside), z.numel(), _dev(z, torch.float64, "z"),
+                               _dev(phi, torch.float64, "phi"), _dev(pix, torch.int32, "pix")),
+           "bm_ang2pix_ring")
+
+
+# ---------------------------------------------------------------- pointing
+def bm_pointing_create(ctx, npix: int, pix, psi, solver: int = BM_SOLVER_IQU):
+    import torch
+    out = ctypes.c_void_p()
+    _check(lib.bm_pointing_create(ctx, int(npix), pix.numel(), _dev(pix, torch.int32, "pix"),
+                                  _dev(psi, None, "psi"), _dtype_code(psi), int(solver), ctypes.byref(out)),
+           "bm_pointing_create")
+    return out
+
+
+def bm_pointing_destroy(p):
+    lib.bm_pointing_destroy(p)
+
+
+def bm_pointing_get_hits(p, hits):
+    import torch
+    _check(lib.bm_pointing_get_hits(p, _dev(hits, torch.int32, "hits")), "bm_pointing_get_hits")
+
+
+def bm_pointing_apply(p, x, y):
+    import torch
+    _check(lib.bm_pointing_apply(p, _dev(x, torch.float64, "x"), _dev(y, torch.float64, "y")),
+           "bm_pointing_apply")
+
+
+def bm_pointing_apply_transpose(p, y, x):
+    import torch
+    _check(lib.bm_pointing_apply_transpose(p, _dev(y, torch.float64, "y"), _dev(x, torch.float64, "x")),
+           "bm_pointing_apply_transpose")
+
+
+# ----------------------------------------------------------- inverse noise
+def bm_inv_noise_create_diag(ctx, det_offsets, inv_var):
+    off, offp = _host(det_offsets, np.int64)
+    iv, ivp = _host(inv_var, np.float64)
+    out = ctypes.c_void_p()
+    _check(lib.bm_inv_noise_create_diag(ctx, off.size - 1, offp, ivp, ctypes.byref(out)),
+           "bm_inv_noise_create_diag")
+    return out
+
+
+def bm_inv_noise_create_toeplitz(ctx, det_offsets, chunk_len: int, coeffs, white_inv_var):
+    off, offp = _host(det_offsets, np.int64)
+    c, cp = _host(coeffs, np.float64)
+    wv, wvp = _host(white_inv_var, np.float64)
+    out = ctypes.c_void_p()
+    _check(lib.bm_inv_noise_create_toeplitz(ctx, off.size - 1, offp, int(chunk_len), c.shape[-1], cp, wvp,
+                                            ctypes.byref(out)), "bm_inv_noise_create_toeplitz")
+    return out
+
+
+def bm_inv_noise_destroy(n):
+    lib.bm_inv_noise_destroy(n)
+
+
+def bm_inv_noise_apply(n, y, z):
+    import torch
+    _check(lib.bm_inv_noise_apply(n, _dev(y, torch.float64, "y"), _dev(z, torch.float64, "z")),
+           "bm_inv_noise_apply")
+
+
+# ---------------------------------------------------------- preconditioner
+def bm_blockdiag_precond_create(p, n, min_hits: int = 3, max_cond: float = 1e3):
+    out = ctypes.c_void_p()
+    _check(lib.bm_blockdiag_precond_create(p, n, int(min_hits), float(max_cond), ctypes.byref(out)),
+           "bm_blockdiag_precond_create")
+    return out
+
+
+def bm_precond_destroy(pc):
+    lib.bm_precond_destroy(pc)
+
+
+def bm_precond_get_mask(pc, mask=None, hits=None):
+    import torch
+    _check(lib.bm_precond_get_mask(pc, _dev(mask, torch.uint8, "mask"), _dev(hits, torch.int32, "hits")),
+           "bm_precond_get_mask")
+
+
+def bm_precond_get_blocks(pc, blocks=None, cond=None):
+    import torch
+    _check(lib.bm_precond_get_blocks(pc, _dev(blocks, torch.float64, "blocks"), _dev(cond, torch.float64, "cond")),
+           "bm_precond_get_blocks")
+
+
+def bm_precond_apply(pc, r, z):
+    import torch
+    _check(lib.bm_precond_apply(pc, _dev(r, torch.float64, "r"), _dev(z, torch.float64, "z")), "bm_precond_apply")
+
+
+# ---------------------------------------------------------------- system
+def bm_rhs(p, n, pc, tod, nrhs: int, b):
+    import torch
+    _check(lib.bm_rhs(p, n, pc, _dev(tod, None, "tod"), _dtype_code(tod), int(nrhs), _dev(b, torch.float64, "b")),
+           "bm_rhs")
+
+
+def bm_matvec(p, n, pc, x, q, prec: int = BM_PREC_FP64):
+    import torch
+    _check(lib.bm_matvec(p, n, pc, _dev(x, torch.float64, "x"), _dev(q, torch.float64, "q"), int(prec)),
+           "bm_matvec")
+
+
+def bm_pcg_solve(p, n, pc, tod, nrhs: int, map_out, tol: float, maxiter: int, prec: int = BM_PREC_FP64,
+                 raise_on_error: bool = True):
+    """Returns (status, [info dict per RHS])."""
+    import torch
+    infos = (bm_solve_info * int(nrhs))()
+    st = lib.bm_pcg_solve(p, n, pc, _dev(tod, None, "tod"), _dtype_code(tod), int(nrhs),
+                          _dev(map_out, torch.float64, "map_out"), float(tol), int(maxiter), int(prec), infos)
+    if raise_on_error and st not in (BM_OK, BM_ERR_NOT_CONVERGED):
+        _check(st, "bm_pcg_solve")
+    return st, [i.as_dict() for i in infos]

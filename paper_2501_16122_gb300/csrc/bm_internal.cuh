@@ -1,0 +1,249 @@
+// Internal declarations of the GB300 GLS map-making library: handle layouts,
+// error plumbing, device helpers and the launch wrappers shared between
+// translation units.  Nothing here is part of the C-ABI (include/brahmap.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/brahmap.h"
+
+namespace bm {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+void clear_error();
+
+struct Error {
+    bm_status status;
+};
+
+#define BM_CUDA(call)                                                                       \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            ::bm::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                            __LINE__);                                                      \
+            throw ::bm::Error{e_ == cudaErrorMemoryAllocation ? BM_ERR_OOM : BM_ERR_CUDA};  \
+        }                                                                                   \
+    } while (0)
+
+#define BM_REQUIRE(cond, ...)                 \
+    do {                                      \
+        if (!(cond)) {                        \
+            ::bm::set_error(__VA_ARGS__);     \
+            throw ::bm::Error{BM_ERR_INVALID}; \
+        }                                     \
+    } while (0)
+
+#define BM_LAUNCH_CHECK() BM_CUDA(cudaGetLastError())
+
+// Device allocation that throws BM_ERR_OOM and is released by DevBuf's destructor.
+template <typename T>
+struct DevBuf {
+    T* ptr = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    explicit DevBuf(size_t count) { alloc(count); }
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept : ptr(o.ptr), n(o.n) { o.ptr = nullptr; o.n = 0; }
+    DevBuf& operator=(DevBuf&& o) noexcept {
+        if (this != &o) { release(); ptr = o.ptr; n = o.n; o.ptr = nullptr; o.n = 0; }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void alloc(size_t count) {
+        release();
+        if (count == 0) return;
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+            throw Error{BM_ERR_OOM};
+        }
+        ptr = static_cast<T*>(p);
+        n = count;
+    }
+    void release() {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        n = 0;
+    }
+    T* get() const { return ptr; }
+};
+
+// Per-kernel-family device time, measured with events on the context stream.
+struct KernelTimer {
+    double total_ms = 0.0;
+    int64_t launches = 0;
+};
+
+}  // namespace bm
+
+// ----------------------------------------------------------------- handles
+struct bm_context {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    bool timing = false;
+    std::map<std::string, bm::KernelTimer> timers;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double* h_pinned = nullptr;  // small pinned host buffer for scalar reads
+    std::map<std::string, bm::DevBuf<char>> ws;  // named grow-only scratch buffers
+};
+
+struct bm_pointing {
+    bm_context* ctx = nullptr;
+    int64_t npix = 0, nsamples = 0, nvalid = 0;
+    int ncomp = 3;
+    bm::DevBuf<int32_t> pix;       // [nsamples] time order, -1 = flagged
+    bm::DevBuf<float2> cs_hi_t;    // [nsamples] (cos 2psi, sin 2psi) rounded to FP32
+    bm::DevBuf<float2> cs_lo_t;    // [nsamples] FP64 value minus hi, rounded to FP32
+    bm::DevBuf<uint32_t> perm;     // [nvalid] sample index, pixel-sorted (stable)
+    bm::DevBuf<int64_t> off;       // [npix + 1] CSR offsets into perm
+    bm::DevBuf<int32_t> hits;      // [npix]
+    bm::DevBuf<float2> cs_hi_s;    // [nvalid] trig in pixel-sorted order
+    bm::DevBuf<float2> cs_lo_s;
+};
+
+struct bm_inv_noise {
+    bm_context* ctx = nullptr;
+    int kind = 0;  // 0 = diagonal white, 1 = banded Toeplitz
+    int ndet = 0;
+    int64_t nsamples = 0;
+    std::vector<int64_t> h_det_off;
+    std::vector<double> h_white;   // diag(N)^-1 per detector (the white level)
+    bm::DevBuf<int64_t> det_off;   // [ndet + 1]
+    bm::DevBuf<double> white;      // [ndet]
+    // Toeplitz
+    int64_t chunk_len = 0;
+    int nlags = 0;
+    bm::DevBuf<double> coeffs64;   // [ndet][nlags]
+    bm::DevBuf<float> coeffs32;    // [ndet][nlags]
+};
+
+struct bm_precond {
+    bm_context* ctx = nullptr;
+    bm_pointing* p = nullptr;
+    bm_inv_noise* n = nullptr;
+    int ncomp = 3, nsym = 6;
+    int32_t min_hits = 3;
+    double max_cond = 1e3;
+    int64_t nkept = 0;
+    bm::DevBuf<double> B;          // [npix][ncomp*ncomp] full symmetric block
+    bm::DevBuf<double> Minv;       // [npix][ncomp*ncomp]
+    bm::DevBuf<double> cond;       // [npix]
+    bm::DevBuf<uint8_t> mask;      // [npix]
+    // Work items: pieces (<= item_max samples) of kept pixels' sorted segments.
+    int64_t nitems = 0;
+    bm::DevBuf<int32_t> item_pix;  // [nitems]
+    bm::DevBuf<int64_t> item_beg;  // [nitems]
+    bm::DevBuf<int32_t> item_len;  // [nitems]
+    bm::DevBuf<int64_t> pitem;     // [npix + 1] CSR: items of pixel p
+    // White noise: weighted sorted stream sqrt(w) (cos, sin) (or w for I-only).
+    bm::DevBuf<float2> wcs;        // [nvalid]
+    bm::DevBuf<float> w1;          // [nvalid] (I-only)
+};
+
+namespace bm {
+
+constexpr int kItemMax = 4096;  // max samples per work item
+
+// Named grow-only scratch buffer owned by the context (released with it).
+void* workspace(bm_context* ctx, const char* name, size_t bytes);
+template <typename T>
+T* workspace_as(bm_context* ctx, const char* name, size_t count) {
+    return static_cast<T*>(workspace(ctx, name, count * sizeof(T)));
+}
+
+// Work items: pieces of <= kItemMax consecutive samples of one pixel's
+// pixel-sorted segment, for every non-empty pixel (mask == NULL) or every
+// kept pixel; pitem[p] .. pitem[p+1] are pixel p's items, in order.
+struct Items {
+    int64_t n = 0;
+    DevBuf<int32_t> pix;
+    DevBuf<int64_t> beg;
+    DevBuf<int32_t> len;
+    DevBuf<int64_t> pitem;  // [npix + 1]
+};
+void plan_items(bm_context* ctx, const int64_t* off, const uint8_t* mask, int64_t npix, Items& it);
+
+// Device-wide exclusive scans.
+void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
+void exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s);
+
+// Deterministic FP64 reductions with a fixed grid: out = sum_i a_i b_i.
+constexpr int kRedBlocks = 512;
+constexpr int kRedThreads = 256;
+
+// Timing helpers
+struct ScopedTimer {
+    bm_context* ctx;
+    const char* name;
+    ScopedTimer(bm_context* c, const char* n);
+    ~ScopedTimer();
+};
+
+// Launch wrappers implemented in the .cu files.
+void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dtype);
+void build_precond(bm_precond* pc);
+void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, double* q,
+            bm_precision prec, int64_t nrhs);
+void rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dtype dt,
+         int64_t nrhs, double* b);
+void precond_apply(bm_precond* pc, const double* r, double* z, int64_t nrhs);
+void pointing_apply(bm_pointing* p, const double* x, double* y);
+void pointing_apply_transpose(bm_pointing* p, const double* y, double* x);
+void inv_noise_apply(bm_inv_noise* n, const double* y, double* z);
+void ang2pix_ring(bm_context* ctx, int64_t nside, int64_t n, const double* z, const double* phi,
+                  int32_t* pix);
+bm_status pcg_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod,
+                    bm_dtype dt, int32_t nrhs, double* map_out, double tol, int32_t maxiter,
+                    bm_precision prec, bm_solve_info* info);
+
+// Grid sizing: a multiple of the SM count.
+inline int grid_for(const bm_context* ctx, int64_t work_units, int per_sm = 8) {
+    int64_t g = (int64_t)ctx->num_sms * per_sm;
+    if (work_units < g) g = work_units > 0 ? work_units : 1;
+    return (int)g;
+}
+
+}  // namespace bm
+
+// ---------------------------------------------------------- device helpers
+#ifdef __CUDACC__
+namespace bm {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Index of the detector owning sample t: largest d with off[d] <= t.
+__device__ __forceinline__ int find_det(const int64_t* off, int ndet, int64_t t) {
+    int lo = 0, hi = ndet - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ double2 trig64(float2 hi, float2 lo) {
+    return make_double2((double)hi.x + (double)lo.x, (double)hi.y + (double)lo.y);
+}
+
+}  // namespace bm
+#endif

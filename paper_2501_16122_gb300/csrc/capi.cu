@@ -1,0 +1,461 @@
+// C-ABI entry points (include/brahmap.h): argument validation, handle
+// lifetime, error translation.  Every entry point catches the library's
+// internal bm::Error and returns its status; no exception crosses the ABI.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "bm_internal.cuh"
+
+namespace bm {
+
+static thread_local char g_last_error[1024] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+}
+void clear_error() { g_last_error[0] = '\0'; }
+
+ScopedTimer::ScopedTimer(bm_context* c, const char* n) : ctx(c), name(n) {
+    if (ctx && ctx->timing) cudaEventRecord(ctx->ev0, ctx->stream);
+}
+ScopedTimer::~ScopedTimer() {
+    if (ctx && ctx->timing) {
+        cudaEventRecord(ctx->ev1, ctx->stream);
+        if (cudaEventSynchronize(ctx->ev1) == cudaSuccess) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+            auto& t = ctx->timers[name];
+            t.total_ms += ms;
+            t.launches += 1;
+        }
+    }
+}
+
+void* workspace(bm_context* ctx, const char* name, size_t bytes) {
+    auto& b = ctx->ws[name];
+    if (b.n < bytes) {
+        BM_CUDA(cudaStreamSynchronize(ctx->stream));  // the old buffer may still be in use
+        b.alloc(bytes + bytes / 8);
+    }
+    return b.get();
+}
+
+}  // namespace bm
+
+using namespace bm;
+
+template <typename F>
+static bm_status guarded(F&& f) {
+    clear_error();
+    try {
+        return f();
+    } catch (const Error& e) {
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return BM_ERR_OOM;
+    } catch (...) {
+        set_error("unexpected internal error");
+        return BM_ERR_CUDA;
+    }
+}
+
+static void use_device(const bm_context* ctx) { BM_CUDA(cudaSetDevice(ctx->device)); }
+
+extern "C" {
+
+const char* bm_status_string(bm_status s) {
+    switch (s) {
+        case BM_OK: return "ok";
+        case BM_ERR_INVALID: return "invalid argument";
+        case BM_ERR_OOM: return "out of device memory";
+        case BM_ERR_CUDA: return "CUDA error";
+        case BM_ERR_NOT_CONVERGED: return "not converged";
+        case BM_ERR_BREAKDOWN: return "CG breakdown";
+        case BM_ERR_TIMEOUT: return "timeout";
+        case BM_ERR_BUSY: return "busy";
+        case BM_ERR_NOT_FOUND: return "not found";
+    }
+    return "unknown status";
+}
+
+const char* bm_last_error(void) { return g_last_error; }
+const char* bm_version(void) { return "brahmap-gb300 0.1 (sm_103a)"; }
+
+bm_status bm_context_create(int device, void* cuda_stream, bm_context** out) {
+    return guarded([&] {
+        BM_REQUIRE(out != nullptr, "out is NULL");
+        *out = nullptr;
+        int ndev = 0;
+        BM_CUDA(cudaGetDeviceCount(&ndev));
+        BM_REQUIRE(device >= 0 && device < ndev, "device %d out of range [0, %d)", device, ndev);
+        BM_CUDA(cudaSetDevice(device));
+        auto* ctx = new bm_context();
+        ctx->device = device;
+        ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+        cudaError_t e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+        if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
+        if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
+        if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_pinned, 4096);
+        if (e != cudaSuccess) {
+            set_error("context setup failed: %s", cudaGetErrorString(e));
+            bm_context_destroy(ctx);
+            return BM_ERR_CUDA;
+        }
+        *out = ctx;
+        return BM_OK;
+    });
+}
+
+void bm_context_destroy(bm_context* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    delete ctx;
+}
+
+bm_status bm_context_set_timing(bm_context* ctx, int enable) {
+    return guarded([&] {
+        BM_REQUIRE(ctx, "ctx is NULL");
+        ctx->timing = enable != 0;
+        return BM_OK;
+    });
+}
+
+bm_status bm_context_kernel_time(bm_context* ctx, const char* name, double* total_ms,
+                                 int64_t* launches) {
+    return guarded([&] {
+        BM_REQUIRE(ctx && name, "ctx/name is NULL");
+        auto it = ctx->timers.find(name);
+        double ms = 0.0;
+        int64_t n = 0;
+        if (it != ctx->timers.end()) {
+            ms = it->second.total_ms;
+            n = it->second.launches;
+            ctx->timers.erase(it);
+        }
+        if (total_ms) *total_ms = ms;
+        if (launches) *launches = n;
+        return BM_OK;
+    });
+}
+
+bm_status bm_ang2pix_ring(bm_context* ctx, int64_t nside, int64_t n, const double* z,
+                          const double* phi, int32_t* pix) {
+    return guarded([&] {
+        BM_REQUIRE(ctx, "ctx is NULL");
+        BM_REQUIRE(nside >= 1 && nside <= 8192, "nside %lld out of [1, 8192]", (long long)nside);
+        BM_REQUIRE(n >= 0, "n < 0");
+        if (n == 0) return BM_OK;
+        BM_REQUIRE(z && phi && pix, "NULL array");
+        use_device(ctx);
+        ang2pix_ring(ctx, nside, n, z, phi, pix);
+        BM_CUDA(cudaStreamSynchronize(ctx->stream));
+        return BM_OK;
+    });
+}
+
+bm_status bm_pointing_create(bm_context* ctx, int64_t npix, int64_t nsamples, const int32_t* pix,
+                             const void* psi, bm_dtype psi_dtype, bm_solver_type solver,
+                             bm_pointing** out) {
+    return guarded([&] {
+        BM_REQUIRE(ctx && out, "ctx/out is NULL");
+        *out = nullptr;
+        BM_REQUIRE(npix >= 1 && npix <= (int64_t(1) << 28), "npix %lld out of [1, 2^28]", (long long)npix);
+        BM_REQUIRE(nsamples >= 1 && nsamples < (int64_t(1) << 32), "nsamples out of [1, 2^32)");
+        BM_REQUIRE(pix && psi, "pix/psi is NULL");
+        BM_REQUIRE(psi_dtype == BM_F32 || psi_dtype == BM_F64, "bad psi dtype");
+        BM_REQUIRE(solver == BM_SOLVER_I || solver == BM_SOLVER_QU || solver == BM_SOLVER_IQU,
+                   "bad solver type %d", (int)solver);
+        use_device(ctx);
+        auto* p = new bm_pointing();
+        p->ctx = ctx;
+        p->npix = npix;
+        p->nsamples = nsamples;
+        p->ncomp = (int)solver;
+        try {
+            ingest(p, pix, psi, psi_dtype);
+        } catch (...) {
+            delete p;
+            throw;
+        }
+        *out = p;
+        return BM_OK;
+    });
+}
+
+void bm_pointing_destroy(bm_pointing* p) {
+    if (!p) return;
+    cudaSetDevice(p->ctx->device);
+    cudaStreamSynchronize(p->ctx->stream);
+    delete p;
+}
+
+bm_status bm_pointing_get_hits(const bm_pointing* p, int32_t* hits) {
+    return guarded([&] {
+        BM_REQUIRE(p && hits, "NULL argument");
+        use_device(p->ctx);
+        BM_CUDA(cudaMemcpyAsync(hits, p->hits.get(), sizeof(int32_t) * p->npix,
+                                cudaMemcpyDeviceToDevice, p->ctx->stream));
+        BM_CUDA(cudaStreamSynchronize(p->ctx->stream));
+        return BM_OK;
+    });
+}
+
+bm_status bm_pointing_apply(bm_pointing* p, const double* x, double* y) {
+    return guarded([&] {
+        BM_REQUIRE(p && x && y, "NULL argument");
+        use_device(p->ctx);
+        pointing_apply(p, x, y);
+        BM_CUDA(cudaStreamSynchronize(p->ctx->stream));
+        return BM_OK;
+    });
+}
+
+bm_status bm_pointing_apply_transpose(bm_pointing* p, const double* y, double* x) {
+    return guarded([&] {
+        BM_REQUIRE(p && x && y, "NULL argument");
+        use_device(p->ctx);
+        pointing_apply_transpose(p, y, x);
+        BM_CUDA(cudaStreamSynchronize(p->ctx->stream));
+        return BM_OK;
+    });
+}
+
+static void check_det_offsets(int32_t ndet, const int64_t* det_offsets) {
+    BM_REQUIRE(ndet >= 1 && ndet <= (1 << 20), "ndet %d out of [1, 2^20]", ndet);
+    BM_REQUIRE(det_offsets != nullptr, "det_offsets is NULL");
+    BM_REQUIRE(det_offsets[0] == 0, "det_offsets[0] must be 0");
+    for (int d = 0; d < ndet; ++d)
+        BM_REQUIRE(det_offsets[d + 1] > det_offsets[d], "det_offsets not increasing at %d", d);
+}
+
+static bm_inv_noise* new_noise(bm_context* ctx, int32_t ndet, const int64_t* det_offsets,
+                               const double* white) {
+    auto* n = new bm_inv_noise();
+    n->ctx = ctx;
+    n->ndet = ndet;
+    n->nsamples = det_offsets[ndet];
+    n->h_det_off.assign(det_offsets, det_offsets + ndet + 1);
+    n->h_white.assign(white, white + ndet);
+    try {
+        n->det_off.alloc(ndet + 1);
+        n->white.alloc(ndet);
+        BM_CUDA(cudaMemcpy(n->det_off.get(), det_offsets, sizeof(int64_t) * (ndet + 1),
+                           cudaMemcpyHostToDevice));
+        BM_CUDA(cudaMemcpy(n->white.get(), white, sizeof(double) * ndet, cudaMemcpyHostToDevice));
+    } catch (...) {
+        delete n;
+        throw;
+    }
+    return n;
+}
+
+bm_status bm_inv_noise_create_diag(bm_context* ctx, int32_t ndet, const int64_t* det_offsets,
+                                   const double* inv_var, bm_inv_noise** out) {
+    return guarded([&] {
+        BM_REQUIRE(ctx && out, "ctx/out is NULL");
+        *out = nullptr;
+        check_det_offsets(ndet, det_offsets);
+        BM_REQUIRE(inv_var != nullptr, "inv_var is NULL");
+        for (int d = 0; d < ndet; ++d)
+            BM_REQUIRE(inv_var[d] > 0 && inv_var[d] < 1e300, "inv_var[%d] not positive finite", d);
+        use_device(ctx);
+        *out = new_noise(ctx, ndet, det_offsets, inv_var);
+        (*out)->kind = 0;
+        return BM_OK;
+    });
+}
+
+bm_status bm_inv_noise_create_toeplitz(bm_context* ctx, int32_t ndet, const int64_t* det_offsets,
+                                       int64_t chunk_len, int32_t nlags, const double* coeffs,
+                                       const double* white_inv_var, bm_inv_noise** out) {
+    return guarded([&] {
+        BM_REQUIRE(ctx && out, "ctx/out is NULL");
+        *out = nullptr;
+        check_det_offsets(ndet, det_offsets);
+        BM_REQUIRE(chunk_len >= 1, "chunk_len < 1");
+        BM_REQUIRE(nlags >= 1 && nlags <= 1024, "nlags %d out of [1, 1024]", nlags);
+        BM_REQUIRE(coeffs && white_inv_var, "coeffs/white_inv_var is NULL");
+        for (int d = 0; d < ndet; ++d)
+            BM_REQUIRE(white_inv_var[d] > 0 && white_inv_var[d] < 1e300,
+                       "white_inv_var[%d] not positive finite", d);
+        for (int64_t i = 0; i < (int64_t)ndet * nlags; ++i)
+            BM_REQUIRE(coeffs[i] == coeffs[i] && coeffs[i] < 1e300 && coeffs[i] > -1e300,
+                       "coeffs[%lld] not finite", (long long)i);
+        use_device(ctx);
+        bm_inv_noise* n = new_noise(ctx, ndet, det_offsets, white_inv_var);
+        n->kind = 1;
+        n->chunk_len = chunk_len;
+        n->nlags = nlags;
+        try {
+            const size_t m = (size_t)ndet * nlags;
+            std::vector<float> c32(coeffs, coeffs + m);
+            n->coeffs64.alloc(m);
+            n->coeffs32.alloc(m);
+            BM_CUDA(cudaMemcpy(n->coeffs64.get(), coeffs, sizeof(double) * m, cudaMemcpyHostToDevice));
+            BM_CUDA(cudaMemcpy(n->coeffs32.get(), c32.data(), sizeof(float) * m, cudaMemcpyHostToDevice));
+        } catch (...) {
+            delete n;
+            throw;
+        }
+        *out = n;
+        return BM_OK;
+    });
+}
+
+void bm_inv_noise_destroy(bm_inv_noise* n) {
+    if (!n) return;
+    cudaSetDevice(n->ctx->device);
+    cudaStreamSynchronize(n->ctx->stream);
+    delete n;
+}
+
+bm_status bm_inv_noise_apply(bm_inv_noise* n, const double* y, double* z) {
+    return guarded([&] {
+        BM_REQUIRE(n && y && z, "NULL argument");
+        use_device(n->ctx);
+        inv_noise_apply(n, y, z);
+        BM_CUDA(cudaStreamSynchronize(n->ctx->stream));
+        return BM_OK;
+    });
+}
+
+bm_status bm_blockdiag_precond_create(bm_pointing* p, bm_inv_noise* n, int32_t min_hits,
+                                      double max_cond, bm_precond** out) {
+    return guarded([&] {
+        BM_REQUIRE(p && n && out, "NULL argument");
+        *out = nullptr;
+        BM_REQUIRE(p->ctx == n->ctx, "pointing and noise belong to different contexts");
+        BM_REQUIRE(n->nsamples == p->nsamples, "noise covers %lld samples, pointing %lld",
+                   (long long)n->nsamples, (long long)p->nsamples);
+        BM_REQUIRE(min_hits >= 0, "min_hits < 0");
+        BM_REQUIRE(max_cond >= 1.0, "max_cond < 1");
+        use_device(p->ctx);
+        auto* pc = new bm_precond();
+        pc->ctx = p->ctx;
+        pc->p = p;
+        pc->n = n;
+        pc->ncomp = p->ncomp;
+        pc->nsym = p->ncomp * (p->ncomp + 1) / 2;
+        pc->min_hits = min_hits;
+        pc->max_cond = max_cond;
+        try {
+            build_precond(pc);
+        } catch (...) {
+            delete pc;
+            throw;
+        }
+        *out = pc;
+        return BM_OK;
+    });
+}
+
+void bm_precond_destroy(bm_precond* pc) {
+    if (!pc) return;
+    cudaSetDevice(pc->ctx->device);
+    cudaStreamSynchronize(pc->ctx->stream);
+    delete pc;
+}
+
+bm_status bm_precond_get_mask(const bm_precond* pc, uint8_t* mask, int32_t* hits) {
+    return guarded([&] {
+        BM_REQUIRE(pc, "pc is NULL");
+        use_device(pc->ctx);
+        const int64_t npix = pc->p->npix;
+        if (mask)
+            BM_CUDA(cudaMemcpyAsync(mask, pc->mask.get(), npix, cudaMemcpyDeviceToDevice, pc->ctx->stream));
+        if (hits)
+            BM_CUDA(cudaMemcpyAsync(hits, pc->p->hits.get(), sizeof(int32_t) * npix,
+                                    cudaMemcpyDeviceToDevice, pc->ctx->stream));
+        BM_CUDA(cudaStreamSynchronize(pc->ctx->stream));
+        return BM_OK;
+    });
+}
+
+bm_status bm_precond_get_blocks(const bm_precond* pc, double* blocks, double* cond) {
+    return guarded([&] {
+        BM_REQUIRE(pc, "pc is NULL");
+        use_device(pc->ctx);
+        const int64_t npix = pc->p->npix;
+        if (blocks)
+            BM_CUDA(cudaMemcpyAsync(blocks, pc->B.get(), sizeof(double) * npix * pc->ncomp * pc->ncomp,
+                                    cudaMemcpyDeviceToDevice, pc->ctx->stream));
+        if (cond)
+            BM_CUDA(cudaMemcpyAsync(cond, pc->cond.get(), sizeof(double) * npix,
+                                    cudaMemcpyDeviceToDevice, pc->ctx->stream));
+        BM_CUDA(cudaStreamSynchronize(pc->ctx->stream));
+        return BM_OK;
+    });
+}
+
+bm_status bm_precond_apply(bm_precond* pc, const double* r, double* z) {
+    return guarded([&] {
+        BM_REQUIRE(pc && r && z, "NULL argument");
+        use_device(pc->ctx);
+        precond_apply(pc, r, z, 1);
+        BM_CUDA(cudaStreamSynchronize(pc->ctx->stream));
+        return BM_OK;
+    });
+}
+
+static void check_system(bm_pointing* p, bm_inv_noise* n, bm_precond* pc) {
+    BM_REQUIRE(p && n && pc, "NULL handle");
+    BM_REQUIRE(pc->p == p && pc->n->nsamples == n->nsamples && p->ctx == n->ctx,
+               "preconditioner was built for another pointing / sample layout");
+    BM_REQUIRE(n->nsamples == p->nsamples, "noise and pointing cover different sample counts");
+    if (n->kind == 0)
+        BM_REQUIRE(pc->n == n, "a white-noise system needs the preconditioner built from that noise");
+}
+
+bm_status bm_rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod,
+                 bm_dtype tod_dtype, int32_t nrhs, double* b) {
+    return guarded([&] {
+        check_system(p, n, pc);
+        BM_REQUIRE(tod && b, "NULL array");
+        BM_REQUIRE(tod_dtype == BM_F32 || tod_dtype == BM_F64, "bad tod dtype");
+        BM_REQUIRE(nrhs >= 1 && nrhs <= 4096, "nrhs out of [1, 4096]");
+        use_device(p->ctx);
+        rhs(p, n, pc, tod, tod_dtype, nrhs, b);
+        BM_CUDA(cudaStreamSynchronize(p->ctx->stream));
+        return BM_OK;
+    });
+}
+
+bm_status bm_matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, double* q,
+                    bm_precision prec) {
+    return guarded([&] {
+        check_system(p, n, pc);
+        BM_REQUIRE(x && q, "NULL array");
+        BM_REQUIRE(prec == BM_PREC_FP64 || prec == BM_PREC_MIXED, "bad precision");
+        use_device(p->ctx);
+        matvec(p, n, pc, x, q, prec, 1);
+        BM_CUDA(cudaStreamSynchronize(p->ctx->stream));
+        return BM_OK;
+    });
+}
+
+bm_status bm_pcg_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod,
+                       bm_dtype tod_dtype, int32_t nrhs, double* map_out, double tol,
+                       int32_t maxiter, bm_precision prec, bm_solve_info* info) {
+    return guarded([&] {
+        check_system(p, n, pc);
+        BM_REQUIRE(tod && map_out, "NULL array");
+        BM_REQUIRE(tod_dtype == BM_F32 || tod_dtype == BM_F64, "bad tod dtype");
+        BM_REQUIRE(nrhs >= 1 && nrhs <= 4096, "nrhs out of [1, 4096]");
+        BM_REQUIRE(tol > 0 && tol < 1, "tol out of (0, 1)");
+        BM_REQUIRE(maxiter >= 1, "maxiter < 1");
+        BM_REQUIRE(prec == BM_PREC_FP64 || prec == BM_PREC_MIXED, "bad precision");
+        use_device(p->ctx);
+        return pcg_solve(p, n, pc, tod, tod_dtype, nrhs, map_out, tol, maxiter, prec, info);
+    });
+}
+
+}  // extern "C"

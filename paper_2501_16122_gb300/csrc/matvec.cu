@@ -1,0 +1,580 @@
+// The operator A = P^T N^-1 P (paper Eq. 6) and the right-hand side
+// b = P^T N^-1 d, plus the individual operators P, P^T and N^-1.
+//
+// White noise (N^-1 diagonal, the paper's InvNoiseCovUnCorr): the matvec
+// streams the samples in pixel-sorted order.  One warp takes one work item
+// (<= kItemMax consecutive samples of one kept pixel p): it gathers
+// y_t = v_t . x_p, weights it, and accumulates w_t y_t v_t; the item partial
+// is written in FP64 and a per-pixel pass sums a pixel's items in item order.
+// No atomics, so every result is bitwise reproducible.
+//   FP32 form: reads the weighted stream u_t = sqrt(w) (cos 2psi, sin 2psi)
+//              (8 B/sample; sqrt(w) = |u_t|), FP32 products, FP32 lane sums,
+//              FP64 warp sums.
+//   FP64 form: reads perm, the FP32 (hi, lo) trig pairs and w_d (20 B/sample),
+//              FP64 products and sums.
+//
+// Toeplitz noise: time-ordered tiles of each chunk gather y = P x (masked and
+// flagged samples give 0), apply the banded filter from a shared-memory halo,
+// and write z; the scatter P^T z is the pixel-sorted gather-reduce
+// q_p = sum_{t in p} z_t v_t.
+#include "bm_internal.cuh"
+
+namespace bm {
+
+namespace {
+
+constexpr int kWarps = 8;  // warps per block in the warp-per-item kernels
+
+// x (FP64, [npix][NC]) -> FP32 copy with masked pixels zeroed.
+template <typename TO>
+__global__ void masked_copy_kernel(const double* __restrict__ x, const uint8_t* __restrict__ mask,
+                                   int64_t npix, int nc, TO* __restrict__ out) {
+    const int64_t n = npix * nc;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = mask[i / nc] ? TO(0) : TO(x[i]);
+}
+
+// ------------------------------------------------------- white, FP32 form
+template <int NC>
+__global__ void __launch_bounds__(kWarps * 32)
+white_matvec_f32_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ item_beg,
+                        const int32_t* __restrict__ item_len, int64_t nitems,
+                        const float2* __restrict__ wcs, const float* __restrict__ w1,
+                        const float* __restrict__ x32, double* __restrict__ partial) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+    for (int64_t k = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); k < nitems; k += nwarps) {
+        const int64_t p = item_pix[k];
+        const int64_t b = item_beg[k];
+        const int len = item_len[k];
+        if (NC == 1) {
+            const float xi = x32[p];
+            float acc = 0.f;
+            int i = lane;
+            for (; i + 96 < len; i += 128) {
+                const float a0 = __ldg(w1 + b + i), a1 = __ldg(w1 + b + i + 32);
+                const float a2 = __ldg(w1 + b + i + 64), a3 = __ldg(w1 + b + i + 96);
+                acc += (a0 + a1) + (a2 + a3);
+            }
+            for (; i < len; i += 32) acc += __ldg(w1 + b + i);
+            const double s = warp_sum((double)acc) * (double)xi;
+            if (lane == 0) partial[k] = s;
+        } else {
+            float xI = 0.f, xQ, xU;
+            if (NC == 3) { xI = x32[3 * p]; xQ = x32[3 * p + 1]; xU = x32[3 * p + 2]; }
+            else { xQ = x32[2 * p]; xU = x32[2 * p + 1]; }
+            float aI = 0.f, aQ = 0.f, aU = 0.f;
+            const float2* src = wcs + b;
+            auto step = [&](float2 u) {
+                // u = sqrt(w) (c, s); sqrt(w) = |u| carries the I column.
+                const float r = NC == 3 ? sqrtf(fmaf(u.x, u.x, u.y * u.y)) : 0.f;
+                const float y = fmaf(u.x, xQ, fmaf(u.y, xU, r * xI));
+                if (NC == 3) aI = fmaf(y, r, aI);
+                aQ = fmaf(y, u.x, aQ);
+                aU = fmaf(y, u.y, aU);
+            };
+            int i = lane;
+            for (; i + 96 < len; i += 128) {
+                const float2 u0 = __ldg(src + i), u1 = __ldg(src + i + 32);
+                const float2 u2 = __ldg(src + i + 64), u3 = __ldg(src + i + 96);
+                step(u0); step(u1); step(u2); step(u3);
+            }
+            for (; i < len; i += 32) step(__ldg(src + i));
+            const double sQ = warp_sum((double)aQ), sU = warp_sum((double)aU);
+            const double sI = NC == 3 ? warp_sum((double)aI) : 0.0;
+            if (lane == 0) {
+                if (NC == 3) { partial[3 * k] = sI; partial[3 * k + 1] = sQ; partial[3 * k + 2] = sU; }
+                else { partial[2 * k] = sQ; partial[2 * k + 1] = sU; }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------- white, FP64 form
+constexpr int kMaxDetSmem = 4096;
+
+template <int NC>
+__global__ void __launch_bounds__(kWarps * 32)
+white_matvec_f64_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ item_beg,
+                        const int32_t* __restrict__ item_len, int64_t nitems,
+                        const uint32_t* __restrict__ perm, const float2* __restrict__ hi,
+                        const float2* __restrict__ lo, const int64_t* __restrict__ det_off, int ndet,
+                        const double* __restrict__ white, const double* __restrict__ x,
+                        double* __restrict__ partial) {
+    __shared__ int64_t s_off[kMaxDetSmem + 1];
+    const bool in_smem = ndet <= kMaxDetSmem;
+    if (in_smem)
+        for (int d = threadIdx.x; d <= ndet; d += blockDim.x) s_off[d] = det_off[d];
+    __syncthreads();
+    const int64_t* offp = in_smem ? s_off : det_off;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+    for (int64_t k = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); k < nitems; k += nwarps) {
+        const int64_t p = item_pix[k];
+        const int64_t b = item_beg[k];
+        const int len = item_len[k];
+        double xv[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) xv[c] = x[NC * p + c];
+        double acc[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+        for (int i = lane; i < len; i += 32) {
+            const int64_t si = b + i;
+            const double w = white[find_det(offp, ndet, perm[si])];
+            if (NC == 1) {
+                acc[0] += w * xv[0];
+            } else {
+                const double2 cs = trig64(hi[si], lo[si]);
+                double y = cs.x * xv[NC - 2] + cs.y * xv[NC - 1];
+                if (NC == 3) y += xv[0];
+                const double wy = w * y;
+                if (NC == 3) acc[0] += wy;
+                acc[NC - 2] += wy * cs.x;
+                acc[NC - 1] += wy * cs.y;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = warp_sum(acc[c]);
+        if (lane == 0)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) partial[NC * k + c] = acc[c];
+    }
+}
+
+// ---------------------------------------------- pixel-sorted gather-reduce
+// q_p partial = sum over item samples of g[perm_i] * f * v_i, where
+// f = w_d(perm_i) when `white` is given, else 1.  G is float or double;
+// the trig is the FP64 (hi + lo) value when EXACT, else hi.
+template <int NC, typename G, bool EXACT>
+__global__ void __launch_bounds__(kWarps * 32)
+gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ item_beg,
+                     const int32_t* __restrict__ item_len, int64_t nitems,
+                     const uint32_t* __restrict__ perm, const float2* __restrict__ hi,
+                     const float2* __restrict__ lo, const G* __restrict__ g,
+                     const int64_t* __restrict__ det_off, int ndet, const double* __restrict__ white,
+                     double* __restrict__ partial) {
+    __shared__ int64_t s_off[kMaxDetSmem + 1];
+    const bool in_smem = white != nullptr && ndet <= kMaxDetSmem;
+    if (in_smem)
+        for (int d = threadIdx.x; d <= ndet; d += blockDim.x) s_off[d] = det_off[d];
+    __syncthreads();
+    const int64_t* offp = in_smem ? s_off : det_off;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+    for (int64_t k = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); k < nitems; k += nwarps) {
+        const int64_t b = item_beg[k];
+        const int len = item_len[k];
+        double acc[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+        for (int i = lane; i < len; i += 32) {
+            const int64_t si = b + i;
+            const uint32_t t = perm[si];
+            double val = (double)g[t];
+            if (white) val *= white[find_det(offp, ndet, t)];
+            if (NC == 1) {
+                acc[0] += val;
+            } else {
+                double c, s;
+                if (EXACT) { const double2 cs = trig64(hi[si], lo[si]); c = cs.x; s = cs.y; }
+                else { const float2 h = hi[si]; c = h.x; s = h.y; }
+                if (NC == 3) acc[0] += val;
+                acc[NC - 2] += val * c;
+                acc[NC - 1] += val * s;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = warp_sum(acc[c]);
+        if (lane == 0)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) partial[NC * k + c] = acc[c];
+    }
+}
+
+// q_p = sum of the partials of pixel p's items (item order); 0 for pixels without items.
+__global__ void finalize_pixels_kernel(const int64_t* __restrict__ pitem, const double* __restrict__ partial,
+                                       int64_t npix, int nc, double* __restrict__ q) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k0 = pitem[p], k1 = pitem[p + 1];
+        for (int c = 0; c < nc; ++c) {
+            double s = 0.0;
+            for (int64_t k = k0; k < k1; ++k) s += partial[k * nc + c];
+            q[p * nc + c] = s;
+        }
+    }
+}
+
+// ------------------------------------------------------- time-ordered work
+// y = P x over every non-flagged sample (FP64 trig).
+__global__ void pointing_apply_kernel(const int32_t* __restrict__ pix, const float2* __restrict__ hi,
+                                      const float2* __restrict__ lo, int64_t n, int nc,
+                                      const double* __restrict__ x, double* __restrict__ y) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p = pix[t];
+        double v = 0.0;
+        if (p >= 0) {
+            if (nc == 1) {
+                v = x[p];
+            } else {
+                const double2 cs = trig64(hi[t], lo[t]);
+                const double* xp = x + (int64_t)p * nc;
+                v = cs.x * xp[nc - 2] + cs.y * xp[nc - 1];
+                if (nc == 3) v += xp[0];
+            }
+        }
+        y[t] = v;
+    }
+}
+
+// --------------------------------------------------------- Toeplitz filter
+// Sample sources for the filter input y_t.
+struct SrcMatvecF32 {  // y_t = v_t . x32[p_t] (x32 zero on masked pixels), FP32 trig
+    const int32_t* pix; const float2* hi; const float* x; int nc;
+    __device__ float operator()(int64_t t) const {
+        const int32_t p = pix[t];
+        if (p < 0) return 0.f;
+        if (nc == 1) return x[p];
+        const float2 h = hi[t];
+        const float* xp = x + (int64_t)p * nc;
+        float v = fmaf(h.x, xp[nc - 2], h.y * xp[nc - 1]);
+        if (nc == 3) v += xp[0];
+        return v;
+    }
+};
+struct SrcMatvecF64 {  // y_t = v_t . xm[p_t] (xm zero on masked pixels), FP64 trig
+    const int32_t* pix; const float2* hi; const float2* lo; const double* x; int nc;
+    __device__ double operator()(int64_t t) const {
+        const int32_t p = pix[t];
+        if (p < 0) return 0.0;
+        if (nc == 1) return x[p];
+        const double2 cs = trig64(hi[t], lo[t]);
+        const double* xp = x + (int64_t)p * nc;
+        double v = cs.x * xp[nc - 2] + cs.y * xp[nc - 1];
+        if (nc == 3) v += xp[0];
+        return v;
+    }
+};
+template <typename D>
+struct SrcMaskedTod {  // y_t = d_t on kept samples, else 0
+    const int32_t* pix; const uint8_t* mask; const D* d;
+    __device__ double operator()(int64_t t) const {
+        const int32_t p = pix[t];
+        if (p < 0 || mask[p]) return 0.0;
+        return (double)d[t];
+    }
+};
+struct SrcPlain {
+    const double* y;
+    __device__ double operator()(int64_t t) const { return y[t]; }
+};
+
+constexpr int kTzThreads = 256;
+
+struct TzGeom {
+    const int64_t* det_off;      // [ndet + 1]
+    const int64_t* tile_start;   // [ndet + 1] prefix of tiles per detector
+    int ndet;
+    int64_t chunk_len;
+    int64_t tiles_per_chunk;
+    int64_t ntiles;
+};
+
+__device__ __forceinline__ int find_tile_det(const int64_t* ts, int ndet, int64_t tile) {
+    int lo = 0, hi = ndet - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ts[mid] <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One block per tile of TT outputs; each thread computes R consecutive
+// outputs from a register window of 2R samples that advances R taps at a
+// time (R*R FMAs per R buffer loads).  The FP32 buffer is padded by one word
+// every 32 (index a -> a + a/32) so that the window loads of the 32 lanes
+// (R = 8 apart) fall in distinct banks.  The tap array is zero-padded to a
+// multiple of R and the buffer carries 2R trailing zeros.
+template <typename T, int R>
+__host__ __device__ __forceinline__ int tz_taps_padded(int L) { return ((2 * L - 1 + R - 1) / R) * R; }
+
+template <typename T, int R, class Src>
+__global__ void __launch_bounds__(kTzThreads)
+toeplitz_kernel(Src src, const T* __restrict__ coeffs, int L, TzGeom geo, T* __restrict__ z) {
+    constexpr int TT = kTzThreads * R;
+    extern __shared__ __align__(16) unsigned char tz_smem[];
+    const int ntap = tz_taps_padded<T, R>(L);
+    T* kern = reinterpret_cast<T*>(tz_smem);  // [ntap]
+    T* buf = kern + ntap;                      // padded halo buffer
+    auto pad = [](int a) { return sizeof(T) == 4 ? a + (a >> 5) : a; };
+
+    for (int64_t tile = blockIdx.x; tile < geo.ntiles; tile += gridDim.x) {
+        const int d = find_tile_det(geo.tile_start, geo.ndet, tile);
+        const int64_t local = tile - geo.tile_start[d];
+        const int64_t c = local / geo.tiles_per_chunk, kk = local % geo.tiles_per_chunk;
+        const int64_t cs = geo.det_off[d] + c * geo.chunk_len;
+        const int64_t ce = min(cs + geo.chunk_len, geo.det_off[d + 1]);
+        const int64_t t0 = cs + kk * TT;
+        if (t0 >= ce) continue;  // uniform across the block
+        const int64_t t1 = min(t0 + (int64_t)TT, ce);
+        const int64_t b0 = t0 - (L - 1);  // buffer index 0 <-> sample b0
+        const int nbuf = (int)(t1 - t0) + 2 * (L - 1);
+        const int nfill = (int)(t1 - t0) + ntap + 2 * R;
+        __syncthreads();  // previous tile done with smem
+        for (int j = threadIdx.x; j < ntap; j += kTzThreads)
+            kern[j] = j < 2 * L - 1 ? coeffs[(int64_t)d * L + abs(j - (L - 1))] : T(0);
+        for (int j = threadIdx.x; j < nfill; j += kTzThreads) {
+            const int64_t t = b0 + j;
+            buf[pad(j)] = (j < nbuf && t >= cs && t < ce) ? T(src(t)) : T(0);
+        }
+        __syncthreads();
+        const int o0 = threadIdx.x * R;  // first output (relative to t0)
+        if (t0 + o0 < t1) {
+            T acc[R];
+            T win[2 * R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) { acc[r] = T(0); win[R + r] = buf[pad(o0 + r)]; }
+            for (int j = 0; j < ntap; j += R) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) { win[r] = win[R + r]; win[R + r] = buf[pad(o0 + j + R + r)]; }
+#pragma unroll
+                for (int jj = 0; jj < R; ++jj) {
+                    const T kj = kern[j + jj];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) acc[r] = fma(kj, win[r + jj], acc[r]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (t0 + o0 + r < t1) z[t0 + o0 + r] = acc[r];
+        }
+    }
+}
+
+template <typename T, int R>
+size_t toeplitz_smem(int L) {
+    const int TT = kTzThreads * R;
+    const int ntap = tz_taps_padded<T, R>(L);
+    const int nfill = TT + ntap + 2 * R;
+    const int padded = sizeof(T) == 4 ? nfill + nfill / 32 + 1 : nfill;
+    return sizeof(T) * ((size_t)ntap + padded);
+}
+
+}  // namespace
+
+// --------------------------------------------------------------- wrappers
+struct ToeplitzPlan {
+    DevBuf<int64_t> tile_start;
+    TzGeom geo;
+};
+
+static void plan_toeplitz(bm_inv_noise* n, int TT, ToeplitzPlan& tp) {
+    int64_t maxlen = 0;
+    for (int d = 0; d < n->ndet; ++d) maxlen = std::max(maxlen, n->h_det_off[d + 1] - n->h_det_off[d]);
+    const int64_t eff_chunk = std::min(n->chunk_len, maxlen);
+    const int64_t tpc = (eff_chunk + TT - 1) / TT;
+    std::vector<int64_t> ts(n->ndet + 1, 0);
+    for (int d = 0; d < n->ndet; ++d) {
+        const int64_t len = n->h_det_off[d + 1] - n->h_det_off[d];
+        const int64_t nch = (len + n->chunk_len - 1) / n->chunk_len;
+        ts[d + 1] = ts[d] + nch * tpc;
+    }
+    tp.tile_start.alloc(n->ndet + 1);
+    BM_CUDA(cudaMemcpy(tp.tile_start.get(), ts.data(), sizeof(int64_t) * (n->ndet + 1), cudaMemcpyHostToDevice));
+    tp.geo = TzGeom{n->det_off.get(), tp.tile_start.get(), n->ndet, n->chunk_len, tpc, ts[n->ndet]};
+}
+
+template <typename T, int R, class Src>
+static void run_toeplitz(bm_inv_noise* n, const Src& src, const T* coeffs, T* z) {
+    bm_context* ctx = n->ctx;
+    ToeplitzPlan tp;
+    plan_toeplitz(n, kTzThreads * R, tp);
+    if (tp.geo.ntiles == 0) return;
+    const size_t smem = toeplitz_smem<T, R>(n->nlags);
+    BM_CUDA(cudaFuncSetAttribute(toeplitz_kernel<T, R, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    const int grid = (int)std::min<int64_t>(tp.geo.ntiles, (int64_t)ctx->num_sms * 8);
+    toeplitz_kernel<T, R, Src><<<grid, kTzThreads, smem, ctx->stream>>>(src, coeffs, n->nlags, tp.geo, z);
+    BM_LAUNCH_CHECK();
+    BM_CUDA(cudaStreamSynchronize(ctx->stream));  // tile_start is released on return
+}
+
+static void finalize(bm_context* ctx, const int64_t* pitem, const double* partial, int64_t npix, int nc,
+                     double* q) {
+    const int threads = 256;
+    finalize_pixels_kernel<<<grid_for(ctx, (npix + threads - 1) / threads, 16), threads, 0, ctx->stream>>>(
+        pitem, partial, npix, nc, q);
+    BM_LAUNCH_CHECK();
+}
+
+template <typename G>
+static void gather_reduce(bm_pointing* p, const int32_t* item_pix, const int64_t* item_beg,
+                          const int32_t* item_len, int64_t nitems, const int64_t* pitem, const G* g,
+                          const int64_t* det_off, int ndet, const double* white, bool exact, double* q) {
+    bm_context* ctx = p->ctx;
+    const int nc = p->ncomp;
+    double* partial = workspace_as<double>(ctx, "partial", (size_t)std::max<int64_t>(nitems, 1) * nc);
+    if (nitems > 0) {
+        const int grid = grid_for(ctx, (nitems + kWarps - 1) / kWarps, 8);
+#define BM_GR(NC, EX)                                                                                     \
+    gather_reduce_kernel<NC, G, EX><<<grid, kWarps * 32, 0, ctx->stream>>>(                                \
+        item_pix, item_beg, item_len, nitems, p->perm.get(), p->cs_hi_s.get(), p->cs_lo_s.get(), g, det_off, \
+        ndet, white, partial)
+        if (exact) {
+            if (nc == 3) BM_GR(3, true); else if (nc == 2) BM_GR(2, true); else BM_GR(1, true);
+        } else {
+            if (nc == 3) BM_GR(3, false); else if (nc == 2) BM_GR(2, false); else BM_GR(1, false);
+        }
+#undef BM_GR
+        BM_LAUNCH_CHECK();
+    }
+    finalize(ctx, pitem, partial, p->npix, nc, q);
+}
+
+void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, double* q,
+            bm_precision prec, int64_t nrhs) {
+    bm_context* ctx = p->ctx;
+    cudaStream_t s = ctx->stream;
+    const int nc = p->ncomp;
+    const int64_t nvec = p->npix * nc;
+    const int threads = 256;
+    const int vgrid = grid_for(ctx, (nvec + threads - 1) / threads, 16);
+    for (int64_t r = 0; r < nrhs; ++r) {
+        const double* xr = x + r * nvec;
+        double* qr = q + r * nvec;
+        if (n->kind == 0) {
+            double* partial = workspace_as<double>(ctx, "partial", (size_t)std::max<int64_t>(pc->nitems, 1) * nc);
+            const int grid = grid_for(ctx, (pc->nitems + kWarps - 1) / kWarps, 8);
+            if (prec == BM_PREC_MIXED) {
+                float* x32 = workspace_as<float>(ctx, "x32", nvec);
+                masked_copy_kernel<float><<<vgrid, threads, 0, s>>>(xr, pc->mask.get(), p->npix, nc, x32);
+                BM_LAUNCH_CHECK();
+                if (pc->nitems > 0) {
+                    ScopedTimer timer(ctx, "matvec_white_f32");
+#define BM_WF32(NC)                                                                                     \
+    white_matvec_f32_kernel<NC><<<grid, kWarps * 32, 0, s>>>(pc->item_pix.get(), pc->item_beg.get(),     \
+                                                             pc->item_len.get(), pc->nitems, pc->wcs.get(), \
+                                                             pc->w1.get(), x32, partial)
+                    if (nc == 3) BM_WF32(3); else if (nc == 2) BM_WF32(2); else BM_WF32(1);
+#undef BM_WF32
+                    BM_LAUNCH_CHECK();
+                }
+            } else if (pc->nitems > 0) {
+                ScopedTimer timer(ctx, "matvec_white_f64");
+#define BM_WF64(NC)                                                                                      \
+    white_matvec_f64_kernel<NC><<<grid, kWarps * 32, 0, s>>>(                                              \
+        pc->item_pix.get(), pc->item_beg.get(), pc->item_len.get(), pc->nitems, p->perm.get(),            \
+        p->cs_hi_s.get(), p->cs_lo_s.get(), n->det_off.get(), n->ndet, n->white.get(), xr, partial)
+                if (nc == 3) BM_WF64(3); else if (nc == 2) BM_WF64(2); else BM_WF64(1);
+#undef BM_WF64
+                BM_LAUNCH_CHECK();
+            }
+            finalize(ctx, pc->pitem.get(), partial, p->npix, nc, qr);
+        } else {
+            if (prec == BM_PREC_MIXED) {
+                float* x32 = workspace_as<float>(ctx, "x32", nvec);
+                float* z32 = workspace_as<float>(ctx, "z32", p->nsamples);
+                masked_copy_kernel<float><<<vgrid, threads, 0, s>>>(xr, pc->mask.get(), p->npix, nc, x32);
+                BM_LAUNCH_CHECK();
+                {
+                    ScopedTimer timer(ctx, "toeplitz_f32");
+                    SrcMatvecF32 src{p->pix.get(), p->cs_hi_t.get(), x32, nc};
+                    run_toeplitz<float, 8>(n, src, n->coeffs32.get(), z32);
+                }
+                gather_reduce<float>(p, pc->item_pix.get(), pc->item_beg.get(), pc->item_len.get(), pc->nitems,
+                                     pc->pitem.get(), z32, nullptr, 0, nullptr, false, qr);
+            } else {
+                double* xm = workspace_as<double>(ctx, "xm", nvec);
+                double* z64 = workspace_as<double>(ctx, "z64", p->nsamples);
+                masked_copy_kernel<double><<<vgrid, threads, 0, s>>>(xr, pc->mask.get(), p->npix, nc, xm);
+                BM_LAUNCH_CHECK();
+                {
+                    ScopedTimer timer(ctx, "toeplitz_f64");
+                    SrcMatvecF64 src{p->pix.get(), p->cs_hi_t.get(), p->cs_lo_t.get(), xm, nc};
+                    run_toeplitz<double, 4>(n, src, n->coeffs64.get(), z64);
+                }
+                gather_reduce<double>(p, pc->item_pix.get(), pc->item_beg.get(), pc->item_len.get(), pc->nitems,
+                                      pc->pitem.get(), z64, nullptr, 0, nullptr, true, qr);
+            }
+        }
+    }
+}
+
+void rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dtype dt, int64_t nrhs,
+         double* b) {
+    bm_context* ctx = p->ctx;
+    const int nc = p->ncomp;
+    const int64_t nvec = p->npix * nc;
+    ScopedTimer timer(ctx, "rhs");
+    for (int64_t r = 0; r < nrhs; ++r) {
+        double* br = b + r * nvec;
+        if (n->kind == 0) {
+            if (dt == BM_F32) {
+                const float* d = static_cast<const float*>(tod) + r * p->nsamples;
+                gather_reduce<float>(p, pc->item_pix.get(), pc->item_beg.get(), pc->item_len.get(), pc->nitems,
+                                     pc->pitem.get(), d, n->det_off.get(), n->ndet, n->white.get(), true, br);
+            } else {
+                const double* d = static_cast<const double*>(tod) + r * p->nsamples;
+                gather_reduce<double>(p, pc->item_pix.get(), pc->item_beg.get(), pc->item_len.get(), pc->nitems,
+                                      pc->pitem.get(), d, n->det_off.get(), n->ndet, n->white.get(), true, br);
+            }
+        } else {
+            double* z64 = workspace_as<double>(ctx, "z64", p->nsamples);
+            if (dt == BM_F32) {
+                SrcMaskedTod<float> src{p->pix.get(), pc->mask.get(),
+                                        static_cast<const float*>(tod) + r * p->nsamples};
+                run_toeplitz<double, 4>(n, src, n->coeffs64.get(), z64);
+            } else {
+                SrcMaskedTod<double> src{p->pix.get(), pc->mask.get(),
+                                         static_cast<const double*>(tod) + r * p->nsamples};
+                run_toeplitz<double, 4>(n, src, n->coeffs64.get(), z64);
+            }
+            gather_reduce<double>(p, pc->item_pix.get(), pc->item_beg.get(), pc->item_len.get(), pc->nitems,
+                                  pc->pitem.get(), z64, nullptr, 0, nullptr, true, br);
+        }
+    }
+}
+
+void pointing_apply(bm_pointing* p, const double* x, double* y) {
+    bm_context* ctx = p->ctx;
+    const int threads = 256;
+    pointing_apply_kernel<<<grid_for(ctx, (p->nsamples + threads - 1) / threads, 16), threads, 0, ctx->stream>>>(
+        p->pix.get(), p->cs_hi_t.get(), p->cs_lo_t.get(), p->nsamples, p->ncomp, x, y);
+    BM_LAUNCH_CHECK();
+}
+
+void pointing_apply_transpose(bm_pointing* p, const double* y, double* x) {
+    Items it;
+    plan_items(p->ctx, p->off.get(), nullptr, p->npix, it);
+    gather_reduce<double>(p, it.pix.get(), it.beg.get(), it.len.get(), it.n, it.pitem.get(), y, nullptr, 0,
+                          nullptr, true, x);
+    BM_CUDA(cudaStreamSynchronize(p->ctx->stream));
+}
+
+void inv_noise_apply(bm_inv_noise* n, const double* y, double* z) {
+    bm_context* ctx = n->ctx;
+    if (n->kind == 0) {
+        // z_t = w_d y_t: reuse the Toeplitz machinery with a single lag.
+        DevBuf<double> c(n->ndet);
+        BM_CUDA(cudaMemcpyAsync(c.get(), n->white.get(), sizeof(double) * n->ndet, cudaMemcpyDeviceToDevice,
+                                ctx->stream));
+        bm_inv_noise tmp;
+        tmp.ctx = ctx;
+        tmp.ndet = n->ndet;
+        tmp.nsamples = n->nsamples;
+        tmp.h_det_off = n->h_det_off;
+        tmp.det_off.alloc(n->ndet + 1);
+        BM_CUDA(cudaMemcpyAsync(tmp.det_off.get(), n->det_off.get(), sizeof(int64_t) * (n->ndet + 1),
+                                cudaMemcpyDeviceToDevice, ctx->stream));
+        tmp.chunk_len = n->nsamples;
+        tmp.nlags = 1;
+        run_toeplitz<double, 4>(&tmp, SrcPlain{y}, c.get(), z);
+    } else {
+        run_toeplitz<double, 4>(n, SrcPlain{y}, n->coeffs64.get(), z);
+    }
+}
+
+}  // namespace bm

@@ -1,0 +1,316 @@
+// Block-diagonal preconditioner (paper Eq. 7) and the pixel mask.
+//
+// B_p = sum_{t in p} w_d(t) v_t v_t^T is accumulated in FP64 over each pixel's
+// pixel-sorted segment (one warp per work item of <= kItemMax samples, item
+// partials summed in item order, so the result is deterministic).  Per pixel:
+// eigenvalue extremes of the symmetric block, condition number, mask, and the
+// FP64 inverse M_p = B_p^-1.  The same pass plans the work items over kept
+// pixels used by every sorted-order kernel, and, for white noise, writes the
+// weighted FP32 stream sqrt(w) (cos 2psi, sin 2psi) that the FP32 matvec reads.
+#include "bm_internal.cuh"
+
+namespace bm {
+
+// ------------------------------------------------------------ item planning
+namespace {
+
+__global__ void item_count_kernel(const int64_t* __restrict__ off, const uint8_t* __restrict__ mask,
+                                  int64_t npix, int64_t* __restrict__ cnt) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t h = off[p + 1] - off[p];
+        const bool keep = h > 0 && (mask == nullptr || mask[p] == 0);
+        cnt[p] = keep ? (h + kItemMax - 1) / kItemMax : 0;
+    }
+}
+
+__global__ void item_fill_kernel(const int64_t* __restrict__ off, const int64_t* __restrict__ pitem,
+                                 int64_t npix, int32_t* __restrict__ item_pix,
+                                 int64_t* __restrict__ item_beg, int32_t* __restrict__ item_len) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k0 = pitem[p], k1 = pitem[p + 1];
+        const int64_t a = off[p], e = off[p + 1];
+        for (int64_t k = k0; k < k1; ++k) {
+            const int64_t b = a + (k - k0) * kItemMax;
+            item_pix[k] = (int32_t)p;
+            item_beg[k] = b;
+            item_len[k] = (int32_t)((e - b) < kItemMax ? (e - b) : kItemMax);
+        }
+    }
+}
+
+}  // namespace
+
+void plan_items(bm_context* ctx, const int64_t* off, const uint8_t* mask, int64_t npix, Items& it) {
+    cudaStream_t s = ctx->stream;
+    const int threads = 256;
+    const int grid = grid_for(ctx, (npix + threads - 1) / threads, 16);
+    DevBuf<int64_t> cnt(npix + 1);
+    it.pitem.alloc(npix + 1);
+    BM_CUDA(cudaMemsetAsync(cnt.get() + npix, 0, sizeof(int64_t), s));
+    item_count_kernel<<<grid, threads, 0, s>>>(off, mask, npix, cnt.get());
+    BM_LAUNCH_CHECK();
+    exclusive_scan_i64(cnt.get(), it.pitem.get(), npix + 1, s);
+    BM_CUDA(cudaMemcpy(&it.n, it.pitem.get() + npix, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    const size_t m = it.n > 0 ? (size_t)it.n : 1;
+    it.pix.alloc(m);
+    it.beg.alloc(m);
+    it.len.alloc(m);
+    if (it.n > 0) {
+        item_fill_kernel<<<grid, threads, 0, s>>>(off, it.pitem.get(), npix, it.pix.get(), it.beg.get(),
+                                                  it.len.get());
+        BM_LAUNCH_CHECK();
+    }
+}
+
+// ------------------------------------------------------------------ blocks
+namespace {
+
+constexpr int kBlkWarps = 8;
+constexpr int kMaxDetSmem = 4096;
+
+// Unique entries of the symmetric block, row-major upper triangle:
+// IQU: (II, IQ, IU, QQ, QU, UU); QU: (QQ, QU, UU); I: (II).
+template <int NC>
+__global__ void __launch_bounds__(kBlkWarps * 32)
+blocks_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ item_beg,
+              const int32_t* __restrict__ item_len, int64_t nitems, const uint32_t* __restrict__ perm,
+              const float2* __restrict__ hi, const float2* __restrict__ lo,
+              const int64_t* __restrict__ det_off, int ndet, const double* __restrict__ white,
+              double* __restrict__ partial) {
+    constexpr int NS = NC * (NC + 1) / 2;
+    __shared__ int64_t s_off[kMaxDetSmem + 1];
+    const bool smem_off = ndet <= kMaxDetSmem;
+    if (smem_off)
+        for (int d = threadIdx.x; d <= ndet; d += blockDim.x) s_off[d] = det_off[d];
+    __syncthreads();
+    const int64_t* offp = smem_off ? s_off : det_off;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t)blockIdx.x * kBlkWarps + (threadIdx.x >> 5);
+    const int64_t nwarps = (int64_t)gridDim.x * kBlkWarps;
+    for (int64_t k = warp; k < nitems; k += nwarps) {
+        const int64_t b = item_beg[k];
+        const int len = item_len[k];
+        double acc[NS];
+#pragma unroll
+        for (int j = 0; j < NS; ++j) acc[j] = 0.0;
+        for (int i = lane; i < len; i += 32) {
+            const int64_t si = b + i;
+            const uint32_t t = perm[si];
+            const double w = white[find_det(offp, ndet, t)];
+            const double2 cs = trig64(hi[si], lo[si]);
+            if (NC == 3) {
+                const double wc = w * cs.x, ws = w * cs.y;
+                acc[0] += w;
+                acc[1] += wc;
+                acc[2] += ws;
+                acc[3] += wc * cs.x;
+                acc[4] += wc * cs.y;
+                acc[5] += ws * cs.y;
+            } else if (NC == 2) {
+                const double wc = w * cs.x, ws = w * cs.y;
+                acc[0] += wc * cs.x;
+                acc[1] += wc * cs.y;
+                acc[2] += ws * cs.y;
+            } else {
+                acc[0] += w;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NS; ++j) acc[j] = warp_sum(acc[j]);
+        if (lane == 0) {
+#pragma unroll
+            for (int j = 0; j < NS; ++j) partial[k * NS + j] = acc[j];
+        }
+    }
+}
+
+__device__ __forceinline__ void eig_sym3(const double a[6], double& lmin, double& lmax) {
+    // a = (a00, a01, a02, a11, a12, a22).  Closed-form eigenvalues of a
+    // symmetric 3x3 matrix via the trigonometric solution of its
+    // characteristic cubic (Smith 1961).
+    const double p1 = a[1] * a[1] + a[2] * a[2] + a[4] * a[4];
+    const double q = (a[0] + a[3] + a[5]) / 3.0;
+    if (p1 == 0.0) {
+        lmin = fmin(a[0], fmin(a[3], a[5]));
+        lmax = fmax(a[0], fmax(a[3], a[5]));
+        return;
+    }
+    const double d0 = a[0] - q, d1 = a[3] - q, d2 = a[5] - q;
+    const double p2 = d0 * d0 + d1 * d1 + d2 * d2 + 2.0 * p1;
+    const double p = sqrt(p2 / 6.0);
+    const double ip = 1.0 / p;
+    const double b00 = d0 * ip, b11 = d1 * ip, b22 = d2 * ip;
+    const double b01 = a[1] * ip, b02 = a[2] * ip, b12 = a[4] * ip;
+    const double detb = b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) +
+                        b02 * (b01 * b12 - b11 * b02);
+    double r = 0.5 * detb;
+    r = fmin(1.0, fmax(-1.0, r));
+    const double phi = acos(r) / 3.0;
+    const double two_pi_3 = 2.0943951023931954923;
+    lmax = q + 2.0 * p * cos(phi);
+    lmin = q + 2.0 * p * cos(phi + two_pi_3);
+}
+
+template <int NC>
+__global__ void finalize_blocks_kernel(const int64_t* __restrict__ pitem, const double* __restrict__ partial,
+                                       const int32_t* __restrict__ hits, int64_t npix, int32_t min_hits,
+                                       double max_cond, double* __restrict__ B, double* __restrict__ Minv,
+                                       double* __restrict__ cond, uint8_t* __restrict__ mask) {
+    constexpr int NS = NC * (NC + 1) / 2;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double a[NS];
+#pragma unroll
+        for (int j = 0; j < NS; ++j) a[j] = 0.0;
+        for (int64_t k = pitem[p]; k < pitem[p + 1]; ++k)
+#pragma unroll
+            for (int j = 0; j < NS; ++j) a[j] += partial[k * NS + j];
+        double lmin, lmax;
+        if (NC == 3) {
+            eig_sym3(a, lmin, lmax);
+        } else if (NC == 2) {
+            const double m = 0.5 * (a[0] + a[2]);
+            const double h = 0.5 * (a[0] - a[2]);
+            const double rad = sqrt(h * h + a[1] * a[1]);
+            lmax = m + rad;
+            lmin = m - rad;
+        } else {
+            lmin = lmax = a[0];
+        }
+        const double c = lmin > 0.0 ? lmax / lmin : INFINITY;
+        bool bad = hits[p] < min_hits;
+        if (NC > 1) bad = bad || !(lmin > 0.0) || c > max_cond;
+        else bad = bad || !(a[0] > 0.0);
+        cond[p] = c;
+        mask[p] = bad ? 1 : 0;
+        double* Bp = B + p * NC * NC;
+        double* Mp = Minv + p * NC * NC;
+        if (NC == 3) {
+            const double b[9] = {a[0], a[1], a[2], a[1], a[3], a[4], a[2], a[4], a[5]};
+#pragma unroll
+            for (int j = 0; j < 9; ++j) Bp[j] = b[j];
+            if (bad) {
+#pragma unroll
+                for (int j = 0; j < 9; ++j) Mp[j] = 0.0;
+            } else {
+                const double c00 = a[3] * a[5] - a[4] * a[4];
+                const double c01 = a[2] * a[4] - a[1] * a[5];
+                const double c02 = a[1] * a[4] - a[2] * a[3];
+                const double c11 = a[0] * a[5] - a[2] * a[2];
+                const double c12 = a[1] * a[2] - a[0] * a[4];
+                const double c22 = a[0] * a[3] - a[1] * a[1];
+                const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+                const double id = 1.0 / det;
+                const double m[9] = {c00 * id, c01 * id, c02 * id, c01 * id, c11 * id,
+                                     c12 * id, c02 * id, c12 * id, c22 * id};
+#pragma unroll
+                for (int j = 0; j < 9; ++j) Mp[j] = m[j];
+            }
+        } else if (NC == 2) {
+            Bp[0] = a[0]; Bp[1] = a[1]; Bp[2] = a[1]; Bp[3] = a[2];
+            if (bad) {
+                Mp[0] = Mp[1] = Mp[2] = Mp[3] = 0.0;
+            } else {
+                const double id = 1.0 / (a[0] * a[2] - a[1] * a[1]);
+                Mp[0] = a[2] * id; Mp[1] = -a[1] * id; Mp[2] = -a[1] * id; Mp[3] = a[0] * id;
+            }
+        } else {
+            Bp[0] = a[0];
+            Mp[0] = bad ? 0.0 : 1.0 / a[0];
+        }
+    }
+}
+
+// Weighted FP32 stream for the white-noise FP32 matvec, in pixel-sorted order.
+__global__ void weighted_stream_kernel(const uint32_t* __restrict__ perm, int64_t n,
+                                       const float2* __restrict__ hi, const float2* __restrict__ lo,
+                                       const int64_t* __restrict__ det_off, int ndet,
+                                       const double* __restrict__ white, int ncomp,
+                                       float2* __restrict__ wcs, float* __restrict__ w1) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double w = white[find_det(det_off, ndet, perm[i])];
+        if (ncomp == 1) {
+            w1[i] = (float)w;
+        } else {
+            const double sw = sqrt(w);
+            const double2 cs = trig64(hi[i], lo[i]);
+            wcs[i] = make_float2((float)(sw * cs.x), (float)(sw * cs.y));
+        }
+    }
+}
+
+}  // namespace
+
+void build_precond(bm_precond* pc) {
+    bm_context* ctx = pc->ctx;
+    cudaStream_t s = ctx->stream;
+    bm_pointing* p = pc->p;
+    bm_inv_noise* n = pc->n;
+    const int64_t npix = p->npix;
+    const int nc = pc->ncomp;
+    const int ns = pc->nsym;
+    const int threads = 256;
+
+    pc->B.alloc(npix * nc * nc);
+    pc->Minv.alloc(npix * nc * nc);
+    pc->cond.alloc(npix);
+    pc->mask.alloc(npix);
+
+    // Blocks over every non-empty pixel.
+    {
+        ScopedTimer timer(ctx, "blocks");
+        Items all;
+        plan_items(ctx, p->off.get(), nullptr, npix, all);
+        DevBuf<double> partial((all.n > 0 ? all.n : 1) * ns);
+        if (all.n > 0) {
+            const int grid = grid_for(ctx, (all.n + kBlkWarps - 1) / kBlkWarps, 8);
+#define BM_BLOCKS(NC)                                                                                   \
+    blocks_kernel<NC><<<grid, kBlkWarps * 32, 0, s>>>(all.pix.get(), all.beg.get(), all.len.get(), all.n, \
+                                                      p->perm.get(), p->cs_hi_s.get(), p->cs_lo_s.get(),  \
+                                                      n->det_off.get(), n->ndet, n->white.get(),          \
+                                                      partial.get())
+            if (nc == 3) BM_BLOCKS(3);
+            else if (nc == 2) BM_BLOCKS(2);
+            else BM_BLOCKS(1);
+#undef BM_BLOCKS
+            BM_LAUNCH_CHECK();
+        }
+        const int pgrid = grid_for(ctx, (npix + threads - 1) / threads, 16);
+#define BM_FIN(NC)                                                                                       \
+    finalize_blocks_kernel<NC><<<pgrid, threads, 0, s>>>(all.pitem.get(), partial.get(), p->hits.get(),  \
+                                                         npix, pc->min_hits, pc->max_cond, pc->B.get(), \
+                                                         pc->Minv.get(), pc->cond.get(), pc->mask.get())
+        if (nc == 3) BM_FIN(3);
+        else if (nc == 2) BM_FIN(2);
+        else BM_FIN(1);
+#undef BM_FIN
+        BM_LAUNCH_CHECK();
+        BM_CUDA(cudaStreamSynchronize(s));
+    }
+
+    // Work items over kept pixels.
+    Items kept;
+    plan_items(ctx, p->off.get(), pc->mask.get(), npix, kept);
+    pc->nitems = kept.n;
+    pc->item_pix = std::move(kept.pix);
+    pc->item_beg = std::move(kept.beg);
+    pc->item_len = std::move(kept.len);
+    pc->pitem = std::move(kept.pitem);
+
+    // White-noise weighted stream.
+    if (n->kind == 0 && p->nvalid > 0) {
+        if (nc == 1) pc->w1.alloc(p->nvalid);
+        else pc->wcs.alloc(p->nvalid);
+        const int grid = grid_for(ctx, (p->nvalid + threads - 1) / threads, 16);
+        weighted_stream_kernel<<<grid, threads, 0, s>>>(p->perm.get(), p->nvalid, p->cs_hi_s.get(),
+                                                        p->cs_lo_s.get(), n->det_off.get(), n->ndet,
+                                                        n->white.get(), nc, pc->wcs.get(), pc->w1.get());
+        BM_LAUNCH_CHECK();
+    }
+    BM_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace bm

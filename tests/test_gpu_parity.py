@@ -1,0 +1,315 @@
+"""Parity of the CUDA library (through the C-ABI) with the FP64 oracle on the
+same seeded inputs.  Tolerances: integers bit-exact; FP64 path <= 1e-10
+relative L2 per Stokes component on kept pixels; refined mixed path <= 1e-6
+(BASELINE targets); single operators in FP64 <= 1e-12."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import gls, healpix
+
+from gpucase import Case, stokes_cols
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import paper_2501_16122_gb300 as pkg
+    pkg.build()
+    from paper_2501_16122_gb300 import _lib
+    return _lib
+
+
+@pytest.fixture(scope="module")
+def ctx(L):
+    c = L.bm_context_create(0)
+    yield c
+    L.bm_context_destroy(c)
+
+
+def rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    den = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (den if den > 0 else 1.0)
+
+
+# ------------------------------------------------------------- HEALPix (K9)
+
+@pytest.mark.parametrize("nside", [1, 2, 16, 256, 512, 8192])
+def test_ang2pix_bit_exact(L, ctx, nside):
+    rng = np.random.default_rng(nside)
+    n = 200_000
+    z = rng.uniform(-1, 1, n)
+    phi = rng.uniform(0, 2 * math.pi, n)
+    # plus pixel centres, ring boundaries, poles and the z = +-2/3 transition
+    pc = np.arange(min(12 * nside * nside, 50_000))
+    zc, phc = healpix.pix2ang_ring(nside, pc)
+    z = np.concatenate([z, zc, [1.0, -1.0, 2 / 3, -2 / 3, 0.0, np.nextafter(2 / 3, 1)]])
+    phi = np.concatenate([phi, phc, [0.0, 6.0, 1.0, 2.0, 0.0, 0.5]])
+    d_pix = torch.empty(z.size, dtype=torch.int32, device="cuda")
+    L.bm_ang2pix_ring(ctx, nside, torch.from_numpy(z).cuda(), torch.from_numpy(phi).cuda(), d_pix)
+    assert np.array_equal(d_pix.cpu().numpy(), healpix.ang2pix_ring(nside, z, phi))
+
+
+def test_ang2pix_on_a_scan(L, ctx):
+    e = synth.make_experiment(256, 16, 50_000, 1001)
+    pt = synth.pointing(e, with_angles=True)
+    d_pix = torch.empty(e.nsamples, dtype=torch.int32, device="cuda")
+    L.bm_ang2pix_ring(ctx, 256, torch.from_numpy(pt["z"]).cuda(), torch.from_numpy(pt["phi"]).cuda(), d_pix)
+    assert np.array_equal(d_pix.cpu().numpy(), healpix.ang2pix_ring(256, pt["z"], pt["phi"]))
+
+
+# ------------------------------------------------------- pointing and blocks
+
+@pytest.mark.parametrize("solver", [3, 2, 1])
+def test_pointing_operators_and_hits(L, ctx, solver):
+    c = Case(L, ctx, 16, 4, 20_000, 2000 + solver, solver=solver, flag=0.02)
+    try:
+        hits = torch.zeros(c.npix, dtype=torch.int32, device="cuda")
+        L.bm_pointing_get_hits(c.p, hits)
+        assert np.array_equal(hits.cpu().numpy(), gls.hits(c.pix, c.npix))
+        rng = np.random.default_rng(1)
+        x = rng.normal(size=(c.npix, solver))
+        y = torch.zeros(c.e.nsamples, dtype=torch.float64, device="cuda")
+        L.bm_pointing_apply(c.p, c.vec(x), y)
+        pe_all = np.where(c.pix >= 0, c.pix, -1)
+        v = gls.pointing_weights(c.psi, solver)
+        assert rel(y.cpu().numpy(), gls.apply_P(pe_all, v, x)) < 1e-13
+        yt = rng.normal(size=c.e.nsamples)
+        xt = c.vec()
+        L.bm_pointing_apply_transpose(c.p, torch.from_numpy(yt).cuda(), xt)
+        assert rel(xt.cpu().numpy(), gls.apply_PT(pe_all, v, yt, c.npix).ravel()) < 1e-13
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("solver", [3, 2, 1])
+def test_blocks_cond_mask(L, ctx, solver):
+    c = Case(L, ctx, 16, 4, 65_536, 1000, solver=solver)
+    try:
+        S = c.S
+        B = torch.zeros(c.npix * solver * solver, dtype=torch.float64, device="cuda")
+        cond = torch.zeros(c.npix, dtype=torch.float64, device="cuda")
+        L.bm_precond_get_blocks(c.pc, B, cond)
+        B = B.cpu().numpy().reshape(c.npix, solver, solver)
+        assert rel(B, S.B) < 1e-13
+        _, _, ocond = gls.block_condition(S.B)
+        # mask bit-exact outside a guard band around the threshold
+        g = 1e-9
+        band = np.isfinite(ocond) & (np.abs(ocond - 1e3) <= g * 1e3)
+        m = c.mask()
+        assert np.array_equal(m[~band], S.mask[~band]), np.nonzero(m != S.mask)
+        assert band.sum() == 0
+        fin = np.isfinite(ocond) & (ocond < 1e6)
+        cg = cond.cpu().numpy()
+        np.testing.assert_allclose(cg[fin], ocond[fin], rtol=1e-9)
+        assert np.all(~np.isfinite(cg[~np.isfinite(ocond)]) | (cg[~np.isfinite(ocond)] > 1e12))
+        # M r against the oracle's inverse blocks
+        r = np.random.default_rng(2).normal(size=(c.npix, solver))
+        z = c.vec()
+        L.bm_precond_apply(c.pc, c.vec(r), z)
+        assert rel(z.cpu().numpy(), S.precond(r).ravel()) < 1e-12
+    finally:
+        c.close()
+
+
+# --------------------------------------------------------------- operator A
+
+@pytest.mark.parametrize("noise", ["white", "toeplitz"])
+@pytest.mark.parametrize("solver", [3, 2, 1])
+def test_matvec_and_rhs(L, ctx, noise, solver):
+    kw = dict(chunk=8192, nlags=64) if noise == "toeplitz" else {}
+    c = Case(L, ctx, 16, 4, 30_000 + 77, 3000 + solver, solver=solver, noise=noise, flag=0.01, **kw)
+    try:
+        S = c.S
+        rng = np.random.default_rng(3)
+        x = rng.normal(size=(c.npix, solver)) * np.array([100.0, 10.0, 10.0])[stokes_cols(solver)]
+        ref = S.matvec(x * (~S.mask)[:, None])
+        for prec, tol in ((L.BM_PREC_FP64, 1e-12), (L.BM_PREC_MIXED, 2e-6)):
+            q = c.vec()
+            L.bm_matvec(c.p, c.n, c.pc, c.vec(x), q, prec)
+            qh = q.cpu().numpy().reshape(c.npix, solver)
+            for k in range(solver):
+                assert rel(qh[:, k], ref[:, k]) < tol, (prec, k, rel(qh[:, k], ref[:, k]))
+            assert np.all(qh[S.mask] == 0)
+        b = c.vec()
+        L.bm_rhs(c.p, c.n, c.pc, c.d_tod, 1, b)
+        bref = S.rhs(c.tod)
+        assert rel(b.cpu().numpy(), bref.ravel()) < 1e-12
+    finally:
+        c.close()
+
+
+def test_matvec_symmetric_and_deterministic(L, ctx):
+    c = Case(L, ctx, 16, 4, 40_000, 77, noise="toeplitz", chunk=5000, nlags=128, build_oracle=False)
+    try:
+        m = c.mask()
+        rng = np.random.default_rng(4)
+        x = rng.normal(size=(c.npix, 3)) * (~m)[:, None]
+        y = rng.normal(size=(c.npix, 3)) * (~m)[:, None]
+        for prec in (L.BM_PREC_FP64, L.BM_PREC_MIXED):
+            ax, ay, ax2 = c.vec(), c.vec(), c.vec()
+            L.bm_matvec(c.p, c.n, c.pc, c.vec(x), ax, prec)
+            L.bm_matvec(c.p, c.n, c.pc, c.vec(y), ay, prec)
+            L.bm_matvec(c.p, c.n, c.pc, c.vec(x), ax2, prec)
+            assert torch.equal(ax, ax2)  # bitwise reproducible
+            a = float((c.vec(y) * ax).sum())
+            b = float((c.vec(x) * ay).sum())
+            tol = 1e-12 if prec == L.BM_PREC_FP64 else 1e-5
+            assert abs(a - b) <= tol * (abs(a) + abs(b))
+    finally:
+        c.close()
+
+
+def test_inv_noise_apply(L, ctx):
+    e = synth.make_experiment(8, 3, 3000, 5)
+    c = synth.toeplitz_band(e.sigma, 0.1, 1.0, 20.0, 4096, 100)
+    N = gls.ToeplitzNoise(c, e.det_offsets, 700, 1 / e.sigma ** 2)
+    n = L.bm_inv_noise_create_toeplitz(ctx, e.det_offsets, 700, c, 1 / e.sigma ** 2)
+    y = np.random.default_rng(5).normal(size=e.nsamples)
+    z = torch.zeros(e.nsamples, dtype=torch.float64, device="cuda")
+    L.bm_inv_noise_apply(n, torch.from_numpy(y).cuda(), z)
+    assert rel(z.cpu().numpy(), N.apply(y)) < 1e-13
+    L.bm_inv_noise_destroy(n)
+    W = gls.WhiteNoise(1 / e.sigma ** 2, e.det_offsets)
+    n = L.bm_inv_noise_create_diag(ctx, e.det_offsets, 1 / e.sigma ** 2)
+    L.bm_inv_noise_apply(n, torch.from_numpy(y).cuda(), z)
+    assert rel(z.cpu().numpy(), W.apply(y)) < 1e-15
+    L.bm_inv_noise_destroy(n)
+
+
+# ------------------------------------------------------------------- solves
+
+def check_map(L, c, out, ref_x, tol):
+    m = c.mask()
+    xh = out.cpu().numpy().reshape(c.npix, c.nc)
+    assert np.array_equal(np.isnan(xh).any(axis=1), m)
+    err = gls.rel_err(xh, ref_x, m)
+    assert all(v <= tol for v in err.values()), err
+    return err
+
+
+def test_config0_fp64_and_mixed(L, ctx):
+    # nside 16, 4 detectors x 65536 samples, FP64, white noise, tol 1e-10.
+    c = Case(L, ctx, 16, 4, 65_536, 1000)
+    try:
+        ref, info = gls.gls_map(c.S, c.tod, tol=1e-13)
+        for prec, tol in ((L.BM_PREC_FP64, 1e-10), (L.BM_PREC_MIXED, 1e-10)):
+            out = c.vec()
+            st, infos = L.bm_pcg_solve(c.p, c.n, c.pc, c.d_tod, 1, out, 1e-10, 100, prec)
+            assert st == L.BM_OK, infos
+            assert infos[0]["rel_residual"] <= 1e-10
+            check_map(L, c, out, ref, tol)
+        # white noise: one PCG iteration in the FP64 path
+        out = c.vec()
+        st, infos = L.bm_pcg_solve(c.p, c.n, c.pc, c.d_tod, 1, out, 1e-10, 100, L.BM_PREC_FP64)
+        assert infos[0]["iterations"] == 1
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("solver", [3, 2, 1])
+def test_toeplitz_solve(L, ctx, solver):
+    c = Case(L, ctx, 8, 4, 2 ** 14 + 123, 4000 + solver, solver=solver, noise="toeplitz", chunk=4096,
+             nlags=256, flag=0.01)
+    try:
+        ref, info = gls.gls_map(c.S, c.tod, tol=1e-13, maxiter=2000)
+        assert info.converged
+        out = c.vec()
+        st, infos = L.bm_pcg_solve(c.p, c.n, c.pc, c.d_tod, 1, out, 1e-11, 2000, L.BM_PREC_FP64)
+        assert st == L.BM_OK, infos
+        check_map(L, c, out, ref, 1e-10)
+        out = c.vec()
+        st, infos = L.bm_pcg_solve(c.p, c.n, c.pc, c.d_tod, 1, out, 1e-8, 2000, L.BM_PREC_MIXED)
+        assert st == L.BM_OK, infos
+        assert infos[0]["outer_iterations"] >= 1
+        check_map(L, c, out, ref, 1e-6)
+    finally:
+        c.close()
+
+
+def test_noiseless_recovery_fp32_inputs(L, ctx):
+    # FP32 TOD and FP32 psi (configs 1-3 store them so): x = s to the
+    # precision of the stored TOD values.
+    c = Case(L, ctx, 32, 16, 8192, 1001, tod_dtype=np.float32, psi_dtype=np.float32, noiseless=True,
+             noise="toeplitz", chunk=2048, nlags=512)
+    try:
+        out = c.vec()
+        st, infos = L.bm_pcg_solve(c.p, c.n, c.pc, c.d_tod, 1, out, 1e-9, 3000, L.BM_PREC_MIXED)
+        assert st == L.BM_OK, infos
+        ref, _ = gls.gls_map(c.S, c.tod.astype(np.float64), tol=1e-13, maxiter=3000)
+        check_map(L, c, out, ref, 1e-6)
+        # and the oracle's map equals the input sky up to FP32 TOD rounding
+        err = gls.rel_err(ref, c.sky, c.S.mask)
+        assert err["all"] < 1e-5
+    finally:
+        c.close()
+
+
+def test_multi_rhs_matches_single(L, ctx):
+    c = Case(L, ctx, 16, 4, 16_384, 11)
+    try:
+        tods = [c.tod, synth.tod(c.e, c.pix, c.psi, synth.sky_map(c.npix, 12))]
+        d = torch.from_numpy(np.stack(tods)).cuda()
+        out = torch.zeros(2 * c.npix * 3, dtype=torch.float64, device="cuda")
+        st, infos = L.bm_pcg_solve(c.p, c.n, c.pc, d, 2, out, 1e-10, 50, L.BM_PREC_MIXED)
+        assert st == L.BM_OK
+        for r in range(2):
+            one = c.vec()
+            L.bm_pcg_solve(c.p, c.n, c.pc, d[r].contiguous(), 1, one, 1e-10, 50, L.BM_PREC_MIXED)
+            assert torch.equal(torch.nan_to_num(one), torch.nan_to_num(out[r * c.npix * 3:(r + 1) * c.npix * 3]))
+    finally:
+        c.close()
+
+
+# --------------------------------------------------------------- edge cases
+
+def test_invalid_pixel_rejected(L, ctx):
+    pix = torch.tensor([0, 1, 5, 12], dtype=torch.int32, device="cuda")  # 12 >= npix
+    psi = torch.zeros(4, dtype=torch.float64, device="cuda")
+    with pytest.raises(L.BrahmapError) as ei:
+        L.bm_pointing_create(ctx, 12, pix, psi, 3)
+    assert ei.value.status == L.BM_ERR_INVALID
+    pix = torch.tensor([0, -2], dtype=torch.int32, device="cuda")
+    with pytest.raises(L.BrahmapError):
+        L.bm_pointing_create(ctx, 12, pix, psi[:2], 3)
+
+
+def test_all_flagged_and_tiny(L, ctx):
+    pix = torch.full((7,), -1, dtype=torch.int32, device="cuda")
+    psi = torch.zeros(7, dtype=torch.float64, device="cuda")
+    p = L.bm_pointing_create(ctx, 12, pix, psi, 3)
+    n = L.bm_inv_noise_create_diag(ctx, np.array([0, 7]), np.array([1.0]))
+    pc = L.bm_blockdiag_precond_create(p, n, 3, 1e3)
+    out = torch.zeros(36, dtype=torch.float64, device="cuda")
+    st, infos = L.bm_pcg_solve(p, n, pc, torch.ones(7, dtype=torch.float64, device="cuda"), 1, out, 1e-8, 10)
+    assert st == L.BM_OK and infos[0]["rel_residual"] == 0.0
+    assert torch.isnan(out).all()
+    for h in (pc, n, p):
+        (L.bm_precond_destroy if h is pc else L.bm_inv_noise_destroy if h is n else L.bm_pointing_destroy)(h)
+    # a single sample
+    p = L.bm_pointing_create(ctx, 12, torch.tensor([3], dtype=torch.int32, device="cuda"),
+                             torch.zeros(1, dtype=torch.float64, device="cuda"), 1)
+    n = L.bm_inv_noise_create_diag(ctx, np.array([0, 1]), np.array([4.0]))
+    pc = L.bm_blockdiag_precond_create(p, n, 1, 1e3)
+    out = torch.zeros(12, dtype=torch.float64, device="cuda")
+    st, infos = L.bm_pcg_solve(p, n, pc, torch.tensor([2.5], dtype=torch.float64, device="cuda"), 1, out,
+                               1e-12, 10)
+    assert st == L.BM_OK and out[3].item() == 2.5
+    L.bm_precond_destroy(pc)
+    L.bm_inv_noise_destroy(n)
+    L.bm_pointing_destroy(p)
+
+
+def test_bad_arguments(L, ctx):
+    e = synth.make_experiment(4, 2, 100, 1)
+    with pytest.raises(L.BrahmapError):
+        L.bm_inv_noise_create_diag(ctx, np.array([0, 50, 40]), np.array([1.0, 1.0]))
+    with pytest.raises(L.BrahmapError):
+        L.bm_inv_noise_create_toeplitz(ctx, e.det_offsets, 10, np.zeros((2, 2000)), np.ones(2))
+    with pytest.raises(L.BrahmapError):
+        L.bm_inv_noise_create_diag(ctx, e.det_offsets, np.array([1.0, -1.0]))
