@@ -1,0 +1,374 @@
+#!/usr/bin/env python3
+"""Benchmark of the GLS map-making hot path (BrahMap, arXiv 2501.16122) on GB300.
+
+Workload (default): HEALPix nside 256 (786,432 pixels), 256 detectors x 2^22
+samples (1,073,741,824 samples) from the seeded spin + precession scan, FP32
+TOD, int32 pixel indices, FP64 polarisation angles, diagonal white noise
+(sigma_d in [1, 2] uK), IQU, pixels with hits < 3 or cond > 1e3 masked, PCG
+to 1e-8 in mixed precision (FP32 per-sample products, FP64 accumulation,
+FP64 iterative refinement).
+
+One step = one pass of the whole hot path over the resident inputs:
+pointing ingest (trig, pixel sort) -> block preconditioner + mask -> RHS ->
+PCG with refinement -> map.  `value` is TOD samples per second of whole
+steps (all ranks); `matvec` gives the P^T N^-1 P matvec throughput alone.
+`e2e` repeats the step through host (pinned) buffers with the host->device
+copies of pix/psi/tod and the device->host copy of the map inside the timed
+region.  `--impl reference` times the FP64 CPU oracle on a bounded sample.
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
+torch.distributed.run (one rank per GPU); ranks run independent replicas of
+the workload (no data-path collective) and the slowest rank's time counts.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TOD samples/s per PᵀN⁻¹P matvec (%HBM peak); PCG time-to-map at 1e-6 rel err"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--nside", type=int, default=256)
+    ap.add_argument("--ndet", type=int, default=256)
+    ap.add_argument("--ns", type=int, default=2 ** 22, help="samples per detector")
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--seed", type=int, default=1001)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--matvec-reps", type=int, default=20)
+    ap.add_argument("--profile", action="store_true", help="short run for ncu: no e2e, cpu, clocks")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu: int):
+        self.gpu, self.proc, self.lines = gpu, None, []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={','.join(self.FIELDS)}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ inputs
+def make_inputs(args, seed):
+    import synth
+    e = synth.make_experiment(args.nside, args.ndet, args.ns, seed)
+    pt = synth.pointing(e)
+    sky = synth.sky_map(e.npix, seed)
+    tod = synth.tod(e, pt["pix"], pt["psi"], sky, dtype=np.float32)
+    return e, pt["pix"], pt["psi"], tod
+
+
+def cpu_oracle_run(nside, ndet, ns, seed, tol):
+    """One oracle map-making pass (system set-up, RHS, PCG) on a sample; returns (samples, seconds)."""
+    import synth
+    from oracle import gls
+    e = synth.make_experiment(nside, ndet, ns, seed)
+    pt = synth.pointing(e)
+    tod = synth.tod(e, pt["pix"], pt["psi"], synth.sky_map(e.npix, seed), dtype=np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    S = gls.System(pt["pix"], pt["psi"], 3, e.npix, gls.WhiteNoise(1.0 / e.sigma ** 2, e.det_offsets))
+    x, info = gls.pcg(S, S.rhs(tod), tol, 100)
+    dt = time.perf_counter() - t0
+    return e.nsamples, dt
+
+
+CPU_SAMPLE = dict(ndet=8, ns=2 ** 19)  # 4.2M samples of the same scan: ~10 s of oracle work
+
+
+# ------------------------------------------------------------- reference
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    steps = []
+    for i in range(args.warmup + args.steps):
+        n, dt = cpu_oracle_run(args.nside, CPU_SAMPLE["ndet"], CPU_SAMPLE["ns"], args.seed, args.tol)
+        if i >= args.warmup:
+            steps.append((n, dt))
+    n = sum(s[0] for s in steps)
+    t = sum(s[1] for s in steps)
+    v = n / t
+    sample = (f"{CPU_SAMPLE['ndet']} detectors x {CPU_SAMPLE['ns']} samples of the nside-{args.nside} scan "
+              f"(one oracle set-up + RHS + PCG per step)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "TOD samples/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t / len(steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded scan, Gaussian sky, white noise)",
+        "config": workload_config(args),
+        "cpu_baseline": {"value": v, "unit": "TOD samples/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "TOD samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args):
+    return {"workload": f"GLS map-making, nside {args.nside}, {args.ndet} det x {args.ns} samples, "
+                        f"white noise, IQU, mixed precision PCG to {args.tol:g}",
+            "nside": args.nside, "npix": 12 * args.nside ** 2, "ndet": args.ndet, "samples_per_det": args.ns,
+            "nsamples": args.ndet * args.ns, "solver": "IQU", "noise": "white", "tod_dtype": "f32",
+            "psi_dtype": "f64", "tol": args.tol, "min_hits": 3, "max_cond": 1e3,
+            "parallelism": f"replicas x{args.gpus}",
+            "l2": "inputs (17 GB) larger than L2 (129 MB); no flush needed"}
+
+
+# ------------------------------------------------------------------ gb300
+def run_gb300(args, rank, world, local_rank):
+    import torch
+    from paper_2501_16122_gb300 import _lib as L
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    t_gen = time.perf_counter()
+    e, pix, psi, tod = make_inputs(args, args.seed)
+    t_gen = time.perf_counter() - t_gen
+    nt = e.nsamples
+    stream = torch.cuda.current_stream()
+    d_pix = torch.from_numpy(pix).cuda()
+    d_psi = torch.from_numpy(psi).cuda()
+    d_tod = torch.from_numpy(tod).cuda()
+    inv_var = 1.0 / e.sigma ** 2
+    ctx = L.bm_context_create(local_rank, stream)
+    out = torch.empty(e.npix * 3, dtype=torch.float64, device="cuda")
+    infos = []
+
+    def step(src_pix, src_psi, src_tod):
+        p = L.bm_pointing_create(ctx, e.npix, src_pix, src_psi, L.BM_SOLVER_IQU)
+        n = L.bm_inv_noise_create_diag(ctx, e.det_offsets, inv_var)
+        pc = L.bm_blockdiag_precond_create(p, n, 3, 1e3)
+        st, info = L.bm_pcg_solve(p, n, pc, src_tod, 1, out, args.tol, 200, L.BM_PREC_MIXED)
+        infos.append((st, info[0]))
+        L.bm_precond_destroy(pc)
+        L.bm_inv_noise_destroy(n)
+        L.bm_pointing_destroy(p)
+
+    for _ in range(args.warmup):
+        step(d_pix, d_psi, d_tod)
+    # --- timed region (device-resident inputs)
+    sampler = ClockSampler(local_rank)
+    if not args.profile:
+        sampler.start()
+    L.bm_context_set_timing(ctx, True)
+    launches0 = L.bm_kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(d_pix, d_psi, d_tod)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = L.bm_kernel_launches() - launches0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    clocks = sampler.stop() if not args.profile else None
+    fam = {}
+    for name in ("ingest", "blocks", "rhs", "matvec_white_f32", "matvec_white_f64"):
+        tot, cnt = L.bm_context_kernel_time(ctx, name)
+        if cnt:
+            fam[name] = {"ms_per_launch": tot / cnt, "launches": cnt, "ms_per_step": tot / args.steps}
+    L.bm_context_set_timing(ctx, False)
+
+    # --- matvec alone (the metric's kernel), x = the solved map
+    p = L.bm_pointing_create(ctx, e.npix, d_pix, d_psi, L.BM_SOLVER_IQU)
+    n = L.bm_inv_noise_create_diag(ctx, e.det_offsets, inv_var)
+    pc = L.bm_blockdiag_precond_create(p, n, 3, 1e3)
+    mask = torch.empty(e.npix, dtype=torch.uint8, device="cuda")
+    hits = torch.empty(e.npix, dtype=torch.int32, device="cuda")
+    L.bm_precond_get_mask(pc, mask, hits)
+    kept = mask == 0
+    n_kept_samples = int(hits[kept].sum().item())
+    n_kept_pix = int(kept.sum().item())
+    x = torch.nan_to_num(out)
+    q = torch.empty_like(x)
+    for _ in range(3):
+        L.bm_matvec(p, n, pc, x, q, L.BM_PREC_MIXED)
+    L.bm_context_set_timing(ctx, True)
+    torch.cuda.synchronize()
+    mv0, mv1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    mv0.record(stream)
+    for _ in range(args.matvec_reps):
+        L.bm_matvec(p, n, pc, x, q, L.BM_PREC_MIXED)
+    mv1.record(stream)
+    torch.cuda.synchronize()
+    mv_call_ms = mv0.elapsed_time(mv1) / args.matvec_reps
+    k_tot, k_cnt = L.bm_context_kernel_time(ctx, "matvec_white_f32")
+    L.bm_context_set_timing(ctx, False)
+    k_ms = k_tot / max(k_cnt, 1)
+    nitems_est = sum(math.ceil(h / 4096) for h in hits[kept].tolist()) if n_kept_pix < 5_000_000 else 0
+    alg_bytes = 8 * n_kept_samples + 12 * n_kept_pix + 24 * nitems_est  # trig pair + x + item partials
+    hbm, peak_kind = peaks()
+    achieved = alg_bytes / (k_ms * 1e-3) / 1e9
+    L.bm_precond_destroy(pc)
+    L.bm_inv_noise_destroy(n)
+    L.bm_pointing_destroy(p)
+
+    # --- end to end from pinned host buffers
+    e2e = None
+    if not args.no_e2e and not args.profile:
+        h_pix = torch.from_numpy(pix).pin_memory()
+        h_psi = torch.from_numpy(psi).pin_memory()
+        h_tod = torch.from_numpy(tod).pin_memory()
+        h_out = torch.empty(e.npix * 3, dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            a = h_pix.to("cuda", non_blocking=True)
+            b = h_psi.to("cuda", non_blocking=True)
+            c = h_tod.to("cuda", non_blocking=True)
+            step(a, b, c)
+            h_out.copy_(out, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+
+        e2e_step()
+        barrier()
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for _ in range(max(1, args.steps // 2)):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        e2e_ms = (time.perf_counter() - w0) * 1000 / max(1, args.steps // 2)
+        e2e = {"ms_per_step": e2e_ms, "h2d_bytes_per_step": int(pix.nbytes + psi.nbytes + tod.nbytes),
+               "d2h_bytes_per_step": int(h_out.numel() * 8)}
+
+    # --- max over ranks
+    vals = torch.tensor([ms, e2e["ms_per_step"] if e2e else 0.0], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    ms_max, e2e_max = vals.tolist()
+
+    # --- CPU baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu and not args.profile:
+        n_s, dt = cpu_oracle_run(args.nside, CPU_SAMPLE["ndet"], CPU_SAMPLE["ns"], args.seed, args.tol)
+        cpu = {"value": n_s / dt, "unit": "TOD samples/s", "cores": 1, "kind": "oracle",
+               "sample": f"{CPU_SAMPLE['ndet']} det x {CPU_SAMPLE['ns']} samples of the same scan "
+                         f"(oracle set-up + RHS + PCG, {dt:.1f} s)"}
+
+    if rank == 0:
+        st_ok = all(s == L.BM_OK for s, _ in infos)
+        last = infos[-1][1]
+        line = {
+            "metric": METRIC, "value": world * nt / (ms_max * 1e-3), "unit": "TOD samples/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 products / f64 accumulation + refinement",
+            "data": "synthetic (seeded spin+precession scan, Gaussian IQU sky, white noise)",
+            "config": workload_config(args),
+            "matvec": {"samples_per_s": nt / (k_ms * 1e-3), "kernel_ms": k_ms, "call_ms": mv_call_ms,
+                       "kept_samples": n_kept_samples, "hbm_frac": achieved / hbm},
+            "time_to_map_ms": ms_max - fam.get("ingest", {}).get("ms_per_step", 0.0),
+            "step_breakdown_ms": {k: v["ms_per_step"] for k, v in fam.items()},
+            "solve": {"status_ok": st_ok, "iterations": last["iterations"],
+                      "outer_iterations": last["outer_iterations"], "rel_residual": last["rel_residual"]},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None, "kernel": "white_matvec_f32_kernel",
+                         "peak_kind": peak_kind, "bytes_per_launch": alg_bytes},
+            "gpu_launches": int(launches),
+            "input_generation_s": t_gen,
+        }
+        if e2e:
+            line["e2e"] = {"value": world * nt / (e2e_max * 1e-3), "unit": "TOD samples/s",
+                           "h2d_bytes_per_step": e2e["h2d_bytes_per_step"],
+                           "d2h_bytes_per_step": e2e["d2h_bytes_per_step"], "ms_per_step": e2e_max}
+        if clocks:
+            line["clocks"] = clocks
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    L.bm_context_destroy(ctx)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    run_gb300(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

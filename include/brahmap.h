@@ -103,6 +103,9 @@ void bm_context_destroy(bm_context* ctx);
 bm_status bm_context_set_timing(bm_context* ctx, int enable);
 bm_status bm_context_kernel_time(bm_context* ctx, const char* name, double* total_ms,
                                  int64_t* launches);
+/* Number of CUDA kernels the library has launched in this process so far
+ * (all contexts and threads). */
+int64_t bm_kernel_launches(void);
 
 /* ------------------------------------------------------------- pixelisation */
 

@@ -56,6 +56,7 @@ _SIGS = {
     "bm_context_destroy": ([_P], None),
     "bm_context_set_timing": ([_P, ctypes.c_int], ctypes.c_int),
     "bm_context_kernel_time": ([_P, ctypes.c_char_p, ctypes.POINTER(_f64), ctypes.POINTER(_i64)], ctypes.c_int),
+    "bm_kernel_launches": ([], _i64),
     "bm_ang2pix_ring": ([_P, _i64, _i64, _P, _P, _P], ctypes.c_int),
     "bm_pointing_create": ([_P, _i64, _i64, _P, _P, ctypes.c_int, ctypes.c_int, _PP], ctypes.c_int),
     "bm_pointing_destroy": ([_P], None),
@@ -152,6 +153,10 @@ def bm_context_destroy(ctx):
 
 def bm_context_set_timing(ctx, enable: bool):
     _check(lib.bm_context_set_timing(ctx, int(bool(enable))), "bm_context_set_timing")
+
+
+def bm_kernel_launches() -> int:
+    return int(lib.bm_kernel_launches())
 
 
 def bm_context_kernel_time(ctx, name: str):

@@ -40,20 +40,37 @@ struct Error {
         }                                     \
     } while (0)
 
-#define BM_LAUNCH_CHECK() BM_CUDA(cudaGetLastError())
+// Every kernel launch of the library goes through BM_LAUNCH_CHECK, which
+// also counts it (bm_kernel_launches()).
+void count_launch();
+#define BM_LAUNCH_CHECK()              \
+    do {                               \
+        ::bm::count_launch();          \
+        BM_CUDA(cudaGetLastError());   \
+    } while (0)
+
+// Stream of the context whose entry point is running on this thread; device
+// buffers are allocated and freed stream-ordered on it (cudaMallocAsync from
+// the device's memory pool, which keeps freed memory for reuse).
+extern thread_local cudaStream_t tl_stream;
 
 // Device allocation that throws BM_ERR_OOM and is released by DevBuf's destructor.
 template <typename T>
 struct DevBuf {
     T* ptr = nullptr;
     size_t n = 0;
+    cudaStream_t stream = nullptr;
     DevBuf() = default;
     explicit DevBuf(size_t count) { alloc(count); }
     DevBuf(const DevBuf&) = delete;
     DevBuf& operator=(const DevBuf&) = delete;
-    DevBuf(DevBuf&& o) noexcept : ptr(o.ptr), n(o.n) { o.ptr = nullptr; o.n = 0; }
+    DevBuf(DevBuf&& o) noexcept : ptr(o.ptr), n(o.n), stream(o.stream) { o.ptr = nullptr; o.n = 0; }
     DevBuf& operator=(DevBuf&& o) noexcept {
-        if (this != &o) { release(); ptr = o.ptr; n = o.n; o.ptr = nullptr; o.n = 0; }
+        if (this != &o) {
+            release();
+            ptr = o.ptr; n = o.n; stream = o.stream;
+            o.ptr = nullptr; o.n = 0;
+        }
         return *this;
     }
     ~DevBuf() { release(); }
@@ -61,17 +78,18 @@ struct DevBuf {
         release();
         if (count == 0) return;
         void* p = nullptr;
-        cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+        stream = tl_stream;
+        cudaError_t e = cudaMallocAsync(&p, count * sizeof(T), stream);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
-            set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+            set_error("device allocation of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
             throw Error{BM_ERR_OOM};
         }
         ptr = static_cast<T*>(p);
         n = count;
     }
     void release() {
-        if (ptr) cudaFree(ptr);
+        if (ptr) cudaFreeAsync(ptr, stream);
         ptr = nullptr;
         n = 0;
     }
@@ -93,7 +111,11 @@ struct bm_context {
     int num_sms = 0;
     bool timing = false;
     std::map<std::string, bm::KernelTimer> timers;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // Event pairs recorded around timed kernels; resolved when queried, so
+    // timing never blocks the host inside a solve.
+    struct Pending { std::string name; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> event_pool;
     double* h_pinned = nullptr;  // small pinned host buffer for scalar reads
     std::map<std::string, bm::DevBuf<char>> ws;  // named grow-only scratch buffers
 };
@@ -186,9 +208,11 @@ constexpr int kRedThreads = 256;
 struct ScopedTimer {
     bm_context* ctx;
     const char* name;
+    cudaEvent_t a = nullptr;
     ScopedTimer(bm_context* c, const char* n);
     ~ScopedTimer();
 };
+void resolve_timers(bm_context* ctx);
 
 // Launch wrappers implemented in the .cu files.
 void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dtype);

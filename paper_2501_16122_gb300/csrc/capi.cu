@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <new>
 
 #include "bm_internal.cuh"
@@ -20,28 +21,63 @@ void set_error(const char* fmt, ...) {
 }
 void clear_error() { g_last_error[0] = '\0'; }
 
+thread_local cudaStream_t tl_stream = nullptr;
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static cudaEvent_t take_event(bm_context* ctx) {
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
 ScopedTimer::ScopedTimer(bm_context* c, const char* n) : ctx(c), name(n) {
-    if (ctx && ctx->timing) cudaEventRecord(ctx->ev0, ctx->stream);
+    if (ctx && ctx->timing) {
+        a = take_event(ctx);
+        if (a) cudaEventRecord(a, ctx->stream);
+    }
 }
 ScopedTimer::~ScopedTimer() {
-    if (ctx && ctx->timing) {
-        cudaEventRecord(ctx->ev1, ctx->stream);
-        if (cudaEventSynchronize(ctx->ev1) == cudaSuccess) {
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
-            auto& t = ctx->timers[name];
-            t.total_ms += ms;
-            t.launches += 1;
+    if (ctx && ctx->timing && a) {
+        cudaEvent_t b = take_event(ctx);
+        if (b) {
+            cudaEventRecord(b, ctx->stream);
+            ctx->pending.push_back({name, a, b});
+        } else {
+            ctx->event_pool.push_back(a);
         }
     }
 }
 
+// Accumulate the recorded event pairs into the per-kernel timers.
+void resolve_timers(bm_context* ctx) {
+    for (auto& pd : ctx->pending) {
+        if (cudaEventSynchronize(pd.b) == cudaSuccess) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, pd.a, pd.b);
+            auto& t = ctx->timers[pd.name];
+            t.total_ms += ms;
+            t.launches += 1;
+        }
+        ctx->event_pool.push_back(pd.a);
+        ctx->event_pool.push_back(pd.b);
+    }
+    ctx->pending.clear();
+    (void)cudaGetLastError();
+}
+
 void* workspace(bm_context* ctx, const char* name, size_t bytes) {
     auto& b = ctx->ws[name];
-    if (b.n < bytes) {
-        BM_CUDA(cudaStreamSynchronize(ctx->stream));  // the old buffer may still be in use
-        b.alloc(bytes + bytes / 8);
-    }
+    if (b.n < bytes) b.alloc(bytes + bytes / 8);  // stream-ordered: old users finish first
     return b.get();
 }
 
@@ -65,7 +101,16 @@ static bm_status guarded(F&& f) {
     }
 }
 
-static void use_device(const bm_context* ctx) { BM_CUDA(cudaSetDevice(ctx->device)); }
+static void use_device(const bm_context* ctx) {
+    BM_CUDA(cudaSetDevice(ctx->device));
+    tl_stream = ctx->stream;
+}
+
+// Host -> device copy ordered on the context stream; returns once the copy is done.
+static void upload(bm_context* ctx, void* dst, const void* src, size_t bytes) {
+    BM_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    BM_CUDA(cudaStreamSynchronize(ctx->stream));
+}
 
 extern "C" {
 
@@ -99,9 +144,15 @@ bm_status bm_context_create(int device, void* cuda_stream, bm_context** out) {
         ctx->device = device;
         ctx->stream = static_cast<cudaStream_t>(cuda_stream);
         cudaError_t e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
-        if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
-        if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
         if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_pinned, 4096);
+        // Keep memory freed back to the device pool for reuse by the next
+        // handle instead of returning it to the driver.
+        cudaMemPool_t pool = nullptr;
+        if (e == cudaSuccess) e = cudaDeviceGetDefaultMemPool(&pool, device);
+        if (e == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
         if (e != cudaSuccess) {
             set_error("context setup failed: %s", cudaGetErrorString(e));
             bm_context_destroy(ctx);
@@ -115,11 +166,21 @@ bm_status bm_context_create(int device, void* cuda_stream, bm_context** out) {
 void bm_context_destroy(bm_context* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
-    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
-    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    tl_stream = ctx->stream;
+    cudaStreamSynchronize(ctx->stream);
+    resolve_timers(ctx);
+    for (cudaEvent_t ev : ctx->event_pool) cudaEventDestroy(ev);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
-    delete ctx;
+    const int dev = ctx->device;
+    delete ctx;  // releases the workspaces (stream-ordered)
+    cudaStreamSynchronize(tl_stream);
+    // Hand the pool's unused memory back to the driver.
+    cudaMemPool_t pool = nullptr;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess && pool) cudaMemPoolTrimTo(pool, 0);
+    (void)cudaGetLastError();
 }
+
+int64_t bm_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 bm_status bm_context_set_timing(bm_context* ctx, int enable) {
     return guarded([&] {
@@ -133,6 +194,8 @@ bm_status bm_context_kernel_time(bm_context* ctx, const char* name, double* tota
                                  int64_t* launches) {
     return guarded([&] {
         BM_REQUIRE(ctx && name, "ctx/name is NULL");
+        use_device(ctx);
+        resolve_timers(ctx);
         auto it = ctx->timers.find(name);
         double ms = 0.0;
         int64_t n = 0;
@@ -248,9 +311,8 @@ static bm_inv_noise* new_noise(bm_context* ctx, int32_t ndet, const int64_t* det
     try {
         n->det_off.alloc(ndet + 1);
         n->white.alloc(ndet);
-        BM_CUDA(cudaMemcpy(n->det_off.get(), det_offsets, sizeof(int64_t) * (ndet + 1),
-                           cudaMemcpyHostToDevice));
-        BM_CUDA(cudaMemcpy(n->white.get(), white, sizeof(double) * ndet, cudaMemcpyHostToDevice));
+        upload(ctx, n->det_off.get(), det_offsets, sizeof(int64_t) * (ndet + 1));
+        upload(ctx, n->white.get(), white, sizeof(double) * ndet);
     } catch (...) {
         delete n;
         throw;
@@ -300,8 +362,8 @@ bm_status bm_inv_noise_create_toeplitz(bm_context* ctx, int32_t ndet, const int6
             std::vector<float> c32(coeffs, coeffs + m);
             n->coeffs64.alloc(m);
             n->coeffs32.alloc(m);
-            BM_CUDA(cudaMemcpy(n->coeffs64.get(), coeffs, sizeof(double) * m, cudaMemcpyHostToDevice));
-            BM_CUDA(cudaMemcpy(n->coeffs32.get(), c32.data(), sizeof(float) * m, cudaMemcpyHostToDevice));
+            upload(ctx, n->coeffs64.get(), coeffs, sizeof(double) * m);
+            upload(ctx, n->coeffs32.get(), c32.data(), sizeof(float) * m);
         } catch (...) {
             delete n;
             throw;

@@ -383,7 +383,9 @@ static void plan_toeplitz(bm_inv_noise* n, int TT, ToeplitzPlan& tp) {
         ts[d + 1] = ts[d] + nch * tpc;
     }
     tp.tile_start.alloc(n->ndet + 1);
-    BM_CUDA(cudaMemcpy(tp.tile_start.get(), ts.data(), sizeof(int64_t) * (n->ndet + 1), cudaMemcpyHostToDevice));
+    BM_CUDA(cudaMemcpyAsync(tp.tile_start.get(), ts.data(), sizeof(int64_t) * (n->ndet + 1), cudaMemcpyHostToDevice,
+                            n->ctx->stream));
+    BM_CUDA(cudaStreamSynchronize(n->ctx->stream));  // ts is a host temporary
     tp.geo = TzGeom{n->det_off.get(), tp.tile_start.get(), n->ndet, n->chunk_len, tpc, ts[n->ndet]};
 }
 
@@ -398,8 +400,7 @@ static void run_toeplitz(bm_inv_noise* n, const Src& src, const T* coeffs, T* z)
                                  (int)smem));
     const int grid = (int)std::min<int64_t>(tp.geo.ntiles, (int64_t)ctx->num_sms * 8);
     toeplitz_kernel<T, R, Src><<<grid, kTzThreads, smem, ctx->stream>>>(src, coeffs, n->nlags, tp.geo, z);
-    BM_LAUNCH_CHECK();
-    BM_CUDA(cudaStreamSynchronize(ctx->stream));  // tile_start is released on return
+    BM_LAUNCH_CHECK();  // tile_start is released stream-ordered after the kernel
 }
 
 static void finalize(bm_context* ctx, const int64_t* pitem, const double* partial, int64_t npix, int nc,

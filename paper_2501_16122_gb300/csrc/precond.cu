@@ -52,7 +52,8 @@ void plan_items(bm_context* ctx, const int64_t* off, const uint8_t* mask, int64_
     item_count_kernel<<<grid, threads, 0, s>>>(off, mask, npix, cnt.get());
     BM_LAUNCH_CHECK();
     exclusive_scan_i64(cnt.get(), it.pitem.get(), npix + 1, s);
-    BM_CUDA(cudaMemcpy(&it.n, it.pitem.get() + npix, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    BM_CUDA(cudaMemcpyAsync(&it.n, it.pitem.get() + npix, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    BM_CUDA(cudaStreamSynchronize(s));
     const size_t m = it.n > 0 ? (size_t)it.n : 1;
     it.pix.alloc(m);
     it.beg.alloc(m);
@@ -126,31 +127,41 @@ blocks_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ 
     }
 }
 
+// One Jacobi rotation in the (i, j) plane of the symmetric matrix m
+// (row-major 3x3) that annihilates m[i][j]: with theta = (m_jj - m_ii) /
+// (2 m_ij), t = tan of the rotation angle = sign(theta) / (|theta| +
+// sqrt(theta^2 + 1)) (the smaller root), c = 1/sqrt(1 + t^2), s = t c.
+__device__ __forceinline__ void jacobi_rotate(double m[3][3], int i, int j) {
+    const double mij = m[i][j];
+    if (mij == 0.0) return;
+    const double theta = (m[j][j] - m[i][i]) / (2.0 * mij);
+    const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+    const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+    const int k = 3 - i - j;
+    const double mik = m[i][k], mjk = m[j][k];
+    m[i][i] -= t * mij;
+    m[j][j] += t * mij;
+    m[i][j] = m[j][i] = 0.0;
+    m[i][k] = m[k][i] = c * mik - s * mjk;
+    m[j][k] = m[k][j] = s * mik + c * mjk;
+}
+
+// Eigenvalue extremes of a symmetric 3x3 matrix a = (a00, a01, a02, a11,
+// a12, a22) by cyclic Jacobi rotations (absolute error ~ eps ||a||, so the
+// smallest eigenvalue keeps relative accuracy ~ eps * cond even when the
+// two largest eigenvalues nearly coincide).
 __device__ __forceinline__ void eig_sym3(const double a[6], double& lmin, double& lmax) {
-    // a = (a00, a01, a02, a11, a12, a22).  Closed-form eigenvalues of a
-    // symmetric 3x3 matrix via the trigonometric solution of its
-    // characteristic cubic (Smith 1961).
-    const double p1 = a[1] * a[1] + a[2] * a[2] + a[4] * a[4];
-    const double q = (a[0] + a[3] + a[5]) / 3.0;
-    if (p1 == 0.0) {
-        lmin = fmin(a[0], fmin(a[3], a[5]));
-        lmax = fmax(a[0], fmax(a[3], a[5]));
-        return;
+    double m[3][3] = {{a[0], a[1], a[2]}, {a[1], a[3], a[4]}, {a[2], a[4], a[5]}};
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        const double off = m[0][1] * m[0][1] + m[0][2] * m[0][2] + m[1][2] * m[1][2];
+        const double diag = m[0][0] * m[0][0] + m[1][1] * m[1][1] + m[2][2] * m[2][2];
+        if (off <= 1e-36 * diag || off == 0.0) break;
+        jacobi_rotate(m, 0, 1);
+        jacobi_rotate(m, 0, 2);
+        jacobi_rotate(m, 1, 2);
     }
-    const double d0 = a[0] - q, d1 = a[3] - q, d2 = a[5] - q;
-    const double p2 = d0 * d0 + d1 * d1 + d2 * d2 + 2.0 * p1;
-    const double p = sqrt(p2 / 6.0);
-    const double ip = 1.0 / p;
-    const double b00 = d0 * ip, b11 = d1 * ip, b22 = d2 * ip;
-    const double b01 = a[1] * ip, b02 = a[2] * ip, b12 = a[4] * ip;
-    const double detb = b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) +
-                        b02 * (b01 * b12 - b11 * b02);
-    double r = 0.5 * detb;
-    r = fmin(1.0, fmax(-1.0, r));
-    const double phi = acos(r) / 3.0;
-    const double two_pi_3 = 2.0943951023931954923;
-    lmax = q + 2.0 * p * cos(phi);
-    lmin = q + 2.0 * p * cos(phi + two_pi_3);
+    lmin = fmin(m[0][0], fmin(m[1][1], m[2][2]));
+    lmax = fmax(m[0][0], fmax(m[1][1], m[2][2]));
 }
 
 template <int NC>

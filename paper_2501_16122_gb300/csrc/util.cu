@@ -113,8 +113,7 @@ void exclusive_scan(const T* in, T* out, int64_t n, cudaStream_t s) {
     scan_top_kernel<T><<<1, kScanThreads, 0, s>>>(sums.get(), nb);
     BM_LAUNCH_CHECK();
     scan_apply_kernel<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, sums.get());
-    BM_LAUNCH_CHECK();
-    BM_CUDA(cudaStreamSynchronize(s));  // sums is released on return
+    BM_LAUNCH_CHECK();  // sums is released stream-ordered after the kernels
 }
 
 }  // namespace

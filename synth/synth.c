@@ -214,6 +214,7 @@ void synth_scan(const synth_scan_params* sp, int64_t nside, int32_t ndet, int64_
         scan_rotation(sp, t, R);
         const double hwp = fmod(2.0 * SYN_PI * sp->hwp_hz * t + sp->hwp_phase0, 2.0 * SYN_PI);
         for (int32_t d = 0; d < ndet; ++d) {
+            /* detector direction in the focal-plane frame */
             const double v0 = sin(ox[d]) * cos(oy[d]);
             const double v1 = sin(oy[d]);
             const double v2 = cos(ox[d]) * cos(oy[d]);

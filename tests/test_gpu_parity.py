@@ -220,7 +220,7 @@ def test_toeplitz_solve(L, ctx, solver):
         ref, info = gls.gls_map(c.S, c.tod, tol=1e-13, maxiter=2000)
         assert info.converged
         out = c.vec()
-        st, infos = L.bm_pcg_solve(c.p, c.n, c.pc, c.d_tod, 1, out, 1e-11, 2000, L.BM_PREC_FP64)
+        st, infos = L.bm_pcg_solve(c.p, c.n, c.pc, c.d_tod, 1, out, 1e-12, 2000, L.BM_PREC_FP64)
         assert st == L.BM_OK, infos
         check_map(L, c, out, ref, 1e-10)
         out = c.vec()
