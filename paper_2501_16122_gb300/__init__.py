@@ -12,7 +12,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 
 
 def build(verbose_ptxas: bool = False, force: bool = False) -> str:
-    from .build import build as _build
+    from .nvcc_build import build as _build
     return _build(verbose_ptxas=verbose_ptxas, force=force)
 
 

@@ -45,5 +45,5 @@ def test_no_cpu_fallback_without_gpu(L):
 
 def test_library_is_built_for_sm_103a():
     # The build passes exactly one -gencode for compute_103a / sm_103a.
-    from paper_2501_16122_gb300 import build as b
+    from paper_2501_16122_gb300 import nvcc_build as b
     assert b.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
