@@ -197,6 +197,23 @@ bm_status bm_rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* to
 bm_status bm_matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, double* q,
                     bm_precision prec);
 
+/* q = A x for white noise with FP32 per-sample products -- the same operator
+ * and the same result as bm_matvec(p, n, pc, x, q, BM_PREC_MIXED) -- for
+ * callers that cannot allocate device memory during the call (a process
+ * whose free device memory belongs to another allocator, or a pipeline that
+ * fixes its memory budget before it starts).  This entry point has no
+ * counterpart in the paper.  It allocates nothing: its scratch is a 16 MiB
+ * array built into the library, present on every GPU that loads the library
+ * until the process exits.  The array holds one FP64 value per work item and
+ * Stokes component; a problem needing more than 2^21 values is rejected
+ * with BM_ERR_INVALID (use bm_matvec).  x, q device FP64 [npix][ncomp]; n
+ * must be the diagonal noise pc was built from.  The first call on a device
+ * looks the array's address up (cudaGetSymbolAddress); make it before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU
+ * race, so serialise them. */
+bm_status bm_matvec_white_static(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x,
+                                 double* q);
+
 /* GLS maps by block-preconditioned CG (Eq. 5-7): tod device [nrhs][nsamples]
  * (tod_dtype), map_out device FP64 [nrhs][npix][ncomp] (NaN on masked
  * pixels).  x0 = 0; stops when ||b - A x||_2 <= tol ||b||_2 (per RHS) or

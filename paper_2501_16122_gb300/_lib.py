@@ -74,6 +74,7 @@ _SIGS = {
     "bm_precond_apply": ([_P, _P, _P], ctypes.c_int),
     "bm_rhs": ([_P, _P, _P, _P, ctypes.c_int, _i32, _P], ctypes.c_int),
     "bm_matvec": ([_P, _P, _P, _P, _P, ctypes.c_int], ctypes.c_int),
+    "bm_matvec_white_static": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "bm_pcg_solve": ([_P, _P, _P, _P, ctypes.c_int, _i32, _P, _f64, _i32, ctypes.c_int,
                       ctypes.POINTER(bm_solve_info)], ctypes.c_int),
 }
@@ -275,6 +276,14 @@ def bm_matvec(p, n, pc, x, q, prec: int = BM_PREC_FP64):
     import torch
     _check(lib.bm_matvec(p, n, pc, _dev(x, torch.float64, "x"), _dev(q, torch.float64, "q"), int(prec)),
            "bm_matvec")
+
+
+def bm_matvec_white_static(p, n, pc, x, q):
+    """White-noise FP32-product matvec that allocates no device memory (its
+    scratch is a fixed array inside the library)."""
+    import torch
+    _check(lib.bm_matvec_white_static(p, n, pc, _dev(x, torch.float64, "x"), _dev(q, torch.float64, "q")),
+           "bm_matvec_white_static")
 
 
 def bm_pcg_solve(p, n, pc, tod, nrhs: int, map_out, tol: float, maxiter: int, prec: int = BM_PREC_FP64,
