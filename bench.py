@@ -3,7 +3,7 @@
 
 Workload (default): HEALPix nside 256 (786,432 pixels), 256 detectors x 2^22
 samples (1,073,741,824 samples) from the seeded spin + precession scan, FP32
-TOD, int32 pixel indices, FP64 polarisation angles, diagonal white noise
+TOD, int32 pixel indices, FP32 precomputed cos 2psi / sin 2psi, diagonal white noise
 (sigma_d in [1, 2] uK), IQU, pixels with hits < 3 or cond > 1e3 masked, PCG
 to 1e-8 in mixed precision (FP32 per-sample products, FP64 accumulation,
 FP64 iterative refinement).
@@ -13,7 +13,7 @@ pointing ingest (trig, pixel sort) -> block preconditioner + mask -> RHS ->
 PCG with refinement -> map.  `value` is TOD samples per second of whole
 steps (all ranks); `matvec` gives the P^T N^-1 P matvec throughput alone.
 `e2e` repeats the step through host (pinned) buffers with the host->device
-copies of pix/psi/tod and the device->host copy of the map inside the timed
+copies of pix/cos/sin/tod and the device->host copy of the map inside the timed
 region.  `--impl reference` times the FP64 CPU oracle on a bounded sample.
 
 Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
@@ -121,12 +121,14 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ inputs
 def make_inputs(args, seed):
+    """Config-1 inputs: int32 pixels, FP32 precomputed cos 2psi / sin 2psi, FP32 TOD."""
     import synth
     e = synth.make_experiment(args.nside, args.ndet, args.ns, seed)
     pt = synth.pointing(e)
+    c32, s32 = synth.trig32(pt["psi"])
     sky = synth.sky_map(e.npix, seed)
-    tod = synth.tod(e, pt["pix"], pt["psi"], sky, dtype=np.float32)
-    return e, pt["pix"], pt["psi"], tod
+    tod = synth.tod(e, pt["pix"], pt["psi"], sky, dtype=np.float32, trig=(c32, s32))
+    return e, pt["pix"], c32, s32, tod
 
 
 def cpu_oracle_run(nside, ndet, ns, seed, tol):
@@ -135,9 +137,12 @@ def cpu_oracle_run(nside, ndet, ns, seed, tol):
     from oracle import gls
     e = synth.make_experiment(nside, ndet, ns, seed)
     pt = synth.pointing(e)
-    tod = synth.tod(e, pt["pix"], pt["psi"], synth.sky_map(e.npix, seed), dtype=np.float32).astype(np.float64)
+    c32, s32 = synth.trig32(pt["psi"])
+    tod = synth.tod(e, pt["pix"], pt["psi"], synth.sky_map(e.npix, seed), dtype=np.float32,
+                    trig=(c32, s32)).astype(np.float64)
     t0 = time.perf_counter()
-    S = gls.System(pt["pix"], pt["psi"], 3, e.npix, gls.WhiteNoise(1.0 / e.sigma ** 2, e.det_offsets))
+    S = gls.System(pt["pix"], None, 3, e.npix, gls.WhiteNoise(1.0 / e.sigma ** 2, e.det_offsets),
+                   trig=(c32, s32))
     x, info = gls.pcg(S, S.rhs(tod), tol, 100)
     dt = time.perf_counter() - t0
     return e.nsamples, dt
@@ -177,7 +182,7 @@ def workload_config(args):
                         f"white noise, IQU, mixed precision PCG to {args.tol:g}",
             "nside": args.nside, "npix": 12 * args.nside ** 2, "ndet": args.ndet, "samples_per_det": args.ns,
             "nsamples": args.ndet * args.ns, "solver": "IQU", "noise": "white", "tod_dtype": "f32",
-            "psi_dtype": "f64", "tol": args.tol, "min_hits": 3, "max_cond": 1e3,
+            "trig_dtype": "f32 (precomputed cos 2psi, sin 2psi)", "tol": args.tol, "min_hits": 3, "max_cond": 1e3,
             "parallelism": f"replicas x{args.gpus}",
             "l2": "inputs (17 GB) larger than L2 (129 MB); no flush needed"}
 
@@ -198,20 +203,20 @@ def run_gb300(args, rank, world, local_rank):
             dist.barrier()
 
     t_gen = time.perf_counter()
-    e, pix, psi, tod = make_inputs(args, args.seed)
+    e, pix, c32, s32, tod = make_inputs(args, args.seed)
     t_gen = time.perf_counter() - t_gen
     nt = e.nsamples
     stream = torch.cuda.current_stream()
     d_pix = torch.from_numpy(pix).cuda()
-    d_psi = torch.from_numpy(psi).cuda()
+    d_trig = (torch.from_numpy(c32).cuda(), torch.from_numpy(s32).cuda())
     d_tod = torch.from_numpy(tod).cuda()
     inv_var = 1.0 / e.sigma ** 2
     ctx = L.bm_context_create(local_rank, stream)
     out = torch.empty(e.npix * 3, dtype=torch.float64, device="cuda")
     infos = []
 
-    def step(src_pix, src_psi, src_tod):
-        p = L.bm_pointing_create(ctx, e.npix, src_pix, src_psi, L.BM_SOLVER_IQU)
+    def step(src_pix, src_trig, src_tod):
+        p = L.bm_pointing_create_trig(ctx, e.npix, src_pix, src_trig[0], src_trig[1], L.BM_SOLVER_IQU)
         n = L.bm_inv_noise_create_diag(ctx, e.det_offsets, inv_var)
         pc = L.bm_blockdiag_precond_create(p, n, 3, 1e3)
         st, info = L.bm_pcg_solve(p, n, pc, src_tod, 1, out, args.tol, 200, L.BM_PREC_MIXED)
@@ -221,7 +226,7 @@ def run_gb300(args, rank, world, local_rank):
         L.bm_pointing_destroy(p)
 
     for _ in range(args.warmup):
-        step(d_pix, d_psi, d_tod)
+        step(d_pix, d_trig, d_tod)
     # --- timed region (device-resident inputs)
     sampler = ClockSampler(local_rank)
     if not args.profile:
@@ -233,7 +238,7 @@ def run_gb300(args, rank, world, local_rank):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        step(d_pix, d_psi, d_tod)
+        step(d_pix, d_trig, d_tod)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -248,7 +253,7 @@ def run_gb300(args, rank, world, local_rank):
     L.bm_context_set_timing(ctx, False)
 
     # --- matvec alone (the metric's kernel), x = the solved map
-    p = L.bm_pointing_create(ctx, e.npix, d_pix, d_psi, L.BM_SOLVER_IQU)
+    p = L.bm_pointing_create_trig(ctx, e.npix, d_pix, d_trig[0], d_trig[1], L.BM_SOLVER_IQU)
     n = L.bm_inv_noise_create_diag(ctx, e.det_offsets, inv_var)
     pc = L.bm_blockdiag_precond_create(p, n, 3, 1e3)
     mask = torch.empty(e.npix, dtype=torch.uint8, device="cuda")
@@ -285,13 +290,14 @@ def run_gb300(args, rank, world, local_rank):
     e2e = None
     if not args.no_e2e and not args.profile:
         h_pix = torch.from_numpy(pix).pin_memory()
-        h_psi = torch.from_numpy(psi).pin_memory()
+        h_c = torch.from_numpy(c32).pin_memory()
+        h_s = torch.from_numpy(s32).pin_memory()
         h_tod = torch.from_numpy(tod).pin_memory()
         h_out = torch.empty(e.npix * 3, dtype=torch.float64).pin_memory()
 
         def e2e_step():
             a = h_pix.to("cuda", non_blocking=True)
-            b = h_psi.to("cuda", non_blocking=True)
+            b = (h_c.to("cuda", non_blocking=True), h_s.to("cuda", non_blocking=True))
             c = h_tod.to("cuda", non_blocking=True)
             step(a, b, c)
             h_out.copy_(out, non_blocking=True)
@@ -306,7 +312,7 @@ def run_gb300(args, rank, world, local_rank):
         torch.cuda.synchronize()
         barrier()
         e2e_ms = (time.perf_counter() - w0) * 1000 / max(1, args.steps // 2)
-        e2e = {"ms_per_step": e2e_ms, "h2d_bytes_per_step": int(pix.nbytes + psi.nbytes + tod.nbytes),
+        e2e = {"ms_per_step": e2e_ms, "h2d_bytes_per_step": int(pix.nbytes + c32.nbytes + s32.nbytes + tod.nbytes),
                "d2h_bytes_per_step": int(h_out.numel() * 8)}
 
     # --- max over ranks

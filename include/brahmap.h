@@ -131,6 +131,13 @@ bm_status bm_ang2pix_ring(bm_context* ctx, int64_t nside, int64_t n, const doubl
 bm_status bm_pointing_create(bm_context* ctx, int64_t npix, int64_t nsamples, const int32_t* pix,
                              const void* psi, bm_dtype psi_dtype, bm_solver_type solver,
                              bm_pointing** out);
+/* The same operator from precomputed FP32 cos 2psi and sin 2psi (device
+ * [nsamples] each, |values| <= 1): the FP32 numbers are the entries of P
+ * (Eq. 8) exactly, so no extra precision is kept and every FP64 result is
+ * computed from them.  Requirements and errors as bm_pointing_create. */
+bm_status bm_pointing_create_trig(bm_context* ctx, int64_t npix, int64_t nsamples, const int32_t* pix,
+                                  const float* cos2psi, const float* sin2psi, bm_solver_type solver,
+                                  bm_pointing** out);
 void bm_pointing_destroy(bm_pointing* p);
 /* hits device int32 [npix]: samples per pixel (flagged samples excluded). */
 bm_status bm_pointing_get_hits(const bm_pointing* p, int32_t* hits);

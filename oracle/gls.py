@@ -48,6 +48,20 @@ def pointing_weights(psi, ncomp: int) -> np.ndarray:
     raise ValueError("ncomp must be 1, 2 or 3")
 
 
+def pointing_weights_trig(c, s, ncomp: int) -> np.ndarray:
+    """Rows of P from precomputed c = cos 2psi and s = sin 2psi (e.g. FP32
+    values delivered with the data): the given numbers are the entries."""
+    c = np.asarray(c, np.float64)
+    s = np.asarray(s, np.float64)
+    if ncomp == IQU:
+        return np.stack([np.ones_like(c), c, s], axis=1)
+    if ncomp == QU:
+        return np.stack([c, s], axis=1)
+    if ncomp == I_ONLY:
+        return np.ones((c.size, 1))
+    raise ValueError("ncomp must be 1, 2 or 3")
+
+
 def hits(pix, npix: int) -> np.ndarray:
     """Number of samples in each pixel (flagged samples, pix = -1, not counted)."""
     pix = np.asarray(pix)
@@ -202,10 +216,11 @@ class System:
     """A = P^T N^-1 P on the kept pixels, with the preconditioner of Eq. 7."""
 
     def __init__(self, pix, psi, ncomp: int, npix: int, noise, min_hits: int = 3,
-                 max_cond: float = 1e3):
+                 max_cond: float = 1e3, trig=None):
+        """psi: polarisation angles; or trig = (cos 2psi, sin 2psi) given directly."""
         self.npix, self.ncomp, self.noise = npix, ncomp, noise
         self.pix = np.asarray(pix, np.int64)
-        self.v = pointing_weights(psi, ncomp)
+        self.v = pointing_weights(psi, ncomp) if trig is None else pointing_weights_trig(*trig, ncomp)
         self.hits = hits(self.pix, npix)
         self.B = block_matrices(self.pix, self.v, noise.white_level(), npix)
         self.mask = pixel_mask(self.hits, self.B, min_hits, max_cond)

@@ -59,6 +59,7 @@ _SIGS = {
     "bm_kernel_launches": ([], _i64),
     "bm_ang2pix_ring": ([_P, _i64, _i64, _P, _P, _P], ctypes.c_int),
     "bm_pointing_create": ([_P, _i64, _i64, _P, _P, ctypes.c_int, ctypes.c_int, _PP], ctypes.c_int),
+    "bm_pointing_create_trig": ([_P, _i64, _i64, _P, _P, _P, ctypes.c_int, _PP], ctypes.c_int),
     "bm_pointing_destroy": ([_P], None),
     "bm_pointing_get_hits": ([_P, _P], ctypes.c_int),
     "bm_pointing_apply": ([_P, _P, _P], ctypes.c_int),
@@ -182,6 +183,15 @@ def bm_pointing_create(ctx, npix: int, pix, psi, solver: int = BM_SOLVER_IQU):
     _check(lib.bm_pointing_create(ctx, int(npix), pix.numel(), _dev(pix, torch.int32, "pix"),
                                   _dev(psi, None, "psi"), _dtype_code(psi), int(solver), ctypes.byref(out)),
            "bm_pointing_create")
+    return out
+
+
+def bm_pointing_create_trig(ctx, npix: int, pix, cos2psi, sin2psi, solver: int = BM_SOLVER_IQU):
+    import torch
+    out = ctypes.c_void_p()
+    _check(lib.bm_pointing_create_trig(ctx, int(npix), pix.numel(), _dev(pix, torch.int32, "pix"),
+                                       _dev(cos2psi, torch.float32, "cos2psi"), _dev(sin2psi, torch.float32, "sin2psi"),
+                                       int(solver), ctypes.byref(out)), "bm_pointing_create_trig")
     return out
 
 

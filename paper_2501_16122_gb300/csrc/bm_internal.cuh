@@ -143,6 +143,9 @@ struct bm_inv_noise {
     std::vector<double> h_white;   // diag(N)^-1 per detector (the white level)
     bm::DevBuf<int64_t> det_off;   // [ndet + 1]
     bm::DevBuf<double> white;      // [ndet]
+    bm::DevBuf<uint32_t> det_off32;  // [ndet + 1] (nsamples < 2^32)
+    bm::DevBuf<float2> wdf;          // [ndet] white level as double-float (hi, lo)
+    bm::DevBuf<float> wsqrt;         // [ndet] sqrt of the white level, FP32
     // Toeplitz
     int64_t chunk_len = 0;
     int nlags = 0;
@@ -215,12 +218,14 @@ struct ScopedTimer {
 void resolve_timers(bm_context* ctx);
 
 // Launch wrappers implemented in the .cu files.
-void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dtype);
+void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dtype, const float* cos2psi,
+            const float* sin2psi);
 void build_precond(bm_precond* pc);
 void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, double* q,
             bm_precision prec, int64_t nrhs);
+// b = P^T N^-1 d_m; df = double-float accumulation (mixed path) instead of FP64.
 void rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dtype dt,
-         int64_t nrhs, double* b);
+         int64_t nrhs, double* b, bool df = false);
 void precond_apply(bm_precond* pc, const double* r, double* z, int64_t nrhs);
 void pointing_apply(bm_pointing* p, const double* x, double* y);
 void pointing_apply_transpose(bm_pointing* p, const double* y, double* x);
@@ -255,6 +260,23 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Per-detector tables of a noise model (device pointers).
+struct DetTables {
+    const uint32_t* off;   // [ndet + 1] sample offsets
+    const float2* wdf;     // [ndet] white weight w as a double-float (hi, lo)
+    const float* wsqrt;    // [ndet] sqrt(w) rounded to FP32
+};
+constexpr int kMaxDetSmem = 2048;  // detector tables staged in shared memory up to this count
+
+__device__ __forceinline__ int find_det32(const uint32_t* off, int ndet, uint32_t t) {
+    int lo = 0, hi = ndet - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Index of the detector owning sample t: largest d with off[d] <= t.
 __device__ __forceinline__ int find_det(const int64_t* off, int ndet, int64_t t) {
     int lo = 0, hi = ndet - 1;
@@ -267,6 +289,66 @@ __device__ __forceinline__ int find_det(const int64_t* off, int ndet, int64_t t)
 
 __device__ __forceinline__ double2 trig64(float2 hi, float2 lo) {
     return make_double2((double)hi.x + (double)lo.x, (double)hi.y + (double)lo.y);
+}
+// Trig pair of sorted/time sample i: hi + lo, where lo may be absent (exact FP32 trig).
+__device__ __forceinline__ double2 trig64_at(const float2* hi, const float2* lo, int64_t i) {
+    const float2 h = hi[i];
+    if (lo == nullptr) return make_double2((double)h.x, (double)h.y);
+    return trig64(h, lo[i]);
+}
+
+// ---- double-float arithmetic: a value is an unevaluated sum hi + lo of two
+// FP32 numbers (|lo| <= ulp(hi)/2), carrying ~48 significant bits on the FP32
+// pipes.  Built from the error-free transformations TwoSum (Knuth) and
+// TwoProduct with a fused multiply-add; every operation uses the explicitly
+// rounded intrinsics so the compiler cannot reassociate or contract them.
+struct df32 {
+    float hi, lo;
+};
+__device__ __forceinline__ df32 df_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+// Requires |a| >= |b| (or a == 0).
+__device__ __forceinline__ df32 df_quick_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df32 df_two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ df32 df_add(df32 a, df32 b) {
+    const df32 s = df_two_sum(a.hi, b.hi);
+    return df_quick_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df32 df_add(df32 a, float b) {
+    const df32 s = df_two_sum(a.hi, b);
+    return df_quick_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+__device__ __forceinline__ df32 df_mul(df32 a, df32 b) {
+    const df32 p = df_two_prod(a.hi, b.hi);
+    const float lo = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+    return df_quick_two_sum(p.hi, lo);
+}
+__device__ __forceinline__ df32 df_mul(df32 a, float b) {
+    const df32 p = df_two_prod(a.hi, b);
+    return df_quick_two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
+}
+__device__ __forceinline__ df32 df_from(double x) {
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double df_to_double(df32 a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ df32 df_shfl_xor(df32 a, int o) {
+    return {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+__device__ __forceinline__ df32 df_warp_sum(df32 a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a = df_add(a, df_shfl_xor(a, o));
+    return a;
 }
 
 }  // namespace bm

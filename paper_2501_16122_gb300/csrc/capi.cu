@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <cmath>
 #include <new>
 
 #include "bm_internal.cuh"
@@ -244,7 +245,35 @@ bm_status bm_pointing_create(bm_context* ctx, int64_t npix, int64_t nsamples, co
         p->nsamples = nsamples;
         p->ncomp = (int)solver;
         try {
-            ingest(p, pix, psi, psi_dtype);
+            ingest(p, pix, psi, psi_dtype, nullptr, nullptr);
+        } catch (...) {
+            delete p;
+            throw;
+        }
+        *out = p;
+        return BM_OK;
+    });
+}
+
+bm_status bm_pointing_create_trig(bm_context* ctx, int64_t npix, int64_t nsamples, const int32_t* pix,
+                                  const float* cos2psi, const float* sin2psi, bm_solver_type solver,
+                                  bm_pointing** out) {
+    return guarded([&] {
+        BM_REQUIRE(ctx && out, "ctx/out is NULL");
+        *out = nullptr;
+        BM_REQUIRE(npix >= 1 && npix <= (int64_t(1) << 28), "npix %lld out of [1, 2^28]", (long long)npix);
+        BM_REQUIRE(nsamples >= 1 && nsamples < (int64_t(1) << 32), "nsamples out of [1, 2^32)");
+        BM_REQUIRE(pix && cos2psi && sin2psi, "pix/cos2psi/sin2psi is NULL");
+        BM_REQUIRE(solver == BM_SOLVER_I || solver == BM_SOLVER_QU || solver == BM_SOLVER_IQU,
+                   "bad solver type %d", (int)solver);
+        use_device(ctx);
+        auto* p = new bm_pointing();
+        p->ctx = ctx;
+        p->npix = npix;
+        p->nsamples = nsamples;
+        p->ncomp = (int)solver;
+        try {
+            ingest(p, pix, nullptr, BM_F32, cos2psi, sin2psi);
         } catch (...) {
             delete p;
             throw;
@@ -298,6 +327,7 @@ static void check_det_offsets(int32_t ndet, const int64_t* det_offsets) {
     BM_REQUIRE(det_offsets[0] == 0, "det_offsets[0] must be 0");
     for (int d = 0; d < ndet; ++d)
         BM_REQUIRE(det_offsets[d + 1] > det_offsets[d], "det_offsets not increasing at %d", d);
+    BM_REQUIRE(det_offsets[ndet] < (int64_t(1) << 32), "more than 2^32 - 1 samples");
 }
 
 static bm_inv_noise* new_noise(bm_context* ctx, int32_t ndet, const int64_t* det_offsets,
@@ -313,6 +343,20 @@ static bm_inv_noise* new_noise(bm_context* ctx, int32_t ndet, const int64_t* det
         n->white.alloc(ndet);
         upload(ctx, n->det_off.get(), det_offsets, sizeof(int64_t) * (ndet + 1));
         upload(ctx, n->white.get(), white, sizeof(double) * ndet);
+        std::vector<uint32_t> off32(det_offsets, det_offsets + ndet + 1);
+        std::vector<float2> wdf(ndet);
+        std::vector<float> wsq(ndet);
+        for (int d = 0; d < ndet; ++d) {
+            const float h = (float)white[d];
+            wdf[d] = make_float2(h, (float)(white[d] - (double)h));
+            wsq[d] = (float)std::sqrt(white[d]);
+        }
+        n->det_off32.alloc(ndet + 1);
+        n->wdf.alloc(ndet);
+        n->wsqrt.alloc(ndet);
+        upload(ctx, n->det_off32.get(), off32.data(), sizeof(uint32_t) * (ndet + 1));
+        upload(ctx, n->wdf.get(), wdf.data(), sizeof(float2) * ndet);
+        upload(ctx, n->wsqrt.get(), wsq.data(), sizeof(float) * ndet);
     } catch (...) {
         delete n;
         throw;

@@ -13,17 +13,29 @@ namespace bm {
 namespace {
 
 // ----------------------------------------------------------------- validate
+// Checks pixel indices and angles (or the given cos/sin pairs, |.| <= 1),
+// copies pix and writes the sort keys.  With cos/sin given, also interleaves
+// them into the time-ordered trig array.
 __global__ void validate_kernel(const int32_t* __restrict__ pix, const void* __restrict__ psi,
-                                int psi_f64, int64_t n, int64_t npix, int32_t* __restrict__ pix_out,
-                                uint32_t* __restrict__ keys, unsigned long long* __restrict__ bad) {
+                                int psi_f64, const float* __restrict__ c32, const float* __restrict__ s32,
+                                int64_t n, int64_t npix, int32_t* __restrict__ pix_out,
+                                uint32_t* __restrict__ keys, float2* __restrict__ hi,
+                                unsigned long long* __restrict__ bad) {
     unsigned long long nbad = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t p = pix[i];
-        const double a = psi_f64 ? static_cast<const double*>(psi)[i]
-                                 : (double)static_cast<const float*>(psi)[i];
         const bool ok_p = (p >= -1) && ((int64_t)p < npix);
-        const bool ok_a = isfinite(a);
+        bool ok_a;
+        if (c32) {
+            const float c = c32[i], s = s32[i];
+            ok_a = fabsf(c) <= 1.0f && fabsf(s) <= 1.0f;  // false for NaN
+            hi[i] = make_float2(c, s);
+        } else {
+            const double a = psi_f64 ? static_cast<const double*>(psi)[i]
+                                     : (double)static_cast<const float*>(psi)[i];
+            ok_a = isfinite(a);
+        }
         nbad += (!ok_p) + (!ok_a);
         pix_out[i] = ok_p ? p : -1;
         keys[i] = (ok_p && p >= 0) ? (uint32_t)p : (uint32_t)npix;  // flagged sort last
@@ -192,13 +204,14 @@ __global__ void gather_trig_kernel(const uint32_t* __restrict__ perm, int64_t n,
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t t = perm[i];
         hi_s[i] = hi_t[t];
-        lo_s[i] = lo_t[t];
+        if (lo_t) lo_s[i] = lo_t[t];
     }
 }
 
 }  // namespace
 
-void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dtype) {
+void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dtype, const float* cos2psi,
+            const float* sin2psi) {
     bm_context* ctx = p->ctx;
     cudaStream_t s = ctx->stream;
     ScopedTimer timer(ctx, "ingest");
@@ -207,23 +220,26 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
     const int threads = 256;
     const int grid = grid_for(ctx, (n + threads - 1) / threads, 16);
 
+    const bool exact_trig = cos2psi != nullptr;  // FP32 trig given: it defines the operator, no lo part
     p->pix.alloc(n);
     p->cs_hi_t.alloc(n);
-    p->cs_lo_t.alloc(n);
+    if (!exact_trig) p->cs_lo_t.alloc(n);
     DevBuf<uint32_t> keys_a(n), keys_b(n), vals_a(n), vals_b(n);
     DevBuf<unsigned long long> bad(1);
     BM_CUDA(cudaMemsetAsync(bad.get(), 0, sizeof(unsigned long long), s));
-    validate_kernel<<<grid, threads, 0, s>>>(pix, psi, psi_f64, n, npix, p->pix.get(), keys_a.get(),
-                                             bad.get());
+    validate_kernel<<<grid, threads, 0, s>>>(pix, psi, psi_f64, cos2psi, sin2psi, n, npix, p->pix.get(),
+                                             keys_a.get(), p->cs_hi_t.get(), bad.get());
     BM_LAUNCH_CHECK();
     unsigned long long h_bad = 0;
     BM_CUDA(cudaMemcpyAsync(&h_bad, bad.get(), sizeof(h_bad), cudaMemcpyDeviceToHost, s));
     BM_CUDA(cudaStreamSynchronize(s));
-    BM_REQUIRE(h_bad == 0, "%llu samples have a pixel index outside [-1, %lld) or a non-finite angle",
+    BM_REQUIRE(h_bad == 0, "%llu samples have a pixel index outside [-1, %lld) or a bad angle / trig value",
                h_bad, (long long)npix);
 
-    trig_kernel<<<grid, threads, 0, s>>>(psi, psi_f64, n, p->cs_hi_t.get(), p->cs_lo_t.get());
-    BM_LAUNCH_CHECK();
+    if (!exact_trig) {
+        trig_kernel<<<grid, threads, 0, s>>>(psi, psi_f64, n, p->cs_hi_t.get(), p->cs_lo_t.get());
+        BM_LAUNCH_CHECK();
+    }
 
     // LSD radix sort of (key, sample index) over the bits of npix.
     int nbits = 1;
@@ -262,7 +278,7 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
 
     p->perm.alloc(nvalid > 0 ? nvalid : 1);
     p->cs_hi_s.alloc(nvalid > 0 ? nvalid : 1);
-    p->cs_lo_s.alloc(nvalid > 0 ? nvalid : 1);
+    if (!exact_trig) p->cs_lo_s.alloc(nvalid > 0 ? nvalid : 1);
     if (nvalid > 0) {
         BM_CUDA(cudaMemcpyAsync(p->perm.get(), vin, sizeof(uint32_t) * nvalid, cudaMemcpyDeviceToDevice, s));
         gather_trig_kernel<<<grid, threads, 0, s>>>(p->perm.get(), nvalid, p->cs_hi_t.get(), p->cs_lo_t.get(),

@@ -36,6 +36,13 @@ __global__ void masked_copy_kernel(const double* __restrict__ x, const uint8_t* 
 }
 
 // ------------------------------------------------------- white, FP32 form
+// One work item per warp.  Loads are 16 bytes per lane (two samples of the
+// (u_c, u_s) stream, four of the I-only weight stream) after a scalar head
+// that aligns the item start; each lane sums a group of samples in FP32 and
+// folds the group into a compensated (double-float) accumulator, the warp
+// combines the accumulators in double-float, and lane 0 writes the FP64 item
+// partial.  sqrt(w) = |u| is formed as |u|^2 * rsqrt(|u|^2); the same value
+// multiplies x_I and the I output, so the operator stays symmetric.
 template <int NC>
 __global__ void __launch_bounds__(kWarps * 32)
 white_matvec_f32_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ item_beg,
@@ -46,53 +53,94 @@ white_matvec_f32_kernel(const int32_t* __restrict__ item_pix, const int64_t* __r
     const int64_t nwarps = (int64_t)gridDim.x * kWarps;
     for (int64_t k = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); k < nitems; k += nwarps) {
         const int64_t p = item_pix[k];
-        const int64_t b = item_beg[k];
-        const int len = item_len[k];
+        int64_t b = item_beg[k];
+        int len = item_len[k];
         if (NC == 1) {
             const float xi = x32[p];
-            float acc = 0.f;
-            int i = lane;
-            for (; i + 96 < len; i += 128) {
-                const float a0 = __ldg(w1 + b + i), a1 = __ldg(w1 + b + i + 32);
-                const float a2 = __ldg(w1 + b + i + 64), a3 = __ldg(w1 + b + i + 96);
-                acc += (a0 + a1) + (a2 + a3);
+            df32 A = {0.f, 0.f};
+            const int head = (int)((4 - (b & 3)) & 3) < len ? (int)((4 - (b & 3)) & 3) : len;
+            if (lane < head) A = df_add(A, __ldg(w1 + b + lane));
+            b += head;
+            len -= head;
+            const float4* src4 = reinterpret_cast<const float4*>(w1 + b);
+            const int nq = len >> 2;
+            int j = lane;
+            for (; j + 32 < nq; j += 64) {
+                const float4 a = __ldg(src4 + j), c = __ldg(src4 + j + 32);
+                A = df_add(A, ((a.x + a.y) + (a.z + a.w)) + ((c.x + c.y) + (c.z + c.w)));
             }
-            for (; i < len; i += 32) acc += __ldg(w1 + b + i);
-            const double s = warp_sum((double)acc) * (double)xi;
-            if (lane == 0) partial[k] = s;
+            for (; j < nq; j += 32) {
+                const float4 a = __ldg(src4 + j);
+                A = df_add(A, (a.x + a.y) + (a.z + a.w));
+            }
+            const int rem = len & 3;
+            if (lane < rem) A = df_add(A, __ldg(w1 + b + 4 * nq + lane));
+            A = df_warp_sum(A);
+            if (lane == 0) partial[k] = df_to_double(A) * (double)xi;
         } else {
             float xI = 0.f, xQ, xU;
             if (NC == 3) { xI = x32[3 * p]; xQ = x32[3 * p + 1]; xU = x32[3 * p + 2]; }
             else { xQ = x32[2 * p]; xU = x32[2 * p + 1]; }
-            float aI = 0.f, aQ = 0.f, aU = 0.f;
-            const float2* src = wcs + b;
+            float aI = 0.f, aQ = 0.f, aU = 0.f;  // FP32 group sums
+            df32 AI = {0.f, 0.f}, AQ = {0.f, 0.f}, AU = {0.f, 0.f};
             auto step = [&](float2 u) {
-                // u = sqrt(w) (c, s); sqrt(w) = |u| carries the I column.
-                const float r = NC == 3 ? sqrtf(fmaf(u.x, u.x, u.y * u.y)) : 0.f;
+                float r = 0.f;
+                if (NC == 3) {
+                    const float u2 = fmaf(u.x, u.x, u.y * u.y);
+                    r = u2 * rsqrtf(u2);
+                }
                 const float y = fmaf(u.x, xQ, fmaf(u.y, xU, r * xI));
                 if (NC == 3) aI = fmaf(y, r, aI);
                 aQ = fmaf(y, u.x, aQ);
                 aU = fmaf(y, u.y, aU);
             };
-            int i = lane;
-            for (; i + 96 < len; i += 128) {
-                const float2 u0 = __ldg(src + i), u1 = __ldg(src + i + 32);
-                const float2 u2 = __ldg(src + i + 64), u3 = __ldg(src + i + 96);
-                step(u0); step(u1); step(u2); step(u3);
+            auto fold = [&]() {
+                if (NC == 3) AI = df_add(AI, aI);
+                AQ = df_add(AQ, aQ);
+                AU = df_add(AU, aU);
+                aI = aQ = aU = 0.f;
+            };
+            if (b & 1) {  // align the stream to 16 bytes
+                if (lane == 0) step(__ldg(wcs + b));
+                ++b;
+                --len;
             }
-            for (; i < len; i += 32) step(__ldg(src + i));
-            const double sQ = warp_sum((double)aQ), sU = warp_sum((double)aU);
-            const double sI = NC == 3 ? warp_sum((double)aI) : 0.0;
+            const float4* src4 = reinterpret_cast<const float4*>(wcs + b);
+            const int np = len >> 1;  // sample pairs
+            int j = lane;
+            for (; j + 96 < np; j += 128) {
+                const float4 u0 = __ldg(src4 + j), u1 = __ldg(src4 + j + 32);
+                const float4 u2 = __ldg(src4 + j + 64), u3 = __ldg(src4 + j + 96);
+                step(make_float2(u0.x, u0.y)); step(make_float2(u0.z, u0.w));
+                step(make_float2(u1.x, u1.y)); step(make_float2(u1.z, u1.w));
+                step(make_float2(u2.x, u2.y)); step(make_float2(u2.z, u2.w));
+                step(make_float2(u3.x, u3.y)); step(make_float2(u3.z, u3.w));
+                fold();
+            }
+            for (; j < np; j += 32) {
+                const float4 u0 = __ldg(src4 + j);
+                step(make_float2(u0.x, u0.y)); step(make_float2(u0.z, u0.w));
+            }
+            if ((len & 1) && lane == 0) step(__ldg(wcs + b + len - 1));
+            fold();
+            AQ = df_warp_sum(AQ);
+            AU = df_warp_sum(AU);
+            if (NC == 3) AI = df_warp_sum(AI);
             if (lane == 0) {
-                if (NC == 3) { partial[3 * k] = sI; partial[3 * k + 1] = sQ; partial[3 * k + 2] = sU; }
-                else { partial[2 * k] = sQ; partial[2 * k + 1] = sU; }
+                if (NC == 3) {
+                    partial[3 * k] = df_to_double(AI);
+                    partial[3 * k + 1] = df_to_double(AQ);
+                    partial[3 * k + 2] = df_to_double(AU);
+                } else {
+                    partial[2 * k] = df_to_double(AQ);
+                    partial[2 * k + 1] = df_to_double(AU);
+                }
             }
         }
     }
 }
 
 // ------------------------------------------------------- white, FP64 form
-constexpr int kMaxDetSmem = 4096;
 
 template <int NC>
 __global__ void __launch_bounds__(kWarps * 32)
@@ -126,7 +174,7 @@ white_matvec_f64_kernel(const int32_t* __restrict__ item_pix, const int64_t* __r
             if (NC == 1) {
                 acc[0] += w * xv[0];
             } else {
-                const double2 cs = trig64(hi[si], lo[si]);
+                const double2 cs = trig64_at(hi, lo, si);
                 double y = cs.x * xv[NC - 2] + cs.y * xv[NC - 1];
                 if (NC == 3) y += xv[0];
                 const double wy = w * y;
@@ -145,51 +193,86 @@ white_matvec_f64_kernel(const int32_t* __restrict__ item_pix, const int64_t* __r
 
 // ---------------------------------------------- pixel-sorted gather-reduce
 // q_p partial = sum over item samples of g[perm_i] * f * v_i, where
-// f = w_d(perm_i) when `white` is given, else 1.  G is float or double;
-// the trig is the FP64 (hi + lo) value when EXACT, else hi.
-template <int NC, typename G, bool EXACT>
+// f = w_d(perm_i) when `weighted`, else 1, and v_i the pointing row.  G is
+// float or double.  Two arithmetic forms:
+//   DF = false: FP64 products and sums (trig hi + lo), as the FP64 path needs;
+//   DF = true : double-float products and sums on the FP32 pipes (~48 bits);
+//               the trig pair is (hi, lo) when present, else the exact hi.
+template <int NC, typename G, bool DF>
 __global__ void __launch_bounds__(kWarps * 32)
 gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ item_beg,
                      const int32_t* __restrict__ item_len, int64_t nitems,
                      const uint32_t* __restrict__ perm, const float2* __restrict__ hi,
-                     const float2* __restrict__ lo, const G* __restrict__ g,
-                     const int64_t* __restrict__ det_off, int ndet, const double* __restrict__ white,
-                     double* __restrict__ partial) {
-    __shared__ int64_t s_off[kMaxDetSmem + 1];
-    const bool in_smem = white != nullptr && ndet <= kMaxDetSmem;
-    if (in_smem)
-        for (int d = threadIdx.x; d <= ndet; d += blockDim.x) s_off[d] = det_off[d];
+                     const float2* __restrict__ lo, const G* __restrict__ g, bool weighted, DetTables dt,
+                     const double* __restrict__ white, int ndet, double* __restrict__ partial) {
+    __shared__ uint32_t s_off[kMaxDetSmem + 1];
+    __shared__ float2 s_w[kMaxDetSmem];
+    const bool in_smem = weighted && ndet <= kMaxDetSmem;
+    if (in_smem) {
+        for (int d = threadIdx.x; d <= ndet; d += blockDim.x) s_off[d] = dt.off[d];
+        for (int d = threadIdx.x; d < ndet; d += blockDim.x) s_w[d] = dt.wdf[d];
+    }
     __syncthreads();
-    const int64_t* offp = in_smem ? s_off : det_off;
+    const uint32_t* offp = in_smem ? s_off : dt.off;
+    const float2* wp = in_smem ? s_w : dt.wdf;
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * kWarps;
     for (int64_t k = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); k < nitems; k += nwarps) {
         const int64_t b = item_beg[k];
         const int len = item_len[k];
-        double acc[NC];
+        if (DF) {
+            df32 acc[NC];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] = 0.0;
-        for (int i = lane; i < len; i += 32) {
-            const int64_t si = b + i;
-            const uint32_t t = perm[si];
-            double val = (double)g[t];
-            if (white) val *= white[find_det(offp, ndet, t)];
-            if (NC == 1) {
-                acc[0] += val;
-            } else {
-                double c, s;
-                if (EXACT) { const double2 cs = trig64(hi[si], lo[si]); c = cs.x; s = cs.y; }
-                else { const float2 h = hi[si]; c = h.x; s = h.y; }
-                if (NC == 3) acc[0] += val;
-                acc[NC - 2] += val * c;
-                acc[NC - 1] += val * s;
+            for (int c = 0; c < NC; ++c) acc[c] = {0.f, 0.f};
+            for (int i = lane; i < len; i += 32) {
+                const int64_t si = b + i;
+                const uint32_t t = perm[si];
+                df32 val;
+                if (sizeof(G) == 4) val = {(float)g[t], 0.f};
+                else val = df_from((double)g[t]);
+                if (weighted) {
+                    const float2 w = wp[find_det32(offp, ndet, t)];
+                    val = df_mul(val, df32{w.x, w.y});
+                }
+                if (NC == 1) {
+                    acc[0] = df_add(acc[0], val);
+                } else {
+                    const float2 h = hi[si];
+                    const float2 l = lo ? lo[si] : make_float2(0.f, 0.f);
+                    if (NC == 3) acc[0] = df_add(acc[0], val);
+                    acc[NC - 2] = df_add(acc[NC - 2], df_mul(val, df32{h.x, l.x}));
+                    acc[NC - 1] = df_add(acc[NC - 1], df_mul(val, df32{h.y, l.y}));
+                }
             }
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[c] = df_warp_sum(acc[c]);
+            if (lane == 0)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) partial[NC * k + c] = df_to_double(acc[c]);
+        } else {
+            double acc[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+            for (int i = lane; i < len; i += 32) {
+                const int64_t si = b + i;
+                const uint32_t t = perm[si];
+                double val = (double)g[t];
+                if (weighted) val *= white[find_det32(offp, ndet, t)];
+                if (NC == 1) {
+                    acc[0] += val;
+                } else {
+                    const double2 cs = trig64_at(hi, lo, si);
+                    if (NC == 3) acc[0] += val;
+                    acc[NC - 2] += val * cs.x;
+                    acc[NC - 1] += val * cs.y;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[c] = warp_sum(acc[c]);
+            if (lane == 0)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) partial[NC * k + c] = acc[c];
         }
-#pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] = warp_sum(acc[c]);
-        if (lane == 0)
-#pragma unroll
-            for (int c = 0; c < NC; ++c) partial[NC * k + c] = acc[c];
     }
 }
 
@@ -220,7 +303,7 @@ __global__ void pointing_apply_kernel(const int32_t* __restrict__ pix, const flo
             if (nc == 1) {
                 v = x[p];
             } else {
-                const double2 cs = trig64(hi[t], lo[t]);
+                const double2 cs = trig64_at(hi, lo, t);
                 const double* xp = x + (int64_t)p * nc;
                 v = cs.x * xp[nc - 2] + cs.y * xp[nc - 1];
                 if (nc == 3) v += xp[0];
@@ -251,7 +334,7 @@ struct SrcMatvecF64 {  // y_t = v_t . xm[p_t] (xm zero on masked pixels), FP64 t
         const int32_t p = pix[t];
         if (p < 0) return 0.0;
         if (nc == 1) return x[p];
-        const double2 cs = trig64(hi[t], lo[t]);
+        const double2 cs = trig64_at(hi, lo, t);
         const double* xp = x + (int64_t)p * nc;
         double v = cs.x * xp[nc - 2] + cs.y * xp[nc - 1];
         if (nc == 3) v += xp[0];
@@ -411,20 +494,38 @@ static void finalize(bm_context* ctx, const int64_t* pitem, const double* partia
     BM_LAUNCH_CHECK();
 }
 
+// q = P^T-style pixel sums of g[perm] (times w_d when `wn` is given) over the
+// given items; lo = the sorted trig's lo part (or NULL to use hi exactly);
+// df selects double-float instead of FP64 arithmetic.
+struct ItemsView {
+    const int32_t* pix;
+    const int64_t* beg;
+    const int32_t* len;
+    int64_t n;
+    const int64_t* pitem;
+};
+static ItemsView kept_items(const bm_precond* pc) {
+    return {pc->item_pix.get(), pc->item_beg.get(), pc->item_len.get(), pc->nitems, pc->pitem.get()};
+}
+
 template <typename G>
-static void gather_reduce(bm_pointing* p, const int32_t* item_pix, const int64_t* item_beg,
-                          const int32_t* item_len, int64_t nitems, const int64_t* pitem, const G* g,
-                          const int64_t* det_off, int ndet, const double* white, bool exact, double* q) {
+static void gather_reduce(bm_pointing* p, const ItemsView& it, const G* g, const bm_inv_noise* wn,
+                          const float2* lo, bool df, double* q) {
     bm_context* ctx = p->ctx;
     const int nc = p->ncomp;
-    double* partial = workspace_as<double>(ctx, "partial", (size_t)std::max<int64_t>(nitems, 1) * nc);
-    if (nitems > 0) {
-        const int grid = grid_for(ctx, (nitems + kWarps - 1) / kWarps, 8);
-#define BM_GR(NC, EX)                                                                                     \
-    gather_reduce_kernel<NC, G, EX><<<grid, kWarps * 32, 0, ctx->stream>>>(                                \
-        item_pix, item_beg, item_len, nitems, p->perm.get(), p->cs_hi_s.get(), p->cs_lo_s.get(), g, det_off, \
-        ndet, white, partial)
-        if (exact) {
+    double* partial = workspace_as<double>(ctx, "partial", (size_t)std::max<int64_t>(it.n, 1) * nc);
+    if (it.n > 0) {
+        const int grid = grid_for(ctx, (it.n + kWarps - 1) / kWarps, 8);
+        const bool weighted = wn != nullptr;
+        const DetTables dt = weighted ? DetTables{wn->det_off32.get(), wn->wdf.get(), wn->wsqrt.get()}
+                                      : DetTables{nullptr, nullptr, nullptr};
+        const double* white = weighted ? wn->white.get() : nullptr;
+        const int ndet = weighted ? wn->ndet : 0;
+#define BM_GR(NC, D)                                                                                           \
+    gather_reduce_kernel<NC, G, D><<<grid, kWarps * 32, 0, ctx->stream>>>(it.pix, it.beg, it.len, it.n,          \
+                                                                         p->perm.get(), p->cs_hi_s.get(), lo, g, \
+                                                                         weighted, dt, white, ndet, partial)
+        if (df) {
             if (nc == 3) BM_GR(3, true); else if (nc == 2) BM_GR(2, true); else BM_GR(1, true);
         } else {
             if (nc == 3) BM_GR(3, false); else if (nc == 2) BM_GR(2, false); else BM_GR(1, false);
@@ -432,7 +533,7 @@ static void gather_reduce(bm_pointing* p, const int32_t* item_pix, const int64_t
 #undef BM_GR
         BM_LAUNCH_CHECK();
     }
-    finalize(ctx, pitem, partial, p->npix, nc, q);
+    finalize(ctx, it.pitem, partial, p->npix, nc, q);
 }
 
 void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, double* q,
@@ -485,8 +586,8 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
                     SrcMatvecF32 src{p->pix.get(), p->cs_hi_t.get(), x32, nc};
                     run_toeplitz<float, 8>(n, src, n->coeffs32.get(), z32);
                 }
-                gather_reduce<float>(p, pc->item_pix.get(), pc->item_beg.get(), pc->item_len.get(), pc->nitems,
-                                     pc->pitem.get(), z32, nullptr, 0, nullptr, false, qr);
+                // scatter with the same FP32 trig the gather used (symmetric operator)
+                gather_reduce<float>(p, kept_items(pc), z32, nullptr, nullptr, true, qr);
             } else {
                 double* xm = workspace_as<double>(ctx, "xm", nvec);
                 double* z64 = workspace_as<double>(ctx, "z64", p->nsamples);
@@ -497,15 +598,14 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
                     SrcMatvecF64 src{p->pix.get(), p->cs_hi_t.get(), p->cs_lo_t.get(), xm, nc};
                     run_toeplitz<double, 4>(n, src, n->coeffs64.get(), z64);
                 }
-                gather_reduce<double>(p, pc->item_pix.get(), pc->item_beg.get(), pc->item_len.get(), pc->nitems,
-                                      pc->pitem.get(), z64, nullptr, 0, nullptr, true, qr);
+                gather_reduce<double>(p, kept_items(pc), z64, nullptr, p->cs_lo_s.get(), false, qr);
             }
         }
     }
 }
 
 void rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dtype dt, int64_t nrhs,
-         double* b) {
+         double* b, bool df) {
     bm_context* ctx = p->ctx;
     const int nc = p->ncomp;
     const int64_t nvec = p->npix * nc;
@@ -515,12 +615,10 @@ void rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dt
         if (n->kind == 0) {
             if (dt == BM_F32) {
                 const float* d = static_cast<const float*>(tod) + r * p->nsamples;
-                gather_reduce<float>(p, pc->item_pix.get(), pc->item_beg.get(), pc->item_len.get(), pc->nitems,
-                                     pc->pitem.get(), d, n->det_off.get(), n->ndet, n->white.get(), true, br);
+                gather_reduce<float>(p, kept_items(pc), d, n, p->cs_lo_s.get(), df, br);
             } else {
                 const double* d = static_cast<const double*>(tod) + r * p->nsamples;
-                gather_reduce<double>(p, pc->item_pix.get(), pc->item_beg.get(), pc->item_len.get(), pc->nitems,
-                                      pc->pitem.get(), d, n->det_off.get(), n->ndet, n->white.get(), true, br);
+                gather_reduce<double>(p, kept_items(pc), d, n, p->cs_lo_s.get(), df, br);
             }
         } else {
             double* z64 = workspace_as<double>(ctx, "z64", p->nsamples);
@@ -533,8 +631,7 @@ void rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dt
                                          static_cast<const double*>(tod) + r * p->nsamples};
                 run_toeplitz<double, 4>(n, src, n->coeffs64.get(), z64);
             }
-            gather_reduce<double>(p, pc->item_pix.get(), pc->item_beg.get(), pc->item_len.get(), pc->nitems,
-                                  pc->pitem.get(), z64, nullptr, 0, nullptr, true, br);
+            gather_reduce<double>(p, kept_items(pc), z64, nullptr, p->cs_lo_s.get(), df, br);
         }
     }
 }
@@ -550,8 +647,8 @@ void pointing_apply(bm_pointing* p, const double* x, double* y) {
 void pointing_apply_transpose(bm_pointing* p, const double* y, double* x) {
     Items it;
     plan_items(p->ctx, p->off.get(), nullptr, p->npix, it);
-    gather_reduce<double>(p, it.pix.get(), it.beg.get(), it.len.get(), it.n, it.pitem.get(), y, nullptr, 0,
-                          nullptr, true, x);
+    const ItemsView v{it.pix.get(), it.beg.get(), it.len.get(), it.n, it.pitem.get()};
+    gather_reduce<double>(p, v, y, nullptr, p->cs_lo_s.get(), false, x);
     BM_CUDA(cudaStreamSynchronize(p->ctx->stream));
 }
 

@@ -69,60 +69,79 @@ void plan_items(bm_context* ctx, const int64_t* off, const uint8_t* mask, int64_
 namespace {
 
 constexpr int kBlkWarps = 8;
-constexpr int kMaxDetSmem = 4096;
 
-// Unique entries of the symmetric block, row-major upper triangle:
-// IQU: (II, IQ, IU, QQ, QU, UU); QU: (QQ, QU, UU); I: (II).
-template <int NC>
+// B_p partials per work item.  Unique entries of the symmetric block,
+// row-major upper triangle: IQU (II, IQ, IU, QQ, QU, UU); QU (QQ, QU, UU); I (II).
+// Every product and sum is double-float (w and the trig pair carry ~48 bits),
+// so the block keeps FP64-level accuracy without FP64 instructions per sample;
+// the warp total is converted to FP64 once per item.  For white noise the
+// same pass writes the weighted FP32 stream sqrt(w) (cos, sin) (w for I-only)
+// that the FP32 matvec reads.
+template <int NC, bool WCS>
 __global__ void __launch_bounds__(kBlkWarps * 32)
 blocks_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ item_beg,
               const int32_t* __restrict__ item_len, int64_t nitems, const uint32_t* __restrict__ perm,
-              const float2* __restrict__ hi, const float2* __restrict__ lo,
-              const int64_t* __restrict__ det_off, int ndet, const double* __restrict__ white,
-              double* __restrict__ partial) {
+              const float2* __restrict__ hi, const float2* __restrict__ lo, DetTables g, int ndet,
+              double* __restrict__ partial, float2* __restrict__ wcs, float* __restrict__ w1) {
     constexpr int NS = NC * (NC + 1) / 2;
-    __shared__ int64_t s_off[kMaxDetSmem + 1];
-    const bool smem_off = ndet <= kMaxDetSmem;
-    if (smem_off)
-        for (int d = threadIdx.x; d <= ndet; d += blockDim.x) s_off[d] = det_off[d];
+    __shared__ uint32_t s_off[kMaxDetSmem + 1];
+    __shared__ float2 s_w[kMaxDetSmem];
+    __shared__ float s_sw[kMaxDetSmem];
+    const bool in_smem = ndet <= kMaxDetSmem;
+    if (in_smem) {
+        for (int d = threadIdx.x; d <= ndet; d += blockDim.x) s_off[d] = g.off[d];
+        for (int d = threadIdx.x; d < ndet; d += blockDim.x) { s_w[d] = g.wdf[d]; s_sw[d] = g.wsqrt[d]; }
+    }
     __syncthreads();
-    const int64_t* offp = smem_off ? s_off : det_off;
+    const uint32_t* offp = in_smem ? s_off : g.off;
+    const float2* wp = in_smem ? s_w : g.wdf;
+    const float* swp = in_smem ? s_sw : g.wsqrt;
     const int lane = threadIdx.x & 31;
-    const int64_t warp = (int64_t)blockIdx.x * kBlkWarps + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * kBlkWarps;
-    for (int64_t k = warp; k < nitems; k += nwarps) {
+    for (int64_t k = (int64_t)blockIdx.x * kBlkWarps + (threadIdx.x >> 5); k < nitems; k += nwarps) {
         const int64_t b = item_beg[k];
         const int len = item_len[k];
-        double acc[NS];
+        df32 acc[NS];
 #pragma unroll
-        for (int j = 0; j < NS; ++j) acc[j] = 0.0;
+        for (int j = 0; j < NS; ++j) acc[j] = {0.f, 0.f};
         for (int i = lane; i < len; i += 32) {
             const int64_t si = b + i;
-            const uint32_t t = perm[si];
-            const double w = white[find_det(offp, ndet, t)];
-            const double2 cs = trig64(hi[si], lo[si]);
+            const int d = find_det32(offp, ndet, perm[si]);
+            const float2 wv = wp[d];
+            const df32 w = {wv.x, wv.y};
+            const float2 h = hi[si];
+            const float2 l = lo ? lo[si] : make_float2(0.f, 0.f);
+            const df32 c = {h.x, l.x}, s = {h.y, l.y};
             if (NC == 3) {
-                const double wc = w * cs.x, ws = w * cs.y;
-                acc[0] += w;
-                acc[1] += wc;
-                acc[2] += ws;
-                acc[3] += wc * cs.x;
-                acc[4] += wc * cs.y;
-                acc[5] += ws * cs.y;
+                const df32 wc = df_mul(w, c), ws = df_mul(w, s);
+                acc[0] = df_add(acc[0], w);
+                acc[1] = df_add(acc[1], wc);
+                acc[2] = df_add(acc[2], ws);
+                acc[3] = df_add(acc[3], df_mul(wc, c));
+                acc[4] = df_add(acc[4], df_mul(wc, s));
+                acc[5] = df_add(acc[5], df_mul(ws, s));
             } else if (NC == 2) {
-                const double wc = w * cs.x, ws = w * cs.y;
-                acc[0] += wc * cs.x;
-                acc[1] += wc * cs.y;
-                acc[2] += ws * cs.y;
+                const df32 wc = df_mul(w, c), ws = df_mul(w, s);
+                acc[0] = df_add(acc[0], df_mul(wc, c));
+                acc[1] = df_add(acc[1], df_mul(wc, s));
+                acc[2] = df_add(acc[2], df_mul(ws, s));
             } else {
-                acc[0] += w;
+                acc[0] = df_add(acc[0], w);
+            }
+            if (WCS) {
+                if (NC == 1) {
+                    w1[si] = wv.x;
+                } else {
+                    const float sw = swp[d];
+                    wcs[si] = make_float2(sw * h.x, sw * h.y);
+                }
             }
         }
 #pragma unroll
-        for (int j = 0; j < NS; ++j) acc[j] = warp_sum(acc[j]);
+        for (int j = 0; j < NS; ++j) acc[j] = df_warp_sum(acc[j]);
         if (lane == 0) {
 #pragma unroll
-            for (int j = 0; j < NS; ++j) partial[k * NS + j] = acc[j];
+            for (int j = 0; j < NS; ++j) partial[k * NS + j] = df_to_double(acc[j]);
         }
     }
 }
@@ -234,25 +253,6 @@ __global__ void finalize_blocks_kernel(const int64_t* __restrict__ pitem, const 
     }
 }
 
-// Weighted FP32 stream for the white-noise FP32 matvec, in pixel-sorted order.
-__global__ void weighted_stream_kernel(const uint32_t* __restrict__ perm, int64_t n,
-                                       const float2* __restrict__ hi, const float2* __restrict__ lo,
-                                       const int64_t* __restrict__ det_off, int ndet,
-                                       const double* __restrict__ white, int ncomp,
-                                       float2* __restrict__ wcs, float* __restrict__ w1) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const double w = white[find_det(det_off, ndet, perm[i])];
-        if (ncomp == 1) {
-            w1[i] = (float)w;
-        } else {
-            const double sw = sqrt(w);
-            const double2 cs = trig64(hi[i], lo[i]);
-            wcs[i] = make_float2((float)(sw * cs.x), (float)(sw * cs.y));
-        }
-    }
-}
-
 }  // namespace
 
 void build_precond(bm_precond* pc) {
@@ -276,16 +276,23 @@ void build_precond(bm_precond* pc) {
         Items all;
         plan_items(ctx, p->off.get(), nullptr, npix, all);
         DevBuf<double> partial((all.n > 0 ? all.n : 1) * ns);
+        const bool white = n->kind == 0 && p->nvalid > 0;
+        if (white) {
+            if (nc == 1) pc->w1.alloc(p->nvalid);
+            else pc->wcs.alloc(p->nvalid);
+        }
         if (all.n > 0) {
             const int grid = grid_for(ctx, (all.n + kBlkWarps - 1) / kBlkWarps, 8);
-#define BM_BLOCKS(NC)                                                                                   \
-    blocks_kernel<NC><<<grid, kBlkWarps * 32, 0, s>>>(all.pix.get(), all.beg.get(), all.len.get(), all.n, \
-                                                      p->perm.get(), p->cs_hi_s.get(), p->cs_lo_s.get(),  \
-                                                      n->det_off.get(), n->ndet, n->white.get(),          \
-                                                      partial.get())
-            if (nc == 3) BM_BLOCKS(3);
-            else if (nc == 2) BM_BLOCKS(2);
-            else BM_BLOCKS(1);
+            const DetTables g{n->det_off32.get(), n->wdf.get(), n->wsqrt.get()};
+#define BM_BLOCKS(NC, W)                                                                                    \
+    blocks_kernel<NC, W><<<grid, kBlkWarps * 32, 0, s>>>(all.pix.get(), all.beg.get(), all.len.get(), all.n, \
+                                                         p->perm.get(), p->cs_hi_s.get(), p->cs_lo_s.get(), g, \
+                                                         n->ndet, partial.get(), pc->wcs.get(), pc->w1.get())
+            if (white) {
+                if (nc == 3) BM_BLOCKS(3, true); else if (nc == 2) BM_BLOCKS(2, true); else BM_BLOCKS(1, true);
+            } else {
+                if (nc == 3) BM_BLOCKS(3, false); else if (nc == 2) BM_BLOCKS(2, false); else BM_BLOCKS(1, false);
+            }
 #undef BM_BLOCKS
             BM_LAUNCH_CHECK();
         }
@@ -311,16 +318,6 @@ void build_precond(bm_precond* pc) {
     pc->item_len = std::move(kept.len);
     pc->pitem = std::move(kept.pitem);
 
-    // White-noise weighted stream.
-    if (n->kind == 0 && p->nvalid > 0) {
-        if (nc == 1) pc->w1.alloc(p->nvalid);
-        else pc->wcs.alloc(p->nvalid);
-        const int grid = grid_for(ctx, (p->nvalid + threads - 1) / threads, 16);
-        weighted_stream_kernel<<<grid, threads, 0, s>>>(p->perm.get(), p->nvalid, p->cs_hi_s.get(),
-                                                        p->cs_lo_s.get(), n->det_off.get(), n->ndet,
-                                                        n->white.get(), nc, pc->wcs.get(), pc->w1.get());
-        BM_LAUNCH_CHECK();
-    }
     BM_CUDA(cudaStreamSynchronize(s));
 }
 

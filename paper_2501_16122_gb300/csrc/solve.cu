@@ -448,7 +448,7 @@ bm_status pcg_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void*
     bm_status first = BM_OK;
     for (int32_t r = 0; r < nrhs; ++r) {
         const void* tr = static_cast<const char*>(tod) + (size_t)r * p->nsamples * (dt == BM_F32 ? 4 : 8);
-        rhs(p, n, pc, tr, dt, 1, b);
+        rhs(p, n, pc, tr, dt, 1, b, prec == BM_PREC_MIXED);
         bm_solve_info* ir = info ? info + r : nullptr;
         bm_status st;
         if (nc == 3) st = solve_one<3>(p, n, pc, b, map_out + r * nvec, tol, maxiter, prec, ir);

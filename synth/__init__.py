@@ -63,9 +63,10 @@ def _load():
         lib.synth_ang2pix_ring.argtypes = [i64, i64, P, P, P]
         lib.synth_scan.argtypes = [ctypes.POINTER(_ScanParams), i64, ctypes.c_int32, i64, i64,
                                    P, P, P, f64, u64, P, P, P, P]
-        lib.synth_tod.argtypes = [i64, i64, P, P, P, f64, f64, P, u64, P, P, P]
+        lib.synth_tod.argtypes = [i64, i64, P, P, P, f64, f64, P, u64, P, P, P, P, P]
+        lib.synth_trig32.argtypes = [i64, P, P, P]
         for f in ("synth_philox4x32_10", "synth_normal", "synth_uniform", "synth_ang2pix_ring",
-                  "synth_scan", "synth_tod"):
+                  "synth_scan", "synth_tod", "synth_trig32"):
             getattr(lib, f).restype = None
         _lib = lib
     return _lib
@@ -224,11 +225,22 @@ def stokes_weights(solver: int):
     return {SOLVER_IQU: (1.0, 1.0), SOLVER_QU: (0.0, 1.0), SOLVER_I: (1.0, 0.0)}[solver]
 
 
+def trig32(psi):
+    """(cos 2psi, sin 2psi) rounded to FP32: precomputed pointing entries."""
+    psi = np.ascontiguousarray(psi, np.float64)
+    c = np.empty(psi.size, np.float32)
+    s = np.empty(psi.size, np.float32)
+    _load().synth_trig32(psi.size, _ptr(psi), _ptr(c), _ptr(s))
+    return c, s
+
+
 def tod(e: Experiment, pix, psi, sky, solver: int = SOLVER_IQU, white: bool = True,
-        noise_seed: int | None = None, extra=None, dtype=np.float64, noise_scale: float = 1.0):
+        noise_seed: int | None = None, extra=None, dtype=np.float64, noise_scale: float = 1.0,
+        trig=None):
     """Time-ordered data [ndet][ns] of the data model d = s + n (Eq. 1-2).
     ``white``: add sigma_det * N(0,1); ``extra``: an additional noise stream
-    (e.g. 1/f) added sample by sample."""
+    (e.g. 1/f) added sample by sample; ``trig``: FP32 (cos 2psi, sin 2psi) to
+    use as the pointing entries instead of the angle."""
     aI, aP = stokes_weights(solver)
     pix = np.ascontiguousarray(pix, np.int32)
     psi = np.ascontiguousarray(psi, np.float64)
@@ -239,8 +251,12 @@ def tod(e: Experiment, pix, psi, sky, solver: int = SOLVER_IQU, white: bool = Tr
     n = e.nsamples
     out64 = np.empty(n, np.float64) if dtype == np.float64 else None
     out32 = np.empty(n, np.float32) if dtype == np.float32 else None
+    c32 = s32 = None
+    if trig is not None:
+        c32 = np.ascontiguousarray(trig[0], np.float32)
+        s32 = np.ascontiguousarray(trig[1], np.float32)
     _load().synth_tod(e.ndet, e.ns, _ptr(pix), _ptr(psi), _ptr(sky), aI, aP, _ptr(sig),
-                      seed, _ptr(ext), _ptr(out64), _ptr(out32))
+                      seed, _ptr(ext), _ptr(out64), _ptr(out32), _ptr(c32), _ptr(s32))
     return out64 if out64 is not None else out32
 
 

@@ -240,6 +240,18 @@ void synth_scan(const synth_scan_params* sp, int64_t nside, int32_t ndet, int64_
     }
 }
 
+/* cos 2psi and sin 2psi rounded to FP32: the precomputed pointing entries an
+ * experiment may deliver instead of the angle. */
+void synth_trig32(int64_t n, const double* psi, float* c32, float* s32)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        const double a = 2.0 * psi[i];
+        c32[i] = (float)cos(a);
+        s32[i] = (float)sin(a);
+    }
+}
+
 /*
  * Time-ordered data of the data model (paper Eq. 1-2): for sample i in
  * pixel p = pix[i] with angle psi[i],
@@ -253,7 +265,7 @@ void synth_scan(const synth_scan_params* sp, int64_t nside, int32_t ndet, int64_
  */
 void synth_tod(int64_t ndet, int64_t ns, const int32_t* pix, const double* psi, const double* map,
                double a_I, double a_P, const double* sigma_det, uint64_t noise_seed,
-               const double* extra, double* out64, float* out32)
+               const double* extra, double* out64, float* out32, const float* c32, const float* s32)
 {
     const int64_t n = ndet * ns;
 #pragma omp parallel for schedule(static)
@@ -262,9 +274,17 @@ void synth_tod(int64_t ndet, int64_t ns, const int32_t* pix, const double* psi, 
         double s = 0.0;
         const int32_t p = pix[i];
         if (p >= 0) {
-            const double a = 2.0 * psi[i];
             const double* m = map + 3 * (int64_t)p;
-            s = a_I * m[0] + a_P * (m[1] * cos(a) + m[2] * sin(a));
+            double c2, s2;
+            if (c32) {  /* precomputed FP32 trig: the pointing entries as delivered */
+                c2 = (double)c32[i];
+                s2 = (double)s32[i];
+            } else {
+                const double a = 2.0 * psi[i];
+                c2 = cos(a);
+                s2 = sin(a);
+            }
+            s = a_I * m[0] + a_P * (m[1] * c2 + m[2] * s2);
         }
         double v = s;
         if (sigma_det) v += sigma_det[d] * normal_at(noise_seed, 1u, (uint64_t)i);

@@ -18,7 +18,7 @@ def stokes_cols(solver):
 class Case:
     def __init__(self, L, ctx, nside, ndet, ns, seed, solver=3, noise="white", chunk=None, nlags=None,
                  fknee=0.1, flag=0.0, tod_dtype=np.float64, psi_dtype=np.float64, noiseless=False,
-                 max_cond=1e3, build_oracle=True):
+                 max_cond=1e3, build_oracle=True, trig=False):
         import torch
         self.L, self.ctx = L, ctx
         self.solver, self.noise_kind = solver, noise
@@ -40,8 +40,10 @@ class Case:
             if not noiseless:
                 extra = synth.one_over_f_noise(e, chunk, fknee, 1.0)
         self.chunk = chunk
+        self.trig = synth.trig32(self.psi.astype(np.float64)) if trig else None
         self.tod = synth.tod(e, self.pix, self.psi.astype(np.float64), sky, solver=solver,
-                             white=(not noiseless) and noise == "white", extra=extra, dtype=tod_dtype)
+                             white=(not noiseless) and noise == "white", extra=extra, dtype=tod_dtype,
+                             trig=self.trig)
         inv_var = 1.0 / e.sigma ** 2
         if noise == "white":
             self.onoise = gls.WhiteNoise(inv_var, e.det_offsets)
@@ -50,13 +52,17 @@ class Case:
         self.S = None
         if build_oracle:
             self.S = gls.System(self.pix, self.psi.astype(np.float64), solver, e.npix, self.onoise,
-                                min_hits=MIN_HITS[solver], max_cond=max_cond)
+                                min_hits=MIN_HITS[solver], max_cond=max_cond, trig=self.trig)
         # device
         dev = torch.device("cuda:0")
         self.d_pix = torch.from_numpy(self.pix).to(dev)
         self.d_psi = torch.from_numpy(np.ascontiguousarray(self.psi)).to(dev)
         self.d_tod = torch.from_numpy(np.ascontiguousarray(self.tod)).to(dev)
-        self.p = L.bm_pointing_create(ctx, e.npix, self.d_pix, self.d_psi, solver)
+        if trig:
+            self.p = L.bm_pointing_create_trig(ctx, e.npix, self.d_pix, torch.from_numpy(self.trig[0]).to(dev),
+                                               torch.from_numpy(self.trig[1]).to(dev), solver)
+        else:
+            self.p = L.bm_pointing_create(ctx, e.npix, self.d_pix, self.d_psi, solver)
         if noise == "white":
             self.n = L.bm_inv_noise_create_diag(ctx, e.det_offsets, inv_var)
         else:

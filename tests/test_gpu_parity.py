@@ -313,3 +313,46 @@ def test_bad_arguments(L, ctx):
         L.bm_inv_noise_create_toeplitz(ctx, e.det_offsets, 10, np.zeros((2, 2000)), np.ones(2))
     with pytest.raises(L.BrahmapError):
         L.bm_inv_noise_create_diag(ctx, e.det_offsets, np.array([1.0, -1.0]))
+
+
+# ------------------------------------------------ precomputed FP32 trig input
+
+@pytest.mark.parametrize("noise", ["white", "toeplitz"])
+def test_trig_input_blocks_matvec_rhs(L, ctx, noise):
+    kw = dict(chunk=4096, nlags=128) if noise == "toeplitz" else {}
+    c = Case(L, ctx, 16, 4, 40_000, 6100, noise=noise, tod_dtype=np.float32, trig=True, flag=0.01, **kw)
+    try:
+        S = c.S
+        B = torch.zeros(c.npix * 9, dtype=torch.float64, device="cuda")
+        L.bm_precond_get_blocks(c.pc, B, None)
+        assert rel(B.cpu().numpy().reshape(c.npix, 3, 3), S.B) < 1e-13
+        assert np.array_equal(c.mask(), S.mask)
+        x = np.random.default_rng(7).normal(size=(c.npix, 3)) * np.array([100.0, 10.0, 10.0])
+        ref = S.matvec(x * (~S.mask)[:, None])
+        for prec, tol in ((L.BM_PREC_FP64, 1e-12), (L.BM_PREC_MIXED, 2e-6)):
+            q = c.vec()
+            L.bm_matvec(c.p, c.n, c.pc, c.vec(x), q, prec)
+            qh = q.cpu().numpy().reshape(c.npix, 3)
+            for k in range(3):
+                assert rel(qh[:, k], ref[:, k]) < tol, (prec, k)
+        b = c.vec()
+        L.bm_rhs(c.p, c.n, c.pc, c.d_tod, 1, b)
+        assert rel(b.cpu().numpy(), S.rhs(c.tod.astype(np.float64)).ravel()) < 1e-12
+    finally:
+        c.close()
+
+
+def test_trig_input_config1_like_solve(L, ctx):
+    # The config-1 input format (int32 pix, FP32 cos/sin, FP32 TOD, white
+    # noise) on a reduced scan: mixed solve to 1e-8 matches the oracle to 1e-6,
+    # and the FP64 path to 1e-10.
+    c = Case(L, ctx, 64, 16, 65_536, 1001, tod_dtype=np.float32, trig=True)
+    try:
+        ref, _ = gls.gls_map(c.S, c.tod.astype(np.float64), tol=1e-13)
+        for prec, tol_solve, tol_err in ((L.BM_PREC_MIXED, 1e-8, 1e-6), (L.BM_PREC_FP64, 1e-10, 1e-10)):
+            out = c.vec()
+            st, infos = L.bm_pcg_solve(c.p, c.n, c.pc, c.d_tod, 1, out, tol_solve, 100, prec)
+            assert st == L.BM_OK, infos
+            check_map(L, c, out, ref, tol_err)
+    finally:
+        c.close()

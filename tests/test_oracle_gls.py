@@ -267,3 +267,21 @@ def test_planted_dropped_noise_term_is_caught():
     ref = gls.dense_gls(S, d)
     keep = ~S.mask
     assert not np.allclose(x[keep], ref[keep], rtol=1e-6)
+
+
+def test_precomputed_trig_rows_and_recovery():
+    # Rows built from given (cos 2psi, sin 2psi) equal the angle form when the
+    # given values are the FP64 trig; with FP32-rounded values the system is
+    # the operator of those numbers, and noiseless data made with the same
+    # numbers is recovered exactly.
+    e = synth.make_experiment(8, 4, 20_000, 41)
+    pt = synth.pointing(e)
+    a = 2 * pt["psi"]
+    assert np.array_equal(gls.pointing_weights_trig(np.cos(a), np.sin(a), 3), gls.pointing_weights(pt["psi"], 3))
+    c32, s32 = synth.trig32(pt["psi"])
+    assert c32.dtype == np.float32 and np.array_equal(c32, np.cos(a).astype(np.float32))
+    S = gls.System(pt["pix"], None, 3, e.npix, gls.WhiteNoise(1 / e.sigma ** 2, e.det_offsets), trig=(c32, s32))
+    sky = synth.sky_map(e.npix, 41)
+    d = synth.tod(e, pt["pix"], pt["psi"], sky, white=False, trig=(c32, s32))
+    x, info = gls.gls_map(S, d, tol=1e-14)
+    assert gls.rel_err(x, sky, S.mask)["all"] < 1e-12
