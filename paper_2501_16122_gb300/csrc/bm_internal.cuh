@@ -118,6 +118,11 @@ struct bm_context {
     std::vector<cudaEvent_t> event_pool;
     double* h_pinned = nullptr;  // small pinned host buffer for scalar reads
     std::map<std::string, bm::DevBuf<char>> ws;  // named grow-only scratch buffers
+    // Library-owned stream for CUDA-graph capture and replay (the caller's
+    // stream may be the legacy default stream, which cannot be captured),
+    // ordered against `stream` with side_ev.
+    cudaStream_t side = nullptr;
+    cudaEvent_t side_ev = nullptr;
 };
 
 struct bm_pointing {
@@ -179,6 +184,14 @@ struct bm_precond {
 namespace bm {
 
 constexpr int kItemMax = 4096;  // max samples per work item
+constexpr int kBatchMax = 256;  // right-hand sides per batched solve
+
+// Batched mixed-precision solve of nrhs white-noise right-hand sides sharing
+// one pointing (groups of at most kBatchMax).
+bm_status batched_white_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dtype dt,
+                              int32_t nrhs, double* map_out, double tol, int32_t maxiter, bm_solve_info* info);
+// Adds kernels launched by a CUDA-graph replay to the launch counter.
+void count_launches(int64_t n);
 
 // Named grow-only scratch buffer owned by the context (released with it).
 void* workspace(bm_context* ctx, const char* name, size_t bytes);
@@ -241,6 +254,18 @@ inline int grid_for(const bm_context* ctx, int64_t work_units, int per_sm = 8) {
     int64_t g = (int64_t)ctx->num_sms * per_sm;
     if (work_units < g) g = work_units > 0 ? work_units : 1;
     return (int)g;
+}
+
+// Resident blocks per SM of a kernel at a block size (queried once per kernel).
+int blocks_per_sm(const void* kernel, int threads, size_t smem);
+
+// Persistent grid: exactly the number of blocks that are resident at once
+// (SM count x occupancy), capped by the work, so a grid-stride loop runs in a
+// single wave.
+template <typename K>
+int resident_grid(const bm_context* ctx, K kernel, int threads, int64_t work_units, size_t smem = 0) {
+    const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(kernel), threads, smem);
+    return grid_for(ctx, work_units, per_sm > 0 ? per_sm : 1);
 }
 
 }  // namespace bm

@@ -6,7 +6,9 @@
 #include <cstring>
 #include <atomic>
 #include <cmath>
+#include <mutex>
 #include <new>
+#include <tuple>
 
 #include "bm_internal.cuh"
 
@@ -26,6 +28,7 @@ thread_local cudaStream_t tl_stream = nullptr;
 
 static std::atomic<int64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 static cudaEvent_t take_event(bm_context* ctx) {
     if (!ctx->event_pool.empty()) {
@@ -74,6 +77,22 @@ void resolve_timers(bm_context* ctx) {
     }
     ctx->pending.clear();
     (void)cudaGetLastError();
+}
+
+int blocks_per_sm(const void* kernel, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, int, size_t>, int> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_tuple(kernel, threads, smem);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess) {
+        (void)cudaGetLastError();
+        n = 1;
+    }
+    cache[key] = n;
+    return n;
 }
 
 void* workspace(bm_context* ctx, const char* name, size_t bytes) {
@@ -146,6 +165,8 @@ bm_status bm_context_create(int device, void* cuda_stream, bm_context** out) {
         ctx->stream = static_cast<cudaStream_t>(cuda_stream);
         cudaError_t e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
         if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_pinned, 4096);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->side_ev, cudaEventDisableTiming);
         // Keep memory freed back to the device pool for reuse by the next
         // handle instead of returning it to the driver.
         cudaMemPool_t pool = nullptr;
@@ -172,6 +193,11 @@ void bm_context_destroy(bm_context* ctx) {
     resolve_timers(ctx);
     for (cudaEvent_t ev : ctx->event_pool) cudaEventDestroy(ev);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    if (ctx->side) {
+        cudaStreamSynchronize(ctx->side);
+        cudaStreamDestroy(ctx->side);
+    }
+    if (ctx->side_ev) cudaEventDestroy(ctx->side_ev);
     const int dev = ctx->device;
     delete ctx;  // releases the workspaces (stream-ordered)
     cudaStreamSynchronize(tl_stream);

@@ -515,14 +515,14 @@ static void gather_reduce(bm_pointing* p, const ItemsView& it, const G* g, const
     const int nc = p->ncomp;
     double* partial = workspace_as<double>(ctx, "partial", (size_t)std::max<int64_t>(it.n, 1) * nc);
     if (it.n > 0) {
-        const int grid = grid_for(ctx, (it.n + kWarps - 1) / kWarps, 8);
+        const int64_t wunits = (it.n + kWarps - 1) / kWarps;
         const bool weighted = wn != nullptr;
         const DetTables dt = weighted ? DetTables{wn->det_off32.get(), wn->wdf.get(), wn->wsqrt.get()}
                                       : DetTables{nullptr, nullptr, nullptr};
         const double* white = weighted ? wn->white.get() : nullptr;
         const int ndet = weighted ? wn->ndet : 0;
 #define BM_GR(NC, D)                                                                                           \
-    gather_reduce_kernel<NC, G, D><<<grid, kWarps * 32, 0, ctx->stream>>>(it.pix, it.beg, it.len, it.n,          \
+    gather_reduce_kernel<NC, G, D><<<resident_grid(ctx, gather_reduce_kernel<NC, G, D>, kWarps * 32, wunits), kWarps * 32, 0, ctx->stream>>>(it.pix, it.beg, it.len, it.n,          \
                                                                          p->perm.get(), p->cs_hi_s.get(), lo, g, \
                                                                          weighted, dt, white, ndet, partial)
         if (df) {
@@ -549,7 +549,7 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
         double* qr = q + r * nvec;
         if (n->kind == 0) {
             double* partial = workspace_as<double>(ctx, "partial", (size_t)std::max<int64_t>(pc->nitems, 1) * nc);
-            const int grid = grid_for(ctx, (pc->nitems + kWarps - 1) / kWarps, 8);
+            const int64_t wunits = (pc->nitems + kWarps - 1) / kWarps;
             if (prec == BM_PREC_MIXED) {
                 float* x32 = workspace_as<float>(ctx, "x32", nvec);
                 masked_copy_kernel<float><<<vgrid, threads, 0, s>>>(xr, pc->mask.get(), p->npix, nc, x32);
@@ -557,7 +557,7 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
                 if (pc->nitems > 0) {
                     ScopedTimer timer(ctx, "matvec_white_f32");
 #define BM_WF32(NC)                                                                                     \
-    white_matvec_f32_kernel<NC><<<grid, kWarps * 32, 0, s>>>(pc->item_pix.get(), pc->item_beg.get(),     \
+    white_matvec_f32_kernel<NC><<<resident_grid(ctx, white_matvec_f32_kernel<NC>, kWarps * 32, wunits), kWarps * 32, 0, s>>>(pc->item_pix.get(), pc->item_beg.get(),     \
                                                              pc->item_len.get(), pc->nitems, pc->wcs.get(), \
                                                              pc->w1.get(), x32, partial)
                     if (nc == 3) BM_WF32(3); else if (nc == 2) BM_WF32(2); else BM_WF32(1);
@@ -567,7 +567,7 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
             } else if (pc->nitems > 0) {
                 ScopedTimer timer(ctx, "matvec_white_f64");
 #define BM_WF64(NC)                                                                                      \
-    white_matvec_f64_kernel<NC><<<grid, kWarps * 32, 0, s>>>(                                              \
+    white_matvec_f64_kernel<NC><<<resident_grid(ctx, white_matvec_f64_kernel<NC>, kWarps * 32, wunits), kWarps * 32, 0, s>>>(                                              \
         pc->item_pix.get(), pc->item_beg.get(), pc->item_len.get(), pc->nitems, p->perm.get(),            \
         p->cs_hi_s.get(), p->cs_lo_s.get(), n->det_off.get(), n->ndet, n->white.get(), xr, partial)
                 if (nc == 3) BM_WF64(3); else if (nc == 2) BM_WF64(2); else BM_WF64(1);

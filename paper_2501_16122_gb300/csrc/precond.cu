@@ -282,10 +282,10 @@ void build_precond(bm_precond* pc) {
             else pc->wcs.alloc(p->nvalid);
         }
         if (all.n > 0) {
-            const int grid = grid_for(ctx, (all.n + kBlkWarps - 1) / kBlkWarps, 8);
+            const int64_t wunits = (all.n + kBlkWarps - 1) / kBlkWarps;
             const DetTables g{n->det_off32.get(), n->wdf.get(), n->wsqrt.get()};
 #define BM_BLOCKS(NC, W)                                                                                    \
-    blocks_kernel<NC, W><<<grid, kBlkWarps * 32, 0, s>>>(all.pix.get(), all.beg.get(), all.len.get(), all.n, \
+    blocks_kernel<NC, W><<<resident_grid(ctx, blocks_kernel<NC, W>, kBlkWarps * 32, wunits), kBlkWarps * 32, 0, s>>>(all.pix.get(), all.beg.get(), all.len.get(), all.n, \
                                                          p->perm.get(), p->cs_hi_s.get(), p->cs_lo_s.get(), g, \
                                                          n->ndet, partial.get(), pc->wcs.get(), pc->w1.get())
             if (white) {
