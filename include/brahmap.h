@@ -231,6 +231,86 @@ bm_status bm_pcg_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const vo
                        bm_dtype tod_dtype, int32_t nrhs, double* map_out, double tol,
                        int32_t maxiter, bm_precision prec, bm_solve_info* info);
 
+/* --------------------------------------------------------------- serving */
+
+/* A request loop that runs map-making solves as they arrive (continuous
+ * batching): up to max_slots requests run at once, each in its own slot with
+ * its own CUDA stream, so their device work overlaps; a request is admitted
+ * when a slot is free and its estimated device memory fits in what is left of
+ * hbm_budget_bytes (first come, first served; the head of the queue waits for
+ * memory rather than being overtaken).  While a request runs, its pointing,
+ * preconditioner and CG state stay resident on the device; they are released
+ * when it completes.  Each request's solve is the same computation as
+ * bm_pointing_create(_trig) + bm_inv_noise_create_* +
+ * bm_blockdiag_precond_create + bm_pcg_solve, so its map does not depend on
+ * what else is running.  All bm_serve_* calls are thread-safe.  This loop has
+ * no counterpart in the paper. */
+typedef struct bm_server bm_server;
+typedef enum { BM_NOISE_WHITE = 0, BM_NOISE_TOEPLITZ = 1 } bm_noise_kind;
+
+/* One map-making request.  Device arrays are the caller's and must stay
+ * valid until bm_serve_poll reports the request finished; host arrays are
+ * copied by bm_serve_submit. */
+typedef struct {
+    int64_t npix, nsamples;
+    bm_solver_type solver;
+    const int32_t* pix;          /* device [nsamples], -1 = flagged */
+    const float* cos2psi;        /* device [nsamples] FP32 trig, or NULL to use psi */
+    const float* sin2psi;        /* device [nsamples] */
+    const void* psi;             /* device [nsamples] (when cos2psi is NULL) */
+    bm_dtype psi_dtype;
+    int32_t ndet;
+    const int64_t* det_offsets;  /* host [ndet + 1] */
+    bm_noise_kind noise;
+    const double* inv_var;       /* host [ndet]: white level 1/sigma_d^2 */
+    int64_t chunk_len;           /* Toeplitz: chunk length */
+    int32_t nlags;               /* Toeplitz: band length */
+    const double* coeffs;        /* host [ndet][nlags] (Toeplitz) */
+    const void* tod;             /* device [nsamples] */
+    bm_dtype tod_dtype;
+    int32_t min_hits;
+    double max_cond;
+    double tol;
+    int32_t maxiter;
+    bm_precision precision;
+    double* map_out;             /* device [npix][ncomp], written by the solve */
+} bm_request;
+
+typedef struct {
+    int32_t status;              /* bm_status of the solve */
+    int32_t iterations, outer_iterations, slot;
+    double rel_residual;
+    double queue_ms;             /* submit -> start */
+    double run_ms;               /* start -> finish */
+    double latency_ms;           /* submit -> finish */
+    int64_t device_bytes;        /* memory reserved for the request */
+} bm_result;
+
+typedef struct {
+    int64_t submitted, completed, rejected, cancelled, running, queued;
+    double p50_ms, p99_ms, mean_ms;   /* latency over completed requests */
+    double samples_per_s;             /* samples of completed requests / wall time since creation */
+    int64_t budget_bytes, reserved_bytes, peak_reserved_bytes;
+} bm_serve_stats;
+
+/* Server on ctx's device with max_slots in [1, 64] slots. */
+bm_status bm_serve_create(bm_context* ctx, size_t hbm_budget_bytes, int32_t max_slots, bm_server** out);
+/* Queue a request; *ticket identifies it.  BM_ERR_BUSY if its estimated
+ * device memory exceeds the whole budget (it could never run). */
+bm_status bm_serve_submit(bm_server* s, const bm_request* req, uint64_t* ticket);
+/* Wait up to timeout_ms (0 = just check) for the request to finish:
+ * BM_OK and *out filled when finished (the ticket is then released),
+ * BM_ERR_TIMEOUT if still queued or running, BM_ERR_NOT_FOUND for an
+ * unknown or released ticket. */
+bm_status bm_serve_poll(bm_server* s, uint64_t ticket, int32_t timeout_ms, bm_result* out);
+/* Cancel a queued request (BM_OK); BM_ERR_BUSY if it is already running,
+ * BM_ERR_NOT_FOUND if unknown.  A cancelled request reports BM_ERR_NOT_FOUND
+ * in its result status. */
+bm_status bm_serve_cancel(bm_server* s, uint64_t ticket);
+bm_status bm_serve_get_stats(bm_server* s, bm_serve_stats* out);
+/* Stop accepting, cancel queued requests, wait for running ones, release. */
+void bm_serve_destroy(bm_server* s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -40,6 +40,38 @@ class bm_solve_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+BM_NOISE_WHITE, BM_NOISE_TOEPLITZ = 0, 1
+
+
+class bm_request(ctypes.Structure):
+    _fields_ = [("npix", ctypes.c_int64), ("nsamples", ctypes.c_int64), ("solver", ctypes.c_int),
+                ("pix", ctypes.c_void_p), ("cos2psi", ctypes.c_void_p), ("sin2psi", ctypes.c_void_p),
+                ("psi", ctypes.c_void_p), ("psi_dtype", ctypes.c_int), ("ndet", ctypes.c_int32),
+                ("det_offsets", ctypes.c_void_p), ("noise", ctypes.c_int), ("inv_var", ctypes.c_void_p),
+                ("chunk_len", ctypes.c_int64), ("nlags", ctypes.c_int32), ("coeffs", ctypes.c_void_p),
+                ("tod", ctypes.c_void_p), ("tod_dtype", ctypes.c_int), ("min_hits", ctypes.c_int32),
+                ("max_cond", ctypes.c_double), ("tol", ctypes.c_double), ("maxiter", ctypes.c_int32),
+                ("precision", ctypes.c_int), ("map_out", ctypes.c_void_p)]
+
+
+class bm_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("outer_iterations", ctypes.c_int32),
+                ("slot", ctypes.c_int32), ("rel_residual", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class bm_serve_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "rejected", "cancelled", "running", "queued")] + \
+               [(n, ctypes.c_double) for n in ("p50_ms", "p99_ms", "mean_ms", "samples_per_s")] + \
+               [(n, ctypes.c_int64) for n in ("budget_bytes", "reserved_bytes", "peak_reserved_bytes")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with paper_2501_16122_gb300.build.build()")
 lib = ctypes.CDLL(LIB_PATH)
@@ -78,6 +110,12 @@ _SIGS = {
     "bm_matvec_white_static": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "bm_pcg_solve": ([_P, _P, _P, _P, ctypes.c_int, _i32, _P, _f64, _i32, ctypes.c_int,
                       ctypes.POINTER(bm_solve_info)], ctypes.c_int),
+    "bm_serve_create": ([_P, ctypes.c_size_t, _i32, _PP], ctypes.c_int),
+    "bm_serve_submit": ([_P, ctypes.POINTER(bm_request), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "bm_serve_poll": ([_P, ctypes.c_uint64, _i32, ctypes.POINTER(bm_result)], ctypes.c_int),
+    "bm_serve_cancel": ([_P, ctypes.c_uint64], ctypes.c_int),
+    "bm_serve_get_stats": ([_P, ctypes.POINTER(bm_serve_stats)], ctypes.c_int),
+    "bm_serve_destroy": ([_P], None),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -306,3 +344,71 @@ def bm_pcg_solve(p, n, pc, tod, nrhs: int, map_out, tol: float, maxiter: int, pr
     if raise_on_error and st not in (BM_OK, BM_ERR_NOT_CONVERGED):
         _check(st, "bm_pcg_solve")
     return st, [i.as_dict() for i in infos]
+
+
+# ------------------------------------------------------------------ serving
+def bm_serve_create(ctx, hbm_budget_bytes: int, max_slots: int):
+    out = ctypes.c_void_p()
+    _check(lib.bm_serve_create(ctx, int(hbm_budget_bytes), int(max_slots), ctypes.byref(out)), "bm_serve_create")
+    return out
+
+
+def make_request(npix, pix, tod, map_out, det_offsets, inv_var, solver=BM_SOLVER_IQU, cos2psi=None, sin2psi=None,
+                 psi=None, coeffs=None, chunk_len=0, min_hits=3, max_cond=1e3, tol=1e-6, maxiter=500,
+                 precision=BM_PREC_MIXED):
+    """Build a bm_request from torch device tensors and host arrays.  Returns
+    (request, keepalive) -- keep the second object alive until submitted."""
+    import torch
+    off, offp = _host(det_offsets, np.int64)
+    iv, ivp = _host(inv_var, np.float64)
+    keep = [off, iv]
+    r = bm_request()
+    r.npix, r.nsamples, r.solver = int(npix), pix.numel(), int(solver)
+    r.pix = _dev(pix, torch.int32, "pix")
+    if cos2psi is not None:
+        r.cos2psi = _dev(cos2psi, torch.float32, "cos2psi")
+        r.sin2psi = _dev(sin2psi, torch.float32, "sin2psi")
+    else:
+        r.psi = _dev(psi, None, "psi")
+        r.psi_dtype = _dtype_code(psi)
+    r.ndet = off.size - 1
+    r.det_offsets, r.inv_var = offp, ivp
+    if coeffs is not None:
+        c, cp = _host(coeffs, np.float64)
+        keep.append(c)
+        r.noise, r.coeffs, r.nlags, r.chunk_len = BM_NOISE_TOEPLITZ, cp, c.shape[-1], int(chunk_len)
+    else:
+        r.noise = BM_NOISE_WHITE
+    r.tod, r.tod_dtype = _dev(tod, None, "tod"), _dtype_code(tod)
+    r.min_hits, r.max_cond, r.tol, r.maxiter, r.precision = int(min_hits), float(max_cond), float(tol), int(maxiter), int(precision)
+    r.map_out = _dev(map_out, torch.float64, "map_out")
+    return r, keep
+
+
+def bm_serve_submit(server, req) -> int:
+    t = ctypes.c_uint64()
+    _check(lib.bm_serve_submit(server, ctypes.byref(req), ctypes.byref(t)), "bm_serve_submit")
+    return t.value
+
+
+def bm_serve_poll(server, ticket: int, timeout_ms: int):
+    """Returns (status, result dict or None); status is BM_OK, BM_ERR_TIMEOUT or BM_ERR_NOT_FOUND."""
+    res = bm_result()
+    st = lib.bm_serve_poll(server, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(res))
+    if st not in (BM_OK, BM_ERR_TIMEOUT, BM_ERR_NOT_FOUND):
+        _check(st, "bm_serve_poll")
+    return st, (res.as_dict() if st == BM_OK else None)
+
+
+def bm_serve_cancel(server, ticket: int) -> int:
+    return lib.bm_serve_cancel(server, ctypes.c_uint64(ticket))
+
+
+def bm_serve_get_stats(server):
+    s = bm_serve_stats()
+    _check(lib.bm_serve_get_stats(server, ctypes.byref(s)), "bm_serve_get_stats")
+    return s.as_dict()
+
+
+def bm_serve_destroy(server):
+    lib.bm_serve_destroy(server)
