@@ -55,6 +55,14 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--matvec-reps", type=int, default=20)
     ap.add_argument("--profile", action="store_true", help="short run for ncu: no e2e, cpu, clocks")
+    ap.add_argument("--workload", default="config1",
+                    choices=["config0", "config1", "config2", "config3", "config4"],
+                    help="config1 (default): nside 256 white-noise solve; config0: small FP64 solve; "
+                         "config2: 512-lag Toeplitz noise; config3: 64 right-hand sides batched; "
+                         "config4: Poisson request stream through the server")
+    ap.add_argument("--horizon", type=float, default=20.0, help="config4: seconds of arrivals")
+    ap.add_argument("--rate", type=float, default=20.0, help="config4: mean arrivals per second")
+    ap.add_argument("--nrhs", type=int, default=64, help="config3: right-hand sides")
     return ap.parse_args()
 
 
@@ -372,6 +380,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.workload != "config1":
+        import bench_workloads
+        bench_workloads.run(args, rank, world, local_rank)
         return
     run_gb300(args, rank, world, local_rank)
 
