@@ -156,6 +156,12 @@ struct bm_inv_noise {
     int nlags = 0;
     bm::DevBuf<double> coeffs64;   // [ndet][nlags]
     bm::DevBuf<float> coeffs32;    // [ndet][nlags]
+    // FFT overlap-save form of the band (sizes 0 = use the direct filter).
+    int fft_n32 = 0, fft_n64 = 0;
+    bm::DevBuf<float> spec32;      // [ndet][fft_n32/2 + 1] real band spectrum
+    bm::DevBuf<double> spec64;     // [ndet][fft_n64/2 + 1]
+    bm::DevBuf<float2> tw32;       // [fft_n32] exp(-2 pi i e / N)
+    bm::DevBuf<double2> tw64;      // [fft_n64]
 };
 
 struct bm_precond {
@@ -243,6 +249,8 @@ void precond_apply(bm_precond* pc, const double* r, double* z, int64_t nrhs);
 void pointing_apply(bm_pointing* p, const double* x, double* y);
 void pointing_apply_transpose(bm_pointing* p, const double* y, double* x);
 void inv_noise_apply(bm_inv_noise* n, const double* y, double* z);
+// Band spectra and twiddle tables for the FFT form of a Toeplitz noise model.
+void prepare_toeplitz_fft(bm_inv_noise* n);
 void ang2pix_ring(bm_context* ctx, int64_t nside, int64_t n, const double* z, const double* phi,
                   int32_t* pix);
 bm_status pcg_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod,

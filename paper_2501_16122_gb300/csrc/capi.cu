@@ -434,6 +434,7 @@ bm_status bm_inv_noise_create_toeplitz(bm_context* ctx, int32_t ndet, const int6
             n->coeffs32.alloc(m);
             upload(ctx, n->coeffs64.get(), coeffs, sizeof(double) * m);
             upload(ctx, n->coeffs32.get(), c32.data(), sizeof(float) * m);
+            prepare_toeplitz_fft(n);
         } catch (...) {
             delete n;
             throw;

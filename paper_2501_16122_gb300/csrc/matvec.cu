@@ -18,6 +18,7 @@
 // and write z; the scatter P^T z is the pixel-sorted gather-reduce
 // q_p = sum_{t in p} z_t v_t.
 #include "bm_internal.cuh"
+#include "fft_filter.cuh"
 
 namespace bm {
 
@@ -486,6 +487,85 @@ static void run_toeplitz(bm_inv_noise* n, const Src& src, const T* coeffs, T* z)
     BM_LAUNCH_CHECK();  // tile_start is released stream-ordered after the kernel
 }
 
+// FFT size for a band of L lags: the smallest power of two with at least half
+// of each transform producing outputs (H >= N/2), grown toward a whole chunk,
+// at most `cap`; 0 if the band is too long for `cap` (direct filter).
+static int fft_size(int L, int64_t chunk_len, int cap) {
+    const int64_t need = 4 * (int64_t)(L - 1);
+    int64_t N = 64;
+    while (N < need) N <<= 1;
+    const int64_t want = chunk_len + 2 * (int64_t)(L - 1);
+    while (N < cap && N < want) N <<= 1;
+    return N <= cap ? (int)N : 0;
+}
+
+constexpr int kFftMinLags = 32;  // shorter bands: the direct filter is cheaper
+
+void prepare_toeplitz_fft(bm_inv_noise* n) {
+    if (n->nlags < kFftMinLags) return;
+    bm_context* ctx = n->ctx;
+    int64_t maxlen = 0;
+    for (int d = 0; d < n->ndet; ++d) maxlen = std::max(maxlen, n->h_det_off[d + 1] - n->h_det_off[d]);
+    const int64_t eff_chunk = std::min(n->chunk_len, maxlen);
+    n->fft_n32 = fft_size(n->nlags, eff_chunk, 8192);
+    n->fft_n64 = fft_size(n->nlags, eff_chunk, 4096);
+    const int threads = 256;
+    if (n->fft_n32) {
+        const int N = n->fft_n32;
+        n->spec32.alloc((size_t)n->ndet * (N / 2 + 1));
+        n->tw32.alloc(N);
+        band_spectrum_kernel<<<grid_for(ctx, ((int64_t)n->ndet * (N / 2 + 1) + threads - 1) / threads, 16), threads, 0,
+                               ctx->stream>>>(n->coeffs64.get(), n->ndet, n->nlags, N, nullptr, n->spec32.get());
+        BM_LAUNCH_CHECK();
+        twiddle_kernel<<<(N + threads - 1) / threads, threads, 0, ctx->stream>>>(N, nullptr, n->tw32.get());
+        BM_LAUNCH_CHECK();
+    }
+    if (n->fft_n64) {
+        const int N = n->fft_n64;
+        n->spec64.alloc((size_t)n->ndet * (N / 2 + 1));
+        n->tw64.alloc(N);
+        band_spectrum_kernel<<<grid_for(ctx, ((int64_t)n->ndet * (N / 2 + 1) + threads - 1) / threads, 16), threads, 0,
+                               ctx->stream>>>(n->coeffs64.get(), n->ndet, n->nlags, N, n->spec64.get(), nullptr);
+        BM_LAUNCH_CHECK();
+        twiddle_kernel<<<(N + threads - 1) / threads, threads, 0, ctx->stream>>>(N, n->tw64.get(), nullptr);
+        BM_LAUNCH_CHECK();
+    }
+    BM_CUDA(cudaStreamSynchronize(ctx->stream));
+}
+
+template <typename T, class Src>
+static void run_toeplitz_fft(bm_inv_noise* n, const Src& src, int N, const T* spec, const cpx<T>* tw, T* z) {
+    bm_context* ctx = n->ctx;
+    const int H = N - 2 * (n->nlags - 1);
+    ToeplitzPlan tp;
+    plan_toeplitz(n, H, tp);
+    if (tp.geo.ntiles == 0) return;
+    const FftGeom geo{tp.geo.det_off, tp.geo.tile_start, tp.geo.ndet, tp.geo.chunk_len, tp.geo.tiles_per_chunk,
+                      tp.geo.ntiles};
+    const size_t smem = (size_t)2 * N * sizeof(T);
+    auto kern = toeplitz_fft_kernel<T, Src>;
+    BM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = resident_grid(ctx, kern, kFftThreads, tp.geo.ntiles, smem);
+    kern<<<grid, kFftThreads, smem, ctx->stream>>>(src, spec, tw, N, n->nlags, geo, z);
+    BM_LAUNCH_CHECK();
+}
+
+// z = band * y per chunk: FFT overlap-save when prepared, else the direct filter.
+template <class Src>
+static void apply_toeplitz_f32(bm_inv_noise* n, const Src& src, float* z) {
+    if (n->fft_n32)
+        run_toeplitz_fft<float>(n, src, n->fft_n32, n->spec32.get(), reinterpret_cast<const cpx<float>*>(n->tw32.get()), z);
+    else
+        run_toeplitz<float, 8>(n, src, n->coeffs32.get(), z);
+}
+template <class Src>
+static void apply_toeplitz_f64(bm_inv_noise* n, const Src& src, double* z) {
+    if (n->fft_n64)
+        run_toeplitz_fft<double>(n, src, n->fft_n64, n->spec64.get(), reinterpret_cast<const cpx<double>*>(n->tw64.get()), z);
+    else
+        run_toeplitz<double, 4>(n, src, n->coeffs64.get(), z);
+}
+
 static void finalize(bm_context* ctx, const int64_t* pitem, const double* partial, int64_t npix, int nc,
                      double* q) {
     const int threads = 256;
@@ -584,7 +664,7 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
                 {
                     ScopedTimer timer(ctx, "toeplitz_f32");
                     SrcMatvecF32 src{p->pix.get(), p->cs_hi_t.get(), x32, nc};
-                    run_toeplitz<float, 8>(n, src, n->coeffs32.get(), z32);
+                    apply_toeplitz_f32(n, src, z32);
                 }
                 // scatter with the same FP32 trig the gather used (symmetric operator)
                 gather_reduce<float>(p, kept_items(pc), z32, nullptr, nullptr, true, qr);
@@ -596,7 +676,7 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
                 {
                     ScopedTimer timer(ctx, "toeplitz_f64");
                     SrcMatvecF64 src{p->pix.get(), p->cs_hi_t.get(), p->cs_lo_t.get(), xm, nc};
-                    run_toeplitz<double, 4>(n, src, n->coeffs64.get(), z64);
+                    apply_toeplitz_f64(n, src, z64);
                 }
                 gather_reduce<double>(p, kept_items(pc), z64, nullptr, p->cs_lo_s.get(), false, qr);
             }
@@ -625,11 +705,11 @@ void rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dt
             if (dt == BM_F32) {
                 SrcMaskedTod<float> src{p->pix.get(), pc->mask.get(),
                                         static_cast<const float*>(tod) + r * p->nsamples};
-                run_toeplitz<double, 4>(n, src, n->coeffs64.get(), z64);
+                apply_toeplitz_f64(n, src, z64);
             } else {
                 SrcMaskedTod<double> src{p->pix.get(), pc->mask.get(),
                                          static_cast<const double*>(tod) + r * p->nsamples};
-                run_toeplitz<double, 4>(n, src, n->coeffs64.get(), z64);
+                apply_toeplitz_f64(n, src, z64);
             }
             gather_reduce<double>(p, kept_items(pc), z64, nullptr, p->cs_lo_s.get(), df, br);
         }
@@ -671,7 +751,7 @@ void inv_noise_apply(bm_inv_noise* n, const double* y, double* z) {
         tmp.nlags = 1;
         run_toeplitz<double, 4>(&tmp, SrcPlain{y}, c.get(), z);
     } else {
-        run_toeplitz<double, 4>(n, SrcPlain{y}, n->coeffs64.get(), z);
+        apply_toeplitz_f64(n, SrcPlain{y}, z);
     }
 }
 

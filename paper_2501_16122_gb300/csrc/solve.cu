@@ -404,11 +404,13 @@ bm_status solve_one(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const doubl
         if (h.done == 2) status = BM_ERR_BREAKDOWN;
     } else {
         // Mixed: outer FP64 residual, inner FP32-product PCG on the correction.
-        double rr = exact_residual<NC>(cg, p, n, b, xs, rs);
+        // x starts at 0, so the first residual is b itself (zero on masked pixels).
+        BM_CUDA(cudaMemcpyAsync(rs, b, sizeof(double) * cg.nvec, cudaMemcpyDeviceToDevice, s));
+        double rr = bb;
         int inner_total = 0, outer = 0;
         const int max_outer = 30;
         while (std::sqrt(rr) > tol * bnorm && inner_total < maxiter && outer < max_outer) {
-            const double inner_tol = std::max(1e-5, 0.5 * tol * bnorm / std::sqrt(rr));
+            const double inner_tol = std::max(1e-6, 0.5 * tol * bnorm / std::sqrt(rr));
             CgState h = run_pcg<NC>(cg, p, n, rs, std::min(inner_tol, 0.5), maxiter - inner_total, BM_PREC_MIXED);
             inner_total += h.iters;
             ++outer;
@@ -421,10 +423,12 @@ bm_status solve_one(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const doubl
         }
         inf.iterations = inner_total;
         inf.outer_iterations = outer;
+        inf.rel_residual = std::sqrt(rr) / bnorm;  // the last outer residual is the final one
     }
-    // Final residual with the FP64 operator.
-    const double rr = bb == 0.0 ? 0.0 : exact_residual<NC>(cg, p, n, b, xs, rs);
-    inf.rel_residual = bb == 0.0 ? 0.0 : std::sqrt(rr) / bnorm;
+    if (bb != 0.0 && prec == BM_PREC_FP64) {
+        // Final residual recomputed with the FP64 operator (the recurrence drifts).
+        inf.rel_residual = std::sqrt(exact_residual<NC>(cg, p, n, b, xs, rs)) / bnorm;
+    }
     if (status == BM_OK && !(inf.rel_residual <= tol)) status = BM_ERR_NOT_CONVERGED;
     inf.status = status;
     const int threads = 256;
