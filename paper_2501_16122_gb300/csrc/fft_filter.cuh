@@ -98,7 +98,7 @@ __device__ cpx<T>* fft_run(cpx<T>* buf0, cpx<T>* buf1, int M, const cpx<T>* __re
     return a;
 }
 
-constexpr int kFftThreads = 256;
+constexpr int kFftThreads = 512;
 
 struct FftGeom {
     const int64_t* det_off;
@@ -141,6 +141,9 @@ toeplitz_fft_kernel(Src src, const T* __restrict__ spec, const cpx<T>* __restric
         const int64_t t1 = min(t0 + (int64_t)H, ce);
         const int64_t b0 = t0 - (L - 1);
         __syncthreads();  // previous block done with the buffers
+        // Gather the block's inputs: four independent sample pairs per
+        // thread and pass, so their dependent loads (pixel, then map) overlap.
+#pragma unroll 4
         for (int n = threadIdx.x; n < M; n += kFftThreads) {
             const int64_t ta = b0 + 2 * n, tb = ta + 1;
             const T ya = (ta >= cs && ta < ce) ? T(src(ta)) : T(0);
