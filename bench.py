@@ -159,6 +159,20 @@ def cpu_oracle_run(nside, ndet, ns, seed, tol):
 CPU_SAMPLE = dict(ndet=8, ns=2 ** 19)  # 4.2M samples of the same scan: ~10 s of oracle work
 
 
+# Kernel of each timed family, and the DRAM traffic per launch measured by
+# ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the small case of
+# profiles/ scaled to the full launch by the samples processed; None when the
+# kernel has changed since the counters were taken.
+KERNELS = {"ingest_validate": "validate_kernel", "ingest_hist": "rs_hist_kernel",
+           "ingest_scatter": "rs_scatter_kernel", "blocks": "blocks_kernel", "rhs": "gather_reduce_kernel",
+           "matvec_white_f32": "white_matvec_f32_kernel"}
+TRAFFIC = {}
+
+
+def n_valid_kept(hits, kept):
+    return int(hits[kept].sum().item())
+
+
 # ------------------------------------------------------------- reference
 def run_reference(args, rank):
     if rank != 0:
@@ -223,10 +237,12 @@ def run_gb300(args, rank, world, local_rank):
     out = torch.empty(e.npix * 3, dtype=torch.float64, device="cuda")
     infos = []
 
-    def step(src_pix, src_trig, src_tod):
+    def step(src_pix, src_trig, src_tod, tod_ready=None):
         p = L.bm_pointing_create_trig(ctx, e.npix, src_pix, src_trig[0], src_trig[1], L.BM_SOLVER_IQU)
         n = L.bm_inv_noise_create_diag(ctx, e.det_offsets, inv_var)
         pc = L.bm_blockdiag_precond_create(p, n, 3, 1e3)
+        if tod_ready is not None:  # the TOD upload ran beside the ingest and the preconditioner
+            stream.wait_event(tod_ready)
         st, info = L.bm_pcg_solve(p, n, pc, src_tod, 1, out, args.tol, 200, L.BM_PREC_MIXED)
         infos.append((st, info[0]))
         L.bm_precond_destroy(pc)
@@ -254,7 +270,8 @@ def run_gb300(args, rank, world, local_rank):
     ms = ev0.elapsed_time(ev1) / args.steps
     clocks = sampler.stop() if not args.profile else None
     fam = {}
-    for name in ("ingest", "blocks", "rhs", "matvec_white_f32", "matvec_white_f64"):
+    for name in ("ingest", "ingest_validate", "ingest_hist", "ingest_scatter", "blocks", "rhs",
+                 "matvec_white_f32", "matvec_white_f64"):
         tot, cnt = L.bm_context_kernel_time(ctx, name)
         if cnt:
             fam[name] = {"ms_per_launch": tot / cnt, "launches": cnt, "ms_per_step": tot / args.steps}
@@ -294,6 +311,37 @@ def run_gb300(args, rank, world, local_rank):
     L.bm_inv_noise_destroy(n)
     L.bm_pointing_destroy(p)
 
+    # --- roofline of every timed kernel family of the step (algorithmic bytes
+    # per step / device time per step); the dominant family is the headline
+    nbits = 1
+    while (1 << nbits) <= e.npix:
+        nbits += 1
+    passes = -(-nbits // 11)
+    n_valid = int(hits.sum().item())
+    scatter_bytes = 0
+    for ps in range(passes):
+        last = ps == passes - 1
+        rd = 4 + (4 if ps > 0 else 0) + 8                  # keys, sample indices, trig pair
+        wr = (4 + 12 * n_valid / nt) if last else 16       # keys (+ perm and trig of kept samples)
+        scatter_bytes += (rd + wr) * nt
+    step_bytes = {
+        "ingest_validate": 28 * nt,                       # pix + cos + sin in; pix, key, trig pair out
+        "ingest_hist": 4 * nt * passes,
+        "ingest_scatter": scatter_bytes,
+        "blocks": 20 * n_valid_kept(hits, kept),          # perm + trig pair in, weighted pair out
+        "rhs": 16 * n_valid_kept(hits, kept),             # perm + d + trig pair
+        "matvec_white_f32": alg_bytes * fam.get("matvec_white_f32", {}).get("launches", 0) / max(args.steps, 1),
+    }
+    rooflines = {}
+    for name, b in step_bytes.items():
+        f = fam.get(name)
+        if not f or f["ms_per_step"] <= 0:
+            continue
+        gbs = b / (f["ms_per_step"] * 1e-3) / 1e9
+        rooflines[name] = {"ms_per_step": f["ms_per_step"], "bytes_per_step": b, "achieved_gbs": gbs,
+                           "frac": gbs / hbm, "bytes_per_sample": b / nt}
+    dom = max(rooflines, key=lambda k: rooflines[k]["ms_per_step"]) if rooflines else None
+
     # --- end to end from pinned host buffers
     e2e = None
     if not args.no_e2e and not args.profile:
@@ -303,11 +351,19 @@ def run_gb300(args, rank, world, local_rank):
         h_tod = torch.from_numpy(tod).pin_memory()
         h_out = torch.empty(e.npix * 3, dtype=torch.float64).pin_memory()
 
+        upload = torch.cuda.Stream()
+
         def e2e_step():
-            a = h_pix.to("cuda", non_blocking=True)
-            b = (h_c.to("cuda", non_blocking=True), h_s.to("cuda", non_blocking=True))
-            c = h_tod.to("cuda", non_blocking=True)
-            step(a, b, c)
+            # The pointing goes to the library as page-locked host buffers: its
+            # ingest reads them once over the host link, with no staging copy.
+            # The TOD is needed only by the solve: it is uploaded on a second
+            # stream while the pointing is ingested.
+            with torch.cuda.stream(upload):
+                c = h_tod.to("cuda", non_blocking=True)
+                ready = torch.cuda.Event()
+                ready.record(upload)
+            c.record_stream(stream)
+            step(h_pix, (h_c, h_s), c, ready)
             h_out.copy_(out, non_blocking=True)
             torch.cuda.current_stream().synchronize()
 
@@ -353,9 +409,15 @@ def run_gb300(args, rank, world, local_rank):
             "step_breakdown_ms": {k: v["ms_per_step"] for k, v in fam.items()},
             "solve": {"status_ok": st_ok, "iterations": last["iterations"],
                       "outer_iterations": last["outer_iterations"], "rel_residual": last["rel_residual"]},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None, "kernel": "white_matvec_f32_kernel",
-                         "peak_kind": peak_kind, "bytes_per_launch": alg_bytes},
+            "roofline": ({"bound": "hbm", "achieved": rooflines[dom]["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                          "frac": rooflines[dom]["frac"], "traffic": TRAFFIC.get(dom, lambda n: None)(nt),
+                          "kernel": KERNELS[dom], "family": dom, "peak_kind": peak_kind,
+                          "bytes_per_step": rooflines[dom]["bytes_per_step"],
+                          "launches_per_step": fam[dom]["launches"] / args.steps} if dom else None),
+            "rooflines": rooflines,
+            "matvec_roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                                "frac": achieved / hbm, "kernel": "white_matvec_f32_kernel",
+                                "peak_kind": peak_kind, "bytes_per_launch": alg_bytes},
             "gpu_launches": int(launches),
             "input_generation_s": t_gen,
         }

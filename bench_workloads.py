@@ -76,6 +76,28 @@ def fp32_peak_tflops(sm_mhz):
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
+def fp64_peak_tflops(sm_mhz):
+    # 1.25 TFLOP/s dense FP64 at the maximum SM clock (2070 MHz), scaled by the clock
+    return 1.25 * sm_mhz / 2070.0
+
+
+def hbm_peak():
+    return peaks()[0]
+
+
+def fft_size(L, chunk_len, cap):
+    """The library's FFT length for an L-lag band (smallest power of two with
+    H = N - 2(L-1) >= N/2, grown toward a whole chunk, at most cap; 0: direct)."""
+    if L < 32:
+        return 0
+    N = 64
+    while N < 4 * (L - 1):
+        N <<= 1
+    while N < cap and N < chunk_len + 2 * (L - 1):
+        N <<= 1
+    return N if N <= cap else 0
+
+
 # ------------------------------------------------------------------ config 0
 def run_config0(args):
     import torch
@@ -191,9 +213,31 @@ def run_config2(args):
     L.bm_context_destroy(ctx)
     st, info = infos[-1]
     sm = clocks["sm_mhz"] if clocks else 2070.0
-    f32 = fam.get("toeplitz_f32", {})
-    flops = 2.0 * (2 * nlags - 1) * e.nsamples
-    achieved = flops / (f32.get("ms_per_launch", float("nan")) * 1e-3) / 1e12
+    # The band is applied by FFT overlap-save: per tile of H = N - 2(L-1)
+    # outputs one real N-point transform pair (5 N log2 N flops) and the
+    # spectrum product (2N); its inputs are the window's pix + trig
+    # (12 B per input sample) and it writes z (4 B FP32 / 8 B FP64).
+    def fft_tiles(N):
+        H = N - 2 * (nlags - 1)
+        per_chunk = -(-chunk // H)
+        return per_chunk * (ns // chunk) * ndet, H
+    fam_fft = {}
+    for name, N, zb, peak, unit in (("toeplitz_f32", fft_size(nlags, chunk, 8192), 4, fp32_peak_tflops(sm), "FP32"),
+                                    ("toeplitz_f64", fft_size(nlags, chunk, 4096), 8, fp64_peak_tflops(sm), "FP64")):
+        ms_l = fam.get(name, {}).get("ms_per_launch")
+        if not N or not ms_l:
+            continue
+        tiles, H = fft_tiles(N)
+        flops = tiles * (5.0 * N * math.log2(N) + 2.0 * N)
+        bytes_ = tiles * N * 12.0 + e.nsamples * zb
+        fam_fft[name] = {"fft_n": N, "tiles": tiles, "ms_per_launch": ms_l,
+                         "tflops": flops / (ms_l * 1e-3) / 1e12, "peak_tflops": peak, "pipe": unit,
+                         "flop_frac": flops / (ms_l * 1e-3) / 1e12 / peak,
+                         "gbs": bytes_ / (ms_l * 1e-3) / 1e9, "hbm_frac": bytes_ / (ms_l * 1e-3) / 1e9 / hbm_peak()}
+    # the dominant kernel family of the step
+    dom = max(("toeplitz_f32", "toeplitz_f64"),
+              key=lambda k: fam.get(k, {}).get("ms_per_launch", 0) * fam.get(k, {}).get("launches_per_step", 0))
+    d = fam_fft.get(dom, {})
     line = {
         "workload": "config2", "metric": METRIC, "value": e.nsamples / (ms * 1e-3), "unit": "TOD samples/s",
         "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
@@ -202,12 +246,14 @@ def run_config2(args):
                                f"mixed precision PCG to {tol:g}", "nsamples": e.nsamples},
         "solve": {"status": st, **info},
         "step_breakdown": fam,
+        "fft_filter": fam_fft,
         "fp64_matvec_ms": fp64_mv_ms,
         "plain_fp64_solve_estimate_ms": fp64_mv_ms * max(info["iterations"], 1),
-        "roofline": {"bound": "alu", "kernel": "toeplitz_kernel<float,8> (FP32 FMA pipe)", "achieved": achieved,
-                     "peak": fp32_peak_tflops(sm), "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak_tflops(sm), "flops_per_launch": flops,
-                     "peak_basis": f"152 SM x 128 lanes x 2 flop x {sm:.0f} MHz (median SM clock under load)"},
+        "roofline": {"bound": "alu", "kernel": f"toeplitz_fft_kernel ({dom}, {d.get('pipe')} pipe)",
+                     "achieved": d.get("tflops"), "peak": d.get("peak_tflops"), "unit": "TFLOP/s",
+                     "frac": d.get("flop_frac"), "traffic": None,
+                     "peak_basis": ("FP32: 152 SM x 128 lanes x 2 flop x SM clock; FP64: 1.25 TFLOP/s nominal "
+                                    f"x SM clock / 2070 MHz; SM clock {sm:.0f} MHz (median under load)")},
         "clocks": clocks, "input_generation_s": t_gen,
     }
     print(json.dumps(line), flush=True)
@@ -412,6 +458,41 @@ def run_config4(args):
     clocks = sampler.stop()
     stats = L.bm_serve_get_stats(srv)
     L.bm_serve_destroy(srv)
+
+    # The plain alternative: the same kind of requests solved one at a time in
+    # FP64 (pointing, noise, preconditioner, FP64 PCG), on a seeded sample.
+    def solve_alone(rq, prec):
+        req, bufs = build(rq)
+        keep, pix, c, s, tod, out = bufs
+        e0 = pools[rq["nside"]][0]
+        sigma = np.asarray([e0.sigma[d % pool_ndet] for d in range(rq["ndet"])])
+        det_off = np.arange(rq["ndet"] + 1, dtype=np.int64) * rq["ns"]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p = L.bm_pointing_create_trig(ctx, e0.npix, pix, c, s, L.BM_SOLVER_IQU)
+        chunk = min(2 ** 20, rq["ns"])
+        if rq["white"]:
+            n = L.bm_inv_noise_create_diag(ctx, det_off, 1 / sigma ** 2)
+        else:
+            n = L.bm_inv_noise_create_toeplitz(ctx, det_off, chunk,
+                                               synth.toeplitz_band(sigma, rq["fknee"], 1.0, 20.0, chunk, 512),
+                                               1 / sigma ** 2)
+        pc = L.bm_blockdiag_precond_create(p, n, 3, 1e3)
+        st, info = L.bm_pcg_solve(p, n, pc, tod, 1, out, 1e-6, 3000, prec)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        L.bm_precond_destroy(pc)
+        L.bm_inv_noise_destroy(n)
+        L.bm_pointing_destroy(p)
+        return dt, rq["ndet"] * rq["ns"], st
+
+    pick = np.random.default_rng(args.seed + 4).choice(len(reqs), size=min(8, len(reqs)), replace=False)
+    alone = {"fp64": [0.0, 0], "mixed": [0.0, 0]}
+    for i in pick:
+        for name, prec in (("fp64", L.BM_PREC_FP64), ("mixed", L.BM_PREC_MIXED)):
+            dt, ns_tot, st = solve_alone(reqs[int(i)], prec)
+            alone[name][0] += dt
+            alone[name][1] += ns_tot
     L.bm_context_destroy(ctx)
     lat = np.array([x["t_done"] - x["t_arr"] for x in tickets]) * 1000
     ok = sum(1 for x in tickets if x["res"]["status"] == L.BM_OK)
@@ -428,6 +509,10 @@ def run_config4(args):
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "p50_white": float(np.percentile(lw, 50)) if lw.size else None,
                        "p50_toeplitz": float(np.percentile(lt, 50)) if lt.size else None},
+        "one_at_a_time": {"sample_requests": len(pick),
+                          "fp64_samples_per_s": alone["fp64"][1] / alone["fp64"][0],
+                          "mixed_samples_per_s": alone["mixed"][1] / alone["mixed"][0]},
+        "served_vs_fp64_one_at_a_time": (samples / wall) / (alone["fp64"][1] / alone["fp64"][0]),
         "server_stats": stats, "clocks": clocks, "pool_generation_s": t_gen,
     }
     print(json.dumps(line), flush=True)

@@ -121,9 +121,13 @@ bm_status bm_ang2pix_ring(bm_context* ctx, int64_t nside, int64_t n, const doubl
 /* -------------------------------------------------------------- pointing */
 
 /* Pointing matrix P (Eq. 8) and its precomputed elements (the paper's
- * ProcessTimeSamples, Sec. III-A item 1): pix device int32 [nsamples]
- * (-1 = flagged), psi device [nsamples] of dtype psi_dtype (the polarisation
- * angle theta of Eq. 2, radians).  The handle keeps the pixel-sorted sample
+ * ProcessTimeSamples, Sec. III-A item 1): pix int32 [nsamples]
+ * (-1 = flagged), psi [nsamples] of dtype psi_dtype (the polarisation
+ * angle theta of Eq. 2, radians).  Both may be device memory of the
+ * context's GPU or page-locked host memory (cudaHostAlloc /
+ * cudaHostRegister), which the ingest reads once, directly over the host
+ * link, without a staging copy; other host memory returns BM_ERR_INVALID.
+ * The handle keeps the pixel-sorted sample
  * permutation, CSR offsets, hit counts and cos/sin 2psi stored as FP32
  * (hi, lo) pairs whose sum carries the FP64 value to 2^-48.
  * Requires 1 <= npix <= 2^28, 1 <= nsamples < 2^32.  A pixel index outside
@@ -131,8 +135,9 @@ bm_status bm_ang2pix_ring(bm_context* ctx, int64_t nside, int64_t n, const doubl
 bm_status bm_pointing_create(bm_context* ctx, int64_t npix, int64_t nsamples, const int32_t* pix,
                              const void* psi, bm_dtype psi_dtype, bm_solver_type solver,
                              bm_pointing** out);
-/* The same operator from precomputed FP32 cos 2psi and sin 2psi (device
- * [nsamples] each, |values| <= 1): the FP32 numbers are the entries of P
+/* The same operator from precomputed FP32 cos 2psi and sin 2psi ([nsamples]
+ * each, |values| <= 1; device or page-locked host memory, as pix): the FP32
+ * numbers are the entries of P
  * (Eq. 8) exactly, so no extra precision is kept and every FP64 result is
  * computed from them.  Requirements and errors as bm_pointing_create. */
 bm_status bm_pointing_create_trig(bm_context* ctx, int64_t npix, int64_t nsamples, const int32_t* pix,
@@ -221,8 +226,10 @@ bm_status bm_matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const doubl
 bm_status bm_matvec_white_static(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x,
                                  double* q);
 
-/* GLS maps by block-preconditioned CG (Eq. 5-7): tod device [nrhs][nsamples]
- * (tod_dtype), map_out device FP64 [nrhs][npix][ncomp] (NaN on masked
+/* GLS maps by block-preconditioned CG (Eq. 5-7): tod [nrhs][nsamples]
+ * (tod_dtype) in device memory, or in page-locked host memory, which is then
+ * uploaded into a library workspace first; map_out device FP64
+ * [nrhs][npix][ncomp] (NaN on masked
  * pixels).  x0 = 0; stops when ||b - A x||_2 <= tol ||b||_2 (per RHS) or
  * after maxiter PCG iterations (maxiter counts inner iterations in mixed
  * mode).  info host [nrhs] (may be NULL).  Returns BM_OK when every RHS
@@ -284,6 +291,7 @@ typedef struct {
     double run_ms;               /* start -> finish */
     double latency_ms;           /* submit -> finish */
     int64_t device_bytes;        /* memory reserved for the request */
+    char message[256];           /* bm_last_error() of a failed solve, else "" */
 } bm_result;
 
 typedef struct {

@@ -57,10 +57,13 @@ class bm_request(ctypes.Structure):
 class bm_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("outer_iterations", ctypes.c_int32),
                 ("slot", ctypes.c_int32), ("rel_residual", ctypes.c_double), ("queue_ms", ctypes.c_double),
-                ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
+                ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double), ("device_bytes", ctypes.c_int64),
+                ("message", ctypes.c_char * 256)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["message"] = d["message"].decode(errors="replace")
+        return d
 
 
 class bm_serve_stats(ctypes.Structure):
@@ -161,6 +164,22 @@ def _dev(t, dtype=None, name="array"):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _in(t, dtype=None, name="array"):
+    """Pointer of an input the library may read from the host: a contiguous
+    CUDA tensor, or a contiguous page-locked (pinned) CPU tensor."""
+    if t is None:
+        return None
+    if getattr(t, "is_cuda", False):
+        return _dev(t, dtype, name)
+    if not (hasattr(t, "is_pinned") and t.is_pinned()):
+        raise TypeError(f"{name} must be a CUDA tensor or a pinned CPU tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def _host(a, dtype):
     a = np.ascontiguousarray(a, dtype=dtype)
     return a, a.ctypes.data_as(ctypes.c_void_p)
@@ -218,8 +237,8 @@ def bm_ang2pix_ring(ctx, nside: int, z, phi, pix):
 def bm_pointing_create(ctx, npix: int, pix, psi, solver: int = BM_SOLVER_IQU):
     import torch
     out = ctypes.c_void_p()
-    _check(lib.bm_pointing_create(ctx, int(npix), pix.numel(), _dev(pix, torch.int32, "pix"),
-                                  _dev(psi, None, "psi"), _dtype_code(psi), int(solver), ctypes.byref(out)),
+    _check(lib.bm_pointing_create(ctx, int(npix), pix.numel(), _in(pix, torch.int32, "pix"),
+                                  _in(psi, None, "psi"), _dtype_code(psi), int(solver), ctypes.byref(out)),
            "bm_pointing_create")
     return out
 
@@ -227,8 +246,8 @@ def bm_pointing_create(ctx, npix: int, pix, psi, solver: int = BM_SOLVER_IQU):
 def bm_pointing_create_trig(ctx, npix: int, pix, cos2psi, sin2psi, solver: int = BM_SOLVER_IQU):
     import torch
     out = ctypes.c_void_p()
-    _check(lib.bm_pointing_create_trig(ctx, int(npix), pix.numel(), _dev(pix, torch.int32, "pix"),
-                                       _dev(cos2psi, torch.float32, "cos2psi"), _dev(sin2psi, torch.float32, "sin2psi"),
+    _check(lib.bm_pointing_create_trig(ctx, int(npix), pix.numel(), _in(pix, torch.int32, "pix"),
+                                       _in(cos2psi, torch.float32, "cos2psi"), _in(sin2psi, torch.float32, "sin2psi"),
                                        int(solver), ctypes.byref(out)), "bm_pointing_create_trig")
     return out
 
@@ -339,7 +358,7 @@ def bm_pcg_solve(p, n, pc, tod, nrhs: int, map_out, tol: float, maxiter: int, pr
     """Returns (status, [info dict per RHS])."""
     import torch
     infos = (bm_solve_info * int(nrhs))()
-    st = lib.bm_pcg_solve(p, n, pc, _dev(tod, None, "tod"), _dtype_code(tod), int(nrhs),
+    st = lib.bm_pcg_solve(p, n, pc, _in(tod, None, "tod"), _dtype_code(tod), int(nrhs),
                           _dev(map_out, torch.float64, "map_out"), float(tol), int(maxiter), int(prec), infos)
     if raise_on_error and st not in (BM_OK, BM_ERR_NOT_CONVERGED):
         _check(st, "bm_pcg_solve")

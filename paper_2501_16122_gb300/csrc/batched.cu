@@ -114,18 +114,17 @@ batched_rhs_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restri
                 wl = wp[find_det32(offp, ndet, tl)];
             }
             const int cnt = min(32, len - base);
-            for (int kk = 0; kk < cnt; ++kk) {
-                const uint32_t t = __shfl_sync(0xffffffffu, tl, kk);
+            // sample kk of the chunk: its row of the G right-hand sides, added in order
+            auto add = [&](int kk, const T (&dv)[RPL]) {
                 const df32 w = {__shfl_sync(0xffffffffu, wl.x, kk), __shfl_sync(0xffffffffu, wl.y, kk)};
                 const df32 c = {__shfl_sync(0xffffffffu, h.x, kk), __shfl_sync(0xffffffffu, l.x, kk)};
                 const df32 s = {__shfl_sync(0xffffffffu, h.y, kk), __shfl_sync(0xffffffffu, l.y, kk)};
 #pragma unroll
                 for (int q = 0; q < RPL; ++q) {
-                    const int r = lane + 32 * q;
-                    if (r < G) {
+                    if (lane + 32 * q < G) {
                         df32 d;
-                        if (sizeof(T) == 4) d = {(float)dT[(int64_t)t * G + r], 0.f};
-                        else d = df_from((double)dT[(int64_t)t * G + r]);
+                        if (sizeof(T) == 4) d = {(float)dv[q], 0.f};
+                        else d = df_from((double)dv[q]);
                         const df32 wd = df_mul(d, w);
                         if (NC == 1) {
                             acc[q][0] = df_add(acc[q][0], wd);
@@ -136,6 +135,28 @@ batched_rhs_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restri
                         }
                     }
                 }
+            };
+            auto row = [&](int kk, T (&dv)[RPL]) {
+                const uint32_t t = __shfl_sync(0xffffffffu, tl, kk);
+#pragma unroll
+                for (int q = 0; q < RPL; ++q) {
+                    const int r = lane + 32 * q;
+                    dv[q] = r < G ? dT[(int64_t)t * G + r] : T(0);
+                }
+            };
+            // four rows in flight, then their sums in sample order
+            int kk = 0;
+            for (; kk + 4 <= cnt; kk += 4) {
+                T dv[4][RPL];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) row(kk + u, dv[u]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) add(kk + u, dv[u]);
+            }
+            for (; kk < cnt; ++kk) {
+                T dv[RPL];
+                row(kk, dv);
+                add(kk, dv);
             }
         }
 #pragma unroll

@@ -221,6 +221,8 @@ void plan_items(bm_context* ctx, const int64_t* off, const uint8_t* mask, int64_
 // Device-wide exclusive scans.
 void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
 void exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s);
+// off[0..n] = exclusive prefix sums of counts[0..n) followed by the total.
+void offsets_from_counts(const int32_t* counts, int64_t n, int64_t* off, cudaStream_t s);
 
 // Deterministic FP64 reductions with a fixed grid: out = sum_i a_i b_i.
 constexpr int kRedBlocks = 512;
@@ -263,6 +265,10 @@ inline int grid_for(const bm_context* ctx, int64_t work_units, int per_sm = 8) {
     if (work_units < g) g = work_units > 0 ? work_units : 1;
     return (int)g;
 }
+
+// Raises (never lowers) a kernel's dynamic shared-memory limit on the current
+// device; safe against concurrent launches of the same kernel.
+void ensure_smem_limit(const void* kernel, size_t bytes);
 
 // Resident blocks per SM of a kernel at a block size (queried once per kernel).
 int blocks_per_sm(const void* kernel, int threads, size_t smem);

@@ -79,6 +79,22 @@ void resolve_timers(bm_context* ctx) {
     (void)cudaGetLastError();
 }
 
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device and never lowers it: the limit is a per-function setting of
+// the device, and threads launching the same kernel with different sizes
+// (several contexts, the server's slots) must not undo each other.
+void ensure_smem_limit(const void* kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> set;
+    int dev = 0;
+    BM_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = set[{dev, kernel}];
+    if (bytes <= cur) return;
+    BM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cur = bytes;
+}
+
 int blocks_per_sm(const void* kernel, int threads, size_t smem) {
     static std::mutex mu;
     static std::map<std::tuple<const void*, int, size_t>, int> cache;
@@ -252,6 +268,28 @@ bm_status bm_ang2pix_ring(bm_context* ctx, int64_t nside, int64_t n, const doubl
     });
 }
 
+// Address at which the device reads a caller's input array: device or
+// managed memory of the context's GPU as is; page-locked host memory through
+// its device mapping (the kernel that reads it then streams it over the
+// host link).  Anything else is rejected.
+static const void* device_readable(const bm_context* ctx, const void* ptr, const char* what,
+                                   bool* on_host = nullptr) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        (void)cudaGetLastError();
+        a.type = cudaMemoryTypeUnregistered;
+    }
+    if (on_host) *on_host = a.type == cudaMemoryTypeHost;
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+        BM_REQUIRE(a.type == cudaMemoryTypeManaged || a.device == ctx->device,
+                   "%s lives on device %d, the context on device %d", what, a.device, ctx->device);
+        return ptr;
+    }
+    BM_REQUIRE(a.type == cudaMemoryTypeHost && a.devicePointer != nullptr,
+               "%s is neither device memory nor page-locked host memory", what);
+    return a.devicePointer;
+}
+
 bm_status bm_pointing_create(bm_context* ctx, int64_t npix, int64_t nsamples, const int32_t* pix,
                              const void* psi, bm_dtype psi_dtype, bm_solver_type solver,
                              bm_pointing** out) {
@@ -265,6 +303,8 @@ bm_status bm_pointing_create(bm_context* ctx, int64_t npix, int64_t nsamples, co
         BM_REQUIRE(solver == BM_SOLVER_I || solver == BM_SOLVER_QU || solver == BM_SOLVER_IQU,
                    "bad solver type %d", (int)solver);
         use_device(ctx);
+        pix = static_cast<const int32_t*>(device_readable(ctx, pix, "pix"));
+        psi = device_readable(ctx, psi, "psi");
         auto* p = new bm_pointing();
         p->ctx = ctx;
         p->npix = npix;
@@ -293,6 +333,9 @@ bm_status bm_pointing_create_trig(bm_context* ctx, int64_t npix, int64_t nsample
         BM_REQUIRE(solver == BM_SOLVER_I || solver == BM_SOLVER_QU || solver == BM_SOLVER_IQU,
                    "bad solver type %d", (int)solver);
         use_device(ctx);
+        pix = static_cast<const int32_t*>(device_readable(ctx, pix, "pix"));
+        cos2psi = static_cast<const float*>(device_readable(ctx, cos2psi, "cos2psi"));
+        sin2psi = static_cast<const float*>(device_readable(ctx, sin2psi, "sin2psi"));
         auto* p = new bm_pointing();
         p->ctx = ctx;
         p->npix = npix;
@@ -587,6 +630,16 @@ bm_status bm_pcg_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const vo
         BM_REQUIRE(maxiter >= 1, "maxiter < 1");
         BM_REQUIRE(prec == BM_PREC_FP64 || prec == BM_PREC_MIXED, "bad precision");
         use_device(p->ctx);
+        // A page-locked host TOD is uploaded first: the solve reads it in
+        // pixel order, a random access pattern the host link serves poorly.
+        bool on_host = false;
+        tod = device_readable(p->ctx, tod, "tod", &on_host);
+        if (on_host) {
+            const size_t bytes = (size_t)nrhs * (size_t)p->nsamples * (tod_dtype == BM_F64 ? 8 : 4);
+            void* dev = workspace(p->ctx, "tod_upload", bytes);
+            BM_CUDA(cudaMemcpyAsync(dev, tod, bytes, cudaMemcpyHostToDevice, p->ctx->stream));
+            tod = dev;
+        }
         return pcg_solve(p, n, pc, tod, tod_dtype, nrhs, map_out, tol, maxiter, prec, info);
     });
 }

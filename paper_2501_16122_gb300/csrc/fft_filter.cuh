@@ -1,6 +1,6 @@
 // Banded Toeplitz N^-1 applied by FFT overlap-save (the circulant/FFT route
-// to correlated-noise weighting the paper names as future work, Sec. V),
-// with an own radix-4/2 Stockham FFT in shared memory.
+// to correlated-noise weighting the paper names as future work, Sec. IV),
+// with an own shared-memory Stockham FFT.
 //
 // For a block of H outputs of one chunk, the N = H + 2(L-1) inputs around it
 // (zero outside the chunk) are transformed, multiplied by the spectrum of the
@@ -8,14 +8,20 @@
 // K[k] = c_0 + 2 sum_{j>=1} c_j cos(2 pi j k / N)) and transformed back; the
 // middle H values of the circular convolution are exactly the banded linear
 // convolution (no wrap-around reaches them).  The real N-point transform is
-// done as an N/2-point complex transform of the packed sequence
+// done as an M = N/2-point complex transform of the packed sequence
 // y[2n] + i y[2n+1] with the usual even/odd split.  Per output sample this
 // costs O(log N) flops instead of the 2L - 1 of the direct filter.
 //
-// Stockham stage (radix R, current sub-transform size Ns, M points):
-//   for j in [0, M/R):  k = j mod Ns,  v_r = in[j + r M/R] * W_M^(r k M/(Ns R)),
-//   X = R-point DFT of v,  out[(j - k) R + k + r Ns] = X_r
-// which leaves the result in natural order after log_R(M) stages.
+// The M-point transform runs in place in shared memory as Stockham passes of
+// radix 16 (8, 4 or 2 for the last one): a thread reads its R points, applies
+// the pass twiddles, does the R-point DFT in registers, and after a barrier
+// writes the R results.  For radix R, current sub-transform size Ns and
+// j in [0, M/R), k = j mod Ns:
+//   v_r = x[j + r M/R] * W_{Ns R}^(r k),  X = DFT_R(v),  x[(j - k) R + k + r Ns] = X_r,
+// which leaves the result in natural order.  The twiddles come from one
+// table of W_N^q (q = 0..M) in shared memory; the buffer is padded by one
+// entry every 16 so that the first pass's stride-16 writes spread over the
+// banks.
 #pragma once
 
 #include "bm_internal.cuh"
@@ -38,67 +44,172 @@ __device__ __forceinline__ cpx<T> csub(cpx<T> a, cpx<T> b) { return {a.x - b.x, 
 template <typename T>
 __device__ __forceinline__ cpx<T> cconj(cpx<T> a) { return {a.x, -a.y}; }
 
-// One Stockham stage.  tw[e] = exp(-2 pi i e / (2M)) (the N-point table), so
-// W_M^e = tw[2e].  INV conjugates the twiddles and the radix-4 rotation.
-template <typename T, int R, bool INV>
-__device__ __forceinline__ void fft_stage(const cpx<T>* __restrict__ in, cpx<T>* __restrict__ out, int M,
-                                          int Ns, const cpx<T>* __restrict__ tw) {
-    const int Q = M / R;
-    const int step = M / (Ns * R);
-    for (int j = threadIdx.x; j < Q; j += blockDim.x) {
-        const int k = j & (Ns - 1);
-        const int e = k * step;
-        cpx<T> v[R];
-        v[0] = in[j];
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-            cpx<T> w = tw[2 * ((r * e) & (M - 1))];
-            if (INV) w.y = -w.y;
-            v[r] = cmul(in[j + r * Q], w);
-        }
-        const int idxD = (j - k) * R + k;
-        if (R == 4) {
-            const cpx<T> a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
-            const cpx<T> a2 = cadd(v[1], v[3]), a3 = csub(v[1], v[3]);
-            const cpx<T> mi3 = {a3.y, -a3.x};  // -i * a3
-            out[idxD] = cadd(a0, a2);
-            out[idxD + 2 * Ns] = csub(a0, a2);
-            if (!INV) {
-                out[idxD + Ns] = cadd(a1, mi3);
-                out[idxD + 3 * Ns] = csub(a1, mi3);
-            } else {
-                out[idxD + Ns] = csub(a1, mi3);
-                out[idxD + 3 * Ns] = cadd(a1, mi3);
-            }
-        } else {
-            out[idxD] = cadd(v[0], v[1]);
-            out[idxD + Ns] = csub(v[0], v[1]);
-        }
+// Padded shared-memory index: one spare entry after every 16.
+__device__ __forceinline__ int fpad(int a) { return a + (a >> 4); }
+__host__ __device__ inline int fft_buf_len(int M) { return M + M / 16 + 1; }
+
+// W_16^e (forward, e = 0..15) from the exact values cos(pi/8), sin(pi/8),
+// sqrt(1/2); INV conjugates.
+template <typename T>
+__device__ __forceinline__ cpx<T> w16(int e, bool inv) {
+    const T c1 = T(0.92387953251128675613), s1 = T(0.38268343236508977173), r2 = T(0.70710678118654752440);
+    T c, s;
+    switch (e & 15) {
+        case 0: c = 1; s = 0; break;
+        case 1: c = c1; s = s1; break;
+        case 2: c = r2; s = r2; break;
+        case 3: c = s1; s = c1; break;
+        case 4: c = 0; s = 1; break;
+        case 5: c = -s1; s = c1; break;
+        case 6: c = -r2; s = r2; break;
+        case 7: c = -c1; s = s1; break;
+        case 8: c = -1; s = 0; break;
+        case 9: c = -c1; s = -s1; break;
+        case 10: c = -r2; s = -r2; break;
+        case 11: c = -s1; s = -c1; break;
+        case 12: c = 0; s = -1; break;
+        case 13: c = s1; s = -c1; break;
+        case 14: c = r2; s = -r2; break;
+        default: c = c1; s = -s1; break;
     }
+    return {c, inv ? s : -s};  // exp(-/+ 2 pi i e / 16)
 }
 
-// M-point transform (M a power of two) from buf0; returns the buffer holding the result.
-template <typename T, bool INV>
-__device__ cpx<T>* fft_run(cpx<T>* buf0, cpx<T>* buf1, int M, const cpx<T>* __restrict__ tw) {
-    cpx<T>* a = buf0;
-    cpx<T>* b = buf1;
-    for (int Ns = 1; Ns < M;) {
-        if ((M / Ns) % 4 == 0) {
-            fft_stage<T, 4, INV>(a, b, M, Ns, tw);
+template <typename T>
+__device__ __forceinline__ void dft2(cpx<T>* v) {
+    const cpx<T> a = v[0];
+    v[0] = cadd(a, v[1]);
+    v[1] = csub(a, v[1]);
+}
+
+// In place on v[0], v[s], v[2s], v[3s].
+template <typename T, int S = 1>
+__device__ __forceinline__ void dft4(cpx<T>* v, bool inv) {
+    const cpx<T> t0 = cadd(v[0], v[2 * S]), t1 = csub(v[0], v[2 * S]);
+    const cpx<T> t2 = cadd(v[S], v[3 * S]), t3 = csub(v[S], v[3 * S]);
+    v[0] = cadd(t0, t2);
+    v[2 * S] = csub(t0, t2);
+    // forward: X1 = t1 - i t3, X3 = t1 + i t3; inverse swaps them
+    const cpx<T> mi3 = inv ? cpx<T>{-t3.y, t3.x} : cpx<T>{t3.y, -t3.x};  // -i t3 (forward), +i t3 (inverse)
+    v[S] = cadd(t1, mi3);
+    v[3 * S] = csub(t1, mi3);
+}
+
+// 8 = 4 x 2: x[2 n1 + n2]; a[n2][k1] = DFT4_n1, times W_8^(n2 k1); X[k1 + 4 k2] = DFT2_n2.
+// The result X[r] is left in v[slot8(r)] = v[2 (r mod 4) + r / 4].
+template <typename T>
+__device__ __forceinline__ void dft8(cpx<T>* v, bool inv) {
+    dft4<T, 2>(v, inv);      // n2 = 0: v[0], v[2], v[4], v[6] -> a[0][k1] at v[2 k1]
+    dft4<T, 2>(v + 1, inv);  // n2 = 1 -> a[1][k1] at v[2 k1 + 1]
+#pragma unroll
+    for (int k1 = 1; k1 < 4; ++k1) v[2 * k1 + 1] = cmul(v[2 * k1 + 1], w16<T>(2 * k1, inv));
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft2<T>(v + 2 * k1);  // X[k1 + 4 k2] at v[2 k1 + k2]
+}
+__host__ __device__ constexpr int slot8(int r) { return 2 * (r & 3) + (r >> 2); }
+
+// 16 = 4 x 4 (done inside the pass): x[4 n1 + n2]; a[n2][k1] = DFT4_n1, times
+// W_16^(n2 k1); X[k1 + 4 k2] = DFT4_n2, left in v[slot16(r)] = v[4 (r mod 4) + r / 4].
+__host__ __device__ constexpr int slot16(int r) { return 4 * (r & 3) + (r >> 2); }
+
+// W_M^e for e in [0, M) from the table tw[q] = W_N^q, q = 0..M (N = 2M).
+template <typename T>
+__device__ __forceinline__ cpx<T> twid(const cpx<T>* tws, int M, int e, bool inv) {
+    const int q = 2 * e;
+    cpx<T> w = q <= M ? tws[q] : cpx<T>{-tws[q - M].x, -tws[q - M].y};
+    if (inv) w.y = -w.y;
+    return w;
+}
+
+// One in-place Stockham pass of radix R; each thread owns up to NB
+// butterflies (j = threadIdx.x + b blockDim.x), whose points it holds in
+// registers across the barrier between the reads and the writes.
+template <typename T, int R, int NB>
+__device__ __forceinline__ void fft_pass(cpx<T>* buf, int M, int Ns, const cpx<T>* tws, bool inv) {
+    const int Q = M / R;
+    cpx<T> v[NB][R];
+#pragma unroll
+    for (int bb = 0; bb < NB; ++bb) {
+        const int j = threadIdx.x + bb * blockDim.x;
+        if (j < Q) {
+            const int k = j & (Ns - 1);
+            const int step = (M / (Ns * R)) * k;  // W_{Ns R}^(r k) = W_M^(r step)
+            auto load = [&](int r) {
+                cpx<T> x = buf[fpad(j + r * Q)];
+                if (r > 0 && Ns > 1) x = cmul(x, twid<T>(tws, M, r * step, inv));
+                return x;
+            };
+            cpx<T>* w = v[bb];
+            if (R == 16) {
+                // four groups x[4 n1 + n2] (n1 = 0..3): load, first DFT-4, inner twiddles
+#pragma unroll
+                for (int n2 = 0; n2 < 4; ++n2) {
+#pragma unroll
+                    for (int n1 = 0; n1 < 4; ++n1) w[n2 + 4 * n1] = load(4 * n1 + n2);
+                    dft4<T, 4>(w + n2, inv);
+#pragma unroll
+                    for (int k1 = 1; k1 < 4; ++k1)
+                        if (n2 > 0) w[n2 + 4 * k1] = cmul(w[n2 + 4 * k1], w16<T>(n2 * k1, inv));
+                }
+#pragma unroll
+                for (int k1 = 0; k1 < 4; ++k1) dft4<T, 1>(w + 4 * k1, inv);
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) w[r] = load(r);
+                if (R == 8) dft8<T>(w, inv);
+                else if (R == 4) dft4<T, 1>(w, inv);
+                else dft2<T>(w);
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int bb = 0; bb < NB; ++bb) {
+        const int j = threadIdx.x + bb * blockDim.x;
+        if (j < Q) {
+            const int k = j & (Ns - 1);
+            const int base = (j - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int sl = R == 16 ? slot16(r) : (R == 8 ? slot8(r) : r);
+                buf[fpad(base + r * Ns)] = v[bb][sl];
+            }
+        }
+    }
+    __syncthreads();
+}
+
+constexpr int kFftThreads = 256;
+
+// M-point transform in place (M a power of two, M <= MMAX), forward or
+// inverse (unnormalised); ends with a barrier.  RMAX caps the radix: 16
+// (M <= 4096, one butterfly per thread and pass) or 4 (for FP64, whose
+// points take twice the registers; up to MMAX / (2 kFftThreads) butterflies
+// per thread).
+template <typename T, int RMAX, int MMAX>
+__device__ __forceinline__ void fft_run(cpx<T>* buf, int M, const cpx<T>* tws, bool inv) {
+    static_assert(RMAX == 16 || RMAX == 4, "radix cap");
+    static_assert(RMAX == 4 || MMAX <= 16 * kFftThreads, "one radix-16 butterfly per thread");
+    constexpr int NB4 = RMAX == 16 ? 1 : (MMAX / 4 + kFftThreads - 1) / kFftThreads;
+    constexpr int NB2 = RMAX == 16 ? 1 : (MMAX / 2 + kFftThreads - 1) / kFftThreads;
+    int Ns = 1;
+    while (Ns < M) {
+        const int rem = M / Ns;
+        if (RMAX == 16 && rem >= 16) {
+            fft_pass<T, 16, 1>(buf, M, Ns, tws, inv);
+            Ns *= 16;
+        } else if (RMAX == 16 && rem == 8) {
+            fft_pass<T, 8, 1>(buf, M, Ns, tws, inv);
+            Ns *= 8;
+        } else if (rem >= 4) {
+            fft_pass<T, 4, NB4>(buf, M, Ns, tws, inv);
             Ns *= 4;
         } else {
-            fft_stage<T, 2, INV>(a, b, M, Ns, tw);
+            fft_pass<T, 2, NB2>(buf, M, Ns, tws, inv);
             Ns *= 2;
         }
-        __syncthreads();
-        cpx<T>* t = a;
-        a = b;
-        b = t;
     }
-    return a;
 }
-
-constexpr int kFftThreads = 512;
 
 struct FftGeom {
     const int64_t* det_off;
@@ -118,16 +229,29 @@ __device__ __forceinline__ int fft_tile_det(const int64_t* ts, int ndet, int64_t
     return lo;
 }
 
+// Radix cap and largest transform per element type (the host sizes the
+// FFT within these: N <= 8192 for FP32, N <= 4096 for FP64).
+template <typename T> constexpr int kFftRadix = sizeof(T) == 4 ? 16 : 4;
+template <typename T> constexpr int kFftMaxM = sizeof(T) == 4 ? 4096 : 2048;
+
+// Shared memory of the filter kernel: the padded buffer and the table.
+template <typename T>
+inline size_t fft_smem(int N) {
+    const int M = N / 2;
+    return sizeof(cpx<T>) * ((size_t)fft_buf_len(M) + (size_t)M + 1);
+}
+
 // One block of H = N - 2(L-1) outputs per iteration (grid-stride over blocks).
 // spec: [ndet][N/2 + 1] real band spectra; tw: [N] twiddles exp(-2 pi i e / N).
 template <typename T, class Src>
-__global__ void __launch_bounds__(kFftThreads)
+__global__ void __launch_bounds__(kFftThreads, 2)
 toeplitz_fft_kernel(Src src, const T* __restrict__ spec, const cpx<T>* __restrict__ tw, int N, int L, FftGeom geo,
                     T* __restrict__ z) {
-    extern __shared__ __align__(16) unsigned char fft_smem[];
+    extern __shared__ __align__(16) unsigned char fft_smem_raw[];
     const int M = N / 2;
-    cpx<T>* buf0 = reinterpret_cast<cpx<T>*>(fft_smem);
-    cpx<T>* buf1 = buf0 + M;
+    cpx<T>* buf = reinterpret_cast<cpx<T>*>(fft_smem_raw);
+    cpx<T>* tws = buf + fft_buf_len(M);  // W_N^q, q = 0..M
+    for (int q = threadIdx.x; q <= M; q += kFftThreads) tws[q] = tw[q];
     const int H = N - 2 * (L - 1);
     const T inv_m = T(1) / T(M);
     for (int64_t tile = blockIdx.x; tile < geo.ntiles; tile += gridDim.x) {
@@ -140,53 +264,58 @@ toeplitz_fft_kernel(Src src, const T* __restrict__ spec, const cpx<T>* __restric
         if (t0 >= ce) continue;  // uniform across the block
         const int64_t t1 = min(t0 + (int64_t)H, ce);
         const int64_t b0 = t0 - (L - 1);
-        __syncthreads();  // previous block done with the buffers
-        // Gather the block's inputs: four independent sample pairs per
-        // thread and pass, so their dependent loads (pixel, then map) overlap.
+        __syncthreads();  // previous block done with the buffer (and the table loaded)
+        // Gather the block's inputs: four sample pairs per thread in flight.
 #pragma unroll 4
         for (int n = threadIdx.x; n < M; n += kFftThreads) {
             const int64_t ta = b0 + 2 * n, tb = ta + 1;
             const T ya = (ta >= cs && ta < ce) ? T(src(ta)) : T(0);
             const T yb = (tb >= cs && tb < ce) ? T(src(tb)) : T(0);
-            buf0[n] = {ya, yb};
+            buf[fpad(n)] = {ya, yb};
         }
         __syncthreads();
-        cpx<T>* Z = fft_run<T, false>(buf0, buf1, M, tw);
-        cpx<T>* Zo = (Z == buf0) ? buf1 : buf0;
-        const T* K = spec + (int64_t)d * (M + 1);
-        // Even/odd split, multiply by the real spectrum, re-pack for the inverse.
-        for (int k = threadIdx.x; k <= M / 2; k += kFftThreads) {
-            const int k2 = M - k;
-            const cpx<T> zk = Z[k], zk2 = Z[k2 & (M - 1)];
-            const cpx<T> wk = tw[k], wk2 = tw[k2];  // W_N^k, W_N^(M-k)
-            // Y[k] = (zk + conj(zk2))/2 + W_N^k (zk - conj(zk2))/(2i)
-            auto yval = [&](cpx<T> a, cpx<T> b, cpx<T> w) {
-                const cpx<T> e = {T(0.5) * (a.x + b.x), T(0.5) * (a.y - b.y)};
-                const cpx<T> dd = {T(0.5) * (a.x - b.x), T(0.5) * (a.y + b.y)};  // (a - conj b)/2
-                const cpx<T> o = {dd.y, -dd.x};                                      // / i
-                return cadd(e, cmul(w, o));
-            };
-            cpx<T> Yk = yval(zk, zk2, wk);
-            cpx<T> Yk2 = yval(zk2, zk, wk2);
-            const T Kk = K[k], Kk2 = K[k2];
-            Yk = {Yk.x * Kk, Yk.y * Kk};
-            Yk2 = {Yk2.x * Kk2, Yk2.y * Kk2};
-            // Z'[k] = E' + i O', E' = (Y[k] + conj(Y[M-k]))/2, O' = (Y[k] - conj(Y[M-k])) conj(W_N^k)/2
-            auto zval = [&](cpx<T> a, cpx<T> b, cpx<T> w) {
-                const cpx<T> e = {T(0.5) * (a.x + b.x), T(0.5) * (a.y - b.y)};
-                const cpx<T> dd = {T(0.5) * (a.x - b.x), T(0.5) * (a.y + b.y)};
-                const cpx<T> o = cmul(dd, cconj(w));
-                return cpx<T>{e.x - o.y, e.y + o.x};  // e + i o
-            };
-            Zo[k] = zval(Yk, Yk2, wk);
-            if (k2 < M && k2 != k) Zo[k2] = zval(Yk2, Yk, wk2);
+        // forward transform, spectrum product, inverse transform: one copy of
+        // the transform code serves both directions
+        for (int dir = 0; dir < 2; ++dir) {
+            fft_run<T, kFftRadix<T>, kFftMaxM<T>>(buf, M, tws, dir == 1);
+            if (dir == 1) break;
+            const T* K = spec + (int64_t)d * (M + 1);
+            // Even/odd split, multiply by the real spectrum, re-pack for the
+            // inverse; each thread owns the pair (k, M - k), so this runs in place.
+            for (int k = threadIdx.x; k <= M / 2; k += kFftThreads) {
+                const int k2 = M - k;
+                const cpx<T> zk = buf[fpad(k)], zk2 = buf[fpad(k2 & (M - 1))];
+                const cpx<T> wk = tws[k], wk2 = tws[k2];  // W_N^k, W_N^(M-k)
+                // Y[k] = (zk + conj(zk2))/2 + W_N^k (zk - conj(zk2))/(2i)
+                auto yval = [&](cpx<T> a, cpx<T> b, cpx<T> w) {
+                    const cpx<T> e = {T(0.5) * (a.x + b.x), T(0.5) * (a.y - b.y)};
+                    const cpx<T> dd = {T(0.5) * (a.x - b.x), T(0.5) * (a.y + b.y)};  // (a - conj b)/2
+                    const cpx<T> o = {dd.y, -dd.x};                                      // / i
+                    return cadd(e, cmul(w, o));
+                };
+                cpx<T> Yk = yval(zk, zk2, wk);
+                cpx<T> Yk2 = yval(zk2, zk, wk2);
+                const T Kk = K[k], Kk2 = K[k2];
+                Yk = {Yk.x * Kk, Yk.y * Kk};
+                Yk2 = {Yk2.x * Kk2, Yk2.y * Kk2};
+                // Z'[k] = E' + i O', E' = (Y[k] + conj(Y[M-k]))/2, O' = (Y[k] - conj(Y[M-k])) conj(W_N^k)/2
+                auto zval = [&](cpx<T> a, cpx<T> b, cpx<T> w) {
+                    const cpx<T> e = {T(0.5) * (a.x + b.x), T(0.5) * (a.y - b.y)};
+                    const cpx<T> dd = {T(0.5) * (a.x - b.x), T(0.5) * (a.y + b.y)};
+                    const cpx<T> o = cmul(dd, cconj(w));
+                    return cpx<T>{e.x - o.y, e.y + o.x};  // e + i o
+                };
+                const cpx<T> zo = zval(Yk, Yk2, wk);
+                const cpx<T> zo2 = zval(Yk2, Yk, wk2);
+                buf[fpad(k)] = zo;
+                if (k2 < M && k2 != k) buf[fpad(k2)] = zo2;
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        cpx<T>* zo = fft_run<T, true>(Zo, Z, M, tw);
         const int nout = (int)(t1 - t0);
         for (int i = threadIdx.x; i < nout; i += kFftThreads) {
             const int m = L - 1 + i;
-            const cpx<T> v = zo[m >> 1];
+            const cpx<T> v = buf[fpad(m >> 1)];
             z[t0 + i] = ((m & 1) ? v.y : v.x) * inv_m;
         }
     }

@@ -1,177 +1,359 @@
 // Pointing ingest: the precomputation the paper performs once before the
-// solve (ProcessTimeSamples, Sec. III-A item 1).  From pix[t] and psi[t]:
-//   - validate pixel indices (-1 = flagged, else [0, npix));
-//   - cos 2psi, sin 2psi in FP64, stored as FP32 (hi, lo) pairs in time order;
-//   - a stable sort of the valid samples by pixel (LSD radix sort, 8-bit
-//     digits, deterministic tile ranks), giving the permutation perm, the CSR
-//     offsets off[npix+1] and the hit counts;
-//   - the trig pairs gathered into pixel-sorted order.
+// solve (ProcessTimeSamples, Sec. III-A item 1).  From pix[t] and psi[t] (or
+// the caller's cos 2psi, sin 2psi):
+//   - validate pixel indices (-1 = flagged, else [0, npix)) and angles;
+//   - cos 2psi, sin 2psi in time order (FP64 from psi, stored as FP32 hi + lo
+//     pairs; or the given FP32 values, which then define the operator);
+//   - a stable sort of the samples by pixel (LSD radix sort), giving the
+//     permutation perm, the trig pairs in pixel-sorted order, and the CSR
+//     offsets off[npix+1] and hit counts of the sorted order.
+//
+// Radix sort layout.  The samples are cut into G contiguous ranges, one per
+// block, each a whole number of 4096-sample tiles.  A pass counts the digits
+// of every range (bins x G counters), scans them digit-major, and each block
+// then walks its own range tile by tile, placing a tile's samples at its
+// running per-digit offsets.  The counter array stays small (G is a few
+// times the SM count), so the digits can be wide: up to 11 bits, two passes
+// for npix <= 2^22 (nside <= 512), one for npix <= 2^11.  Inside a tile the
+// stable rank of a sample comes from per-warp counters updated round by round
+// (match_any groups equal digits within a round), and the tile is staged in
+// shared memory in digit order so that each digit's run is written
+// contiguously.  Each thread loads its 16 samples (key, index, trig pair)
+// before ranking them, so a tile costs one memory latency, not one per round.
+//
+// The trig pairs travel with the keys as payload (each pass reads and writes
+// them once, in tile order): on this part a random 8-byte read moves about
+// 100 bytes of DRAM traffic, so gathering them through perm afterwards would
+// cost several times more.  The CSR offsets come from a binary search per
+// pixel in the sorted keys.
 #include "bm_internal.cuh"
 
 namespace bm {
 
 namespace {
 
+constexpr int IG_THREADS = 256;
+constexpr int IG_WARPS = IG_THREADS / 32;
+constexpr int IG_PER_THREAD = 16;
+constexpr int IG_TILE = IG_THREADS * IG_PER_THREAD;  // 4096 samples
+constexpr int IG_WARP_SPAN = IG_TILE / IG_WARPS;     // 512 consecutive samples per warp
+constexpr int RS_MAX_BITS = 11;
+constexpr uint32_t kNoDigit = 0xFFFFFFFFu;
+
+struct SortPlan {
+    int bits = 1, passes = 1, bins = 2, grid = 1;
+    int64_t range = IG_TILE;  // samples per block, a multiple of IG_TILE
+};
+
+__device__ __forceinline__ int64_t range_begin(int64_t range) { return (int64_t)blockIdx.x * range; }
+
+// Stores that ask L2 to keep their lines (evict_last): a scatter pass writes
+// each digit's output run a few samples per tile, so a 32-byte sector is
+// completed by later tiles of the same block; evicting it half written would
+// cost a read-modify-write in DRAM.
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void st_keep(uint32_t* p, uint32_t v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_keep(float2* p, float2 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y), "l"(pol)
+                 : "memory");
+}
+
 // ----------------------------------------------------------------- validate
 // Checks pixel indices and angles (or the given cos/sin pairs, |.| <= 1),
-// copies pix and writes the sort keys.  With cos/sin given, also interleaves
-// them into the time-ordered trig array.
+// copies pix, writes the sort keys (flagged samples get key npix and sort
+// last) and the time-ordered trig pairs.  counters[0] = invalid samples,
+// counters[1] = flagged samples.
+// MODE: kTrigIn (cos/sin given), kPsi64 or kPsi32 (angles given).
+constexpr int kTrigIn = 0, kPsi64 = 1, kPsi32 = 2;
+template <int MODE>
 __global__ void validate_kernel(const int32_t* __restrict__ pix, const void* __restrict__ psi,
-                                int psi_f64, const float* __restrict__ c32, const float* __restrict__ s32,
-                                int64_t n, int64_t npix, int32_t* __restrict__ pix_out,
-                                uint32_t* __restrict__ keys, float2* __restrict__ hi,
-                                unsigned long long* __restrict__ bad) {
-    unsigned long long nbad = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t p = pix[i];
+                                const float* __restrict__ c32, const float* __restrict__ s32, int64_t n,
+                                int64_t npix, int32_t* __restrict__ pix_out, uint32_t* __restrict__ keys,
+                                float2* __restrict__ hi, float2* __restrict__ lo,
+                                unsigned long long* __restrict__ counters) {
+    unsigned nbad = 0, nflag = 0;
+    auto one = [&](int64_t i, int32_t p, float c, float s, double a) {
         const bool ok_p = (p >= -1) && ((int64_t)p < npix);
         bool ok_a;
-        if (c32) {
-            const float c = c32[i], s = s32[i];
+        if constexpr (MODE == kTrigIn) {
             ok_a = fabsf(c) <= 1.0f && fabsf(s) <= 1.0f;  // false for NaN
             hi[i] = make_float2(c, s);
         } else {
-            const double a = psi_f64 ? static_cast<const double*>(psi)[i]
-                                     : (double)static_cast<const float*>(psi)[i];
             ok_a = isfinite(a);
+            double sn, cs;
+            sincos(2.0 * (ok_a ? a : 0.0), &sn, &cs);
+            const float ch = (float)cs, sh = (float)sn;
+            hi[i] = make_float2(ch, sh);
+            lo[i] = make_float2((float)(cs - (double)ch), (float)(sn - (double)sh));
         }
+        const bool kept = ok_p && p >= 0;
         nbad += (!ok_p) + (!ok_a);
+        nflag += !kept;
         pix_out[i] = ok_p ? p : -1;
-        keys[i] = (ok_p && p >= 0) ? (uint32_t)p : (uint32_t)npix;  // flagged sort last
+        keys[i] = kept ? (uint32_t)p : (uint32_t)npix;
+    };
+    // four samples per thread and pass, their loads issued together
+    constexpr int U = 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += U * stride) {
+        int32_t p[U];
+        float c[U], sv[U];
+        double a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + u * stride;
+            const bool v = i < n;
+            p[u] = v ? __ldcs(pix + i) : 0;
+            c[u] = sv[u] = 0.f;
+            a[u] = 0.0;
+            if constexpr (MODE == kTrigIn) {
+                if (v) {
+                    c[u] = __ldcs(c32 + i);
+                    sv[u] = __ldcs(s32 + i);
+                }
+            } else if constexpr (MODE == kPsi64) {
+                if (v) a[u] = __ldcs(static_cast<const double*>(psi) + i);
+            } else {
+                if (v) a[u] = (double)__ldcs(static_cast<const float*>(psi) + i);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) one(i, p[u], c[u], sv[u], a[u]);
+        }
     }
-    nbad = __reduce_add_sync(0xffffffffu, (unsigned)nbad);
-    if ((threadIdx.x & 31) == 0 && nbad) atomicAdd(bad, nbad);
-}
-
-// cos 2psi and sin 2psi in FP64, split into FP32 hi + FP32 lo.
-__global__ void trig_kernel(const void* __restrict__ psi, int psi_f64, int64_t n,
-                            float2* __restrict__ hi, float2* __restrict__ lo) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const double a = psi_f64 ? static_cast<const double*>(psi)[i]
-                                 : (double)static_cast<const float*>(psi)[i];
-        double s, c;
-        sincos(2.0 * a, &s, &c);
-        const float ch = (float)c, sh = (float)s;
-        hi[i] = make_float2(ch, sh);
-        lo[i] = make_float2((float)(c - (double)ch), (float)(s - (double)sh));
+    nbad = __reduce_add_sync(0xffffffffu, nbad);
+    nflag = __reduce_add_sync(0xffffffffu, nflag);
+    if ((threadIdx.x & 31) == 0) {
+        if (nbad) atomicAdd(&counters[0], (unsigned long long)nbad);
+        if (nflag) atomicAdd(&counters[1], (unsigned long long)nflag);
     }
 }
 
 // ------------------------------------------------------------ radix sort
-constexpr int RS_THREADS = 256;
-constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_ROUNDS = 16;                         // 32-element rounds per warp
-constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;       // 4096 keys per tile
-constexpr int RS_BINS = 256;
-
-__global__ void rs_hist_kernel(const uint32_t* __restrict__ keys, int64_t n, int shift,
-                               int64_t ntiles, uint32_t* __restrict__ hist) {
-    __shared__ uint32_t h[RS_BINS];
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        for (int d = threadIdx.x; d < RS_BINS; d += RS_THREADS) h[d] = 0;
-        __syncthreads();
-        const int64_t base = tile * RS_TILE;
-        for (int j = threadIdx.x; j < RS_TILE; j += RS_THREADS) {
-            const int64_t i = base + j;
-            if (i < n) atomicAdd(&h[(keys[i] >> shift) & 0xFF], 1u);
+// Digit counts of the block's range for one pass: hist[d * G + block].
+// Each thread counts 16 consecutive keys (vector loads), adding runs of equal
+// digits at once into its warp's own histogram; the warp histograms are
+// summed at the end.
+__global__ void __launch_bounds__(IG_THREADS)
+rs_hist_kernel(const uint32_t* __restrict__ keys, int64_t n, int64_t range, int shift, int bins, int G,
+               uint32_t* __restrict__ hist) {
+    extern __shared__ __align__(16) uint32_t hh[];  // [IG_WARPS][bins]
+    for (int d = threadIdx.x; d < IG_WARPS * bins; d += IG_THREADS) hh[d] = 0;
+    __syncthreads();
+    uint32_t* mine = hh + (threadIdx.x >> 5) * bins;
+    const uint32_t dmask = (uint32_t)bins - 1u;
+    const int64_t begin = range_begin(range);
+    const int64_t end = begin + range < n ? begin + range : n;
+    for (int64_t base = begin; base < end; base += IG_TILE) {
+        const int64_t i0 = base + (int64_t)threadIdx.x * IG_PER_THREAD;
+        uint32_t k[IG_PER_THREAD];
+        if (i0 + IG_PER_THREAD <= end) {
+            const uint4* v = reinterpret_cast<const uint4*>(keys + i0);  // i0 is a multiple of 16
+#pragma unroll
+            for (int q = 0; q < IG_PER_THREAD / 4; ++q) {
+                const uint4 x = __ldcs(v + q);
+                k[4 * q] = x.x;
+                k[4 * q + 1] = x.y;
+                k[4 * q + 2] = x.z;
+                k[4 * q + 3] = x.w;
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < IG_PER_THREAD; ++r) k[r] = i0 + r < end ? keys[i0 + r] : kNoDigit;
         }
-        __syncthreads();
-        for (int d = threadIdx.x; d < RS_BINS; d += RS_THREADS) hist[(int64_t)d * ntiles + tile] = h[d];
-        __syncthreads();
+        uint32_t cur = kNoDigit, run = 0;
+#pragma unroll
+        for (int r = 0; r < IG_PER_THREAD; ++r) {
+            const uint32_t d = k[r] == kNoDigit ? kNoDigit : ((k[r] >> shift) & dmask);
+            if (d == cur) {
+                ++run;
+            } else {
+                if (run) atomicAdd(&mine[cur], run);
+                cur = d;
+                run = d != kNoDigit;
+            }
+        }
+        if (run) atomicAdd(&mine[cur], run);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < bins; d += IG_THREADS) {
+        uint32_t t = 0;
+#pragma unroll
+        for (int q = 0; q < IG_WARPS; ++q) t += hh[q * bins + d];
+        hist[(int64_t)d * G + blockIdx.x] = t;
     }
 }
 
-// Stable scatter of one digit pass.  Each warp owns 512 consecutive keys of
-// the tile and ranks them in order (match_any + popc), warps are combined by
-// a per-digit prefix, and the tile is staged in shared memory in digit order
-// so that the global writes of a digit run are contiguous.
-__global__ void __launch_bounds__(RS_THREADS)
-rs_scatter_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-                  int64_t n, int shift, int64_t ntiles, const uint32_t* __restrict__ offs,
-                  uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out) {
-    __shared__ uint32_t s_keys[RS_TILE];
-    __shared__ uint32_t s_vals[RS_TILE];
-    __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];
-    __shared__ uint32_t dstart[RS_BINS];
-    __shared__ uint32_t gbase[RS_BINS];
-    __shared__ uint32_t wtot[RS_WARPS];
+// Exclusive scan of cnt[0, bins) into start[] by the whole block.
+__device__ void scan_bins(const uint32_t* cnt, uint32_t* start, int bins, uint32_t* wtot) {
+    const int per = bins >= IG_THREADS ? bins / IG_THREADS : 1;
+    const int b0 = threadIdx.x * per;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t local = 0;
+    for (int k = 0; k < per; ++k)
+        if (b0 + k < bins) local += cnt[b0 + k];
+    uint32_t x = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wtot[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        const uint32_t t = lane < IG_WARPS ? wtot[lane] : 0u;
+        uint32_t s = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < IG_WARPS) wtot[lane] = s - t;
+    }
+    __syncthreads();
+    uint32_t run = x - local + wtot[w];
+    for (int k = 0; k < per; ++k)
+        if (b0 + k < bins) {
+            start[b0 + k] = run;
+            run += cnt[b0 + k];
+        }
+}
+
+struct ScatterArgs {
+    const uint32_t* keys_in;
+    const uint32_t* vals_in;  // null: the sample index itself (first pass)
+    const float2* hi_in;      // trig payload in the input order of this pass
+    const float2* lo_in;      // null when the trig has no lo part
+    int64_t n;
+    int64_t range;
+    int shift, bins, G;
+    const uint32_t* offs;  // [bins][G] exclusive digit-major scan of the counts
+    uint32_t* keys_out;
+    uint32_t* vals_out;  // sample indices; the last pass writes perm
+    float2* hi_out;
+    float2* lo_out;
+    uint32_t key_limit;  // last pass: samples with keys >= key_limit (flagged) get no perm / trig entry
+};
+
+inline size_t scatter_smem(int bins) {
+    return sizeof(uint32_t) * (2 * (size_t)IG_TILE + 3 * (size_t)bins) + sizeof(float2) * IG_TILE +
+           sizeof(uint16_t) * (IG_TILE + (size_t)IG_WARPS * bins);
+}
+
+// One stable scatter pass over the block's range (see the file comment).
+// The lo half of an FP64 trig pair, when present, is not staged: it is read
+// back from the tile's window of the input (L2-resident) at write time.
+template <bool LAST>
+__global__ void __launch_bounds__(IG_THREADS, 2) rs_scatter_kernel(ScatterArgs a) {
+    extern __shared__ __align__(16) uint32_t ss[];
+    float2* s_hi = reinterpret_cast<float2*>(ss);
+    uint32_t* s_keys = reinterpret_cast<uint32_t*>(s_hi + IG_TILE);
+    uint32_t* s_vals = s_keys + IG_TILE;
+    uint32_t* run_base = s_vals + IG_TILE;  // next global position per digit
+    uint32_t* tcnt = run_base + a.bins;     // tile count per digit
+    uint32_t* tstart = tcnt + a.bins;       // tile-local start per digit
+    uint16_t* s_src = reinterpret_cast<uint16_t*>(tstart + a.bins);  // tile position of a staged sample
+    uint16_t* wcnt = s_src + IG_TILE;                                 // [warp][digit]
+    __shared__ uint32_t wtot[IG_WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
+    const int bins = a.bins;
+    const uint32_t dmask = (uint32_t)bins - 1u;
+    const int64_t begin = range_begin(a.range);
+    const int64_t end = begin + a.range < a.n ? begin + a.range : a.n;
+    const uint64_t pol = l2_keep_policy();
 
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t base = tile * RS_TILE;
-        const int cnt = (int)((n - base) < RS_TILE ? (n - base) : RS_TILE);
-        for (int d = threadIdx.x; d < RS_BINS; d += RS_THREADS) {
+    for (int d = threadIdx.x; d < bins; d += IG_THREADS) {
+        run_base[d] = a.offs[(int64_t)d * a.G + blockIdx.x];
 #pragma unroll
-            for (int q = 0; q < RS_WARPS; ++q) wcnt[q][d] = 0;
-            gbase[d] = offs[(int64_t)d * ntiles + tile];
+        for (int q = 0; q < IG_WARPS; ++q) wcnt[q * bins + d] = 0;
+    }
+    __syncthreads();
+
+    for (int64_t base = begin; base < end; base += IG_TILE) {
+        const int cnt = (int)(end - base < IG_TILE ? end - base : IG_TILE);
+        uint32_t key[IG_PER_THREAD], val[IG_PER_THREAD], rank[IG_PER_THREAD];
+        float2 hv[IG_PER_THREAD];
+        // 1. the warp's 512 consecutive samples, 32 per round
+#pragma unroll
+        for (int r = 0; r < IG_PER_THREAD; ++r) {
+            const int j = w * IG_WARP_SPAN + r * 32 + lane;
+            const bool v = j < cnt;
+            key[r] = v ? __ldcs(a.keys_in + base + j) : 0u;
+            val[r] = v ? (a.vals_in ? __ldcs(a.vals_in + base + j) : (uint32_t)(base + j)) : 0u;
+            hv[r] = v ? __ldcs(a.hi_in + base + j) : make_float2(0.f, 0.f);
         }
-        __syncthreads();
-        // 1. per-warp digit counts
-        for (int r = 0; r < RS_ROUNDS; ++r) {
-            const int j = w * (RS_TILE / RS_WARPS) + r * 32 + lane;
-            const bool valid = j < cnt;
-            const uint32_t d = valid ? ((keys_in[base + j] >> shift) & 0xFF) : 0x100u;
+        // 2. stable rank within the warp: counters advance round by round
+#pragma unroll
+        for (int r = 0; r < IG_PER_THREAD; ++r) {
+            const int j = w * IG_WARP_SPAN + r * 32 + lane;
+            const uint32_t d = j < cnt ? ((key[r] >> a.shift) & dmask) : kNoDigit;
             const unsigned peers = __match_any_sync(0xffffffffu, d);
-            if (valid && lane == __ffs(peers) - 1) wcnt[w][d] += __popc(peers);
+            const int leader = __ffs(peers) - 1;
+            uint32_t old = 0;
+            if (d != kNoDigit && lane == leader) {
+                old = wcnt[w * bins + d];
+                wcnt[w * bins + d] = (uint16_t)(old + __popc(peers));
+            }
+            old = __shfl_sync(0xffffffffu, old, leader);
+            rank[r] = old + __popc(peers & lt_mask);
             __syncwarp();
         }
         __syncthreads();
-        // 2. per digit: exclusive prefix over warps; tile total
-        uint32_t tot = 0;
-        if (threadIdx.x < RS_BINS) {
-            const int d = threadIdx.x;
+        // 3. per digit: exclusive prefix over warps, tile count; then over digits
+        for (int d = threadIdx.x; d < bins; d += IG_THREADS) {
+            uint32_t t = 0;
 #pragma unroll
-            for (int q = 0; q < RS_WARPS; ++q) {
-                const uint32_t c = wcnt[q][d];
-                wcnt[q][d] = tot;
-                tot += c;
+            for (int q = 0; q < IG_WARPS; ++q) {
+                const uint32_t c = wcnt[q * bins + d];
+                wcnt[q * bins + d] = (uint16_t)t;
+                t += c;
             }
+            tcnt[d] = t;
         }
-        // exclusive scan of tile totals over digits (RS_BINS == RS_THREADS)
-        {
-            uint32_t x = tot;
+        __syncthreads();
+        scan_bins(tcnt, tstart, bins, wtot);
+        __syncthreads();
+        // 4. stage the tile in digit order
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
+        for (int r = 0; r < IG_PER_THREAD; ++r) {
+            const int j = w * IG_WARP_SPAN + r * 32 + lane;
+            if (j < cnt) {
+                const uint32_t d = (key[r] >> a.shift) & dmask;
+                const uint32_t pos = tstart[d] + wcnt[w * bins + d] + rank[r];
+                s_keys[pos] = key[r];
+                s_vals[pos] = val[r];
+                s_hi[pos] = hv[r];
+                s_src[pos] = (uint16_t)j;
             }
-            if (lane == 31) wtot[w] = x;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                uint32_t run = 0;
-                for (int q = 0; q < RS_WARPS; ++q) { const uint32_t t = wtot[q]; wtot[q] = run; run += t; }
-            }
-            __syncthreads();
-            dstart[threadIdx.x] = x - tot + wtot[w];
         }
         __syncthreads();
-        // 3. ranks; stage keys/vals in digit order
-        for (int r = 0; r < RS_ROUNDS; ++r) {
-            const int j = w * (RS_TILE / RS_WARPS) + r * 32 + lane;
-            const bool valid = j < cnt;
-            const uint32_t key = valid ? keys_in[base + j] : 0u;
-            const uint32_t d = valid ? ((key >> shift) & 0xFF) : 0x100u;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-            if (valid) {
-                const uint32_t pos = dstart[d] + wcnt[w][d] + __popc(peers & lt_mask);
-                s_keys[pos] = key;
-                s_vals[pos] = vals_in ? vals_in[base + j] : (uint32_t)(base + j);
+        // 5. each digit's run goes to its running global offset
+        for (int j = threadIdx.x; j < cnt; j += IG_THREADS) {
+            const uint32_t k = s_keys[j];
+            const uint32_t d = (k >> a.shift) & dmask;
+            const uint32_t g = run_base[d] + (uint32_t)j - tstart[d];
+            st_keep(a.keys_out + g, k, pol);
+            if (!LAST || k < a.key_limit) {
+                st_keep(a.vals_out + g, s_vals[j], pol);
+                st_keep(a.hi_out + g, s_hi[j], pol);
+                if (a.lo_in) st_keep(a.lo_out + g, a.lo_in[base + s_src[j]], pol);
             }
-            __syncwarp();
-            if (valid && lane == __ffs(peers) - 1) wcnt[w][d] += __popc(peers);
-            __syncwarp();
         }
         __syncthreads();
-        // 4. contiguous writes per digit run
-        for (int j = threadIdx.x; j < cnt; j += RS_THREADS) {
-            const uint32_t key = s_keys[j];
-            const uint32_t d = (key >> shift) & 0xFF;
-            const uint64_t pos = (uint64_t)gbase[d] + (uint64_t)(j - (int)dstart[d]);
-            keys_out[pos] = key;
-            vals_out[pos] = s_vals[j];
+        // 6. advance the running offsets, clear the warp counters
+        for (int d = threadIdx.x; d < bins; d += IG_THREADS) {
+            run_base[d] += tcnt[d];
+#pragma unroll
+            for (int q = 0; q < IG_WARPS; ++q) wcnt[q * bins + d] = 0;
         }
         __syncthreads();
     }
@@ -179,7 +361,7 @@ rs_scatter_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restri
 
 // off[p] = first sorted index whose key >= p, for p in [0, npix].
 __global__ void lower_bound_kernel(const uint32_t* __restrict__ keys, int64_t n, int64_t npix,
-                                   int64_t* __restrict__ off, int32_t* __restrict__ hits_unused) {
+                                   int64_t* __restrict__ off) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p <= npix;
          p += (int64_t)gridDim.x * blockDim.x) {
         int64_t lo = 0, hi = n;
@@ -197,15 +379,27 @@ __global__ void hits_kernel(const int64_t* __restrict__ off, int64_t npix, int32
         hits[p] = (int32_t)(off[p + 1] - off[p]);
 }
 
-__global__ void gather_trig_kernel(const uint32_t* __restrict__ perm, int64_t n,
-                                   const float2* __restrict__ hi_t, const float2* __restrict__ lo_t,
-                                   float2* __restrict__ hi_s, float2* __restrict__ lo_s) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t t = perm[i];
-        hi_s[i] = hi_t[t];
-        if (lo_t) lo_s[i] = lo_t[t];
-    }
+
+SortPlan plan_sort(const bm_context* ctx, int64_t n, int64_t npix) {
+    SortPlan sp;
+    int nbits = 1;
+    while (((int64_t)1 << nbits) <= npix) ++nbits;  // the flagged key npix must fit too
+    sp.passes = (nbits + RS_MAX_BITS - 1) / RS_MAX_BITS;
+    sp.bits = (nbits + sp.passes - 1) / sp.passes;
+    sp.bins = 1 << sp.bits;
+    const size_t smem = scatter_smem(sp.bins);
+    ensure_smem_limit(reinterpret_cast<const void*>(rs_scatter_kernel<false>), smem);
+    ensure_smem_limit(reinterpret_cast<const void*>(rs_scatter_kernel<true>), smem);
+    ensure_smem_limit(reinterpret_cast<const void*>(rs_hist_kernel), sizeof(uint32_t) * IG_WARPS * sp.bins);
+    int per_sm = blocks_per_sm(reinterpret_cast<const void*>(rs_scatter_kernel<true>), IG_THREADS, smem);
+    if (per_sm < 1) per_sm = 1;
+    // four waves of equal ranges keep the tail short
+    const int64_t want = (int64_t)ctx->num_sms * per_sm * 4;
+    const int64_t ntiles = (n + IG_TILE - 1) / IG_TILE;
+    const int64_t tiles_per_block = (ntiles + want - 1) / want;
+    sp.range = tiles_per_block * IG_TILE;
+    sp.grid = (int)((n + sp.range - 1) / sp.range);
+    return sp;
 }
 
 }  // namespace
@@ -216,75 +410,114 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
     cudaStream_t s = ctx->stream;
     ScopedTimer timer(ctx, "ingest");
     const int64_t n = p->nsamples, npix = p->npix;
-    const int psi_f64 = psi_dtype == BM_F64;
-    const int threads = 256;
-    const int grid = grid_for(ctx, (n + threads - 1) / threads, 16);
-
     const bool exact_trig = cos2psi != nullptr;  // FP32 trig given: it defines the operator, no lo part
+    const bool has_lo = !exact_trig;
+    const SortPlan sp = plan_sort(ctx, n, npix);
+    const int threads = 256;
+
     p->pix.alloc(n);
     p->cs_hi_t.alloc(n);
-    if (!exact_trig) p->cs_lo_t.alloc(n);
-    DevBuf<uint32_t> keys_a(n), keys_b(n), vals_a(n), vals_b(n);
-    DevBuf<unsigned long long> bad(1);
-    BM_CUDA(cudaMemsetAsync(bad.get(), 0, sizeof(unsigned long long), s));
-    validate_kernel<<<grid, threads, 0, s>>>(pix, psi, psi_f64, cos2psi, sin2psi, n, npix, p->pix.get(),
-                                             keys_a.get(), p->cs_hi_t.get(), bad.get());
-    BM_LAUNCH_CHECK();
-    unsigned long long h_bad = 0;
-    BM_CUDA(cudaMemcpyAsync(&h_bad, bad.get(), sizeof(h_bad), cudaMemcpyDeviceToHost, s));
-    BM_CUDA(cudaStreamSynchronize(s));
-    BM_REQUIRE(h_bad == 0, "%llu samples have a pixel index outside [-1, %lld) or a bad angle / trig value",
-               h_bad, (long long)npix);
-
-    if (!exact_trig) {
-        trig_kernel<<<grid, threads, 0, s>>>(psi, psi_f64, n, p->cs_hi_t.get(), p->cs_lo_t.get());
+    if (has_lo) p->cs_lo_t.alloc(n);
+    DevBuf<uint32_t> keys_a(n), keys_b(n);
+    DevBuf<unsigned long long> counters(2);
+    BM_CUDA(cudaMemsetAsync(counters.get(), 0, 2 * sizeof(unsigned long long), s));
+    {
+        ScopedTimer vt(ctx, "ingest_validate");
+        auto kern = exact_trig ? validate_kernel<kTrigIn>
+                               : (psi_dtype == BM_F64 ? validate_kernel<kPsi64> : validate_kernel<kPsi32>);
+        const int grid = resident_grid(ctx, kern, threads, (n + threads - 1) / threads);
+        kern<<<grid, threads, 0, s>>>(pix, psi, cos2psi, sin2psi, n, npix, p->pix.get(), keys_a.get(),
+                                      p->cs_hi_t.get(), p->cs_lo_t.get(), counters.get());
         BM_LAUNCH_CHECK();
     }
+    unsigned long long h_cnt[2] = {0, 0};
+    BM_CUDA(cudaMemcpyAsync(h_cnt, counters.get(), sizeof(h_cnt), cudaMemcpyDeviceToHost, s));
+    BM_CUDA(cudaStreamSynchronize(s));
+    BM_REQUIRE(h_cnt[0] == 0, "%llu samples have a pixel index outside [-1, %lld) or a bad angle / trig value",
+               h_cnt[0], (long long)npix);
+    const int64_t nvalid = n - (int64_t)h_cnt[1];
+    p->nvalid = nvalid;
+    p->perm.alloc(nvalid > 0 ? nvalid : 1);
+    p->cs_hi_s.alloc(nvalid > 0 ? nvalid : 1);
+    if (has_lo) p->cs_lo_s.alloc(nvalid > 0 ? nvalid : 1);
 
-    // LSD radix sort of (key, sample index) over the bits of npix.
-    int nbits = 1;
-    while (((int64_t)1 << nbits) <= npix) ++nbits;
-    const int passes = (nbits + 7) / 8;
-    const int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
-    DevBuf<uint32_t> hist((size_t)RS_BINS * ntiles);
-    const int rs_grid = (int)std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * 4);
+    // Ping-pong buffers of the intermediate passes: sample indices and the
+    // trig payload (hi, and lo when the angles were given).
+    DevBuf<uint32_t> hist((size_t)sp.bins * sp.grid);
+    DevBuf<uint32_t> vals_a, vals_b;
+    DevBuf<float2> hi_a, hi_b, lo_a, lo_b;
+    if (sp.passes > 1) {
+        vals_a.alloc(n);
+        hi_a.alloc(n);
+        if (has_lo) lo_a.alloc(n);
+    }
+    if (sp.passes > 2) {
+        vals_b.alloc(n);
+        hi_b.alloc(n);
+        if (has_lo) lo_b.alloc(n);
+    }
+    const size_t smem = scatter_smem(sp.bins);
     uint32_t* kin = keys_a.get();
     uint32_t* kout = keys_b.get();
-    uint32_t* vin = nullptr;  // identity on the first pass
-    uint32_t* vout = vals_b.get();
-    for (int pass = 0; pass < passes; ++pass) {
-        const int shift = 8 * pass;
-        rs_hist_kernel<<<rs_grid, RS_THREADS, 0, s>>>(kin, n, shift, ntiles, hist.get());
-        BM_LAUNCH_CHECK();
-        exclusive_scan_u32(hist.get(), hist.get(), (int64_t)RS_BINS * ntiles, s);
-        rs_scatter_kernel<<<rs_grid, RS_THREADS, 0, s>>>(kin, vin, n, shift, ntiles, hist.get(), kout, vout);
-        BM_LAUNCH_CHECK();
+    const uint32_t* vin = nullptr;  // the sample index on the first pass
+    uint32_t* vout = vals_a.get();
+    const float2* hin = p->cs_hi_t.get();
+    const float2* lin = has_lo ? p->cs_lo_t.get() : nullptr;
+    float2* hout = hi_a.get();
+    float2* lout = lo_a.get();
+    for (int pass = 0; pass < sp.passes; ++pass) {
+        const int shift = pass * sp.bits;
+        {
+            ScopedTimer ht(ctx, "ingest_hist");
+            rs_hist_kernel<<<sp.grid, IG_THREADS, sizeof(uint32_t) * IG_WARPS * sp.bins, s>>>(kin, n, sp.range, shift,
+                                                                                         sp.bins, sp.grid, hist.get());
+            BM_LAUNCH_CHECK();
+        }
+        exclusive_scan_u32(hist.get(), hist.get(), (int64_t)sp.bins * sp.grid, s);
+        ScatterArgs a{};
+        a.keys_in = kin;
+        a.vals_in = vin;
+        a.hi_in = hin;
+        a.lo_in = lin;
+        a.n = n;
+        a.range = sp.range;
+        a.shift = shift;
+        a.bins = sp.bins;
+        a.G = sp.grid;
+        a.offs = hist.get();
+        a.keys_out = kout;
+        if (pass + 1 < sp.passes) {
+            a.vals_out = vout;
+            a.hi_out = hout;
+            a.lo_out = lout;
+            ScopedTimer st(ctx, "ingest_scatter");
+            rs_scatter_kernel<false><<<sp.grid, IG_THREADS, smem, s>>>(a);
+            BM_LAUNCH_CHECK();
+            vin = vout;
+            hin = hout;
+            lin = has_lo ? lout : nullptr;
+            vout = (vout == vals_a.get()) ? vals_b.get() : vals_a.get();
+            hout = (hout == hi_a.get()) ? hi_b.get() : hi_a.get();
+            lout = (lout == lo_a.get()) ? lo_b.get() : lo_a.get();
+        } else {
+            a.vals_out = p->perm.get();
+            a.hi_out = p->cs_hi_s.get();
+            a.lo_out = has_lo ? p->cs_lo_s.get() : nullptr;
+            a.key_limit = (uint32_t)npix;
+            ScopedTimer st(ctx, "ingest_scatter");
+            rs_scatter_kernel<true><<<sp.grid, IG_THREADS, smem, s>>>(a);
+            BM_LAUNCH_CHECK();
+        }
         std::swap(kin, kout);
-        vin = vout;
-        vout = (vout == vals_b.get()) ? vals_a.get() : vals_b.get();
     }
-    // kin / vin now hold the sorted keys and sample indices.
+    // kin holds the sorted keys (flagged samples, key npix, last).
     p->off.alloc(npix + 1);
     p->hits.alloc(npix);
     const int pgrid = grid_for(ctx, (npix + 1 + threads - 1) / threads, 16);
-    lower_bound_kernel<<<pgrid, threads, 0, s>>>(kin, n, npix, p->off.get(), nullptr);
+    lower_bound_kernel<<<pgrid, threads, 0, s>>>(kin, n, npix, p->off.get());
     BM_LAUNCH_CHECK();
     hits_kernel<<<pgrid, threads, 0, s>>>(p->off.get(), npix, p->hits.get());
     BM_LAUNCH_CHECK();
-    int64_t nvalid = 0;
-    BM_CUDA(cudaMemcpyAsync(&nvalid, p->off.get() + npix, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    BM_CUDA(cudaStreamSynchronize(s));
-    p->nvalid = nvalid;
-
-    p->perm.alloc(nvalid > 0 ? nvalid : 1);
-    p->cs_hi_s.alloc(nvalid > 0 ? nvalid : 1);
-    if (!exact_trig) p->cs_lo_s.alloc(nvalid > 0 ? nvalid : 1);
-    if (nvalid > 0) {
-        BM_CUDA(cudaMemcpyAsync(p->perm.get(), vin, sizeof(uint32_t) * nvalid, cudaMemcpyDeviceToDevice, s));
-        gather_trig_kernel<<<grid, threads, 0, s>>>(p->perm.get(), nvalid, p->cs_hi_t.get(), p->cs_lo_t.get(),
-                                                    p->cs_hi_s.get(), p->cs_lo_s.get());
-        BM_LAUNCH_CHECK();
-    }
     BM_CUDA(cudaStreamSynchronize(s));
 }
 

@@ -225,12 +225,10 @@ gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __rest
             df32 acc[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) acc[c] = {0.f, 0.f};
-            for (int i = lane; i < len; i += 32) {
-                const int64_t si = b + i;
-                const uint32_t t = perm[si];
+            auto add = [&](uint32_t t, G gv, float2 h, float2 l) {
                 df32 val;
-                if (sizeof(G) == 4) val = {(float)g[t], 0.f};
-                else val = df_from((double)g[t]);
+                if (sizeof(G) == 4) val = {(float)gv, 0.f};
+                else val = df_from((double)gv);
                 if (weighted) {
                     const float2 w = wp[find_det32(offp, ndet, t)];
                     val = df_mul(val, df32{w.x, w.y});
@@ -238,12 +236,35 @@ gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __rest
                 if (NC == 1) {
                     acc[0] = df_add(acc[0], val);
                 } else {
-                    const float2 h = hi[si];
-                    const float2 l = lo ? lo[si] : make_float2(0.f, 0.f);
                     if (NC == 3) acc[0] = df_add(acc[0], val);
                     acc[NC - 2] = df_add(acc[NC - 2], df_mul(val, df32{h.x, l.x}));
                     acc[NC - 1] = df_add(acc[NC - 1], df_mul(val, df32{h.y, l.y}));
                 }
+            };
+            // Four samples per lane in flight (the gathers g[perm] are
+            // independent); the lane's samples are still added in order.
+            int i = lane;
+            for (; i + 96 < len; i += 128) {
+                uint32_t t[4];
+                G gv[4];
+                float2 h[4], l[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) t[u] = perm[b + i + 32 * u];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    gv[u] = g[t[u]];
+                    h[u] = NC > 1 ? hi[b + i + 32 * u] : make_float2(0.f, 0.f);
+                    l[u] = (NC > 1 && lo) ? lo[b + i + 32 * u] : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) add(t[u], gv[u], h[u], l[u]);
+            }
+            for (; i < len; i += 32) {
+                const int64_t si = b + i;
+                const uint32_t t = perm[si];
+                const float2 h = NC > 1 ? hi[si] : make_float2(0.f, 0.f);
+                const float2 l = (NC > 1 && lo) ? lo[si] : make_float2(0.f, 0.f);
+                add(t, g[t], h, l);
             }
 #pragma unroll
             for (int c = 0; c < NC; ++c) acc[c] = df_warp_sum(acc[c]);
@@ -254,10 +275,8 @@ gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __rest
             double acc[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) acc[c] = 0.0;
-            for (int i = lane; i < len; i += 32) {
-                const int64_t si = b + i;
-                const uint32_t t = perm[si];
-                double val = (double)g[t];
+            auto add = [&](uint32_t t, G gv, int64_t si) {
+                double val = (double)gv;
                 if (weighted) val *= white[find_det32(offp, ndet, t)];
                 if (NC == 1) {
                     acc[0] += val;
@@ -267,6 +286,21 @@ gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __rest
                     acc[NC - 2] += val * cs.x;
                     acc[NC - 1] += val * cs.y;
                 }
+            };
+            int i = lane;
+            for (; i + 96 < len; i += 128) {
+                uint32_t t[4];
+                G gv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) t[u] = perm[b + i + 32 * u];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) gv[u] = g[t[u]];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) add(t[u], gv[u], b + i + 32 * u);
+            }
+            for (; i < len; i += 32) {
+                const uint32_t t = perm[b + i];
+                add(t, g[t], b + i);
             }
 #pragma unroll
             for (int c = 0; c < NC; ++c) acc[c] = warp_sum(acc[c]);
@@ -480,8 +514,7 @@ static void run_toeplitz(bm_inv_noise* n, const Src& src, const T* coeffs, T* z)
     plan_toeplitz(n, kTzThreads * R, tp);
     if (tp.geo.ntiles == 0) return;
     const size_t smem = toeplitz_smem<T, R>(n->nlags);
-    BM_CUDA(cudaFuncSetAttribute(toeplitz_kernel<T, R, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
+    ensure_smem_limit(reinterpret_cast<const void*>(toeplitz_kernel<T, R, Src>), smem);
     const int grid = (int)std::min<int64_t>(tp.geo.ntiles, (int64_t)ctx->num_sms * 8);
     toeplitz_kernel<T, R, Src><<<grid, kTzThreads, smem, ctx->stream>>>(src, coeffs, n->nlags, tp.geo, z);
     BM_LAUNCH_CHECK();  // tile_start is released stream-ordered after the kernel
@@ -542,9 +575,9 @@ static void run_toeplitz_fft(bm_inv_noise* n, const Src& src, int N, const T* sp
     if (tp.geo.ntiles == 0) return;
     const FftGeom geo{tp.geo.det_off, tp.geo.tile_start, tp.geo.ndet, tp.geo.chunk_len, tp.geo.tiles_per_chunk,
                       tp.geo.ntiles};
-    const size_t smem = (size_t)2 * N * sizeof(T);
+    const size_t smem = fft_smem<T>(N);
     auto kern = toeplitz_fft_kernel<T, Src>;
-    BM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ensure_smem_limit(reinterpret_cast<const void*>(kern), smem);
     const int grid = resident_grid(ctx, kern, kFftThreads, tp.geo.ntiles, smem);
     kern<<<grid, kFftThreads, smem, ctx->stream>>>(src, spec, tw, N, n->nlags, geo, z);
     BM_LAUNCH_CHECK();

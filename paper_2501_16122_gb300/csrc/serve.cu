@@ -13,6 +13,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -138,9 +139,12 @@ void worker_main(bm_server* s, int slot) {
         s->running += 1;
         lk.unlock();
         const bm_status st = ok ? run_request(ctx, job) : BM_ERR_CUDA;
+        char msg[sizeof(job.res.message)] = "";
+        if (st != BM_OK) std::snprintf(msg, sizeof(msg), "%s", ok ? bm_last_error() : "worker context failed");
         lk.lock();
         job.t_done = Clock::now();
         job.res.status = st;
+        std::memcpy(job.res.message, msg, sizeof(msg));
         job.res.queue_ms = ms_between(job.t_submit, job.t_start);
         job.res.run_ms = ms_between(job.t_start, job.t_done);
         job.res.latency_ms = ms_between(job.t_submit, job.t_done);

@@ -1,5 +1,5 @@
-// Device-wide exclusive scans used by the ingest (radix-sort offsets) and by
-// the work-item planner.  Three phases with a fixed decomposition, so the
+// Device-wide exclusive scans used by the ingest (radix-sort offsets, CSR
+// offsets from hit counts) and by the work-item planner.  Three phases with a fixed decomposition, so the
 // result never depends on scheduling.
 #include "bm_internal.cuh"
 
@@ -41,8 +41,8 @@ __device__ T block_exclusive_scan(T v, T* warp_tot, T* total) {
     return r;
 }
 
-template <typename T>
-__global__ void scan_reduce_kernel(const T* __restrict__ in, int64_t n, T* __restrict__ sums) {
+template <typename TI, typename T>
+__global__ void scan_reduce_kernel(const TI* __restrict__ in, int64_t n, T* __restrict__ sums) {
     __shared__ T red[kScanThreads];
     const int64_t base = (int64_t)blockIdx.x * kScanChunk;
     T acc = 0;
@@ -56,9 +56,10 @@ __global__ void scan_reduce_kernel(const T* __restrict__ in, int64_t n, T* __res
     if (threadIdx.x == 0) sums[blockIdx.x] = red[0];
 }
 
-// Exclusive scan of the block sums in place (single block, sequential tiles).
+// Exclusive scan of the block sums in place (single block, sequential tiles);
+// the grand total goes to *total_out when given.
 template <typename T>
-__global__ void scan_top_kernel(T* __restrict__ sums, int64_t nb) {
+__global__ void scan_top_kernel(T* __restrict__ sums, int64_t nb, T* __restrict__ total_out) {
     __shared__ T warp_tot[kScanThreads / 32];
     __shared__ T total;
     T carry = 0;
@@ -70,10 +71,11 @@ __global__ void scan_top_kernel(T* __restrict__ sums, int64_t nb) {
         carry += total;
         __syncthreads();
     }
+    if (total_out && threadIdx.x == 0) *total_out = carry;
 }
 
-template <typename T>
-__global__ void scan_apply_kernel(const T* __restrict__ in, T* __restrict__ out, int64_t n,
+template <typename TI, typename T>
+__global__ void scan_apply_kernel(const TI* __restrict__ in, T* __restrict__ out, int64_t n,
                                   const T* __restrict__ sums) {
     __shared__ T warp_tot[kScanThreads / 32];
     __shared__ T total;
@@ -87,7 +89,7 @@ __global__ void scan_apply_kernel(const T* __restrict__ in, T* __restrict__ out,
 #pragma unroll
         for (int k = 0; k < kScanItems; ++k) {
             const int64_t i = base + (int64_t)threadIdx.x * kScanItems + k;
-            v[k] = i < n ? in[i] : T(0);
+            v[k] = i < n ? T(in[i]) : T(0);
             local += v[k];
         }
         T e = block_exclusive_scan(local, warp_tot, &total);
@@ -103,26 +105,29 @@ __global__ void scan_apply_kernel(const T* __restrict__ in, T* __restrict__ out,
     }
 }
 
-template <typename T>
-void exclusive_scan(const T* in, T* out, int64_t n, cudaStream_t s) {
+template <typename TI, typename T>
+void exclusive_scan(const TI* in, T* out, int64_t n, cudaStream_t s, T* total_out = nullptr) {
     if (n <= 0) return;
     const int64_t nb = (n + kScanChunk - 1) / kScanChunk;
     DevBuf<T> sums(nb);
-    scan_reduce_kernel<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums.get());
+    scan_reduce_kernel<TI, T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums.get());
     BM_LAUNCH_CHECK();
-    scan_top_kernel<T><<<1, kScanThreads, 0, s>>>(sums.get(), nb);
+    scan_top_kernel<T><<<1, kScanThreads, 0, s>>>(sums.get(), nb, total_out);
     BM_LAUNCH_CHECK();
-    scan_apply_kernel<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, sums.get());
+    scan_apply_kernel<TI, T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, sums.get());
     BM_LAUNCH_CHECK();  // sums is released stream-ordered after the kernels
 }
 
 }  // namespace
 
 void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s) {
-    exclusive_scan<int64_t>(in, out, n, s);
+    exclusive_scan<int64_t, int64_t>(in, out, n, s);
 }
 void exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s) {
-    exclusive_scan<uint32_t>(in, out, n, s);
+    exclusive_scan<uint32_t, uint32_t>(in, out, n, s);
+}
+void offsets_from_counts(const int32_t* counts, int64_t n, int64_t* off, cudaStream_t s) {
+    exclusive_scan<int32_t, int64_t>(counts, off, n, s, off + n);
 }
 
 }  // namespace bm

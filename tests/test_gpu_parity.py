@@ -87,6 +87,44 @@ def test_pointing_operators_and_hits(L, ctx, solver):
         c.close()
 
 
+@pytest.mark.parametrize("nside,n,trig", [(8, 200_003, False),       # 10-bit keys: one sort pass
+                                          (64, 3_000_001, True),     # 16 bits: two passes, many ranges
+                                          (1024, 500_009, False)])   # 24 bits: three passes
+def test_sort_plans_random_pixels(L, ctx, nside, n, trig):
+    """The pixel sort behind P^T for every pass count, on random pixels with
+    10 % flagged samples and a ragged last tile: hit counts bit-exact, P^T y
+    and P x against the oracle's definition of Eq. 8."""
+    npix = 12 * nside * nside
+    rng = np.random.default_rng(nside)
+    pix = rng.integers(0, npix, size=n).astype(np.int32)
+    # runs of repeated pixels, as a scan produces
+    pix[1::3] = pix[0::3][: pix[1::3].size]
+    pix[rng.random(n) < 0.1] = -1
+    psi = rng.uniform(0, np.pi, size=n)
+    d_pix = torch.from_numpy(pix).cuda()
+    if trig:
+        c32, s32 = synth.trig32(psi)
+        p = L.bm_pointing_create_trig(ctx, npix, d_pix, torch.from_numpy(c32).cuda(), torch.from_numpy(s32).cuda(), 3)
+        v = gls.pointing_weights_trig(c32, s32, 3)
+    else:
+        p = L.bm_pointing_create(ctx, npix, d_pix, torch.from_numpy(psi).cuda(), 3)
+        v = gls.pointing_weights(psi, 3)
+    try:
+        hits = torch.zeros(npix, dtype=torch.int32, device="cuda")
+        L.bm_pointing_get_hits(p, hits)
+        assert np.array_equal(hits.cpu().numpy(), gls.hits(pix, npix))
+        y = rng.normal(size=n)
+        xt = torch.zeros(npix * 3, dtype=torch.float64, device="cuda")
+        L.bm_pointing_apply_transpose(p, torch.from_numpy(y).cuda(), xt)
+        assert rel(xt.cpu().numpy(), gls.apply_PT(pix, v, y, npix).ravel()) < 1e-13
+        x = rng.normal(size=(npix, 3))
+        yy = torch.zeros(n, dtype=torch.float64, device="cuda")
+        L.bm_pointing_apply(p, torch.from_numpy(x.ravel()).cuda(), yy)
+        assert rel(yy.cpu().numpy(), gls.apply_P(pix, v, x)) < 1e-13
+    finally:
+        L.bm_pointing_destroy(p)
+
+
 @pytest.mark.parametrize("solver", [3, 2, 1])
 def test_blocks_cond_mask(L, ctx, solver):
     c = Case(L, ctx, 16, 4, 65_536, 1000, solver=solver)
@@ -375,5 +413,48 @@ def test_trig_input_config1_like_solve(L, ctx):
             st, infos = L.bm_pcg_solve(c.p, c.n, c.pc, c.d_tod, 1, out, tol_solve, 100, prec)
             assert st == L.BM_OK, infos
             check_map(L, c, out, ref, tol_err)
+    finally:
+        c.close()
+
+
+def test_pinned_host_inputs_match_device_inputs(L, ctx):
+    """Page-locked host pix / trig / TOD go through the same computation as
+    device arrays: hits, P^T y and the solved map are bitwise equal."""
+    c = Case(L, ctx, 16, 4, 40_000, 4242, flag=0.01, trig=True, tod_dtype=np.float32, build_oracle=False)
+    try:
+        c32, s32 = c.trig
+        dev = L.bm_pointing_create_trig(ctx, c.npix, c.d_pix, torch.from_numpy(c32).cuda(),
+                                        torch.from_numpy(s32).cuda(), 3)
+        host = L.bm_pointing_create_trig(ctx, c.npix, torch.from_numpy(c.pix).pin_memory(),
+                                         torch.from_numpy(c32).pin_memory(), torch.from_numpy(s32).pin_memory(), 3)
+        with pytest.raises(Exception):  # pageable host memory is refused
+            L.bm_pointing_create_trig(ctx, c.npix, torch.from_numpy(c.pix), torch.from_numpy(c32),
+                                      torch.from_numpy(s32), 3)
+        try:
+            h1 = torch.zeros(c.npix, dtype=torch.int32, device="cuda")
+            h2 = torch.zeros_like(h1)
+            L.bm_pointing_get_hits(dev, h1)
+            L.bm_pointing_get_hits(host, h2)
+            assert torch.equal(h1, h2)
+            y = torch.randn(c.e.nsamples, dtype=torch.float64, device="cuda")
+            x1 = torch.zeros(c.npix * 3, dtype=torch.float64, device="cuda")
+            x2 = torch.zeros_like(x1)
+            L.bm_pointing_apply_transpose(dev, y, x1)
+            L.bm_pointing_apply_transpose(host, y, x2)
+            assert torch.equal(x1, x2)
+            n = L.bm_inv_noise_create_diag(ctx, c.e.det_offsets, 1.0 / c.e.sigma ** 2)
+            pc1 = L.bm_blockdiag_precond_create(dev, n, 3, 1e3)
+            pc2 = L.bm_blockdiag_precond_create(host, n, 3, 1e3)
+            m1 = torch.zeros(c.npix * 3, dtype=torch.float64, device="cuda")
+            m2 = torch.zeros_like(m1)
+            L.bm_pcg_solve(dev, n, pc1, c.d_tod, 1, m1, 1e-8, 100, L.BM_PREC_MIXED)
+            L.bm_pcg_solve(host, n, pc2, torch.from_numpy(c.tod).pin_memory(), 1, m2, 1e-8, 100, L.BM_PREC_MIXED)
+            assert torch.equal(torch.nan_to_num(m1, 7.0), torch.nan_to_num(m2, 7.0))
+            L.bm_precond_destroy(pc1)
+            L.bm_precond_destroy(pc2)
+            L.bm_inv_noise_destroy(n)
+        finally:
+            L.bm_pointing_destroy(dev)
+            L.bm_pointing_destroy(host)
     finally:
         c.close()
