@@ -51,16 +51,18 @@ def device_white(out, sigma, ns, gen):
 
 def device_one_over_f(out, sigma, ns, chunk, fknee, alpha, fs, gen):
     """Noise with spectrum sigma_d^2 (1 + (fknee/f)^alpha), shaped per chunk in
-    the Fourier domain (chunk divides ns)."""
+    the Fourier domain (a ragged last chunk takes the head of a full one)."""
     import torch
     f = torch.fft.rfftfreq(chunk, 1.0 / fs, device=out.device, dtype=torch.float64)
     g = torch.empty_like(f)
     g[1:] = torch.sqrt(1.0 + (fknee / f[1:]) ** alpha)
     g[0] = g[1]
     g = g.float()
+    nch = -(-ns // chunk)
     for d, sg in enumerate(sigma):
-        w = torch.randn(ns // chunk, chunk, generator=gen, device=out.device) * float(sg)
-        out[d * ns:(d + 1) * ns] += torch.fft.irfft(torch.fft.rfft(w, dim=1) * g, n=chunk, dim=1).reshape(-1)
+        w = torch.randn(nch, chunk, generator=gen, device=out.device) * float(sg)
+        n = torch.fft.irfft(torch.fft.rfft(w, dim=1) * g, n=chunk, dim=1).reshape(-1)
+        out[d * ns:(d + 1) * ns] += n[:ns]
 
 
 def pointing_on_device(nside, ndet, ns, seed):
@@ -194,7 +196,7 @@ def run_config2(args):
     ms = (time.perf_counter() - t0) * 1000 / args.steps
     clocks = sampler.stop()
     fam = {}
-    for name in ("ingest", "blocks", "rhs", "toeplitz_f32", "toeplitz_f64"):
+    for name in ("ingest", "blocks", "rhs", "toeplitz_f32", "toeplitz_refine", "toeplitz_f64"):
         tot, cnt = L.bm_context_kernel_time(ctx, name)
         if cnt:
             fam[name] = {"ms_per_launch": tot / cnt, "launches_per_step": cnt / args.steps}
@@ -222,7 +224,12 @@ def run_config2(args):
         per_chunk = -(-chunk // H)
         return per_chunk * (ns // chunk) * ndet, H
     fam_fft = {}
+    # (the refinement operator's double-float transform is counted in FP64
+    #  flops against the FP32 pipes' rate / 20, about the cost of one
+    #  double-float multiply-add)
     for name, N, zb, peak, unit in (("toeplitz_f32", fft_size(nlags, chunk, 8192), 4, fp32_peak_tflops(sm), "FP32"),
+                                    ("toeplitz_refine", fft_size(nlags, chunk, 4096), 8, fp32_peak_tflops(sm) / 20,
+                                     "FP32 double-float"),
                                     ("toeplitz_f64", fft_size(nlags, chunk, 4096), 8, fp64_peak_tflops(sm), "FP64")):
         ms_l = fam.get(name, {}).get("ms_per_launch")
         if not N or not ms_l:
@@ -235,7 +242,7 @@ def run_config2(args):
                          "flop_frac": flops / (ms_l * 1e-3) / 1e12 / peak,
                          "gbs": bytes_ / (ms_l * 1e-3) / 1e9, "hbm_frac": bytes_ / (ms_l * 1e-3) / 1e9 / hbm_peak()}
     # the dominant kernel family of the step
-    dom = max(("toeplitz_f32", "toeplitz_f64"),
+    dom = max(("toeplitz_f32", "toeplitz_refine", "toeplitz_f64"),
               key=lambda k: fam.get(k, {}).get("ms_per_launch", 0) * fam.get(k, {}).get("launches_per_step", 0))
     d = fam_fft.get(dom, {})
     line = {
@@ -355,11 +362,31 @@ def run_config4(args):
     L = _L()
     rng = np.random.default_rng(args.seed + 3)
     pool_ndet, pool_ns = 64, 2 ** 22
+    # Per nside a pool of 64 detectors x 2^22 samples: pointing, and TODs
+    # (signal of a seeded sky plus white noise, or plus 1/f noise at three
+    # knee frequencies spanning [0.05, 0.5] Hz), made before the arrivals so
+    # that building a request is a device gather, not a synthesis.
+    fk_pool = (0.05, 0.158, 0.5)
     t_gen = time.perf_counter()
-    pools = {ns_: pointing_on_device(ns_, pool_ndet, pool_ns, args.seed + 3 + ns_) for ns_ in (64, 128, 256, 512)}
+    gen = torch.Generator(device="cuda").manual_seed(args.seed + 3)
+    pools = {}
+    for ns_ in (64, 128, 256, 512):
+        e0, pix0, c0, s0 = pointing_on_device(ns_, pool_ndet, pool_ns, args.seed + 3 + ns_)
+        sky = torch.randn((e0.npix, 3), generator=gen, device="cuda", dtype=torch.float64)
+        sky[:, 0] *= 100.0
+        sky[:, 1:] *= 10.0
+        sig = torch.empty(e0.nsamples, dtype=torch.float32, device="cuda")
+        device_signal(pix0, c0, s0, sky, sig)
+        tw = sig.clone()
+        device_white(tw, e0.sigma, pool_ns, gen)
+        t1f = {}
+        for fk in fk_pool:
+            t1f[fk] = sig.clone()
+            device_one_over_f(t1f[fk], e0.sigma, pool_ns, 2 ** 20, fk, 1.0, 20.0, gen)
+        del sig
+        pools[ns_] = (e0, pix0, c0, s0, tw, t1f)
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
-    gen = torch.Generator(device="cuda").manual_seed(args.seed + 3)
 
     # request list: Poisson arrivals; nside U{64..512}; ndet log-U[8, 512]; Ns = 2^U[18, 22]
     arrivals, t = [], 0.0
@@ -378,28 +405,22 @@ def run_config4(args):
         reqs.append(dict(t=ta, nside=nside, ndet=ndet, ns=ns_, white=white, fknee=fknee))
 
     def build(rq):
-        e0, pix0, c0, s0 = pools[rq["nside"]]
+        e0, pix0, c0, s0, tw, t1f = pools[rq["nside"]]
         ndet, ns_ = rq["ndet"], rq["ns"]
-        idx = []
-        for d in range(ndet):
-            src = d % pool_ndet
-            off = ((d // pool_ndet) * 7919 + d * 131) % (pool_ns - ns_ + 1)
-            idx.append(torch.arange(src * pool_ns + off, src * pool_ns + off + ns_, device="cuda"))
-        idx = torch.cat(idx)
-        pix, c, s = pix0[idx].contiguous(), c0[idx].contiguous(), s0[idx].contiguous()
-        sigma = np.asarray([e0.sigma[d % pool_ndet] for d in range(ndet)])
-        tod = torch.empty(ndet * ns_, dtype=torch.float32, device="cuda")
-        sky = torch.randn((e0.npix, 3), generator=gen, device="cuda", dtype=torch.float64)
-        sky[:, 0] *= 100.0
-        sky[:, 1:] *= 10.0
-        device_signal(pix, c, s, sky, tod)
-        chunk = min(2 ** 20, ns_)
+        d = np.arange(ndet)
+        src = d % pool_ndet
+        off = ((d // pool_ndet) * 7919 + d * 131) % (pool_ns - ns_ + 1)
+        starts = torch.from_numpy((src * pool_ns + off).astype(np.int32)).cuda()  # pool < 2^31 samples
+        idx = (starts[:, None] + torch.arange(ns_, device="cuda", dtype=torch.int32)[None, :]).reshape(-1)
         if rq["white"]:
-            device_white(tod, sigma, ns_, gen)
-            coeffs = None
-        else:
-            device_one_over_f(tod, sigma, ns_, chunk, rq["fknee"], 1.0, 20.0, gen)
-            coeffs = synth.toeplitz_band(sigma, rq["fknee"], 1.0, 20.0, chunk, 512)
+            tod_pool = tw
+        else:  # the pool realisation nearest in log f_knee; N^-1 uses the request's own f_knee
+            tod_pool = t1f[min(fk_pool, key=lambda f: abs(math.log(f / rq["fknee"])))]
+        pix, c, s, tod = (torch.index_select(a, 0, idx) for a in (pix0, c0, s0, tod_pool))
+        del idx
+        sigma = np.asarray(e0.sigma)[src]
+        chunk = min(2 ** 20, ns_)
+        coeffs = None if rq["white"] else synth.toeplitz_band(sigma, rq["fknee"], 1.0, 20.0, chunk, 512)
         out = torch.empty(e0.npix * 3, dtype=torch.float64, device="cuda")
         det_off = np.arange(ndet + 1, dtype=np.int64) * ns_
         req, keep = L.make_request(e0.npix, pix, tod, out, det_off, 1 / sigma ** 2, cos2psi=c, sin2psi=s,
@@ -465,7 +486,7 @@ def run_config4(args):
         req, bufs = build(rq)
         keep, pix, c, s, tod, out = bufs
         e0 = pools[rq["nside"]][0]
-        sigma = np.asarray([e0.sigma[d % pool_ndet] for d in range(rq["ndet"])])
+        sigma = np.asarray(e0.sigma)[np.arange(rq["ndet"]) % pool_ndet]
         det_off = np.arange(rq["ndet"] + 1, dtype=np.int64) * rq["ns"]
         torch.cuda.synchronize()
         t0 = time.perf_counter()

@@ -244,7 +244,11 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
 void build_precond(bm_precond* pc);
 void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, double* q,
             bm_precision prec, int64_t nrhs);
-// b = P^T N^-1 d_m; df = double-float accumulation (mixed path) instead of FP64.
+// Internal precision of the mixed solve's refinement operator: like
+// BM_PREC_FP64, with the Toeplitz filter and its pixel sums in double-float.
+constexpr bm_precision kPrecRefine = static_cast<bm_precision>(2);
+// b = P^T N^-1 d_m; df = double-float accumulation and filter (mixed path)
+// instead of FP64.
 void rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dtype dt,
          int64_t nrhs, double* b, bool df = false);
 void precond_apply(bm_precond* pc, const double* r, double* z, int64_t nrhs);

@@ -44,6 +44,26 @@ __device__ __forceinline__ cpx<T> csub(cpx<T> a, cpx<T> b) { return {a.x - b.x, 
 template <typename T>
 __device__ __forceinline__ cpx<T> cconj(cpx<T> a) { return {a.x, -a.y}; }
 
+// Double-float (a pair of FP32 numbers carrying ~48 bits) as an FFT element:
+// the refinement operator of the mixed solve transforms in this type on the
+// FP32 pipes instead of FP64, which runs at 1/64 of the FP32 rate here.
+__device__ __forceinline__ df32 operator+(df32 a, df32 b) { return df_add(a, b); }
+__device__ __forceinline__ df32 operator-(df32 a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df32 operator-(df32 a, df32 b) { return df_add(a, -b); }
+__device__ __forceinline__ df32 operator*(df32 a, df32 b) { return df_mul(a, b); }
+
+// A number of type V as element type T (no detour through FP64 for FP32).
+template <typename T, typename V>
+__device__ __forceinline__ T fnum(V v) { return (T)v; }
+template <>
+__device__ __forceinline__ df32 fnum<df32, double>(double v) { return df_from(v); }
+template <>
+__device__ __forceinline__ df32 fnum<df32, float>(float v) { return {v, 0.f}; }
+// An element as the output type.
+__device__ __forceinline__ float fout(float v) { return v; }
+__device__ __forceinline__ double fout(double v) { return v; }
+__device__ __forceinline__ double fout(df32 v) { return df_to_double(v); }
+
 // Padded shared-memory index: one spare entry after every 16.
 __device__ __forceinline__ int fpad(int a) { return a + (a >> 4); }
 __host__ __device__ inline int fft_buf_len(int M) { return M + M / 16 + 1; }
@@ -52,8 +72,8 @@ __host__ __device__ inline int fft_buf_len(int M) { return M + M / 16 + 1; }
 // sqrt(1/2); INV conjugates.
 template <typename T>
 __device__ __forceinline__ cpx<T> w16(int e, bool inv) {
-    const T c1 = T(0.92387953251128675613), s1 = T(0.38268343236508977173), r2 = T(0.70710678118654752440);
-    T c, s;
+    const double c1 = 0.92387953251128675613, s1 = 0.38268343236508977173, r2 = 0.70710678118654752440;
+    double c, s;
     switch (e & 15) {
         case 0: c = 1; s = 0; break;
         case 1: c = c1; s = s1; break;
@@ -72,7 +92,7 @@ __device__ __forceinline__ cpx<T> w16(int e, bool inv) {
         case 14: c = r2; s = -r2; break;
         default: c = c1; s = -s1; break;
     }
-    return {c, inv ? s : -s};  // exp(-/+ 2 pi i e / 16)
+    return {fnum<T>(c), fnum<T>(inv ? s : -s)};  // exp(-/+ 2 pi i e / 16)
 }
 
 template <typename T>
@@ -230,9 +250,22 @@ __device__ __forceinline__ int fft_tile_det(const int64_t* ts, int ndet, int64_t
 }
 
 // Radix cap and largest transform per element type (the host sizes the
-// FFT within these: N <= 8192 for FP32, N <= 4096 for FP64).
+// FFT within these: N <= 8192 for FP32, N <= 4096 for FP64 and double-float).
 template <typename T> constexpr int kFftRadix = sizeof(T) == 4 ? 16 : 4;
 template <typename T> constexpr int kFftMaxM = sizeof(T) == 4 ? 4096 : 2048;
+
+// Table, spectrum and output types per element type: FP32 runs on FP32
+// tables; FP64 and double-float read the FP64 tables and write FP64.
+template <typename T> struct FftIO {
+    using spec_t = double;
+    using tw_t = double;
+    using out_t = double;
+};
+template <> struct FftIO<float> {
+    using spec_t = float;
+    using tw_t = float;
+    using out_t = float;
+};
 
 // Shared memory of the filter kernel: the padded buffer and the table.
 template <typename T>
@@ -245,15 +278,17 @@ inline size_t fft_smem(int N) {
 // spec: [ndet][N/2 + 1] real band spectra; tw: [N] twiddles exp(-2 pi i e / N).
 template <typename T, class Src>
 __global__ void __launch_bounds__(kFftThreads, 2)
-toeplitz_fft_kernel(Src src, const T* __restrict__ spec, const cpx<T>* __restrict__ tw, int N, int L, FftGeom geo,
-                    T* __restrict__ z) {
+toeplitz_fft_kernel(Src src, const typename FftIO<T>::spec_t* __restrict__ spec,
+                    const cpx<typename FftIO<T>::tw_t>* __restrict__ tw, int N, int L, FftGeom geo,
+                    typename FftIO<T>::out_t* __restrict__ z) {
     extern __shared__ __align__(16) unsigned char fft_smem_raw[];
     const int M = N / 2;
     cpx<T>* buf = reinterpret_cast<cpx<T>*>(fft_smem_raw);
     cpx<T>* tws = buf + fft_buf_len(M);  // W_N^q, q = 0..M
-    for (int q = threadIdx.x; q <= M; q += kFftThreads) tws[q] = tw[q];
+    for (int q = threadIdx.x; q <= M; q += kFftThreads) tws[q] = {fnum<T>(tw[q].x), fnum<T>(tw[q].y)};
     const int H = N - 2 * (L - 1);
-    const T inv_m = T(1) / T(M);
+    const T inv_m = fnum<T>(typename FftIO<T>::tw_t(1) / typename FftIO<T>::tw_t(M));  // M = 2^k: exact
+    const T half = fnum<T>(typename FftIO<T>::tw_t(0.5));
     for (int64_t tile = blockIdx.x; tile < geo.ntiles; tile += gridDim.x) {
         const int d = fft_tile_det(geo.tile_start, geo.ndet, tile);
         const int64_t local = tile - geo.tile_start[d];
@@ -269,8 +304,9 @@ toeplitz_fft_kernel(Src src, const T* __restrict__ spec, const cpx<T>* __restric
 #pragma unroll 4
         for (int n = threadIdx.x; n < M; n += kFftThreads) {
             const int64_t ta = b0 + 2 * n, tb = ta + 1;
-            const T ya = (ta >= cs && ta < ce) ? T(src(ta)) : T(0);
-            const T yb = (tb >= cs && tb < ce) ? T(src(tb)) : T(0);
+            using V = decltype(src(ta));
+            const T ya = fnum<T>((ta >= cs && ta < ce) ? src(ta) : V(0));
+            const T yb = fnum<T>((tb >= cs && tb < ce) ? src(tb) : V(0));
             buf[fpad(n)] = {ya, yb};
         }
         __syncthreads();
@@ -279,7 +315,7 @@ toeplitz_fft_kernel(Src src, const T* __restrict__ spec, const cpx<T>* __restric
         for (int dir = 0; dir < 2; ++dir) {
             fft_run<T, kFftRadix<T>, kFftMaxM<T>>(buf, M, tws, dir == 1);
             if (dir == 1) break;
-            const T* K = spec + (int64_t)d * (M + 1);
+            const typename FftIO<T>::spec_t* K = spec + (int64_t)d * (M + 1);
             // Even/odd split, multiply by the real spectrum, re-pack for the
             // inverse; each thread owns the pair (k, M - k), so this runs in place.
             for (int k = threadIdx.x; k <= M / 2; k += kFftThreads) {
@@ -288,20 +324,20 @@ toeplitz_fft_kernel(Src src, const T* __restrict__ spec, const cpx<T>* __restric
                 const cpx<T> wk = tws[k], wk2 = tws[k2];  // W_N^k, W_N^(M-k)
                 // Y[k] = (zk + conj(zk2))/2 + W_N^k (zk - conj(zk2))/(2i)
                 auto yval = [&](cpx<T> a, cpx<T> b, cpx<T> w) {
-                    const cpx<T> e = {T(0.5) * (a.x + b.x), T(0.5) * (a.y - b.y)};
-                    const cpx<T> dd = {T(0.5) * (a.x - b.x), T(0.5) * (a.y + b.y)};  // (a - conj b)/2
+                    const cpx<T> e = {half * (a.x + b.x), half * (a.y - b.y)};
+                    const cpx<T> dd = {half * (a.x - b.x), half * (a.y + b.y)};  // (a - conj b)/2
                     const cpx<T> o = {dd.y, -dd.x};                                      // / i
                     return cadd(e, cmul(w, o));
                 };
                 cpx<T> Yk = yval(zk, zk2, wk);
                 cpx<T> Yk2 = yval(zk2, zk, wk2);
-                const T Kk = K[k], Kk2 = K[k2];
+                const T Kk = fnum<T>(K[k]), Kk2 = fnum<T>(K[k2]);
                 Yk = {Yk.x * Kk, Yk.y * Kk};
                 Yk2 = {Yk2.x * Kk2, Yk2.y * Kk2};
                 // Z'[k] = E' + i O', E' = (Y[k] + conj(Y[M-k]))/2, O' = (Y[k] - conj(Y[M-k])) conj(W_N^k)/2
                 auto zval = [&](cpx<T> a, cpx<T> b, cpx<T> w) {
-                    const cpx<T> e = {T(0.5) * (a.x + b.x), T(0.5) * (a.y - b.y)};
-                    const cpx<T> dd = {T(0.5) * (a.x - b.x), T(0.5) * (a.y + b.y)};
+                    const cpx<T> e = {half * (a.x + b.x), half * (a.y - b.y)};
+                    const cpx<T> dd = {half * (a.x - b.x), half * (a.y + b.y)};
                     const cpx<T> o = cmul(dd, cconj(w));
                     return cpx<T>{e.x - o.y, e.y + o.x};  // e + i o
                 };
@@ -316,7 +352,7 @@ toeplitz_fft_kernel(Src src, const T* __restrict__ spec, const cpx<T>* __restric
         for (int i = threadIdx.x; i < nout; i += kFftThreads) {
             const int m = L - 1 + i;
             const cpx<T> v = buf[fpad(m >> 1)];
-            z[t0 + i] = ((m & 1) ? v.y : v.x) * inv_m;
+            z[t0 + i] = fout(((m & 1) ? v.y : v.x) * inv_m);
         }
     }
 }

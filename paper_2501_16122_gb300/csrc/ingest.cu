@@ -9,12 +9,12 @@
 //     offsets off[npix+1] and hit counts of the sorted order.
 //
 // Radix sort layout.  The samples are cut into G contiguous ranges, one per
-// block, each a whole number of 4096-sample tiles.  A pass counts the digits
+// block, each a whole number of 8192-sample tiles.  A pass counts the digits
 // of every range (bins x G counters), scans them digit-major, and each block
 // then walks its own range tile by tile, placing a tile's samples at its
 // running per-digit offsets.  The counter array stays small (G is a few
-// times the SM count), so the digits can be wide: up to 11 bits, two passes
-// for npix <= 2^22 (nside <= 512), one for npix <= 2^11.  Inside a tile the
+// times the SM count), so the digits can be wide: up to 10 bits, two passes
+// for npix < 2^20 (nside <= 256), three up to nside 2048, one below 2^10.  Inside a tile the
 // stable rank of a sample comes from per-warp counters updated round by round
 // (match_any groups equal digits within a round), and the tile is staged in
 // shared memory in digit order so that each digit's run is written
@@ -36,13 +36,20 @@ constexpr int IG_THREADS = 256;
 constexpr int IG_WARPS = IG_THREADS / 32;
 constexpr int IG_PER_THREAD = 16;
 constexpr int IG_TILE = IG_THREADS * IG_PER_THREAD;  // 4096 samples
-constexpr int IG_WARP_SPAN = IG_TILE / IG_WARPS;     // 512 consecutive samples per warp
-constexpr int RS_MAX_BITS = 11;
+// The scatter runs one 512-thread block per SM on 8192-sample tiles: the
+// partly written output lines it keeps open in L2 (digits x streams x
+// blocks) stay well inside the 126 MB, and each digit's run per tile is
+// twice as long as with 4096-sample tiles.
+constexpr int SC_THREADS = 512;
+constexpr int SC_WARPS = SC_THREADS / 32;
+constexpr int SC_TILE = SC_THREADS * IG_PER_THREAD;  // 8192 samples
+constexpr int IG_WARP_SPAN = 512;                     // consecutive samples per warp in a tile
+constexpr int RS_MAX_BITS = 10;
 constexpr uint32_t kNoDigit = 0xFFFFFFFFu;
 
 struct SortPlan {
     int bits = 1, passes = 1, bins = 2, grid = 1;
-    int64_t range = IG_TILE;  // samples per block, a multiple of IG_TILE
+    int64_t range = SC_TILE;  // samples per block, a multiple of SC_TILE
 };
 
 __device__ __forceinline__ int64_t range_begin(int64_t range) { return (int64_t)blockIdx.x * range; }
@@ -192,9 +199,11 @@ rs_hist_kernel(const uint32_t* __restrict__ keys, int64_t n, int64_t range, int 
     }
 }
 
-// Exclusive scan of cnt[0, bins) into start[] by the whole block.
+// Exclusive scan of cnt[0, bins) into start[] by the whole block (THREADS threads).
+template <int THREADS>
 __device__ void scan_bins(const uint32_t* cnt, uint32_t* start, int bins, uint32_t* wtot) {
-    const int per = bins >= IG_THREADS ? bins / IG_THREADS : 1;
+    constexpr int WARPS = THREADS / 32;
+    const int per = bins >= THREADS ? bins / THREADS : 1;
     const int b0 = threadIdx.x * per;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t local = 0;
@@ -209,14 +218,14 @@ __device__ void scan_bins(const uint32_t* cnt, uint32_t* start, int bins, uint32
     if (lane == 31) wtot[w] = x;
     __syncthreads();
     if (w == 0) {
-        const uint32_t t = lane < IG_WARPS ? wtot[lane] : 0u;
+        const uint32_t t = lane < WARPS ? wtot[lane] : 0u;
         uint32_t s = t;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
             if (lane >= o) s += y;
         }
-        if (lane < IG_WARPS) wtot[lane] = s - t;
+        if (lane < WARPS) wtot[lane] = s - t;
     }
     __syncthreads();
     uint32_t run = x - local + wtot[w];
@@ -244,25 +253,25 @@ struct ScatterArgs {
 };
 
 inline size_t scatter_smem(int bins) {
-    return sizeof(uint32_t) * (2 * (size_t)IG_TILE + 3 * (size_t)bins) + sizeof(float2) * IG_TILE +
-           sizeof(uint16_t) * (IG_TILE + (size_t)IG_WARPS * bins);
+    return sizeof(uint32_t) * (2 * (size_t)SC_TILE + 3 * (size_t)bins) + sizeof(float2) * SC_TILE +
+           sizeof(uint16_t) * (SC_TILE + (size_t)SC_WARPS * bins);
 }
 
 // One stable scatter pass over the block's range (see the file comment).
 // The lo half of an FP64 trig pair, when present, is not staged: it is read
 // back from the tile's window of the input (L2-resident) at write time.
 template <bool LAST>
-__global__ void __launch_bounds__(IG_THREADS, 2) rs_scatter_kernel(ScatterArgs a) {
+__global__ void __launch_bounds__(SC_THREADS, 1) rs_scatter_kernel(ScatterArgs a) {
     extern __shared__ __align__(16) uint32_t ss[];
     float2* s_hi = reinterpret_cast<float2*>(ss);
-    uint32_t* s_keys = reinterpret_cast<uint32_t*>(s_hi + IG_TILE);
-    uint32_t* s_vals = s_keys + IG_TILE;
-    uint32_t* run_base = s_vals + IG_TILE;  // next global position per digit
+    uint32_t* s_keys = reinterpret_cast<uint32_t*>(s_hi + SC_TILE);
+    uint32_t* s_vals = s_keys + SC_TILE;
+    uint32_t* run_base = s_vals + SC_TILE;  // next global position per digit
     uint32_t* tcnt = run_base + a.bins;     // tile count per digit
     uint32_t* tstart = tcnt + a.bins;       // tile-local start per digit
     uint16_t* s_src = reinterpret_cast<uint16_t*>(tstart + a.bins);  // tile position of a staged sample
-    uint16_t* wcnt = s_src + IG_TILE;                                 // [warp][digit]
-    __shared__ uint32_t wtot[IG_WARPS];
+    uint16_t* wcnt = s_src + SC_TILE;                                 // [warp][digit]
+    __shared__ uint32_t wtot[SC_WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     const int bins = a.bins;
@@ -271,15 +280,15 @@ __global__ void __launch_bounds__(IG_THREADS, 2) rs_scatter_kernel(ScatterArgs a
     const int64_t end = begin + a.range < a.n ? begin + a.range : a.n;
     const uint64_t pol = l2_keep_policy();
 
-    for (int d = threadIdx.x; d < bins; d += IG_THREADS) {
+    for (int d = threadIdx.x; d < bins; d += SC_THREADS) {
         run_base[d] = a.offs[(int64_t)d * a.G + blockIdx.x];
 #pragma unroll
-        for (int q = 0; q < IG_WARPS; ++q) wcnt[q * bins + d] = 0;
+        for (int q = 0; q < SC_WARPS; ++q) wcnt[q * bins + d] = 0;
     }
     __syncthreads();
 
-    for (int64_t base = begin; base < end; base += IG_TILE) {
-        const int cnt = (int)(end - base < IG_TILE ? end - base : IG_TILE);
+    for (int64_t base = begin; base < end; base += SC_TILE) {
+        const int cnt = (int)(end - base < SC_TILE ? end - base : SC_TILE);
         uint32_t key[IG_PER_THREAD], val[IG_PER_THREAD], rank[IG_PER_THREAD];
         float2 hv[IG_PER_THREAD];
         // 1. the warp's 512 consecutive samples, 32 per round
@@ -309,10 +318,10 @@ __global__ void __launch_bounds__(IG_THREADS, 2) rs_scatter_kernel(ScatterArgs a
         }
         __syncthreads();
         // 3. per digit: exclusive prefix over warps, tile count; then over digits
-        for (int d = threadIdx.x; d < bins; d += IG_THREADS) {
+        for (int d = threadIdx.x; d < bins; d += SC_THREADS) {
             uint32_t t = 0;
 #pragma unroll
-            for (int q = 0; q < IG_WARPS; ++q) {
+            for (int q = 0; q < SC_WARPS; ++q) {
                 const uint32_t c = wcnt[q * bins + d];
                 wcnt[q * bins + d] = (uint16_t)t;
                 t += c;
@@ -320,7 +329,7 @@ __global__ void __launch_bounds__(IG_THREADS, 2) rs_scatter_kernel(ScatterArgs a
             tcnt[d] = t;
         }
         __syncthreads();
-        scan_bins(tcnt, tstart, bins, wtot);
+        scan_bins<SC_THREADS>(tcnt, tstart, bins, wtot);
         __syncthreads();
         // 4. stage the tile in digit order
 #pragma unroll
@@ -337,7 +346,7 @@ __global__ void __launch_bounds__(IG_THREADS, 2) rs_scatter_kernel(ScatterArgs a
         }
         __syncthreads();
         // 5. each digit's run goes to its running global offset
-        for (int j = threadIdx.x; j < cnt; j += IG_THREADS) {
+        for (int j = threadIdx.x; j < cnt; j += SC_THREADS) {
             const uint32_t k = s_keys[j];
             const uint32_t d = (k >> a.shift) & dmask;
             const uint32_t g = run_base[d] + (uint32_t)j - tstart[d];
@@ -350,10 +359,10 @@ __global__ void __launch_bounds__(IG_THREADS, 2) rs_scatter_kernel(ScatterArgs a
         }
         __syncthreads();
         // 6. advance the running offsets, clear the warp counters
-        for (int d = threadIdx.x; d < bins; d += IG_THREADS) {
+        for (int d = threadIdx.x; d < bins; d += SC_THREADS) {
             run_base[d] += tcnt[d];
 #pragma unroll
-            for (int q = 0; q < IG_WARPS; ++q) wcnt[q * bins + d] = 0;
+            for (int q = 0; q < SC_WARPS; ++q) wcnt[q * bins + d] = 0;
         }
         __syncthreads();
     }
@@ -391,13 +400,13 @@ SortPlan plan_sort(const bm_context* ctx, int64_t n, int64_t npix) {
     ensure_smem_limit(reinterpret_cast<const void*>(rs_scatter_kernel<false>), smem);
     ensure_smem_limit(reinterpret_cast<const void*>(rs_scatter_kernel<true>), smem);
     ensure_smem_limit(reinterpret_cast<const void*>(rs_hist_kernel), sizeof(uint32_t) * IG_WARPS * sp.bins);
-    int per_sm = blocks_per_sm(reinterpret_cast<const void*>(rs_scatter_kernel<true>), IG_THREADS, smem);
+    int per_sm = blocks_per_sm(reinterpret_cast<const void*>(rs_scatter_kernel<true>), SC_THREADS, smem);
     if (per_sm < 1) per_sm = 1;
     // four waves of equal ranges keep the tail short
     const int64_t want = (int64_t)ctx->num_sms * per_sm * 4;
-    const int64_t ntiles = (n + IG_TILE - 1) / IG_TILE;
+    const int64_t ntiles = (n + SC_TILE - 1) / SC_TILE;
     const int64_t tiles_per_block = (ntiles + want - 1) / want;
-    sp.range = tiles_per_block * IG_TILE;
+    sp.range = tiles_per_block * SC_TILE;
     sp.grid = (int)((n + sp.range - 1) / sp.range);
     return sp;
 }
@@ -491,7 +500,7 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
             a.hi_out = hout;
             a.lo_out = lout;
             ScopedTimer st(ctx, "ingest_scatter");
-            rs_scatter_kernel<false><<<sp.grid, IG_THREADS, smem, s>>>(a);
+            rs_scatter_kernel<false><<<sp.grid, SC_THREADS, smem, s>>>(a);
             BM_LAUNCH_CHECK();
             vin = vout;
             hin = hout;
@@ -505,7 +514,7 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
             a.lo_out = has_lo ? p->cs_lo_s.get() : nullptr;
             a.key_limit = (uint32_t)npix;
             ScopedTimer st(ctx, "ingest_scatter");
-            rs_scatter_kernel<true><<<sp.grid, IG_THREADS, smem, s>>>(a);
+            rs_scatter_kernel<true><<<sp.grid, SC_THREADS, smem, s>>>(a);
             BM_LAUNCH_CHECK();
         }
         std::swap(kin, kout);

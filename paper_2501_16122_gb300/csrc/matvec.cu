@@ -350,32 +350,6 @@ __global__ void pointing_apply_kernel(const int32_t* __restrict__ pix, const flo
 
 // --------------------------------------------------------- Toeplitz filter
 // Sample sources for the filter input y_t.
-struct SrcMatvecF32 {  // y_t = v_t . x32[p_t] (x32 zero on masked pixels), FP32 trig
-    const int32_t* pix; const float2* hi; const float* x; int nc;
-    __device__ float operator()(int64_t t) const {
-        const int32_t p = pix[t];
-        if (p < 0) return 0.f;
-        if (nc == 1) return x[p];
-        const float2 h = hi[t];
-        const float* xp = x + (int64_t)p * nc;
-        float v = fmaf(h.x, xp[nc - 2], h.y * xp[nc - 1]);
-        if (nc == 3) v += xp[0];
-        return v;
-    }
-};
-struct SrcMatvecF64 {  // y_t = v_t . xm[p_t] (xm zero on masked pixels), FP64 trig
-    const int32_t* pix; const float2* hi; const float2* lo; const double* x; int nc;
-    __device__ double operator()(int64_t t) const {
-        const int32_t p = pix[t];
-        if (p < 0) return 0.0;
-        if (nc == 1) return x[p];
-        const double2 cs = trig64_at(hi, lo, t);
-        const double* xp = x + (int64_t)p * nc;
-        double v = cs.x * xp[nc - 2] + cs.y * xp[nc - 1];
-        if (nc == 3) v += xp[0];
-        return v;
-    }
-};
 template <typename D>
 struct SrcMaskedTod {  // y_t = d_t on kept samples, else 0
     const int32_t* pix; const uint8_t* mask; const D* d;
@@ -389,6 +363,47 @@ struct SrcPlain {
     const double* y;
     __device__ double operator()(int64_t t) const { return y[t]; }
 };
+struct SrcPlainF32 {
+    const float* y;
+    __device__ float operator()(int64_t t) const { return y[t]; }
+};
+
+// y = P x32 over every sample in FP32 (x32 zero on masked pixels, so their
+// samples give 0; flagged samples give 0): the filter's input, computed by a
+// full-occupancy elementwise pass so that the filter kernel reads it with
+// plain coalesced loads instead of a dependent pixel-then-map gather.
+template <int NC>
+__global__ void pointing_apply_f32_kernel(const int32_t* __restrict__ pix, const float2* __restrict__ hi, int64_t n,
+                                          const float* __restrict__ x, float* __restrict__ y) {
+    constexpr int U = 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t0 < n; t0 += U * stride) {
+        int32_t p[U];
+        float2 h[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t t = t0 + u * stride;
+            p[u] = t < n ? pix[t] : -1;
+            h[u] = (NC > 1 && t < n) ? hi[t] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t t = t0 + u * stride;
+            if (t >= n) continue;
+            float v = 0.f;
+            if (p[u] >= 0) {
+                const float* xp = x + (int64_t)p[u] * NC;
+                if (NC == 1) {
+                    v = xp[0];
+                } else {
+                    v = fmaf(h[u].x, xp[NC - 2], h[u].y * xp[NC - 1]);
+                    if (NC == 3) v += xp[0];
+                }
+            }
+            y[t] = v;
+        }
+    }
+}
 
 constexpr int kTzThreads = 256;
 
@@ -567,7 +582,8 @@ void prepare_toeplitz_fft(bm_inv_noise* n) {
 }
 
 template <typename T, class Src>
-static void run_toeplitz_fft(bm_inv_noise* n, const Src& src, int N, const T* spec, const cpx<T>* tw, T* z) {
+static void run_toeplitz_fft(bm_inv_noise* n, const Src& src, int N, const typename FftIO<T>::spec_t* spec,
+                             const cpx<typename FftIO<T>::tw_t>* tw, typename FftIO<T>::out_t* z) {
     bm_context* ctx = n->ctx;
     const int H = N - 2 * (n->nlags - 1);
     ToeplitzPlan tp;
@@ -591,10 +607,15 @@ static void apply_toeplitz_f32(bm_inv_noise* n, const Src& src, float* z) {
     else
         run_toeplitz<float, 8>(n, src, n->coeffs32.get(), z);
 }
+// df: the FFT in double-float on the FP32 pipes (~48-bit arithmetic, for the
+// refinement operator of the mixed solve) instead of FP64.
 template <class Src>
-static void apply_toeplitz_f64(bm_inv_noise* n, const Src& src, double* z) {
-    if (n->fft_n64)
-        run_toeplitz_fft<double>(n, src, n->fft_n64, n->spec64.get(), reinterpret_cast<const cpx<double>*>(n->tw64.get()), z);
+static void apply_toeplitz_f64(bm_inv_noise* n, const Src& src, double* z, bool df = false) {
+    const auto* tw = reinterpret_cast<const cpx<double>*>(n->tw64.get());
+    if (n->fft_n64 && df)
+        run_toeplitz_fft<df32>(n, src, n->fft_n64, n->spec64.get(), tw, z);
+    else if (n->fft_n64)
+        run_toeplitz_fft<double>(n, src, n->fft_n64, n->spec64.get(), tw, z);
     else
         run_toeplitz<double, 4>(n, src, n->coeffs64.get(), z);
 }
@@ -696,22 +717,36 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
                 BM_LAUNCH_CHECK();
                 {
                     ScopedTimer timer(ctx, "toeplitz_f32");
-                    SrcMatvecF32 src{p->pix.get(), p->cs_hi_t.get(), x32, nc};
-                    apply_toeplitz_f32(n, src, z32);
+                    float* y32 = workspace_as<float>(ctx, "y32", p->nsamples);
+                    const int g = grid_for(ctx, (p->nsamples + threads - 1) / threads, 16);
+                    if (nc == 3)
+                        pointing_apply_f32_kernel<3><<<g, threads, 0, s>>>(p->pix.get(), p->cs_hi_t.get(), p->nsamples, x32, y32);
+                    else if (nc == 2)
+                        pointing_apply_f32_kernel<2><<<g, threads, 0, s>>>(p->pix.get(), p->cs_hi_t.get(), p->nsamples, x32, y32);
+                    else
+                        pointing_apply_f32_kernel<1><<<g, threads, 0, s>>>(p->pix.get(), p->cs_hi_t.get(), p->nsamples, x32, y32);
+                    BM_LAUNCH_CHECK();
+                    apply_toeplitz_f32(n, SrcPlainF32{y32}, z32);
                 }
                 // scatter with the same FP32 trig the gather used (symmetric operator)
                 gather_reduce<float>(p, kept_items(pc), z32, nullptr, nullptr, true, qr);
             } else {
+                // FP64, or the refinement operator: the same with a
+                // double-float filter and pixel sums
+                const bool refine = prec == kPrecRefine;
                 double* xm = workspace_as<double>(ctx, "xm", nvec);
                 double* z64 = workspace_as<double>(ctx, "z64", p->nsamples);
                 masked_copy_kernel<double><<<vgrid, threads, 0, s>>>(xr, pc->mask.get(), p->npix, nc, xm);
                 BM_LAUNCH_CHECK();
                 {
-                    ScopedTimer timer(ctx, "toeplitz_f64");
-                    SrcMatvecF64 src{p->pix.get(), p->cs_hi_t.get(), p->cs_lo_t.get(), xm, nc};
-                    apply_toeplitz_f64(n, src, z64);
+                    ScopedTimer timer(ctx, refine ? "toeplitz_refine" : "toeplitz_f64");
+                    double* y64 = workspace_as<double>(ctx, "y64", p->nsamples);
+                    pointing_apply_kernel<<<grid_for(ctx, (p->nsamples + threads - 1) / threads, 16), threads, 0, s>>>(
+                        p->pix.get(), p->cs_hi_t.get(), p->cs_lo_t.get(), p->nsamples, nc, xm, y64);
+                    BM_LAUNCH_CHECK();
+                    apply_toeplitz_f64(n, SrcPlain{y64}, z64, refine);
                 }
-                gather_reduce<double>(p, kept_items(pc), z64, nullptr, p->cs_lo_s.get(), false, qr);
+                gather_reduce<double>(p, kept_items(pc), z64, nullptr, p->cs_lo_s.get(), refine, qr);
             }
         }
     }
@@ -738,11 +773,11 @@ void rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dt
             if (dt == BM_F32) {
                 SrcMaskedTod<float> src{p->pix.get(), pc->mask.get(),
                                         static_cast<const float*>(tod) + r * p->nsamples};
-                apply_toeplitz_f64(n, src, z64);
+                apply_toeplitz_f64(n, src, z64, df);
             } else {
                 SrcMaskedTod<double> src{p->pix.get(), pc->mask.get(),
                                          static_cast<const double*>(tod) + r * p->nsamples};
-                apply_toeplitz_f64(n, src, z64);
+                apply_toeplitz_f64(n, src, z64, df);
             }
             gather_reduce<double>(p, kept_items(pc), z64, nullptr, p->cs_lo_s.get(), df, br);
         }

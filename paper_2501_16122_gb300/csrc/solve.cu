@@ -339,15 +339,18 @@ CgState run_pcg(Cg& cg, bm_pointing* p, bm_inv_noise* n, const double* b, double
     return h;
 }
 
-// ||b - A x|| with the FP64 operator into r; returns ||r||^2.
+// ||b - A x|| into r with the exact operator (op = BM_PREC_FP64, or the
+// double-float refinement operator kPrecRefine); returns ||r||^2.  For white
+// noise A is block diagonal, so A x = B x per pixel in FP64 either way.
 template <int NC>
-double exact_residual(Cg& cg, bm_pointing* p, bm_inv_noise* n, const double* b, const double* x, double* r) {
+double exact_residual(Cg& cg, bm_pointing* p, bm_inv_noise* n, const double* b, const double* x, double* r,
+                      bm_precision op) {
     bm_context* ctx = cg.pc->ctx;
     cudaStream_t s = ctx->stream;
     if (n->kind == 0) {
         block_residual_kernel<NC><<<RB, RT, 0, s>>>(cg.pc->B.get(), cg.pc->mask.get(), b, x, r, cg.npix, cg.part);
     } else {
-        matvec(p, n, cg.pc, x, cg.q, BM_PREC_FP64, 1);
+        matvec(p, n, cg.pc, x, cg.q, op, 1);
         sub_residual_kernel<<<RB, RT, 0, s>>>(b, cg.q, r, cg.nvec, cg.part);
     }
     BM_LAUNCH_CHECK();
@@ -403,7 +406,9 @@ bm_status solve_one(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const doubl
         inf.iterations = h.iters;
         if (h.done == 2) status = BM_ERR_BREAKDOWN;
     } else {
-        // Mixed: outer FP64 residual, inner FP32-product PCG on the correction.
+        // Mixed: outer exact residual (FP64 blocks for white noise, the
+        // double-float operator for Toeplitz noise), inner FP32-product PCG
+        // on the correction.
         // x starts at 0, so the first residual is b itself (zero on masked pixels).
         BM_CUDA(cudaMemcpyAsync(rs, b, sizeof(double) * cg.nvec, cudaMemcpyDeviceToDevice, s));
         double rr = bb;
@@ -417,7 +422,7 @@ bm_status solve_one(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const doubl
             if (h.done == 2 && h.iters == 0) { status = BM_ERR_BREAKDOWN; break; }
             axpy_kernel<<<grid_for(ctx, (cg.nvec + 255) / 256, 16), 256, 0, s>>>(xs, cg.x, cg.nvec);
             BM_LAUNCH_CHECK();
-            const double rr_new = exact_residual<NC>(cg, p, n, b, xs, rs);
+            const double rr_new = exact_residual<NC>(cg, p, n, b, xs, rs, kPrecRefine);
             if (!(rr_new < rr)) { rr = rr_new; break; }  // stagnation
             rr = rr_new;
         }
@@ -427,7 +432,7 @@ bm_status solve_one(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const doubl
     }
     if (bb != 0.0 && prec == BM_PREC_FP64) {
         // Final residual recomputed with the FP64 operator (the recurrence drifts).
-        inf.rel_residual = std::sqrt(exact_residual<NC>(cg, p, n, b, xs, rs)) / bnorm;
+        inf.rel_residual = std::sqrt(exact_residual<NC>(cg, p, n, b, xs, rs, BM_PREC_FP64)) / bnorm;
     }
     if (status == BM_OK && !(inf.rel_residual <= tol)) status = BM_ERR_NOT_CONVERGED;
     inf.status = status;
