@@ -166,7 +166,12 @@ CPU_SAMPLE = dict(ndet=8, ns=2 ** 19)  # 4.2M samples of the same scan: ~10 s of
 KERNELS = {"ingest_validate": "validate_kernel", "ingest_hist": "rs_hist_kernel",
            "ingest_scatter": "rs_scatter_kernel", "blocks": "blocks_kernel", "rhs": "gather_reduce_kernel",
            "matvec_white_f32": "white_matvec_f32_kernel"}
-TRAFFIC = {}
+TRAFFIC = {
+    # profiles/ingest_sort_nside256_256x262144.md: 29.0 and 31.3 DRAM bytes per
+    # sample for the two scatter passes (mean 30.15), 67M-sample case; the
+    # traffic grows in proportion to the samples
+    "ingest_scatter": lambda n: 30.15 * n,
+}
 
 
 def n_valid_kept(hits, kept):
@@ -316,17 +321,19 @@ def run_gb300(args, rank, world, local_rank):
     nbits = 1
     while (1 << nbits) <= e.npix:
         nbits += 1
-    passes = -(-nbits // 11)
+    passes = -(-nbits // 10)
     n_valid = int(hits.sum().item())
     scatter_bytes = 0
+    hist_bytes = 0
     for ps in range(passes):
         last = ps == passes - 1
-        rd = 4 + (4 if ps > 0 else 0) + 8                  # keys, sample indices, trig pair
-        wr = (4 + 12 * n_valid / nt) if last else 16       # keys (+ perm and trig of kept samples)
+        rd = 16 if ps > 0 else 12                          # 16-byte records, or key + trig pair in time order
+        wr = (12 * n_valid / nt) if last else 16           # perm + trig of kept samples, or records
         scatter_bytes += (rd + wr) * nt
+        hist_bytes += (16 if ps > 0 else 4) * nt           # keys, read from the records after the first pass
     step_bytes = {
         "ingest_validate": 28 * nt,                       # pix + cos + sin in; pix, key, trig pair out
-        "ingest_hist": 4 * nt * passes,
+        "ingest_hist": hist_bytes,
         "ingest_scatter": scatter_bytes,
         "blocks": 20 * n_valid_kept(hits, kept),          # perm + trig pair in, weighted pair out
         "rhs": 16 * n_valid_kept(hits, kept),             # perm + d + trig pair
@@ -412,8 +419,9 @@ def run_gb300(args, rank, world, local_rank):
             "roofline": ({"bound": "hbm", "achieved": rooflines[dom]["achieved_gbs"], "peak": hbm, "unit": "GB/s",
                           "frac": rooflines[dom]["frac"], "traffic": TRAFFIC.get(dom, lambda n: None)(nt),
                           "kernel": KERNELS[dom], "family": dom, "peak_kind": peak_kind,
-                          "bytes_per_step": rooflines[dom]["bytes_per_step"],
-                          "launches_per_step": fam[dom]["launches"] / args.steps} if dom else None),
+                          "launches_per_step": fam[dom]["launches"] / args.steps,
+                          "bytes_per_launch": rooflines[dom]["bytes_per_step"] / (fam[dom]["launches"] / args.steps),
+                          "ms_per_launch": fam[dom]["ms_per_launch"]} if dom else None),
             "rooflines": rooflines,
             "matvec_roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                                 "frac": achieved / hbm, "kernel": "white_matvec_f32_kernel",

@@ -111,7 +111,7 @@ batched_rhs_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restri
                 tl = perm[b + j];
                 h = hi[b + j];
                 if (lo) l = lo[b + j];
-                wl = wp[find_det32(offp, ndet, tl)];
+                wl = wp[det_of(offp, ndet, dt.ns, dt.inv_ns, tl)];
             }
             const int cnt = min(32, len - base);
             // sample kk of the chunk: its row of the G right-hand sides, added in order
@@ -540,7 +540,7 @@ void launch_rhs_v(bm_context* ctx, bm_pointing* p, bm_inv_noise* n, bm_precond* 
                   int R, double* b, double* partial, bool exact_lo) {
     auto kern = batched_rhs_kernel<NC, T, RPL, 4>;
     const int grid = resident_grid(ctx, kern, 4 * 32, (pc->nitems + 3) / 4);
-    const DetTables dt{n->det_off32.get(), n->wdf.get(), n->wsqrt.get()};
+    const DetTables dt{n->det_off32.get(), n->wdf.get(), n->wsqrt.get(), n->ns_uniform, n->inv_ns};
     kern<<<grid, 4 * 32, 0, ctx->stream>>>(pc->item_pix.get(), pc->item_beg.get(), pc->item_len.get(), pc->nitems,
                                           pc->pitem.get(), p->perm.get(), p->cs_hi_s.get(),
                                           exact_lo ? p->cs_lo_s.get() : nullptr, dT, G, r0, R, dt, n->ndet, b,

@@ -420,6 +420,11 @@ static bm_inv_noise* new_noise(bm_context* ctx, int32_t ndet, const int64_t* det
             wdf[d] = make_float2(h, (float)(white[d] - (double)h));
             wsq[d] = (float)std::sqrt(white[d]);
         }
+        const int64_t len0 = det_offsets[1] - det_offsets[0];
+        bool uniform = det_offsets[0] == 0 && len0 >= 1 && ndet < (1 << 20);
+        for (int d = 1; d < ndet && uniform; ++d) uniform = det_offsets[d + 1] - det_offsets[d] == len0;
+        n->ns_uniform = uniform ? (uint32_t)len0 : 0u;
+        n->inv_ns = uniform ? (float)(1.0 / (double)len0) : 0.f;
         n->det_off32.alloc(ndet + 1);
         n->wdf.alloc(ndet);
         n->wsqrt.alloc(ndet);

@@ -59,6 +59,8 @@ template <>
 __device__ __forceinline__ df32 fnum<df32, double>(double v) { return df_from(v); }
 template <>
 __device__ __forceinline__ df32 fnum<df32, float>(float v) { return {v, 0.f}; }
+template <>
+__device__ __forceinline__ df32 fnum<df32, float2>(float2 v) { return {v.x, v.y}; }
 // An element as the output type.
 __device__ __forceinline__ float fout(float v) { return v; }
 __device__ __forceinline__ double fout(double v) { return v; }
@@ -255,9 +257,16 @@ template <typename T> constexpr int kFftRadix = sizeof(T) == 4 ? 16 : 4;
 template <typename T> constexpr int kFftMaxM = sizeof(T) == 4 ? 4096 : 2048;
 
 // Table, spectrum and output types per element type: FP32 runs on FP32
-// tables; FP64 and double-float read the FP64 tables and write FP64.
+// tables; FP64 reads the FP64 tables; double-float reads its spectrum as
+// (hi, lo) pairs and the FP64 twiddles (converted once per block); both write
+// FP64.
 template <typename T> struct FftIO {
     using spec_t = double;
+    using tw_t = double;
+    using out_t = double;
+};
+template <> struct FftIO<df32> {
+    using spec_t = float2;
     using tw_t = double;
     using out_t = double;
 };
@@ -277,7 +286,7 @@ inline size_t fft_smem(int N) {
 // One block of H = N - 2(L-1) outputs per iteration (grid-stride over blocks).
 // spec: [ndet][N/2 + 1] real band spectra; tw: [N] twiddles exp(-2 pi i e / N).
 template <typename T, class Src>
-__global__ void __launch_bounds__(kFftThreads, 2)
+__global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 3 : 2)
 toeplitz_fft_kernel(Src src, const typename FftIO<T>::spec_t* __restrict__ spec,
                     const cpx<typename FftIO<T>::tw_t>* __restrict__ tw, int N, int L, FftGeom geo,
                     typename FftIO<T>::out_t* __restrict__ z) {
@@ -360,7 +369,8 @@ toeplitz_fft_kernel(Src src, const typename FftIO<T>::spec_t* __restrict__ spec,
 // K[d][k] = c_0 + 2 sum_{j=1}^{L-1} c_j cos(2 pi j k / N), k = 0..N/2, in FP64
 // (the argument reduced exactly with the integer j k mod N).
 __global__ void band_spectrum_kernel(const double* __restrict__ coeffs, int ndet, int L, int N,
-                                     double* __restrict__ spec64, float* __restrict__ spec32) {
+                                     double* __restrict__ spec64, float* __restrict__ spec32,
+                                     float2* __restrict__ spec_df) {
     const int M = N / 2;
     const int64_t total = (int64_t)ndet * (M + 1);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
@@ -375,6 +385,10 @@ __global__ void band_spectrum_kernel(const double* __restrict__ coeffs, int ndet
         const double v = c[0] + 2.0 * s;
         if (spec64) spec64[i] = v;
         if (spec32) spec32[i] = (float)v;
+        if (spec_df) {
+            const float h = (float)v;
+            spec_df[i] = make_float2(h, (float)(v - (double)h));
+        }
     }
 }
 

@@ -24,8 +24,10 @@
 // The trig pairs travel with the keys as payload (each pass reads and writes
 // them once, in tile order): on this part a random 8-byte read moves about
 // 100 bytes of DRAM traffic, so gathering them through perm afterwards would
-// cost several times more.  The CSR offsets come from a binary search per
-// pixel in the sorted keys.
+// cost several times more.  Between passes a sample is one 16-byte record
+// {key, sample index, cos, sin}; the last pass writes only perm and the
+// sorted trig pairs, and the CSR offsets come from a binary search per pixel
+// over pix[perm[i]].
 #include "bm_internal.cuh"
 
 namespace bm {
@@ -149,9 +151,10 @@ __global__ void validate_kernel(const int32_t* __restrict__ pix, const void* __r
 // Each thread counts 16 consecutive keys (vector loads), adding runs of equal
 // digits at once into its warp's own histogram; the warp histograms are
 // summed at the end.
+template <bool REC>
 __global__ void __launch_bounds__(IG_THREADS)
-rs_hist_kernel(const uint32_t* __restrict__ keys, int64_t n, int64_t range, int shift, int bins, int G,
-               uint32_t* __restrict__ hist) {
+rs_hist_kernel(const uint32_t* __restrict__ keys, const uint4* __restrict__ rec, int64_t n, int64_t range,
+               int shift, int bins, int G, uint32_t* __restrict__ hist) {
     extern __shared__ __align__(16) uint32_t hh[];  // [IG_WARPS][bins]
     for (int d = threadIdx.x; d < IG_WARPS * bins; d += IG_THREADS) hh[d] = 0;
     __syncthreads();
@@ -162,7 +165,10 @@ rs_hist_kernel(const uint32_t* __restrict__ keys, int64_t n, int64_t range, int 
     for (int64_t base = begin; base < end; base += IG_TILE) {
         const int64_t i0 = base + (int64_t)threadIdx.x * IG_PER_THREAD;
         uint32_t k[IG_PER_THREAD];
-        if (i0 + IG_PER_THREAD <= end) {
+        if (REC) {
+#pragma unroll
+            for (int r = 0; r < IG_PER_THREAD; ++r) k[r] = i0 + r < end ? __ldcs(rec + i0 + r).x : kNoDigit;
+        } else if (i0 + IG_PER_THREAD <= end) {
             const uint4* v = reinterpret_cast<const uint4*>(keys + i0);  // i0 is a multiple of 16
 #pragma unroll
             for (int q = 0; q < IG_PER_THREAD / 4; ++q) {
@@ -236,20 +242,23 @@ __device__ void scan_bins(const uint32_t* cnt, uint32_t* start, int bins, uint32
         }
 }
 
+// A sample between passes: one 16-byte record {key, sample index, cos, sin}
+// (one store stream instead of three: the scatter's short digit runs then
+// fill whole lines, which measured twice as fast).
 struct ScatterArgs {
-    const uint32_t* keys_in;
-    const uint32_t* vals_in;  // null: the sample index itself (first pass)
-    const float2* hi_in;      // trig payload in the input order of this pass
-    const float2* lo_in;      // null when the trig has no lo part
+    const uint4* rec_in;      // records of the previous pass, or null on the first pass:
+    const uint32_t* keys_in;  //   then keys, the sample index itself and the trig pairs
+    const float2* hi_in;      //   in time order
+    const float2* lo_in;      // lo halves of the trig pairs in this pass's input order, or null
     int64_t n;
     int64_t range;
     int shift, bins, G;
     const uint32_t* offs;  // [bins][G] exclusive digit-major scan of the counts
-    uint32_t* keys_out;
-    uint32_t* vals_out;  // sample indices; the last pass writes perm
+    uint4* rec_out;        // intermediate passes
+    uint32_t* perm_out;    // last pass: sample indices (perm) and trig pairs of the kept samples
     float2* hi_out;
-    float2* lo_out;
-    uint32_t key_limit;  // last pass: samples with keys >= key_limit (flagged) get no perm / trig entry
+    float2* lo_out;        // every pass with lo_in: the lo halves in this pass's output order
+    uint32_t key_limit;    // last pass: samples with keys >= key_limit (flagged) get no entry
 };
 
 inline size_t scatter_smem(int bins) {
@@ -296,9 +305,16 @@ __global__ void __launch_bounds__(SC_THREADS, 1) rs_scatter_kernel(ScatterArgs a
         for (int r = 0; r < IG_PER_THREAD; ++r) {
             const int j = w * IG_WARP_SPAN + r * 32 + lane;
             const bool v = j < cnt;
-            key[r] = v ? __ldcs(a.keys_in + base + j) : 0u;
-            val[r] = v ? (a.vals_in ? __ldcs(a.vals_in + base + j) : (uint32_t)(base + j)) : 0u;
-            hv[r] = v ? __ldcs(a.hi_in + base + j) : make_float2(0.f, 0.f);
+            if (a.rec_in) {
+                const uint4 x = v ? __ldcs(a.rec_in + base + j) : make_uint4(0u, 0u, 0u, 0u);
+                key[r] = x.x;
+                val[r] = x.y;
+                hv[r] = make_float2(__uint_as_float(x.z), __uint_as_float(x.w));
+            } else {
+                key[r] = v ? __ldcs(a.keys_in + base + j) : 0u;
+                val[r] = (uint32_t)(base + j);
+                hv[r] = v ? __ldcs(a.hi_in + base + j) : make_float2(0.f, 0.f);
+            }
         }
         // 2. stable rank within the warp: counters advance round by round
 #pragma unroll
@@ -350,9 +366,12 @@ __global__ void __launch_bounds__(SC_THREADS, 1) rs_scatter_kernel(ScatterArgs a
             const uint32_t k = s_keys[j];
             const uint32_t d = (k >> a.shift) & dmask;
             const uint32_t g = run_base[d] + (uint32_t)j - tstart[d];
-            st_keep(a.keys_out + g, k, pol);
-            if (!LAST || k < a.key_limit) {
-                st_keep(a.vals_out + g, s_vals[j], pol);
+            if (!LAST) {
+                const float2 h = s_hi[j];
+                a.rec_out[g] = make_uint4(k, s_vals[j], __float_as_uint(h.x), __float_as_uint(h.y));
+                if (a.lo_in) st_keep(a.lo_out + g, a.lo_in[base + s_src[j]], pol);
+            } else if (k < a.key_limit) {
+                st_keep(a.perm_out + g, s_vals[j], pol);
                 st_keep(a.hi_out + g, s_hi[j], pol);
                 if (a.lo_in) st_keep(a.lo_out + g, a.lo_in[base + s_src[j]], pol);
             }
@@ -368,15 +387,17 @@ __global__ void __launch_bounds__(SC_THREADS, 1) rs_scatter_kernel(ScatterArgs a
     }
 }
 
-// off[p] = first sorted index whose key >= p, for p in [0, npix].
-__global__ void lower_bound_kernel(const uint32_t* __restrict__ keys, int64_t n, int64_t npix,
-                                   int64_t* __restrict__ off) {
+// off[p] = first sorted position whose pixel is >= p, for p in [0, npix]:
+// a binary search over the kept samples, the pixel of sorted position i
+// being pix[perm[i]].
+__global__ void lower_bound_kernel(const uint32_t* __restrict__ perm, const int32_t* __restrict__ pix,
+                                   int64_t nvalid, int64_t npix, int64_t* __restrict__ off) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p <= npix;
          p += (int64_t)gridDim.x * blockDim.x) {
-        int64_t lo = 0, hi = n;
+        int64_t lo = 0, hi = nvalid;
         while (lo < hi) {
             const int64_t mid = (lo + hi) >> 1;
-            if ((int64_t)keys[mid] < p) lo = mid + 1; else hi = mid;
+            if ((int64_t)pix[perm[mid]] < p) lo = mid + 1; else hi = mid;
         }
         off[p] = lo;
     }
@@ -399,7 +420,8 @@ SortPlan plan_sort(const bm_context* ctx, int64_t n, int64_t npix) {
     const size_t smem = scatter_smem(sp.bins);
     ensure_smem_limit(reinterpret_cast<const void*>(rs_scatter_kernel<false>), smem);
     ensure_smem_limit(reinterpret_cast<const void*>(rs_scatter_kernel<true>), smem);
-    ensure_smem_limit(reinterpret_cast<const void*>(rs_hist_kernel), sizeof(uint32_t) * IG_WARPS * sp.bins);
+    ensure_smem_limit(reinterpret_cast<const void*>(rs_hist_kernel<false>), sizeof(uint32_t) * IG_WARPS * sp.bins);
+    ensure_smem_limit(reinterpret_cast<const void*>(rs_hist_kernel<true>), sizeof(uint32_t) * IG_WARPS * sp.bins);
     int per_sm = blocks_per_sm(reinterpret_cast<const void*>(rs_scatter_kernel<true>), SC_THREADS, smem);
     if (per_sm < 1) per_sm = 1;
     // four waves of equal ranges keep the tail short
@@ -427,7 +449,7 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
     p->pix.alloc(n);
     p->cs_hi_t.alloc(n);
     if (has_lo) p->cs_lo_t.alloc(n);
-    DevBuf<uint32_t> keys_a(n), keys_b(n);
+    DevBuf<uint32_t> keys_a(n);
     DevBuf<unsigned long long> counters(2);
     BM_CUDA(cudaMemsetAsync(counters.get(), 0, 2 * sizeof(unsigned long long), s));
     {
@@ -450,43 +472,42 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
     p->cs_hi_s.alloc(nvalid > 0 ? nvalid : 1);
     if (has_lo) p->cs_lo_s.alloc(nvalid > 0 ? nvalid : 1);
 
-    // Ping-pong buffers of the intermediate passes: sample indices and the
-    // trig payload (hi, and lo when the angles were given).
+    // Ping-pong record buffers of the intermediate passes (and the lo halves
+    // of the trig pairs when the angles were given).
     DevBuf<uint32_t> hist((size_t)sp.bins * sp.grid);
-    DevBuf<uint32_t> vals_a, vals_b;
-    DevBuf<float2> hi_a, hi_b, lo_a, lo_b;
+    DevBuf<uint4> rec_a, rec_b;
+    DevBuf<float2> lo_a, lo_b;
     if (sp.passes > 1) {
-        vals_a.alloc(n);
-        hi_a.alloc(n);
+        rec_a.alloc(n);
         if (has_lo) lo_a.alloc(n);
     }
     if (sp.passes > 2) {
-        vals_b.alloc(n);
-        hi_b.alloc(n);
+        rec_b.alloc(n);
         if (has_lo) lo_b.alloc(n);
     }
     const size_t smem = scatter_smem(sp.bins);
-    uint32_t* kin = keys_a.get();
-    uint32_t* kout = keys_b.get();
-    const uint32_t* vin = nullptr;  // the sample index on the first pass
-    uint32_t* vout = vals_a.get();
-    const float2* hin = p->cs_hi_t.get();
+    const uint4* rin = nullptr;  // the first pass reads keys, indices and trig in time order
+    uint4* rout = rec_a.get();
     const float2* lin = has_lo ? p->cs_lo_t.get() : nullptr;
-    float2* hout = hi_a.get();
     float2* lout = lo_a.get();
     for (int pass = 0; pass < sp.passes; ++pass) {
         const int shift = pass * sp.bits;
         {
             ScopedTimer ht(ctx, "ingest_hist");
-            rs_hist_kernel<<<sp.grid, IG_THREADS, sizeof(uint32_t) * IG_WARPS * sp.bins, s>>>(kin, n, sp.range, shift,
-                                                                                         sp.bins, sp.grid, hist.get());
+            const size_t hsm = sizeof(uint32_t) * IG_WARPS * sp.bins;
+            if (rin)
+                rs_hist_kernel<true><<<sp.grid, IG_THREADS, hsm, s>>>(nullptr, rin, n, sp.range, shift, sp.bins,
+                                                                      sp.grid, hist.get());
+            else
+                rs_hist_kernel<false><<<sp.grid, IG_THREADS, hsm, s>>>(keys_a.get(), nullptr, n, sp.range, shift,
+                                                                       sp.bins, sp.grid, hist.get());
             BM_LAUNCH_CHECK();
         }
         exclusive_scan_u32(hist.get(), hist.get(), (int64_t)sp.bins * sp.grid, s);
         ScatterArgs a{};
-        a.keys_in = kin;
-        a.vals_in = vin;
-        a.hi_in = hin;
+        a.rec_in = rin;
+        a.keys_in = keys_a.get();
+        a.hi_in = p->cs_hi_t.get();
         a.lo_in = lin;
         a.n = n;
         a.range = sp.range;
@@ -494,36 +515,29 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
         a.bins = sp.bins;
         a.G = sp.grid;
         a.offs = hist.get();
-        a.keys_out = kout;
+        ScopedTimer st(ctx, "ingest_scatter");
         if (pass + 1 < sp.passes) {
-            a.vals_out = vout;
-            a.hi_out = hout;
+            a.rec_out = rout;
             a.lo_out = lout;
-            ScopedTimer st(ctx, "ingest_scatter");
             rs_scatter_kernel<false><<<sp.grid, SC_THREADS, smem, s>>>(a);
             BM_LAUNCH_CHECK();
-            vin = vout;
-            hin = hout;
+            rin = rout;
+            rout = (rout == rec_a.get()) ? rec_b.get() : rec_a.get();
             lin = has_lo ? lout : nullptr;
-            vout = (vout == vals_a.get()) ? vals_b.get() : vals_a.get();
-            hout = (hout == hi_a.get()) ? hi_b.get() : hi_a.get();
             lout = (lout == lo_a.get()) ? lo_b.get() : lo_a.get();
         } else {
-            a.vals_out = p->perm.get();
+            a.perm_out = p->perm.get();
             a.hi_out = p->cs_hi_s.get();
             a.lo_out = has_lo ? p->cs_lo_s.get() : nullptr;
             a.key_limit = (uint32_t)npix;
-            ScopedTimer st(ctx, "ingest_scatter");
             rs_scatter_kernel<true><<<sp.grid, SC_THREADS, smem, s>>>(a);
             BM_LAUNCH_CHECK();
         }
-        std::swap(kin, kout);
     }
-    // kin holds the sorted keys (flagged samples, key npix, last).
     p->off.alloc(npix + 1);
     p->hits.alloc(npix);
     const int pgrid = grid_for(ctx, (npix + 1 + threads - 1) / threads, 16);
-    lower_bound_kernel<<<pgrid, threads, 0, s>>>(kin, n, npix, p->off.get());
+    lower_bound_kernel<<<pgrid, threads, 0, s>>>(p->perm.get(), p->pix.get(), nvalid, npix, p->off.get());
     BM_LAUNCH_CHECK();
     hits_kernel<<<pgrid, threads, 0, s>>>(p->off.get(), npix, p->hits.get());
     BM_LAUNCH_CHECK();

@@ -36,6 +36,24 @@ __global__ void masked_copy_kernel(const double* __restrict__ x, const uint8_t* 
         out[i] = mask[i / nc] ? TO(0) : TO(x[i]);
 }
 
+// x (FP64, [npix][NC]) -> one FP32 (a, b, c, 0) per pixel with y = a + b cos
+// + c sin, masked pixels zeroed: IQU (I, Q, U), QU (0, Q, U), I (I, 0, 0).
+// Sixteen aligned bytes per pixel, so P x reads its map entry in one load.
+__global__ void masked_copy4_kernel(const double* __restrict__ x, const uint8_t* __restrict__ mask,
+                                    int64_t npix, int nc, float4* __restrict__ out) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!mask[p]) {
+            const double* xp = x + p * nc;
+            if (nc == 3) v = make_float4((float)xp[0], (float)xp[1], (float)xp[2], 0.f);
+            else if (nc == 2) v = make_float4(0.f, (float)xp[0], (float)xp[1], 0.f);
+            else v.x = (float)xp[0];
+        }
+        out[p] = v;
+    }
+}
+
 // ------------------------------------------------------- white, FP32 form
 // One work item per warp.  Loads are 16 bytes per lane (two samples of the
 // (u_c, u_s) stream, four of the I-only weight stream) after a scalar head
@@ -148,15 +166,15 @@ __global__ void __launch_bounds__(kWarps * 32)
 white_matvec_f64_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ item_beg,
                         const int32_t* __restrict__ item_len, int64_t nitems,
                         const uint32_t* __restrict__ perm, const float2* __restrict__ hi,
-                        const float2* __restrict__ lo, const int64_t* __restrict__ det_off, int ndet,
-                        const double* __restrict__ white, const double* __restrict__ x,
-                        double* __restrict__ partial) {
-    __shared__ int64_t s_off[kMaxDetSmem + 1];
+                        const float2* __restrict__ lo, const uint32_t* __restrict__ det_off, int ndet,
+                        uint32_t ns, float inv_ns, const double* __restrict__ white,
+                        const double* __restrict__ x, double* __restrict__ partial) {
+    __shared__ uint32_t s_off[kMaxDetSmem + 1];
     const bool in_smem = ndet <= kMaxDetSmem;
     if (in_smem)
         for (int d = threadIdx.x; d <= ndet; d += blockDim.x) s_off[d] = det_off[d];
     __syncthreads();
-    const int64_t* offp = in_smem ? s_off : det_off;
+    const uint32_t* offp = in_smem ? s_off : det_off;
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * kWarps;
     for (int64_t k = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); k < nitems; k += nwarps) {
@@ -171,7 +189,7 @@ white_matvec_f64_kernel(const int32_t* __restrict__ item_pix, const int64_t* __r
         for (int c = 0; c < NC; ++c) acc[c] = 0.0;
         for (int i = lane; i < len; i += 32) {
             const int64_t si = b + i;
-            const double w = white[find_det(offp, ndet, perm[si])];
+            const double w = white[det_of(offp, ndet, ns, inv_ns, perm[si])];
             if (NC == 1) {
                 acc[0] += w * xv[0];
             } else {
@@ -230,7 +248,7 @@ gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __rest
                 if (sizeof(G) == 4) val = {(float)gv, 0.f};
                 else val = df_from((double)gv);
                 if (weighted) {
-                    const float2 w = wp[find_det32(offp, ndet, t)];
+                    const float2 w = wp[det_of(offp, ndet, dt.ns, dt.inv_ns, t)];
                     val = df_mul(val, df32{w.x, w.y});
                 }
                 if (NC == 1) {
@@ -277,7 +295,7 @@ gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __rest
             for (int c = 0; c < NC; ++c) acc[c] = 0.0;
             auto add = [&](uint32_t t, G gv, int64_t si) {
                 double val = (double)gv;
-                if (weighted) val *= white[find_det32(offp, ndet, t)];
+                if (weighted) val *= white[det_of(offp, ndet, dt.ns, dt.inv_ns, t)];
                 if (NC == 1) {
                     acc[0] += val;
                 } else {
@@ -351,12 +369,12 @@ __global__ void pointing_apply_kernel(const int32_t* __restrict__ pix, const flo
 // --------------------------------------------------------- Toeplitz filter
 // Sample sources for the filter input y_t.
 template <typename D>
-struct SrcMaskedTod {  // y_t = d_t on kept samples, else 0
+struct SrcMaskedTod {  // y_t = d_t on kept samples, else 0 (in the TOD's own type)
     const int32_t* pix; const uint8_t* mask; const D* d;
-    __device__ double operator()(int64_t t) const {
+    __device__ D operator()(int64_t t) const {
         const int32_t p = pix[t];
-        if (p < 0 || mask[p]) return 0.0;
-        return (double)d[t];
+        if (p < 0 || mask[p]) return D(0);
+        return d[t];
     }
 };
 struct SrcPlain {
@@ -368,13 +386,13 @@ struct SrcPlainF32 {
     __device__ float operator()(int64_t t) const { return y[t]; }
 };
 
-// y = P x32 over every sample in FP32 (x32 zero on masked pixels, so their
-// samples give 0; flagged samples give 0): the filter's input, computed by a
-// full-occupancy elementwise pass so that the filter kernel reads it with
-// plain coalesced loads instead of a dependent pixel-then-map gather.
-template <int NC>
+// y = P x over every sample in FP32, from the padded map x4 (zero on masked
+// pixels, so their samples give 0; flagged samples give 0): the filter's
+// input, computed by a full-occupancy elementwise pass so that the filter
+// kernel reads it with plain coalesced loads instead of a dependent
+// pixel-then-map gather.
 __global__ void pointing_apply_f32_kernel(const int32_t* __restrict__ pix, const float2* __restrict__ hi, int64_t n,
-                                          const float* __restrict__ x, float* __restrict__ y) {
+                                          const float4* __restrict__ x4, float* __restrict__ y) {
     constexpr int U = 4;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t0 < n; t0 += U * stride) {
@@ -384,23 +402,15 @@ __global__ void pointing_apply_f32_kernel(const int32_t* __restrict__ pix, const
         for (int u = 0; u < U; ++u) {
             const int64_t t = t0 + u * stride;
             p[u] = t < n ? pix[t] : -1;
-            h[u] = (NC > 1 && t < n) ? hi[t] : make_float2(0.f, 0.f);
+            h[u] = t < n ? hi[t] : make_float2(0.f, 0.f);
         }
+        float4 xv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) xv[u] = p[u] >= 0 ? x4[p[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int64_t t = t0 + u * stride;
-            if (t >= n) continue;
-            float v = 0.f;
-            if (p[u] >= 0) {
-                const float* xp = x + (int64_t)p[u] * NC;
-                if (NC == 1) {
-                    v = xp[0];
-                } else {
-                    v = fmaf(h[u].x, xp[NC - 2], h[u].y * xp[NC - 1]);
-                    if (NC == 3) v += xp[0];
-                }
-            }
-            y[t] = v;
+            if (t < n) y[t] = fmaf(h[u].x, xv[u].y, fmaf(h[u].y, xv[u].z, xv[u].x));
         }
     }
 }
@@ -563,7 +573,8 @@ void prepare_toeplitz_fft(bm_inv_noise* n) {
         n->spec32.alloc((size_t)n->ndet * (N / 2 + 1));
         n->tw32.alloc(N);
         band_spectrum_kernel<<<grid_for(ctx, ((int64_t)n->ndet * (N / 2 + 1) + threads - 1) / threads, 16), threads, 0,
-                               ctx->stream>>>(n->coeffs64.get(), n->ndet, n->nlags, N, nullptr, n->spec32.get());
+                               ctx->stream>>>(n->coeffs64.get(), n->ndet, n->nlags, N, nullptr, n->spec32.get(),
+                                              nullptr);
         BM_LAUNCH_CHECK();
         twiddle_kernel<<<(N + threads - 1) / threads, threads, 0, ctx->stream>>>(N, nullptr, n->tw32.get());
         BM_LAUNCH_CHECK();
@@ -571,9 +582,11 @@ void prepare_toeplitz_fft(bm_inv_noise* n) {
     if (n->fft_n64) {
         const int N = n->fft_n64;
         n->spec64.alloc((size_t)n->ndet * (N / 2 + 1));
+        n->spec_df.alloc((size_t)n->ndet * (N / 2 + 1));
         n->tw64.alloc(N);
         band_spectrum_kernel<<<grid_for(ctx, ((int64_t)n->ndet * (N / 2 + 1) + threads - 1) / threads, 16), threads, 0,
-                               ctx->stream>>>(n->coeffs64.get(), n->ndet, n->nlags, N, n->spec64.get(), nullptr);
+                               ctx->stream>>>(n->coeffs64.get(), n->ndet, n->nlags, N, n->spec64.get(), nullptr,
+                                              n->spec_df.get());
         BM_LAUNCH_CHECK();
         twiddle_kernel<<<(N + threads - 1) / threads, threads, 0, ctx->stream>>>(N, n->tw64.get(), nullptr);
         BM_LAUNCH_CHECK();
@@ -613,7 +626,7 @@ template <class Src>
 static void apply_toeplitz_f64(bm_inv_noise* n, const Src& src, double* z, bool df = false) {
     const auto* tw = reinterpret_cast<const cpx<double>*>(n->tw64.get());
     if (n->fft_n64 && df)
-        run_toeplitz_fft<df32>(n, src, n->fft_n64, n->spec64.get(), tw, z);
+        run_toeplitz_fft<df32>(n, src, n->fft_n64, n->spec_df.get(), tw, z);
     else if (n->fft_n64)
         run_toeplitz_fft<double>(n, src, n->fft_n64, n->spec64.get(), tw, z);
     else
@@ -651,8 +664,9 @@ static void gather_reduce(bm_pointing* p, const ItemsView& it, const G* g, const
     if (it.n > 0) {
         const int64_t wunits = (it.n + kWarps - 1) / kWarps;
         const bool weighted = wn != nullptr;
-        const DetTables dt = weighted ? DetTables{wn->det_off32.get(), wn->wdf.get(), wn->wsqrt.get()}
-                                      : DetTables{nullptr, nullptr, nullptr};
+        const DetTables dt = weighted ? DetTables{wn->det_off32.get(), wn->wdf.get(), wn->wsqrt.get(), wn->ns_uniform,
+                                                  wn->inv_ns}
+                                      : DetTables{nullptr, nullptr, nullptr, 0u, 0.f};
         const double* white = weighted ? wn->white.get() : nullptr;
         const int ndet = weighted ? wn->ndet : 0;
 #define BM_GR(NC, D)                                                                                           \
@@ -703,7 +717,8 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
 #define BM_WF64(NC)                                                                                      \
     white_matvec_f64_kernel<NC><<<resident_grid(ctx, white_matvec_f64_kernel<NC>, kWarps * 32, wunits), kWarps * 32, 0, s>>>(                                              \
         pc->item_pix.get(), pc->item_beg.get(), pc->item_len.get(), pc->nitems, p->perm.get(),            \
-        p->cs_hi_s.get(), p->cs_lo_s.get(), n->det_off.get(), n->ndet, n->white.get(), xr, partial)
+        p->cs_hi_s.get(), p->cs_lo_s.get(), n->det_off32.get(), n->ndet, n->ns_uniform, n->inv_ns, n->white.get(), \
+        xr, partial)
                 if (nc == 3) BM_WF64(3); else if (nc == 2) BM_WF64(2); else BM_WF64(1);
 #undef BM_WF64
                 BM_LAUNCH_CHECK();
@@ -711,20 +726,16 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
             finalize(ctx, pc->pitem.get(), partial, p->npix, nc, qr);
         } else {
             if (prec == BM_PREC_MIXED) {
-                float* x32 = workspace_as<float>(ctx, "x32", nvec);
                 float* z32 = workspace_as<float>(ctx, "z32", p->nsamples);
-                masked_copy_kernel<float><<<vgrid, threads, 0, s>>>(xr, pc->mask.get(), p->npix, nc, x32);
-                BM_LAUNCH_CHECK();
                 {
                     ScopedTimer timer(ctx, "toeplitz_f32");
                     float* y32 = workspace_as<float>(ctx, "y32", p->nsamples);
-                    const int g = grid_for(ctx, (p->nsamples + threads - 1) / threads, 16);
-                    if (nc == 3)
-                        pointing_apply_f32_kernel<3><<<g, threads, 0, s>>>(p->pix.get(), p->cs_hi_t.get(), p->nsamples, x32, y32);
-                    else if (nc == 2)
-                        pointing_apply_f32_kernel<2><<<g, threads, 0, s>>>(p->pix.get(), p->cs_hi_t.get(), p->nsamples, x32, y32);
-                    else
-                        pointing_apply_f32_kernel<1><<<g, threads, 0, s>>>(p->pix.get(), p->cs_hi_t.get(), p->nsamples, x32, y32);
+                    float4* x4 = workspace_as<float4>(ctx, "x4", p->npix);
+                    masked_copy4_kernel<<<grid_for(ctx, (p->npix + threads - 1) / threads, 16), threads, 0, s>>>(
+                        xr, pc->mask.get(), p->npix, nc, x4);
+                    BM_LAUNCH_CHECK();
+                    pointing_apply_f32_kernel<<<grid_for(ctx, (p->nsamples + threads - 1) / threads, 16), threads, 0, s>>>(
+                        p->pix.get(), p->cs_hi_t.get(), p->nsamples, x4, y32);
                     BM_LAUNCH_CHECK();
                     apply_toeplitz_f32(n, SrcPlainF32{y32}, z32);
                 }

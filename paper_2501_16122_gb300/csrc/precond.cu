@@ -106,7 +106,7 @@ blocks_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ 
         for (int j = 0; j < NS; ++j) acc[j] = {0.f, 0.f};
         for (int i = lane; i < len; i += 32) {
             const int64_t si = b + i;
-            const int d = find_det32(offp, ndet, perm[si]);
+            const int d = det_of(offp, ndet, g.ns, g.inv_ns, perm[si]);
             const float2 wv = wp[d];
             const df32 w = {wv.x, wv.y};
             const float2 h = hi[si];
@@ -283,7 +283,7 @@ void build_precond(bm_precond* pc) {
         }
         if (all.n > 0) {
             const int64_t wunits = (all.n + kBlkWarps - 1) / kBlkWarps;
-            const DetTables g{n->det_off32.get(), n->wdf.get(), n->wsqrt.get()};
+            const DetTables g{n->det_off32.get(), n->wdf.get(), n->wsqrt.get(), n->ns_uniform, n->inv_ns};
 #define BM_BLOCKS(NC, W)                                                                                    \
     blocks_kernel<NC, W><<<resident_grid(ctx, blocks_kernel<NC, W>, kBlkWarps * 32, wunits), kBlkWarps * 32, 0, s>>>(all.pix.get(), all.beg.get(), all.len.get(), all.n, \
                                                          p->perm.get(), p->cs_hi_s.get(), p->cs_lo_s.get(), g, \

@@ -458,3 +458,38 @@ def test_pinned_host_inputs_match_device_inputs(L, ctx):
             L.bm_pointing_destroy(host)
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_uneven_detector_lengths(L, ctx, prec):
+    """Detectors of different lengths (the offsets' binary search; equal
+    lengths take the t / ns path): blocks, RHS, matvec and the solve against
+    the oracle."""
+    e = synth.make_experiment(16, 4, 20_000, 515)
+    pt = synth.pointing(e, flag_frac=0.01)
+    det_off = np.array([0, 7_000, 29_000, 29_001, 80_000], np.int64)
+    inv_var = np.array([1.0, 0.4, 2.5, 0.7])
+    sky = synth.sky_map(e.npix, 515)
+    tod = synth.tod(e, pt["pix"], pt["psi"], sky, white=False)
+    tod = tod + np.random.default_rng(5).normal(size=tod.size) / np.sqrt(inv_var[gls.sample_detector(det_off)])
+    S = gls.System(pt["pix"], pt["psi"], 3, e.npix, gls.WhiteNoise(inv_var, det_off))
+    p = L.bm_pointing_create(ctx, e.npix, torch.from_numpy(pt["pix"]).cuda(), torch.from_numpy(pt["psi"]).cuda(), 3)
+    n = L.bm_inv_noise_create_diag(ctx, det_off, inv_var)
+    pc = L.bm_blockdiag_precond_create(p, n, 3, 1e3)
+    try:
+        P = L.BM_PREC_FP64 if prec == "fp64" else L.BM_PREC_MIXED
+        x = np.random.default_rng(6).normal(size=(e.npix, 3))
+        q = torch.zeros(e.npix * 3, dtype=torch.float64, device="cuda")
+        L.bm_matvec(p, n, pc, torch.from_numpy(x.ravel()).cuda(), q, P)
+        ref = S.matvec(x * (~S.mask)[:, None])
+        assert rel(q.cpu().numpy(), ref.ravel()) < (1e-12 if prec == "fp64" else 2e-6)
+        out = torch.zeros(e.npix * 3, dtype=torch.float64, device="cuda")
+        st, _ = L.bm_pcg_solve(p, n, pc, torch.from_numpy(tod).cuda(), 1, out, 1e-11, 200, P)
+        assert st == L.BM_OK
+        oref, _ = gls.gls_map(S, tod, tol=1e-13)
+        err = gls.rel_err(out.cpu().numpy().reshape(e.npix, 3), oref, S.mask)
+        assert max(err.values()) < (1e-10 if prec == "fp64" else 1e-6), err
+    finally:
+        L.bm_precond_destroy(pc)
+        L.bm_inv_noise_destroy(n)
+        L.bm_pointing_destroy(p)
