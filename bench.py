@@ -166,12 +166,7 @@ CPU_SAMPLE = dict(ndet=8, ns=2 ** 19)  # 4.2M samples of the same scan: ~10 s of
 KERNELS = {"ingest_validate": "validate_kernel", "ingest_hist": "rs_hist_kernel",
            "ingest_scatter": "rs_scatter_kernel", "blocks": "blocks_kernel", "rhs": "gather_reduce_kernel",
            "matvec_white_f32": "white_matvec_f32_kernel"}
-TRAFFIC = {
-    # profiles/ingest_sort_nside256_256x262144.md: 29.0 and 31.3 DRAM bytes per
-    # sample for the two scatter passes (mean 30.15), 67M-sample case; the
-    # traffic grows in proportion to the samples
-    "ingest_scatter": lambda n: 30.15 * n,
-}
+TRAFFIC = {}
 
 
 def n_valid_kept(hits, kept):

@@ -262,20 +262,21 @@ struct ScatterArgs {
 };
 
 inline size_t scatter_smem(int bins) {
-    return sizeof(uint32_t) * (2 * (size_t)SC_TILE + 3 * (size_t)bins) + sizeof(float2) * SC_TILE +
-           sizeof(uint16_t) * (SC_TILE + (size_t)SC_WARPS * bins);
+    return sizeof(uint32_t) * ((size_t)SC_TILE + 3 * (size_t)bins) +
+           sizeof(uint16_t) * ((size_t)SC_TILE + (size_t)SC_WARPS * bins);
 }
 
 // One stable scatter pass over the block's range (see the file comment).
-// The lo half of an FP64 trig pair, when present, is not staged: it is read
-// back from the tile's window of the input (L2-resident) at write time.
+// Only the key and the tile position of each sample are staged in shared
+// memory (6 bytes a sample, so two 512-thread blocks fit on an SM); at write
+// time the rest of the sample (index, trig pair, lo half) is read back from
+// the tile's window of the input, which the key loads have just brought
+// into L2.
 template <bool LAST>
-__global__ void __launch_bounds__(SC_THREADS, 1) rs_scatter_kernel(ScatterArgs a) {
+__global__ void __launch_bounds__(SC_THREADS, 2) rs_scatter_kernel(ScatterArgs a) {
     extern __shared__ __align__(16) uint32_t ss[];
-    float2* s_hi = reinterpret_cast<float2*>(ss);
-    uint32_t* s_keys = reinterpret_cast<uint32_t*>(s_hi + SC_TILE);
-    uint32_t* s_vals = s_keys + SC_TILE;
-    uint32_t* run_base = s_vals + SC_TILE;  // next global position per digit
+    uint32_t* s_keys = ss;
+    uint32_t* run_base = s_keys + SC_TILE;  // next global position per digit
     uint32_t* tcnt = run_base + a.bins;     // tile count per digit
     uint32_t* tstart = tcnt + a.bins;       // tile-local start per digit
     uint16_t* s_src = reinterpret_cast<uint16_t*>(tstart + a.bins);  // tile position of a staged sample
@@ -288,6 +289,7 @@ __global__ void __launch_bounds__(SC_THREADS, 1) rs_scatter_kernel(ScatterArgs a
     const int64_t begin = range_begin(a.range);
     const int64_t end = begin + a.range < a.n ? begin + a.range : a.n;
     const uint64_t pol = l2_keep_policy();
+    const uint32_t* rec_keys = reinterpret_cast<const uint32_t*>(a.rec_in);  // key = word 0 of a record
 
     for (int d = threadIdx.x; d < bins; d += SC_THREADS) {
         run_base[d] = a.offs[(int64_t)d * a.G + blockIdx.x];
@@ -298,23 +300,12 @@ __global__ void __launch_bounds__(SC_THREADS, 1) rs_scatter_kernel(ScatterArgs a
 
     for (int64_t base = begin; base < end; base += SC_TILE) {
         const int cnt = (int)(end - base < SC_TILE ? end - base : SC_TILE);
-        uint32_t key[IG_PER_THREAD], val[IG_PER_THREAD], rank[IG_PER_THREAD];
-        float2 hv[IG_PER_THREAD];
-        // 1. the warp's 512 consecutive samples, 32 per round
+        uint32_t key[IG_PER_THREAD], rank[IG_PER_THREAD];
+        // 1. the warp's 512 consecutive keys, 32 per round
 #pragma unroll
         for (int r = 0; r < IG_PER_THREAD; ++r) {
             const int j = w * IG_WARP_SPAN + r * 32 + lane;
-            const bool v = j < cnt;
-            if (a.rec_in) {
-                const uint4 x = v ? __ldcs(a.rec_in + base + j) : make_uint4(0u, 0u, 0u, 0u);
-                key[r] = x.x;
-                val[r] = x.y;
-                hv[r] = make_float2(__uint_as_float(x.z), __uint_as_float(x.w));
-            } else {
-                key[r] = v ? __ldcs(a.keys_in + base + j) : 0u;
-                val[r] = (uint32_t)(base + j);
-                hv[r] = v ? __ldcs(a.hi_in + base + j) : make_float2(0.f, 0.f);
-            }
+            key[r] = j < cnt ? (a.rec_in ? rec_keys[4 * (base + j)] : a.keys_in[base + j]) : 0u;
         }
         // 2. stable rank within the warp: counters advance round by round
 #pragma unroll
@@ -347,7 +338,7 @@ __global__ void __launch_bounds__(SC_THREADS, 1) rs_scatter_kernel(ScatterArgs a
         __syncthreads();
         scan_bins<SC_THREADS>(tcnt, tstart, bins, wtot);
         __syncthreads();
-        // 4. stage the tile in digit order
+        // 4. stage keys and tile positions in digit order
 #pragma unroll
         for (int r = 0; r < IG_PER_THREAD; ++r) {
             const int j = w * IG_WARP_SPAN + r * 32 + lane;
@@ -355,25 +346,44 @@ __global__ void __launch_bounds__(SC_THREADS, 1) rs_scatter_kernel(ScatterArgs a
                 const uint32_t d = (key[r] >> a.shift) & dmask;
                 const uint32_t pos = tstart[d] + wcnt[w * bins + d] + rank[r];
                 s_keys[pos] = key[r];
-                s_vals[pos] = val[r];
-                s_hi[pos] = hv[r];
                 s_src[pos] = (uint16_t)j;
             }
         }
         __syncthreads();
-        // 5. each digit's run goes to its running global offset
-        for (int j = threadIdx.x; j < cnt; j += SC_THREADS) {
-            const uint32_t k = s_keys[j];
-            const uint32_t d = (k >> a.shift) & dmask;
-            const uint32_t g = run_base[d] + (uint32_t)j - tstart[d];
-            if (!LAST) {
-                const float2 h = s_hi[j];
-                a.rec_out[g] = make_uint4(k, s_vals[j], __float_as_uint(h.x), __float_as_uint(h.y));
-                if (a.lo_in) st_keep(a.lo_out + g, a.lo_in[base + s_src[j]], pol);
-            } else if (k < a.key_limit) {
-                st_keep(a.perm_out + g, s_vals[j], pol);
-                st_keep(a.hi_out + g, s_hi[j], pol);
-                if (a.lo_in) st_keep(a.lo_out + g, a.lo_in[base + s_src[j]], pol);
+        // 5. each digit's run goes to its running global offset, the rest of
+        //    each sample read back from the input window; four per thread in
+        //    flight
+        for (int j0 = threadIdx.x; j0 < cnt; j0 += 4 * SC_THREADS) {
+            uint32_t kk[4], gg[4], src[4];
+            uint4 rr[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = j0 + u * SC_THREADS;
+                kk[u] = kNoDigit;
+                if (j < cnt) {
+                    kk[u] = s_keys[j];
+                    src[u] = s_src[j];
+                    const uint32_t d = (kk[u] >> a.shift) & dmask;
+                    gg[u] = run_base[d] + (uint32_t)j - tstart[d];
+                    if (a.rec_in) {
+                        rr[u] = a.rec_in[base + src[u]];
+                    } else {
+                        const float2 h = a.hi_in[base + src[u]];
+                        rr[u] = make_uint4(kk[u], (uint32_t)(base + src[u]), __float_as_uint(h.x), __float_as_uint(h.y));
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (kk[u] == kNoDigit) continue;
+                if (!LAST) {
+                    a.rec_out[gg[u]] = make_uint4(kk[u], rr[u].y, rr[u].z, rr[u].w);
+                    if (a.lo_in) st_keep(a.lo_out + gg[u], a.lo_in[base + src[u]], pol);
+                } else if (kk[u] < a.key_limit) {
+                    st_keep(a.perm_out + gg[u], rr[u].y, pol);
+                    st_keep(a.hi_out + gg[u], make_float2(__uint_as_float(rr[u].z), __uint_as_float(rr[u].w)), pol);
+                    if (a.lo_in) st_keep(a.lo_out + gg[u], a.lo_in[base + src[u]], pol);
+                }
             }
         }
         __syncthreads();
