@@ -166,7 +166,12 @@ CPU_SAMPLE = dict(ndet=8, ns=2 ** 19)  # 4.2M samples of the same scan: ~10 s of
 KERNELS = {"ingest_validate": "validate_kernel", "ingest_hist": "rs_hist_kernel",
            "ingest_scatter": "rs_scatter_kernel", "blocks": "blocks_kernel", "rhs": "gather_reduce_kernel",
            "matvec_white_f32": "white_matvec_f32_kernel"}
-TRAFFIC = {}
+TRAFFIC = {
+    # profiles/ingest_sort_nside256_256x262144.md: 43.8 and 39.5 DRAM bytes
+    # per sample for the two scatter passes (mean 41.65) on the 67M-sample
+    # case; the traffic grows in proportion to the samples
+    "ingest_scatter": lambda n: 41.65 * n,
+}
 
 
 def n_valid_kept(hits, kept):
@@ -303,6 +308,24 @@ def run_gb300(args, rank, world, local_rank):
     k_tot, k_cnt = L.bm_context_kernel_time(ctx, "matvec_white_f32")
     L.bm_context_set_timing(ctx, False)
     k_ms = k_tot / max(k_cnt, 1)
+    # the plain FP64 path on the same system, beside the refined one (solve
+    # only: pointing, noise model and preconditioner already built)
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+    out_alt = torch.empty_like(out)
+    fp64_path = {
+        "matvec_ms": timed(lambda: L.bm_matvec(p, n, pc, x, q, L.BM_PREC_FP64)),
+        "solve_ms": timed(lambda: L.bm_pcg_solve(p, n, pc, d_tod, 1, out_alt, args.tol, 200, L.BM_PREC_FP64)),
+        "mixed_solve_ms": timed(lambda: L.bm_pcg_solve(p, n, pc, d_tod, 1, out_alt, args.tol, 200, L.BM_PREC_MIXED)),
+    }
     nitems_est = sum(math.ceil(h / 4096) for h in hits[kept].tolist()) if n_kept_pix < 5_000_000 else 0
     alg_bytes = 8 * n_kept_samples + 12 * n_kept_pix + 24 * nitems_est  # trig pair + x + item partials
     hbm, peak_kind = peaks()
@@ -322,10 +345,10 @@ def run_gb300(args, rank, world, local_rank):
     hist_bytes = 0
     for ps in range(passes):
         last = ps == passes - 1
-        rd = 16 if ps > 0 else 12                          # 16-byte records, or key + trig pair in time order
-        wr = (12 * n_valid / nt) if last else 16           # perm + trig of kept samples, or records
+        rd = 4 + (16 if ps > 0 else 8)                     # keys + records, or keys + trig pair in time order
+        wr = (12 * n_valid / nt) if last else 20           # perm + trig of kept samples, or records + keys
         scatter_bytes += (rd + wr) * nt
-        hist_bytes += (16 if ps > 0 else 4) * nt           # keys, read from the records after the first pass
+        hist_bytes += 4 * nt                               # keys
     step_bytes = {
         "ingest_validate": 28 * nt,                       # pix + cos + sin in; pix, key, trig pair out
         "ingest_hist": hist_bytes,
@@ -408,6 +431,7 @@ def run_gb300(args, rank, world, local_rank):
             "matvec": {"samples_per_s": nt / (k_ms * 1e-3), "kernel_ms": k_ms, "call_ms": mv_call_ms,
                        "kept_samples": n_kept_samples, "hbm_frac": achieved / hbm},
             "time_to_map_ms": ms_max - fam.get("ingest", {}).get("ms_per_step", 0.0),
+            "solve_only_ms": fp64_path,
             "step_breakdown_ms": {k: v["ms_per_step"] for k, v in fam.items()},
             "solve": {"status_ok": st_ok, "iterations": last["iterations"],
                       "outer_iterations": last["outer_iterations"], "rel_residual": last["rel_residual"]},

@@ -25,7 +25,8 @@
 // them once, in tile order): on this part a random 8-byte read moves about
 // 100 bytes of DRAM traffic, so gathering them through perm afterwards would
 // cost several times more.  Between passes a sample is one 16-byte record
-// {key, sample index, cos, sin}; the last pass writes only perm and the
+// {key, sample index, cos, sin}, with the keys also written alone for the
+// next pass's histogram and ranking; the last pass writes only perm and the
 // sorted trig pairs, and the CSR offsets come from a binary search per pixel
 // over pix[perm[i]].
 #include "bm_internal.cuh"
@@ -151,10 +152,9 @@ __global__ void validate_kernel(const int32_t* __restrict__ pix, const void* __r
 // Each thread counts 16 consecutive keys (vector loads), adding runs of equal
 // digits at once into its warp's own histogram; the warp histograms are
 // summed at the end.
-template <bool REC>
 __global__ void __launch_bounds__(IG_THREADS)
-rs_hist_kernel(const uint32_t* __restrict__ keys, const uint4* __restrict__ rec, int64_t n, int64_t range,
-               int shift, int bins, int G, uint32_t* __restrict__ hist) {
+rs_hist_kernel(const uint32_t* __restrict__ keys, int64_t n, int64_t range, int shift, int bins, int G,
+               uint32_t* __restrict__ hist) {
     extern __shared__ __align__(16) uint32_t hh[];  // [IG_WARPS][bins]
     for (int d = threadIdx.x; d < IG_WARPS * bins; d += IG_THREADS) hh[d] = 0;
     __syncthreads();
@@ -165,10 +165,7 @@ rs_hist_kernel(const uint32_t* __restrict__ keys, const uint4* __restrict__ rec,
     for (int64_t base = begin; base < end; base += IG_TILE) {
         const int64_t i0 = base + (int64_t)threadIdx.x * IG_PER_THREAD;
         uint32_t k[IG_PER_THREAD];
-        if (REC) {
-#pragma unroll
-            for (int r = 0; r < IG_PER_THREAD; ++r) k[r] = i0 + r < end ? __ldcs(rec + i0 + r).x : kNoDigit;
-        } else if (i0 + IG_PER_THREAD <= end) {
+        if (i0 + IG_PER_THREAD <= end) {
             const uint4* v = reinterpret_cast<const uint4*>(keys + i0);  // i0 is a multiple of 16
 #pragma unroll
             for (int q = 0; q < IG_PER_THREAD / 4; ++q) {
@@ -247,14 +244,16 @@ __device__ void scan_bins(const uint32_t* cnt, uint32_t* start, int bins, uint32
 // fill whole lines, which measured twice as fast).
 struct ScatterArgs {
     const uint4* rec_in;      // records of the previous pass, or null on the first pass:
-    const uint32_t* keys_in;  //   then keys, the sample index itself and the trig pairs
-    const float2* hi_in;      //   in time order
+                              //   then the sample index itself and the trig pairs in time order
+    const uint32_t* keys_in;  // keys in this pass's input order
+    const float2* hi_in;
     const float2* lo_in;      // lo halves of the trig pairs in this pass's input order, or null
     int64_t n;
     int64_t range;
     int shift, bins, G;
     const uint32_t* offs;  // [bins][G] exclusive digit-major scan of the counts
-    uint4* rec_out;        // intermediate passes
+    uint4* rec_out;        // intermediate passes: records, and the keys alone for the next pass
+    uint32_t* keys_out;
     uint32_t* perm_out;    // last pass: sample indices (perm) and trig pairs of the kept samples
     float2* hi_out;
     float2* lo_out;        // every pass with lo_in: the lo halves in this pass's output order
@@ -289,7 +288,6 @@ __global__ void __launch_bounds__(SC_THREADS, 2) rs_scatter_kernel(ScatterArgs a
     const int64_t begin = range_begin(a.range);
     const int64_t end = begin + a.range < a.n ? begin + a.range : a.n;
     const uint64_t pol = l2_keep_policy();
-    const uint32_t* rec_keys = reinterpret_cast<const uint32_t*>(a.rec_in);  // key = word 0 of a record
 
     for (int d = threadIdx.x; d < bins; d += SC_THREADS) {
         run_base[d] = a.offs[(int64_t)d * a.G + blockIdx.x];
@@ -305,7 +303,7 @@ __global__ void __launch_bounds__(SC_THREADS, 2) rs_scatter_kernel(ScatterArgs a
 #pragma unroll
         for (int r = 0; r < IG_PER_THREAD; ++r) {
             const int j = w * IG_WARP_SPAN + r * 32 + lane;
-            key[r] = j < cnt ? (a.rec_in ? rec_keys[4 * (base + j)] : a.keys_in[base + j]) : 0u;
+            key[r] = j < cnt ? a.keys_in[base + j] : 0u;
         }
         // 2. stable rank within the warp: counters advance round by round
 #pragma unroll
@@ -378,6 +376,7 @@ __global__ void __launch_bounds__(SC_THREADS, 2) rs_scatter_kernel(ScatterArgs a
                 if (kk[u] == kNoDigit) continue;
                 if (!LAST) {
                     a.rec_out[gg[u]] = make_uint4(kk[u], rr[u].y, rr[u].z, rr[u].w);
+                    a.keys_out[gg[u]] = kk[u];
                     if (a.lo_in) st_keep(a.lo_out + gg[u], a.lo_in[base + src[u]], pol);
                 } else if (kk[u] < a.key_limit) {
                     st_keep(a.perm_out + gg[u], rr[u].y, pol);
@@ -430,8 +429,7 @@ SortPlan plan_sort(const bm_context* ctx, int64_t n, int64_t npix) {
     const size_t smem = scatter_smem(sp.bins);
     ensure_smem_limit(reinterpret_cast<const void*>(rs_scatter_kernel<false>), smem);
     ensure_smem_limit(reinterpret_cast<const void*>(rs_scatter_kernel<true>), smem);
-    ensure_smem_limit(reinterpret_cast<const void*>(rs_hist_kernel<false>), sizeof(uint32_t) * IG_WARPS * sp.bins);
-    ensure_smem_limit(reinterpret_cast<const void*>(rs_hist_kernel<true>), sizeof(uint32_t) * IG_WARPS * sp.bins);
+    ensure_smem_limit(reinterpret_cast<const void*>(rs_hist_kernel), sizeof(uint32_t) * IG_WARPS * sp.bins);
     int per_sm = blocks_per_sm(reinterpret_cast<const void*>(rs_scatter_kernel<true>), SC_THREADS, smem);
     if (per_sm < 1) per_sm = 1;
     // four waves of equal ranges keep the tail short
@@ -486,15 +484,19 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
     // of the trig pairs when the angles were given).
     DevBuf<uint32_t> hist((size_t)sp.bins * sp.grid);
     DevBuf<uint4> rec_a, rec_b;
+    DevBuf<uint32_t> keys_b;
     DevBuf<float2> lo_a, lo_b;
     if (sp.passes > 1) {
         rec_a.alloc(n);
+        keys_b.alloc(n);
         if (has_lo) lo_a.alloc(n);
     }
     if (sp.passes > 2) {
         rec_b.alloc(n);
         if (has_lo) lo_b.alloc(n);
     }
+    uint32_t* kin = keys_a.get();
+    uint32_t* kout = keys_b.get();
     const size_t smem = scatter_smem(sp.bins);
     const uint4* rin = nullptr;  // the first pass reads keys, indices and trig in time order
     uint4* rout = rec_a.get();
@@ -505,18 +507,13 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
         {
             ScopedTimer ht(ctx, "ingest_hist");
             const size_t hsm = sizeof(uint32_t) * IG_WARPS * sp.bins;
-            if (rin)
-                rs_hist_kernel<true><<<sp.grid, IG_THREADS, hsm, s>>>(nullptr, rin, n, sp.range, shift, sp.bins,
-                                                                      sp.grid, hist.get());
-            else
-                rs_hist_kernel<false><<<sp.grid, IG_THREADS, hsm, s>>>(keys_a.get(), nullptr, n, sp.range, shift,
-                                                                       sp.bins, sp.grid, hist.get());
+            rs_hist_kernel<<<sp.grid, IG_THREADS, hsm, s>>>(kin, n, sp.range, shift, sp.bins, sp.grid, hist.get());
             BM_LAUNCH_CHECK();
         }
         exclusive_scan_u32(hist.get(), hist.get(), (int64_t)sp.bins * sp.grid, s);
         ScatterArgs a{};
         a.rec_in = rin;
-        a.keys_in = keys_a.get();
+        a.keys_in = kin;
         a.hi_in = p->cs_hi_t.get();
         a.lo_in = lin;
         a.n = n;
@@ -528,9 +525,11 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
         ScopedTimer st(ctx, "ingest_scatter");
         if (pass + 1 < sp.passes) {
             a.rec_out = rout;
+            a.keys_out = kout;
             a.lo_out = lout;
             rs_scatter_kernel<false><<<sp.grid, SC_THREADS, smem, s>>>(a);
             BM_LAUNCH_CHECK();
+            std::swap(kin, kout);
             rin = rout;
             rout = (rout == rec_a.get()) ? rec_b.get() : rec_a.get();
             lin = has_lo ? lout : nullptr;

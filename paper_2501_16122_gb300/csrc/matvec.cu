@@ -259,23 +259,24 @@ gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __rest
                     acc[NC - 1] = df_add(acc[NC - 1], df_mul(val, df32{h.y, l.y}));
                 }
             };
-            // Four samples per lane in flight (the gathers g[perm] are
+            // Eight samples per lane in flight (the gathers g[perm] are
             // independent); the lane's samples are still added in order.
+            constexpr int U = 8;
             int i = lane;
-            for (; i + 96 < len; i += 128) {
-                uint32_t t[4];
-                G gv[4];
-                float2 h[4], l[4];
+            for (; i + 32 * (U - 1) < len; i += 32 * U) {
+                uint32_t t[U];
+                G gv[U];
+                float2 h[U], l[U];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) t[u] = perm[b + i + 32 * u];
+                for (int u = 0; u < U; ++u) t[u] = perm[b + i + 32 * u];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < U; ++u) {
                     gv[u] = g[t[u]];
                     h[u] = NC > 1 ? hi[b + i + 32 * u] : make_float2(0.f, 0.f);
                     l[u] = (NC > 1 && lo) ? lo[b + i + 32 * u] : make_float2(0.f, 0.f);
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) add(t[u], gv[u], h[u], l[u]);
+                for (int u = 0; u < U; ++u) add(t[u], gv[u], h[u], l[u]);
             }
             for (; i < len; i += 32) {
                 const int64_t si = b + i;
