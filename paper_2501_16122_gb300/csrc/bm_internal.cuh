@@ -165,6 +165,13 @@ struct bm_inv_noise {
     bm::DevBuf<float2> spec_df;    // the same as double-float (hi, lo) pairs
     bm::DevBuf<float2> tw32;       // [fft_n32] exp(-2 pi i e / N)
     bm::DevBuf<double2> tw64;      // [fft_n64]
+    // Filter tiling per tile length: [ndet + 1] prefix of tiles per detector
+    // on the device, built on first use.
+    struct TilePlan {
+        bm::DevBuf<int64_t> tile_start;
+        int64_t tiles_per_chunk = 0, ntiles = 0;
+    };
+    std::map<int, TilePlan> tile_plans;
 };
 
 struct bm_precond {

@@ -511,26 +511,35 @@ size_t toeplitz_smem(int L) {
 
 // --------------------------------------------------------------- wrappers
 struct ToeplitzPlan {
-    DevBuf<int64_t> tile_start;
     TzGeom geo;
 };
 
+// Tiles of TT outputs per chunk of each detector; the per-detector tile
+// prefix is uploaded once per noise model and tile length.
 static void plan_toeplitz(bm_inv_noise* n, int TT, ToeplitzPlan& tp) {
-    int64_t maxlen = 0;
-    for (int d = 0; d < n->ndet; ++d) maxlen = std::max(maxlen, n->h_det_off[d + 1] - n->h_det_off[d]);
-    const int64_t eff_chunk = std::min(n->chunk_len, maxlen);
-    const int64_t tpc = (eff_chunk + TT - 1) / TT;
-    std::vector<int64_t> ts(n->ndet + 1, 0);
-    for (int d = 0; d < n->ndet; ++d) {
-        const int64_t len = n->h_det_off[d + 1] - n->h_det_off[d];
-        const int64_t nch = (len + n->chunk_len - 1) / n->chunk_len;
-        ts[d + 1] = ts[d] + nch * tpc;
+    auto it = n->tile_plans.find(TT);
+    if (it == n->tile_plans.end()) {
+        int64_t maxlen = 0;
+        for (int d = 0; d < n->ndet; ++d) maxlen = std::max(maxlen, n->h_det_off[d + 1] - n->h_det_off[d]);
+        const int64_t eff_chunk = std::min(n->chunk_len, maxlen);
+        const int64_t tpc = (eff_chunk + TT - 1) / TT;
+        std::vector<int64_t> ts(n->ndet + 1, 0);
+        for (int d = 0; d < n->ndet; ++d) {
+            const int64_t len = n->h_det_off[d + 1] - n->h_det_off[d];
+            const int64_t nch = (len + n->chunk_len - 1) / n->chunk_len;
+            ts[d + 1] = ts[d] + nch * tpc;
+        }
+        bm_inv_noise::TilePlan& pl = n->tile_plans[TT];
+        pl.tile_start.alloc(n->ndet + 1);
+        BM_CUDA(cudaMemcpyAsync(pl.tile_start.get(), ts.data(), sizeof(int64_t) * (n->ndet + 1),
+                                cudaMemcpyHostToDevice, n->ctx->stream));
+        BM_CUDA(cudaStreamSynchronize(n->ctx->stream));  // ts is a host temporary
+        pl.tiles_per_chunk = tpc;
+        pl.ntiles = ts[n->ndet];
+        it = n->tile_plans.find(TT);
     }
-    tp.tile_start.alloc(n->ndet + 1);
-    BM_CUDA(cudaMemcpyAsync(tp.tile_start.get(), ts.data(), sizeof(int64_t) * (n->ndet + 1), cudaMemcpyHostToDevice,
-                            n->ctx->stream));
-    BM_CUDA(cudaStreamSynchronize(n->ctx->stream));  // ts is a host temporary
-    tp.geo = TzGeom{n->det_off.get(), tp.tile_start.get(), n->ndet, n->chunk_len, tpc, ts[n->ndet]};
+    tp.geo = TzGeom{n->det_off.get(), it->second.tile_start.get(), n->ndet, n->chunk_len,
+                    it->second.tiles_per_chunk, it->second.ntiles};
 }
 
 template <typename T, int R, class Src>
@@ -741,6 +750,7 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
                     apply_toeplitz_f32(n, SrcPlainF32{y32}, z32);
                 }
                 // scatter with the same FP32 trig the gather used (symmetric operator)
+                ScopedTimer timer(ctx, "toeplitz_pt");
                 gather_reduce<float>(p, kept_items(pc), z32, nullptr, nullptr, true, qr);
             } else {
                 // FP64, or the refinement operator: the same with a
@@ -758,6 +768,7 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
                     BM_LAUNCH_CHECK();
                     apply_toeplitz_f64(n, SrcPlain{y64}, z64, refine);
                 }
+                ScopedTimer timer(ctx, "toeplitz_pt");
                 gather_reduce<double>(p, kept_items(pc), z64, nullptr, p->cs_lo_s.get(), refine, qr);
             }
         }
