@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--horizon", type=float, default=20.0, help="config4: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=20.0, help="config4: mean arrivals per second")
     ap.add_argument("--nrhs", type=int, default=64, help="config3: right-hand sides")
+    ap.add_argument("--rhs-path", choices=["carried", "gather"], default="carried",
+                    help="config1: the TOD sorted along with the pointing (carried, default) or "
+                         "gathered through the permutation by the solve (gather)")
     return ap.parse_args()
 
 
@@ -211,6 +214,8 @@ def workload_config(args):
             "nsamples": args.ndet * args.ns, "solver": "IQU", "noise": "white", "tod_dtype": "f32",
             "trig_dtype": "f32 (precomputed cos 2psi, sin 2psi)", "tol": args.tol, "min_hits": 3, "max_cond": 1e3,
             "parallelism": f"replicas x{args.gpus}",
+            "tod_path": ("sorted along with the pointing, read in pixel order by the RHS"
+                         if args.rhs_path == "carried" else "gathered through the sort permutation by the RHS"),
             "l2": "inputs (17 GB) larger than L2 (129 MB); no flush needed"}
 
 
@@ -242,13 +247,20 @@ def run_gb300(args, rank, world, local_rank):
     out = torch.empty(e.npix * 3, dtype=torch.float64, device="cuda")
     infos = []
 
+    carried = args.rhs_path == "carried"
+
     def step(src_pix, src_trig, src_tod, tod_ready=None):
-        p = L.bm_pointing_create_trig(ctx, e.npix, src_pix, src_trig[0], src_trig[1], L.BM_SOLVER_IQU)
+        if carried:  # the TOD rides through the pixel sort; the solve reads it in sorted order
+            p = L.bm_pointing_create_with_tod(ctx, e.npix, src_pix, src_tod, cos2psi=src_trig[0],
+                                              sin2psi=src_trig[1])
+        else:
+            p = L.bm_pointing_create_trig(ctx, e.npix, src_pix, src_trig[0], src_trig[1], L.BM_SOLVER_IQU)
         n = L.bm_inv_noise_create_diag(ctx, e.det_offsets, inv_var)
         pc = L.bm_blockdiag_precond_create(p, n, 3, 1e3)
         if tod_ready is not None:  # the TOD upload ran beside the ingest and the preconditioner
             stream.wait_event(tod_ready)
-        st, info = L.bm_pcg_solve(p, n, pc, src_tod, 1, out, args.tol, 200, L.BM_PREC_MIXED)
+        st, info = L.bm_pcg_solve(p, n, pc, None if carried else src_tod, 1, out, args.tol, 200,
+                                  L.BM_PREC_MIXED)
         infos.append((st, info[0]))
         L.bm_precond_destroy(pc)
         L.bm_inv_noise_destroy(n)
@@ -345,8 +357,10 @@ def run_gb300(args, rank, world, local_rank):
     hist_bytes = 0
     for ps in range(passes):
         last = ps == passes - 1
-        rd = 4 + (16 if ps > 0 else 8)                     # keys + records, or keys + trig pair in time order
-        wr = (12 * n_valid / nt) if last else 20           # perm + trig of kept samples, or records + keys
+        # keys + records, or keys + trig pair (+ TOD) in time order
+        rd = 4 + (16 if ps > 0 else (12 if carried else 8))
+        # perm + trig (+ TOD) of kept samples, or records + keys
+        wr = ((16 if carried else 12) * n_valid / nt) if last else 20
         scatter_bytes += (rd + wr) * nt
         hist_bytes += 4 * nt                               # keys
     step_bytes = {
@@ -354,7 +368,7 @@ def run_gb300(args, rank, world, local_rank):
         "ingest_hist": hist_bytes,
         "ingest_scatter": scatter_bytes,
         "blocks": 20 * n_valid_kept(hits, kept),          # perm + trig pair in, weighted pair out
-        "rhs": 16 * n_valid_kept(hits, kept),             # perm + d + trig pair
+        "rhs": 16 * n_valid_kept(hits, kept),             # perm + d (sorted or gathered) + trig pair
         "matvec_white_f32": alg_bytes * fam.get("matvec_white_f32", {}).get("launches", 0) / max(args.steps, 1),
     }
     rooflines = {}
@@ -381,8 +395,14 @@ def run_gb300(args, rank, world, local_rank):
         def e2e_step():
             # The pointing goes to the library as page-locked host buffers: its
             # ingest reads them once over the host link, with no staging copy.
-            # The TOD is needed only by the solve: it is uploaded on a second
-            # stream while the pointing is ingested.
+            # A carried TOD is read the same way by the ingest; otherwise it is
+            # needed only by the solve and is uploaded on a second stream while
+            # the pointing is ingested.
+            if carried:
+                step(h_pix, (h_c, h_s), h_tod)
+                h_out.copy_(out, non_blocking=True)
+                torch.cuda.current_stream().synchronize()
+                return
             with torch.cuda.stream(upload):
                 c = h_tod.to("cuda", non_blocking=True)
                 ready = torch.cuda.Event()

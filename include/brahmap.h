@@ -143,6 +143,22 @@ bm_status bm_pointing_create(bm_context* ctx, int64_t npix, int64_t nsamples, co
 bm_status bm_pointing_create_trig(bm_context* ctx, int64_t npix, int64_t nsamples, const int32_t* pix,
                                   const float* cos2psi, const float* sin2psi, bm_solver_type solver,
                                   bm_pointing** out);
+/* bm_pointing_create (psi given, cos2psi = sin2psi = NULL) or
+ * bm_pointing_create_trig (cos2psi and sin2psi given, psi = NULL) that also
+ * sorts one FP32 TOD d [nsamples] (device or page-locked host memory) along
+ * with the samples: the handle keeps d of the kept samples in pixel-sorted
+ * order (4 bytes a sample), and bm_rhs / bm_pcg_solve called with tod = NULL
+ * read it as a stream instead of gathering d through the permutation.  The
+ * operator is the one the other constructors build; d is copied, so the
+ * caller's array may be freed on return.  The carried TOD serves one
+ * right-hand side of a white-noise system (a Toeplitz N^-1 filters in time
+ * order).  This entry point has no counterpart in the paper.  Errors as
+ * bm_pointing_create; BM_ERR_INVALID when both or neither of psi and the trig
+ * pair are given, or tod is NULL. */
+bm_status bm_pointing_create_with_tod(bm_context* ctx, int64_t npix, int64_t nsamples, const int32_t* pix,
+                                      const void* psi, bm_dtype psi_dtype, const float* cos2psi,
+                                      const float* sin2psi, const float* tod, bm_solver_type solver,
+                                      bm_pointing** out);
 void bm_pointing_destroy(bm_pointing* p);
 /* hits device int32 [npix]: samples per pixel (flagged samples excluded). */
 bm_status bm_pointing_get_hits(const bm_pointing* p, int32_t* hits);
@@ -196,7 +212,10 @@ bm_status bm_precond_apply(bm_precond* pc, const double* r, double* z);
 
 /* b = P^T N^-1 d_m (Eq. 6) where d_m is d with the samples of flagged or
  * masked pixels set to 0: tod device [nrhs][nsamples] of dtype tod_dtype,
- * b device FP64 [nrhs][npix][ncomp].  FP64 arithmetic, deterministic. */
+ * b device FP64 [nrhs][npix][ncomp].  FP64 arithmetic, deterministic.
+ * tod = NULL uses the TOD the pointing was created with
+ * (bm_pointing_create_with_tod; nrhs = 1, white noise, tod_dtype unused but
+ * checked); else BM_ERR_INVALID. */
 bm_status bm_rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod,
                  bm_dtype tod_dtype, int32_t nrhs, double* b);
 
@@ -228,7 +247,8 @@ bm_status bm_matvec_white_static(bm_pointing* p, bm_inv_noise* n, bm_precond* pc
 
 /* GLS maps by block-preconditioned CG (Eq. 5-7): tod [nrhs][nsamples]
  * (tod_dtype) in device memory, or in page-locked host memory, which is then
- * uploaded into a library workspace first; map_out device FP64
+ * uploaded into a library workspace first, or NULL for the TOD the pointing
+ * was created with (as bm_rhs); map_out device FP64
  * [nrhs][npix][ncomp] (NaN on masked
  * pixels).  x0 = 0; stops when ||b - A x||_2 <= tol ||b||_2 (per RHS) or
  * after maxiter PCG iterations (maxiter counts inner iterations in mixed

@@ -95,6 +95,8 @@ _SIGS = {
     "bm_ang2pix_ring": ([_P, _i64, _i64, _P, _P, _P], ctypes.c_int),
     "bm_pointing_create": ([_P, _i64, _i64, _P, _P, ctypes.c_int, ctypes.c_int, _PP], ctypes.c_int),
     "bm_pointing_create_trig": ([_P, _i64, _i64, _P, _P, _P, ctypes.c_int, _PP], ctypes.c_int),
+    "bm_pointing_create_with_tod": ([_P, _i64, _i64, _P, _P, ctypes.c_int, _P, _P, _P, ctypes.c_int, _PP],
+                                    ctypes.c_int),
     "bm_pointing_destroy": ([_P], None),
     "bm_pointing_get_hits": ([_P, _P], ctypes.c_int),
     "bm_pointing_apply": ([_P, _P, _P], ctypes.c_int),
@@ -252,6 +254,21 @@ def bm_pointing_create_trig(ctx, npix: int, pix, cos2psi, sin2psi, solver: int =
     return out
 
 
+def bm_pointing_create_with_tod(ctx, npix: int, pix, tod, psi=None, cos2psi=None, sin2psi=None,
+                                solver: int = BM_SOLVER_IQU):
+    """A pointing that also carries one FP32 TOD in pixel-sorted order: give
+    psi, or cos2psi and sin2psi.  bm_rhs / bm_pcg_solve with tod=None use it."""
+    import torch
+    out = ctypes.c_void_p()
+    _check(lib.bm_pointing_create_with_tod(
+        ctx, int(npix), pix.numel(), _in(pix, torch.int32, "pix"),
+        _in(psi, None, "psi") if psi is not None else None, _dtype_code(psi) if psi is not None else 0,
+        _in(cos2psi, torch.float32, "cos2psi") if cos2psi is not None else None,
+        _in(sin2psi, torch.float32, "sin2psi") if sin2psi is not None else None,
+        _in(tod, torch.float32, "tod"), int(solver), ctypes.byref(out)), "bm_pointing_create_with_tod")
+    return out
+
+
 def bm_pointing_destroy(p):
     lib.bm_pointing_destroy(p)
 
@@ -335,7 +352,9 @@ def bm_precond_apply(pc, r, z):
 # ---------------------------------------------------------------- system
 def bm_rhs(p, n, pc, tod, nrhs: int, b):
     import torch
-    _check(lib.bm_rhs(p, n, pc, _dev(tod, None, "tod"), _dtype_code(tod), int(nrhs), _dev(b, torch.float64, "b")),
+    # tod=None: the TOD the pointing was created with
+    _check(lib.bm_rhs(p, n, pc, _dev(tod, None, "tod") if tod is not None else None,
+                      _dtype_code(tod) if tod is not None else BM_F32, int(nrhs), _dev(b, torch.float64, "b")),
            "bm_rhs")
 
 
@@ -358,7 +377,8 @@ def bm_pcg_solve(p, n, pc, tod, nrhs: int, map_out, tol: float, maxiter: int, pr
     """Returns (status, [info dict per RHS])."""
     import torch
     infos = (bm_solve_info * int(nrhs))()
-    st = lib.bm_pcg_solve(p, n, pc, _in(tod, None, "tod"), _dtype_code(tod), int(nrhs),
+    st = lib.bm_pcg_solve(p, n, pc, _in(tod, None, "tod") if tod is not None else None,
+                          _dtype_code(tod) if tod is not None else BM_F32, int(nrhs),
                           _dev(map_out, torch.float64, "map_out"), float(tol), int(maxiter), int(prec), infos)
     if raise_on_error and st not in (BM_OK, BM_ERR_NOT_CONVERGED):
         _check(st, "bm_pcg_solve")

@@ -687,10 +687,15 @@ bm_status batched_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const v
             launch_matvec<NC>(ctx, pc, var, bb.x32, r0, std::min(per, R - r0), R, bb.q, bb.partial);
         ctx->stream = saved;
         batched_finalize_kernel<<<vgrid, threads, 0, st>>>(pc->pitem.get(), bb.partial, npix, RNC, bb.q);
+        BM_LAUNCH_CHECK();
         b_dot_kernel<<<rgrid, kRT, 0, st>>>(geo, NC, bb.pv, bb.q, bb.part);
+        BM_LAUNCH_CHECK();
         b_alpha_kernel<<<sgrid, 128, 0, st>>>(bb.part, rgrid, R, bb.st);
+        BM_LAUNCH_CHECK();
         b_update_kernel<NC><<<rgrid, kRT, 0, st>>>(geo, pc->Minv.get(), bb.e, bb.rcg, bb.z, bb.pv, bb.q, bb.st, bb.part);
+        BM_LAUNCH_CHECK();
         b_beta_kernel<<<sgrid, 128, 0, st>>>(bb.part, rgrid, R, bb.st);
+        BM_LAUNCH_CHECK();
         b_pupdate_kernel<<<rgrid, kRT, 0, st>>>(geo, NC, bb.pv, bb.z, bb.st);
         BM_LAUNCH_CHECK();
     };
@@ -715,6 +720,7 @@ bm_status batched_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const v
         }
         BM_CUDA(cudaMemcpyAsync(bb.tolr, tolr.data(), sizeof(double) * R, cudaMemcpyHostToDevice, s));
         b_init_kernel<NC><<<rgrid, kRT, 0, s>>>(geo, pc->Minv.get(), bb.r, bb.e, bb.rcg, bb.z, bb.pv, bb.part);
+        BM_LAUNCH_CHECK();
         b_init_finalize<<<sgrid, 128, 0, s>>>(bb.part, rgrid, R, bb.tolr, bb.st);
         BM_LAUNCH_CHECK();
         int it = 0;
@@ -758,7 +764,9 @@ bm_status batched_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const v
         inner_total += std::max(itmax, 1);
         ++outer;
         b_axpy_kernel<<<vgrid, threads, 0, s>>>(bb.x, bb.e, nv);
+        BM_LAUNCH_CHECK();
         b_residual_kernel<NC><<<rgrid, kRT, 0, s>>>(geo, pc->B.get(), pc->mask.get(), bb.b, bb.x, bb.r, bb.part);
+        BM_LAUNCH_CHECK();
         b_sum2_kernel<<<sgrid, 128, 0, s>>>(bb.part, rgrid, R, bb.sums);
         BM_LAUNCH_CHECK();
         BM_CUDA(cudaMemcpyAsync(hs.data(), bb.sums, sizeof(double) * R, cudaMemcpyDeviceToHost, s));

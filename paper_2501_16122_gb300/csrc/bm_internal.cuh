@@ -137,6 +137,7 @@ struct bm_pointing {
     bm::DevBuf<int32_t> hits;      // [npix]
     bm::DevBuf<float2> cs_hi_s;    // [nvalid] trig in pixel-sorted order
     bm::DevBuf<float2> cs_lo_s;
+    bm::DevBuf<float> tod_s;       // [nvalid] a TOD sorted along with the samples, or empty
 };
 
 struct bm_inv_noise {
@@ -250,7 +251,7 @@ void resolve_timers(bm_context* ctx);
 
 // Launch wrappers implemented in the .cu files.
 void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dtype, const float* cos2psi,
-            const float* sin2psi);
+            const float* sin2psi, const float* tod = nullptr, bool tod_on_host = false);
 void build_precond(bm_precond* pc);
 void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, double* q,
             bm_precision prec, int64_t nrhs);

@@ -290,28 +290,41 @@ static const void* device_readable(const bm_context* ctx, const void* ptr, const
     return a.devicePointer;
 }
 
-bm_status bm_pointing_create(bm_context* ctx, int64_t npix, int64_t nsamples, const int32_t* pix,
-                             const void* psi, bm_dtype psi_dtype, bm_solver_type solver,
-                             bm_pointing** out) {
+// The three pointing constructors: angles (psi) or FP32 trig pairs, and
+// optionally one FP32 TOD sorted along with the samples.
+static bm_status create_pointing(bm_context* ctx, int64_t npix, int64_t nsamples, const int32_t* pix,
+                                 const void* psi, bm_dtype psi_dtype, const float* cos2psi,
+                                 const float* sin2psi, const float* tod, bm_solver_type solver,
+                                 bm_pointing** out) {
     return guarded([&] {
         BM_REQUIRE(ctx && out, "ctx/out is NULL");
         *out = nullptr;
         BM_REQUIRE(npix >= 1 && npix <= (int64_t(1) << 28), "npix %lld out of [1, 2^28]", (long long)npix);
         BM_REQUIRE(nsamples >= 1 && nsamples < (int64_t(1) << 32), "nsamples out of [1, 2^32)");
-        BM_REQUIRE(pix && psi, "pix/psi is NULL");
-        BM_REQUIRE(psi_dtype == BM_F32 || psi_dtype == BM_F64, "bad psi dtype");
+        BM_REQUIRE(pix, "pix is NULL");
+        BM_REQUIRE((psi != nullptr) != (cos2psi != nullptr || sin2psi != nullptr),
+                   "give either psi or cos2psi and sin2psi");
+        BM_REQUIRE(psi || (cos2psi && sin2psi), "cos2psi/sin2psi is NULL");
+        if (psi) BM_REQUIRE(psi_dtype == BM_F32 || psi_dtype == BM_F64, "bad psi dtype");
         BM_REQUIRE(solver == BM_SOLVER_I || solver == BM_SOLVER_QU || solver == BM_SOLVER_IQU,
                    "bad solver type %d", (int)solver);
         use_device(ctx);
         pix = static_cast<const int32_t*>(device_readable(ctx, pix, "pix"));
-        psi = device_readable(ctx, psi, "psi");
+        if (psi) {
+            psi = device_readable(ctx, psi, "psi");
+        } else {
+            cos2psi = static_cast<const float*>(device_readable(ctx, cos2psi, "cos2psi"));
+            sin2psi = static_cast<const float*>(device_readable(ctx, sin2psi, "sin2psi"));
+        }
+        bool tod_on_host = false;
+        if (tod) tod = static_cast<const float*>(device_readable(ctx, tod, "tod", &tod_on_host));
         auto* p = new bm_pointing();
         p->ctx = ctx;
         p->npix = npix;
         p->nsamples = nsamples;
         p->ncomp = (int)solver;
         try {
-            ingest(p, pix, psi, psi_dtype, nullptr, nullptr);
+            ingest(p, pix, psi, psi_dtype, cos2psi, sin2psi, tod, tod_on_host);
         } catch (...) {
             delete p;
             throw;
@@ -321,35 +334,27 @@ bm_status bm_pointing_create(bm_context* ctx, int64_t npix, int64_t nsamples, co
     });
 }
 
+bm_status bm_pointing_create(bm_context* ctx, int64_t npix, int64_t nsamples, const int32_t* pix,
+                             const void* psi, bm_dtype psi_dtype, bm_solver_type solver,
+                             bm_pointing** out) {
+    if (!psi) return guarded([&]() -> bm_status { BM_REQUIRE(false, "psi is NULL"); return BM_OK; });
+    return create_pointing(ctx, npix, nsamples, pix, psi, psi_dtype, nullptr, nullptr, nullptr, solver, out);
+}
+
 bm_status bm_pointing_create_trig(bm_context* ctx, int64_t npix, int64_t nsamples, const int32_t* pix,
                                   const float* cos2psi, const float* sin2psi, bm_solver_type solver,
                                   bm_pointing** out) {
-    return guarded([&] {
-        BM_REQUIRE(ctx && out, "ctx/out is NULL");
-        *out = nullptr;
-        BM_REQUIRE(npix >= 1 && npix <= (int64_t(1) << 28), "npix %lld out of [1, 2^28]", (long long)npix);
-        BM_REQUIRE(nsamples >= 1 && nsamples < (int64_t(1) << 32), "nsamples out of [1, 2^32)");
-        BM_REQUIRE(pix && cos2psi && sin2psi, "pix/cos2psi/sin2psi is NULL");
-        BM_REQUIRE(solver == BM_SOLVER_I || solver == BM_SOLVER_QU || solver == BM_SOLVER_IQU,
-                   "bad solver type %d", (int)solver);
-        use_device(ctx);
-        pix = static_cast<const int32_t*>(device_readable(ctx, pix, "pix"));
-        cos2psi = static_cast<const float*>(device_readable(ctx, cos2psi, "cos2psi"));
-        sin2psi = static_cast<const float*>(device_readable(ctx, sin2psi, "sin2psi"));
-        auto* p = new bm_pointing();
-        p->ctx = ctx;
-        p->npix = npix;
-        p->nsamples = nsamples;
-        p->ncomp = (int)solver;
-        try {
-            ingest(p, pix, nullptr, BM_F32, cos2psi, sin2psi);
-        } catch (...) {
-            delete p;
-            throw;
-        }
-        *out = p;
-        return BM_OK;
-    });
+    if (!cos2psi || !sin2psi)
+        return guarded([&]() -> bm_status { BM_REQUIRE(false, "cos2psi/sin2psi is NULL"); return BM_OK; });
+    return create_pointing(ctx, npix, nsamples, pix, nullptr, BM_F32, cos2psi, sin2psi, nullptr, solver, out);
+}
+
+bm_status bm_pointing_create_with_tod(bm_context* ctx, int64_t npix, int64_t nsamples, const int32_t* pix,
+                                      const void* psi, bm_dtype psi_dtype, const float* cos2psi,
+                                      const float* sin2psi, const float* tod, bm_solver_type solver,
+                                      bm_pointing** out) {
+    if (!tod) return guarded([&]() -> bm_status { BM_REQUIRE(false, "tod is NULL"); return BM_OK; });
+    return create_pointing(ctx, npix, nsamples, pix, psi, psi_dtype, cos2psi, sin2psi, tod, solver, out);
 }
 
 void bm_pointing_destroy(bm_pointing* p) {
@@ -596,11 +601,21 @@ static void check_system(bm_pointing* p, bm_inv_noise* n, bm_precond* pc) {
         BM_REQUIRE(pc->n == n, "a white-noise system needs the preconditioner built from that noise");
 }
 
+// tod = NULL selects the TOD the pointing was created with (one RHS, white
+// noise: a Toeplitz filter runs in time order).
+static void check_carried_tod(const bm_pointing* p, const bm_inv_noise* n, int32_t nrhs) {
+    BM_REQUIRE(p->tod_s.get() != nullptr, "tod is NULL and the pointing was not created with a TOD");
+    BM_REQUIRE(nrhs == 1, "the TOD carried by the pointing is one right-hand side (nrhs = %d)", nrhs);
+    BM_REQUIRE(n->kind == 0, "the TOD carried by the pointing is pixel-sorted; Toeplitz noise needs the "
+                             "time-ordered TOD");
+}
+
 bm_status bm_rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod,
                  bm_dtype tod_dtype, int32_t nrhs, double* b) {
     return guarded([&] {
         check_system(p, n, pc);
-        BM_REQUIRE(tod && b, "NULL array");
+        BM_REQUIRE(b, "NULL array");
+        if (!tod) check_carried_tod(p, n, nrhs);
         BM_REQUIRE(tod_dtype == BM_F32 || tod_dtype == BM_F64, "bad tod dtype");
         BM_REQUIRE(nrhs >= 1 && nrhs <= 4096, "nrhs out of [1, 4096]");
         use_device(p->ctx);
@@ -628,7 +643,8 @@ bm_status bm_pcg_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const vo
                        int32_t maxiter, bm_precision prec, bm_solve_info* info) {
     return guarded([&] {
         check_system(p, n, pc);
-        BM_REQUIRE(tod && map_out, "NULL array");
+        BM_REQUIRE(map_out, "NULL array");
+        if (!tod) check_carried_tod(p, n, nrhs);
         BM_REQUIRE(tod_dtype == BM_F32 || tod_dtype == BM_F64, "bad tod dtype");
         BM_REQUIRE(nrhs >= 1 && nrhs <= 4096, "nrhs out of [1, 4096]");
         BM_REQUIRE(tol > 0 && tol < 1, "tol out of (0, 1)");
@@ -638,7 +654,7 @@ bm_status bm_pcg_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const vo
         // A page-locked host TOD is uploaded first: the solve reads it in
         // pixel order, a random access pattern the host link serves poorly.
         bool on_host = false;
-        tod = device_readable(p->ctx, tod, "tod", &on_host);
+        if (tod) tod = device_readable(p->ctx, tod, "tod", &on_host);
         if (on_host) {
             const size_t bytes = (size_t)nrhs * (size_t)p->nsamples * (tod_dtype == BM_F64 ? 8 : 4);
             void* dev = workspace(p->ctx, "tod_upload", bytes);

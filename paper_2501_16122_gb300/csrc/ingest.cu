@@ -69,6 +69,11 @@ __device__ __forceinline__ uint64_t l2_keep_policy() {
 __device__ __forceinline__ void st_keep(uint32_t* p, uint32_t v, uint64_t pol) {
     asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
 }
+__device__ __forceinline__ void st_keep(uint4* p, uint4 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y),
+                 "r"(v.z), "r"(v.w), "l"(pol)
+                 : "memory");
+}
 __device__ __forceinline__ void st_keep(float2* p, float2 v, uint64_t pol) {
     asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y), "l"(pol)
                  : "memory");
@@ -78,7 +83,8 @@ __device__ __forceinline__ void st_keep(float2* p, float2 v, uint64_t pol) {
 // Checks pixel indices and angles (or the given cos/sin pairs, |.| <= 1),
 // copies pix, writes the sort keys (flagged samples get key npix and sort
 // last) and the time-ordered trig pairs.  counters[0] = invalid samples,
-// counters[1] = flagged samples.
+// counters[1] = flagged samples.  With tod_dst, also copies the TOD
+// (a host-memory source read once over the host link).
 // MODE: kTrigIn (cos/sin given), kPsi64 or kPsi32 (angles given).
 constexpr int kTrigIn = 0, kPsi64 = 1, kPsi32 = 2;
 template <int MODE>
@@ -86,6 +92,7 @@ __global__ void validate_kernel(const int32_t* __restrict__ pix, const void* __r
                                 const float* __restrict__ c32, const float* __restrict__ s32, int64_t n,
                                 int64_t npix, int32_t* __restrict__ pix_out, uint32_t* __restrict__ keys,
                                 float2* __restrict__ hi, float2* __restrict__ lo,
+                                const float* __restrict__ tod_src, float* __restrict__ tod_dst,
                                 unsigned long long* __restrict__ counters) {
     unsigned nbad = 0, nflag = 0;
     auto one = [&](int64_t i, int32_t p, float c, float s, double a) {
@@ -137,6 +144,13 @@ __global__ void validate_kernel(const int32_t* __restrict__ pix, const void* __r
         for (int u = 0; u < U; ++u) {
             const int64_t i = i0 + u * stride;
             if (i < n) one(i, p[u], c[u], sv[u], a[u]);
+        }
+        if (tod_dst) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t i = i0 + u * stride;
+                if (i < n) tod_dst[i] = __ldcs(tod_src + i);
+            }
         }
     }
     nbad = __reduce_add_sync(0xffffffffu, nbad);
@@ -239,14 +253,17 @@ __device__ void scan_bins(const uint32_t* cnt, uint32_t* start, int bins, uint32
         }
 }
 
-// A sample between passes: one 16-byte record {key, sample index, cos, sin}
-// (one store stream instead of three: the scatter's short digit runs then
-// fill whole lines, which measured twice as fast).
+// A sample between passes: one 16-byte record {TOD value, sample index,
+// cos, sin} (one store stream instead of three: the scatter's short digit
+// runs then fill whole lines, which measured twice as fast).  The keys travel
+// as their own stream, so the first word of the record is free for the TOD
+// sample when one is sorted along (else it is unused).
 struct ScatterArgs {
     const uint4* rec_in;      // records of the previous pass, or null on the first pass:
-                              //   then the sample index itself and the trig pairs in time order
+                              //   then the sample index itself, the trig pairs and the TOD in time order
     const uint32_t* keys_in;  // keys in this pass's input order
     const float2* hi_in;
+    const float* tod_in;      // first pass: the TOD in time order, or null
     const float2* lo_in;      // lo halves of the trig pairs in this pass's input order, or null
     int64_t n;
     int64_t range;
@@ -256,6 +273,7 @@ struct ScatterArgs {
     uint32_t* keys_out;
     uint32_t* perm_out;    // last pass: sample indices (perm) and trig pairs of the kept samples
     float2* hi_out;
+    float* tod_out;        // last pass: the TOD of the kept samples in sorted order, or null
     float2* lo_out;        // every pass with lo_in: the lo halves in this pass's output order
     uint32_t key_limit;    // last pass: samples with keys >= key_limit (flagged) get no entry
 };
@@ -271,7 +289,7 @@ inline size_t scatter_smem(int bins) {
 // time the rest of the sample (index, trig pair, lo half) is read back from
 // the tile's window of the input, which the key loads have just brought
 // into L2.
-template <bool LAST>
+template <bool LAST, bool FIRST>
 __global__ void __launch_bounds__(SC_THREADS, 2) rs_scatter_kernel(ScatterArgs a) {
     extern __shared__ __align__(16) uint32_t ss[];
     uint32_t* s_keys = ss;
@@ -352,7 +370,7 @@ __global__ void __launch_bounds__(SC_THREADS, 2) rs_scatter_kernel(ScatterArgs a
         //    each sample read back from the input window; four per thread in
         //    flight
         for (int j0 = threadIdx.x; j0 < cnt; j0 += 4 * SC_THREADS) {
-            uint32_t kk[4], gg[4], src[4];
+            uint32_t kk[4];
             uint4 rr[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -360,28 +378,33 @@ __global__ void __launch_bounds__(SC_THREADS, 2) rs_scatter_kernel(ScatterArgs a
                 kk[u] = kNoDigit;
                 if (j < cnt) {
                     kk[u] = s_keys[j];
-                    src[u] = s_src[j];
-                    const uint32_t d = (kk[u] >> a.shift) & dmask;
-                    gg[u] = run_base[d] + (uint32_t)j - tstart[d];
-                    if (a.rec_in) {
-                        rr[u] = a.rec_in[base + src[u]];
+                    const uint32_t src = s_src[j];
+                    if (!FIRST) {
+                        rr[u] = a.rec_in[base + src];
                     } else {
-                        const float2 h = a.hi_in[base + src[u]];
-                        rr[u] = make_uint4(kk[u], (uint32_t)(base + src[u]), __float_as_uint(h.x), __float_as_uint(h.y));
+                        const float2 h = a.hi_in[base + src];
+                        const float d = a.tod_in ? a.tod_in[base + src] : 0.f;
+                        rr[u] = make_uint4(__float_as_uint(d), (uint32_t)(base + src), __float_as_uint(h.x),
+                                           __float_as_uint(h.y));
                     }
                 }
             }
+            // the output positions while the loads are in flight
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 if (kk[u] == kNoDigit) continue;
+                const int j = j0 + u * SC_THREADS;
+                const uint32_t d = (kk[u] >> a.shift) & dmask;
+                const uint32_t g = run_base[d] + (uint32_t)j - tstart[d];
                 if (!LAST) {
-                    a.rec_out[gg[u]] = make_uint4(kk[u], rr[u].y, rr[u].z, rr[u].w);
-                    a.keys_out[gg[u]] = kk[u];
-                    if (a.lo_in) st_keep(a.lo_out + gg[u], a.lo_in[base + src[u]], pol);
+                    a.rec_out[g] = rr[u];
+                    a.keys_out[g] = kk[u];
+                    if (a.lo_in) st_keep(a.lo_out + g, a.lo_in[base + s_src[j]], pol);
                 } else if (kk[u] < a.key_limit) {
-                    st_keep(a.perm_out + gg[u], rr[u].y, pol);
-                    st_keep(a.hi_out + gg[u], make_float2(__uint_as_float(rr[u].z), __uint_as_float(rr[u].w)), pol);
-                    if (a.lo_in) st_keep(a.lo_out + gg[u], a.lo_in[base + src[u]], pol);
+                    st_keep(a.perm_out + g, rr[u].y, pol);
+                    st_keep(a.hi_out + g, make_float2(__uint_as_float(rr[u].z), __uint_as_float(rr[u].w)), pol);
+                    if (a.tod_out) st_keep(reinterpret_cast<uint32_t*>(a.tod_out) + g, rr[u].x, pol);
+                    if (a.lo_in) st_keep(a.lo_out + g, a.lo_in[base + s_src[j]], pol);
                 }
             }
         }
@@ -427,10 +450,12 @@ SortPlan plan_sort(const bm_context* ctx, int64_t n, int64_t npix) {
     sp.bits = (nbits + sp.passes - 1) / sp.passes;
     sp.bins = 1 << sp.bits;
     const size_t smem = scatter_smem(sp.bins);
-    ensure_smem_limit(reinterpret_cast<const void*>(rs_scatter_kernel<false>), smem);
-    ensure_smem_limit(reinterpret_cast<const void*>(rs_scatter_kernel<true>), smem);
+    ensure_smem_limit(reinterpret_cast<const void*>(rs_scatter_kernel<false, true>), smem);
+    ensure_smem_limit(reinterpret_cast<const void*>(rs_scatter_kernel<false, false>), smem);
+    ensure_smem_limit(reinterpret_cast<const void*>(rs_scatter_kernel<true, true>), smem);
+    ensure_smem_limit(reinterpret_cast<const void*>(rs_scatter_kernel<true, false>), smem);
     ensure_smem_limit(reinterpret_cast<const void*>(rs_hist_kernel), sizeof(uint32_t) * IG_WARPS * sp.bins);
-    int per_sm = blocks_per_sm(reinterpret_cast<const void*>(rs_scatter_kernel<true>), SC_THREADS, smem);
+    int per_sm = blocks_per_sm(reinterpret_cast<const void*>(rs_scatter_kernel<true, false>), SC_THREADS, smem);
     if (per_sm < 1) per_sm = 1;
     // four waves of equal ranges keep the tail short
     const int64_t want = (int64_t)ctx->num_sms * per_sm * 4;
@@ -444,7 +469,7 @@ SortPlan plan_sort(const bm_context* ctx, int64_t n, int64_t npix) {
 }  // namespace
 
 void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dtype, const float* cos2psi,
-            const float* sin2psi) {
+            const float* sin2psi, const float* tod, bool tod_on_host) {
     bm_context* ctx = p->ctx;
     cudaStream_t s = ctx->stream;
     ScopedTimer timer(ctx, "ingest");
@@ -458,6 +483,9 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
     p->cs_hi_t.alloc(n);
     if (has_lo) p->cs_lo_t.alloc(n);
     DevBuf<uint32_t> keys_a(n);
+    DevBuf<float> tod_copy;  // a host TOD, copied by the validation pass
+    if (tod && tod_on_host) tod_copy.alloc(n);
+    const float* tod_t = tod_on_host ? tod_copy.get() : tod;
     DevBuf<unsigned long long> counters(2);
     BM_CUDA(cudaMemsetAsync(counters.get(), 0, 2 * sizeof(unsigned long long), s));
     {
@@ -466,7 +494,8 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
                                : (psi_dtype == BM_F64 ? validate_kernel<kPsi64> : validate_kernel<kPsi32>);
         const int grid = resident_grid(ctx, kern, threads, (n + threads - 1) / threads);
         kern<<<grid, threads, 0, s>>>(pix, psi, cos2psi, sin2psi, n, npix, p->pix.get(), keys_a.get(),
-                                      p->cs_hi_t.get(), p->cs_lo_t.get(), counters.get());
+                                      p->cs_hi_t.get(), p->cs_lo_t.get(), tod_on_host ? tod : nullptr,
+                                      tod_copy.get(), counters.get());
         BM_LAUNCH_CHECK();
     }
     unsigned long long h_cnt[2] = {0, 0};
@@ -479,6 +508,8 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
     p->perm.alloc(nvalid > 0 ? nvalid : 1);
     p->cs_hi_s.alloc(nvalid > 0 ? nvalid : 1);
     if (has_lo) p->cs_lo_s.alloc(nvalid > 0 ? nvalid : 1);
+    if (tod) p->tod_s.alloc(nvalid > 0 ? nvalid : 1);
+    else p->tod_s.release();
 
     // Ping-pong record buffers of the intermediate passes (and the lo halves
     // of the trig pairs when the angles were given).
@@ -515,6 +546,7 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
         a.rec_in = rin;
         a.keys_in = kin;
         a.hi_in = p->cs_hi_t.get();
+        a.tod_in = pass == 0 ? tod_t : nullptr;
         a.lo_in = lin;
         a.n = n;
         a.range = sp.range;
@@ -527,7 +559,8 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
             a.rec_out = rout;
             a.keys_out = kout;
             a.lo_out = lout;
-            rs_scatter_kernel<false><<<sp.grid, SC_THREADS, smem, s>>>(a);
+            if (pass == 0) rs_scatter_kernel<false, true><<<sp.grid, SC_THREADS, smem, s>>>(a);
+            else rs_scatter_kernel<false, false><<<sp.grid, SC_THREADS, smem, s>>>(a);
             BM_LAUNCH_CHECK();
             std::swap(kin, kout);
             rin = rout;
@@ -537,9 +570,11 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
         } else {
             a.perm_out = p->perm.get();
             a.hi_out = p->cs_hi_s.get();
+            a.tod_out = tod ? p->tod_s.get() : nullptr;
             a.lo_out = has_lo ? p->cs_lo_s.get() : nullptr;
             a.key_limit = (uint32_t)npix;
-            rs_scatter_kernel<true><<<sp.grid, SC_THREADS, smem, s>>>(a);
+            if (pass == 0) rs_scatter_kernel<true, true><<<sp.grid, SC_THREADS, smem, s>>>(a);
+            else rs_scatter_kernel<true, false><<<sp.grid, SC_THREADS, smem, s>>>(a);
             BM_LAUNCH_CHECK();
         }
     }

@@ -213,7 +213,9 @@ white_matvec_f64_kernel(const int32_t* __restrict__ item_pix, const int64_t* __r
 // ---------------------------------------------- pixel-sorted gather-reduce
 // q_p partial = sum over item samples of g[perm_i] * f * v_i, where
 // f = w_d(perm_i) when `weighted`, else 1, and v_i the pointing row.  G is
-// float or double.  Two arithmetic forms:
+// float or double.  With gs (an FP32 TOD already in pixel-sorted order) the
+// value is gs[i], read as a stream, instead of the gather g[perm_i].  Two
+// arithmetic forms:
 //   DF = false: FP64 products and sums (trig hi + lo), as the FP64 path needs;
 //   DF = true : double-float products and sums on the FP32 pipes (~48 bits);
 //               the trig pair is (hi, lo) when present, else the exact hi.
@@ -222,8 +224,9 @@ __global__ void __launch_bounds__(kWarps * 32)
 gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ item_beg,
                      const int32_t* __restrict__ item_len, int64_t nitems,
                      const uint32_t* __restrict__ perm, const float2* __restrict__ hi,
-                     const float2* __restrict__ lo, const G* __restrict__ g, bool weighted, DetTables dt,
-                     const double* __restrict__ white, int ndet, double* __restrict__ partial) {
+                     const float2* __restrict__ lo, const G* __restrict__ g, const float* __restrict__ gs,
+                     bool weighted, DetTables dt, const double* __restrict__ white, int ndet,
+                     double* __restrict__ partial) {
     __shared__ uint32_t s_off[kMaxDetSmem + 1];
     __shared__ float2 s_w[kMaxDetSmem];
     const bool in_smem = weighted && ndet <= kMaxDetSmem;
@@ -271,7 +274,7 @@ gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __rest
                 for (int u = 0; u < U; ++u) t[u] = perm[b + i + 32 * u];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    gv[u] = g[t[u]];
+                    gv[u] = gs ? (G)gs[b + i + 32 * u] : g[t[u]];
                     h[u] = NC > 1 ? hi[b + i + 32 * u] : make_float2(0.f, 0.f);
                     l[u] = (NC > 1 && lo) ? lo[b + i + 32 * u] : make_float2(0.f, 0.f);
                 }
@@ -283,7 +286,7 @@ gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __rest
                 const uint32_t t = perm[si];
                 const float2 h = NC > 1 ? hi[si] : make_float2(0.f, 0.f);
                 const float2 l = (NC > 1 && lo) ? lo[si] : make_float2(0.f, 0.f);
-                add(t, g[t], h, l);
+                add(t, gs ? (G)gs[si] : g[t], h, l);
             }
 #pragma unroll
             for (int c = 0; c < NC; ++c) acc[c] = df_warp_sum(acc[c]);
@@ -313,13 +316,13 @@ gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __rest
 #pragma unroll
                 for (int u = 0; u < 4; ++u) t[u] = perm[b + i + 32 * u];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) gv[u] = g[t[u]];
+                for (int u = 0; u < 4; ++u) gv[u] = gs ? (G)gs[b + i + 32 * u] : g[t[u]];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) add(t[u], gv[u], b + i + 32 * u);
             }
             for (; i < len; i += 32) {
                 const uint32_t t = perm[b + i];
-                add(t, g[t], b + i);
+                add(t, gs ? (G)gs[b + i] : g[t], b + i);
             }
 #pragma unroll
             for (int c = 0; c < NC; ++c) acc[c] = warp_sum(acc[c]);
@@ -750,7 +753,7 @@ static void gather_reduce_f32(bm_pointing* p, const ItemsView& it, const float* 
 
 template <typename G>
 static void gather_reduce(bm_pointing* p, const ItemsView& it, const G* g, const bm_inv_noise* wn,
-                          const float2* lo, bool df, double* q) {
+                          const float2* lo, bool df, double* q, const float* gs = nullptr) {
     bm_context* ctx = p->ctx;
     const int nc = p->ncomp;
     double* partial = workspace_as<double>(ctx, "partial", (size_t)std::max<int64_t>(it.n, 1) * nc);
@@ -764,7 +767,7 @@ static void gather_reduce(bm_pointing* p, const ItemsView& it, const G* g, const
         const int ndet = weighted ? wn->ndet : 0;
 #define BM_GR(NC, D)                                                                                           \
     gather_reduce_kernel<NC, G, D><<<resident_grid(ctx, gather_reduce_kernel<NC, G, D>, kWarps * 32, wunits), kWarps * 32, 0, ctx->stream>>>(it.pix, it.beg, it.len, it.n,          \
-                                                                         p->perm.get(), p->cs_hi_s.get(), lo, g, \
+                                                                         p->perm.get(), p->cs_hi_s.get(), lo, g, gs, \
                                                                          weighted, dt, white, ndet, partial)
         if (df) {
             if (nc == 3) BM_GR(3, true); else if (nc == 2) BM_GR(2, true); else BM_GR(1, true);
@@ -867,7 +870,9 @@ void rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dt
     for (int64_t r = 0; r < nrhs; ++r) {
         double* br = b + r * nvec;
         if (n->kind == 0) {
-            if (dt == BM_F32) {
+            if (!tod) {  // the TOD sorted along with the pointing
+                gather_reduce<float>(p, kept_items(pc), nullptr, n, p->cs_lo_s.get(), df, br, p->tod_s.get());
+            } else if (dt == BM_F32) {
                 const float* d = static_cast<const float*>(tod) + r * p->nsamples;
                 gather_reduce<float>(p, kept_items(pc), d, n, p->cs_lo_s.get(), df, br);
             } else {

@@ -104,13 +104,10 @@ blocks_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ 
         df32 acc[NS];
 #pragma unroll
         for (int j = 0; j < NS; ++j) acc[j] = {0.f, 0.f};
-        for (int i = lane; i < len; i += 32) {
-            const int64_t si = b + i;
-            const int d = det_of(offp, ndet, g.ns, g.inv_ns, perm[si]);
+        auto add = [&](int64_t si, uint32_t t, float2 h, float2 l) {
+            const int d = det_of(offp, ndet, g.ns, g.inv_ns, t);
             const float2 wv = wp[d];
             const df32 w = {wv.x, wv.y};
-            const float2 h = hi[si];
-            const float2 l = lo ? lo[si] : make_float2(0.f, 0.f);
             const df32 c = {h.x, l.x}, s = {h.y, l.y};
             if (NC == 3) {
                 const df32 wc = df_mul(w, c), ws = df_mul(w, s);
@@ -136,6 +133,26 @@ blocks_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ 
                     wcs[si] = make_float2(sw * h.x, sw * h.y);
                 }
             }
+        };
+        // four samples per lane in flight (their loads issued together); the
+        // lane's samples are still added in order
+        int i = lane;
+        for (; i + 96 < len; i += 128) {
+            uint32_t t[4];
+            float2 h[4], l[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t si = b + i + 32 * u;
+                t[u] = perm[si];
+                h[u] = hi[si];
+                l[u] = lo ? lo[si] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) add(b + i + 32 * u, t[u], h[u], l[u]);
+        }
+        for (; i < len; i += 32) {
+            const int64_t si = b + i;
+            add(si, perm[si], hi[si], lo ? lo[si] : make_float2(0.f, 0.f));
         }
 #pragma unroll
         for (int j = 0; j < NS; ++j) acc[j] = df_warp_sum(acc[j]);

@@ -308,9 +308,13 @@ template <int NC>
 void cg_iteration(Cg& cg, bm_pointing* p, bm_inv_noise* n, bm_precision prec, cudaStream_t s) {
     matvec(p, n, cg.pc, cg.p, cg.q, prec, 1);
     dot_kernel<<<RB, RT, 0, s>>>(cg.p, cg.q, cg.nvec, cg.st, cg.part);
+    BM_LAUNCH_CHECK();
     alpha_kernel<<<1, RT, 0, s>>>(cg.part, cg.st);
+    BM_LAUNCH_CHECK();
     cg_update_kernel<NC><<<RB, RT, 0, s>>>(cg.pc->Minv.get(), cg.x, cg.r, cg.z, cg.p, cg.q, cg.npix, cg.st, cg.part);
+    BM_LAUNCH_CHECK();
     beta_kernel<<<1, RT, 0, s>>>(cg.part, cg.st);
+    BM_LAUNCH_CHECK();
     p_update_kernel<<<grid_for(cg.pc->ctx, (cg.nvec + RT - 1) / RT, 16), RT, 0, s>>>(cg.p, cg.z, cg.nvec, cg.st);
     BM_LAUNCH_CHECK();
 }
@@ -389,6 +393,7 @@ bm_status solve_one(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const doubl
         // ||b||^2 (as the residual of x = 0)
         BM_CUDA(cudaMemsetAsync(cg.x, 0, sizeof(double) * cg.nvec, s));
         sub_residual_kernel<<<RB, RT, 0, s>>>(b, cg.x, rs, cg.nvec, cg.part);
+        BM_LAUNCH_CHECK();
         double* out = reinterpret_cast<double*>(cg.st) + 16;
         sum_kernel<<<1, RT, 0, s>>>(cg.part, out);
         BM_LAUNCH_CHECK();
@@ -461,7 +466,8 @@ bm_status pcg_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void*
     double* b = workspace_as<double>(ctx, "solve_b", nvec);
     bm_status first = BM_OK;
     for (int32_t r = 0; r < nrhs; ++r) {
-        const void* tr = static_cast<const char*>(tod) + (size_t)r * p->nsamples * (dt == BM_F32 ? 4 : 8);
+        const void* tr = tod ? static_cast<const char*>(tod) + (size_t)r * p->nsamples * (dt == BM_F32 ? 4 : 8)
+                             : nullptr;  // the TOD sorted along with the pointing
         rhs(p, n, pc, tr, dt, 1, b, prec == BM_PREC_MIXED);
         bm_solve_info* ir = info ? info + r : nullptr;
         bm_status st;
