@@ -170,10 +170,10 @@ KERNELS = {"ingest_validate": "validate_kernel", "ingest_hist": "rs_hist_kernel"
            "ingest_scatter": "rs_scatter_kernel", "blocks": "blocks_kernel", "rhs": "gather_reduce_kernel",
            "matvec_white_f32": "white_matvec_f32_kernel"}
 TRAFFIC = {
-    # profiles/ingest_sort_nside256_256x262144.md: 43.8 and 39.5 DRAM bytes
-    # per sample for the two scatter passes (mean 41.65) on the 67M-sample
-    # case; the traffic grows in proportion to the samples
-    "ingest_scatter": lambda n: 41.65 * n,
+    # profiles/ingest_sort_nside256_256x262144.md: 47.8 and 49.6 DRAM bytes
+    # per sample for the two scatter passes (mean 48.7; TOD sorted along) on
+    # the 67M-sample case; the traffic grows in proportion to the samples
+    "ingest_scatter": lambda n: 48.7 * n,
 }
 
 
@@ -364,11 +364,14 @@ def run_gb300(args, rank, world, local_rank):
         scatter_bytes += (rd + wr) * nt
         hist_bytes += 4 * nt                               # keys
     step_bytes = {
-        "ingest_validate": 28 * nt,                       # pix + cos + sin in; pix, key, trig pair out
+        "ingest_validate": 24 * nt,                       # pix + cos + sin in; pix, trig pair out
         "ingest_hist": hist_bytes,
         "ingest_scatter": scatter_bytes,
-        "blocks": 20 * n_valid_kept(hits, kept),          # perm + trig pair in, weighted pair out
-        "rhs": 16 * n_valid_kept(hits, kept),             # perm + d (sorted or gathered) + trig pair
+        # perm + trig pair (+ the carried TOD, whose RHS this pass also sums) in, weighted pair out
+        "blocks": (24 if carried else 20) * n_valid_kept(hits, kept),
+        # perm + gathered d + trig pair; with the carried TOD the RHS was summed
+        # with the blocks and the solve copies it (read + write of the map-sized b)
+        "rhs": 16 * n_valid_kept(hits, kept) if not carried else 2 * 8 * 3 * e.npix,
         "matvec_white_f32": alg_bytes * fam.get("matvec_white_f32", {}).get("launches", 0) / max(args.steps, 1),
     }
     rooflines = {}

@@ -196,6 +196,9 @@ struct bm_precond {
     // White noise: weighted sorted stream sqrt(w) (cos, sin) (or w for I-only).
     bm::DevBuf<float2> wcs;        // [nvalid]
     bm::DevBuf<float> w1;          // [nvalid] (I-only)
+    // White noise and a TOD carried by the pointing: b = P^T N^-1 d_m of that
+    // TOD in double-float (the mixed solve's RHS), zero on masked pixels.
+    bm::DevBuf<double> b_tod;      // [npix][ncomp] or empty
 };
 
 namespace bm {

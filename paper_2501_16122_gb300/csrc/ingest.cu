@@ -25,9 +25,11 @@
 // them once, in tile order): on this part a random 8-byte read moves about
 // 100 bytes of DRAM traffic, so gathering them through perm afterwards would
 // cost several times more.  Between passes a sample is one 16-byte record
-// {key, sample index, cos, sin}, with the keys also written alone for the
-// next pass's histogram and ranking; the last pass writes only perm and the
-// sorted trig pairs, and the CSR offsets come from a binary search per pixel
+// {TOD value, sample index, cos, sin} (the TOD word is used when a TOD is
+// sorted along), with the keys written as their own stream for the next
+// pass's histogram and ranking; the first pass takes its keys from the
+// validated pixel indices.  The last pass writes only perm, the sorted trig
+// pairs (and TOD), and the CSR offsets come from a binary search per pixel
 // over pix[perm[i]].
 #include "bm_internal.cuh"
 
@@ -47,6 +49,7 @@ constexpr int SC_THREADS = 512;
 constexpr int SC_WARPS = SC_THREADS / 32;
 constexpr int SC_TILE = SC_THREADS * IG_PER_THREAD;  // 8192 samples
 constexpr int IG_WARP_SPAN = 512;                     // consecutive samples per warp in a tile
+constexpr int SC_INFLIGHT = 4;                        // write-out: samples per thread with loads in flight
 constexpr int RS_MAX_BITS = 10;
 constexpr uint32_t kNoDigit = 0xFFFFFFFFu;
 
@@ -81,8 +84,9 @@ __device__ __forceinline__ void st_keep(float2* p, float2 v, uint64_t pol) {
 
 // ----------------------------------------------------------------- validate
 // Checks pixel indices and angles (or the given cos/sin pairs, |.| <= 1),
-// copies pix, writes the sort keys (flagged samples get key npix and sort
-// last) and the time-ordered trig pairs.  counters[0] = invalid samples,
+// copies pix (the first sort pass reads its keys from this copy: flagged
+// samples get key npix and sort last) and writes the time-ordered trig
+// pairs.  counters[0] = invalid samples,
 // counters[1] = flagged samples.  With tod_dst, also copies the TOD
 // (a host-memory source read once over the host link).
 // MODE: kTrigIn (cos/sin given), kPsi64 or kPsi32 (angles given).
@@ -90,7 +94,7 @@ constexpr int kTrigIn = 0, kPsi64 = 1, kPsi32 = 2;
 template <int MODE>
 __global__ void validate_kernel(const int32_t* __restrict__ pix, const void* __restrict__ psi,
                                 const float* __restrict__ c32, const float* __restrict__ s32, int64_t n,
-                                int64_t npix, int32_t* __restrict__ pix_out, uint32_t* __restrict__ keys,
+                                int64_t npix, int32_t* __restrict__ pix_out,
                                 float2* __restrict__ hi, float2* __restrict__ lo,
                                 const float* __restrict__ tod_src, float* __restrict__ tod_dst,
                                 unsigned long long* __restrict__ counters) {
@@ -113,7 +117,6 @@ __global__ void validate_kernel(const int32_t* __restrict__ pix, const void* __r
         nbad += (!ok_p) + (!ok_a);
         nflag += !kept;
         pix_out[i] = ok_p ? p : -1;
-        keys[i] = kept ? (uint32_t)p : (uint32_t)npix;
     };
     // four samples per thread and pass, their loads issued together
     constexpr int U = 4;
@@ -162,13 +165,19 @@ __global__ void validate_kernel(const int32_t* __restrict__ pix, const void* __r
 }
 
 // ------------------------------------------------------------ radix sort
+// The first pass reads the validated pixel indices as its keys: -1 (flagged)
+// becomes flag_key = npix.  Later passes (flag_key = 0) read keys as stored.
+__device__ __forceinline__ uint32_t pixel_key(uint32_t raw, uint32_t flag_key) {
+    return (flag_key && (int32_t)raw < 0) ? flag_key : raw;
+}
+
 // Digit counts of the block's range for one pass: hist[d * G + block].
 // Each thread counts 16 consecutive keys (vector loads), adding runs of equal
 // digits at once into its warp's own histogram; the warp histograms are
 // summed at the end.
 __global__ void __launch_bounds__(IG_THREADS)
 rs_hist_kernel(const uint32_t* __restrict__ keys, int64_t n, int64_t range, int shift, int bins, int G,
-               uint32_t* __restrict__ hist) {
+               uint32_t flag_key, uint32_t* __restrict__ hist) {
     extern __shared__ __align__(16) uint32_t hh[];  // [IG_WARPS][bins]
     for (int d = threadIdx.x; d < IG_WARPS * bins; d += IG_THREADS) hh[d] = 0;
     __syncthreads();
@@ -184,14 +193,14 @@ rs_hist_kernel(const uint32_t* __restrict__ keys, int64_t n, int64_t range, int 
 #pragma unroll
             for (int q = 0; q < IG_PER_THREAD / 4; ++q) {
                 const uint4 x = __ldcs(v + q);
-                k[4 * q] = x.x;
-                k[4 * q + 1] = x.y;
-                k[4 * q + 2] = x.z;
-                k[4 * q + 3] = x.w;
+                k[4 * q] = pixel_key(x.x, flag_key);
+                k[4 * q + 1] = pixel_key(x.y, flag_key);
+                k[4 * q + 2] = pixel_key(x.z, flag_key);
+                k[4 * q + 3] = pixel_key(x.w, flag_key);
             }
         } else {
 #pragma unroll
-            for (int r = 0; r < IG_PER_THREAD; ++r) k[r] = i0 + r < end ? keys[i0 + r] : kNoDigit;
+            for (int r = 0; r < IG_PER_THREAD; ++r) k[r] = i0 + r < end ? pixel_key(keys[i0 + r], flag_key) : kNoDigit;
         }
         uint32_t cur = kNoDigit, run = 0;
 #pragma unroll
@@ -276,6 +285,7 @@ struct ScatterArgs {
     float* tod_out;        // last pass: the TOD of the kept samples in sorted order, or null
     float2* lo_out;        // every pass with lo_in: the lo halves in this pass's output order
     uint32_t key_limit;    // last pass: samples with keys >= key_limit (flagged) get no entry
+    uint32_t flag_key;     // first pass: keys_in are pixel indices, -1 maps to flag_key (= npix)
 };
 
 inline size_t scatter_smem(int bins) {
@@ -321,7 +331,7 @@ __global__ void __launch_bounds__(SC_THREADS, 2) rs_scatter_kernel(ScatterArgs a
 #pragma unroll
         for (int r = 0; r < IG_PER_THREAD; ++r) {
             const int j = w * IG_WARP_SPAN + r * 32 + lane;
-            key[r] = j < cnt ? a.keys_in[base + j] : 0u;
+            key[r] = j < cnt ? (FIRST ? pixel_key(a.keys_in[base + j], a.flag_key) : a.keys_in[base + j]) : 0u;
         }
         // 2. stable rank within the warp: counters advance round by round
 #pragma unroll
@@ -369,11 +379,11 @@ __global__ void __launch_bounds__(SC_THREADS, 2) rs_scatter_kernel(ScatterArgs a
         // 5. each digit's run goes to its running global offset, the rest of
         //    each sample read back from the input window; four per thread in
         //    flight
-        for (int j0 = threadIdx.x; j0 < cnt; j0 += 4 * SC_THREADS) {
-            uint32_t kk[4];
-            uint4 rr[4];
+        for (int j0 = threadIdx.x; j0 < cnt; j0 += SC_INFLIGHT * SC_THREADS) {
+            uint32_t kk[SC_INFLIGHT];
+            uint4 rr[SC_INFLIGHT];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < SC_INFLIGHT; ++u) {
                 const int j = j0 + u * SC_THREADS;
                 kk[u] = kNoDigit;
                 if (j < cnt) {
@@ -391,14 +401,14 @@ __global__ void __launch_bounds__(SC_THREADS, 2) rs_scatter_kernel(ScatterArgs a
             }
             // the output positions while the loads are in flight
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < SC_INFLIGHT; ++u) {
                 if (kk[u] == kNoDigit) continue;
                 const int j = j0 + u * SC_THREADS;
                 const uint32_t d = (kk[u] >> a.shift) & dmask;
                 const uint32_t g = run_base[d] + (uint32_t)j - tstart[d];
                 if (!LAST) {
-                    a.rec_out[g] = rr[u];
-                    a.keys_out[g] = kk[u];
+                    st_keep(a.rec_out + g, rr[u], pol);
+                    st_keep(a.keys_out + g, kk[u], pol);
                     if (a.lo_in) st_keep(a.lo_out + g, a.lo_in[base + s_src[j]], pol);
                 } else if (kk[u] < a.key_limit) {
                     st_keep(a.perm_out + g, rr[u].y, pol);
@@ -482,7 +492,6 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
     p->pix.alloc(n);
     p->cs_hi_t.alloc(n);
     if (has_lo) p->cs_lo_t.alloc(n);
-    DevBuf<uint32_t> keys_a(n);
     DevBuf<float> tod_copy;  // a host TOD, copied by the validation pass
     if (tod && tod_on_host) tod_copy.alloc(n);
     const float* tod_t = tod_on_host ? tod_copy.get() : tod;
@@ -493,7 +502,7 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
         auto kern = exact_trig ? validate_kernel<kTrigIn>
                                : (psi_dtype == BM_F64 ? validate_kernel<kPsi64> : validate_kernel<kPsi32>);
         const int grid = resident_grid(ctx, kern, threads, (n + threads - 1) / threads);
-        kern<<<grid, threads, 0, s>>>(pix, psi, cos2psi, sin2psi, n, npix, p->pix.get(), keys_a.get(),
+        kern<<<grid, threads, 0, s>>>(pix, psi, cos2psi, sin2psi, n, npix, p->pix.get(),
                                       p->cs_hi_t.get(), p->cs_lo_t.get(), tod_on_host ? tod : nullptr,
                                       tod_copy.get(), counters.get());
         BM_LAUNCH_CHECK();
@@ -515,19 +524,21 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
     // of the trig pairs when the angles were given).
     DevBuf<uint32_t> hist((size_t)sp.bins * sp.grid);
     DevBuf<uint4> rec_a, rec_b;
-    DevBuf<uint32_t> keys_b;
+    DevBuf<uint32_t> keys_a, keys_b;
     DevBuf<float2> lo_a, lo_b;
     if (sp.passes > 1) {
         rec_a.alloc(n);
-        keys_b.alloc(n);
+        keys_a.alloc(n);
         if (has_lo) lo_a.alloc(n);
     }
     if (sp.passes > 2) {
         rec_b.alloc(n);
+        keys_b.alloc(n);
         if (has_lo) lo_b.alloc(n);
     }
-    uint32_t* kin = keys_a.get();
-    uint32_t* kout = keys_b.get();
+    // the first pass reads its keys from the validated pixel indices
+    const uint32_t* kin = reinterpret_cast<const uint32_t*>(p->pix.get());
+    uint32_t* kout = keys_a.get();
     const size_t smem = scatter_smem(sp.bins);
     const uint4* rin = nullptr;  // the first pass reads keys, indices and trig in time order
     uint4* rout = rec_a.get();
@@ -538,7 +549,8 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
         {
             ScopedTimer ht(ctx, "ingest_hist");
             const size_t hsm = sizeof(uint32_t) * IG_WARPS * sp.bins;
-            rs_hist_kernel<<<sp.grid, IG_THREADS, hsm, s>>>(kin, n, sp.range, shift, sp.bins, sp.grid, hist.get());
+            rs_hist_kernel<<<sp.grid, IG_THREADS, hsm, s>>>(kin, n, sp.range, shift, sp.bins, sp.grid,
+                                                            pass == 0 ? (uint32_t)npix : 0u, hist.get());
             BM_LAUNCH_CHECK();
         }
         exclusive_scan_u32(hist.get(), hist.get(), (int64_t)sp.bins * sp.grid, s);
@@ -554,6 +566,7 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
         a.bins = sp.bins;
         a.G = sp.grid;
         a.offs = hist.get();
+        a.flag_key = (uint32_t)npix;
         ScopedTimer st(ctx, "ingest_scatter");
         if (pass + 1 < sp.passes) {
             a.rec_out = rout;
@@ -562,7 +575,8 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
             if (pass == 0) rs_scatter_kernel<false, true><<<sp.grid, SC_THREADS, smem, s>>>(a);
             else rs_scatter_kernel<false, false><<<sp.grid, SC_THREADS, smem, s>>>(a);
             BM_LAUNCH_CHECK();
-            std::swap(kin, kout);
+            kin = kout;
+            kout = (kout == keys_a.get()) ? keys_b.get() : keys_a.get();
             rin = rout;
             rout = (rout == rec_a.get()) ? rec_b.get() : rec_a.get();
             lin = has_lo ? lout : nullptr;

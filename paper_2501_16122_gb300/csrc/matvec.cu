@@ -870,7 +870,10 @@ void rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dt
     for (int64_t r = 0; r < nrhs; ++r) {
         double* br = b + r * nvec;
         if (n->kind == 0) {
-            if (!tod) {  // the TOD sorted along with the pointing
+            if (!tod && df && pc->b_tod.get()) {  // assembled with the preconditioner's blocks
+                BM_CUDA(cudaMemcpyAsync(br, pc->b_tod.get(), sizeof(double) * nvec, cudaMemcpyDeviceToDevice,
+                                        ctx->stream));
+            } else if (!tod) {  // the TOD sorted along with the pointing
                 gather_reduce<float>(p, kept_items(pc), nullptr, n, p->cs_lo_s.get(), df, br, p->tod_s.get());
             } else if (dt == BM_F32) {
                 const float* d = static_cast<const float*>(tod) + r * p->nsamples;

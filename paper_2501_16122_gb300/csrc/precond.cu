@@ -76,13 +76,17 @@ constexpr int kBlkWarps = 8;
 // so the block keeps FP64-level accuracy without FP64 instructions per sample;
 // the warp total is converted to FP64 once per item.  For white noise the
 // same pass writes the weighted FP32 stream sqrt(w) (cos, sin) (w for I-only)
-// that the FP32 matvec reads.
-template <int NC, bool WCS>
+// that the FP32 matvec reads.  With RHS (white noise and a TOD sorted along
+// with the pointing) it also sums b = P^T N^-1 d per item into rpartial, with
+// the double-float steps of the pixel-sorted gather-reduce of the RHS (the
+// same operations in the same order, so the same bits).
+template <int NC, bool WCS, bool RHS>
 __global__ void __launch_bounds__(kBlkWarps * 32)
 blocks_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ item_beg,
               const int32_t* __restrict__ item_len, int64_t nitems, const uint32_t* __restrict__ perm,
               const float2* __restrict__ hi, const float2* __restrict__ lo, DetTables g, int ndet,
-              double* __restrict__ partial, float2* __restrict__ wcs, float* __restrict__ w1) {
+              double* __restrict__ partial, float2* __restrict__ wcs, float* __restrict__ w1,
+              const float* __restrict__ tod_s, double* __restrict__ rpartial) {
     constexpr int NS = NC * (NC + 1) / 2;
     __shared__ uint32_t s_off[kMaxDetSmem + 1];
     __shared__ float2 s_w[kMaxDetSmem];
@@ -101,14 +105,26 @@ blocks_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ 
     for (int64_t k = (int64_t)blockIdx.x * kBlkWarps + (threadIdx.x >> 5); k < nitems; k += nwarps) {
         const int64_t b = item_beg[k];
         const int len = item_len[k];
-        df32 acc[NS];
+        df32 acc[NS], racc[NC];
 #pragma unroll
         for (int j = 0; j < NS; ++j) acc[j] = {0.f, 0.f};
-        auto add = [&](int64_t si, uint32_t t, float2 h, float2 l) {
+#pragma unroll
+        for (int j = 0; j < NC; ++j) racc[j] = {0.f, 0.f};
+        auto add = [&](int64_t si, uint32_t t, float2 h, float2 l, float dv) {
             const int d = det_of(offp, ndet, g.ns, g.inv_ns, t);
             const float2 wv = wp[d];
             const df32 w = {wv.x, wv.y};
             const df32 c = {h.x, l.x}, s = {h.y, l.y};
+            if (RHS) {
+                const df32 val = df_mul(df32{dv, 0.f}, w);
+                if (NC == 1) {
+                    racc[0] = df_add(racc[0], val);
+                } else {
+                    if (NC == 3) racc[0] = df_add(racc[0], val);
+                    racc[NC - 2] = df_add(racc[NC - 2], df_mul(val, c));
+                    racc[NC - 1] = df_add(racc[NC - 1], df_mul(val, s));
+                }
+            }
             if (NC == 3) {
                 const df32 wc = df_mul(w, c), ws = df_mul(w, s);
                 acc[0] = df_add(acc[0], w);
@@ -140,25 +156,49 @@ blocks_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ 
         for (; i + 96 < len; i += 128) {
             uint32_t t[4];
             float2 h[4], l[4];
+            float dv[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int64_t si = b + i + 32 * u;
                 t[u] = perm[si];
                 h[u] = hi[si];
                 l[u] = lo ? lo[si] : make_float2(0.f, 0.f);
+                dv[u] = RHS ? tod_s[si] : 0.f;
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) add(b + i + 32 * u, t[u], h[u], l[u]);
+            for (int u = 0; u < 4; ++u) add(b + i + 32 * u, t[u], h[u], l[u], dv[u]);
         }
         for (; i < len; i += 32) {
             const int64_t si = b + i;
-            add(si, perm[si], hi[si], lo ? lo[si] : make_float2(0.f, 0.f));
+            add(si, perm[si], hi[si], lo ? lo[si] : make_float2(0.f, 0.f), RHS ? tod_s[si] : 0.f);
         }
 #pragma unroll
         for (int j = 0; j < NS; ++j) acc[j] = df_warp_sum(acc[j]);
+        if (RHS) {
+#pragma unroll
+            for (int j = 0; j < NC; ++j) racc[j] = df_warp_sum(racc[j]);
+        }
         if (lane == 0) {
 #pragma unroll
             for (int j = 0; j < NS; ++j) partial[k * NS + j] = df_to_double(acc[j]);
+            if (RHS) {
+#pragma unroll
+                for (int j = 0; j < NC; ++j) rpartial[NC * k + j] = df_to_double(racc[j]);
+            }
+        }
+    }
+}
+
+// b_p = sum of the pixel's item partials in item order, 0 on masked pixels.
+__global__ void finalize_rhs_kernel(const int64_t* __restrict__ pitem, const double* __restrict__ rpartial,
+                                    const uint8_t* __restrict__ mask, int64_t npix, int nc, double* __restrict__ b) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k0 = mask[p] ? 0 : pitem[p], k1 = mask[p] ? 0 : pitem[p + 1];
+        for (int c = 0; c < nc; ++c) {
+            double s = 0.0;
+            for (int64_t k = k0; k < k1; ++k) s += rpartial[k * nc + c];
+            b[p * nc + c] = s;
         }
     }
 }
@@ -298,17 +338,28 @@ void build_precond(bm_precond* pc) {
             if (nc == 1) pc->w1.alloc(p->nvalid);
             else pc->wcs.alloc(p->nvalid);
         }
+        // b = P^T N^-1 d of a TOD the pointing carries, in the same pass
+        const bool with_rhs = white && p->tod_s.get() != nullptr;
+        DevBuf<double> rpartial;
+        if (with_rhs) {
+            rpartial.alloc((all.n > 0 ? all.n : 1) * nc);
+            pc->b_tod.alloc(npix * nc);
+        } else {
+            pc->b_tod.release();
+        }
         if (all.n > 0) {
             const int64_t wunits = (all.n + kBlkWarps - 1) / kBlkWarps;
             const DetTables g{n->det_off32.get(), n->wdf.get(), n->wsqrt.get(), n->ns_uniform, n->inv_ns};
-#define BM_BLOCKS(NC, W)                                                                                    \
-    blocks_kernel<NC, W><<<resident_grid(ctx, blocks_kernel<NC, W>, kBlkWarps * 32, wunits), kBlkWarps * 32, 0, s>>>(all.pix.get(), all.beg.get(), all.len.get(), all.n, \
-                                                         p->perm.get(), p->cs_hi_s.get(), p->cs_lo_s.get(), g, \
-                                                         n->ndet, partial.get(), pc->wcs.get(), pc->w1.get())
-            if (white) {
-                if (nc == 3) BM_BLOCKS(3, true); else if (nc == 2) BM_BLOCKS(2, true); else BM_BLOCKS(1, true);
+#define BM_BLOCKS(NC, W, R)                                                                                 \
+    blocks_kernel<NC, W, R><<<resident_grid(ctx, blocks_kernel<NC, W, R>, kBlkWarps * 32, wunits), kBlkWarps * 32, 0, s>>>( \
+        all.pix.get(), all.beg.get(), all.len.get(), all.n, p->perm.get(), p->cs_hi_s.get(), p->cs_lo_s.get(), g,     \
+        n->ndet, partial.get(), pc->wcs.get(), pc->w1.get(), p->tod_s.get(), rpartial.get())
+            if (with_rhs) {
+                if (nc == 3) BM_BLOCKS(3, true, true); else if (nc == 2) BM_BLOCKS(2, true, true); else BM_BLOCKS(1, true, true);
+            } else if (white) {
+                if (nc == 3) BM_BLOCKS(3, true, false); else if (nc == 2) BM_BLOCKS(2, true, false); else BM_BLOCKS(1, true, false);
             } else {
-                if (nc == 3) BM_BLOCKS(3, false); else if (nc == 2) BM_BLOCKS(2, false); else BM_BLOCKS(1, false);
+                if (nc == 3) BM_BLOCKS(3, false, false); else if (nc == 2) BM_BLOCKS(2, false, false); else BM_BLOCKS(1, false, false);
             }
 #undef BM_BLOCKS
             BM_LAUNCH_CHECK();
@@ -323,6 +374,11 @@ void build_precond(bm_precond* pc) {
         else BM_FIN(1);
 #undef BM_FIN
         BM_LAUNCH_CHECK();
+        if (with_rhs) {
+            finalize_rhs_kernel<<<pgrid, threads, 0, s>>>(all.pitem.get(), rpartial.get(), pc->mask.get(), npix, nc,
+                                                          pc->b_tod.get());
+            BM_LAUNCH_CHECK();
+        }
         BM_CUDA(cudaStreamSynchronize(s));
     }
 
