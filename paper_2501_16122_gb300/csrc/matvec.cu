@@ -187,9 +187,16 @@ white_matvec_f64_kernel(const int32_t* __restrict__ item_pix, const int64_t* __r
         double acc[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) acc[c] = 0.0;
-        for (int i = lane; i < len; i += 32) {
-            const int64_t si = b + i;
-            const double w = white[det_of(offp, ndet, ns, inv_ns, perm[si])];
+        // the lane's samples are in increasing time order: the detector is
+        // looked up only when t passes the current one's end
+        uint32_t dend = 0;
+        double w = 0.0;
+        auto add = [&](int64_t si, uint32_t t) {
+            if (t >= dend) {
+                const int d = det_of(offp, ndet, ns, inv_ns, t);
+                dend = ns ? (uint32_t)(d + 1) * ns : offp[d + 1];
+                w = white[d];
+            }
             if (NC == 1) {
                 acc[0] += w * xv[0];
             } else {
@@ -201,7 +208,16 @@ white_matvec_f64_kernel(const int32_t* __restrict__ item_pix, const int64_t* __r
                 acc[NC - 2] += wy * cs.x;
                 acc[NC - 1] += wy * cs.y;
             }
+        };
+        int i = lane;
+        for (; i + 96 < len; i += 128) {  // four samples' permutation loads together
+            uint32_t t[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) t[u] = perm[b + i + 32 * u];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) add(b + i + 32 * u, t[u]);
         }
+        for (; i < len; i += 32) add(b + i, perm[b + i]);
 #pragma unroll
         for (int c = 0; c < NC; ++c) acc[c] = warp_sum(acc[c]);
         if (lane == 0)
@@ -246,12 +262,20 @@ gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __rest
             df32 acc[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) acc[c] = {0.f, 0.f};
+            // a lane's samples of one item are in increasing time order: the
+            // detector is looked up only when t passes the current one's end
+            uint32_t dend = 0;
+            float2 w = make_float2(0.f, 0.f);
             auto add = [&](uint32_t t, G gv, float2 h, float2 l) {
                 df32 val;
                 if (sizeof(G) == 4) val = {(float)gv, 0.f};
                 else val = df_from((double)gv);
                 if (weighted) {
-                    const float2 w = wp[det_of(offp, ndet, dt.ns, dt.inv_ns, t)];
+                    if (t >= dend) {
+                        const int d = det_of(offp, ndet, dt.ns, dt.inv_ns, t);
+                        dend = dt.ns ? (uint32_t)(d + 1) * dt.ns : offp[d + 1];
+                        w = wp[d];
+                    }
                     val = df_mul(val, df32{w.x, w.y});
                 }
                 if (NC == 1) {
@@ -297,9 +321,18 @@ gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __rest
             double acc[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+            uint32_t dend = 0;
+            double wd = 0.0;
             auto add = [&](uint32_t t, G gv, int64_t si) {
                 double val = (double)gv;
-                if (weighted) val *= white[det_of(offp, ndet, dt.ns, dt.inv_ns, t)];
+                if (weighted) {
+                    if (t >= dend) {
+                        const int d = det_of(offp, ndet, dt.ns, dt.inv_ns, t);
+                        dend = dt.ns ? (uint32_t)(d + 1) * dt.ns : offp[d + 1];
+                        wd = white[d];
+                    }
+                    val *= wd;
+                }
                 if (NC == 1) {
                     acc[0] += val;
                 } else {
