@@ -170,10 +170,9 @@ KERNELS = {"ingest_validate": "validate_kernel", "ingest_hist": "rs_hist_kernel"
            "ingest_scatter": "rs_scatter_kernel", "blocks": "blocks_kernel", "rhs": "gather_reduce_kernel",
            "matvec_white_f32": "white_matvec_f32_kernel"}
 TRAFFIC = {
-    # profiles/ingest_sort_nside256_256x262144.md: 47.8 and 49.6 DRAM bytes
-    # per sample for the two scatter passes (mean 48.7; TOD sorted along) on
-    # the 67M-sample case; the traffic grows in proportion to the samples
-    "ingest_scatter": lambda n: 48.7 * n,
+    # ncu DRAM bytes per launch, per family, from a capture of the current
+    # kernel on the 67M-sample case scaled by the samples (none yet for the
+    # shared-memory-staged scatter: reported as null)
 }
 
 

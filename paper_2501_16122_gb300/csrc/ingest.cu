@@ -41,15 +41,15 @@ constexpr int IG_THREADS = 256;
 constexpr int IG_WARPS = IG_THREADS / 32;
 constexpr int IG_PER_THREAD = 16;
 constexpr int IG_TILE = IG_THREADS * IG_PER_THREAD;  // 4096 samples
-// The scatter runs one 512-thread block per SM on 8192-sample tiles: the
-// partly written output lines it keeps open in L2 (digits x streams x
-// blocks) stay well inside the 126 MB, and each digit's run per tile is
-// twice as long as with 4096-sample tiles.
+// The scatter: SC_THREADS threads a block, 16 samples a thread, so a tile of
+// SC_TILE samples; the tile's keys and payload window sit in shared memory
+// (see scatter_smem).
 constexpr int SC_THREADS = 512;
 constexpr int SC_WARPS = SC_THREADS / 32;
-constexpr int SC_TILE = SC_THREADS * IG_PER_THREAD;  // 8192 samples
-constexpr int IG_WARP_SPAN = 512;                     // consecutive samples per warp in a tile
-constexpr int SC_INFLIGHT = 4;                        // write-out: samples per thread with loads in flight
+constexpr int SC_TILE = SC_THREADS * IG_PER_THREAD;
+constexpr int SC_MIN_BLOCKS = SC_THREADS == 256 ? 2 : 1;  // blocks per SM the shared memory allows
+constexpr int IG_WARP_SPAN = 512;                          // consecutive samples per warp in a tile
+constexpr int kRankRows = SC_TILE >> 10;                   // warps that rank at once (tables of 2^10 lane masks)
 constexpr int RS_MAX_BITS = 10;
 constexpr uint32_t kNoDigit = 0xFFFFFFFFu;
 
@@ -226,8 +226,8 @@ rs_hist_kernel(const uint32_t* __restrict__ keys, int64_t n, int64_t range, int 
 }
 
 // Exclusive scan of cnt[0, bins) into start[] by the whole block (THREADS threads).
-template <int THREADS>
-__device__ void scan_bins(const uint32_t* cnt, uint32_t* start, int bins, uint32_t* wtot) {
+template <int THREADS, typename T>
+__device__ void scan_bins(const T* cnt, T* start, int bins, uint32_t* wtot) {
     constexpr int WARPS = THREADS / 32;
     const int per = bins >= THREADS ? bins / THREADS : 1;
     const int b0 = threadIdx.x * per;
@@ -257,7 +257,7 @@ __device__ void scan_bins(const uint32_t* cnt, uint32_t* start, int bins, uint32
     uint32_t run = x - local + wtot[w];
     for (int k = 0; k < per; ++k)
         if (b0 + k < bins) {
-            start[b0 + k] = run;
+            start[b0 + k] = (T)run;
             run += cnt[b0 + k];
         }
 }
@@ -286,29 +286,74 @@ struct ScatterArgs {
     float2* lo_out;        // every pass with lo_in: the lo halves in this pass's output order
     uint32_t key_limit;    // last pass: samples with keys >= key_limit (flagged) get no entry
     uint32_t flag_key;     // first pass: keys_in are pixel indices, -1 maps to flag_key (= npix)
+    unsigned long long* err;  // set to 1 if a wait for a bulk copy gave up
 };
 
+// Shared memory of one scatter block: the tile's payload window (records,
+// or trig pairs + TOD values on the first pass), its keys (input order; the
+// lane-mask tables of the ranking; then the keys staged in digit order), the
+// tile position of each staged sample, the per-warp digit counters, and per
+// digit the running global offset and the tile's count and start.
 inline size_t scatter_smem(int bins) {
-    return sizeof(uint32_t) * ((size_t)SC_TILE + 3 * (size_t)bins) +
-           sizeof(uint16_t) * ((size_t)SC_TILE + (size_t)SC_WARPS * bins);
+    const size_t tile = SC_TILE;
+    return 16 * tile + 4 * tile + 2 * tile + 2 * (size_t)SC_WARPS * bins + 4 * (size_t)bins + 2 * 2 * (size_t)bins;
+}
+
+// Bulk copies global -> shared memory by the TMA engine, completed on an
+// mbarrier (transaction bytes), and bounded waits on it.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// Polls for the completion of the barrier phase with this parity; false if
+// it did not complete within the poll limit (each poll may suspend the
+// thread for a short, hardware-defined time).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t addr = smem_u32(bar);
+    for (uint32_t i = 0; i < (1u << 22); ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
 }
 
 // One stable scatter pass over the block's range (see the file comment).
-// Only the key and the tile position of each sample are staged in shared
-// memory (6 bytes a sample, so two 512-thread blocks fit on an SM); at write
-// time the rest of the sample (index, trig pair, lo half) is read back from
-// the tile's window of the input, which the key loads have just brought
-// into L2.
+// Per tile, one thread starts two bulk copies into shared memory: the keys
+// and the payload window (the intermediate records, or on the first pass
+// the time-ordered trig pairs and TOD values).  The keys are ranked as soon
+// as they arrive, while the window is still on its way; each sample's key
+// and tile position are then staged in digit order, and the write-out reads
+// the payload of a staged sample from the window in shared memory and
+// stores the digit runs at their running global offsets.
 template <bool LAST, bool FIRST>
-__global__ void __launch_bounds__(SC_THREADS, 2) rs_scatter_kernel(ScatterArgs a) {
-    extern __shared__ __align__(16) uint32_t ss[];
-    uint32_t* s_keys = ss;
-    uint32_t* run_base = s_keys + SC_TILE;  // next global position per digit
-    uint32_t* tcnt = run_base + a.bins;     // tile count per digit
-    uint32_t* tstart = tcnt + a.bins;       // tile-local start per digit
-    uint16_t* s_src = reinterpret_cast<uint16_t*>(tstart + a.bins);  // tile position of a staged sample
-    uint16_t* wcnt = s_src + SC_TILE;                                 // [warp][digit]
+__global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(ScatterArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint4* s_rec = reinterpret_cast<uint4*>(smem);                          // window: records
+    float2* s_hi = reinterpret_cast<float2*>(smem);                         // window, first pass: trig pairs
+    float* s_tod = reinterpret_cast<float*>(smem + 8 * SC_TILE);            //   and TOD values
+    uint32_t* s_keys = reinterpret_cast<uint32_t*>(smem + 16 * SC_TILE);    // keys
+    uint16_t* s_src = reinterpret_cast<uint16_t*>(smem + 20 * SC_TILE);     // tile position of a staged sample
+    uint16_t* wcnt = reinterpret_cast<uint16_t*>(smem + 22 * SC_TILE);      // [warp][digit]
+    uint32_t* run_base = reinterpret_cast<uint32_t*>(wcnt + SC_WARPS * a.bins);  // next global position per digit
+    uint16_t* tcnt = reinterpret_cast<uint16_t*>(run_base + a.bins);       // tile count per digit
+    uint16_t* tstart = tcnt + a.bins;                                       // tile-local start per digit
     __shared__ uint32_t wtot[SC_WARPS];
+    __shared__ __align__(8) uint64_t bar[2];  // [0] keys, [1] window
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     const int bins = a.bins;
@@ -316,7 +361,15 @@ __global__ void __launch_bounds__(SC_THREADS, 2) rs_scatter_kernel(ScatterArgs a
     const int64_t begin = range_begin(a.range);
     const int64_t end = begin + a.range < a.n ? begin + a.range : a.n;
     const uint64_t pol = l2_keep_policy();
+    // a caller's TOD array may start off a 16-byte boundary: then it is read
+    // with plain loads
+    const bool tod_bulk = FIRST && a.tod_in && (reinterpret_cast<uintptr_t>(a.tod_in) & 15u) == 0;
 
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0]);
+        mbar_init(&bar[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     for (int d = threadIdx.x; d < bins; d += SC_THREADS) {
         run_base[d] = a.offs[(int64_t)d * a.G + blockIdx.x];
 #pragma unroll
@@ -324,32 +377,104 @@ __global__ void __launch_bounds__(SC_THREADS, 2) rs_scatter_kernel(ScatterArgs a
     }
     __syncthreads();
 
-    for (int64_t base = begin; base < end; base += SC_TILE) {
+    // One thread starts the copies of the tile at `base`: whole 16-byte
+    // units (the rest of a ragged last tile is loaded by the threads).
+    auto issue = [&](int64_t base, int cnt) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // after the block's last reads of both buffers
+        const uint32_t kbytes = (uint32_t)(cnt & ~3) * 4u;
+        mbar_arrive_expect(&bar[0], kbytes);
+        if (kbytes) bulk_g2s(s_keys, a.keys_in + base, kbytes, &bar[0]);
+        if (!FIRST) {
+            mbar_arrive_expect(&bar[1], (uint32_t)cnt * 16u);
+            bulk_g2s(s_rec, a.rec_in + base, (uint32_t)cnt * 16u, &bar[1]);
+        } else {
+            const uint32_t hbytes = (uint32_t)(cnt & ~1) * 8u;
+            const uint32_t tbytes = tod_bulk ? (uint32_t)(cnt & ~3) * 4u : 0u;
+            mbar_arrive_expect(&bar[1], hbytes + tbytes);
+            if (hbytes) bulk_g2s(s_hi, a.hi_in + base, hbytes, &bar[1]);
+            if (tbytes) bulk_g2s(s_tod, a.tod_in + base, tbytes, &bar[1]);
+        }
+    };
+    // Gives up the block after a failed wait: flags the error, waits (again
+    // bounded) for the copies still in flight so that none lands after the
+    // block has exited, and returns true.
+    auto give_up = [&](bool failed, uint32_t parity) {
+        if (!__syncthreads_or(failed)) return false;
+        if (threadIdx.x == 0) {
+            atomicExch(a.err, 1ull);
+            mbar_wait(&bar[0], parity);
+            mbar_wait(&bar[1], parity);
+        }
+        return true;
+    };
+
+    if (threadIdx.x == 0 && begin < end) issue(begin, (int)(end - begin < SC_TILE ? end - begin : SC_TILE));
+    uint32_t parity = 0;
+    for (int64_t base = begin; base < end; base += SC_TILE, parity ^= 1u) {
         const int cnt = (int)(end - base < SC_TILE ? end - base : SC_TILE);
+        // the ragged end of the last tile, with plain loads
+        for (int j = (cnt & ~3) + threadIdx.x; j < cnt; j += SC_THREADS) s_keys[j] = a.keys_in[base + j];
+        if (FIRST) {
+            if ((cnt & 1) && threadIdx.x == 0) s_hi[cnt - 1] = a.hi_in[base + cnt - 1];
+            if (a.tod_in)
+                for (int j = (tod_bulk ? (cnt & ~3) : 0) + threadIdx.x; j < cnt; j += SC_THREADS)
+                    s_tod[j] = a.tod_in[base + j];
+        }
+        if (give_up(!mbar_wait(&bar[0], parity), parity)) return;
+        __syncthreads();  // the plain-loaded keys too
         uint32_t key[IG_PER_THREAD], rank[IG_PER_THREAD];
         // 1. the warp's 512 consecutive keys, 32 per round
 #pragma unroll
         for (int r = 0; r < IG_PER_THREAD; ++r) {
             const int j = w * IG_WARP_SPAN + r * 32 + lane;
-            key[r] = j < cnt ? (FIRST ? pixel_key(a.keys_in[base + j], a.flag_key) : a.keys_in[base + j]) : 0u;
+            key[r] = j < cnt ? (FIRST ? pixel_key(s_keys[j], a.flag_key) : s_keys[j]) : 0u;
         }
-        // 2. stable rank within the warp: counters advance round by round
-#pragma unroll
-        for (int r = 0; r < IG_PER_THREAD; ++r) {
-            const int j = w * IG_WARP_SPAN + r * 32 + lane;
-            const uint32_t d = j < cnt ? ((key[r] >> a.shift) & dmask) : kNoDigit;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-            const int leader = __ffs(peers) - 1;
-            uint32_t old = 0;
-            if (d != kNoDigit && lane == leader) {
-                old = wcnt[w * bins + d];
-                wcnt[w * bins + d] = (uint16_t)(old + __popc(peers));
-            }
-            old = __shfl_sync(0xffffffffu, old, leader);
-            rank[r] = old + __popc(peers & lt_mask);
-            __syncwarp();
+        // 2. stable rank within the warp, round by round.  The lanes of a
+        //    round that hold the same digit are found through a table of
+        //    lane masks in shared memory (each lane ORs its bit into its
+        //    digit's entry and reads the entry back; the lowest lane of the
+        //    group clears it): a warp-wide match instruction costs ~60 cycles
+        //    of the SM here, these shared-memory operations ~2.  The group's
+        //    leader adds the group size to the warp's digit counter and
+        //    broadcasts the count before it; rounds add in program order, so
+        //    ranks follow the input order (a stable sort).  The tables use
+        //    the keys' buffer, free once the keys are in registers: one table
+        //    of 2^10 entries per warp of a wave, the warps in
+        //    SC_WARPS / kRankRows waves.  Two 16-bit digit counters share a
+        //    32-bit word (a warp counts at most 512 samples a digit), so an
+        //    add never carries into the neighbour.
+        __syncthreads();  // every warp has its keys
+        {
+            uint4* z = reinterpret_cast<uint4*>(s_keys);
+            for (int i = threadIdx.x; i < SC_TILE / 4; i += SC_THREADS) z[i] = make_uint4(0u, 0u, 0u, 0u);
         }
         __syncthreads();
+        uint32_t* wcnt32 = reinterpret_cast<uint32_t*>(wcnt);
+        for (int wave = 0; wave < SC_WARPS / kRankRows; ++wave) {
+            if (w / kRankRows == wave) {
+                uint32_t* tbl = s_keys + (w % kRankRows) * 1024;
+#pragma unroll
+                for (int r = 0; r < IG_PER_THREAD; ++r) {
+                    const int j = w * IG_WARP_SPAN + r * 32 + lane;
+                    const bool valid = j < cnt;
+                    const uint32_t d = (key[r] >> a.shift) & dmask;
+                    if (valid) atomicOr(tbl + d, 1u << lane);
+                    __syncwarp();
+                    const unsigned peers = valid ? tbl[d] : (1u << lane);
+                    __syncwarp();
+                    const int leader = __ffs(peers) - 1;
+                    uint32_t old = 0;
+                    if (valid && lane == leader) {
+                        const uint32_t sh = 16u * (d & 1u);
+                        old = (atomicAdd(wcnt32 + ((w * bins + d) >> 1), (uint32_t)__popc(peers) << sh) >> sh) & 0xFFFFu;
+                        tbl[d] = 0u;
+                    }
+                    rank[r] = __shfl_sync(0xffffffffu, old, leader) + __popc(peers & lt_mask);
+                    __syncwarp();  // the entry is clear before the next round's ORs
+                }
+            }
+            __syncthreads();
+        }
         // 3. per digit: exclusive prefix over warps, tile count; then over digits
         for (int d = threadIdx.x; d < bins; d += SC_THREADS) {
             uint32_t t = 0;
@@ -359,12 +484,13 @@ __global__ void __launch_bounds__(SC_THREADS, 2) rs_scatter_kernel(ScatterArgs a
                 wcnt[q * bins + d] = (uint16_t)t;
                 t += c;
             }
-            tcnt[d] = t;
+            tcnt[d] = (uint16_t)t;
         }
         __syncthreads();
         scan_bins<SC_THREADS>(tcnt, tstart, bins, wtot);
         __syncthreads();
-        // 4. stage keys and tile positions in digit order
+        // 4. stage keys and tile positions in digit order (in the keys'
+        //    buffer: the lane-mask tables are all clear and done with)
 #pragma unroll
         for (int r = 0; r < IG_PER_THREAD; ++r) {
             const int j = w * IG_WARP_SPAN + r * 32 + lane;
@@ -376,55 +502,43 @@ __global__ void __launch_bounds__(SC_THREADS, 2) rs_scatter_kernel(ScatterArgs a
             }
         }
         __syncthreads();
+        if (give_up(!mbar_wait(&bar[1], parity), parity)) return;
         // 5. each digit's run goes to its running global offset, the rest of
-        //    each sample read back from the input window; four per thread in
-        //    flight
-        for (int j0 = threadIdx.x; j0 < cnt; j0 += SC_INFLIGHT * SC_THREADS) {
-            uint32_t kk[SC_INFLIGHT];
-            uint4 rr[SC_INFLIGHT];
-#pragma unroll
-            for (int u = 0; u < SC_INFLIGHT; ++u) {
-                const int j = j0 + u * SC_THREADS;
-                kk[u] = kNoDigit;
-                if (j < cnt) {
-                    kk[u] = s_keys[j];
-                    const uint32_t src = s_src[j];
-                    if (!FIRST) {
-                        rr[u] = a.rec_in[base + src];
-                    } else {
-                        const float2 h = a.hi_in[base + src];
-                        const float d = a.tod_in ? a.tod_in[base + src] : 0.f;
-                        rr[u] = make_uint4(__float_as_uint(d), (uint32_t)(base + src), __float_as_uint(h.x),
-                                           __float_as_uint(h.y));
-                    }
-                }
+        //    each sample from the window in shared memory
+        for (int j = threadIdx.x; j < cnt; j += SC_THREADS) {
+            const uint32_t k = s_keys[j];
+            const uint32_t src = s_src[j];
+            const uint32_t d = (k >> a.shift) & dmask;
+            const uint32_t g = run_base[d] + (uint32_t)j - tstart[d];
+            uint4 rr;
+            if (!FIRST) {
+                rr = s_rec[src];
+            } else {
+                const float2 h = s_hi[src];
+                const float dv = a.tod_in ? s_tod[src] : 0.f;
+                rr = make_uint4(__float_as_uint(dv), (uint32_t)(base + src), __float_as_uint(h.x), __float_as_uint(h.y));
             }
-            // the output positions while the loads are in flight
-#pragma unroll
-            for (int u = 0; u < SC_INFLIGHT; ++u) {
-                if (kk[u] == kNoDigit) continue;
-                const int j = j0 + u * SC_THREADS;
-                const uint32_t d = (kk[u] >> a.shift) & dmask;
-                const uint32_t g = run_base[d] + (uint32_t)j - tstart[d];
-                if (!LAST) {
-                    st_keep(a.rec_out + g, rr[u], pol);
-                    st_keep(a.keys_out + g, kk[u], pol);
-                    if (a.lo_in) st_keep(a.lo_out + g, a.lo_in[base + s_src[j]], pol);
-                } else if (kk[u] < a.key_limit) {
-                    st_keep(a.perm_out + g, rr[u].y, pol);
-                    st_keep(a.hi_out + g, make_float2(__uint_as_float(rr[u].z), __uint_as_float(rr[u].w)), pol);
-                    if (a.tod_out) st_keep(reinterpret_cast<uint32_t*>(a.tod_out) + g, rr[u].x, pol);
-                    if (a.lo_in) st_keep(a.lo_out + g, a.lo_in[base + s_src[j]], pol);
-                }
+            if (!LAST) {
+                st_keep(a.rec_out + g, rr, pol);
+                st_keep(a.keys_out + g, k, pol);
+                if (a.lo_in) st_keep(a.lo_out + g, a.lo_in[base + src], pol);
+            } else if (k < a.key_limit) {
+                st_keep(a.perm_out + g, rr.y, pol);
+                st_keep(a.hi_out + g, make_float2(__uint_as_float(rr.z), __uint_as_float(rr.w)), pol);
+                if (a.tod_out) st_keep(reinterpret_cast<uint32_t*>(a.tod_out) + g, rr.x, pol);
+                if (a.lo_in) st_keep(a.lo_out + g, a.lo_in[base + src], pol);
             }
         }
         __syncthreads();
-        // 6. advance the running offsets, clear the warp counters
+        // 6. advance the running offsets, clear the warp counters, start the
+        //    next tile's copies
         for (int d = threadIdx.x; d < bins; d += SC_THREADS) {
             run_base[d] += tcnt[d];
 #pragma unroll
             for (int q = 0; q < SC_WARPS; ++q) wcnt[q * bins + d] = 0;
         }
+        if (threadIdx.x == 0 && base + SC_TILE < end)
+            issue(base + SC_TILE, (int)(end - base - SC_TILE < SC_TILE ? end - base - SC_TILE : SC_TILE));
         __syncthreads();
     }
 }
@@ -495,8 +609,8 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
     DevBuf<float> tod_copy;  // a host TOD, copied by the validation pass
     if (tod && tod_on_host) tod_copy.alloc(n);
     const float* tod_t = tod_on_host ? tod_copy.get() : tod;
-    DevBuf<unsigned long long> counters(2);
-    BM_CUDA(cudaMemsetAsync(counters.get(), 0, 2 * sizeof(unsigned long long), s));
+    DevBuf<unsigned long long> counters(3);  // invalid samples, flagged samples, a scatter wait that gave up
+    BM_CUDA(cudaMemsetAsync(counters.get(), 0, 3 * sizeof(unsigned long long), s));
     {
         ScopedTimer vt(ctx, "ingest_validate");
         auto kern = exact_trig ? validate_kernel<kTrigIn>
@@ -567,6 +681,7 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
         a.G = sp.grid;
         a.offs = hist.get();
         a.flag_key = (uint32_t)npix;
+        a.err = counters.get() + 2;
         ScopedTimer st(ctx, "ingest_scatter");
         if (pass + 1 < sp.passes) {
             a.rec_out = rout;
@@ -599,7 +714,13 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
     BM_LAUNCH_CHECK();
     hits_kernel<<<pgrid, threads, 0, s>>>(p->off.get(), npix, p->hits.get());
     BM_LAUNCH_CHECK();
+    unsigned long long h_err = 0;
+    BM_CUDA(cudaMemcpyAsync(&h_err, counters.get() + 2, sizeof(h_err), cudaMemcpyDeviceToHost, s));
     BM_CUDA(cudaStreamSynchronize(s));
+    if (h_err) {
+        set_error("the pixel sort gave up waiting for a bulk copy into shared memory");
+        throw Error{BM_ERR_TIMEOUT};
+    }
 }
 
 }  // namespace bm
