@@ -31,6 +31,8 @@
 // validated pixel indices.  The last pass writes only perm, the sorted trig
 // pairs (and TOD), and the CSR offsets come from a binary search per pixel
 // over pix[perm[i]].
+#include <algorithm>
+
 #include "bm_internal.cuh"
 
 namespace bm {
@@ -290,13 +292,15 @@ struct ScatterArgs {
 };
 
 // Shared memory of one scatter block: the tile's payload window (records,
-// or trig pairs + TOD values on the first pass), its keys (input order; the
-// lane-mask tables of the ranking; then the keys staged in digit order), the
-// tile position of each staged sample, the per-warp digit counters, and per
-// digit the running global offset and the tile's count and start.
+// or trig pairs + TOD values on the first pass), its keys (input order, then
+// the lane-mask tables of the ranking), the tile position of each staged
+// sample, the per-warp digit counters (whose region then holds the keys
+// staged in digit order), and per digit the running global offset and the
+// tile's count and start.
 inline size_t scatter_smem(int bins) {
     const size_t tile = SC_TILE;
-    return 16 * tile + 4 * tile + 2 * tile + 2 * (size_t)SC_WARPS * bins + 4 * (size_t)bins + 2 * 2 * (size_t)bins;
+    return 16 * tile + 4 * tile + 2 * tile + std::max(2 * (size_t)SC_WARPS * bins, 4 * tile) + 4 * (size_t)bins +
+           2 * 2 * (size_t)bins;
 }
 
 // Bulk copies global -> shared memory by the TMA engine, completed on an
@@ -349,7 +353,9 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
     uint32_t* s_keys = reinterpret_cast<uint32_t*>(smem + 16 * SC_TILE);    // keys
     uint16_t* s_src = reinterpret_cast<uint16_t*>(smem + 20 * SC_TILE);     // tile position of a staged sample
     uint16_t* wcnt = reinterpret_cast<uint16_t*>(smem + 22 * SC_TILE);      // [warp][digit]
-    uint32_t* run_base = reinterpret_cast<uint32_t*>(wcnt + SC_WARPS * a.bins);  // next global position per digit
+    uint32_t* s_stk = reinterpret_cast<uint32_t*>(wcnt);                   // staged keys (after the counters' use)
+    uint32_t* run_base = reinterpret_cast<uint32_t*>(
+        smem + 22 * SC_TILE + (2 * SC_WARPS * a.bins > 4 * SC_TILE ? 2 * SC_WARPS * a.bins : 4 * SC_TILE));  // next global position per digit
     uint16_t* tcnt = reinterpret_cast<uint16_t*>(run_base + a.bins);       // tile count per digit
     uint16_t* tstart = tcnt + a.bins;                                       // tile-local start per digit
     __shared__ uint32_t wtot[SC_WARPS];
@@ -377,13 +383,18 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
     }
     __syncthreads();
 
-    // One thread starts the copies of the tile at `base`: whole 16-byte
-    // units (the rest of a ragged last tile is loaded by the threads).
-    auto issue = [&](int64_t base, int cnt) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // after the block's last reads of both buffers
+    // One thread starts the copies of the tile at `base`, keys and window
+    // separately: whole 16-byte units (the rest of a ragged last tile is
+    // loaded by the threads).  The fence orders the block's earlier accesses
+    // of the buffer (made visible by a barrier) before the copy's writes.
+    auto issue_keys = [&](int64_t base, int cnt) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         const uint32_t kbytes = (uint32_t)(cnt & ~3) * 4u;
         mbar_arrive_expect(&bar[0], kbytes);
         if (kbytes) bulk_g2s(s_keys, a.keys_in + base, kbytes, &bar[0]);
+    };
+    auto issue_win = [&](int64_t base, int cnt) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         if (!FIRST) {
             mbar_arrive_expect(&bar[1], (uint32_t)cnt * 16u);
             bulk_g2s(s_rec, a.rec_in + base, (uint32_t)cnt * 16u, &bar[1]);
@@ -398,17 +409,20 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
     // Gives up the block after a failed wait: flags the error, waits (again
     // bounded) for the copies still in flight so that none lands after the
     // block has exited, and returns true.
-    auto give_up = [&](bool failed, uint32_t parity) {
+    auto give_up = [&](bool failed, uint32_t key_parity, uint32_t win_parity) {
         if (!__syncthreads_or(failed)) return false;
         if (threadIdx.x == 0) {
             atomicExch(a.err, 1ull);
-            mbar_wait(&bar[0], parity);
-            mbar_wait(&bar[1], parity);
+            mbar_wait(&bar[0], key_parity);
+            mbar_wait(&bar[1], win_parity);
         }
         return true;
     };
 
-    if (threadIdx.x == 0 && begin < end) issue(begin, (int)(end - begin < SC_TILE ? end - begin : SC_TILE));
+    if (threadIdx.x == 0 && begin < end) {
+        issue_keys(begin, (int)(end - begin < SC_TILE ? end - begin : SC_TILE));
+        issue_win(begin, (int)(end - begin < SC_TILE ? end - begin : SC_TILE));
+    }
     uint32_t parity = 0;
     for (int64_t base = begin; base < end; base += SC_TILE, parity ^= 1u) {
         const int cnt = (int)(end - base < SC_TILE ? end - base : SC_TILE);
@@ -420,7 +434,7 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
                 for (int j = (tod_bulk ? (cnt & ~3) : 0) + threadIdx.x; j < cnt; j += SC_THREADS)
                     s_tod[j] = a.tod_in[base + j];
         }
-        if (give_up(!mbar_wait(&bar[0], parity), parity)) return;
+        if (give_up(!mbar_wait(&bar[0], parity), parity, parity)) return;
         __syncthreads();  // the plain-loaded keys too
         uint32_t key[IG_PER_THREAD], rank[IG_PER_THREAD];
         // 1. the warp's 512 consecutive keys, 32 per round
@@ -489,24 +503,33 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
         __syncthreads();
         scan_bins<SC_THREADS>(tcnt, tstart, bins, wtot);
         __syncthreads();
-        // 4. stage keys and tile positions in digit order (in the keys'
-        //    buffer: the lane-mask tables are all clear and done with)
+        // 4. stage keys and tile positions in digit order: the positions
+        //    first (they read the counters), then the keys into the
+        //    counters' region; the keys' buffer is free from here on, so the
+        //    next tile's keys start arriving during the write-out
+#pragma unroll
+        for (int r = 0; r < IG_PER_THREAD; ++r) {
+            const uint32_t d = (key[r] >> a.shift) & dmask;
+            rank[r] += tstart[d] + wcnt[w * bins + d];
+        }
+        __syncthreads();
 #pragma unroll
         for (int r = 0; r < IG_PER_THREAD; ++r) {
             const int j = w * IG_WARP_SPAN + r * 32 + lane;
             if (j < cnt) {
-                const uint32_t d = (key[r] >> a.shift) & dmask;
-                const uint32_t pos = tstart[d] + wcnt[w * bins + d] + rank[r];
-                s_keys[pos] = key[r];
-                s_src[pos] = (uint16_t)j;
+                s_stk[rank[r]] = key[r];
+                s_src[rank[r]] = (uint16_t)j;
             }
         }
         __syncthreads();
-        if (give_up(!mbar_wait(&bar[1], parity), parity)) return;
+        if (threadIdx.x == 0 && base + SC_TILE < end)
+            issue_keys(base + SC_TILE, (int)(end - base - SC_TILE < SC_TILE ? end - base - SC_TILE : SC_TILE));
+        // (the next tile's keys may be on their way: the other key phase)
+        if (give_up(!mbar_wait(&bar[1], parity), base + SC_TILE < end ? parity ^ 1u : parity, parity)) return;
         // 5. each digit's run goes to its running global offset, the rest of
         //    each sample from the window in shared memory
         for (int j = threadIdx.x; j < cnt; j += SC_THREADS) {
-            const uint32_t k = s_keys[j];
+            const uint32_t k = s_stk[j];
             const uint32_t src = s_src[j];
             const uint32_t d = (k >> a.shift) & dmask;
             const uint32_t g = run_base[d] + (uint32_t)j - tstart[d];
@@ -531,14 +554,14 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
         }
         __syncthreads();
         // 6. advance the running offsets, clear the warp counters, start the
-        //    next tile's copies
+        //    next tile's window
         for (int d = threadIdx.x; d < bins; d += SC_THREADS) {
             run_base[d] += tcnt[d];
 #pragma unroll
             for (int q = 0; q < SC_WARPS; ++q) wcnt[q * bins + d] = 0;
         }
         if (threadIdx.x == 0 && base + SC_TILE < end)
-            issue(base + SC_TILE, (int)(end - base - SC_TILE < SC_TILE ? end - base - SC_TILE : SC_TILE));
+            issue_win(base + SC_TILE, (int)(end - base - SC_TILE < SC_TILE ? end - base - SC_TILE : SC_TILE));
         __syncthreads();
     }
 }
