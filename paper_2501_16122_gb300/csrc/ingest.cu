@@ -51,7 +51,6 @@ constexpr int SC_WARPS = SC_THREADS / 32;
 constexpr int SC_TILE = SC_THREADS * IG_PER_THREAD;
 constexpr int SC_MIN_BLOCKS = SC_THREADS == 256 ? 2 : 1;  // blocks per SM the shared memory allows
 constexpr int IG_WARP_SPAN = 512;                          // consecutive samples per warp in a tile
-constexpr int kRankRows = SC_TILE >> 10;                   // warps that rank at once (tables of 2^10 lane masks)
 constexpr int RS_MAX_BITS = 10;
 constexpr uint32_t kNoDigit = 0xFFFFFFFFu;
 
@@ -359,7 +358,11 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
     uint16_t* tcnt = reinterpret_cast<uint16_t*>(run_base + a.bins);       // tile count per digit
     uint16_t* tstart = tcnt + a.bins;                                       // tile-local start per digit
     __shared__ uint32_t wtot[SC_WARPS];
-    __shared__ __align__(8) uint64_t bar[2];  // [0] keys, [1] window
+    __shared__ __align__(8) uint64_t bar[3];  // [0] keys, [1] window: first part, [2] window: second part
+    // lane-mask tables of the ranking, one per warp (2^10 entries): in the
+    // window's second half (records of the tile's second half, or the TOD
+    // values), which is copied in after the ranking
+    uint32_t* s_tbl = reinterpret_cast<uint32_t*>(smem + 8 * SC_TILE);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     const int bins = a.bins;
@@ -374,6 +377,7 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
     if (threadIdx.x == 0) {
         mbar_init(&bar[0]);
         mbar_init(&bar[1]);
+        mbar_init(&bar[2]);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int d = threadIdx.x; d < bins; d += SC_THREADS) {
@@ -393,48 +397,59 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
         mbar_arrive_expect(&bar[0], kbytes);
         if (kbytes) bulk_g2s(s_keys, a.keys_in + base, kbytes, &bar[0]);
     };
-    auto issue_win = [&](int64_t base, int cnt) {
+    // the window's first part: records of the tile's first half, or the
+    // trig pairs
+    auto issue_win1 = [&](int64_t base, int cnt) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         if (!FIRST) {
-            mbar_arrive_expect(&bar[1], (uint32_t)cnt * 16u);
-            bulk_g2s(s_rec, a.rec_in + base, (uint32_t)cnt * 16u, &bar[1]);
+            const uint32_t n1 = cnt < SC_TILE / 2 ? (uint32_t)cnt : SC_TILE / 2;
+            mbar_arrive_expect(&bar[1], n1 * 16u);
+            bulk_g2s(s_rec, a.rec_in + base, n1 * 16u, &bar[1]);
         } else {
             const uint32_t hbytes = (uint32_t)(cnt & ~1) * 8u;
-            const uint32_t tbytes = tod_bulk ? (uint32_t)(cnt & ~3) * 4u : 0u;
-            mbar_arrive_expect(&bar[1], hbytes + tbytes);
+            mbar_arrive_expect(&bar[1], hbytes);
             if (hbytes) bulk_g2s(s_hi, a.hi_in + base, hbytes, &bar[1]);
-            if (tbytes) bulk_g2s(s_tod, a.tod_in + base, tbytes, &bar[1]);
+        }
+    };
+    // the second part, over the ranking tables: records of the second half,
+    // or the TOD values
+    auto issue_win2 = [&](int64_t base, int cnt) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (!FIRST) {
+            const uint32_t n2 = cnt > SC_TILE / 2 ? (uint32_t)(cnt - SC_TILE / 2) : 0u;
+            mbar_arrive_expect(&bar[2], n2 * 16u);
+            if (n2) bulk_g2s(s_rec + SC_TILE / 2, a.rec_in + base + SC_TILE / 2, n2 * 16u, &bar[2]);
+        } else {
+            const uint32_t tbytes = tod_bulk ? (uint32_t)(cnt & ~3) * 4u : 0u;
+            mbar_arrive_expect(&bar[2], tbytes);
+            if (tbytes) bulk_g2s(s_tod, a.tod_in + base, tbytes, &bar[2]);
         }
     };
     // Gives up the block after a failed wait: flags the error, waits (again
     // bounded) for the copies still in flight so that none lands after the
     // block has exited, and returns true.
-    auto give_up = [&](bool failed, uint32_t key_parity, uint32_t win_parity) {
+    auto give_up = [&](bool failed, uint32_t key_parity, uint32_t win_parity, bool win2_issued) {
         if (!__syncthreads_or(failed)) return false;
         if (threadIdx.x == 0) {
             atomicExch(a.err, 1ull);
             mbar_wait(&bar[0], key_parity);
             mbar_wait(&bar[1], win_parity);
+            if (win2_issued) mbar_wait(&bar[2], win_parity);
         }
         return true;
     };
 
     if (threadIdx.x == 0 && begin < end) {
         issue_keys(begin, (int)(end - begin < SC_TILE ? end - begin : SC_TILE));
-        issue_win(begin, (int)(end - begin < SC_TILE ? end - begin : SC_TILE));
+        issue_win1(begin, (int)(end - begin < SC_TILE ? end - begin : SC_TILE));
     }
     uint32_t parity = 0;
     for (int64_t base = begin; base < end; base += SC_TILE, parity ^= 1u) {
         const int cnt = (int)(end - base < SC_TILE ? end - base : SC_TILE);
         // the ragged end of the last tile, with plain loads
         for (int j = (cnt & ~3) + threadIdx.x; j < cnt; j += SC_THREADS) s_keys[j] = a.keys_in[base + j];
-        if (FIRST) {
-            if ((cnt & 1) && threadIdx.x == 0) s_hi[cnt - 1] = a.hi_in[base + cnt - 1];
-            if (a.tod_in)
-                for (int j = (tod_bulk ? (cnt & ~3) : 0) + threadIdx.x; j < cnt; j += SC_THREADS)
-                    s_tod[j] = a.tod_in[base + j];
-        }
-        if (give_up(!mbar_wait(&bar[0], parity), parity, parity)) return;
+        if (FIRST && (cnt & 1) && threadIdx.x == 0) s_hi[cnt - 1] = a.hi_in[base + cnt - 1];
+        if (give_up(!mbar_wait(&bar[0], parity), parity, parity, false)) return;
         __syncthreads();  // the plain-loaded keys too
         uint32_t key[IG_PER_THREAD], rank[IG_PER_THREAD];
         // 1. the warp's 512 consecutive keys, 32 per round
@@ -451,44 +466,41 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
         //    of the SM here, these shared-memory operations ~2.  The group's
         //    leader adds the group size to the warp's digit counter and
         //    broadcasts the count before it; rounds add in program order, so
-        //    ranks follow the input order (a stable sort).  The tables use
-        //    the keys' buffer, free once the keys are in registers: one table
-        //    of 2^10 entries per warp of a wave, the warps in
-        //    SC_WARPS / kRankRows waves.  Two 16-bit digit counters share a
-        //    32-bit word (a warp counts at most 512 samples a digit), so an
-        //    add never carries into the neighbour.
-        __syncthreads();  // every warp has its keys
+        //    ranks follow the input order (a stable sort).  One table of 2^10
+        //    entries per warp, in the window's second half.  Two 16-bit digit
+        //    counters share a 32-bit word (a warp counts at most 512 samples
+        //    a digit), so an add never carries into the neighbour.
         {
-            uint4* z = reinterpret_cast<uint4*>(s_keys);
-            for (int i = threadIdx.x; i < SC_TILE / 4; i += SC_THREADS) z[i] = make_uint4(0u, 0u, 0u, 0u);
+            uint4* z = reinterpret_cast<uint4*>(s_tbl);
+            for (int i = threadIdx.x; i < SC_TILE / 2; i += SC_THREADS) z[i] = make_uint4(0u, 0u, 0u, 0u);
         }
         __syncthreads();
-        uint32_t* wcnt32 = reinterpret_cast<uint32_t*>(wcnt);
-        for (int wave = 0; wave < SC_WARPS / kRankRows; ++wave) {
-            if (w / kRankRows == wave) {
-                uint32_t* tbl = s_keys + (w % kRankRows) * 1024;
+        {
+            uint32_t* wcnt32 = reinterpret_cast<uint32_t*>(wcnt);
+            uint32_t* tbl = s_tbl + w * 1024;
 #pragma unroll
-                for (int r = 0; r < IG_PER_THREAD; ++r) {
-                    const int j = w * IG_WARP_SPAN + r * 32 + lane;
-                    const bool valid = j < cnt;
-                    const uint32_t d = (key[r] >> a.shift) & dmask;
-                    if (valid) atomicOr(tbl + d, 1u << lane);
-                    __syncwarp();
-                    const unsigned peers = valid ? tbl[d] : (1u << lane);
-                    __syncwarp();
-                    const int leader = __ffs(peers) - 1;
-                    uint32_t old = 0;
-                    if (valid && lane == leader) {
-                        const uint32_t sh = 16u * (d & 1u);
-                        old = (atomicAdd(wcnt32 + ((w * bins + d) >> 1), (uint32_t)__popc(peers) << sh) >> sh) & 0xFFFFu;
-                        tbl[d] = 0u;
-                    }
-                    rank[r] = __shfl_sync(0xffffffffu, old, leader) + __popc(peers & lt_mask);
-                    __syncwarp();  // the entry is clear before the next round's ORs
+            for (int r = 0; r < IG_PER_THREAD; ++r) {
+                const int j = w * IG_WARP_SPAN + r * 32 + lane;
+                const bool valid = j < cnt;
+                const uint32_t d = (key[r] >> a.shift) & dmask;
+                if (valid) atomicOr(tbl + d, 1u << lane);
+                __syncwarp();
+                const unsigned peers = valid ? tbl[d] : (1u << lane);
+                __syncwarp();
+                const int leader = __ffs(peers) - 1;
+                uint32_t old = 0;
+                if (valid && lane == leader) {
+                    const uint32_t sh = 16u * (d & 1u);
+                    old = (atomicAdd(wcnt32 + ((w * bins + d) >> 1), (uint32_t)__popc(peers) << sh) >> sh) & 0xFFFFu;
+                    tbl[d] = 0u;
                 }
+                rank[r] = __shfl_sync(0xffffffffu, old, leader) + __popc(peers & lt_mask);
+                __syncwarp();  // the entry is clear before the next round's ORs
             }
-            __syncthreads();
         }
+        __syncthreads();
+        // the tables are done with: the window's second part can come in
+        if (threadIdx.x == 0) issue_win2(base, cnt);
         // 3. per digit: exclusive prefix over warps, tile count; then over digits
         for (int d = threadIdx.x; d < bins; d += SC_THREADS) {
             uint32_t t = 0;
@@ -521,11 +533,19 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
                 s_src[rank[r]] = (uint16_t)j;
             }
         }
+        // a TOD that is not bulk-copied (off a 16-byte boundary, or the
+        // ragged end), with plain loads
+        if (FIRST && a.tod_in)
+            for (int j = (tod_bulk ? (cnt & ~3) : 0) + threadIdx.x; j < cnt; j += SC_THREADS) s_tod[j] = a.tod_in[base + j];
         __syncthreads();
         if (threadIdx.x == 0 && base + SC_TILE < end)
             issue_keys(base + SC_TILE, (int)(end - base - SC_TILE < SC_TILE ? end - base - SC_TILE : SC_TILE));
         // (the next tile's keys may be on their way: the other key phase)
-        if (give_up(!mbar_wait(&bar[1], parity), base + SC_TILE < end ? parity ^ 1u : parity, parity)) return;
+        {
+            const uint32_t kp = base + SC_TILE < end ? parity ^ 1u : parity;
+            if (give_up(!mbar_wait(&bar[1], parity), kp, parity, true)) return;
+            if (give_up(!mbar_wait(&bar[2], parity), kp, parity, true)) return;
+        }
         // 5. each digit's run goes to its running global offset, the rest of
         //    each sample from the window in shared memory
         for (int j = threadIdx.x; j < cnt; j += SC_THREADS) {
@@ -561,7 +581,7 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
             for (int q = 0; q < SC_WARPS; ++q) wcnt[q * bins + d] = 0;
         }
         if (threadIdx.x == 0 && base + SC_TILE < end)
-            issue_win(base + SC_TILE, (int)(end - base - SC_TILE < SC_TILE ? end - base - SC_TILE : SC_TILE));
+            issue_win1(base + SC_TILE, (int)(end - base - SC_TILE < SC_TILE ? end - base - SC_TILE : SC_TILE));
         __syncthreads();
     }
 }
