@@ -170,9 +170,10 @@ KERNELS = {"ingest_validate": "validate_kernel", "ingest_hist": "rs_hist_kernel"
            "ingest_scatter": "rs_scatter_kernel", "blocks": "blocks_kernel", "rhs": "gather_reduce_kernel",
            "matvec_white_f32": "white_matvec_f32_kernel"}
 TRAFFIC = {
-    # ncu DRAM bytes per launch, per family, from a capture of the current
-    # kernel on the 67M-sample case scaled by the samples (none yet for the
-    # shared-memory-staged scatter: reported as null)
+    # profiles/ingest_sort_nside256_256x262144.md: 42.4 and 44.0 DRAM bytes
+    # per sample for the two scatter passes (mean 43.2) on the 67M-sample
+    # case; the traffic grows in proportion to the samples
+    "ingest_scatter": lambda n: 43.2 * n,
 }
 
 
