@@ -79,8 +79,10 @@ constexpr int kBlkWarps = 8;
 // that the FP32 matvec reads.  With RHS (white noise and a TOD sorted along
 // with the pointing) it also sums b = P^T N^-1 d per item into rpartial, with
 // the double-float steps of the pixel-sorted gather-reduce of the RHS (the
-// same operations in the same order, so the same bits).
-template <int NC, bool WCS, bool RHS>
+// same operations in the same order, so the same bits).  EXACT: the trig
+// pairs are exact FP32 values (no lo part), so the block products multiply
+// by a float instead of a double-float.
+template <int NC, bool WCS, bool RHS, bool EXACT>
 __global__ void __launch_bounds__(kBlkWarps * 32)
 blocks_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ item_beg,
               const int32_t* __restrict__ item_len, int64_t nitems, const uint32_t* __restrict__ perm,
@@ -110,9 +112,19 @@ blocks_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ 
         for (int j = 0; j < NS; ++j) acc[j] = {0.f, 0.f};
 #pragma unroll
         for (int j = 0; j < NC; ++j) racc[j] = {0.f, 0.f};
+        // A lane's samples of one item are in increasing time order (the sort
+        // is stable), so its detector changes only when t passes the current
+        // detector's end: look the detector up only then.
+        uint32_t dend = 0;
+        float2 wv = make_float2(0.f, 0.f);
+        float swv = 0.f;
         auto add = [&](int64_t si, uint32_t t, float2 h, float2 l, float dv) {
-            const int d = det_of(offp, ndet, g.ns, g.inv_ns, t);
-            const float2 wv = wp[d];
+            if (t >= dend) {
+                const int d = det_of(offp, ndet, g.ns, g.inv_ns, t);
+                dend = g.ns ? (uint32_t)(d + 1) * g.ns : offp[d + 1];
+                wv = wp[d];
+                if (WCS && NC > 1) swv = swp[d];
+            }
             const df32 w = {wv.x, wv.y};
             const df32 c = {h.x, l.x}, s = {h.y, l.y};
             if (RHS) {
@@ -126,18 +138,18 @@ blocks_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ 
                 }
             }
             if (NC == 3) {
-                const df32 wc = df_mul(w, c), ws = df_mul(w, s);
+                const df32 wc = EXACT ? df_mul(w, h.x) : df_mul(w, c), ws = EXACT ? df_mul(w, h.y) : df_mul(w, s);
                 acc[0] = df_add(acc[0], w);
                 acc[1] = df_add(acc[1], wc);
                 acc[2] = df_add(acc[2], ws);
-                acc[3] = df_add(acc[3], df_mul(wc, c));
-                acc[4] = df_add(acc[4], df_mul(wc, s));
-                acc[5] = df_add(acc[5], df_mul(ws, s));
+                acc[3] = df_add(acc[3], EXACT ? df_mul(wc, h.x) : df_mul(wc, c));
+                acc[4] = df_add(acc[4], EXACT ? df_mul(wc, h.y) : df_mul(wc, s));
+                acc[5] = df_add(acc[5], EXACT ? df_mul(ws, h.y) : df_mul(ws, s));
             } else if (NC == 2) {
-                const df32 wc = df_mul(w, c), ws = df_mul(w, s);
-                acc[0] = df_add(acc[0], df_mul(wc, c));
-                acc[1] = df_add(acc[1], df_mul(wc, s));
-                acc[2] = df_add(acc[2], df_mul(ws, s));
+                const df32 wc = EXACT ? df_mul(w, h.x) : df_mul(w, c), ws = EXACT ? df_mul(w, h.y) : df_mul(w, s);
+                acc[0] = df_add(acc[0], EXACT ? df_mul(wc, h.x) : df_mul(wc, c));
+                acc[1] = df_add(acc[1], EXACT ? df_mul(wc, h.y) : df_mul(wc, s));
+                acc[2] = df_add(acc[2], EXACT ? df_mul(ws, h.y) : df_mul(ws, s));
             } else {
                 acc[0] = df_add(acc[0], w);
             }
@@ -145,32 +157,32 @@ blocks_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ 
                 if (NC == 1) {
                     w1[si] = wv.x;
                 } else {
-                    const float sw = swp[d];
-                    wcs[si] = make_float2(sw * h.x, sw * h.y);
+                    wcs[si] = make_float2(swv * h.x, swv * h.y);
                 }
             }
         };
-        // four samples per lane in flight (their loads issued together); the
-        // lane's samples are still added in order
+        // kUnroll samples per lane in flight (their loads issued together);
+        // the lane's samples are still added in order
+        constexpr int kUnroll = 4;
         int i = lane;
-        for (; i + 96 < len; i += 128) {
-            uint32_t t[4];
-            float2 h[4], l[4];
-            float dv[4];
+        for (; i + 32 * (kUnroll - 1) < len; i += 32 * kUnroll) {
+            uint32_t t[kUnroll];
+            float2 h[kUnroll], l[kUnroll];
+            float dv[kUnroll];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kUnroll; ++u) {
                 const int64_t si = b + i + 32 * u;
                 t[u] = perm[si];
                 h[u] = hi[si];
-                l[u] = lo ? lo[si] : make_float2(0.f, 0.f);
+                l[u] = (!EXACT && lo) ? lo[si] : make_float2(0.f, 0.f);
                 dv[u] = RHS ? tod_s[si] : 0.f;
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) add(b + i + 32 * u, t[u], h[u], l[u], dv[u]);
+            for (int u = 0; u < kUnroll; ++u) add(b + i + 32 * u, t[u], h[u], l[u], dv[u]);
         }
         for (; i < len; i += 32) {
             const int64_t si = b + i;
-            add(si, perm[si], hi[si], lo ? lo[si] : make_float2(0.f, 0.f), RHS ? tod_s[si] : 0.f);
+            add(si, perm[si], hi[si], (!EXACT && lo) ? lo[si] : make_float2(0.f, 0.f), RHS ? tod_s[si] : 0.f);
         }
 #pragma unroll
         for (int j = 0; j < NS; ++j) acc[j] = df_warp_sum(acc[j]);
@@ -350,10 +362,16 @@ void build_precond(bm_precond* pc) {
         if (all.n > 0) {
             const int64_t wunits = (all.n + kBlkWarps - 1) / kBlkWarps;
             const DetTables g{n->det_off32.get(), n->wdf.get(), n->wsqrt.get(), n->ns_uniform, n->inv_ns};
-#define BM_BLOCKS(NC, W, R)                                                                                 \
-    blocks_kernel<NC, W, R><<<resident_grid(ctx, blocks_kernel<NC, W, R>, kBlkWarps * 32, wunits), kBlkWarps * 32, 0, s>>>( \
+#define BM_BLOCKS3(NC, W, R, E)                                                                              \
+    blocks_kernel<NC, W, R, E><<<resident_grid(ctx, blocks_kernel<NC, W, R, E>, kBlkWarps * 32, wunits), kBlkWarps * 32, 0, s>>>( \
         all.pix.get(), all.beg.get(), all.len.get(), all.n, p->perm.get(), p->cs_hi_s.get(), p->cs_lo_s.get(), g,     \
         n->ndet, partial.get(), pc->wcs.get(), pc->w1.get(), p->tod_s.get(), rpartial.get())
+#define BM_BLOCKS(NC, W, R)                  \
+    do {                                     \
+        if (exact) BM_BLOCKS3(NC, W, R, true); \
+        else BM_BLOCKS3(NC, W, R, false);    \
+    } while (0)
+            const bool exact = p->cs_lo_s.get() == nullptr;  // FP32 trig given: exact float multiplies
             if (with_rhs) {
                 if (nc == 3) BM_BLOCKS(3, true, true); else if (nc == 2) BM_BLOCKS(2, true, true); else BM_BLOCKS(1, true, true);
             } else if (white) {
@@ -361,6 +379,7 @@ void build_precond(bm_precond* pc) {
             } else {
                 if (nc == 3) BM_BLOCKS(3, false, false); else if (nc == 2) BM_BLOCKS(2, false, false); else BM_BLOCKS(1, false, false);
             }
+#undef BM_BLOCKS3
 #undef BM_BLOCKS
             BM_LAUNCH_CHECK();
         }
