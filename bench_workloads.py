@@ -196,7 +196,7 @@ def run_config2(args):
     ms = (time.perf_counter() - t0) * 1000 / args.steps
     clocks = sampler.stop()
     fam = {}
-    for name in ("ingest", "blocks", "rhs", "toeplitz_f32", "toeplitz_refine", "toeplitz_f64", "toeplitz_pt"):
+    for name in ("ingest", "blocks", "rhs", "toeplitz_f32", "toeplitz_refine", "toeplitz_f64", "toeplitz_pt", "toeplitz_pt_bounds"):
         tot, cnt = L.bm_context_kernel_time(ctx, name)
         if cnt:
             fam[name] = {"ms_per_launch": tot / cnt, "launches_per_step": cnt / args.steps}

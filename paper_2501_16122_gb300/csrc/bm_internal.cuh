@@ -199,6 +199,11 @@ struct bm_precond {
     // White noise and a TOD carried by the pointing: b = P^T N^-1 d_m of that
     // TOD in double-float (the mixed solve's RHS), zero on masked pixels.
     bm::DevBuf<double> b_tod;      // [npix][ncomp] or empty
+    // Toeplitz noise, inner operator's transpose by time chunks: per pixel,
+    // the start of its samples in each chunk (built on first use; pt_nch = 0
+    // not built yet, -1 not used)
+    int pt_nch = 0;
+    bm::DevBuf<int32_t> pt_sub;    // [pt_nch + 1][npix]
 };
 
 namespace bm {

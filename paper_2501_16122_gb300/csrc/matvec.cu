@@ -446,6 +446,129 @@ __global__ void finalize_pixels_kernel(const int64_t* __restrict__ pitem, const 
     }
 }
 
+// ------------------------------------------------ time-chunked transpose
+// The mixed Toeplitz operator's transpose q_p = sum_i z[perm_i] v_i gathers
+// 4-byte z values at random time positions: each costs a DRAM sector.  It
+// runs instead one time chunk of kPtChunk samples at a time (64 MB of z, which
+// stays in L2), over each kept pixel's samples in that chunk: a pixel's
+// samples are in time order in the sorted layout, so those of one chunk are
+// contiguous.  Each pixel's double-float accumulator is updated chunk after
+// chunk by one group of lanes (a fixed order: deterministic).
+constexpr int kPtChunkBits = 24;
+constexpr int kPtLanes = 8;  // lanes per pixel
+
+// sub[c * npix + p] = the first position of pixel p's run (counted from
+// off[p]) whose sample lies in chunk c or later, for c in [0, nch]; c = nch
+// gives the run's length.  Chunk-major, so that a chunk's pass reads two
+// contiguous rows.  One warp per pixel; every entry is written exactly once.
+__global__ void pt_bounds_kernel(const int64_t* __restrict__ off, const uint32_t* __restrict__ perm, int64_t npix,
+                                 int nch, int32_t* __restrict__ sub) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < npix; p += nwarps) {
+        const int64_t b = off[p];
+        const int32_t len = (int32_t)(off[p + 1] - b);
+        int32_t* s = sub + p;
+        const int f = len ? (int)(perm[b] >> kPtChunkBits) : nch;
+        const int l = len ? (int)(perm[b + len - 1] >> kPtChunkBits) : nch;
+        for (int c = lane; c <= nch; c += 32) {
+            if (c <= f) s[(int64_t)c * npix] = 0;
+            else if (c > l) s[(int64_t)c * npix] = len;
+        }
+        for (int32_t i = lane + 1; i < len; i += 32) {
+            const int c0 = (int)(perm[b + i - 1] >> kPtChunkBits), c1 = (int)(perm[b + i] >> kPtChunkBits);
+            for (int c = c0 + 1; c <= c1; ++c) s[(int64_t)c * npix] = i;
+        }
+    }
+}
+
+// One chunk of the transpose: per kept pixel, the sum over its samples in
+// chunk c of z v (FP32 products, summed in FP32 groups of up to 4 per lane and
+// folded into double-float), added to the pixel's accumulator.  kPtLanes lanes per pixel, the warp's groups on consecutive
+// pixels.
+template <int NC>
+__global__ void __launch_bounds__(kWarps * 32)
+pt_chunk_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ sub, const uint8_t* __restrict__ mask,
+                int64_t npix, int nch, int c, const uint32_t* __restrict__ perm, const float2* __restrict__ hi,
+                const float* __restrict__ z, float2* __restrict__ acc) {
+    constexpr int G = 32 / kPtLanes;
+    const int lane = threadIdx.x & 31, gl = lane % kPtLanes, grp = lane / kPtLanes;
+    const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+    for (int64_t pw = ((int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5)) * G; pw < npix; pw += nwarps * G) {
+        const int64_t p = pw + grp;
+        int64_t b = 0;
+        int32_t s0 = 0, s1 = 0;
+        if (p < npix && !mask[p]) {
+            b = off[p];
+            s0 = sub[(int64_t)c * npix + p];
+            s1 = sub[(int64_t)(c + 1) * npix + p];
+        }
+        float a[NC];
+        df32 A[NC];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            a[k] = 0.f;
+            A[k] = {0.f, 0.f};
+        }
+        // four samples per lane with their loads issued together, summed in
+        // FP32 and folded into double-float per batch
+        for (int32_t i0 = s0; i0 < s1; i0 += 4 * kPtLanes) {
+            uint32_t t[4];
+            float v[4];
+            float2 h[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int32_t i = i0 + gl + u * kPtLanes;
+                t[u] = i < s1 ? perm[b + i] : 0xFFFFFFFFu;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int32_t i = i0 + gl + u * kPtLanes;
+                v[u] = t[u] != 0xFFFFFFFFu ? z[t[u]] : 0.f;
+                h[u] = (NC > 1 && i < s1) ? hi[b + i] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (NC == 1) {
+                    a[0] += v[u];
+                } else {
+                    if (NC == 3) a[0] += v[u];
+                    a[NC - 2] = fmaf(v[u], h[u].x, a[NC - 2]);
+                    a[NC - 1] = fmaf(v[u], h[u].y, a[NC - 1]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+                A[k] = df_add(A[k], a[k]);
+                a[k] = 0.f;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            A[k] = df_add(A[k], a[k]);
+#pragma unroll
+            for (int o = kPtLanes / 2; o > 0; o >>= 1) A[k] = df_add(A[k], df_shfl_xor(A[k], o));
+        }
+        if (gl == 0 && s1 > s0) {
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+                const float2 old = acc[p * NC + k];
+                const df32 s = df_add(df32{old.x, old.y}, A[k]);
+                acc[p * NC + k] = make_float2(s.hi, s.lo);
+            }
+        }
+    }
+}
+
+__global__ void pt_finalize_kernel(const float2* __restrict__ acc, const uint8_t* __restrict__ mask, int64_t npix,
+                                   int nc, double* __restrict__ q) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x)
+        for (int k = 0; k < nc; ++k) {
+            const float2 s = acc[p * nc + k];
+            q[p * nc + k] = mask[p] ? 0.0 : (double)s.x + (double)s.y;
+        }
+}
+
 // ------------------------------------------------------- time-ordered work
 // y = P x over every non-flagged sample (FP64 trig).
 __global__ void pointing_apply_kernel(const int32_t* __restrict__ pix, const float2* __restrict__ hi,
@@ -784,6 +907,47 @@ static void gather_reduce_f32(bm_pointing* p, const ItemsView& it, const float* 
     finalize(ctx, it.pitem, partial, p->npix, nc, q);
 }
 
+// The inner Toeplitz operator's transpose, time chunk by time chunk (see
+// pt_chunk_kernel); the plain pixel-sorted gather when the table of sub-run
+// bounds would exceed kPtSubMaxBytes.
+constexpr size_t kPtSubMaxBytes = size_t(1) << 31;
+static void pt_chunked(bm_pointing* p, bm_precond* pc, const float* z, double* q) {
+    bm_context* ctx = p->ctx;
+    cudaStream_t s = ctx->stream;
+    const int nc = p->ncomp;
+    const int64_t npix = p->npix;
+    const int nch = (int)((p->nsamples + (int64_t(1) << kPtChunkBits) - 1) >> kPtChunkBits);
+    if (pc->pt_nch == 0) {  // first use: the table of sub-run bounds
+        if ((size_t)npix * (size_t)(nch + 1) * sizeof(int32_t) > kPtSubMaxBytes) {
+            pc->pt_nch = -1;
+        } else {
+            ScopedTimer timer(ctx, "toeplitz_pt_bounds");
+            pc->pt_sub.alloc((size_t)npix * (nch + 1));
+            pt_bounds_kernel<<<grid_for(ctx, (npix + 7) / 8, 16), 256, 0, s>>>(p->off.get(), p->perm.get(), npix, nch,
+                                                                             pc->pt_sub.get());
+            BM_LAUNCH_CHECK();
+            pc->pt_nch = nch;
+        }
+    }
+    if (pc->pt_nch < 0) {
+        gather_reduce_f32(p, kept_items(pc), z, q);
+        return;
+    }
+    float2* acc = workspace_as<float2>(ctx, "pt_acc", (size_t)npix * nc);
+    BM_CUDA(cudaMemsetAsync(acc, 0, sizeof(float2) * (size_t)npix * nc, s));
+    const int64_t wunits = ((npix + 3) / 4 + kWarps - 1) / kWarps;
+    for (int c = 0; c < nch; ++c) {
+#define BM_PT(NC)                                                                                                  \
+    pt_chunk_kernel<NC><<<resident_grid(ctx, pt_chunk_kernel<NC>, kWarps * 32, wunits), kWarps * 32, 0, s>>>(       \
+        p->off.get(), pc->pt_sub.get(), pc->mask.get(), npix, nch, c, p->perm.get(), p->cs_hi_s.get(), z, acc)
+        if (nc == 3) BM_PT(3); else if (nc == 2) BM_PT(2); else BM_PT(1);
+#undef BM_PT
+        BM_LAUNCH_CHECK();
+    }
+    pt_finalize_kernel<<<grid_for(ctx, (npix + 255) / 256, 16), 256, 0, s>>>(acc, pc->mask.get(), npix, nc, q);
+    BM_LAUNCH_CHECK();
+}
+
 template <typename G>
 static void gather_reduce(bm_pointing* p, const ItemsView& it, const G* g, const bm_inv_noise* wn,
                           const float2* lo, bool df, double* q, const float* gs = nullptr) {
@@ -870,7 +1034,7 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
                 }
                 // scatter with the same FP32 trig the gather used (symmetric operator)
                 ScopedTimer timer(ctx, "toeplitz_pt");
-                gather_reduce_f32(p, kept_items(pc), z32, qr);
+                pt_chunked(p, pc, z32, qr);
             } else {
                 // FP64, or the refinement operator: the same with a
                 // double-float filter and pixel sums

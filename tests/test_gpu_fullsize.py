@@ -163,6 +163,44 @@ def test_config2_full_size(L, ctx):
         f(h)
 
 
+def test_toeplitz_mixed_matvec_over_time_chunks(L, ctx):
+    """The mixed-precision Toeplitz matvec, whose transpose runs one time chunk
+    of 2^24 samples at a time, over three chunks with a ragged last one
+    (8 det x (2^22 + 4097) samples): against the oracle's windowed evaluation
+    on sampled pixels (the FP32 operator's tolerance), next to the FP64 path."""
+    e = synth.make_experiment(64, 8, 2 ** 22 + 4097, 1404)
+    pt = synth.pointing(e, flag_frac=0.01)
+    c32, s32 = synth.trig32(pt["psi"])
+    chunk = 2 ** 20
+    coeffs = synth.toeplitz_band(e.sigma, 0.1, 1.0, 20.0, chunk, 128)
+    p = L.bm_pointing_create_trig(ctx, e.npix, torch.from_numpy(pt["pix"]).cuda(), torch.from_numpy(c32).cuda(),
+                                  torch.from_numpy(s32).cuda(), 3)
+    n = L.bm_inv_noise_create_toeplitz(ctx, e.det_offsets, chunk, coeffs, 1 / e.sigma ** 2)
+    pc = L.bm_blockdiag_precond_create(p, n, 3, 1e3)
+    mask = torch.zeros(e.npix, dtype=torch.uint8, device="cuda")
+    hits = torch.zeros(e.npix, dtype=torch.int32, device="cuda")
+    L.bm_precond_get_mask(pc, mask, hits)
+    mask_h, hits_h = mask.cpu().numpy().astype(bool), hits.cpu().numpy()
+    rng = np.random.default_rng(2)
+    x = rng.normal(size=(e.npix, 3)) * np.array([100.0, 10.0, 10.0])
+    pixels = sampled_pixels(hits_h, mask_h, rng, n=10)
+    ref = oracle_toeplitz_matvec_pixels(e, pt["pix"], c32, s32, coeffs, chunk, mask_h, x * (~mask_h)[:, None], pixels)
+    for prec, tol in ((L.BM_PREC_FP64, 1e-10), (L.BM_PREC_MIXED, 2e-6)):
+        q = torch.zeros(e.npix * 3, dtype=torch.float64, device="cuda")
+        L.bm_matvec(p, n, pc, torch.from_numpy(x.ravel()).cuda(), q, prec)
+        qh = q.cpu().numpy().reshape(e.npix, 3)
+        for k in range(3):
+            err = np.linalg.norm(qh[pixels, k] - ref[:, k]) / np.linalg.norm(ref[:, k])
+            assert err < tol, (prec, k, err)
+        assert np.all(qh[mask_h] == 0)
+        if prec == L.BM_PREC_MIXED:  # deterministic: a second call gives the same bits
+            q2 = torch.zeros_like(q)
+            L.bm_matvec(p, n, pc, torch.from_numpy(x.ravel()).cuda(), q2, prec)
+            assert torch.equal(q, q2)
+    for h, f in ((pc, L.bm_precond_destroy), (n, L.bm_inv_noise_destroy), (p, L.bm_pointing_destroy)):
+        f(h)
+
+
 def test_config3_full_size(L, ctx):
     e = synth.make_experiment(512, 64, 2 ** 22, 1003)
     pt = synth.pointing(e)
