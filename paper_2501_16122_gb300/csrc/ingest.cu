@@ -14,12 +14,12 @@
 // then walks its own range tile by tile, placing a tile's samples at its
 // running per-digit offsets.  The counter array stays small (G is a few
 // times the SM count), so the digits can be wide: up to 10 bits, two passes
-// for npix < 2^20 (nside <= 256), three up to nside 2048, one below 2^10.  Inside a tile the
+// for npix < 2^20 (nside <= 256), three up to nside 2048, one below 2^10.  A
+// tile's keys and payload arrive in shared memory by bulk (TMA) copies; the
 // stable rank of a sample comes from per-warp counters updated round by round
-// (match_any groups equal digits within a round), and the tile is staged in
-// shared memory in digit order so that each digit's run is written
-// contiguously.  Each thread loads its 16 samples (key, index, trig pair)
-// before ranking them, so a tile costs one memory latency, not one per round.
+// (the lanes of a round holding the same digit found through lane-mask tables
+// in shared memory), and the tile is staged in digit order so that each
+// digit's run is written contiguously (see rs_scatter_kernel).
 //
 // The trig pairs travel with the keys as payload (each pass reads and writes
 // them once, in tile order): on this part a random 8-byte read moves about
