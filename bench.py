@@ -43,7 +43,7 @@ METRIC = "TOD samples/s per PᵀN⁻¹P matvec (%HBM peak); PCG time-to-map at 1
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--nside", type=int, default=256)
@@ -86,12 +86,13 @@ class ClockSampler:
 
     def __init__(self, gpu: int):
         self.gpu, self.proc, self.lines = gpu, None, []
+        self.window = None  # (t0, t1) monotonic seconds of the timed region, when marked
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={','.join(self.FIELDS)}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50", "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
@@ -99,7 +100,11 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def mark(self, t0: float, t1: float):
+        """Keep only the samples taken between t0 and t1 (time.monotonic())."""
+        self.window = (t0, t1)
 
     def stop(self):
         if self.proc is None:
@@ -112,7 +117,10 @@ class ClockSampler:
         self.t.join(timeout=2)
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = self.lines
+        if self.window is not None:
+            lines = [(ts, ln) for ts, ln in lines if self.window[0] <= ts <= self.window[1]]
+        for _, ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -266,22 +274,26 @@ def run_gb300(args, rank, world, local_rank):
         L.bm_inv_noise_destroy(n)
         L.bm_pointing_destroy(p)
 
-    for _ in range(args.warmup):
-        step(d_pix, d_trig, d_tod)
-    # --- timed region (device-resident inputs)
+    # clocks are sampled from before the warm-up (nvidia-smi takes a moment to
+    # start) and kept for the timed region only
     sampler = ClockSampler(local_rank)
     if not args.profile:
         sampler.start()
+    for _ in range(args.warmup):
+        step(d_pix, d_trig, d_tod)
+    # --- timed region (device-resident inputs)
     L.bm_context_set_timing(ctx, True)
     launches0 = L.bm_kernel_launches()
     barrier()
     torch.cuda.synchronize()
+    t_wall0 = time.monotonic()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
         step(d_pix, d_trig, d_tod)
     ev1.record(stream)
     torch.cuda.synchronize()
+    sampler.mark(t_wall0, time.monotonic())
     barrier()
     launches = L.bm_kernel_launches() - launches0
     ms = ev0.elapsed_time(ev1) / args.steps
