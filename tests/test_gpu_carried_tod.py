@@ -147,3 +147,31 @@ def test_carried_tod_errors(L, ctx):
             L.bm_pointing_create_with_tod(ctx, c.npix, c.d_pix, c.d_tod)
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("offset", [1, 2, 3])
+def test_carried_tod_off_a_16_byte_boundary(L, ctx, offset):
+    """A TOD view that starts 4, 8 or 12 bytes past a 16-byte boundary is read
+    with plain loads instead of bulk copies by the first sort pass: the same
+    RHS, bit for bit, as the gathered time-ordered TOD (two sort passes, a
+    ragged last tile)."""
+    c = Case(L, ctx, 64, 3, 400_001, 91 + offset, flag=0.02, trig=True, tod_dtype=np.float32)
+    try:
+        c32, s32 = c.trig
+        full = torch.zeros(c.e.nsamples + offset, dtype=torch.float32, device="cuda")
+        full[offset:] = c.d_tod
+        tod = full[offset:]
+        assert tod.data_ptr() % 16 != 0
+        p1 = L.bm_pointing_create_with_tod(ctx, c.npix, c.d_pix, tod, cos2psi=torch.from_numpy(c32).cuda(),
+                                           sin2psi=torch.from_numpy(s32).cuda())
+        pc1 = L.bm_blockdiag_precond_create(p1, c.n, 3, 1e3)
+        try:
+            b0, b1 = c.vec(), c.vec()
+            L.bm_rhs(c.p, c.n, c.pc, c.d_tod, 1, b0)
+            L.bm_rhs(p1, c.n, pc1, None, 1, b1)
+            assert torch.equal(b0, b1)
+        finally:
+            L.bm_precond_destroy(pc1)
+            L.bm_pointing_destroy(p1)
+    finally:
+        c.close()
