@@ -185,6 +185,18 @@ bm_status bm_inv_noise_create_diag(bm_context* ctx, int32_t ndet, const int64_t*
 bm_status bm_inv_noise_create_toeplitz(bm_context* ctx, int32_t ndet, const int64_t* det_offsets,
                                        int64_t chunk_len, int32_t nlags, const double* coeffs,
                                        const double* white_inv_var, bm_inv_noise** out);
+/* Diagonal N^-1 = W with a weight per sample: the general weighting of
+ * Eq. 4 restricted to a diagonal W (s = (P^T W P)^-1 P^T W d), which covers
+ * gap treatment (weight 0 for samples to ignore) and sample-dependent noise
+ * levels.  weights FP64 [nsamples], each >= 0 and finite, in device or
+ * page-locked host memory; copied, so the caller may free them on return.
+ * The preconditioner of Eq. 7 is then exact per pixel (A is block diagonal),
+ * as for white noise; bm_blockdiag_precond_create gathers the weights into
+ * pixel-sorted order once (20 bytes a kept sample on the device).  Errors:
+ * BM_ERR_INVALID for nsamples outside [1, 2^32) or a negative or non-finite
+ * weight. */
+bm_status bm_inv_noise_create_sample_weights(bm_context* ctx, int64_t nsamples, const double* weights,
+                                             bm_inv_noise** out);
 void bm_inv_noise_destroy(bm_inv_noise* n);
 /* z = N^-1 y in FP64: y, z device FP64 [nsamples]. */
 bm_status bm_inv_noise_apply(bm_inv_noise* n, const double* y, double* z);

@@ -123,6 +123,23 @@ class WhiteNoise:
 
 
 @dataclass
+class SampleWeightNoise:
+    """Diagonal N^-1 = W with its own weight w_t >= 0 for every sample: the
+    general weighting of Eq. 4 with a diagonal W.  A weight of 0 takes the
+    sample out of every sum (gap treatment)."""
+    weights: np.ndarray  # [nsamples]
+
+    def sample_weights(self) -> np.ndarray:
+        return np.asarray(self.weights, np.float64)
+
+    def apply(self, y) -> np.ndarray:
+        return self.sample_weights() * y
+
+    def white_level(self) -> np.ndarray:
+        return self.sample_weights()
+
+
+@dataclass
 class ToeplitzNoise:
     """Banded symmetric Toeplitz N^-1 per chunk of each detector's samples:
     z_t = c_0 y_t + sum_{k=1}^{L-1} c_k (y_{t-k} + y_{t+k}), with y taken as
@@ -311,7 +328,7 @@ def dense_pointing(pe, v, npix: int) -> np.ndarray:
 
 def dense_inv_noise(noise, nt: int) -> np.ndarray:
     """N^-1 as a dense Nt x Nt matrix (diagonal, or block-diagonal Toeplitz bands)."""
-    if isinstance(noise, WhiteNoise):
+    if isinstance(noise, (WhiteNoise, SampleWeightNoise)):
         return np.diag(noise.sample_weights())
     Ni = np.zeros((nt, nt))
     off = np.asarray(noise.det_offsets, np.int64)

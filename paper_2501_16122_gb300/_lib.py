@@ -103,6 +103,7 @@ _SIGS = {
     "bm_pointing_apply_transpose": ([_P, _P, _P], ctypes.c_int),
     "bm_inv_noise_create_diag": ([_P, _i32, _P, _P, _PP], ctypes.c_int),
     "bm_inv_noise_create_toeplitz": ([_P, _i32, _P, _i64, _i32, _P, _P, _PP], ctypes.c_int),
+    "bm_inv_noise_create_sample_weights": ([_P, _i64, _P, _PP], ctypes.c_int),
     "bm_inv_noise_destroy": ([_P], None),
     "bm_inv_noise_apply": ([_P, _P, _P], ctypes.c_int),
     "bm_blockdiag_precond_create": ([_P, _P, _i32, _f64, _PP], ctypes.c_int),
@@ -307,6 +308,15 @@ def bm_inv_noise_create_toeplitz(ctx, det_offsets, chunk_len: int, coeffs, white
     out = ctypes.c_void_p()
     _check(lib.bm_inv_noise_create_toeplitz(ctx, off.size - 1, offp, int(chunk_len), c.shape[-1], cp, wvp,
                                             ctypes.byref(out)), "bm_inv_noise_create_toeplitz")
+    return out
+
+
+def bm_inv_noise_create_sample_weights(ctx, weights):
+    """Diagonal N^-1 with a weight per sample (FP64 device or pinned host tensor)."""
+    import torch
+    out = ctypes.c_void_p()
+    _check(lib.bm_inv_noise_create_sample_weights(ctx, weights.numel(), _in(weights, torch.float64, "weights"),
+                                                  ctypes.byref(out)), "bm_inv_noise_create_sample_weights")
     return out
 
 

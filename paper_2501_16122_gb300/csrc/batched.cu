@@ -218,7 +218,7 @@ batched_matvec_kernel(const int32_t* __restrict__ item_pix, const int64_t* __res
                     float rr = 0.f;
                     if (NC == 3) {
                         const float u2 = fmaf(ux, ux, uy * uy);
-                        rr = u2 * rsqrtf(u2);
+                        rr = u2 > 0.f ? u2 * rsqrtf(u2) : 0.f;
                     }
 #pragma unroll
                     for (int q = 0; q < RPL; ++q) {

@@ -142,13 +142,15 @@ struct bm_pointing {
 
 struct bm_inv_noise {
     bm_context* ctx = nullptr;
-    int kind = 0;  // 0 = diagonal white, 1 = banded Toeplitz
+    int kind = 0;  // 0 = diagonal white (a weight per detector), 1 = banded Toeplitz,
+                   // 2 = diagonal with a weight per sample (wsamp)
     int ndet = 0;
     int64_t nsamples = 0;
     std::vector<int64_t> h_det_off;
     std::vector<double> h_white;   // diag(N)^-1 per detector (the white level)
     bm::DevBuf<int64_t> det_off;   // [ndet + 1]
     bm::DevBuf<double> white;      // [ndet]
+    bm::DevBuf<double> wsamp;      // kind 2: [nsamples] weight of every sample, time order
     bm::DevBuf<uint32_t> det_off32;  // [ndet + 1] (nsamples < 2^32)
     bm::DevBuf<float2> wdf;          // [ndet] white level as double-float (hi, lo)
     bm::DevBuf<float> wsqrt;         // [ndet] sqrt of the white level, FP32
@@ -199,6 +201,10 @@ struct bm_precond {
     // White noise and a TOD carried by the pointing: b = P^T N^-1 d_m of that
     // TOD in double-float (the mixed solve's RHS), zero on masked pixels.
     bm::DevBuf<double> b_tod;      // [npix][ncomp] or empty
+    // Noise with a weight per sample: the weights in pixel-sorted order.
+    bm::DevBuf<float2> ws_df;      // [nvalid] double-float
+    bm::DevBuf<float> ws_sqrt;     // [nvalid] sqrt(w) in FP32
+    bm::DevBuf<double> ws64;       // [nvalid] FP64
     // Toeplitz noise, inner operator's transpose by time chunks: per pixel,
     // the start of its samples in each chunk (built on first use; pt_nch = 0
     // not built yet, -1 not used)
@@ -329,8 +335,28 @@ struct DetTables {
     const float* wsqrt;    // [ndet] sqrt(w) rounded to FP32
     uint32_t ns;           // samples per detector when all detectors have as many (else 0)
     float inv_ns;          // 1 / ns rounded to FP32
+    // Per-sample weights (diagonal W with a weight per sample), in pixel-sorted
+    // order, indexed like perm; null for per-detector weights.
+    const float2* wsort = nullptr;    // [nvalid] w as a double-float
+    const float* ssort = nullptr;     // [nvalid] sqrt(w) in FP32
+    const double* w64sort = nullptr;  // [nvalid] w in FP64
 };
 constexpr int kMaxDetSmem = 2048;  // detector tables staged in shared memory up to this count
+
+// The weight tables of a diagonal noise model for the pixel-sorted kernels:
+// per detector, plus (weights per sample) the preconditioner's sorted copy.
+inline DetTables det_tables(const bm_inv_noise* n, const bm_precond* pc) {
+    DetTables t{n->det_off32.get(), n->wdf.get(), n->wsqrt.get(), n->ns_uniform, n->inv_ns};
+    if (n->kind == 2 && pc) {
+        t.wsort = pc->ws_df.get();
+        t.ssort = pc->ws_sqrt.get();
+        t.w64sort = pc->ws64.get();
+    }
+    return t;
+}
+// N^-1 diagonal (a weight per detector or per sample): A = P^T N^-1 P is block
+// diagonal and the white-noise paths apply.
+inline bool diagonal_noise(const bm_inv_noise* n) { return n->kind != 1; }
 
 __device__ __forceinline__ int find_det32(const uint32_t* off, int ndet, uint32_t t) {
     int lo = 0, hi = ndet - 1;

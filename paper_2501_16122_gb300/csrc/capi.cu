@@ -459,6 +459,54 @@ bm_status bm_inv_noise_create_diag(bm_context* ctx, int32_t ndet, const int64_t*
     });
 }
 
+// Copies the per-sample weights and counts those that are negative or not
+// finite.
+__global__ void copy_check_weights_kernel(const double* __restrict__ w, int64_t n, double* __restrict__ out,
+                                          unsigned long long* __restrict__ nbad) {
+    unsigned bad = 0;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const double x = w[t];
+        bad += !(x >= 0.0 && x < 1e300);  // false for NaN
+        out[t] = x;
+    }
+    bad = __reduce_add_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0 && bad) atomicAdd(nbad, (unsigned long long)bad);
+}
+
+bm_status bm_inv_noise_create_sample_weights(bm_context* ctx, int64_t nsamples, const double* weights,
+                                             bm_inv_noise** out) {
+    return guarded([&] {
+        BM_REQUIRE(ctx && out, "ctx/out is NULL");
+        *out = nullptr;
+        BM_REQUIRE(nsamples >= 1 && nsamples < (int64_t(1) << 32), "nsamples out of [1, 2^32)");
+        BM_REQUIRE(weights != nullptr, "weights is NULL");
+        use_device(ctx);
+        weights = static_cast<const double*>(device_readable(ctx, weights, "weights"));
+        // one pseudo-detector of unit weight keeps the per-detector tables valid
+        const int64_t off[2] = {0, nsamples};
+        const double one = 1.0;
+        bm_inv_noise* n = new_noise(ctx, 1, off, &one);
+        try {
+            n->kind = 2;
+            n->wsamp.alloc(nsamples);
+            DevBuf<unsigned long long> nbad(1);
+            BM_CUDA(cudaMemsetAsync(nbad.get(), 0, sizeof(unsigned long long), ctx->stream));
+            copy_check_weights_kernel<<<grid_for(ctx, (nsamples + 255) / 256, 16), 256, 0, ctx->stream>>>(
+                weights, nsamples, n->wsamp.get(), nbad.get());
+            BM_LAUNCH_CHECK();
+            unsigned long long h_bad = 0;
+            BM_CUDA(cudaMemcpyAsync(&h_bad, nbad.get(), sizeof(h_bad), cudaMemcpyDeviceToHost, ctx->stream));
+            BM_CUDA(cudaStreamSynchronize(ctx->stream));
+            BM_REQUIRE(h_bad == 0, "%llu weights are negative or not finite", h_bad);
+        } catch (...) {
+            delete n;
+            throw;
+        }
+        *out = n;
+        return BM_OK;
+    });
+}
+
 bm_status bm_inv_noise_create_toeplitz(bm_context* ctx, int32_t ndet, const int64_t* det_offsets,
                                        int64_t chunk_len, int32_t nlags, const double* coeffs,
                                        const double* white_inv_var, bm_inv_noise** out) {
@@ -597,8 +645,8 @@ static void check_system(bm_pointing* p, bm_inv_noise* n, bm_precond* pc) {
     BM_REQUIRE(pc->p == p && pc->n->nsamples == n->nsamples && p->ctx == n->ctx,
                "preconditioner was built for another pointing / sample layout");
     BM_REQUIRE(n->nsamples == p->nsamples, "noise and pointing cover different sample counts");
-    if (n->kind == 0)
-        BM_REQUIRE(pc->n == n, "a white-noise system needs the preconditioner built from that noise");
+    if (diagonal_noise(n))
+        BM_REQUIRE(pc->n == n, "a diagonal-noise system needs the preconditioner built from that noise");
 }
 
 // tod = NULL selects the TOD the pointing was created with (one RHS, white
@@ -606,7 +654,7 @@ static void check_system(bm_pointing* p, bm_inv_noise* n, bm_precond* pc) {
 static void check_carried_tod(const bm_pointing* p, const bm_inv_noise* n, int32_t nrhs) {
     BM_REQUIRE(p->tod_s.get() != nullptr, "tod is NULL and the pointing was not created with a TOD");
     BM_REQUIRE(nrhs == 1, "the TOD carried by the pointing is one right-hand side (nrhs = %d)", nrhs);
-    BM_REQUIRE(n->kind == 0, "the TOD carried by the pointing is pixel-sorted; Toeplitz noise needs the "
+    BM_REQUIRE(diagonal_noise(n), "the TOD carried by the pointing is pixel-sorted; Toeplitz noise needs the "
                              "time-ordered TOD");
 }
 

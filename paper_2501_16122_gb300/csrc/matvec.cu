@@ -106,7 +106,7 @@ white_matvec_f32_kernel(const int32_t* __restrict__ item_pix, const int64_t* __r
                 float r = 0.f;
                 if (NC == 3) {
                     const float u2 = fmaf(u.x, u.x, u.y * u.y);
-                    r = u2 * rsqrtf(u2);
+                    r = u2 > 0.f ? u2 * rsqrtf(u2) : 0.f;  // sqrt(w); a zero weight gives 0
                 }
                 const float y = fmaf(u.x, xQ, fmaf(u.y, xU, r * xI));
                 if (NC == 3) aI = fmaf(y, r, aI);
@@ -168,7 +168,8 @@ white_matvec_f64_kernel(const int32_t* __restrict__ item_pix, const int64_t* __r
                         const uint32_t* __restrict__ perm, const float2* __restrict__ hi,
                         const float2* __restrict__ lo, const uint32_t* __restrict__ det_off, int ndet,
                         uint32_t ns, float inv_ns, const double* __restrict__ white,
-                        const double* __restrict__ x, double* __restrict__ partial) {
+                        const double* __restrict__ w64sort, const double* __restrict__ x,
+                        double* __restrict__ partial) {
     __shared__ uint32_t s_off[kMaxDetSmem + 1];
     const bool in_smem = ndet <= kMaxDetSmem;
     if (in_smem)
@@ -192,7 +193,9 @@ white_matvec_f64_kernel(const int32_t* __restrict__ item_pix, const int64_t* __r
         uint32_t dend = 0;
         double w = 0.0;
         auto add = [&](int64_t si, uint32_t t) {
-            if (t >= dend) {
+            if (w64sort) {  // a weight per sample
+                w = w64sort[si];
+            } else if (t >= dend) {
                 const int d = det_of(offp, ndet, ns, inv_ns, t);
                 dend = ns ? (uint32_t)(d + 1) * ns : offp[d + 1];
                 w = white[d];
@@ -266,12 +269,14 @@ gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __rest
             // detector is looked up only when t passes the current one's end
             uint32_t dend = 0;
             float2 w = make_float2(0.f, 0.f);
-            auto add = [&](uint32_t t, G gv, float2 h, float2 l) {
+            auto add = [&](int64_t si, uint32_t t, G gv, float2 h, float2 l) {
                 df32 val;
                 if (sizeof(G) == 4) val = {(float)gv, 0.f};
                 else val = df_from((double)gv);
                 if (weighted) {
-                    if (t >= dend) {
+                    if (dt.wsort) {  // a weight per sample
+                        w = dt.wsort[si];
+                    } else if (t >= dend) {
                         const int d = det_of(offp, ndet, dt.ns, dt.inv_ns, t);
                         dend = dt.ns ? (uint32_t)(d + 1) * dt.ns : offp[d + 1];
                         w = wp[d];
@@ -303,14 +308,14 @@ gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __rest
                     l[u] = (NC > 1 && lo) ? lo[b + i + 32 * u] : make_float2(0.f, 0.f);
                 }
 #pragma unroll
-                for (int u = 0; u < U; ++u) add(t[u], gv[u], h[u], l[u]);
+                for (int u = 0; u < U; ++u) add(b + i + 32 * u, t[u], gv[u], h[u], l[u]);
             }
             for (; i < len; i += 32) {
                 const int64_t si = b + i;
                 const uint32_t t = perm[si];
                 const float2 h = NC > 1 ? hi[si] : make_float2(0.f, 0.f);
                 const float2 l = (NC > 1 && lo) ? lo[si] : make_float2(0.f, 0.f);
-                add(t, gs ? (G)gs[si] : g[t], h, l);
+                add(si, t, gs ? (G)gs[si] : g[t], h, l);
             }
 #pragma unroll
             for (int c = 0; c < NC; ++c) acc[c] = df_warp_sum(acc[c]);
@@ -326,7 +331,9 @@ gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __rest
             auto add = [&](uint32_t t, G gv, int64_t si) {
                 double val = (double)gv;
                 if (weighted) {
-                    if (t >= dend) {
+                    if (dt.w64sort) {  // a weight per sample
+                        wd = dt.w64sort[si];
+                    } else if (t >= dend) {
                         const int d = det_of(offp, ndet, dt.ns, dt.inv_ns, t);
                         dend = dt.ns ? (uint32_t)(d + 1) * dt.ns : offp[d + 1];
                         wd = white[d];
@@ -950,16 +957,17 @@ static void pt_chunked(bm_pointing* p, bm_precond* pc, const float* z, double* q
 
 template <typename G>
 static void gather_reduce(bm_pointing* p, const ItemsView& it, const G* g, const bm_inv_noise* wn,
-                          const float2* lo, bool df, double* q, const float* gs = nullptr) {
+                          const float2* lo, bool df, double* q, const float* gs = nullptr,
+                          const bm_precond* wpc = nullptr) {
     bm_context* ctx = p->ctx;
     const int nc = p->ncomp;
     double* partial = workspace_as<double>(ctx, "partial", (size_t)std::max<int64_t>(it.n, 1) * nc);
     if (it.n > 0) {
         const int64_t wunits = (it.n + kWarps - 1) / kWarps;
         const bool weighted = wn != nullptr;
-        const DetTables dt = weighted ? DetTables{wn->det_off32.get(), wn->wdf.get(), wn->wsqrt.get(), wn->ns_uniform,
-                                                  wn->inv_ns}
-                                      : DetTables{nullptr, nullptr, nullptr, 0u, 0.f};
+        // (wpc: the preconditioner holding the sorted weights of a noise
+        // model with a weight per sample)
+        const DetTables dt = weighted ? det_tables(wn, wpc) : DetTables{nullptr, nullptr, nullptr, 0u, 0.f};
         const double* white = weighted ? wn->white.get() : nullptr;
         const int ndet = weighted ? wn->ndet : 0;
 #define BM_GR(NC, D)                                                                                           \
@@ -988,7 +996,7 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
     for (int64_t r = 0; r < nrhs; ++r) {
         const double* xr = x + r * nvec;
         double* qr = q + r * nvec;
-        if (n->kind == 0) {
+        if (diagonal_noise(n)) {
             double* partial = workspace_as<double>(ctx, "partial", (size_t)std::max<int64_t>(pc->nitems, 1) * nc);
             const int64_t wunits = (pc->nitems + kWarps - 1) / kWarps;
             if (prec == BM_PREC_MIXED) {
@@ -1011,7 +1019,7 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
     white_matvec_f64_kernel<NC><<<resident_grid(ctx, white_matvec_f64_kernel<NC>, kWarps * 32, wunits), kWarps * 32, 0, s>>>(                                              \
         pc->item_pix.get(), pc->item_beg.get(), pc->item_len.get(), pc->nitems, p->perm.get(),            \
         p->cs_hi_s.get(), p->cs_lo_s.get(), n->det_off32.get(), n->ndet, n->ns_uniform, n->inv_ns, n->white.get(), \
-        xr, partial)
+        n->kind == 2 ? pc->ws64.get() : nullptr, xr, partial)
                 if (nc == 3) BM_WF64(3); else if (nc == 2) BM_WF64(2); else BM_WF64(1);
 #undef BM_WF64
                 BM_LAUNCH_CHECK();
@@ -1066,18 +1074,18 @@ void rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dt
     ScopedTimer timer(ctx, "rhs");
     for (int64_t r = 0; r < nrhs; ++r) {
         double* br = b + r * nvec;
-        if (n->kind == 0) {
+        if (diagonal_noise(n)) {
             if (!tod && df && pc->b_tod.get()) {  // assembled with the preconditioner's blocks
                 BM_CUDA(cudaMemcpyAsync(br, pc->b_tod.get(), sizeof(double) * nvec, cudaMemcpyDeviceToDevice,
                                         ctx->stream));
             } else if (!tod) {  // the TOD sorted along with the pointing
-                gather_reduce<float>(p, kept_items(pc), nullptr, n, p->cs_lo_s.get(), df, br, p->tod_s.get());
+                gather_reduce<float>(p, kept_items(pc), nullptr, n, p->cs_lo_s.get(), df, br, p->tod_s.get(), pc);
             } else if (dt == BM_F32) {
                 const float* d = static_cast<const float*>(tod) + r * p->nsamples;
-                gather_reduce<float>(p, kept_items(pc), d, n, p->cs_lo_s.get(), df, br);
+                gather_reduce<float>(p, kept_items(pc), d, n, p->cs_lo_s.get(), df, br, nullptr, pc);
             } else {
                 const double* d = static_cast<const double*>(tod) + r * p->nsamples;
-                gather_reduce<double>(p, kept_items(pc), d, n, p->cs_lo_s.get(), df, br);
+                gather_reduce<double>(p, kept_items(pc), d, n, p->cs_lo_s.get(), df, br, nullptr, pc);
             }
         } else {
             double* z64 = workspace_as<double>(ctx, "z64", p->nsamples);
@@ -1111,9 +1119,20 @@ void pointing_apply_transpose(bm_pointing* p, const double* y, double* x) {
     BM_CUDA(cudaStreamSynchronize(p->ctx->stream));
 }
 
+// z_t = w_t y_t for a weight per sample.
+__global__ void sample_weight_apply_kernel(const double* __restrict__ w, const double* __restrict__ y, int64_t n,
+                                           double* __restrict__ z) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        z[t] = w[t] * y[t];
+}
+
 void inv_noise_apply(bm_inv_noise* n, const double* y, double* z) {
     bm_context* ctx = n->ctx;
-    if (n->kind == 0) {
+    if (n->kind == 2) {
+        sample_weight_apply_kernel<<<grid_for(ctx, (n->nsamples + 255) / 256, 16), 256, 0, ctx->stream>>>(
+            n->wsamp.get(), y, n->nsamples, z);
+        BM_LAUNCH_CHECK();
+    } else if (n->kind == 0) {
         // z_t = w_d y_t: reuse the Toeplitz machinery with a single lag.
         DevBuf<double> c(n->ndet);
         BM_CUDA(cudaMemcpyAsync(c.get(), n->white.get(), sizeof(double) * n->ndet, cudaMemcpyDeviceToDevice,

@@ -119,7 +119,10 @@ blocks_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ 
         float2 wv = make_float2(0.f, 0.f);
         float swv = 0.f;
         auto add = [&](int64_t si, uint32_t t, float2 h, float2 l, float dv) {
-            if (t >= dend) {
+            if (g.wsort) {  // a weight per sample
+                wv = g.wsort[si];
+                if (WCS && NC > 1) swv = g.ssort[si];
+            } else if (t >= dend) {
                 const int d = det_of(offp, ndet, g.ns, g.inv_ns, t);
                 dend = g.ns ? (uint32_t)(d + 1) * g.ns : offp[d + 1];
                 wv = wp[d];
@@ -212,6 +215,19 @@ __global__ void finalize_rhs_kernel(const int64_t* __restrict__ pitem, const dou
             for (int64_t k = k0; k < k1; ++k) s += rpartial[k * nc + c];
             b[p * nc + c] = s;
         }
+    }
+}
+
+// The weights of a noise model with a weight per sample, in pixel-sorted
+// order: as a double-float pair, its square root in FP32, and in FP64.
+__global__ void sort_weights_kernel(const uint32_t* __restrict__ perm, int64_t nvalid, const double* __restrict__ w,
+                                    float2* __restrict__ wdf, float* __restrict__ wsq, double* __restrict__ w64) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvalid; i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = w[perm[i]];
+        const float hi = (float)x;
+        wdf[i] = make_float2(hi, (float)(x - (double)hi));
+        wsq[i] = sqrtf((float)x);
+        w64[i] = x;
     }
 }
 
@@ -345,7 +361,15 @@ void build_precond(bm_precond* pc) {
         Items all;
         plan_items(ctx, p->off.get(), nullptr, npix, all);
         DevBuf<double> partial((all.n > 0 ? all.n : 1) * ns);
-        const bool white = n->kind == 0 && p->nvalid > 0;
+        const bool white = diagonal_noise(n) && p->nvalid > 0;
+        if (n->kind == 2 && p->nvalid > 0) {  // a weight per sample: gathered once into sorted order
+            pc->ws_df.alloc(p->nvalid);
+            pc->ws_sqrt.alloc(p->nvalid);
+            pc->ws64.alloc(p->nvalid);
+            sort_weights_kernel<<<grid_for(ctx, (p->nvalid + threads - 1) / threads, 16), threads, 0, s>>>(
+                p->perm.get(), p->nvalid, n->wsamp.get(), pc->ws_df.get(), pc->ws_sqrt.get(), pc->ws64.get());
+            BM_LAUNCH_CHECK();
+        }
         if (white) {
             if (nc == 1) pc->w1.alloc(p->nvalid);
             else pc->wcs.alloc(p->nvalid);
@@ -361,7 +385,7 @@ void build_precond(bm_precond* pc) {
         }
         if (all.n > 0) {
             const int64_t wunits = (all.n + kBlkWarps - 1) / kBlkWarps;
-            const DetTables g{n->det_off32.get(), n->wdf.get(), n->wsqrt.get(), n->ns_uniform, n->inv_ns};
+            const DetTables g = det_tables(n, pc);
 #define BM_BLOCKS3(NC, W, R, E)                                                                              \
     blocks_kernel<NC, W, R, E><<<resident_grid(ctx, blocks_kernel<NC, W, R, E>, kBlkWarps * 32, wunits), kBlkWarps * 32, 0, s>>>( \
         all.pix.get(), all.beg.get(), all.len.get(), all.n, p->perm.get(), p->cs_hi_s.get(), p->cs_lo_s.get(), g,     \

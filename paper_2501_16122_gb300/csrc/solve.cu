@@ -351,7 +351,7 @@ double exact_residual(Cg& cg, bm_pointing* p, bm_inv_noise* n, const double* b, 
                       bm_precision op) {
     bm_context* ctx = cg.pc->ctx;
     cudaStream_t s = ctx->stream;
-    if (n->kind == 0) {
+    if (diagonal_noise(n)) {
         block_residual_kernel<NC><<<RB, RT, 0, s>>>(cg.pc->B.get(), cg.pc->mask.get(), b, x, r, cg.npix, cg.part);
     } else {
         matvec(p, n, cg.pc, x, cg.q, op, 1);

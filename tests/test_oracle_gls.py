@@ -285,3 +285,54 @@ def test_precomputed_trig_rows_and_recovery():
     d = synth.tod(e, pt["pix"], pt["psi"], sky, white=False, trig=(c32, s32))
     x, info = gls.gls_map(S, d, tol=1e-14)
     assert gls.rel_err(x, sky, S.mask)["all"] < 1e-12
+
+
+# ------------------------------------------------ per-sample weights (Eq. 4)
+
+def test_sample_weights_equal_per_detector_weights():
+    # W = diag(w_t) with w_t = 1/sigma_d^2 of the sample's detector is the
+    # white-noise N^-1: same blocks, mask, operator, RHS and map.
+    e, pt, S = make_case(8, 4, 8000, 41, flag=0.02)
+    w = (1.0 / e.sigma ** 2)[np.repeat(np.arange(e.ndet), e.ns)]
+    S2 = gls.System(pt["pix"], pt["psi"], 3, e.npix, gls.SampleWeightNoise(w), min_hits=3, max_cond=1e3)
+    assert np.array_equal(S.B, S2.B) and np.array_equal(S.mask, S2.mask)
+    d = synth.tod(e, pt["pix"], pt["psi"], synth.sky_map(e.npix, 41))
+    np.testing.assert_array_equal(S.rhs(d), S2.rhs(d))
+    x1, _ = gls.gls_map(S, d)
+    x2, _ = gls.gls_map(S2, d)
+    np.testing.assert_array_equal(np.nan_to_num(x1), np.nan_to_num(x2))
+
+
+def test_zero_weights_are_gaps():
+    # A weight of 0 takes a sample out of every sum: the map equals the one
+    # with those samples flagged (on the pixels both keep; the hit counts,
+    # hence min_hits, still see the zero-weight samples).
+    e, pt, S = make_case(8, 4, 8000, 42)
+    rng = np.random.default_rng(42)
+    gap = rng.random(e.nsamples) < 0.15
+    w = (1.0 / e.sigma ** 2)[np.repeat(np.arange(e.ndet), e.ns)] * rng.uniform(0.5, 2.0, e.nsamples)
+    d = synth.tod(e, pt["pix"], pt["psi"], synth.sky_map(e.npix, 42))
+    Sg = gls.System(pt["pix"], pt["psi"], 3, e.npix, gls.SampleWeightNoise(np.where(gap, 0.0, w)), min_hits=3,
+                    max_cond=1e3)
+    pix_f = np.where(gap, -1, pt["pix"])
+    Sf = gls.System(pix_f, pt["psi"], 3, e.npix, gls.SampleWeightNoise(w), min_hits=3, max_cond=1e3)
+    np.testing.assert_allclose(Sg.B, Sf.B, rtol=0, atol=1e-9 * np.abs(Sf.B).max())
+    xg, _ = gls.gls_map(Sg, d, tol=1e-13)
+    xf, _ = gls.gls_map(Sf, d, tol=1e-13)
+    both = ~Sg.mask & ~Sf.mask
+    assert both.sum() > 100
+    np.testing.assert_allclose(xg[both], xf[both], rtol=1e-9, atol=1e-9 * np.abs(xf[both]).max())
+
+
+def test_sample_weights_dense_definition():
+    # Eq. 4 with a diagonal W, against the dense solve of P^T W P x = P^T W d.
+    e, pt, S = make_case(1, 2, 400, 43)
+    w = np.random.default_rng(43).uniform(0.0, 3.0, e.nsamples)
+    S2 = gls.System(pt["pix"], pt["psi"], 3, e.npix, gls.SampleWeightNoise(w), min_hits=3, max_cond=1e3)
+    d = synth.tod(e, pt["pix"], pt["psi"], synth.sky_map(e.npix, 43))
+    keep = np.repeat(~S2.mask, 3)
+    P = gls.dense_pointing(S2.pe, S2.v, e.npix)[:, keep]
+    W = np.diag(w)
+    ref = np.linalg.solve(P.T @ W @ P, P.T @ W @ S2.masked_tod(d))
+    x, _ = gls.gls_map(S2, d, tol=1e-14)
+    np.testing.assert_allclose(x.ravel()[keep], ref, rtol=1e-10, atol=1e-10 * np.abs(ref).max())
