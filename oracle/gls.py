@@ -140,6 +140,48 @@ class SampleWeightNoise:
 
 
 @dataclass
+class OffsetFilterNoise:
+    """White N^-1 (weight 1/sigma_d^2) with a baseline offset per interval
+    marginalised out (a filtering template): W = Nk - Nk F (F^T Nk F)^+ F^T Nk,
+    where F is the indicator matrix of the baseline intervals (each detector's
+    samples cut into intervals of ``baseline_len``, the last one possibly
+    shorter) and Nk is N^-1 restricted to the kept samples (``kept``, set by
+    the System: flagged samples and samples of masked pixels do not enter the
+    offset fit).  Written out: on a kept sample, (W y)_t = w_t (y_t - mean of
+    y over the kept samples of its interval); 0 elsewhere."""
+    inv_var: np.ndarray
+    det_offsets: np.ndarray
+    baseline_len: int
+    kept: np.ndarray = None  # [nsamples] bool
+
+    def with_kept(self, kept) -> "OffsetFilterNoise":
+        return OffsetFilterNoise(self.inv_var, self.det_offsets, self.baseline_len, np.asarray(kept, bool))
+
+    def white_level(self) -> np.ndarray:
+        return np.asarray(self.inv_var, np.float64)[sample_detector(self.det_offsets)]
+
+    def intervals(self):
+        off = np.asarray(self.det_offsets, np.int64)
+        for d in range(off.size - 1):
+            for a in range(off[d], off[d + 1], self.baseline_len):
+                yield a, min(a + self.baseline_len, off[d + 1])
+
+    def apply(self, y) -> np.ndarray:
+        y = np.asarray(y, np.float64)
+        k = np.ones(y.size, bool) if self.kept is None else self.kept
+        w = self.white_level()
+        z = np.zeros_like(y)
+        for a, e in self.intervals():
+            kk = k[a:e]
+            n = int(kk.sum())
+            if n == 0:
+                continue
+            m = y[a:e][kk].sum() / n
+            z[a:e] = np.where(kk, w[a:e] * (y[a:e] - m), 0.0)
+        return z
+
+
+@dataclass
 class ToeplitzNoise:
     """Banded symmetric Toeplitz N^-1 per chunk of each detector's samples:
     z_t = c_0 y_t + sum_{k=1}^{L-1} c_k (y_{t-k} + y_{t+k}), with y taken as
@@ -243,6 +285,8 @@ class System:
         self.mask = pixel_mask(self.hits, self.B, min_hits, max_cond)
         self.M = block_inverse(self.B, self.mask)
         self.pe = effective_pixels(self.pix, self.mask)
+        if hasattr(noise, "with_kept"):  # a weighting that depends on which samples enter the system
+            self.noise = noise.with_kept(self.pe >= 0)
 
     def masked_tod(self, d) -> np.ndarray:
         """d with the samples of flagged or masked pixels set to zero."""

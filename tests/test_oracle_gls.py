@@ -336,3 +336,54 @@ def test_sample_weights_dense_definition():
     ref = np.linalg.solve(P.T @ W @ P, P.T @ W @ S2.masked_tod(d))
     x, _ = gls.gls_map(S2, d, tol=1e-14)
     np.testing.assert_allclose(x.ravel()[keep], ref, rtol=1e-10, atol=1e-10 * np.abs(ref).max())
+
+
+# ------------------------------------------- baseline-offset template (Eq. 4)
+
+def _offset_case(seed, baseline_len, flag=0.02):
+    e = synth.make_experiment(8, 4, 6000, seed)
+    pt = synth.pointing(e, flag_frac=flag)
+    N = gls.OffsetFilterNoise(1.0 / e.sigma ** 2, e.det_offsets, baseline_len)
+    S = gls.System(pt["pix"], pt["psi"], 3, e.npix, N, min_hits=3, max_cond=1e3)
+    return e, pt, S
+
+
+def test_offset_filter_is_the_marginalised_projector():
+    # W = Nk - Nk F (F^T Nk F)^+ F^T Nk written out densely on a small case.
+    e, pt, S = _offset_case(51, 700)
+    n = S.noise
+    nt = e.nsamples
+    F = np.zeros((nt, sum(1 for _ in n.intervals())))
+    for j, (a, b) in enumerate(n.intervals()):
+        F[a:b, j] = 1.0
+    Nk = np.diag(n.white_level() * n.kept)
+    W = Nk - Nk @ F @ np.linalg.pinv(F.T @ Nk @ F) @ F.T @ Nk
+    rng = np.random.default_rng(51)
+    for _ in range(3):
+        y = rng.normal(size=nt)
+        np.testing.assert_allclose(n.apply(y), W @ y, rtol=1e-10, atol=1e-10 * np.abs(W @ y).max())
+    # interval-constant vectors are annihilated; W is symmetric
+    a = rng.normal(size=F.shape[1])
+    assert np.abs(n.apply(F @ a)).max() < 1e-12 * np.abs(a).max() * n.white_level().max()
+    x, y = rng.normal(size=nt), rng.normal(size=nt)
+    assert abs(x @ n.apply(y) - y @ n.apply(x)) < 1e-10 * abs(x @ n.apply(y))
+
+
+def test_offset_filter_removes_offsets_from_the_map():
+    # d = P s + F a: the GLS map with the offsets marginalised recovers s on
+    # the kept pixels, Q and U exactly and I up to its monopole (a constant I
+    # map is an offset on every interval, hence in the null space of A).
+    e, pt, S = _offset_case(52, 500)
+    sky = synth.sky_map(e.npix, 52)
+    d = synth.tod(e, pt["pix"], pt["psi"], sky, white=False)
+    rng = np.random.default_rng(52)
+    for a, b in S.noise.intervals():
+        d[a:b] += rng.normal(0.0, 300.0)
+    x, info = gls.gls_map(S, d, tol=1e-12, maxiter=3000)
+    assert info.converged, info
+    keep = ~S.mask
+    assert keep.sum() > 100
+    for k in (1, 2):
+        np.testing.assert_allclose(x[keep, k], sky[keep, k], rtol=0, atol=1e-8 * np.abs(sky[keep, k]).max())
+    di = (x[keep, 0] - x[keep, 0].mean()) - (sky[keep, 0] - sky[keep, 0].mean())
+    assert np.abs(di).max() < 1e-8 * np.abs(sky[keep, 0]).max()
