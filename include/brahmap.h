@@ -197,6 +197,25 @@ bm_status bm_inv_noise_create_toeplitz(bm_context* ctx, int32_t ndet, const int6
  * weight. */
 bm_status bm_inv_noise_create_sample_weights(bm_context* ctx, int64_t nsamples, const double* weights,
                                              bm_inv_noise** out);
+/* White N^-1 with one baseline offset per interval marginalised out: the
+ * general weighting of Eq. 4 with the offsets as a filtering template
+ * (Sec. IV names filtering templates among the needs of real data),
+ *   W = Nk - Nk F (F^T Nk F)^-1 F^T Nk,
+ * F the indicator matrix of the intervals (each detector's samples cut into
+ * intervals of baseline_len, the last one possibly shorter), Nk the white N^-1
+ * (inv_var host FP64 [ndet], as for bm_inv_noise_create_diag) restricted to
+ * the kept samples of the system (not flagged, pixel not masked).  On a kept
+ * sample of interval I, (W y)_t = w_d (y_t - mean of y over I's kept samples).
+ * A constant I map is an offset on every interval, so the I monopole is in
+ * the null space of A: the solve converges to one solution of a consistent
+ * system, defined up to that monopole.  The preconditioner of Eq. 7 uses
+ * diag(N)^-1 = w_d; it must be built from this noise handle (it also counts
+ * each interval's kept samples).  bm_inv_noise_apply takes every sample as
+ * kept.  Errors: BM_ERR_INVALID for baseline_len < 1 or the det_offsets /
+ * inv_var rules of bm_inv_noise_create_diag; at solve time for a
+ * preconditioner built from another noise handle. */
+bm_status bm_inv_noise_create_offset_filter(bm_context* ctx, int32_t ndet, const int64_t* det_offsets,
+                                            const double* inv_var, int64_t baseline_len, bm_inv_noise** out);
 void bm_inv_noise_destroy(bm_inv_noise* n);
 /* z = N^-1 y in FP64: y, z device FP64 [nsamples]. */
 bm_status bm_inv_noise_apply(bm_inv_noise* n, const double* y, double* z);

@@ -104,6 +104,7 @@ _SIGS = {
     "bm_inv_noise_create_diag": ([_P, _i32, _P, _P, _PP], ctypes.c_int),
     "bm_inv_noise_create_toeplitz": ([_P, _i32, _P, _i64, _i32, _P, _P, _PP], ctypes.c_int),
     "bm_inv_noise_create_sample_weights": ([_P, _i64, _P, _PP], ctypes.c_int),
+    "bm_inv_noise_create_offset_filter": ([_P, _i32, _P, _P, _i64, _PP], ctypes.c_int),
     "bm_inv_noise_destroy": ([_P], None),
     "bm_inv_noise_apply": ([_P, _P, _P], ctypes.c_int),
     "bm_blockdiag_precond_create": ([_P, _P, _i32, _f64, _PP], ctypes.c_int),
@@ -317,6 +318,16 @@ def bm_inv_noise_create_sample_weights(ctx, weights):
     out = ctypes.c_void_p()
     _check(lib.bm_inv_noise_create_sample_weights(ctx, weights.numel(), _in(weights, torch.float64, "weights"),
                                                   ctypes.byref(out)), "bm_inv_noise_create_sample_weights")
+    return out
+
+
+def bm_inv_noise_create_offset_filter(ctx, det_offsets, inv_var, baseline_len: int):
+    """White N^-1 with a baseline offset per interval of baseline_len samples marginalised out."""
+    off, offp = _host(det_offsets, np.int64)
+    iv, ivp = _host(inv_var, np.float64)
+    out = ctypes.c_void_p()
+    _check(lib.bm_inv_noise_create_offset_filter(ctx, off.size - 1, offp, ivp, int(baseline_len),
+                                                 ctypes.byref(out)), "bm_inv_noise_create_offset_filter")
     return out
 
 

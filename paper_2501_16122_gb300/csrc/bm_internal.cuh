@@ -143,7 +143,8 @@ struct bm_pointing {
 struct bm_inv_noise {
     bm_context* ctx = nullptr;
     int kind = 0;  // 0 = diagonal white (a weight per detector), 1 = banded Toeplitz,
-                   // 2 = diagonal with a weight per sample (wsamp)
+                   // 2 = diagonal with a weight per sample (wsamp), 3 = white with a
+                   // baseline offset per interval marginalised out
     int ndet = 0;
     int64_t nsamples = 0;
     std::vector<int64_t> h_det_off;
@@ -154,6 +155,12 @@ struct bm_inv_noise {
     bm::DevBuf<uint32_t> det_off32;  // [ndet + 1] (nsamples < 2^32)
     bm::DevBuf<float2> wdf;          // [ndet] white level as double-float (hi, lo)
     bm::DevBuf<float> wsqrt;         // [ndet] sqrt of the white level, FP32
+    // Offset filter: each detector's samples cut into intervals of
+    // baseline_len (the last one may be shorter); int_start[d] = the index of
+    // detector d's first interval, int_start[ndet] = nint.
+    int64_t baseline_len = 0;
+    int64_t nint = 0;
+    bm::DevBuf<int64_t> int_start;  // [ndet + 1]
     // Toeplitz
     int64_t chunk_len = 0;
     int nlags = 0;
@@ -210,6 +217,8 @@ struct bm_precond {
     // not built yet, -1 not used)
     int pt_nch = 0;
     bm::DevBuf<int32_t> pt_sub;    // [pt_nch + 1][npix]
+    // Offset filter: 1 / (the kept samples of each interval), 0 where none.
+    bm::DevBuf<double> ofs_inv;    // [nint]
 };
 
 namespace bm {
@@ -282,6 +291,8 @@ void pointing_apply_transpose(bm_pointing* p, const double* y, double* x);
 void inv_noise_apply(bm_inv_noise* n, const double* y, double* z);
 // Band spectra and twiddle tables for the FFT form of a Toeplitz noise model.
 void prepare_toeplitz_fft(bm_inv_noise* n);
+// pc->ofs_inv of an offset-filter noise from the pointing and the pixel mask.
+void build_offset_counts(bm_precond* pc);
 void ang2pix_ring(bm_context* ctx, int64_t nside, int64_t n, const double* z, const double* phi,
                   int32_t* pix);
 bm_status pcg_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod,
@@ -356,7 +367,7 @@ inline DetTables det_tables(const bm_inv_noise* n, const bm_precond* pc) {
 }
 // N^-1 diagonal (a weight per detector or per sample): A = P^T N^-1 P is block
 // diagonal and the white-noise paths apply.
-inline bool diagonal_noise(const bm_inv_noise* n) { return n->kind != 1; }
+inline bool diagonal_noise(const bm_inv_noise* n) { return n->kind == 0 || n->kind == 2; }
 
 __device__ __forceinline__ int find_det32(const uint32_t* off, int ndet, uint32_t t) {
     int lo = 0, hi = ndet - 1;

@@ -1,6 +1,7 @@
 // C-ABI entry points (include/brahmap.h): argument validation, handle
 // lifetime, error translation.  Every entry point catches the library's
 // internal bm::Error and returns its status; no exception crosses the ABI.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -507,6 +508,40 @@ bm_status bm_inv_noise_create_sample_weights(bm_context* ctx, int64_t nsamples, 
     });
 }
 
+bm_status bm_inv_noise_create_offset_filter(bm_context* ctx, int32_t ndet, const int64_t* det_offsets,
+                                            const double* inv_var, int64_t baseline_len, bm_inv_noise** out) {
+    return guarded([&] {
+        BM_REQUIRE(ctx && out, "ctx/out is NULL");
+        *out = nullptr;
+        check_det_offsets(ndet, det_offsets);
+        BM_REQUIRE(inv_var != nullptr, "inv_var is NULL");
+        BM_REQUIRE(baseline_len >= 1, "baseline_len < 1");
+        for (int d = 0; d < ndet; ++d)
+            BM_REQUIRE(inv_var[d] > 0 && inv_var[d] < 1e300, "inv_var[%d] not positive finite", d);
+        // no detector is longer than nsamples: a longer baseline is the same filter
+        const int64_t bl = std::min<int64_t>(baseline_len, det_offsets[ndet]);
+        std::vector<int64_t> start(ndet + 1, 0);
+        for (int d = 0; d < ndet; ++d) {
+            const int64_t len = det_offsets[d + 1] - det_offsets[d];
+            start[d + 1] = start[d] + len / bl + (len % bl != 0);
+        }
+        use_device(ctx);
+        bm_inv_noise* n = new_noise(ctx, ndet, det_offsets, inv_var);
+        try {
+            n->kind = 3;
+            n->baseline_len = bl;
+            n->nint = start[ndet];
+            n->int_start.alloc(ndet + 1);
+            upload(ctx, n->int_start.get(), start.data(), sizeof(int64_t) * (ndet + 1));
+        } catch (...) {
+            delete n;
+            throw;
+        }
+        *out = n;
+        return BM_OK;
+    });
+}
+
 bm_status bm_inv_noise_create_toeplitz(bm_context* ctx, int32_t ndet, const int64_t* det_offsets,
                                        int64_t chunk_len, int32_t nlags, const double* coeffs,
                                        const double* white_inv_var, bm_inv_noise** out) {
@@ -647,6 +682,9 @@ static void check_system(bm_pointing* p, bm_inv_noise* n, bm_precond* pc) {
     BM_REQUIRE(n->nsamples == p->nsamples, "noise and pointing cover different sample counts");
     if (diagonal_noise(n))
         BM_REQUIRE(pc->n == n, "a diagonal-noise system needs the preconditioner built from that noise");
+    if (n->kind == 3)
+        BM_REQUIRE(pc->n == n, "an offset-filter system needs the preconditioner built from that noise "
+                               "(its kept samples per interval)");
 }
 
 // tod = NULL selects the TOD the pointing was created with (one RHS, white
@@ -654,8 +692,8 @@ static void check_system(bm_pointing* p, bm_inv_noise* n, bm_precond* pc) {
 static void check_carried_tod(const bm_pointing* p, const bm_inv_noise* n, int32_t nrhs) {
     BM_REQUIRE(p->tod_s.get() != nullptr, "tod is NULL and the pointing was not created with a TOD");
     BM_REQUIRE(nrhs == 1, "the TOD carried by the pointing is one right-hand side (nrhs = %d)", nrhs);
-    BM_REQUIRE(diagonal_noise(n), "the TOD carried by the pointing is pixel-sorted; Toeplitz noise needs the "
-                             "time-ordered TOD");
+    BM_REQUIRE(diagonal_noise(n), "the TOD carried by the pointing is pixel-sorted; a time-ordered N^-1 "
+                                  "(Toeplitz, offset filter) needs the time-ordered TOD");
 }
 
 bm_status bm_rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod,

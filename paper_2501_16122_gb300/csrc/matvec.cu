@@ -875,6 +875,127 @@ static void apply_toeplitz_f64(bm_inv_noise* n, const Src& src, double* z, bool 
         run_toeplitz<double, 4>(n, src, n->coeffs64.get(), z);
 }
 
+// ----------------------------------------------------------- offset filter
+// W y for white noise with one baseline offset per interval marginalised out
+// (Eq. 4 with the offsets as a template, W = Nk - Nk F (F^T Nk F)^-1 F^T Nk,
+// F the interval indicators): on the kept samples of interval I,
+// z_t = w_d (y_t - m_I), m_I the mean of y over those samples.  y is zero on
+// every sample that is not kept (flagged, or in a masked pixel), so m_I is the
+// interval's plain sum times 1 / (its kept samples).  The transpose reads z
+// on kept samples only; elsewhere z is written by the same formula.
+struct OffsetGeom {
+    const int64_t* det_off;    // [ndet + 1]
+    const int64_t* int_start;  // [ndet + 1] index of each detector's first interval
+    int ndet;
+    int64_t baseline_len;
+    int64_t nint;
+};
+
+__device__ __forceinline__ void offset_interval(const OffsetGeom& g, int64_t j, int& d, int64_t& a, int64_t& e) {
+    d = find_tile_det(g.int_start, g.ndet, j);
+    a = g.det_off[d] + (j - g.int_start[d]) * g.baseline_len;
+    e = min(a + g.baseline_len, g.det_off[d + 1]);
+}
+
+// One warp per interval.  The sum: FP32 (or FP64) groups of up to 8 per lane
+// folded into FP64, then a butterfly over the warp, which leaves the same
+// value in every lane (IEEE addition commutes); a fixed order, so the result
+// is deterministic.  The second pass reads the interval again (from L2 for
+// intervals of a few thousand samples) and writes z.
+template <typename T, class Src>
+__global__ void __launch_bounds__(256)
+offset_filter_kernel(Src src, OffsetGeom g, const double* __restrict__ white, const double* __restrict__ inv_cnt,
+                     T* __restrict__ z) {
+    constexpr int U = 8;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < g.nint; j += nwarps) {
+        int d;
+        int64_t a, e;
+        offset_interval(g, j, d, a, e);
+        double s = 0.0;
+        for (int64_t t0 = a + lane; t0 < e; t0 += 32 * U) {
+            T v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = t0 + 32 * u < e ? src(t0 + 32 * u) : T(0);
+            T ps = v[0];
+#pragma unroll
+            for (int u = 1; u < U; ++u) ps += v[u];
+            s += (double)ps;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const double m = s * (inv_cnt ? inv_cnt[j] : 1.0 / (double)(e - a));
+        const T mt = (T)m, w = (T)white[d];
+        for (int64_t t0 = a + lane; t0 < e; t0 += 32 * U) {
+            T v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = t0 + 32 * u < e ? src(t0 + 32 * u) : T(0);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (t0 + 32 * u < e) z[t0 + 32 * u] = w * (v[u] - mt);
+        }
+    }
+}
+
+// 1 / (the kept samples of each interval), 0 where there are none; a sample
+// is kept when it is not flagged and its pixel is not masked.
+__global__ void offset_counts_kernel(const int32_t* __restrict__ pix, const uint8_t* __restrict__ mask, OffsetGeom g,
+                                     double* __restrict__ inv) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < g.nint; j += nwarps) {
+        int d;
+        int64_t a, e;
+        offset_interval(g, j, d, a, e);
+        unsigned c = 0;
+        for (int64_t t = a + lane; t < e; t += 32) {
+            const int32_t p = pix[t];
+            c += p >= 0 && !mask[p];
+        }
+        c = __reduce_add_sync(0xffffffffu, c);
+        if (lane == 0) inv[j] = c ? 1.0 / (double)c : 0.0;
+    }
+}
+
+static OffsetGeom offset_geom(const bm_inv_noise* n) {
+    return {n->det_off.get(), n->int_start.get(), n->ndet, n->baseline_len, n->nint};
+}
+
+void build_offset_counts(bm_precond* pc) {
+    bm_context* ctx = pc->ctx;
+    const bm_inv_noise* n = pc->n;
+    pc->ofs_inv.alloc(std::max<int64_t>(n->nint, 1));
+    if (n->nint == 0) return;
+    offset_counts_kernel<<<resident_grid(ctx, offset_counts_kernel, 256, (n->nint + 7) / 8), 256, 0, ctx->stream>>>(
+        pc->p->pix.get(), pc->mask.get(), offset_geom(n), pc->ofs_inv.get());
+    BM_LAUNCH_CHECK();
+}
+
+// inv_cnt = NULL: every sample is kept.
+template <typename T, class Src>
+static void run_offset_filter(bm_inv_noise* n, const Src& src, const double* inv_cnt, T* z) {
+    bm_context* ctx = n->ctx;
+    if (n->nint == 0) return;
+    auto kern = offset_filter_kernel<T, Src>;
+    kern<<<resident_grid(ctx, kern, 256, (n->nint + 7) / 8), 256, 0, ctx->stream>>>(src, offset_geom(n),
+                                                                                    n->white.get(), inv_cnt, z);
+    BM_LAUNCH_CHECK();
+}
+
+// The time-ordered N^-1 of a non-diagonal model (a Toeplitz band or the
+// offset filter) on the kept samples of the system `pc` belongs to.
+template <class Src>
+static void apply_filter_f32(bm_inv_noise* n, const bm_precond* pc, const Src& src, float* z) {
+    if (n->kind == 3) run_offset_filter<float>(n, src, pc->ofs_inv.get(), z);
+    else apply_toeplitz_f32(n, src, z);
+}
+template <class Src>
+static void apply_filter_f64(bm_inv_noise* n, const bm_precond* pc, const Src& src, double* z, bool df) {
+    if (n->kind == 3) run_offset_filter<double>(n, src, pc->ofs_inv.get(), z);
+    else apply_toeplitz_f64(n, src, z, df);
+}
+
 static void finalize(bm_context* ctx, const int64_t* pitem, const double* partial, int64_t npix, int nc,
                      double* q) {
     const int threads = 256;
@@ -1038,7 +1159,7 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
                     pointing_apply_f32_kernel<<<grid_for(ctx, (p->nsamples + threads - 1) / threads, 16), threads, 0, s>>>(
                         p->pix.get(), p->cs_hi_t.get(), p->nsamples, x4, y32);
                     BM_LAUNCH_CHECK();
-                    apply_toeplitz_f32(n, SrcPlainF32{y32}, z32);
+                    apply_filter_f32(n, pc, SrcPlainF32{y32}, z32);
                 }
                 // scatter with the same FP32 trig the gather used (symmetric operator)
                 ScopedTimer timer(ctx, "toeplitz_pt");
@@ -1057,7 +1178,7 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
                     pointing_apply_kernel<<<grid_for(ctx, (p->nsamples + threads - 1) / threads, 16), threads, 0, s>>>(
                         p->pix.get(), p->cs_hi_t.get(), p->cs_lo_t.get(), p->nsamples, nc, xm, y64);
                     BM_LAUNCH_CHECK();
-                    apply_toeplitz_f64(n, SrcPlain{y64}, z64, refine);
+                    apply_filter_f64(n, pc, SrcPlain{y64}, z64, refine);
                 }
                 ScopedTimer timer(ctx, "toeplitz_pt");
                 gather_reduce<double>(p, kept_items(pc), z64, nullptr, p->cs_lo_s.get(), refine, qr);
@@ -1092,11 +1213,11 @@ void rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dt
             if (dt == BM_F32) {
                 SrcMaskedTod<float> src{p->pix.get(), pc->mask.get(),
                                         static_cast<const float*>(tod) + r * p->nsamples};
-                apply_toeplitz_f64(n, src, z64, df);
+                apply_filter_f64(n, pc, src, z64, df);
             } else {
                 SrcMaskedTod<double> src{p->pix.get(), pc->mask.get(),
                                          static_cast<const double*>(tod) + r * p->nsamples};
-                apply_toeplitz_f64(n, src, z64, df);
+                apply_filter_f64(n, pc, src, z64, df);
             }
             gather_reduce<double>(p, kept_items(pc), z64, nullptr, p->cs_lo_s.get(), df, br);
         }
@@ -1148,6 +1269,8 @@ void inv_noise_apply(bm_inv_noise* n, const double* y, double* z) {
         tmp.chunk_len = n->nsamples;
         tmp.nlags = 1;
         run_toeplitz<double, 4>(&tmp, SrcPlain{y}, c.get(), z);
+    } else if (n->kind == 3) {
+        run_offset_filter<double>(n, SrcPlain{y}, nullptr, z);
     } else {
         apply_toeplitz_f64(n, SrcPlain{y}, z);
     }

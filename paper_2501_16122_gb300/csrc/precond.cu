@@ -433,6 +433,7 @@ void build_precond(bm_precond* pc) {
     pc->item_beg = std::move(kept.beg);
     pc->item_len = std::move(kept.len);
     pc->pitem = std::move(kept.pitem);
+    if (n->kind == 3) build_offset_counts(pc);
 
     BM_CUDA(cudaStreamSynchronize(s));
 }
