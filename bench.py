@@ -56,10 +56,11 @@ def parse():
     ap.add_argument("--matvec-reps", type=int, default=20)
     ap.add_argument("--profile", action="store_true", help="short run for ncu: no e2e, cpu, clocks")
     ap.add_argument("--workload", default="config1",
-                    choices=["config0", "config1", "config2", "config3", "config4"],
+                    choices=["config0", "config1", "config2", "config3", "config4", "offsets"],
                     help="config1 (default): nside 256 white-noise solve; config0: small FP64 solve; "
                          "config2: 512-lag Toeplitz noise; config3: 64 right-hand sides batched; "
-                         "config4: Poisson request stream through the server")
+                         "config4: Poisson request stream through the server; offsets: config2's 1/f TOD "
+                         "with a baseline offset per 60 s marginalised out instead of the Toeplitz N^-1")
     ap.add_argument("--horizon", type=float, default=20.0, help="config4: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=20.0, help="config4: mean arrivals per second")
     ap.add_argument("--nrhs", type=int, default=64, help="config3: right-hand sides")

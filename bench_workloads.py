@@ -143,11 +143,15 @@ def run_config0(args):
 
 
 # ------------------------------------------------------------------ config 2
-def run_config2(args):
+def run_config2(args, noise="toeplitz"):
+    """The correlated-noise solve: a 512-lag Toeplitz N^-1 (noise = "toeplitz"),
+    or white N^-1 with a baseline offset per 60 s interval marginalised out
+    (noise = "offsets"), on the same 1/f TOD."""
     import torch
     L = _L()
     nside, ndet, ns = args.nside, args.ndet, args.ns
     chunk, nlags, fknee, alpha = 2 ** 20, 512, 0.1, 1.0
+    baseline_len = 1200  # 60 s at 20 Hz
     chunk = min(chunk, ns)
     tol = 1e-7
     t_gen = time.perf_counter()
@@ -167,7 +171,10 @@ def run_config2(args):
 
     def make():
         p = L.bm_pointing_create_trig(ctx, e.npix, d_pix, d_c, d_s, 3)
-        n = L.bm_inv_noise_create_toeplitz(ctx, e.det_offsets, chunk, coeffs, inv_var)
+        if noise == "toeplitz":
+            n = L.bm_inv_noise_create_toeplitz(ctx, e.det_offsets, chunk, coeffs, inv_var)
+        else:
+            n = L.bm_inv_noise_create_offset_filter(ctx, e.det_offsets, inv_var, baseline_len)
         pc = L.bm_blockdiag_precond_create(p, n, 3, 1e3)
         return p, n, pc
 
@@ -196,7 +203,10 @@ def run_config2(args):
     ms = (time.perf_counter() - t0) * 1000 / args.steps
     clocks = sampler.stop()
     fam = {}
-    for name in ("ingest", "blocks", "rhs", "toeplitz_f32", "toeplitz_refine", "toeplitz_f64", "toeplitz_pt", "toeplitz_pt_bounds"):
+    for name in ("ingest", "blocks", "rhs", "toeplitz_f32", "toeplitz_refine", "toeplitz_f64", "toeplitz_pt",
+                 "toeplitz_pt_bounds", "offset_filter_f32", "offset_filter_f64", "offset_means_f32",
+                 "offset_matvec_f32", "offset_means_df", "offset_pt_df", "ingest_validate", "ingest_hist",
+                 "ingest_scatter"):
         tot, cnt = L.bm_context_kernel_time(ctx, name)
         if cnt:
             fam[name] = {"ms_per_launch": tot / cnt, "launches_per_step": cnt / args.steps}
@@ -215,6 +225,29 @@ def run_config2(args):
     L.bm_context_destroy(ctx)
     st, info = infos[-1]
     sm = clocks["sm_mhz"] if clocks else 2070.0
+    if noise == "offsets":
+        # time-ordered steps of the inner operator (toeplitz_f32 = the FP32
+        # P x plus the filter; toeplitz_pt = its transpose)
+        of = fam.get("offset_filter_f32", {})
+        ms_l = of.get("ms_per_launch")
+        gbs = e.nsamples * 8.0 / (ms_l * 1e-3) / 1e9 if ms_l else None
+        line = {
+            "workload": "offsets", "metric": METRIC, "value": e.nsamples / (ms * 1e-3), "unit": "TOD samples/s",
+            "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+            "config": {"workload": f"GLS map-making, nside {nside}, {ndet} det x {ns} samples, 1/f noise "
+                                   f"(fknee {fknee} Hz, alpha {alpha}), white N^-1 with one offset per "
+                                   f"{baseline_len}-sample baseline marginalised out, mixed precision PCG to {tol:g}",
+                       "nsamples": e.nsamples},
+            "solve": {"status": st, **info},
+            "step_breakdown": fam,
+            "fp64_matvec_ms": fp64_mv_ms,
+            "roofline": {"bound": "hbm", "kernel": "offset_filter_kernel<float> (read y, write z: 8 B a sample)",
+                         "achieved": gbs, "peak": hbm_peak(), "unit": "GB/s",
+                         "frac": gbs / hbm_peak() if gbs else None, "traffic": None},
+            "clocks": clocks, "input_generation_s": t_gen,
+        }
+        print(json.dumps(line), flush=True)
+        return
     # The band is applied by FFT overlap-save: per tile of H = N - 2(L-1)
     # outputs one real N-point transform pair (5 N log2 N flops) and the
     # spectrum product (2N); its inputs are the window's pix + trig
@@ -541,5 +574,8 @@ def run_config4(args):
 
 def run(args, rank, world, local_rank):
     if rank != 0:
+        return
+    if args.workload == "offsets":
+        run_config2(args, noise="offsets")
         return
     {"config0": run_config0, "config2": run_config2, "config3": run_config3, "config4": run_config4}[args.workload](args)

@@ -91,7 +91,10 @@ const char* bm_version(void);
 
 /* Bind the library to CUDA device `device` and stream `cuda_stream`
  * (a cudaStream_t; NULL = the legacy default stream).  The stream is
- * borrowed: the caller keeps it alive until bm_context_destroy. */
+ * borrowed: the caller keeps it alive until bm_context_destroy.  The context
+ * keeps its scratch buffers (the pixel sort's ping-pong buffers, up to
+ * 20-28 bytes a sample, and the solver's vectors) in a device memory pool of
+ * its own for reuse by later calls; bm_context_destroy releases them. */
 bm_status bm_context_create(int device, void* cuda_stream, bm_context** out);
 void bm_context_destroy(bm_context* ctx);
 

@@ -88,6 +88,25 @@ struct DevBuf {
         ptr = static_cast<T*>(p);
         n = count;
     }
+    // The same from a given memory pool (NULL: the device's default pool).
+    void alloc_from(cudaMemPool_t pool, size_t count) {
+        if (!pool) {
+            alloc(count);
+            return;
+        }
+        release();
+        if (count == 0) return;
+        void* p = nullptr;
+        stream = tl_stream;
+        cudaError_t e = cudaMallocFromPoolAsync(&p, count * sizeof(T), pool, stream);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            set_error("device allocation of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+            throw Error{BM_ERR_OOM};
+        }
+        ptr = static_cast<T*>(p);
+        n = count;
+    }
     void release() {
         if (ptr) cudaFreeAsync(ptr, stream);
         ptr = nullptr;
@@ -117,7 +136,12 @@ struct bm_context {
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> event_pool;
     double* h_pinned = nullptr;  // small pinned host buffer for scalar reads
-    std::map<std::string, bm::DevBuf<char>> ws;  // named grow-only scratch buffers
+    // Named grow-only scratch buffers, from a pool of their own: long-lived
+    // workspaces taken between the allocations of short-lived handles would
+    // split the default pool's blocks and make later large allocations map
+    // new memory.
+    cudaMemPool_t ws_pool = nullptr;
+    std::map<std::string, bm::DevBuf<char>> ws;
     // Library-owned stream for CUDA-graph capture and replay (the caller's
     // stream may be the legacy default stream, which cannot be captured),
     // ordered against `stream` with side_ev.
@@ -217,8 +241,10 @@ struct bm_precond {
     // not built yet, -1 not used)
     int pt_nch = 0;
     bm::DevBuf<int32_t> pt_sub;    // [pt_nch + 1][npix]
-    // Offset filter: 1 / (the kept samples of each interval), 0 where none.
+    // Offset filter: 1 / (the kept samples of each interval), 0 where none;
+    // the interval of every sample in pixel-sorted order.
     bm::DevBuf<double> ofs_inv;    // [nint]
+    bm::DevBuf<uint32_t> ofs_isort;  // [nvalid]
 };
 
 namespace bm {

@@ -114,7 +114,7 @@ int blocks_per_sm(const void* kernel, int threads, size_t smem) {
 
 void* workspace(bm_context* ctx, const char* name, size_t bytes) {
     auto& b = ctx->ws[name];
-    if (b.n < bytes) b.alloc(bytes + bytes / 8);  // stream-ordered: old users finish first
+    if (b.n < bytes) b.alloc_from(ctx->ws_pool, bytes + bytes / 8);  // stream-ordered: old users finish first
     return b.get();
 }
 
@@ -192,6 +192,15 @@ bm_status bm_context_create(int device, void* cuda_stream, bm_context** out) {
             uint64_t thr = UINT64_MAX;
             e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
         }
+        if (e == cudaSuccess) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = device;
+            e = cudaMemPoolCreate(&ctx->ws_pool, &props);
+            uint64_t thr = UINT64_MAX;
+            if (e == cudaSuccess) e = cudaMemPoolSetAttribute(ctx->ws_pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
         if (e != cudaSuccess) {
             set_error("context setup failed: %s", cudaGetErrorString(e));
             bm_context_destroy(ctx);
@@ -216,8 +225,10 @@ void bm_context_destroy(bm_context* ctx) {
     }
     if (ctx->side_ev) cudaEventDestroy(ctx->side_ev);
     const int dev = ctx->device;
+    cudaMemPool_t ws_pool = ctx->ws_pool;
     delete ctx;  // releases the workspaces (stream-ordered)
     cudaStreamSynchronize(tl_stream);
+    if (ws_pool) cudaMemPoolDestroy(ws_pool);
     // Hand the pool's unused memory back to the driver.
     cudaMemPool_t pool = nullptr;
     if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess && pool) cudaMemPoolTrimTo(pool, 0);

@@ -678,29 +678,31 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
     else p->tod_s.release();
 
     // Ping-pong record buffers of the intermediate passes (and the lo halves
-    // of the trig pairs when the angles were given).
+    // of the trig pairs when the angles were given): context workspaces, kept
+    // for the next ingest, so that these large transient buffers do not
+    // fragment the device memory pool the handles allocate from.
     DevBuf<uint32_t> hist((size_t)sp.bins * sp.grid);
-    DevBuf<uint4> rec_a, rec_b;
-    DevBuf<uint32_t> keys_a, keys_b;
-    DevBuf<float2> lo_a, lo_b;
+    uint4 *rec_a = nullptr, *rec_b = nullptr;
+    uint32_t *keys_a = nullptr, *keys_b = nullptr;
+    float2 *lo_a = nullptr, *lo_b = nullptr;
     if (sp.passes > 1) {
-        rec_a.alloc(n);
-        keys_a.alloc(n);
-        if (has_lo) lo_a.alloc(n);
+        rec_a = workspace_as<uint4>(ctx, "ingest_rec_a", n);
+        keys_a = workspace_as<uint32_t>(ctx, "ingest_keys_a", n);
+        if (has_lo) lo_a = workspace_as<float2>(ctx, "ingest_lo_a", n);
     }
     if (sp.passes > 2) {
-        rec_b.alloc(n);
-        keys_b.alloc(n);
-        if (has_lo) lo_b.alloc(n);
+        rec_b = workspace_as<uint4>(ctx, "ingest_rec_b", n);
+        keys_b = workspace_as<uint32_t>(ctx, "ingest_keys_b", n);
+        if (has_lo) lo_b = workspace_as<float2>(ctx, "ingest_lo_b", n);
     }
     // the first pass reads its keys from the validated pixel indices
     const uint32_t* kin = reinterpret_cast<const uint32_t*>(p->pix.get());
-    uint32_t* kout = keys_a.get();
+    uint32_t* kout = keys_a;
     const size_t smem = scatter_smem(sp.bins);
     const uint4* rin = nullptr;  // the first pass reads keys, indices and trig in time order
-    uint4* rout = rec_a.get();
+    uint4* rout = rec_a;
     const float2* lin = has_lo ? p->cs_lo_t.get() : nullptr;
-    float2* lout = lo_a.get();
+    float2* lout = lo_a;
     for (int pass = 0; pass < sp.passes; ++pass) {
         const int shift = pass * sp.bits;
         {
@@ -734,11 +736,11 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
             else rs_scatter_kernel<false, false><<<sp.grid, SC_THREADS, smem, s>>>(a);
             BM_LAUNCH_CHECK();
             kin = kout;
-            kout = (kout == keys_a.get()) ? keys_b.get() : keys_a.get();
+            kout = (kout == keys_a) ? keys_b : keys_a;
             rin = rout;
-            rout = (rout == rec_a.get()) ? rec_b.get() : rec_a.get();
+            rout = (rout == rec_a) ? rec_b : rec_a;
             lin = has_lo ? lout : nullptr;
-            lout = (lout == lo_a.get()) ? lo_b.get() : lo_a.get();
+            lout = (lout == lo_a) ? lo_b : lo_a;
         } else {
             a.perm_out = p->perm.get();
             a.hi_out = p->cs_hi_s.get();

@@ -958,6 +958,276 @@ __global__ void offset_counts_kernel(const int32_t* __restrict__ pix, const uint
     }
 }
 
+static void finalize(bm_context* ctx, const int64_t* pitem, const double* partial, int64_t npix, int nc,
+                     double* q);
+
+// isort[i] = the interval of sample perm[i] (pixel-sorted order).
+__global__ void offset_isort_kernel(const uint32_t* __restrict__ perm, int64_t nvalid, OffsetGeom g,
+                                    uint32_t* __restrict__ isort) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvalid;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = perm[i];
+        const int d = find_tile_det(g.det_off, g.ndet, t);
+        // t - det_off[d] < 2^32 and baseline_len <= nsamples < 2^32: a 32-bit division
+        isort[i] = (uint32_t)g.int_start[d] + (uint32_t)(t - g.det_off[d]) / (uint32_t)g.baseline_len;
+    }
+}
+
+// The mixed operator of the offset template in its destriping form,
+//   A x = P^T Nk P x - P^T Nk F m,   m = (F^T Nk F)^-1 F^T Nk P x,
+// two streaming passes instead of P x, the filter and a transpose.  The
+// first, in time order, gives each interval's mean of P x over its kept
+// samples (x4 is zero on masked pixels and flagged samples give 0, so the
+// interval's plain sum over the kept count); it stores sqrt(w_d) m_I for
+// IQU and QU (the sorted pass forms sqrt(w) v . x from the weighted stream)
+// and m_I for I.  One warp per interval, sums as in offset_filter_kernel.
+__global__ void __launch_bounds__(256)
+offset_means_f32_kernel(const int32_t* __restrict__ pix, const float2* __restrict__ hi,
+                        const float4* __restrict__ x4, OffsetGeom g, const double* __restrict__ inv_cnt,
+                        const double* __restrict__ white, bool sqrt_weighted, float* __restrict__ mw) {
+    constexpr int U = 8;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < g.nint; j += nwarps) {
+        int d;
+        int64_t a, e;
+        offset_interval(g, j, d, a, e);
+        double s = 0.0;
+        for (int64_t t0 = a + lane; t0 < e; t0 += 32 * U) {
+            int32_t p[U];
+            float2 h[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t t = t0 + 32 * u;
+                p[u] = t < e ? pix[t] : -1;
+                h[u] = t < e ? hi[t] : make_float2(0.f, 0.f);
+            }
+            float ps = 0.f;
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (p[u] >= 0) {
+                    const float4 xv = x4[p[u]];
+                    ps += fmaf(h[u].x, xv.y, fmaf(h[u].y, xv.z, xv.x));
+                }
+            s += (double)ps;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            const double m = s * inv_cnt[j];
+            mw[j] = (float)(sqrt_weighted ? m * sqrt(white[d]) : m);
+        }
+    }
+}
+
+// The pixel-sorted pass: per kept sample, with u = sqrt(w)(cos, sin) from
+// the weighted stream and r = |u| = sqrt(w),
+//   y = r x_I + u . (x_Q, x_U) - sqrt(w) m_I,  q += y (r, u)   (IQU, QU),
+//   q_I += w (x_I - m_I)                                      (I),
+// summed per work item as the white kernel does (FP32 groups of 8 per lane
+// folded into double-float, warp sums in double-float).
+template <int NC>
+__global__ void __launch_bounds__(kWarps * 32)
+offset_matvec_f32_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ item_beg,
+                         const int32_t* __restrict__ item_len, int64_t nitems, const float2* __restrict__ wcs,
+                         const float* __restrict__ w1, const uint32_t* __restrict__ isort,
+                         const float* __restrict__ mw, const float4* __restrict__ x4,
+                         double* __restrict__ partial) {
+    constexpr int U = 8;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+    for (int64_t k = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); k < nitems; k += nwarps) {
+        const int64_t p = item_pix[k];
+        const int64_t b = item_beg[k], e = b + item_len[k];
+        const float4 xv = x4[p];
+        float a[NC];
+        df32 A[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            a[c] = 0.f;
+            A[c] = {0.f, 0.f};
+        }
+        for (int64_t i0 = b + lane; i0 < e; i0 += 32 * U) {
+            // every stream load of the group is issued before the dependent
+            // gathers of the means
+            float m[U];
+            uint32_t it[U];
+            float2 wv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool in = i0 + 32 * u < e;
+                it[u] = in ? __ldg(isort + i0 + 32 * u) : 0u;
+                if (NC == 1) wv[u].x = in ? __ldg(w1 + i0 + 32 * u) : 0.f;
+                else wv[u] = in ? __ldg(wcs + i0 + 32 * u) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) m[u] = i0 + 32 * u < e ? __ldg(mw + it[u]) : 0.f;
+            if (NC == 1) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) a[0] = fmaf(wv[u].x, xv.x - m[u], a[0]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const float2 w = wv[u];
+                    float r = 0.f;
+                    if (NC == 3) {
+                        const float u2 = fmaf(w.x, w.x, w.y * w.y);
+                        r = u2 > 0.f ? u2 * rsqrtf(u2) : 0.f;
+                    }
+                    const float y = fmaf(w.x, xv.y, fmaf(w.y, xv.z, r * xv.x)) - m[u];
+                    if (NC == 3) a[0] = fmaf(y, r, a[0]);
+                    a[NC - 2] = fmaf(y, w.x, a[NC - 2]);
+                    a[NC - 1] = fmaf(y, w.y, a[NC - 1]);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                A[c] = df_add(A[c], a[c]);
+                a[c] = 0.f;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) A[c] = df_warp_sum(A[c]);
+        if (lane == 0)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) partial[NC * k + c] = df_to_double(A[c]);
+    }
+}
+
+// x (FP64, [npix][NC]) -> per pixel two float4 of double-float pairs
+// (I.hi, I.lo, Q.hi, Q.lo), (U.hi, U.lo, 0, 0); zero on masked pixels and
+// for the components the system does not have.
+__global__ void masked_copy_df_kernel(const double* __restrict__ x, const uint8_t* __restrict__ mask, int64_t npix,
+                                      int nc, float4* __restrict__ out) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double v[3] = {0.0, 0.0, 0.0};
+        if (!mask[p]) {
+            const double* xp = x + p * nc;
+            if (nc == 3) { v[0] = xp[0]; v[1] = xp[1]; v[2] = xp[2]; }
+            else if (nc == 2) { v[1] = xp[0]; v[2] = xp[1]; }
+            else v[0] = xp[0];
+        }
+        df32 d[3];
+        for (int c = 0; c < 3; ++c) d[c] = df_from(v[c]);
+        out[2 * p] = make_float4(d[0].hi, d[0].lo, d[1].hi, d[1].lo);
+        out[2 * p + 1] = make_float4(d[2].hi, d[2].lo, 0.f, 0.f);
+    }
+}
+
+// The refinement operator of the offset template (the destriping form of
+// offset_means_f32_kernel in double-float, ~48-bit): each interval's mean of
+// P x over its kept samples, times w_d, stored as a double-float pair.
+// Products and sums per sample in double-float on the FP32 pipes; lo = NULL
+// when the trig is exact in FP32.
+__global__ void __launch_bounds__(256)
+offset_means_df_kernel(const int32_t* __restrict__ pix, const float2* __restrict__ hi, const float2* __restrict__ lo,
+                       const float4* __restrict__ xd, OffsetGeom g, const double* __restrict__ inv_cnt,
+                       const double* __restrict__ white, int nc, float2* __restrict__ mwd) {
+    constexpr int U = 4;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < g.nint; j += nwarps) {
+        int d;
+        int64_t a, e;
+        offset_interval(g, j, d, a, e);
+        df32 acc = {0.f, 0.f};
+        for (int64_t t0 = a + lane; t0 < e; t0 += 32 * U) {
+            int32_t p[U];
+            float2 h[U], l[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t t = t0 + 32 * u;
+                p[u] = t < e ? pix[t] : -1;
+                h[u] = (t < e && nc > 1) ? hi[t] : make_float2(0.f, 0.f);
+                l[u] = (t < e && nc > 1 && lo) ? lo[t] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (p[u] < 0) continue;
+                const float4 a0 = xd[2 * (int64_t)p[u]];
+                df32 y = {a0.x, a0.y};
+                if (nc > 1) {
+                    const float4 a1 = xd[2 * (int64_t)p[u] + 1];
+                    y = df_add(y, df_mul(df32{a0.z, a0.w}, df32{h[u].x, l[u].x}));
+                    y = df_add(y, df_mul(df32{a1.x, a1.y}, df32{h[u].y, l[u].y}));
+                }
+                acc = df_add(acc, y);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc = df_add(acc, df_shfl_xor(acc, o));
+        if (lane == 0) {
+            const df32 m = df_from(df_to_double(acc) * inv_cnt[j] * white[d]);
+            mwd[j] = make_float2(m.hi, m.lo);
+        }
+    }
+}
+
+// q_p partial = sum over the item's samples of (w_d m_I) (1, cos, sin) in
+// double-float, the interval read from the sorted table.
+template <int NC>
+__global__ void __launch_bounds__(kWarps * 32)
+offset_pt_df_kernel(const int64_t* __restrict__ item_beg, const int32_t* __restrict__ item_len, int64_t nitems,
+                    const uint32_t* __restrict__ isort, const float2* __restrict__ hi, const float2* __restrict__ lo,
+                    const float2* __restrict__ mwd, double* __restrict__ partial) {
+    constexpr int U = 4;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+    for (int64_t k = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); k < nitems; k += nwarps) {
+        const int64_t b = item_beg[k], e = b + item_len[k];
+        df32 A[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) A[c] = {0.f, 0.f};
+        for (int64_t i0 = b + lane; i0 < e; i0 += 32 * U) {
+            uint32_t it[U];
+            float2 h[U], l[U], m[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool in = i0 + 32 * u < e;
+                it[u] = in ? isort[i0 + 32 * u] : 0u;
+                h[u] = (in && NC > 1) ? hi[i0 + 32 * u] : make_float2(0.f, 0.f);
+                l[u] = (in && NC > 1 && lo) ? lo[i0 + 32 * u] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) m[u] = i0 + 32 * u < e ? mwd[it[u]] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const df32 v = {m[u].x, m[u].y};
+                if (NC != 2) A[0] = df_add(A[0], v);
+                if (NC > 1) {
+                    A[NC - 2] = df_add(A[NC - 2], df_mul(v, df32{h[u].x, l[u].x}));
+                    A[NC - 1] = df_add(A[NC - 1], df_mul(v, df32{h[u].y, l[u].y}));
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) A[c] = df_warp_sum(A[c]);
+        if (lane == 0)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) partial[NC * k + c] = df_to_double(A[c]);
+    }
+}
+
+// q_p = B_p x_p - t_p on kept pixels (B the FP64 blocks P^T Nk P of the
+// preconditioner build), 0 on masked ones.
+template <int NC>
+__global__ void block_minus_kernel(const double* __restrict__ B, const uint8_t* __restrict__ mask,
+                                   const double* __restrict__ x, int64_t npix, double* __restrict__ q) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const double* Bp = B + p * NC * NC;
+        const double* xp = x + p * NC;
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+            double s = 0.0;
+#pragma unroll
+            for (int j = 0; j < NC; ++j) s = fma(Bp[i * NC + j], xp[j], s);
+            q[p * NC + i] = mask[p] ? 0.0 : s - q[p * NC + i];
+        }
+    }
+}
+
 static OffsetGeom offset_geom(const bm_inv_noise* n) {
     return {n->det_off.get(), n->int_start.get(), n->ndet, n->baseline_len, n->nint};
 }
@@ -965,11 +1235,86 @@ static OffsetGeom offset_geom(const bm_inv_noise* n) {
 void build_offset_counts(bm_precond* pc) {
     bm_context* ctx = pc->ctx;
     const bm_inv_noise* n = pc->n;
+    const bm_pointing* p = pc->p;
     pc->ofs_inv.alloc(std::max<int64_t>(n->nint, 1));
+    pc->ofs_isort.alloc(std::max<int64_t>(p->nvalid, 1));
     if (n->nint == 0) return;
     offset_counts_kernel<<<resident_grid(ctx, offset_counts_kernel, 256, (n->nint + 7) / 8), 256, 0, ctx->stream>>>(
-        pc->p->pix.get(), pc->mask.get(), offset_geom(n), pc->ofs_inv.get());
+        p->pix.get(), pc->mask.get(), offset_geom(n), pc->ofs_inv.get());
     BM_LAUNCH_CHECK();
+    if (p->nvalid > 0) {
+        offset_isort_kernel<<<grid_for(ctx, (p->nvalid + 255) / 256, 16), 256, 0, ctx->stream>>>(
+            p->perm.get(), p->nvalid, offset_geom(n), pc->ofs_isort.get());
+        BM_LAUNCH_CHECK();
+    }
+}
+
+// q = A x with the refinement operator of the offset template (see
+// offset_means_df_kernel).
+static void offset_matvec_refine(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, double* q) {
+    bm_context* ctx = p->ctx;
+    cudaStream_t s = ctx->stream;
+    const int nc = p->ncomp;
+    const int threads = 256;
+    const int pgrid = grid_for(ctx, (p->npix + threads - 1) / threads, 16);
+    float4* xd = workspace_as<float4>(ctx, "ofs_xd", 2 * p->npix);
+    masked_copy_df_kernel<<<pgrid, threads, 0, s>>>(x, pc->mask.get(), p->npix, nc, xd);
+    BM_LAUNCH_CHECK();
+    float2* mwd = workspace_as<float2>(ctx, "ofs_mwd", std::max<int64_t>(n->nint, 1));
+    if (n->nint > 0) {
+        ScopedTimer timer(ctx, "offset_means_df");
+        offset_means_df_kernel<<<resident_grid(ctx, offset_means_df_kernel, 256, (n->nint + 7) / 8), 256, 0, s>>>(
+            p->pix.get(), p->cs_hi_t.get(), p->cs_lo_t.get(), xd, offset_geom(n), pc->ofs_inv.get(), n->white.get(),
+            nc, mwd);
+        BM_LAUNCH_CHECK();
+    }
+    double* partial = workspace_as<double>(ctx, "partial", (size_t)std::max<int64_t>(pc->nitems, 1) * nc);
+    if (pc->nitems > 0) {
+        ScopedTimer timer(ctx, "offset_pt_df");
+        const int64_t wunits = (pc->nitems + kWarps - 1) / kWarps;
+#define BM_OP(NC)                                                                                                  \
+    offset_pt_df_kernel<NC><<<resident_grid(ctx, offset_pt_df_kernel<NC>, kWarps * 32, wunits), kWarps * 32, 0, s>>>( \
+        pc->item_beg.get(), pc->item_len.get(), pc->nitems, pc->ofs_isort.get(), p->cs_hi_s.get(), p->cs_lo_s.get(), \
+        mwd, partial)
+        if (nc == 3) BM_OP(3); else if (nc == 2) BM_OP(2); else BM_OP(1);
+#undef BM_OP
+        BM_LAUNCH_CHECK();
+    }
+    finalize(ctx, pc->pitem.get(), partial, p->npix, nc, q);
+#define BM_BM(NC) block_minus_kernel<NC><<<pgrid, threads, 0, s>>>(pc->B.get(), pc->mask.get(), x, p->npix, q)
+    if (nc == 3) BM_BM(3); else if (nc == 2) BM_BM(2); else BM_BM(1);
+#undef BM_BM
+    BM_LAUNCH_CHECK();
+}
+
+// q = A x with the mixed operator of the offset template (see
+// offset_means_f32_kernel).
+static void offset_matvec_mixed(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, double* q) {
+    bm_context* ctx = p->ctx;
+    cudaStream_t s = ctx->stream;
+    const int nc = p->ncomp;
+    const int threads = 256;
+    float4* x4 = workspace_as<float4>(ctx, "x4", p->npix);
+    masked_copy4_kernel<<<grid_for(ctx, (p->npix + threads - 1) / threads, 16), threads, 0, s>>>(
+        x, pc->mask.get(), p->npix, nc, x4);
+    BM_LAUNCH_CHECK();
+    float* mw = workspace_as<float>(ctx, "ofs_mw", std::max<int64_t>(n->nint, 1));
+    if (n->nint > 0) {
+        ScopedTimer timer(ctx, "offset_means_f32");
+        offset_means_f32_kernel<<<resident_grid(ctx, offset_means_f32_kernel, 256, (n->nint + 7) / 8), 256, 0, s>>>(
+            p->pix.get(), p->cs_hi_t.get(), x4, offset_geom(n), pc->ofs_inv.get(), n->white.get(), nc > 1, mw);
+        BM_LAUNCH_CHECK();
+    }
+    double* partial = workspace_as<double>(ctx, "partial", (size_t)std::max<int64_t>(pc->nitems, 1) * nc);
+    if (pc->nitems > 0) {
+        ScopedTimer timer(ctx, "offset_matvec_f32");
+        const int64_t wunits = (pc->nitems + kWarps - 1) / kWarps;
+#define BM_OM(NC)                                                                                                      offset_matvec_f32_kernel<NC><<<resident_grid(ctx, offset_matvec_f32_kernel<NC>, kWarps * 32, wunits),                                             kWarps * 32, 0, s>>>(pc->item_pix.get(), pc->item_beg.get(), pc->item_len.get(),                                                         pc->nitems, pc->wcs.get(), pc->w1.get(),                                                                           pc->ofs_isort.get(), mw, x4, partial)
+        if (nc == 3) BM_OM(3); else if (nc == 2) BM_OM(2); else BM_OM(1);
+#undef BM_OM
+        BM_LAUNCH_CHECK();
+    }
+    finalize(ctx, pc->pitem.get(), partial, p->npix, nc, q);
 }
 
 // inv_cnt = NULL: every sample is kept.
@@ -977,6 +1322,7 @@ template <typename T, class Src>
 static void run_offset_filter(bm_inv_noise* n, const Src& src, const double* inv_cnt, T* z) {
     bm_context* ctx = n->ctx;
     if (n->nint == 0) return;
+    ScopedTimer timer(ctx, sizeof(T) == 4 ? "offset_filter_f32" : "offset_filter_f64");
     auto kern = offset_filter_kernel<T, Src>;
     kern<<<resident_grid(ctx, kern, 256, (n->nint + 7) / 8), 256, 0, ctx->stream>>>(src, offset_geom(n),
                                                                                     n->white.get(), inv_cnt, z);
@@ -1146,6 +1492,10 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
                 BM_LAUNCH_CHECK();
             }
             finalize(ctx, pc->pitem.get(), partial, p->npix, nc, qr);
+        } else if (n->kind == 3 && prec == BM_PREC_MIXED) {
+            offset_matvec_mixed(p, n, pc, xr, qr);
+        } else if (n->kind == 3 && prec == kPrecRefine) {
+            offset_matvec_refine(p, n, pc, xr, qr);
         } else {
             if (prec == BM_PREC_MIXED) {
                 float* z32 = workspace_as<float>(ctx, "z32", p->nsamples);

@@ -361,7 +361,9 @@ void build_precond(bm_precond* pc) {
         Items all;
         plan_items(ctx, p->off.get(), nullptr, npix, all);
         DevBuf<double> partial((all.n > 0 ? all.n : 1) * ns);
-        const bool white = diagonal_noise(n) && p->nvalid > 0;
+        // the weighted sorted stream: white noise, and the offset template's
+        // mixed operator (its white part)
+        const bool white = (diagonal_noise(n) || n->kind == 3) && p->nvalid > 0;
         if (n->kind == 2 && p->nvalid > 0) {  // a weight per sample: gathered once into sorted order
             pc->ws_df.alloc(p->nvalid);
             pc->ws_sqrt.alloc(p->nvalid);
@@ -375,7 +377,7 @@ void build_precond(bm_precond* pc) {
             else pc->wcs.alloc(p->nvalid);
         }
         // b = P^T N^-1 d of a TOD the pointing carries, in the same pass
-        const bool with_rhs = white && p->tod_s.get() != nullptr;
+        const bool with_rhs = white && diagonal_noise(n) && p->tod_s.get() != nullptr;
         DevBuf<double> rpartial;
         if (with_rhs) {
             rpartial.alloc((all.n > 0 ? all.n : 1) * nc);

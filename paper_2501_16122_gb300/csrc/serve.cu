@@ -112,6 +112,8 @@ bm_status run_request(bm_context* ctx, Job& job) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     ctx->ws.clear();
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->ws_pool) cudaMemPoolTrimTo(ctx->ws_pool, 0);  // the budget counts this memory as released
     return st;
 }
 
