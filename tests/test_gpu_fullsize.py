@@ -9,7 +9,10 @@ times, on outputs the FP64 oracle can compute one pixel at a time:
     FP64 matvec on sampled pixels (each needs only +-511-sample windows
     around its samples), and exact recovery of the sky from noiseless TOD;
   * config 3 (nside 512, 64 det x 2^22 samples, 64 right-hand sides): every
-    right-hand side's map on sampled pixels.
+    right-hand side's map on sampled pixels;
+  * the offset template on config 2's scan: the operators on sampled pixels
+    (each needs only the baselines its samples fall in), the I monopole in the
+    null space, symmetry, and the solve of a sky plus baseline offsets.
 """
 import gc
 
@@ -197,6 +200,100 @@ def test_toeplitz_mixed_matvec_over_time_chunks(L, ctx):
             q2 = torch.zeros_like(q)
             L.bm_matvec(p, n, pc, torch.from_numpy(x.ravel()).cuda(), q2, prec)
             assert torch.equal(q, q2)
+    for h, f in ((pc, L.bm_precond_destroy), (n, L.bm_inv_noise_destroy), (p, L.bm_pointing_destroy)):
+        f(h)
+
+
+def oracle_offset_matvec_pixels(e, pix, c32, s32, bl, mask, x, pixels):
+    """(P^T W P x)_p for the sampled pixels with the baseline-offset W: each
+    sample t of p contributes w_d v_t (y_t - m_I), m_I the mean of y = P x
+    over the kept samples of t's interval I, so only the intervals the
+    sampled pixels touch are evaluated (all their samples)."""
+    idx = select_samples(pix, e.npix, pixels)
+    keep_pix = np.where((pix >= 0) & ~mask[np.where(pix >= 0, pix, 0)], pix, -1)
+    idx = idx[keep_pix[idx] >= 0]
+    d = idx // e.ns
+    ipd = -(-e.ns // bl)                                   # intervals per detector
+    I = d * ipd + (idx - d * e.ns) // bl
+    m = {}
+    for j in np.unique(I):
+        dd, k = divmod(int(j), ipd)
+        a = dd * e.ns + k * bl
+        win = np.arange(a, min(a + bl, (dd + 1) * e.ns))
+        kp = keep_pix[win]
+        v = gls.pointing_weights_trig(c32[win], s32[win], 3)
+        y = gls.apply_P(kp, v, x)                          # 0 on samples that are not kept
+        m[int(j)] = y.sum() / max(int((kp >= 0).sum()), 1)
+    w = 1.0 / e.sigma ** 2
+    v = gls.pointing_weights_trig(c32[idx], s32[idx], 3)
+    y = gls.apply_P(keep_pix[idx], v, x)
+    z = w[d] * (y - np.array([m[int(j)] for j in I]))
+    where = {p: i for i, p in enumerate(pixels)}
+    q = np.zeros((len(pixels), 3))
+    np.add.at(q, np.array([where[p] for p in keep_pix[idx]]), z[:, None] * v)
+    return q
+
+
+def test_offsets_full_size(L, ctx):
+    """The offset template at the bench's size (config 2's scan, 1.07e9
+    samples, 1200-sample baselines): the FP64 and mixed operators on sampled
+    pixels against the oracle's evaluation; the I monopole in the null space
+    and the symmetry of the operator (properties at any size); and a mixed
+    solve of a noiseless sky plus a random offset per baseline, which gives
+    back Q and U and the I map up to its monopole."""
+    e = synth.make_experiment(256, 256, 2 ** 22, 1002)
+    pt = synth.pointing(e)
+    c32, s32 = synth.trig32(pt["psi"])
+    bl = 1200
+    p = L.bm_pointing_create_trig(ctx, e.npix, torch.from_numpy(pt["pix"]).cuda(), torch.from_numpy(c32).cuda(),
+                                  torch.from_numpy(s32).cuda(), 3)
+    n = L.bm_inv_noise_create_offset_filter(ctx, e.det_offsets, 1 / e.sigma ** 2, bl)
+    pc = L.bm_blockdiag_precond_create(p, n, 3, 1e3)
+    mask = torch.zeros(e.npix, dtype=torch.uint8, device="cuda")
+    hits = torch.zeros(e.npix, dtype=torch.int32, device="cuda")
+    L.bm_precond_get_mask(pc, mask, hits)
+    mask_h, hits_h = mask.cpu().numpy().astype(bool), hits.cpu().numpy()
+    rng = np.random.default_rng(3)
+    x = rng.normal(size=(e.npix, 3)) * np.array([100.0, 10.0, 10.0])
+    xm = x * (~mask_h)[:, None]
+    pixels = sampled_pixels(hits_h, mask_h, rng, n=6)
+    ref = oracle_offset_matvec_pixels(e, pt["pix"], c32, s32, bl, mask_h, xm, pixels)
+
+    def mv(vec, prec):
+        q = torch.zeros(e.npix * 3, dtype=torch.float64, device="cuda")
+        L.bm_matvec(p, n, pc, torch.from_numpy(np.ascontiguousarray(vec).ravel()).cuda(), q, prec)
+        return q.cpu().numpy().reshape(e.npix, 3)
+
+    for prec, tol in ((L.BM_PREC_FP64, 1e-10), (L.BM_PREC_MIXED, 2e-6)):
+        qh = mv(x, prec)
+        for k in range(3):
+            err = np.linalg.norm(qh[pixels, k] - ref[:, k]) / np.linalg.norm(ref[:, k])
+            assert err < tol, (prec, k, err)
+        assert np.all(qh[mask_h] == 0)
+        # a constant I map is an offset on every baseline: A maps it to ~0
+        one = np.zeros((e.npix, 3))
+        one[:, 0] = 1.0
+        B1 = np.linalg.norm(hits_h[~mask_h] / e.sigma.min() ** 2)
+        assert np.linalg.norm(mv(one, prec)) < (1e-12 if prec == L.BM_PREC_FP64 else 1e-6) * B1
+    y2 = rng.normal(size=(e.npix, 3)) * np.array([100.0, 10.0, 10.0]) * (~mask_h)[:, None]
+    a, b = np.sum(xm * mv(y2, L.BM_PREC_FP64)), np.sum(y2 * mv(xm, L.BM_PREC_FP64))
+    assert abs(a - b) < 1e-12 * (abs(a) + abs(b))
+    # noiseless sky + offsets: the mixed solve recovers the sky up to the I monopole
+    sky = synth.sky_map(e.npix, 1002)
+    tod = synth.tod(e, pt["pix"], pt["psi"], sky, white=False, dtype=np.float64, trig=(c32, s32))
+    ipd = -(-e.ns // bl)
+    off = rng.normal(0.0, 30.0, (e.ndet, ipd))
+    tod += np.repeat(off, bl, axis=1)[:, :e.ns].ravel()
+    out = torch.zeros(e.npix * 3, dtype=torch.float64, device="cuda")
+    st, info = L.bm_pcg_solve(p, n, pc, torch.from_numpy(tod).cuda(), 1, out, 1e-9, 3000, L.BM_PREC_MIXED)
+    assert st == L.BM_OK, info
+    got = out.cpu().numpy().reshape(e.npix, 3)
+    keep = ~mask_h
+    got[keep, 0] -= got[keep, 0].mean()
+    sky = sky.copy()
+    sky[keep, 0] -= sky[keep, 0].mean()
+    err = gls.rel_err(got, sky, mask_h)
+    assert all(v < 1e-6 for v in err.values()), err
     for h, f in ((pc, L.bm_precond_destroy), (n, L.bm_inv_noise_destroy), (p, L.bm_pointing_destroy)):
         f(h)
 
