@@ -375,7 +375,8 @@ def run_gb300(args, rank, world, local_rank):
         # perm + trig (+ TOD) of kept samples, or records + keys
         wr = ((16 if carried else 12) * n_valid / nt) if last else 20
         scatter_bytes += (rd + wr) * nt
-        hist_bytes += 4 * nt                               # keys
+        if ps > 0:                                         # (the first pass's counts come from validation)
+            hist_bytes += 4 * nt                           # keys
     step_bytes = {
         "ingest_validate": 24 * nt,                       # pix + cos + sin in; pix, trig pair out
         "ingest_hist": hist_bytes,

@@ -91,14 +91,30 @@ __device__ __forceinline__ void st_keep(float2* p, float2 v, uint64_t pol) {
 // counters[1] = flagged samples.  With tod_dst, also copies the TOD
 // (a host-memory source read once over the host link).
 // MODE: kTrigIn (cos/sin given), kPsi64 or kPsi32 (angles given).
+// HIST: also the first sort pass's digit counts (the sort key of each
+// validated sample, flagged ones as npix, masked to the low digit) of each
+// range of `range` samples, hist[d * G + range], as rs_hist_kernel counts
+// them; `sub` blocks share a range (its equal parts), each adding its counts
+// to the zeroed hist.  Without HIST the loop is grid-strided.
 constexpr int kTrigIn = 0, kPsi64 = 1, kPsi32 = 2;
-template <int MODE>
-__global__ void validate_kernel(const int32_t* __restrict__ pix, const void* __restrict__ psi,
-                                const float* __restrict__ c32, const float* __restrict__ s32, int64_t n,
-                                int64_t npix, int32_t* __restrict__ pix_out,
-                                float2* __restrict__ hi, float2* __restrict__ lo,
-                                const float* __restrict__ tod_src, float* __restrict__ tod_dst,
-                                unsigned long long* __restrict__ counters) {
+constexpr int kVHist = 4;  // shared-memory digit histograms per validation block
+template <int MODE, bool HIST>
+__global__ void __launch_bounds__(256)
+validate_kernel(const int32_t* __restrict__ pix, const void* __restrict__ psi,
+                const float* __restrict__ c32, const float* __restrict__ s32, int64_t n,
+                int64_t npix, int32_t* __restrict__ pix_out,
+                float2* __restrict__ hi, float2* __restrict__ lo,
+                const float* __restrict__ tod_src, float* __restrict__ tod_dst,
+                unsigned long long* __restrict__ counters, int64_t range, int sub, int bins, int G,
+                uint32_t* __restrict__ hist) {
+    extern __shared__ __align__(16) uint32_t vh[];  // HIST: [kVHist][bins], one per pair of warps
+    uint32_t* mine = nullptr;
+    if (HIST) {
+        for (int d = threadIdx.x; d < kVHist * bins; d += blockDim.x) vh[d] = 0;
+        __syncthreads();
+        mine = vh + ((threadIdx.x >> 5) % kVHist) * bins;
+    }
+    const uint32_t dmask = (uint32_t)bins - 1u;
     unsigned nbad = 0, nflag = 0;
     auto one = [&](int64_t i, int32_t p, float c, float s, double a) {
         const bool ok_p = (p >= -1) && ((int64_t)p < npix);
@@ -118,18 +134,23 @@ __global__ void validate_kernel(const int32_t* __restrict__ pix, const void* __r
         nbad += (!ok_p) + (!ok_a);
         nflag += !kept;
         pix_out[i] = ok_p ? p : -1;
+        if (HIST) atomicAdd(&mine[(kept ? (uint32_t)p : (uint32_t)npix) & dmask], 1u);
     };
     // four samples per thread and pass, their loads issued together
     constexpr int U = 4;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += U * stride) {
+    const int64_t stride = HIST ? (int64_t)blockDim.x : (int64_t)gridDim.x * blockDim.x;
+    const int64_t part = range / sub;
+    const int64_t begin = HIST ? (int64_t)(blockIdx.x / sub) * range + (int64_t)(blockIdx.x % sub) * part : 0;
+    const int64_t end = HIST ? (begin + part < n ? begin + part : n) : n;
+    for (int64_t i0 = begin + (HIST ? 0 : (int64_t)blockIdx.x * blockDim.x) + threadIdx.x; i0 < end;
+         i0 += U * stride) {
         int32_t p[U];
         float c[U], sv[U];
         double a[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int64_t i = i0 + u * stride;
-            const bool v = i < n;
+            const bool v = i < end;
             p[u] = v ? __ldcs(pix + i) : 0;
             c[u] = sv[u] = 0.f;
             a[u] = 0.0;
@@ -147,14 +168,22 @@ __global__ void validate_kernel(const int32_t* __restrict__ pix, const void* __r
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int64_t i = i0 + u * stride;
-            if (i < n) one(i, p[u], c[u], sv[u], a[u]);
+            if (i < end) one(i, p[u], c[u], sv[u], a[u]);
         }
         if (tod_dst) {
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int64_t i = i0 + u * stride;
-                if (i < n) tod_dst[i] = __ldcs(tod_src + i);
+                if (i < end) tod_dst[i] = __ldcs(tod_src + i);
             }
+        }
+    }
+    if (HIST) {
+        __syncthreads();
+        for (int d = threadIdx.x; d < bins; d += blockDim.x) {
+            uint32_t t = 0;
+            for (int q = 0; q < kVHist; ++q) t += vh[q * bins + d];
+            if (t) atomicAdd(&hist[(int64_t)d * G + blockIdx.x / sub], t);
         }
     }
     nbad = __reduce_add_sync(0xffffffffu, nbad);
@@ -622,6 +651,10 @@ SortPlan plan_sort(const bm_context* ctx, int64_t n, int64_t npix) {
     ensure_smem_limit(reinterpret_cast<const void*>(rs_scatter_kernel<true, true>), smem);
     ensure_smem_limit(reinterpret_cast<const void*>(rs_scatter_kernel<true, false>), smem);
     ensure_smem_limit(reinterpret_cast<const void*>(rs_hist_kernel), sizeof(uint32_t) * IG_WARPS * sp.bins);
+    for (const void* k : {reinterpret_cast<const void*>(validate_kernel<kTrigIn, true>),
+                          reinterpret_cast<const void*>(validate_kernel<kPsi64, true>),
+                          reinterpret_cast<const void*>(validate_kernel<kPsi32, true>)})
+        ensure_smem_limit(k, sizeof(uint32_t) * kVHist * sp.bins);
     int per_sm = blocks_per_sm(reinterpret_cast<const void*>(rs_scatter_kernel<true, false>), SC_THREADS, smem);
     if (per_sm < 1) per_sm = 1;
     // four waves of equal ranges keep the tail short
@@ -654,14 +687,18 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
     const float* tod_t = tod_on_host ? tod_copy.get() : tod;
     DevBuf<unsigned long long> counters(3);  // invalid samples, flagged samples, a scatter wait that gave up
     BM_CUDA(cudaMemsetAsync(counters.get(), 0, 3 * sizeof(unsigned long long), s));
+    // digit counts of every sort pass; the first pass's come from the validation
+    DevBuf<uint32_t> hist((size_t)sp.bins * sp.grid);
     {
         ScopedTimer vt(ctx, "ingest_validate");
-        auto kern = exact_trig ? validate_kernel<kTrigIn>
-                               : (psi_dtype == BM_F64 ? validate_kernel<kPsi64> : validate_kernel<kPsi32>);
-        const int grid = resident_grid(ctx, kern, threads, (n + threads - 1) / threads);
-        kern<<<grid, threads, 0, s>>>(pix, psi, cos2psi, sin2psi, n, npix, p->pix.get(),
-                                      p->cs_hi_t.get(), p->cs_lo_t.get(), tod_on_host ? tod : nullptr,
-                                      tod_copy.get(), counters.get());
+        BM_CUDA(cudaMemsetAsync(hist.get(), 0, sizeof(uint32_t) * (size_t)sp.bins * sp.grid, s));
+        auto kern = exact_trig ? validate_kernel<kTrigIn, true>
+                               : (psi_dtype == BM_F64 ? validate_kernel<kPsi64, true> : validate_kernel<kPsi32, true>);
+        constexpr int kSub = 2;  // two blocks a range: eight resident blocks per SM
+        kern<<<sp.grid * kSub, IG_THREADS, sizeof(uint32_t) * kVHist * sp.bins, s>>>(
+            pix, psi, cos2psi, sin2psi, n, npix, p->pix.get(), p->cs_hi_t.get(), p->cs_lo_t.get(),
+            tod_on_host ? tod : nullptr, tod_copy.get(), counters.get(), sp.range, kSub, sp.bins, sp.grid,
+            hist.get());
         BM_LAUNCH_CHECK();
     }
     unsigned long long h_cnt[2] = {0, 0};
@@ -681,7 +718,6 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
     // of the trig pairs when the angles were given): context workspaces, kept
     // for the next ingest, so that these large transient buffers do not
     // fragment the device memory pool the handles allocate from.
-    DevBuf<uint32_t> hist((size_t)sp.bins * sp.grid);
     uint4 *rec_a = nullptr, *rec_b = nullptr;
     uint32_t *keys_a = nullptr, *keys_b = nullptr;
     float2 *lo_a = nullptr, *lo_b = nullptr;
@@ -705,7 +741,7 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
     float2* lout = lo_a;
     for (int pass = 0; pass < sp.passes; ++pass) {
         const int shift = pass * sp.bits;
-        {
+        if (pass > 0) {
             ScopedTimer ht(ctx, "ingest_hist");
             const size_t hsm = sizeof(uint32_t) * IG_WARPS * sp.bins;
             rs_hist_kernel<<<sp.grid, IG_THREADS, hsm, s>>>(kin, n, sp.range, shift, sp.bins, sp.grid,
