@@ -1322,19 +1322,18 @@ template <typename T, class Src>
 static void run_offset_filter(bm_inv_noise* n, const Src& src, const double* inv_cnt, T* z) {
     bm_context* ctx = n->ctx;
     if (n->nint == 0) return;
-    ScopedTimer timer(ctx, sizeof(T) == 4 ? "offset_filter_f32" : "offset_filter_f64");
+    ScopedTimer timer(ctx, "offset_filter_f64");
     auto kern = offset_filter_kernel<T, Src>;
     kern<<<resident_grid(ctx, kern, 256, (n->nint + 7) / 8), 256, 0, ctx->stream>>>(src, offset_geom(n),
                                                                                     n->white.get(), inv_cnt, z);
     BM_LAUNCH_CHECK();
 }
 
-// The time-ordered N^-1 of a non-diagonal model (a Toeplitz band or the
-// offset filter) on the kept samples of the system `pc` belongs to.
+// The time-ordered N^-1 of a non-diagonal model (a Toeplitz band or, in
+// FP64, the offset filter) on the kept samples of the system `pc` belongs to.
 template <class Src>
-static void apply_filter_f32(bm_inv_noise* n, const bm_precond* pc, const Src& src, float* z) {
-    if (n->kind == 3) run_offset_filter<float>(n, src, pc->ofs_inv.get(), z);
-    else apply_toeplitz_f32(n, src, z);
+static void apply_filter_f32(bm_inv_noise* n, const bm_precond*, const Src& src, float* z) {
+    apply_toeplitz_f32(n, src, z);  // the offset template's mixed operator is offset_matvec_mixed
 }
 template <class Src>
 static void apply_filter_f64(bm_inv_noise* n, const bm_precond* pc, const Src& src, double* z, bool df) {
