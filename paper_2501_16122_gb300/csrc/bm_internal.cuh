@@ -492,5 +492,52 @@ __device__ __forceinline__ df32 df_warp_sum(df32 a) {
     return a;
 }
 
+// Lazily renormalised sums of many double-float terms.  A product is kept
+// as an unnormalised pair (p, e): p = fl(a.hi b.hi), e = its exact rounding
+// error plus the cross terms.  acc_add adds p to the accumulator's leading
+// part exactly (two_sum) and the rounding error and e to its trailing part;
+// acc_norm (every kLazyNorm terms of a lane, and before the lanes are
+// combined) renormalises the pair.  The trailing part then stays within a
+// few units of the leading part's last place: about a third fewer
+// instructions than a normalised double-float product and sum per term, at
+// an error of a few 2^-48 per term.
+constexpr int kLazyNorm = 4;
+__device__ __forceinline__ void prod_u(float hi, float lo, float b, float& p, float& e) {
+    p = __fmul_rn(hi, b);
+    e = __fmaf_rn(lo, b, __fmaf_rn(hi, b, -p));
+}
+__device__ __forceinline__ void prod_u2(float ah, float al, float bh, float bl, float& p, float& e) {
+    p = __fmul_rn(ah, bh);
+    e = __fmaf_rn(al, bh, __fmaf_rn(ah, bl, __fmaf_rn(ah, bh, -p)));
+}
+__device__ __forceinline__ void acc_add(df32& a, float p, float e) {
+    const df32 s = df_two_sum(a.hi, p);
+    a.hi = s.hi;
+    a.lo = __fadd_rn(a.lo, __fadd_rn(s.lo, e));
+}
+__device__ __forceinline__ void acc_norm(df32& a) { a = df_two_sum(a.hi, a.lo); }
+
+// One sample's terms of b = P^T N^-1 d (and of the weighted transposes) in
+// the lazy form: val = d w (d a float: `dh`, dl = 0; or a double-float), then
+// acc[I] += val, acc[Q] += val c, acc[U] += val s with the trig pair as
+// double-float (hi, lo; lo = 0 for exact FP32 trig).  Shared by the block
+// assembly's fused RHS and the pixel-sorted gather-reduce, so both give the
+// same bits.
+template <int NC>
+__device__ __forceinline__ void rhs_term_lazy(df32* acc, float dh, float dl, bool weighted, float2 w, float2 h,
+                                              float2 l) {
+    float vp, ve;
+    if (weighted) prod_u2(dh, dl, w.x, w.y, vp, ve);
+    else { vp = dh; ve = dl; }
+    if (NC != 2) acc_add(acc[0], vp, ve);
+    if (NC > 1) {
+        float p, e;
+        prod_u2(vp, ve, h.x, l.x, p, e);
+        acc_add(acc[NC - 2], p, e);
+        prod_u2(vp, ve, h.y, l.y, p, e);
+        acc_add(acc[NC - 1], p, e);
+    }
+}
+
 }  // namespace bm
 #endif

@@ -269,6 +269,10 @@ gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __rest
             // detector is looked up only when t passes the current one's end
             uint32_t dend = 0;
             float2 w = make_float2(0.f, 0.f);
+            // lazily renormalised sums (rhs_term_lazy, the block assembly's
+            // fused RHS uses the same steps): renormalised after every
+            // kLazyNorm samples of the lane and at the end
+            int nadd = 0;
             auto add = [&](int64_t si, uint32_t t, G gv, float2 h, float2 l) {
                 df32 val;
                 if (sizeof(G) == 4) val = {(float)gv, 0.f};
@@ -281,14 +285,12 @@ gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __rest
                         dend = dt.ns ? (uint32_t)(d + 1) * dt.ns : offp[d + 1];
                         w = wp[d];
                     }
-                    val = df_mul(val, df32{w.x, w.y});
                 }
-                if (NC == 1) {
-                    acc[0] = df_add(acc[0], val);
-                } else {
-                    if (NC == 3) acc[0] = df_add(acc[0], val);
-                    acc[NC - 2] = df_add(acc[NC - 2], df_mul(val, df32{h.x, l.x}));
-                    acc[NC - 1] = df_add(acc[NC - 1], df_mul(val, df32{h.y, l.y}));
+                rhs_term_lazy<NC>(acc, val.hi, val.lo, weighted, w, h, l);
+                if (++nadd == kLazyNorm) {
+                    nadd = 0;
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) acc_norm(acc[c]);
                 }
             };
             // Eight samples per lane in flight (the gathers g[perm] are
@@ -318,7 +320,10 @@ gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __rest
                 add(si, t, gs ? (G)gs[si] : g[t], h, l);
             }
 #pragma unroll
-            for (int c = 0; c < NC; ++c) acc[c] = df_warp_sum(acc[c]);
+            for (int c = 0; c < NC; ++c) {
+                acc_norm(acc[c]);
+                acc[c] = df_warp_sum(acc[c]);
+            }
             if (lane == 0)
 #pragma unroll
                 for (int c = 0; c < NC; ++c) partial[NC * k + c] = df_to_double(acc[c]);

@@ -83,24 +83,6 @@ constexpr int kBlkWarps = 8;
 // same operations in the same order, so the same bits).  EXACT: the trig
 // pairs are exact FP32 values (no lo part), so the block products multiply
 // by a float instead of a double-float.
-// EXACT block sums: a product (hi, lo) * b as an unnormalised pair, p =
-// fl(hi b) and e = its exact rounding error plus lo b; the accumulator adds p
-// to its leading part exactly (two_sum) and the rounding error and e to its
-// trailing part, and is renormalised every kUnroll samples (acc_norm), which
-// keeps the trailing part within a few units of the leading part's last
-// place: about a third fewer instructions than a normalised double-float add
-// and product per term, at an error of a few 2^-48 per term.
-__device__ __forceinline__ void prod_u(float hi, float lo, float b, float& p, float& e) {
-    p = __fmul_rn(hi, b);
-    e = __fmaf_rn(lo, b, __fmaf_rn(hi, b, -p));
-}
-__device__ __forceinline__ void acc_add(df32& a, float p, float e) {
-    const df32 s = df_two_sum(a.hi, p);
-    a.hi = s.hi;
-    a.lo = __fadd_rn(a.lo, __fadd_rn(s.lo, e));
-}
-__device__ __forceinline__ void acc_norm(df32& a) { a = df_two_sum(a.hi, a.lo); }
-
 template <int NC, bool WCS, bool RHS, bool EXACT>
 __global__ void __launch_bounds__(kBlkWarps * 32)
 blocks_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ item_beg,
@@ -149,16 +131,7 @@ blocks_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ 
             }
             const df32 w = {wv.x, wv.y};
             const df32 c = {h.x, l.x}, s = {h.y, l.y};
-            if (RHS) {
-                const df32 val = df_mul(df32{dv, 0.f}, w);
-                if (NC == 1) {
-                    racc[0] = df_add(racc[0], val);
-                } else {
-                    if (NC == 3) racc[0] = df_add(racc[0], val);
-                    racc[NC - 2] = df_add(racc[NC - 2], df_mul(val, c));
-                    racc[NC - 1] = df_add(racc[NC - 1], df_mul(val, s));
-                }
-            }
+            if (RHS) rhs_term_lazy<NC>(racc, dv, 0.f, true, wv, h, l);
             if (EXACT) {
                 if (NC == 1) {
                     acc_add(acc[0], w.hi, w.lo);
@@ -205,6 +178,20 @@ blocks_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ 
         // kUnroll samples per lane in flight (their loads issued together);
         // the lane's samples are still added in order
         constexpr int kUnroll = 4;
+        // the lazy sums are renormalised after every kLazyNorm samples of the
+        // lane (kUnroll == kLazyNorm: at the end of each group) and at the end
+        auto norm = [&]() {
+            if (EXACT) {
+#pragma unroll
+                for (int j = 0; j < NS; ++j) acc_norm(acc[j]);
+            }
+            if (RHS) {
+#pragma unroll
+                for (int j = 0; j < NC; ++j) acc_norm(racc[j]);
+            }
+        };
+        static_assert(kUnroll == kLazyNorm, "groups end on renormalisation points");
+        int nadd = 0;
         int i = lane;
         for (; i + 32 * (kUnroll - 1) < len; i += 32 * kUnroll) {
             uint32_t t[kUnroll];
@@ -220,19 +207,17 @@ blocks_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ 
             }
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) add(b + i + 32 * u, t[u], h[u], l[u], dv[u]);
-            if (EXACT) {
-#pragma unroll
-                for (int j = 0; j < NS; ++j) acc_norm(acc[j]);
-            }
+            norm();
         }
         for (; i < len; i += 32) {
             const int64_t si = b + i;
             add(si, perm[si], hi[si], (!EXACT && lo) ? lo[si] : make_float2(0.f, 0.f), RHS ? tod_s[si] : 0.f);
-            if (EXACT) {
-#pragma unroll
-                for (int j = 0; j < NS; ++j) acc_norm(acc[j]);
+            if (++nadd == kLazyNorm) {
+                nadd = 0;
+                norm();
             }
         }
+        norm();
 #pragma unroll
         for (int j = 0; j < NS; ++j) acc[j] = df_warp_sum(acc[j]);
         if (RHS) {
