@@ -112,8 +112,6 @@ bm_status run_request(bm_context* ctx, Job& job) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     ctx->ws.clear();
-    cudaStreamSynchronize(ctx->stream);
-    if (ctx->ws_pool) cudaMemPoolTrimTo(ctx->ws_pool, 0);  // the budget counts this memory as released
     return st;
 }
 
@@ -123,6 +121,13 @@ void worker_main(bm_server* s, int slot) {
     bm_context* ctx = nullptr;
     bool ok = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) == cudaSuccess &&
               bm_context_create(s->device, stream, &ctx) == BM_OK;
+    // A worker's scratch comes from the device's default pool: released per
+    // request (the budget accounts per request) into memory that the other
+    // workers and the next request reuse without mapping it again.
+    if (ok && ctx->ws_pool) {
+        cudaMemPoolDestroy(ctx->ws_pool);
+        ctx->ws_pool = nullptr;
+    }
     std::unique_lock<std::mutex> lk(s->mu);
     while (true) {
         s->cv_work.wait(lk, [&] {
