@@ -1,7 +1,7 @@
 """Parity of the CUDA library (through the C-ABI) with the FP64 oracle on the
 same seeded inputs.  Tolerances: integers bit-exact; FP64 path <= 1e-10
 relative L2 per Stokes component on kept pixels; refined mixed path <= 1e-6
-(BASELINE targets); single operators in FP64 <= 1e-12."""
+(the map accuracy targets of the workloads); single operators in FP64 <= 1e-12."""
 import math
 
 import numpy as np
