@@ -462,7 +462,8 @@ def run_gb300(args, rank, world, local_rank):
             "metric": METRIC, "value": world * nt / (ms_max * 1e-3), "unit": "TOD samples/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 products / f64 accumulation + refinement",
+            "dtype": "f32",
+            "precision": "f32 per-sample products; double-float / f64 accumulation; f64 blocks, CG scalars and refinement",
             "data": "synthetic (seeded spin+precession scan, Gaussian IQU sky, white noise)",
             "config": workload_config(args),
             "matvec": {"samples_per_s": nt / (k_ms * 1e-3), "kernel_ms": k_ms, "call_ms": mv_call_ms,
