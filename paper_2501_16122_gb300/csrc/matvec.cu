@@ -17,6 +17,8 @@
 // flagged samples give 0), apply the banded filter from a shared-memory halo,
 // and write z; the scatter P^T z is the pixel-sorted gather-reduce
 // q_p = sum_{t in p} z_t v_t.
+#include <type_traits>
+
 #include "bm_internal.cuh"
 #include "fft_filter.cuh"
 
@@ -912,6 +914,7 @@ __global__ void __launch_bounds__(256)
 offset_filter_kernel(Src src, OffsetGeom g, const double* __restrict__ white, const double* __restrict__ inv_cnt,
                      T* __restrict__ z) {
     constexpr int U = 8;
+    constexpr bool kF32Src = std::is_same<decltype(src(int64_t(0))), float>::value && std::is_same<T, double>::value;
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < g.nint; j += nwarps) {
@@ -919,17 +922,34 @@ offset_filter_kernel(Src src, OffsetGeom g, const double* __restrict__ white, co
         int64_t a, e;
         offset_interval(g, j, d, a, e);
         double s = 0.0;
-        for (int64_t t0 = a + lane; t0 < e; t0 += 32 * U) {
-            T v[U];
+        if constexpr (kF32Src) {
+            // an FP32 source summed in double-float on the FP32 pipes (the
+            // FP64 pipe runs at 1/64 of their rate); df_add commutes, so the
+            // butterfly leaves the same pair in every lane
+            df32 acc = {0.f, 0.f};
+            for (int64_t t0 = a + lane; t0 < e; t0 += 32 * U) {
+                float v[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) v[u] = t0 + 32 * u < e ? src(t0 + 32 * u) : T(0);
-            T ps = v[0];
+                for (int u = 0; u < U; ++u) v[u] = t0 + 32 * u < e ? src(t0 + 32 * u) : 0.f;
 #pragma unroll
-            for (int u = 1; u < U; ++u) ps += v[u];
-            s += (double)ps;
+                for (int u = 0; u < U; ++u) acc = df_add(acc, v[u]);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc = df_add(acc, df_shfl_xor(acc, o));
+            s = df_to_double(acc);
+        } else {
+            for (int64_t t0 = a + lane; t0 < e; t0 += 32 * U) {
+                T v[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) v[u] = t0 + 32 * u < e ? src(t0 + 32 * u) : T(0);
+                T ps = v[0];
+#pragma unroll
+                for (int u = 1; u < U; ++u) ps += v[u];
+                s += (double)ps;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         const double m = s * (inv_cnt ? inv_cnt[j] : 1.0 / (double)(e - a));
         const T mt = (T)m, w = (T)white[d];
         for (int64_t t0 = a + lane; t0 < e; t0 += 32 * U) {
