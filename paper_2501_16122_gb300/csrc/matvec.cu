@@ -240,6 +240,17 @@ white_matvec_f64_kernel(const int32_t* __restrict__ item_pix, const int64_t* __r
 //   DF = false: FP64 products and sums (trig hi + lo), as the FP64 path needs;
 //   DF = true : double-float products and sums on the FP32 pipes (~48 bits);
 //               the trig pair is (hi, lo) when present, else the exact hi.
+// The gathered value as a double-float pair or an FP64 number: an FP32
+// value, an FP64 value, or a double-float pair stored as float2 (hi, lo).
+__device__ __forceinline__ df32 as_df(float v) { return {v, 0.f}; }
+__device__ __forceinline__ df32 as_df(double v) { return df_from(v); }
+__device__ __forceinline__ df32 as_df(float2 v) { return {v.x, v.y}; }
+__device__ __forceinline__ double as_f64(float v) { return v; }
+__device__ __forceinline__ double as_f64(double v) { return v; }
+__device__ __forceinline__ double as_f64(float2 v) { return (double)v.x + (double)v.y; }
+template <typename G> __device__ __forceinline__ G from_f32(float v) { return (G)v; }
+template <> __device__ __forceinline__ float2 from_f32<float2>(float v) { return make_float2(v, 0.f); }
+
 template <int NC, typename G, bool DF>
 __global__ void __launch_bounds__(kWarps * 32)
 gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ item_beg,
@@ -277,8 +288,7 @@ gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __rest
             int nadd = 0;
             auto add = [&](int64_t si, uint32_t t, G gv, float2 h, float2 l) {
                 df32 val;
-                if (sizeof(G) == 4) val = {(float)gv, 0.f};
-                else val = df_from((double)gv);
+                val = as_df(gv);
                 if (weighted) {
                     if (dt.wsort) {  // a weight per sample
                         w = dt.wsort[si];
@@ -307,7 +317,7 @@ gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __rest
                 for (int u = 0; u < U; ++u) t[u] = perm[b + i + 32 * u];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    gv[u] = gs ? (G)gs[b + i + 32 * u] : g[t[u]];
+                    gv[u] = gs ? from_f32<G>(gs[b + i + 32 * u]) : g[t[u]];
                     h[u] = NC > 1 ? hi[b + i + 32 * u] : make_float2(0.f, 0.f);
                     l[u] = (NC > 1 && lo) ? lo[b + i + 32 * u] : make_float2(0.f, 0.f);
                 }
@@ -319,7 +329,7 @@ gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __rest
                 const uint32_t t = perm[si];
                 const float2 h = NC > 1 ? hi[si] : make_float2(0.f, 0.f);
                 const float2 l = (NC > 1 && lo) ? lo[si] : make_float2(0.f, 0.f);
-                add(si, t, gs ? (G)gs[si] : g[t], h, l);
+                add(si, t, gs ? from_f32<G>(gs[si]) : g[t], h, l);
             }
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
@@ -336,7 +346,7 @@ gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __rest
             uint32_t dend = 0;
             double wd = 0.0;
             auto add = [&](uint32_t t, G gv, int64_t si) {
-                double val = (double)gv;
+                double val = as_f64(gv);
                 if (weighted) {
                     if (dt.w64sort) {  // a weight per sample
                         wd = dt.w64sort[si];
@@ -363,13 +373,13 @@ gather_reduce_kernel(const int32_t* __restrict__ item_pix, const int64_t* __rest
 #pragma unroll
                 for (int u = 0; u < 4; ++u) t[u] = perm[b + i + 32 * u];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) gv[u] = gs ? (G)gs[b + i + 32 * u] : g[t[u]];
+                for (int u = 0; u < 4; ++u) gv[u] = gs ? from_f32<G>(gs[b + i + 32 * u]) : g[t[u]];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) add(t[u], gv[u], b + i + 32 * u);
             }
             for (; i < len; i += 32) {
                 const uint32_t t = perm[b + i];
-                add(t, gs ? (G)gs[b + i] : g[t], b + i);
+                add(t, gs ? from_f32<G>(gs[b + i]) : g[t], b + i);
             }
 #pragma unroll
             for (int c = 0; c < NC; ++c) acc[c] = warp_sum(acc[c]);
@@ -909,10 +919,12 @@ __device__ __forceinline__ void offset_interval(const OffsetGeom& g, int64_t j, 
 // value in every lane (IEEE addition commutes); a fixed order, so the result
 // is deterministic.  The second pass reads the interval again (from L2 for
 // intervals of a few thousand samples) and writes z.
-template <typename T, class Src>
+// Out = float2: z as double-float pairs (hi, lo), computed on the FP32 pipes
+// (the gather-reduce reads them without FP64 conversions).
+template <typename T, class Src, typename Out = T>
 __global__ void __launch_bounds__(256)
 offset_filter_kernel(Src src, OffsetGeom g, const double* __restrict__ white, const double* __restrict__ inv_cnt,
-                     T* __restrict__ z) {
+                     Out* __restrict__ z) {
     constexpr int U = 8;
     constexpr bool kF32Src = std::is_same<decltype(src(int64_t(0))), float>::value && std::is_same<T, double>::value;
     const int lane = threadIdx.x & 31;
@@ -951,14 +963,31 @@ offset_filter_kernel(Src src, OffsetGeom g, const double* __restrict__ white, co
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         }
         const double m = s * (inv_cnt ? inv_cnt[j] : 1.0 / (double)(e - a));
-        const T mt = (T)m, w = (T)white[d];
-        for (int64_t t0 = a + lane; t0 < e; t0 += 32 * U) {
-            T v[U];
+        if constexpr (std::is_same<Out, float2>::value) {
+            using V = decltype(src(int64_t(0)));
+            const df32 md = df_from(m), wd = df_from(white[d]);
+            const df32 nm = {-md.hi, -md.lo};
+            for (int64_t t0 = a + lane; t0 < e; t0 += 32 * U) {
+                V v[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) v[u] = t0 + 32 * u < e ? src(t0 + 32 * u) : T(0);
+                for (int u = 0; u < U; ++u) v[u] = t0 + 32 * u < e ? src(t0 + 32 * u) : V(0);
 #pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (t0 + 32 * u < e) z[t0 + 32 * u] = w * (v[u] - mt);
+                for (int u = 0; u < U; ++u)
+                    if (t0 + 32 * u < e) {
+                        const df32 zz = df_mul(wd, df_add(as_df(v[u]), nm));
+                        z[t0 + 32 * u] = make_float2(zz.hi, zz.lo);
+                    }
+            }
+        } else {
+            const T mt = (T)m, w = (T)white[d];
+            for (int64_t t0 = a + lane; t0 < e; t0 += 32 * U) {
+                T v[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) v[u] = t0 + 32 * u < e ? src(t0 + 32 * u) : T(0);
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (t0 + 32 * u < e) z[t0 + 32 * u] = w * (v[u] - mt);
+            }
         }
     }
 }
@@ -1343,12 +1372,12 @@ static void offset_matvec_mixed(bm_pointing* p, bm_inv_noise* n, bm_precond* pc,
 }
 
 // inv_cnt = NULL: every sample is kept.
-template <typename T, class Src>
-static void run_offset_filter(bm_inv_noise* n, const Src& src, const double* inv_cnt, T* z) {
+template <typename T, class Src, typename Out = T>
+static void run_offset_filter(bm_inv_noise* n, const Src& src, const double* inv_cnt, Out* z) {
     bm_context* ctx = n->ctx;
     if (n->nint == 0) return;
     ScopedTimer timer(ctx, "offset_filter_f64");
-    auto kern = offset_filter_kernel<T, Src>;
+    auto kern = offset_filter_kernel<T, Src, Out>;
     kern<<<resident_grid(ctx, kern, 256, (n->nint + 7) / 8), 256, 0, ctx->stream>>>(src, offset_geom(n),
                                                                                     n->white.get(), inv_cnt, z);
     BM_LAUNCH_CHECK();
@@ -1582,6 +1611,19 @@ void rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dt
                 const double* d = static_cast<const double*>(tod) + r * p->nsamples;
                 gather_reduce<double>(p, kept_items(pc), d, n, p->cs_lo_s.get(), df, br, nullptr, pc);
             }
+        } else if (n->kind == 3 && df) {
+            // the offset template's double-float RHS: z as double-float pairs
+            float2* z2 = workspace_as<float2>(ctx, "z2", p->nsamples);
+            if (dt == BM_F32) {
+                SrcMaskedTod<float> src{p->pix.get(), pc->mask.get(),
+                                        static_cast<const float*>(tod) + r * p->nsamples};
+                run_offset_filter<double, SrcMaskedTod<float>, float2>(n, src, pc->ofs_inv.get(), z2);
+            } else {
+                SrcMaskedTod<double> src{p->pix.get(), pc->mask.get(),
+                                         static_cast<const double*>(tod) + r * p->nsamples};
+                run_offset_filter<double, SrcMaskedTod<double>, float2>(n, src, pc->ofs_inv.get(), z2);
+            }
+            gather_reduce<float2>(p, kept_items(pc), z2, nullptr, p->cs_lo_s.get(), true, br);
         } else {
             double* z64 = workspace_as<double>(ctx, "z64", p->nsamples);
             if (dt == BM_F32) {
