@@ -387,3 +387,30 @@ def test_offset_filter_removes_offsets_from_the_map():
         np.testing.assert_allclose(x[keep, k], sky[keep, k], rtol=0, atol=1e-8 * np.abs(sky[keep, k]).max())
     di = (x[keep, 0] - x[keep, 0].mean()) - (sky[keep, 0] - sky[keep, 0].mean())
     assert np.abs(di).max() < 1e-8 * np.abs(sky[keep, 0]).max()
+
+
+def test_offset_filter_special_cases():
+    # closed forms of W = Nk - Nk F (F^T Nk F)^+ F^T Nk on ragged detectors
+    off = np.array([0, 7, 20, 21, 40])
+    iv = np.array([0.5, 1.0, 2.0, 4.0])
+    rng = np.random.default_rng(61)
+    y = rng.normal(size=40) + 3.0
+    w = iv[gls.sample_detector(off)]
+    # a baseline as long as the longest detector: each detector's mean removed
+    z = gls.OffsetFilterNoise(iv, off, 40).apply(y)
+    ref = np.concatenate([w[a:b] * (y[a:b] - y[a:b].mean()) for a, b in zip(off[:-1], off[1:])])
+    np.testing.assert_allclose(z, ref, rtol=1e-13, atol=1e-13)
+    # a baseline of one sample: every sample is its own offset, W = 0
+    assert np.all(gls.OffsetFilterNoise(iv, off, 1).apply(y) == 0.0)
+    # samples that are not kept neither receive a value nor enter any mean
+    kept = np.ones(40, bool)
+    kept[8:12] = False                                 # detector 1's intervals (baseline 5): [7, 12) keeps 7 only,
+    kept[12:17] = False                                # [12, 17) keeps none
+    n = gls.OffsetFilterNoise(iv, off, 5).with_kept(kept)
+    y2 = y.copy()
+    y2[~kept] = rng.normal(size=(~kept).sum()) * 1e3
+    z1, z2 = n.apply(y), n.apply(y2)
+    assert np.all(z1[~kept] == 0.0)
+    np.testing.assert_array_equal(z1, z2)
+    a, b = 7, 12                                       # the interval [7, 12): kept samples 7 only
+    np.testing.assert_allclose(z1[a:b][kept[a:b]], 0.0, atol=1e-15)
