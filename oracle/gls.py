@@ -62,6 +62,31 @@ def pointing_weights_trig(c, s, ncomp: int) -> np.ndarray:
     raise ValueError("ncomp must be 1, 2 or 3")
 
 
+def hwp_angles(det_offsets, psi_det, nu, phi0) -> np.ndarray:
+    """Polarisation angle of every sample under a rotating half-wave plate
+    (Eq. 2: theta includes the optics; the build's reading of the HWP is
+    theta = psi_d + 2 phi_hwp): sample k of detector d (k counted from the
+    detector's first sample, which is taken at k = 0) has
+        theta = psi_d + 2 phi_hwp(k),   phi_hwp(k) = 2 pi nu k + phi0,
+    nu the plate's turns per sample (f_hwp / f_samp).  2 pi nu k is a multiple
+    of 2 pi plus 2 pi frac(nu k); frac(nu k) is formed exactly from the
+    rational value of nu (a binary FP64 number) with Python integers, so the
+    angle keeps FP64 accuracy however long the detector.  Samples laid out
+    detector by detector; FP64 [nsamples]."""
+    from fractions import Fraction
+    off = np.asarray(det_offsets, np.int64)
+    psi_det = np.asarray(psi_det, np.float64)
+    fr = Fraction(float(nu))
+    num, den = fr.numerator, fr.denominator
+    out = np.empty(int(off[-1]))
+    for d in range(off.size - 1):
+        n = int(off[d + 1] - off[d])
+        # frac(nu k) = ((num k) mod den) / den, exactly, then rounded once
+        turns = np.array([((num * k) % den) / den for k in range(n)], np.float64)
+        out[off[d]:off[d + 1]] = psi_det[d] + 2.0 * (2.0 * np.pi * turns + phi0)
+    return out
+
+
 def hits(pix, npix: int) -> np.ndarray:
     """Number of samples in each pixel (flagged samples, pix = -1, not counted)."""
     pix = np.asarray(pix)

@@ -414,3 +414,58 @@ def test_offset_filter_special_cases():
     np.testing.assert_array_equal(z1, z2)
     a, b = 7, 12                                       # the interval [7, 12): kept samples 7 only
     np.testing.assert_allclose(z1[a:b][kept[a:b]], 0.0, atol=1e-15)
+
+
+# ---------------------------------------------------------------- HWP angles
+def test_hwp_angles_without_rotation_are_the_detector_angles():
+    """nu = 0: every sample of detector d has theta = psi_d + 2 phi0."""
+    off = np.array([0, 7, 20, 21])
+    psi_d = np.array([0.1, 2.0, 3.0])
+    th = gls.hwp_angles(off, psi_d, 0.0, 0.25)
+    for d in range(3):
+        assert np.all(th[off[d]:off[d + 1]] == psi_d[d] + 0.5)
+
+
+def test_hwp_angles_quarter_turn_per_sample():
+    """nu = 1/4 (exact in binary): phi_hwp advances by pi/2 a sample, theta by
+    pi, so theta(k) - theta(0) = pi (k mod 4) and cos 2 theta is constant."""
+    off = np.array([0, 1001])
+    th = gls.hwp_angles(off, [0.3], 0.25, 0.1)
+    k = np.arange(1001)
+    np.testing.assert_allclose(th - th[0], np.pi * (k % 4), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(np.cos(2 * th), np.cos(2 * th[0]), rtol=0, atol=1e-13)
+
+
+def test_hwp_angles_against_the_closed_form_and_the_scan_generator():
+    """nu = 1 Hz / 20 Hz: near the start the unreduced closed form
+    psi_d + 2 (2 pi nu k + phi0) is exact to FP64 rounding (equal angles up
+    to whole turns, so equal cos 2 theta and sin 2 theta), and over a whole
+    detector the seeded scan generator's angles (C, theta reduced with fmod in
+    FP64, a separate implementation) give the same cos 2 theta, sin 2 theta."""
+    import synth
+    e = synth.make_experiment(8, 3, 40_000, 77)
+    nu = e.scan.hwp_hz / e.scan.fsamp
+    th = gls.hwp_angles(e.det_offsets, e.psi_det, nu, e.hwp_phase0)
+    k = np.arange(2000)
+    for d in range(3):
+        naive = e.psi_det[d] + 2.0 * (2.0 * np.pi * nu * k + e.hwp_phase0)
+        for f in (np.cos, np.sin):
+            np.testing.assert_allclose(f(2 * th[d * e.ns + k]), f(2 * naive), rtol=0, atol=1e-11)
+    psi = synth.pointing(e)["psi"]
+    np.testing.assert_allclose(np.cos(2 * th), np.cos(2 * psi), rtol=0, atol=1e-10)
+    np.testing.assert_allclose(np.sin(2 * th), np.sin(2 * psi), rtol=0, atol=1e-10)
+
+
+def test_hwp_angles_stay_exact_far_from_the_start():
+    """The phase is reduced exactly: with nu = 1/20 the angle repeats every 20
+    samples even 2^31 samples in (where nu k ~ 1e8 turns and the unreduced
+    FP64 product has lost ~1e-8 of a turn)."""
+    nu = 1.0 / 20.0
+    from fractions import Fraction
+    k0 = 2 ** 31
+    fr = Fraction(nu)
+    # the oracle's exact reduction at a large k equals its value at k mod 20
+    # up to the (tiny) difference between the binary nu and 1/20
+    assert abs(float((fr * k0) % 1) - float((fr * (k0 % 20)) % 1)) < 1e-6
+    th = gls.hwp_angles(np.array([0, 40]), [0.0], nu, 0.0)
+    np.testing.assert_allclose(th[20:40], th[0:20], rtol=0, atol=1e-12)
