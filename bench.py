@@ -17,8 +17,12 @@ copies of pix/cos/sin/tod and the device->host copy of the map inside the timed
 region.  `--impl reference` times the FP64 CPU oracle on a bounded sample.
 
 Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
-torch.distributed.run (one rank per GPU); ranks run independent replicas of
-the workload (no data-path collective) and the slowest rank's time counts.
+torch.distributed.run (one rank per GPU) the same workload is sharded by
+detector (the paper's data distribution): each rank ingests and solves over
+its own detectors, and the library sums the per-pixel partial blocks, RHS and
+A x over the ranks with an NCCL all-reduce (bm_context_set_allreduce); the
+slowest rank's time counts and `value` is the whole workload's samples per
+second (strong scaling).
 """
 from __future__ import annotations
 
@@ -53,10 +57,12 @@ def parse():
     ap.add_argument("--seed", type=int, default=1001)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-procs", type=int, default=-1,
+                    help="host processes of the multi-core oracle figure (-1: every core, 0: skip)")
     ap.add_argument("--matvec-reps", type=int, default=20)
     ap.add_argument("--profile", action="store_true", help="short run for ncu: no e2e, cpu, clocks")
     ap.add_argument("--workload", default="config1",
-                    choices=["config0", "config1", "config2", "config3", "config4", "offsets"],
+                    choices=["config0", "config1", "config2", "config3", "config4", "offsets", "hwp"],
                     help="config1 (default): nside 256 white-noise solve; config0: small FP64 solve; "
                          "config2: 512-lag Toeplitz noise; config3: 64 right-hand sides batched; "
                          "config4: Poisson request stream through the server; offsets: config2's 1/f TOD "
@@ -64,6 +70,7 @@ def parse():
     ap.add_argument("--horizon", type=float, default=20.0, help="config4: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=20.0, help="config4: mean arrivals per second")
     ap.add_argument("--nrhs", type=int, default=64, help="config3: right-hand sides")
+    ap.add_argument("--no-fp64-solve", action="store_true", help="config2: skip the timed plain FP64 solve")
     ap.add_argument("--rhs-path", choices=["carried", "gather"], default="carried",
                     help="config1: the TOD sorted along with the pointing (carried, default) or "
                          "gathered through the permutation by the solve (gather)")
@@ -171,6 +178,70 @@ def cpu_oracle_run(nside, ndet, ns, seed, tol):
 CPU_SAMPLE = dict(ndet=8, ns=2 ** 19)  # 4.2M samples of the same scan: ~10 s of oracle work
 
 
+def _oracle_slice_worker(k, nside, ndet, ns, seed, ready, start, out):
+    """One host process of the multi-core oracle run: generates its own
+    detectors' samples (untimed), waits for the common start, then computes
+    its partial sums with the oracle's functions: the blocks of Eq. 7, the hit
+    counts and b = P^T N^-1 d of its samples (white noise)."""
+    import synth
+    from oracle import gls
+    e = synth.make_experiment(nside, ndet, ns, seed)
+    pt = synth.pointing(e)
+    c32, s32 = synth.trig32(pt["psi"])
+    d = synth.tod(e, pt["pix"], pt["psi"], synth.sky_map(e.npix, seed), dtype=np.float32,
+                  trig=(c32, s32)).astype(np.float64)
+    ready.put(k)
+    start.wait()
+    t0 = time.perf_counter()
+    pix = pt["pix"].astype(np.int64)
+    v = gls.pointing_weights_trig(c32, s32, 3)
+    w = (1.0 / e.sigma ** 2)[gls.sample_detector(e.det_offsets)]
+    B = gls.block_matrices(pix, v, w, e.npix)
+    h = gls.hits(pix, e.npix)
+    b = gls.apply_PT(pix, v, w * d, e.npix)
+    out.put((k, e.nsamples, B, h, b, t0, time.perf_counter()))
+
+
+def cpu_oracle_multicore(nside, nproc, seed):
+    """The oracle over nproc host processes, split by detector (each process
+    a slice of CPU_SAMPLE's size with detectors of its own): partial blocks,
+    hits and RHS per process, summed in process order (a fixed order), then
+    the mask, the block inverse and the white-noise GLS map x = M b (the PCG's
+    one-iteration solution).  Returns (samples, seconds from the common start
+    to the map)."""
+    import multiprocessing as mp
+    from oracle import gls
+    ctx = mp.get_context("spawn")  # GPU work already ran in this process: no fork
+    ready, start, out = ctx.Queue(), ctx.Event(), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_slice_worker,
+                         args=(k, nside, CPU_SAMPLE["ndet"], CPU_SAMPLE["ns"], seed + 7919 * (k + 1), ready, start,
+                               out))
+             for k in range(nproc)]
+    for pr in procs:
+        pr.start()
+    for _ in procs:  # every process has generated its inputs
+        ready.get(timeout=600)
+    start.set()
+    parts = sorted((out.get(timeout=600) for _ in procs), key=lambda p_: p_[0])
+    for pr in procs:
+        pr.join()
+    t_parts = max(p_[6] for p_ in parts)
+    tc = time.perf_counter()
+    n = sum(p_[1] for p_ in parts)
+    B, h, b = parts[0][2].copy(), parts[0][3].copy(), parts[0][4].copy()
+    for p_ in parts[1:]:  # fixed order: process 0, 1, ...
+        B += p_[2]
+        h += p_[3]
+        b += p_[4]
+    mask = gls.pixel_mask(h, B, 3, 1e3)
+    M = gls.block_inverse(B, mask)
+    b[mask] = 0.0
+    gls.precond_apply(M, b)
+    combine = time.perf_counter() - tc
+    t0 = min(p_[5] for p_ in parts)
+    return n, (t_parts - t0) + combine
+
+
 # Kernel of each timed family, and the DRAM traffic per launch measured by
 # ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the small case of
 # profiles/ scaled to the full launch by the samples processed; None when the
@@ -207,7 +278,7 @@ def run_reference(args, rank):
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "TOD samples/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t / len(steps),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded scan, Gaussian sky, white noise)",
         "config": workload_config(args),
         "cpu_baseline": {"value": v, "unit": "TOD samples/s", "cores": 1, "kind": "oracle", "sample": sample},
@@ -222,7 +293,8 @@ def workload_config(args):
             "nside": args.nside, "npix": 12 * args.nside ** 2, "ndet": args.ndet, "samples_per_det": args.ns,
             "nsamples": args.ndet * args.ns, "solver": "IQU", "noise": "white", "tod_dtype": "f32",
             "trig_dtype": "f32 (precomputed cos 2psi, sin 2psi)", "tol": args.tol, "min_hits": 3, "max_cond": 1e3,
-            "parallelism": f"replicas x{args.gpus}",
+            "parallelism": (f"detector-sharded x{args.gpus} (NCCL all-reduce of per-pixel partial sums)"
+                            if args.gpus > 1 else "1 GPU"),
             "tod_path": ("sorted along with the pointing, read in pixel order by the RHS"
                          if args.rhs_path == "carried" else "gathered through the sort permutation by the RHS"),
             "l2": "inputs (17 GB) larger than L2 (129 MB); no flush needed"}
@@ -246,13 +318,21 @@ def run_gb300(args, rank, world, local_rank):
     t_gen = time.perf_counter()
     e, pix, c32, s32, tod = make_inputs(args, args.seed)
     t_gen = time.perf_counter() - t_gen
-    nt = e.nsamples
+    nt_total = e.nsamples
+    det_offsets, inv_var = e.det_offsets, 1.0 / e.sigma ** 2
+    if world > 1:  # this rank's detectors only
+        d0, d1, det_offsets = L.detector_shard(e.det_offsets, rank, world)
+        s0, s1 = int(e.det_offsets[d0]), int(e.det_offsets[d1])
+        pix, c32, s32, tod = pix[s0:s1], c32[s0:s1], s32[s0:s1], tod[s0:s1]
+        inv_var = inv_var[d0:d1]
+    nt = pix.size
     stream = torch.cuda.current_stream()
     d_pix = torch.from_numpy(pix).cuda()
     d_trig = (torch.from_numpy(c32).cuda(), torch.from_numpy(s32).cuda())
     d_tod = torch.from_numpy(tod).cuda()
-    inv_var = 1.0 / e.sigma ** 2
     ctx = L.bm_context_create(local_rank, stream)
+    if world > 1:  # partial per-pixel sums over the ranks: NCCL all-reduce
+        L.bm_context_set_allreduce(ctx, L.torch_allreduce())
     out = torch.empty(e.npix * 3, dtype=torch.float64, device="cuda")
     infos = []
 
@@ -264,7 +344,7 @@ def run_gb300(args, rank, world, local_rank):
                                               sin2psi=src_trig[1])
         else:
             p = L.bm_pointing_create_trig(ctx, e.npix, src_pix, src_trig[0], src_trig[1], L.BM_SOLVER_IQU)
-        n = L.bm_inv_noise_create_diag(ctx, e.det_offsets, inv_var)
+        n = L.bm_inv_noise_create_diag(ctx, det_offsets, inv_var)
         pc = L.bm_blockdiag_precond_create(p, n, 3, 1e3)
         if tod_ready is not None:  # the TOD upload ran beside the ingest and the preconditioner
             stream.wait_event(tod_ready)
@@ -309,11 +389,12 @@ def run_gb300(args, rank, world, local_rank):
 
     # --- matvec alone (the metric's kernel), x = the solved map
     p = L.bm_pointing_create_trig(ctx, e.npix, d_pix, d_trig[0], d_trig[1], L.BM_SOLVER_IQU)
-    n = L.bm_inv_noise_create_diag(ctx, e.det_offsets, inv_var)
+    n = L.bm_inv_noise_create_diag(ctx, det_offsets, inv_var)
     pc = L.bm_blockdiag_precond_create(p, n, 3, 1e3)
     mask = torch.empty(e.npix, dtype=torch.uint8, device="cuda")
     hits = torch.empty(e.npix, dtype=torch.int32, device="cuda")
-    L.bm_precond_get_mask(pc, mask, hits)
+    L.bm_precond_get_mask(pc, mask, None)
+    L.bm_pointing_get_hits(p, hits)  # this rank's samples (all of them at N = 1)
     kept = mask == 0
     n_kept_samples = int(hits[kept].sum().item())
     n_kept_pix = int(kept.sum().item())
@@ -454,20 +535,31 @@ def run_gb300(args, rank, world, local_rank):
         cpu = {"value": n_s / dt, "unit": "TOD samples/s", "cores": 1, "kind": "oracle",
                "sample": f"{CPU_SAMPLE['ndet']} det x {CPU_SAMPLE['ns']} samples of the same scan "
                          f"(oracle set-up + RHS + PCG, {dt:.1f} s)"}
+        if args.cpu_procs != 0:
+            nproc = args.cpu_procs if args.cpu_procs > 0 else (os.cpu_count() or 1)
+            n_m, dt_m = cpu_oracle_multicore(args.nside, nproc, args.seed)
+            cpu["multi_core"] = {
+                "value": n_m / dt_m, "unit": "TOD samples/s", "cores": nproc, "kind": "oracle",
+                "sample": (f"{nproc} host processes, each {CPU_SAMPLE['ndet']} det x {CPU_SAMPLE['ns']} samples of "
+                           f"the same scan (detectors of its own): the oracle's blocks, hits and RHS per process, "
+                           f"summed in process order, then mask, inverse and x = M b ({dt_m:.1f} s)")}
 
     if rank == 0:
         st_ok = all(s == L.BM_OK for s, _ in infos)
         last = infos[-1][1]
         line = {
-            "metric": METRIC, "value": world * nt / (ms_max * 1e-3), "unit": "TOD samples/s",
+            "metric": METRIC, "value": nt_total / (ms_max * 1e-3), "unit": "TOD samples/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
             "dtype": "f32",
             "precision": "f32 per-sample products; double-float / f64 accumulation; f64 blocks, CG scalars and refinement",
             "data": "synthetic (seeded spin+precession scan, Gaussian IQU sky, white noise)",
             "config": workload_config(args),
-            "matvec": {"samples_per_s": nt / (k_ms * 1e-3), "kernel_ms": k_ms, "call_ms": mv_call_ms,
-                       "kept_samples": n_kept_samples, "hbm_frac": achieved / hbm},
+            "matvec": {"samples_per_s": nt / (k_ms * 1e-3), "kept_samples_per_s": n_kept_samples / (k_ms * 1e-3),
+                       "kernel_ms": k_ms, "call_ms": mv_call_ms, "kept_samples": n_kept_samples,
+                       "hbm_frac": achieved / hbm,
+                       "note": ("this rank's samples; the call includes the all-reduce of A x" if world > 1
+                                else "samples of the step's TOD (kept: in unmasked pixels)")},
             "time_to_map_ms": ms_max - fam.get("ingest", {}).get("ms_per_step", 0.0),
             "solve_only_ms": fp64_path,
             "step_breakdown_ms": {k: v["ms_per_step"] for k, v in fam.items()},
@@ -487,7 +579,7 @@ def run_gb300(args, rank, world, local_rank):
             "input_generation_s": t_gen,
         }
         if e2e:
-            line["e2e"] = {"value": world * nt / (e2e_max * 1e-3), "unit": "TOD samples/s",
+            line["e2e"] = {"value": nt_total / (e2e_max * 1e-3), "unit": "TOD samples/s",
                            "h2d_bytes_per_step": e2e["h2d_bytes_per_step"],
                            "d2h_bytes_per_step": e2e["d2h_bytes_per_step"], "ms_per_step": e2e_max}
         if clocks:

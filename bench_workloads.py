@@ -8,6 +8,9 @@
            sharing one pointing: one batched solve vs one-at-a-time solves.
   config4  Poisson arrivals of requests of mixed size and noise model through
            the serving loop: p50/p99 latency and throughput.
+  hwp      the config-1 scan with its angle rebuilt on the device from the
+           half-wave-plate model (bm_pointing_create_hwp): the whole step and
+           the matvec that reads 4 bytes a sample, beside the stored-trig one.
 
 Each prints one JSON line.  Large TODs are synthesised on the device from the
 seeded pointing (signal gathered from a seeded sky, noise from a seeded torch
@@ -73,14 +76,20 @@ def pointing_on_device(nside, ndet, ns, seed):
     return e, torch.from_numpy(pt["pix"]).cuda(), torch.from_numpy(c32).cuda(), torch.from_numpy(s32).cuda()
 
 
-def fp32_peak_tflops(sm_mhz):
+def fp32_nominal_tflops(sm_mhz):
     # 152 SMs x 128 FP32 lanes x 2 flops per FMA x clock
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def fp64_peak_tflops(sm_mhz):
+def fp64_nominal_tflops(sm_mhz):
     # 1.25 TFLOP/s dense FP64 at the maximum SM clock (2070 MHz), scaled by the clock
     return 1.25 * sm_mhz / 2070.0
+
+
+def measured_fma_tflops(L, ctx):
+    """FP32 and FP64 FMA rates measured on this GPU by the library's own
+    microbenchmark (bm_measure_fma_peak), in TFLOP/s."""
+    return (L.bm_measure_fma_peak(ctx, L.BM_F32) / 1e12, L.bm_measure_fma_peak(ctx, L.BM_F64) / 1e12)
 
 
 def hbm_peak():
@@ -165,6 +174,7 @@ def run_config2(args, noise="toeplitz"):
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
     ctx = L.bm_context_create(0)
+    fp32_tf, fp64_tf = measured_fma_tflops(L, ctx)
     out = torch.zeros(e.npix * 3, dtype=torch.float64, device="cuda")
     inv_var = 1 / e.sigma ** 2
     infos = []
@@ -210,7 +220,10 @@ def run_config2(args, noise="toeplitz"):
         tot, cnt = L.bm_context_kernel_time(ctx, name)
         if cnt:
             fam[name] = {"ms_per_launch": tot / cnt, "launches_per_step": cnt / args.steps}
-    # one FP64 matvec, to size the plain FP64 solve
+    # one FP64 matvec, and the solve alone (RHS + PCG on handles already
+    # built) in both precisions: the plain FP64 solve against the refined
+    # mixed-precision one, to the same tolerance
+    L.bm_context_set_timing(ctx, False)
     h = make()
     x = torch.nan_to_num(out)
     q = torch.empty_like(x)
@@ -220,6 +233,27 @@ def run_config2(args, noise="toeplitz"):
     L.bm_matvec(h[0], h[1], h[2], x, q, L.BM_PREC_FP64)
     torch.cuda.synchronize()
     fp64_mv_ms = (time.perf_counter() - t1) * 1000
+    solve_only = {}
+    if not args.no_fp64_solve:
+        for name, prec in (("mixed", L.BM_PREC_MIXED), ("fp64", L.BM_PREC_FP64)):
+            o = torch.zeros_like(out)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            st_s, inf_s = L.bm_pcg_solve(h[0], h[1], h[2], d_tod, 1, o, tol, 3000, prec, raise_on_error=False)
+            torch.cuda.synchronize()
+            solve_only[name] = {"ms": (time.perf_counter() - t1) * 1000, "status": st_s,
+                                "iterations": inf_s[0]["iterations"],
+                                "outer_iterations": inf_s[0]["outer_iterations"],
+                                "rel_residual": inf_s[0]["rel_residual"]}
+            if name == "mixed":
+                o_mixed = o
+            else:  # the two maps agree on observed pixels
+                m = torch.isfinite(o_mixed) & torch.isfinite(o)
+                solve_only["mixed_vs_fp64_rel_l2"] = float(torch.linalg.norm(o_mixed[m] - o[m]) /
+                                                           torch.linalg.norm(o[m]))
+            del o
+        if "fp64" in solve_only:
+            solve_only["fp64_over_mixed"] = solve_only["fp64"]["ms"] / solve_only["mixed"]["ms"]
     free(h)
     L.bm_context_set_timing(ctx, False)
     L.bm_context_destroy(ctx)
@@ -260,10 +294,10 @@ def run_config2(args, noise="toeplitz"):
     # (the refinement operator's double-float transform is counted in FP64
     #  flops against the FP32 pipes' rate / 20, about the cost of one
     #  double-float multiply-add)
-    for name, N, zb, peak, unit in (("toeplitz_f32", fft_size(nlags, chunk, 8192), 4, fp32_peak_tflops(sm), "FP32"),
-                                    ("toeplitz_refine", fft_size(nlags, chunk, 4096), 8, fp32_peak_tflops(sm) / 20,
+    for name, N, zb, peak, unit in (("toeplitz_f32", fft_size(nlags, chunk, 8192), 4, fp32_tf, "FP32"),
+                                    ("toeplitz_refine", fft_size(nlags, chunk, 4096), 8, fp32_tf / 20,
                                      "FP32 double-float"),
-                                    ("toeplitz_f64", fft_size(nlags, chunk, 4096), 8, fp64_peak_tflops(sm), "FP64")):
+                                    ("toeplitz_f64", fft_size(nlags, chunk, 4096), 8, fp64_tf, "FP64")):
         ms_l = fam.get(name, {}).get("ms_per_launch")
         if not N or not ms_l:
             continue
@@ -288,12 +322,14 @@ def run_config2(args, noise="toeplitz"):
         "step_breakdown": fam,
         "fft_filter": fam_fft,
         "fp64_matvec_ms": fp64_mv_ms,
-        "plain_fp64_solve_estimate_ms": fp64_mv_ms * max(info["iterations"], 1),
+        "solve_only_ms": solve_only,
+        "fma_peaks_tflops": {"fp32_measured": fp32_tf, "fp64_measured": fp64_tf,
+                             "fp32_nominal": fp32_nominal_tflops(sm), "fp64_nominal": fp64_nominal_tflops(sm)},
         "roofline": {"bound": "alu", "kernel": f"toeplitz_fft_kernel ({dom}, {d.get('pipe')} pipe)",
                      "achieved": d.get("tflops"), "peak": d.get("peak_tflops"), "unit": "TFLOP/s",
                      "frac": d.get("flop_frac"), "traffic": None,
-                     "peak_basis": ("FP32: 152 SM x 128 lanes x 2 flop x SM clock; FP64: 1.25 TFLOP/s nominal "
-                                    f"x SM clock / 2070 MHz; SM clock {sm:.0f} MHz (median under load)")},
+                     "peak_basis": ("measured FMA rate of this GPU (bm_measure_fma_peak); the double-float "
+                                    "transform against the FP32 rate / 20")},
         "clocks": clocks, "input_generation_s": t_gen,
     }
     print(json.dumps(line), flush=True)
@@ -572,10 +608,122 @@ def run_config4(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ hwp
+def run_hwp(args):
+    """Config 1's scan and white noise with the angle of every sample rebuilt
+    from the half-wave-plate model theta = psi_d + 2 (2 pi nu k + phi0),
+    nu = 1 Hz / 20 Hz (the scan generator's own model): one step is the
+    ingest (angles from the model), the preconditioner, the RHS and the mixed
+    solve.  The matvec alone is timed for this pointing (it reads the sorted
+    time index, 4 B a sample, and rebuilds the angle) and for the stored-trig
+    pointing of the same samples (8 B a sample of weighted trig)."""
+    import torch
+    L = _L()
+    nside, ndet, ns = args.nside, args.ndet, args.ns
+    tol = args.tol
+    t_gen = time.perf_counter()
+    e, d_pix, d_c, d_s = pointing_on_device(nside, ndet, ns, args.seed)
+    sky = torch.from_numpy(synth.sky_map(e.npix, args.seed)).cuda()
+    d_tod = torch.empty(e.nsamples, dtype=torch.float32, device="cuda")
+    device_signal(d_pix, d_c, d_s, sky, d_tod)
+    gen = torch.Generator(device="cuda").manual_seed(args.seed)
+    device_white(d_tod, e.sigma, ns, gen)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    nu, phi0 = e.scan.hwp_hz / e.scan.fsamp, e.hwp_phase0
+    ctx = L.bm_context_create(0)
+    out = torch.zeros(e.npix * 3, dtype=torch.float64, device="cuda")
+    inv_var = 1 / e.sigma ** 2
+    infos = []
+
+    def step():
+        p = L.bm_pointing_create_hwp(ctx, e.npix, d_pix, e.det_offsets, e.psi_det, nu, phi0, 3)
+        n = L.bm_inv_noise_create_diag(ctx, e.det_offsets, inv_var)
+        pc = L.bm_blockdiag_precond_create(p, n, 3, 1e3)
+        st, info = L.bm_pcg_solve(p, n, pc, d_tod, 1, out, tol, 200, L.BM_PREC_MIXED)
+        infos.append((st, info[0]))
+        L.bm_precond_destroy(pc)
+        L.bm_inv_noise_destroy(n)
+        L.bm_pointing_destroy(p)
+
+    for _ in range(args.warmup):
+        step()
+    sampler = ClockSampler(0)
+    sampler.start()
+    L.bm_context_set_timing(ctx, True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1000 / args.steps
+    clocks = sampler.stop()
+    fam = {}
+    for name in ("ingest", "ingest_validate", "ingest_hist", "ingest_scatter", "blocks", "rhs",
+                 "matvec_white_hwp"):
+        tot, cnt = L.bm_context_kernel_time(ctx, name)
+        if cnt:
+            fam[name] = {"ms_per_launch": tot / cnt, "launches_per_step": cnt / args.steps}
+    # the matvec alone: this pointing against the stored-trig one
+    x = torch.nan_to_num(out)
+    q = torch.empty_like(x)
+    mv = {}
+    for name in ("hwp", "stored"):
+        if name == "hwp":
+            p = L.bm_pointing_create_hwp(ctx, e.npix, d_pix, e.det_offsets, e.psi_det, nu, phi0, 3)
+        else:
+            p = L.bm_pointing_create_trig(ctx, e.npix, d_pix, d_c, d_s, 3)
+        n = L.bm_inv_noise_create_diag(ctx, e.det_offsets, inv_var)
+        pc = L.bm_blockdiag_precond_create(p, n, 3, 1e3)
+        hits = torch.empty(e.npix, dtype=torch.int32, device="cuda")
+        mask = torch.empty(e.npix, dtype=torch.uint8, device="cuda")
+        L.bm_precond_get_mask(pc, mask, hits)
+        kept = mask == 0
+        n_kept_s, n_kept_p = int(hits[kept].sum().item()), int(kept.sum().item())
+        for _ in range(3):
+            L.bm_matvec(p, n, pc, x, q, L.BM_PREC_MIXED)
+        fam_name = "matvec_white_hwp" if name == "hwp" else "matvec_white_f32"
+        L.bm_context_kernel_time(ctx, fam_name)  # reset
+        for _ in range(args.matvec_reps):
+            L.bm_matvec(p, n, pc, x, q, L.BM_PREC_MIXED)
+        tot, cnt = L.bm_context_kernel_time(ctx, fam_name)
+        k_ms = tot / max(cnt, 1)
+        bps = 4 if name == "hwp" else 8  # sorted time index | weighted trig pair
+        nitems = n_kept_p + n_kept_s // 4096
+        alg = bps * n_kept_s + 12 * n_kept_p + 24 * nitems
+        gbs = alg / (k_ms * 1e-3) / 1e9
+        mv[name] = {"kernel_ms": k_ms, "kept_samples_per_s": n_kept_s / (k_ms * 1e-3),
+                    "bytes_per_kept_sample": bps, "algorithmic_bytes": alg, "achieved_gbs": gbs,
+                    "hbm_frac": gbs / hbm_peak()}
+        L.bm_precond_destroy(pc)
+        L.bm_inv_noise_destroy(n)
+        L.bm_pointing_destroy(p)
+    L.bm_context_set_timing(ctx, False)
+    L.bm_context_destroy(ctx)
+    st, info = infos[-1]
+    h = mv["hwp"]
+    line = {
+        "workload": "hwp", "metric": METRIC, "value": e.nsamples / (ms * 1e-3), "unit": "TOD samples/s",
+        "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+        "config": {"workload": f"GLS map-making, nside {nside}, {ndet} det x {ns} samples, white noise, IQU, "
+                               f"angle rebuilt from the half-wave-plate model (nu = {nu:g} turns a sample), "
+                               f"mixed precision PCG to {tol:g}", "nsamples": e.nsamples},
+        "solve": {"status": st, **info},
+        "step_breakdown": fam,
+        "matvec": mv,
+        "roofline": {"bound": "hbm", "kernel": "white_matvec_hwp_kernel (sorted time index: 4 B a kept sample)",
+                     "achieved": h["achieved_gbs"], "peak": hbm_peak(), "unit": "GB/s", "frac": h["hbm_frac"],
+                     "traffic": None},
+        "clocks": clocks, "input_generation_s": t_gen,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run(args, rank, world, local_rank):
     if rank != 0:
         return
     if args.workload == "offsets":
         run_config2(args, noise="offsets")
         return
-    {"config0": run_config0, "config2": run_config2, "config3": run_config3, "config4": run_config4}[args.workload](args)
+    {"config0": run_config0, "config2": run_config2, "config3": run_config3, "config4": run_config4,
+     "hwp": run_hwp}[args.workload](args)

@@ -98,6 +98,36 @@ const char* bm_version(void);
 bm_status bm_context_create(int device, void* cuda_stream, bm_context** out);
 void bm_context_destroy(bm_context* ctx);
 
+/* Detector-sharded solve (paper Sec. III-A item 1: every process owns a
+ * subset of the samples and its own operator instances; Sec. III-B: the
+ * pointing operator's transpose sums its partial map over the processes).
+ * A reduction callback: sum the FP64 array buf (device memory of the
+ * context's GPU, count values) over every rank, in place, so that every rank
+ * holds the same bits; return BM_OK, or another status to fail the calling
+ * entry point with it.  For example ncclAllReduce followed by a stream
+ * synchronize, or a copy to the host, an MPI or gloo allreduce and a copy
+ * back.  The library calls it from the calling thread after synchronising the
+ * context stream, and uses buf again only after it returns. */
+typedef bm_status (*bm_allreduce_fn)(double* buf, int64_t count, void* user);
+/* Make ctx one rank of a detector-sharded solve (fn = NULL: unsharded again).
+ * Every pointing and noise handle built on it then holds this rank's
+ * samples only (its own detectors, with det_offsets of its own layout), and
+ * the library sums over the ranks, through fn, exactly the per-pixel
+ * quantities that need it: the hit counts and blocks of
+ * bm_blockdiag_precond_create (before the mask, the condition numbers and
+ * the inverse, which every rank then computes from the same sums), the
+ * right-hand side b of bm_rhs / bm_pcg_solve, A x of bm_matvec and of every
+ * PCG iteration, and P^T y of bm_pointing_apply_transpose.  Everything else
+ * (CG vectors and scalars, map) is replicated: every rank computes the same
+ * values.  All ranks must therefore make the same sequence of these calls
+ * with the same npix, solver, min_hits, max_cond, tol and maxiter; a Toeplitz
+ * chunk or an offset interval never spans two ranks, since both stay within
+ * a detector.  bm_matvec_white_static and bm_pointing_get_hits return this
+ * rank's partial values (no reduction); bm_precond_get_mask returns the hit
+ * counts summed over the ranks.  Several right-hand sides of a sharded solve
+ * are solved one after another. */
+bm_status bm_context_set_allreduce(bm_context* ctx, bm_allreduce_fn fn, void* user);
+
 /* Kernel timing: when enabled, the library brackets its main kernels with
  * CUDA events on the context stream and accumulates per-kernel device time.
  * bm_context_kernel_time returns the accumulated milliseconds and launch
@@ -109,6 +139,14 @@ bm_status bm_context_kernel_time(bm_context* ctx, const char* name, double* tota
 /* Number of CUDA kernels the library has launched in this process so far
  * (all contexts and threads). */
 int64_t bm_kernel_launches(void);
+
+/* Measured FP32 (dtype BM_F32) or FP64 (BM_F64) fused multiply-add rate of
+ * the context's GPU in flop/s (2 per FMA): independent FMA chains on every
+ * SM, timed with CUDA events on the context stream (best of three after a
+ * warm-up, a few ms each).  The denominator of the rooflines of the
+ * arithmetic-bound kernels.  A measurement helper with no counterpart in the
+ * paper. */
+bm_status bm_measure_fma_peak(bm_context* ctx, bm_dtype dtype, double* flops_per_s);
 
 /* ------------------------------------------------------------- pixelisation */
 
@@ -162,6 +200,31 @@ bm_status bm_pointing_create_with_tod(bm_context* ctx, int64_t npix, int64_t nsa
                                       const void* psi, bm_dtype psi_dtype, const float* cos2psi,
                                       const float* sin2psi, const float* tod, bm_solver_type solver,
                                       bm_pointing** out);
+/* Pointing whose polarisation angle is rebuilt on the device from a rotating
+ * half-wave plate instead of being read per sample (Eq. 2: the angle theta
+ * includes the optics).  Sample k of detector d (k counted from the
+ * detector's first sample, samples laid out detector by detector) has
+ *     theta = psi_det[d] + 2 phi_hwp(k),
+ *     phi_hwp(k) = 2 pi hwp_turns_per_sample k + hwp_phase0,
+ * hwp_turns_per_sample = f_hwp / f_samp (taken modulo 1 and to 2^-64 of a
+ * turn: exact for every FP64 value of at least 2^-11), hwp_phase0 in radians.
+ * The phase is reduced exactly in 64-bit fixed point, so the angle keeps
+ * FP64 accuracy however long the detector.  pix as for bm_pointing_create
+ * (device or page-locked host int32 [nsamples]); det_offsets host int64
+ * [ndet + 1] (det_offsets[0] = 0, increasing, det_offsets[ndet] =
+ * nsamples); psi_det host FP64 [ndet].  The handle keeps what
+ * bm_pointing_create keeps for the FP64 angles of this model (the FP64
+ * operator, blocks and right-hand sides read them), and the mixed-precision
+ * white-noise matvec with a per-detector N^-1 rebuilds (cos 2 theta,
+ * sin 2 theta) in FP32 from each pixel-sorted sample's time index (4 bytes a
+ * sample) instead of streaming a stored weighted pair (8 bytes a sample).
+ * Errors as bm_pointing_create, and BM_ERR_INVALID for bad det_offsets or a
+ * non-finite angle or rate.  This entry point has no counterpart in the
+ * paper. */
+bm_status bm_pointing_create_hwp(bm_context* ctx, int64_t npix, int64_t nsamples, const int32_t* pix,
+                                 int32_t ndet, const int64_t* det_offsets, const double* psi_det,
+                                 double hwp_turns_per_sample, double hwp_phase0, bm_solver_type solver,
+                                 bm_pointing** out);
 void bm_pointing_destroy(bm_pointing* p);
 /* hits device int32 [npix]: samples per pixel (flagged samples excluded). */
 bm_status bm_pointing_get_hits(const bm_pointing* p, int32_t* hits);

@@ -95,6 +95,7 @@ _SIGS = {
     "bm_ang2pix_ring": ([_P, _i64, _i64, _P, _P, _P], ctypes.c_int),
     "bm_pointing_create": ([_P, _i64, _i64, _P, _P, ctypes.c_int, ctypes.c_int, _PP], ctypes.c_int),
     "bm_pointing_create_trig": ([_P, _i64, _i64, _P, _P, _P, ctypes.c_int, _PP], ctypes.c_int),
+    "bm_pointing_create_hwp": ([_P, _i64, _i64, _P, _i32, _P, _P, _f64, _f64, ctypes.c_int, _PP], ctypes.c_int),
     "bm_pointing_create_with_tod": ([_P, _i64, _i64, _P, _P, ctypes.c_int, _P, _P, _P, ctypes.c_int, _PP],
                                     ctypes.c_int),
     "bm_pointing_destroy": ([_P], None),
@@ -115,6 +116,8 @@ _SIGS = {
     "bm_rhs": ([_P, _P, _P, _P, ctypes.c_int, _i32, _P], ctypes.c_int),
     "bm_matvec": ([_P, _P, _P, _P, _P, ctypes.c_int], ctypes.c_int),
     "bm_matvec_white_static": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "bm_measure_fma_peak": ([_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "bm_context_set_allreduce": ([_P, _P, _P], ctypes.c_int),
     "bm_pcg_solve": ([_P, _P, _P, _P, ctypes.c_int, _i32, _P, _f64, _i32, ctypes.c_int,
                       ctypes.POINTER(bm_solve_info)], ctypes.c_int),
     "bm_serve_create": ([_P, ctypes.c_size_t, _i32, _PP], ctypes.c_int),
@@ -135,6 +138,7 @@ def header_functions() -> list[str]:
     with open(HEADER) as f:
         text = f.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"typedef[^;]*;", "", text)  # function-pointer types are not functions
     return sorted(set(re.findall(r"\b(bm_[a-z0-9_]+)\s*\(", text)))
 
 
@@ -211,7 +215,67 @@ def bm_context_create(device: int = 0, stream=None):
 
 
 def bm_context_destroy(ctx):
+    _REDUCERS.pop(ctx.value, None)
     lib.bm_context_destroy(ctx)
+
+
+# bm_allreduce_fn: bm_status (*)(double* buf, int64_t count, void* user)
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p)
+_REDUCERS = {}  # context -> the ctypes callback object (kept alive while set)
+
+
+def bm_context_set_allreduce(ctx, fn):
+    """Make ctx one rank of a detector-sharded solve: fn(ptr, count) sums the
+    FP64 device array at ptr over every rank in place and returns a bm_status
+    (0 = BM_OK); None makes the context unsharded again."""
+    if fn is None:
+        _check(lib.bm_context_set_allreduce(ctx, None, None), "bm_context_set_allreduce")
+        _REDUCERS.pop(ctx.value, None)
+        return
+
+    def call(ptr, count, _user):
+        try:
+            return int(fn(ptr, count) or 0)
+        except Exception as exc:  # no exception may cross the C-ABI
+            import sys
+            print(f"allreduce callback failed: {exc!r}", file=sys.stderr)
+            return BM_ERR_CUDA
+
+    cb = ALLREDUCE_FN(call)
+    _check(lib.bm_context_set_allreduce(ctx, ctypes.cast(cb, ctypes.c_void_p), None), "bm_context_set_allreduce")
+    _REDUCERS[ctx.value] = cb
+
+
+class _DeviceArray:
+    """A view of count FP64 values at a device address, for torch.as_tensor."""
+
+    def __init__(self, ptr, count):
+        self.__cuda_array_interface__ = {"shape": (int(count),), "typestr": "<f8", "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+def torch_allreduce(group=None):
+    """A reduction for bm_context_set_allreduce over a torch.distributed
+    process group: NCCL sums the device array in place; another backend
+    (gloo) sums a host copy, which is copied back."""
+    import torch
+    import torch.distributed as dist
+
+    def reduce(ptr, count):
+        t = torch.as_tensor(_DeviceArray(ptr, count), device="cuda")
+        if dist.get_backend(group) == "nccl":
+            dist.all_reduce(t, group=group)
+        else:
+            h = t.cpu()
+            dist.all_reduce(h, group=group)
+            t.copy_(h)
+        torch.cuda.current_stream().synchronize()
+        return BM_OK
+
+    return reduce
+
+
+from .shard import detector_shard  # noqa: E402,F401  (host-side partition of a sharded solve)
 
 
 def bm_context_set_timing(ctx, enable: bool):
@@ -253,6 +317,22 @@ def bm_pointing_create_trig(ctx, npix: int, pix, cos2psi, sin2psi, solver: int =
     _check(lib.bm_pointing_create_trig(ctx, int(npix), pix.numel(), _in(pix, torch.int32, "pix"),
                                        _in(cos2psi, torch.float32, "cos2psi"), _in(sin2psi, torch.float32, "sin2psi"),
                                        int(solver), ctypes.byref(out)), "bm_pointing_create_trig")
+    return out
+
+
+def bm_pointing_create_hwp(ctx, npix: int, pix, det_offsets, psi_det, hwp_turns_per_sample: float,
+                           hwp_phase0: float, solver: int = BM_SOLVER_IQU):
+    """Pointing whose angle follows a rotating half-wave plate: sample k of
+    detector d has theta = psi_det[d] + 2 (2 pi hwp_turns_per_sample k +
+    hwp_phase0).  pix: int32 device or pinned host tensor; det_offsets and
+    psi_det: host arrays."""
+    import torch
+    off, offp = _host(det_offsets, np.int64)
+    pd, pdp = _host(psi_det, np.float64)
+    out = ctypes.c_void_p()
+    _check(lib.bm_pointing_create_hwp(ctx, int(npix), pix.numel(), _in(pix, torch.int32, "pix"), off.size - 1, offp,
+                                      pdp, float(hwp_turns_per_sample), float(hwp_phase0), int(solver),
+                                      ctypes.byref(out)), "bm_pointing_create_hwp")
     return out
 
 
@@ -391,6 +471,13 @@ def bm_matvec_white_static(p, n, pc, x, q):
     import torch
     _check(lib.bm_matvec_white_static(p, n, pc, _dev(x, torch.float64, "x"), _dev(q, torch.float64, "q")),
            "bm_matvec_white_static")
+
+
+def bm_measure_fma_peak(ctx, dtype: int) -> float:
+    """Measured FMA rate of the device in flop/s: dtype BM_F32 or BM_F64."""
+    v = ctypes.c_double()
+    _check(lib.bm_measure_fma_peak(ctx, int(dtype), ctypes.byref(v)), "bm_measure_fma_peak")
+    return v.value
 
 
 def bm_pcg_solve(p, n, pc, tod, nrhs: int, map_out, tol: float, maxiter: int, prec: int = BM_PREC_FP64,

@@ -147,7 +147,30 @@ struct bm_context {
     // ordered against `stream` with side_ev.
     cudaStream_t side = nullptr;
     cudaEvent_t side_ev = nullptr;
+    // Device address of the allocation-free matvec's static scratch array on
+    // this context's device (looked up when the context is created).
+    double* static_scratch = nullptr;
+    // Detector-sharded solve (bm_context_set_allreduce): the caller's sum of
+    // per-pixel partial results over the ranks; NULL on an unsharded context.
+    bm_allreduce_fn allreduce = nullptr;
+    void* allreduce_user = nullptr;
 };
+
+namespace bm {
+// The angle model of a half-wave-plate pointing (bm_pointing_create_hwp): the
+// angle 2 theta of sample k of detector d, in turns, is
+// turn0[d] + 4 frac(nu k) (mod 1), all as 64-bit fixed-point fractions of a
+// turn, so the phase is reduced exactly.
+struct HwpModel {
+    const uint32_t* off = nullptr;            // [ndet + 1] sample offsets
+    const unsigned long long* turn0 = nullptr;  // [ndet] (2 psi_d + 4 phi0) / (2 pi) mod 1
+    unsigned long long nu = 0;                // turns per sample mod 1
+    int ndet = 0;
+    uint32_t ns = 0;                          // samples per detector when all are equal, else 0
+    float inv_ns = 0.f;
+    const double2* tab64 = nullptr;           // [kHwpTab] (cos, sin)(2 pi j / kHwpTab) in FP64
+};
+}  // namespace bm
 
 struct bm_pointing {
     bm_context* ctx = nullptr;
@@ -162,6 +185,13 @@ struct bm_pointing {
     bm::DevBuf<float2> cs_hi_s;    // [nvalid] trig in pixel-sorted order
     bm::DevBuf<float2> cs_lo_s;
     bm::DevBuf<float> tod_s;       // [nvalid] a TOD sorted along with the samples, or empty
+    // Half-wave-plate angle model (bm_pointing_create_hwp), else hwp = false.
+    bool hwp = false;
+    bm::HwpModel hwp_model;                 // device pointers into the buffers below
+    bm::DevBuf<uint32_t> hwp_off;           // [ndet + 1]
+    bm::DevBuf<unsigned long long> hwp_turn0;  // [ndet]
+    bm::DevBuf<float2> hwp_tab;             // [kHwpTab] (cos, sin)(2 pi j / kHwpTab) in FP32
+    bm::DevBuf<double2> hwp_tab64;          // [kHwpTab] the same in FP64
 };
 
 struct bm_inv_noise {
@@ -220,6 +250,7 @@ struct bm_precond {
     bm::DevBuf<double> Minv;       // [npix][ncomp*ncomp]
     bm::DevBuf<double> cond;       // [npix]
     bm::DevBuf<uint8_t> mask;      // [npix]
+    bm::DevBuf<int32_t> hits_global;  // [npix] hit counts over all ranks (sharded context), else empty
     // Work items: pieces (<= item_max samples) of kept pixels' sorted segments.
     int64_t nitems = 0;
     bm::DevBuf<int32_t> item_pix;  // [nitems]
@@ -236,11 +267,18 @@ struct bm_precond {
     bm::DevBuf<float2> ws_df;      // [nvalid] double-float
     bm::DevBuf<float> ws_sqrt;     // [nvalid] sqrt(w) in FP32
     bm::DevBuf<double> ws64;       // [nvalid] FP64
-    // Toeplitz noise, inner operator's transpose by time chunks: per pixel,
-    // the start of its samples in each chunk (built on first use; pt_nch = 0
-    // not built yet, -1 not used)
+    // Toeplitz noise, inner operator's transpose by time chunks (built on
+    // first use; pt_nch = 0 not built yet, -1 not used): the kept samples'
+    // time index and trig pair in (time chunk, pixel, time) order, and the
+    // segments of that order (one per chunk and pixel with samples there),
+    // chunk by chunk.
     int pt_nch = 0;
-    bm::DevBuf<int32_t> pt_sub;    // [pt_nch + 1][npix]
+    bm::DevBuf<uint32_t> cm_t;     // [kept samples] time index
+    bm::DevBuf<float2> cm_cs;      // [kept samples] trig pair (FP32 hi)
+    bm::DevBuf<int32_t> seg_pix;   // [segments] pixel
+    bm::DevBuf<uint32_t> seg_beg;  // [segments] first position in cm_t / cm_cs
+    bm::DevBuf<int32_t> seg_len;   // [segments] samples
+    std::vector<int64_t> cseg;     // [pt_nch + 1] first segment of each chunk (host)
     // Offset filter: 1 / (the kept samples of each interval), 0 where none;
     // the interval of every sample in pixel-sorted order.
     bm::DevBuf<double> ofs_inv;    // [nint]
@@ -298,9 +336,19 @@ struct ScopedTimer {
 };
 void resolve_timers(bm_context* ctx);
 
+// Sum of a device FP64 array over the ranks of a sharded context (in place;
+// nothing on an unsharded one): synchronises the context stream, then calls
+// the caller's reduction, which returns once buf holds the sum.
+void shard_reduce(bm_context* ctx, double* buf, int64_t count);
+
+// Device address of the static scratch array of bm_matvec_white_static on
+// the current device, with the code of the kernels that use it loaded.
+double* static_scratch_setup();
+
 // Launch wrappers implemented in the .cu files.
 void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dtype, const float* cos2psi,
-            const float* sin2psi, const float* tod = nullptr, bool tod_on_host = false);
+            const float* sin2psi, const float* tod = nullptr, bool tod_on_host = false,
+            const HwpModel* hwp = nullptr);
 void build_precond(bm_precond* pc);
 void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, double* q,
             bm_precision prec, int64_t nrhs);
@@ -416,6 +464,56 @@ __device__ __forceinline__ int det_of(const uint32_t* off, int ndet, uint32_t ns
         return (int)q;
     }
     return find_det32(off, ndet, t);
+}
+
+// Angle 2 theta of sample t (time index) of a half-wave-plate pointing, in
+// turns as a 64-bit fraction: turn0[d] + 4 frac(nu k), k = t - off[d].
+__device__ __forceinline__ unsigned long long hwp_turns(const HwpModel& m, int d, uint32_t t) {
+    const uint32_t k = t - (m.ns ? (uint32_t)d * m.ns : m.off[d]);
+    return m.turn0[d] + ((m.nu * (unsigned long long)k) << 2);
+}
+// The top 32 bits of the turn fraction of sample k of a detector whose
+// turn0 has top bits turn0_hi: turn0 + 4 frac(nu k), with frac(nu k) the
+// exact 64-bit product nu k mod 2^64; the carry from the dropped low bits
+// (at most one unit of 2^-32 of a turn) is left out.
+__device__ __forceinline__ uint32_t hwp_turns32(unsigned long long nu, uint32_t turn0_hi, uint32_t k) {
+    const uint32_t nlo = (uint32_t)nu, nhi = (uint32_t)(nu >> 32);
+    const uint32_t plo = nlo * k;
+    const uint32_t phi = __umulhi(nlo, k) + nhi * k;
+    return turn0_hi + ((phi << 2) | (plo >> 30));
+}
+// (cos, sin) of 2 pi a for a turn fraction whose top 32 bits are a32, in
+// FP32: the table entry of the top kHwpTabBits bits rotated by the remainder
+// delta (< 2 pi / kHwpTab), cos delta = 1 - delta^2/2, sin delta =
+// delta (1 - delta^2/6) (truncation errors below 1e-10); bits under 2^-32 of
+// a turn are dropped.  Absolute error about 1.5e-7.
+constexpr int kHwpTabBits = 10;
+constexpr int kHwpTab = 1 << kHwpTabBits;
+__device__ __forceinline__ float2 hwp_trig32(uint32_t a32, const float2* tab) {
+    const float2 cs = tab[a32 >> (32 - kHwpTabBits)];
+    const float dl = (float)(a32 & ((1u << (32 - kHwpTabBits)) - 1u)) * 1.4629180792671596e-9f;  // 2 pi / 2^32
+    const float d2 = dl * dl;
+    const float cd = fmaf(-0.5f, d2, 1.0f);
+    const float sd = dl * fmaf(-0.16666667f, d2, 1.0f);
+    return make_float2(fmaf(cs.x, cd, -cs.y * sd), fmaf(cs.y, cd, cs.x * sd));
+}
+// (cos, sin) of 2 pi a for a 64-bit turn fraction a in FP64: the table entry
+// of the top kHwpTabBits bits rotated by the remainder delta (< 2 pi /
+// kHwpTab = 0.0062), cos delta = 1 - delta^2/2 + delta^4/24, sin delta =
+// delta - delta^3/6 + delta^5/120 (truncation errors below 8e-17).
+__device__ __forceinline__ void hwp_trig64(unsigned long long a, const double2* tab, double& c, double& s) {
+    const double2 cs = tab[a >> (64 - kHwpTabBits)];
+    const double dl = (double)(a & ((1ull << (64 - kHwpTabBits)) - 1ull)) * 3.4061215800865545e-19;  // 2 pi / 2^64
+    const double d2 = dl * dl;
+    const double cd = fma(fma(d2, 1.0 / 24.0, -0.5), d2, 1.0);
+    const double sd = dl * fma(fma(d2, 1.0 / 120.0, -1.0 / 6.0), d2, 1.0);
+    c = fma(cs.x, cd, -cs.y * sd);
+    s = fma(cs.y, cd, cs.x * sd);
+}
+// (cos, sin) of 2 pi a for a 64-bit turn fraction a, in FP32 (hwp_trig32 of
+// its top 32 bits).
+__device__ __forceinline__ float2 hwp_trig_f32(unsigned long long a, const float2* tab) {
+    return hwp_trig32((uint32_t)(a >> 32), tab);
 }
 
 // Index of the detector owning sample t: largest d with off[d] <= t.

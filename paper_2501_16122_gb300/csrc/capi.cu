@@ -112,6 +112,17 @@ int blocks_per_sm(const void* kernel, int threads, size_t smem) {
     return n;
 }
 
+void shard_reduce(bm_context* ctx, double* buf, int64_t count) {
+    if (!ctx->allreduce || count <= 0) return;
+    BM_CUDA(cudaStreamSynchronize(ctx->stream));
+    const bm_status st = ctx->allreduce(buf, count, ctx->allreduce_user);
+    if (st != BM_OK) {
+        set_error("the sharded solve's reduction of %lld values failed (%s)", (long long)count, bm_status_string(st));
+        throw Error{st};
+    }
+    BM_CUDA(cudaSetDevice(ctx->device));  // the callback may have switched devices
+}
+
 void* workspace(bm_context* ctx, const char* name, size_t bytes) {
     auto& b = ctx->ws[name];
     if (b.n < bytes) b.alloc_from(ctx->ws_pool, bytes + bytes / 8);  // stream-ordered: old users finish first
@@ -206,7 +217,22 @@ bm_status bm_context_create(int device, void* cuda_stream, bm_context** out) {
             bm_context_destroy(ctx);
             return BM_ERR_CUDA;
         }
+        try {
+            ctx->static_scratch = static_scratch_setup();
+        } catch (...) {
+            bm_context_destroy(ctx);
+            throw;
+        }
         *out = ctx;
+        return BM_OK;
+    });
+}
+
+bm_status bm_context_set_allreduce(bm_context* ctx, bm_allreduce_fn fn, void* user) {
+    return guarded([&] {
+        BM_REQUIRE(ctx, "ctx is NULL");
+        ctx->allreduce = fn;
+        ctx->allreduce_user = fn ? user : nullptr;
         return BM_OK;
     });
 }
@@ -367,6 +393,97 @@ bm_status bm_pointing_create_with_tod(bm_context* ctx, int64_t npix, int64_t nsa
                                       bm_pointing** out) {
     if (!tod) return guarded([&]() -> bm_status { BM_REQUIRE(false, "tod is NULL"); return BM_OK; });
     return create_pointing(ctx, npix, nsamples, pix, psi, psi_dtype, cos2psi, sin2psi, tod, solver, out);
+}
+
+static void check_det_offsets(int32_t ndet, const int64_t* det_offsets);
+
+namespace bm {
+namespace {
+// tab[j] = (cos, sin)(2 pi j / kHwpTab) in FP64, and rounded to FP32.
+__global__ void hwp_table_kernel(float2* __restrict__ tab, double2* __restrict__ tab64) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < kHwpTab; j += gridDim.x * blockDim.x) {
+        double sn, cs;
+        sincospi(2.0 * (double)j / (double)kHwpTab, &sn, &cs);
+        tab[j] = make_float2((float)cs, (float)sn);
+        tab64[j] = make_double2(cs, sn);
+    }
+}
+
+// A fraction of a turn in [0, 1) as a 64-bit fixed-point number (exact: x
+// times a power of two, truncated only below 2^-64).
+unsigned long long turn_fixed(double x) {
+    x -= std::floor(x);
+    const double v = std::ldexp(x, 64);
+    return v >= 18446744073709551616.0 ? 0ull : (unsigned long long)v;
+}
+}  // namespace
+}  // namespace bm
+
+bm_status bm_pointing_create_hwp(bm_context* ctx, int64_t npix, int64_t nsamples, const int32_t* pix,
+                                 int32_t ndet, const int64_t* det_offsets, const double* psi_det,
+                                 double hwp_turns_per_sample, double hwp_phase0, bm_solver_type solver,
+                                 bm_pointing** out) {
+    return guarded([&] {
+        BM_REQUIRE(ctx && out, "ctx/out is NULL");
+        *out = nullptr;
+        BM_REQUIRE(npix >= 1 && npix <= (int64_t(1) << 28), "npix %lld out of [1, 2^28]", (long long)npix);
+        BM_REQUIRE(nsamples >= 1 && nsamples < (int64_t(1) << 32), "nsamples out of [1, 2^32)");
+        BM_REQUIRE(pix && psi_det, "pix/psi_det is NULL");
+        BM_REQUIRE(solver == BM_SOLVER_I || solver == BM_SOLVER_QU || solver == BM_SOLVER_IQU,
+                   "bad solver type %d", (int)solver);
+        check_det_offsets(ndet, det_offsets);
+        BM_REQUIRE(det_offsets[ndet] == nsamples, "det_offsets[ndet] = %lld != nsamples %lld",
+                   (long long)det_offsets[ndet], (long long)nsamples);
+        BM_REQUIRE(std::isfinite(hwp_turns_per_sample) && std::isfinite(hwp_phase0),
+                   "non-finite half-wave-plate rate or phase");
+        for (int d = 0; d < ndet; ++d) BM_REQUIRE(std::isfinite(psi_det[d]), "psi_det[%d] is not finite", d);
+        use_device(ctx);
+        pix = static_cast<const int32_t*>(device_readable(ctx, pix, "pix"));
+        auto* p = new bm_pointing();
+        p->ctx = ctx;
+        p->npix = npix;
+        p->nsamples = nsamples;
+        p->ncomp = (int)solver;
+        try {
+            // the model: 2 theta = 2 psi_d + 4 phi0 + 4 (2 pi nu k), in turns
+            const double two_pi = 6.283185307179586476925287;
+            std::vector<uint32_t> off(ndet + 1);
+            std::vector<unsigned long long> turn0(ndet);
+            bool uniform = true;
+            for (int d = 0; d <= ndet; ++d) off[d] = (uint32_t)det_offsets[d];
+            for (int d = 0; d < ndet; ++d) {
+                turn0[d] = turn_fixed((2.0 * psi_det[d] + 4.0 * hwp_phase0) / two_pi);
+                uniform = uniform && (det_offsets[d + 1] - det_offsets[d] == det_offsets[1]);
+            }
+            p->hwp = true;
+            p->hwp_off.alloc(ndet + 1);
+            p->hwp_turn0.alloc(ndet);
+            p->hwp_tab.alloc(kHwpTab);
+            p->hwp_tab64.alloc(kHwpTab);
+            BM_CUDA(cudaMemcpyAsync(p->hwp_off.get(), off.data(), sizeof(uint32_t) * (ndet + 1),
+                                    cudaMemcpyHostToDevice, ctx->stream));
+            BM_CUDA(cudaMemcpyAsync(p->hwp_turn0.get(), turn0.data(), sizeof(unsigned long long) * ndet,
+                                    cudaMemcpyHostToDevice, ctx->stream));
+            hwp_table_kernel<<<(kHwpTab + 255) / 256, 256, 0, ctx->stream>>>(p->hwp_tab.get(), p->hwp_tab64.get());
+            BM_LAUNCH_CHECK();
+            HwpModel& m = p->hwp_model;
+            m.off = p->hwp_off.get();
+            m.turn0 = p->hwp_turn0.get();
+            m.tab64 = p->hwp_tab64.get();
+            m.nu = turn_fixed(hwp_turns_per_sample);
+            m.ndet = ndet;
+            // t / ns for uniform detectors (as the noise handles do; fewer than 2^20 detectors)
+            m.ns = uniform ? (uint32_t)det_offsets[1] : 0u;
+            m.inv_ns = uniform ? (float)(1.0 / (double)det_offsets[1]) : 0.f;
+            ingest(p, pix, nullptr, BM_F64, nullptr, nullptr, nullptr, false, &m);
+            BM_CUDA(cudaStreamSynchronize(ctx->stream));  // the host tables above are released on return
+        } catch (...) {
+            delete p;
+            throw;
+        }
+        *out = p;
+        return BM_OK;
+    });
 }
 
 void bm_pointing_destroy(bm_pointing* p) {
@@ -652,9 +769,9 @@ bm_status bm_precond_get_mask(const bm_precond* pc, uint8_t* mask, int32_t* hits
         const int64_t npix = pc->p->npix;
         if (mask)
             BM_CUDA(cudaMemcpyAsync(mask, pc->mask.get(), npix, cudaMemcpyDeviceToDevice, pc->ctx->stream));
-        if (hits)
-            BM_CUDA(cudaMemcpyAsync(hits, pc->p->hits.get(), sizeof(int32_t) * npix,
-                                    cudaMemcpyDeviceToDevice, pc->ctx->stream));
+        if (hits)  // a shard's preconditioner keeps the hit counts of all ranks
+            BM_CUDA(cudaMemcpyAsync(hits, pc->hits_global.get() ? pc->hits_global.get() : pc->p->hits.get(),
+                                    sizeof(int32_t) * npix, cudaMemcpyDeviceToDevice, pc->ctx->stream));
         BM_CUDA(cudaStreamSynchronize(pc->ctx->stream));
         return BM_OK;
     });

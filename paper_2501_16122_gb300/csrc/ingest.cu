@@ -96,7 +96,7 @@ __device__ __forceinline__ void st_keep(float2* p, float2 v, uint64_t pol) {
 // range of `range` samples, hist[d * G + range], as rs_hist_kernel counts
 // them; `sub` blocks share a range (its equal parts), each adding its counts
 // to the zeroed hist.  Without HIST the loop is grid-strided.
-constexpr int kTrigIn = 0, kPsi64 = 1, kPsi32 = 2;
+constexpr int kTrigIn = 0, kPsi64 = 1, kPsi32 = 2, kHwp = 3;
 constexpr int kVHist = 4;  // shared-memory digit histograms per validation block
 template <int MODE, bool HIST>
 __global__ void __launch_bounds__(256)
@@ -106,7 +106,7 @@ validate_kernel(const int32_t* __restrict__ pix, const void* __restrict__ psi,
                 float2* __restrict__ hi, float2* __restrict__ lo,
                 const float* __restrict__ tod_src, float* __restrict__ tod_dst,
                 unsigned long long* __restrict__ counters, int64_t range, int sub, int bins, int G,
-                uint32_t* __restrict__ hist) {
+                uint32_t* __restrict__ hist, HwpModel hwp) {
     extern __shared__ __align__(16) uint32_t vh[];  // HIST: [kVHist][bins], one per pair of warps
     uint32_t* mine = nullptr;
     if (HIST) {
@@ -122,6 +122,17 @@ validate_kernel(const int32_t* __restrict__ pix, const void* __restrict__ psi,
         if constexpr (MODE == kTrigIn) {
             ok_a = fabsf(c) <= 1.0f && fabsf(s) <= 1.0f;  // false for NaN
             hi[i] = make_float2(c, s);
+        } else if constexpr (MODE == kHwp) {
+            // 2 theta of the half-wave-plate model in turns, reduced exactly,
+            // and its cos and sin in FP64 (table and short polynomials)
+            ok_a = true;
+            const int d = det_of(hwp.off, hwp.ndet, hwp.ns, hwp.inv_ns, (uint32_t)i);
+            const unsigned long long a2 = hwp_turns(hwp, d, (uint32_t)i);
+            double sn, cs;
+            hwp_trig64(a2, hwp.tab64, cs, sn);
+            const float ch = (float)cs, sh = (float)sn;
+            hi[i] = make_float2(ch, sh);
+            lo[i] = make_float2((float)(cs - (double)ch), (float)(sn - (double)sh));
         } else {
             ok_a = isfinite(a);
             double sn, cs;
@@ -653,7 +664,8 @@ SortPlan plan_sort(const bm_context* ctx, int64_t n, int64_t npix) {
     ensure_smem_limit(reinterpret_cast<const void*>(rs_hist_kernel), sizeof(uint32_t) * IG_WARPS * sp.bins);
     for (const void* k : {reinterpret_cast<const void*>(validate_kernel<kTrigIn, true>),
                           reinterpret_cast<const void*>(validate_kernel<kPsi64, true>),
-                          reinterpret_cast<const void*>(validate_kernel<kPsi32, true>)})
+                          reinterpret_cast<const void*>(validate_kernel<kPsi32, true>),
+                          reinterpret_cast<const void*>(validate_kernel<kHwp, true>)})
         ensure_smem_limit(k, sizeof(uint32_t) * kVHist * sp.bins);
     int per_sm = blocks_per_sm(reinterpret_cast<const void*>(rs_scatter_kernel<true, false>), SC_THREADS, smem);
     if (per_sm < 1) per_sm = 1;
@@ -669,7 +681,7 @@ SortPlan plan_sort(const bm_context* ctx, int64_t n, int64_t npix) {
 }  // namespace
 
 void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dtype, const float* cos2psi,
-            const float* sin2psi, const float* tod, bool tod_on_host) {
+            const float* sin2psi, const float* tod, bool tod_on_host, const HwpModel* hwp) {
     bm_context* ctx = p->ctx;
     cudaStream_t s = ctx->stream;
     ScopedTimer timer(ctx, "ingest");
@@ -693,12 +705,13 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
         ScopedTimer vt(ctx, "ingest_validate");
         BM_CUDA(cudaMemsetAsync(hist.get(), 0, sizeof(uint32_t) * (size_t)sp.bins * sp.grid, s));
         auto kern = exact_trig ? validate_kernel<kTrigIn, true>
+                    : hwp      ? validate_kernel<kHwp, true>
                                : (psi_dtype == BM_F64 ? validate_kernel<kPsi64, true> : validate_kernel<kPsi32, true>);
         constexpr int kSub = 2;  // two blocks a range: eight resident blocks per SM
         kern<<<sp.grid * kSub, IG_THREADS, sizeof(uint32_t) * kVHist * sp.bins, s>>>(
             pix, psi, cos2psi, sin2psi, n, npix, p->pix.get(), p->cs_hi_t.get(), p->cs_lo_t.get(),
             tod_on_host ? tod : nullptr, tod_copy.get(), counters.get(), sp.range, kSub, sp.bins, sp.grid,
-            hist.get());
+            hist.get(), hwp ? *hwp : HwpModel{});
         BM_LAUNCH_CHECK();
     }
     unsigned long long h_cnt[2] = {0, 0};

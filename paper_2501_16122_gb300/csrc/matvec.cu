@@ -21,12 +21,14 @@
 
 #include "bm_internal.cuh"
 #include "fft_filter.cuh"
+#include "white_matvec.cuh"
 
 namespace bm {
 
 namespace {
 
 constexpr int kWarps = 8;  // warps per block in the warp-per-item kernels
+static_assert(kWarps == kWhiteWarps, "the white-noise kernels share the warp-per-item grid");
 
 // x (FP64, [npix][NC]) -> FP32 copy with masked pixels zeroed.
 template <typename TO>
@@ -56,106 +58,84 @@ __global__ void masked_copy4_kernel(const double* __restrict__ x, const uint8_t*
     }
 }
 
-// ------------------------------------------------------- white, FP32 form
-// One work item per warp.  Loads are 16 bytes per lane (two samples of the
-// (u_c, u_s) stream, four of the I-only weight stream) after a scalar head
-// that aligns the item start; each lane sums a group of samples in FP32 and
-// folds the group into a compensated (double-float) accumulator, the warp
-// combines the accumulators in double-float, and lane 0 writes the FP64 item
-// partial.  sqrt(w) = |u| is formed as |u|^2 * rsqrt(|u|^2); the same value
-// multiplies x_I and the I output, so the operator stays symmetric.
+// ---------------------------------- white, FP32 form, half-wave-plate angle
+// The same operator for a pointing whose angle follows the half-wave-plate
+// model (bm_pointing_create_hwp): per sorted sample the kernel reads only its
+// time index t (4 bytes), finds the detector d (looked up only when t passes
+// the current detector's end: a lane's samples of one pixel are in time
+// order), rebuilds (cos 2 theta, sin 2 theta) in FP32 from the exactly
+// reduced phase (hwp_trig_f32: a table of kHwpTab entries in shared memory
+// and a short polynomial), and accumulates w_d y v with y = v . x_p:
+// FP32 products, FP32 group sums of 8 samples folded into double-float, warp
+// sums in double-float, an FP64 partial per item.
 template <int NC>
 __global__ void __launch_bounds__(kWarps * 32)
-white_matvec_f32_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ item_beg,
-                        const int32_t* __restrict__ item_len, int64_t nitems,
-                        const float2* __restrict__ wcs, const float* __restrict__ w1,
+white_matvec_hwp_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ item_beg,
+                        const int32_t* __restrict__ item_len, int64_t nitems, const uint32_t* __restrict__ perm,
+                        HwpModel m, const float2* __restrict__ tab_g, const float2* __restrict__ wdf,
                         const float* __restrict__ x32, double* __restrict__ partial) {
+    static_assert(NC > 1, "I-only maps do not depend on the angle");
+    __shared__ float2 tab[kHwpTab];
+    for (int j = threadIdx.x; j < kHwpTab; j += blockDim.x) tab[j] = tab_g[j];
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * kWarps;
     for (int64_t k = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); k < nitems; k += nwarps) {
         const int64_t p = item_pix[k];
-        int64_t b = item_beg[k];
-        int len = item_len[k];
-        if (NC == 1) {
-            const float xi = x32[p];
-            df32 A = {0.f, 0.f};
-            const int head = (int)((4 - (b & 3)) & 3) < len ? (int)((4 - (b & 3)) & 3) : len;
-            if (lane < head) A = df_add(A, __ldg(w1 + b + lane));
-            b += head;
-            len -= head;
-            const float4* src4 = reinterpret_cast<const float4*>(w1 + b);
-            const int nq = len >> 2;
-            int j = lane;
-            for (; j + 32 < nq; j += 64) {
-                const float4 a = __ldg(src4 + j), c = __ldg(src4 + j + 32);
-                A = df_add(A, ((a.x + a.y) + (a.z + a.w)) + ((c.x + c.y) + (c.z + c.w)));
+        const int64_t b = item_beg[k];
+        const int len = item_len[k];
+        float xI = 0.f, xQ, xU;
+        if (NC == 3) { xI = x32[3 * p]; xQ = x32[3 * p + 1]; xU = x32[3 * p + 2]; }
+        else { xQ = x32[2 * p]; xU = x32[2 * p + 1]; }
+        float aI = 0.f, aQ = 0.f, aU = 0.f;
+        df32 AI = {0.f, 0.f}, AQ = {0.f, 0.f}, AU = {0.f, 0.f};
+        // the current detector's end, first sample, angle offset and weight
+        uint32_t dend = 0, dbeg = 0, a0 = 0;
+        float w = 0.f;
+        auto step = [&](uint32_t t) {
+            if (t >= dend) {
+                const int d = det_of(m.off, m.ndet, m.ns, m.inv_ns, t);
+                dbeg = m.ns ? (uint32_t)d * m.ns : m.off[d];
+                dend = m.ns ? dbeg + m.ns : m.off[d + 1];
+                a0 = (uint32_t)(__ldg(m.turn0 + d) >> 32);
+                w = __ldg(&wdf[d].x);
             }
-            for (; j < nq; j += 32) {
-                const float4 a = __ldg(src4 + j);
-                A = df_add(A, (a.x + a.y) + (a.z + a.w));
-            }
-            const int rem = len & 3;
-            if (lane < rem) A = df_add(A, __ldg(w1 + b + 4 * nq + lane));
-            A = df_warp_sum(A);
-            if (lane == 0) partial[k] = df_to_double(A) * (double)xi;
-        } else {
-            float xI = 0.f, xQ, xU;
-            if (NC == 3) { xI = x32[3 * p]; xQ = x32[3 * p + 1]; xU = x32[3 * p + 2]; }
-            else { xQ = x32[2 * p]; xU = x32[2 * p + 1]; }
-            float aI = 0.f, aQ = 0.f, aU = 0.f;  // FP32 group sums
-            df32 AI = {0.f, 0.f}, AQ = {0.f, 0.f}, AU = {0.f, 0.f};
-            auto step = [&](float2 u) {
-                float r = 0.f;
-                if (NC == 3) {
-                    const float u2 = fmaf(u.x, u.x, u.y * u.y);
-                    r = u2 > 0.f ? u2 * rsqrtf(u2) : 0.f;  // sqrt(w); a zero weight gives 0
-                }
-                const float y = fmaf(u.x, xQ, fmaf(u.y, xU, r * xI));
-                if (NC == 3) aI = fmaf(y, r, aI);
-                aQ = fmaf(y, u.x, aQ);
-                aU = fmaf(y, u.y, aU);
-            };
-            auto fold = [&]() {
-                if (NC == 3) AI = df_add(AI, aI);
-                AQ = df_add(AQ, aQ);
-                AU = df_add(AU, aU);
-                aI = aQ = aU = 0.f;
-            };
-            if (b & 1) {  // align the stream to 16 bytes
-                if (lane == 0) step(__ldg(wcs + b));
-                ++b;
-                --len;
-            }
-            const float4* src4 = reinterpret_cast<const float4*>(wcs + b);
-            const int np = len >> 1;  // sample pairs
-            int j = lane;
-            for (; j + 96 < np; j += 128) {
-                const float4 u0 = __ldg(src4 + j), u1 = __ldg(src4 + j + 32);
-                const float4 u2 = __ldg(src4 + j + 64), u3 = __ldg(src4 + j + 96);
-                step(make_float2(u0.x, u0.y)); step(make_float2(u0.z, u0.w));
-                step(make_float2(u1.x, u1.y)); step(make_float2(u1.z, u1.w));
-                step(make_float2(u2.x, u2.y)); step(make_float2(u2.z, u2.w));
-                step(make_float2(u3.x, u3.y)); step(make_float2(u3.z, u3.w));
-                fold();
-            }
-            for (; j < np; j += 32) {
-                const float4 u0 = __ldg(src4 + j);
-                step(make_float2(u0.x, u0.y)); step(make_float2(u0.z, u0.w));
-            }
-            if ((len & 1) && lane == 0) step(__ldg(wcs + b + len - 1));
+            const float2 cs = hwp_trig32(hwp_turns32(m.nu, a0, t - dbeg), tab);
+            float y = fmaf(cs.x, xQ, cs.y * xU);
+            if (NC == 3) y += xI;
+            const float wy = w * y;
+            if (NC == 3) aI += wy;
+            aQ = fmaf(wy, cs.x, aQ);
+            aU = fmaf(wy, cs.y, aU);
+        };
+        auto fold = [&]() {
+            if (NC == 3) AI = df_add(AI, aI);
+            AQ = df_add(AQ, aQ);
+            AU = df_add(AU, aU);
+            aI = aQ = aU = 0.f;
+        };
+        int i = lane;
+        for (; i + 224 < len; i += 256) {  // eight samples a lane, their loads issued together
+            uint32_t t[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) t[u] = __ldg(perm + b + i + 32 * u);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) step(t[u]);
             fold();
-            AQ = df_warp_sum(AQ);
-            AU = df_warp_sum(AU);
-            if (NC == 3) AI = df_warp_sum(AI);
-            if (lane == 0) {
-                if (NC == 3) {
-                    partial[3 * k] = df_to_double(AI);
-                    partial[3 * k + 1] = df_to_double(AQ);
-                    partial[3 * k + 2] = df_to_double(AU);
-                } else {
-                    partial[2 * k] = df_to_double(AQ);
-                    partial[2 * k + 1] = df_to_double(AU);
-                }
+        }
+        for (; i < len; i += 32) step(__ldg(perm + b + i));
+        fold();
+        AQ = df_warp_sum(AQ);
+        AU = df_warp_sum(AU);
+        if (NC == 3) AI = df_warp_sum(AI);
+        if (lane == 0) {
+            if (NC == 3) {
+                partial[3 * k] = df_to_double(AI);
+                partial[3 * k + 1] = df_to_double(AQ);
+                partial[3 * k + 2] = df_to_double(AU);
+            } else {
+                partial[2 * k] = df_to_double(AQ);
+                partial[2 * k + 1] = df_to_double(AU);
             }
         }
     }
@@ -456,20 +436,6 @@ gather_reduce_f32_kernel(const int64_t* __restrict__ item_beg, const int32_t* __
     }
 }
 
-// q_p = sum of the partials of pixel p's items (item order); 0 for pixels without items.
-__global__ void finalize_pixels_kernel(const int64_t* __restrict__ pitem, const double* __restrict__ partial,
-                                       int64_t npix, int nc, double* __restrict__ q) {
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k0 = pitem[p], k1 = pitem[p + 1];
-        for (int c = 0; c < nc; ++c) {
-            double s = 0.0;
-            for (int64_t k = k0; k < k1; ++k) s += partial[k * nc + c];
-            q[p * nc + c] = s;
-        }
-    }
-}
-
 // ------------------------------------------------ time-chunked transpose
 // The mixed Toeplitz operator's transpose q_p = sum_i z[perm_i] v_i gathers
 // 4-byte z values at random time positions: each costs a DRAM sector.  It
@@ -506,53 +472,108 @@ __global__ void pt_bounds_kernel(const int64_t* __restrict__ off, const uint32_t
     }
 }
 
-// One chunk of the transpose: per kept pixel, the sum over its samples in
-// chunk c of z v (FP32 products, summed in FP32 groups of up to 4 per lane and
-// folded into double-float), added to the pixel's accumulator.  kPtLanes lanes per pixel, the warp's groups on consecutive
-// pixels.
+// The chunk-major copy of the kept samples.  seglen[c][p] = samples of kept
+// pixel p in chunk c (0 for masked pixels), nz[c][p] = 1 if any.
+__global__ void cm_seglen_kernel(const int32_t* __restrict__ sub, const uint8_t* __restrict__ mask, int64_t npix,
+                                 int nch, uint32_t* __restrict__ seglen, uint32_t* __restrict__ nz) {
+    const int64_t n = (int64_t)nch * npix;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = e % npix;
+        const uint32_t len = mask[p] ? 0u : (uint32_t)(sub[e + npix] - sub[e]);
+        seglen[e] = len;
+        nz[e] = len ? 1u : 0u;
+    }
+}
+
+// Sample i of kept pixel p's sorted run goes to segpos[c][p] + (i - sub[c][p])
+// with c its time chunk: within a segment the samples keep their (time)
+// order.  One warp per pixel.
+__global__ void cm_scatter_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ sub,
+                                  const uint32_t* __restrict__ segpos, const uint8_t* __restrict__ mask,
+                                  int64_t npix, const uint32_t* __restrict__ perm, const float2* __restrict__ hi,
+                                  uint32_t* __restrict__ cm_t, float2* __restrict__ cm_cs) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < npix; p += nwarps) {
+        if (mask[p]) continue;
+        const int64_t b = off[p];
+        const int32_t len = (int32_t)(off[p + 1] - b);
+        for (int32_t i = lane; i < len; i += 32) {
+            const uint32_t t = perm[b + i];
+            const int64_t e = (int64_t)(t >> kPtChunkBits) * npix + p;
+            const uint32_t dst = segpos[e] + (uint32_t)(i - sub[e]);
+            cm_t[dst] = t;
+            cm_cs[dst] = hi[b + i];
+        }
+    }
+}
+
+// The non-empty segments in (chunk, pixel) order.
+__global__ void cm_segments_kernel(const uint32_t* __restrict__ seglen, const uint32_t* __restrict__ segpos,
+                                   const uint32_t* __restrict__ segidx, int64_t npix, int nch,
+                                   int32_t* __restrict__ seg_pix, uint32_t* __restrict__ seg_beg,
+                                   int32_t* __restrict__ seg_len) {
+    const int64_t n = (int64_t)nch * npix;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t len = seglen[e];
+        if (!len) continue;
+        const uint32_t k = segidx[e];
+        seg_pix[k] = (int32_t)(e % npix);
+        seg_beg[k] = segpos[e];
+        seg_len[k] = (int32_t)len;
+    }
+}
+
+// One chunk of the transpose: per segment (a kept pixel's samples in chunk
+// c, contiguous in the chunk-major order), the sum of z v (FP32 products,
+// summed in FP32 groups of up to 8 per lane and folded into double-float),
+// added to the pixel's accumulator.  z stays in time order: a chunk of it is
+// 64 MB, which L2 keeps while the launch gathers from it; the chunk-major
+// streams are read once with an evict-first hint so that they do not push it
+// out.  kPtLanes lanes per segment, the warp's groups on consecutive
+// segments; within a chunk a pixel has one segment, so each accumulator has
+// one writer per launch, and the launches run in chunk order
+// (deterministic).
 template <int NC>
 __global__ void __launch_bounds__(kWarps * 32)
-pt_chunk_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ sub, const uint8_t* __restrict__ mask,
-                int64_t npix, int nch, int c, const uint32_t* __restrict__ perm, const float2* __restrict__ hi,
+pt_chunk_kernel(const int32_t* __restrict__ seg_pix, const uint32_t* __restrict__ seg_beg,
+                const int32_t* __restrict__ seg_len, int64_t seg0, int64_t nseg,
+                const uint32_t* __restrict__ cm_t, const float2* __restrict__ cm_cs,
                 const float* __restrict__ z, float2* __restrict__ acc) {
     constexpr int G = 32 / kPtLanes;
+    constexpr int U = 8;
     const int lane = threadIdx.x & 31, gl = lane % kPtLanes, grp = lane / kPtLanes;
     const int64_t nwarps = (int64_t)gridDim.x * kWarps;
-    for (int64_t pw = ((int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5)) * G; pw < npix; pw += nwarps * G) {
-        const int64_t p = pw + grp;
-        int64_t b = 0;
-        int32_t s0 = 0, s1 = 0;
-        if (p < npix && !mask[p]) {
-            b = off[p];
-            s0 = sub[(int64_t)c * npix + p];
-            s1 = sub[(int64_t)(c + 1) * npix + p];
+    for (int64_t kw = ((int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5)) * G; kw < nseg; kw += nwarps * G) {
+        const int64_t k = kw + grp;
+        int64_t p = 0, b = 0;
+        int32_t len = 0;
+        if (k < nseg) {
+            p = seg_pix[seg0 + k];
+            b = seg_beg[seg0 + k];
+            len = seg_len[seg0 + k];
         }
         float a[NC];
         df32 A[NC];
 #pragma unroll
-        for (int k = 0; k < NC; ++k) {
-            a[k] = 0.f;
-            A[k] = {0.f, 0.f};
+        for (int c = 0; c < NC; ++c) {
+            a[c] = 0.f;
+            A[c] = {0.f, 0.f};
         }
-        // four samples per lane with their loads issued together, summed in
-        // FP32 and folded into double-float per batch
-        for (int32_t i0 = s0; i0 < s1; i0 += 4 * kPtLanes) {
-            uint32_t t[4];
-            float v[4];
-            float2 h[4];
+        for (int32_t i0 = 0; i0 < len; i0 += U * kPtLanes) {
+            uint32_t t[U];
+            float v[U];
+            float2 h[U];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < U; ++u) {
                 const int32_t i = i0 + gl + u * kPtLanes;
-                t[u] = i < s1 ? perm[b + i] : 0xFFFFFFFFu;
+                t[u] = i < len ? __ldcs(cm_t + b + i) : 0xFFFFFFFFu;
+                h[u] = (NC > 1 && i < len) ? __ldcs(cm_cs + b + i) : make_float2(0.f, 0.f);
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int32_t i = i0 + gl + u * kPtLanes;
-                v[u] = t[u] != 0xFFFFFFFFu ? z[t[u]] : 0.f;
-                h[u] = (NC > 1 && i < s1) ? hi[b + i] : make_float2(0.f, 0.f);
-            }
+            for (int u = 0; u < U; ++u) v[u] = t[u] != 0xFFFFFFFFu ? z[t[u]] : 0.f;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < U; ++u) {
                 if (NC == 1) {
                     a[0] += v[u];
                 } else {
@@ -562,23 +583,22 @@ pt_chunk_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ sub
                 }
             }
 #pragma unroll
-            for (int k = 0; k < NC; ++k) {
-                A[k] = df_add(A[k], a[k]);
-                a[k] = 0.f;
+            for (int c = 0; c < NC; ++c) {
+                A[c] = df_add(A[c], a[c]);
+                a[c] = 0.f;
             }
         }
 #pragma unroll
-        for (int k = 0; k < NC; ++k) {
-            A[k] = df_add(A[k], a[k]);
+        for (int c = 0; c < NC; ++c) {
 #pragma unroll
-            for (int o = kPtLanes / 2; o > 0; o >>= 1) A[k] = df_add(A[k], df_shfl_xor(A[k], o));
+            for (int o = kPtLanes / 2; o > 0; o >>= 1) A[c] = df_add(A[c], df_shfl_xor(A[c], o));
         }
-        if (gl == 0 && s1 > s0) {
+        if (gl == 0 && len > 0) {
 #pragma unroll
-            for (int k = 0; k < NC; ++k) {
-                const float2 old = acc[p * NC + k];
-                const df32 s = df_add(df32{old.x, old.y}, A[k]);
-                acc[p * NC + k] = make_float2(s.hi, s.lo);
+            for (int c = 0; c < NC; ++c) {
+                const float2 old = acc[p * NC + c];
+                const df32 s = df_add(df32{old.x, old.y}, A[c]);
+                acc[p * NC + c] = make_float2(s.hi, s.lo);
             }
         }
     }
@@ -643,25 +663,33 @@ struct SrcPlainF32 {
 // pixel-then-map gather.
 __global__ void pointing_apply_f32_kernel(const int32_t* __restrict__ pix, const float2* __restrict__ hi, int64_t n,
                                           const float4* __restrict__ x4, float* __restrict__ y) {
-    constexpr int U = 4;
+    // four consecutive samples per thread and iteration, with 16-byte loads
+    // and stores (pix and y by four, the trig pairs by two) and the four map
+    // gathers issued together; the arrays are 16-byte aligned device buffers
+    const int64_t nq = n >> 2;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t0 < n; t0 += U * stride) {
-        int32_t p[U];
-        float2 h[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t t = t0 + u * stride;
-            p[u] = t < n ? pix[t] : -1;
-            h[u] = t < n ? hi[t] : make_float2(0.f, 0.f);
-        }
-        float4 xv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) xv[u] = p[u] >= 0 ? x4[p[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t t = t0 + u * stride;
-            if (t < n) y[t] = fmaf(h[u].x, xv[u].y, fmaf(h[u].y, xv[u].z, xv[u].x));
-        }
+    const int4* pix4 = reinterpret_cast<const int4*>(pix);
+    const float4* hi4 = reinterpret_cast<const float4*>(hi);
+    float4* y4 = reinterpret_cast<float4*>(y);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += stride) {
+        const int4 p = __ldcs(pix4 + q);
+        const float4 ha = __ldcs(hi4 + 2 * q), hb = __ldcs(hi4 + 2 * q + 1);
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 x0 = p.x >= 0 ? x4[p.x] : z, x1 = p.y >= 0 ? x4[p.y] : z;
+        const float4 x2 = p.z >= 0 ? x4[p.z] : z, x3 = p.w >= 0 ? x4[p.w] : z;
+        float4 out;
+        out.x = fmaf(ha.x, x0.y, fmaf(ha.y, x0.z, x0.x));
+        out.y = fmaf(ha.z, x1.y, fmaf(ha.w, x1.z, x1.x));
+        out.z = fmaf(hb.x, x2.y, fmaf(hb.y, x2.z, x2.x));
+        out.w = fmaf(hb.z, x3.y, fmaf(hb.w, x3.z, x3.x));
+        y4[q] = out;
+    }
+    // the last n mod 4 samples
+    for (int64_t t = 4 * nq + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+        const int32_t pp = pix[t];
+        const float2 h = hi[t];
+        const float4 xv = pp >= 0 ? x4[pp] : make_float4(0.f, 0.f, 0.f, 0.f);
+        y[t] = fmaf(h.x, xv.y, fmaf(h.y, xv.z, xv.x));
     }
 }
 
@@ -1435,38 +1463,88 @@ static void gather_reduce_f32(bm_pointing* p, const ItemsView& it, const float* 
 }
 
 // The inner Toeplitz operator's transpose, time chunk by time chunk (see
-// pt_chunk_kernel); the plain pixel-sorted gather when the table of sub-run
-// bounds would exceed kPtSubMaxBytes.
-constexpr size_t kPtSubMaxBytes = size_t(1) << 31;
+// pt_chunk_kernel), over the chunk-major order of the kept samples; built on
+// first use for an FFT-form filter unless its temporary tables would exceed
+// kPtTableMaxBytes (then the plain pixel-sorted gather runs instead).
+constexpr size_t kPtTableMaxBytes = size_t(1) << 32;
+static void build_chunk_major(bm_pointing* p, bm_precond* pc, int nch) {
+    bm_context* ctx = p->ctx;
+    cudaStream_t s = ctx->stream;
+    const int64_t npix = p->npix;
+    const int64_t ne = (int64_t)nch * npix;
+    ScopedTimer timer(ctx, "toeplitz_pt_bounds");
+    // sub[c][p]: position of pixel p's first sample in chunk c or later
+    DevBuf<int32_t> sub((size_t)npix * (nch + 1));
+    pt_bounds_kernel<<<grid_for(ctx, (npix + 7) / 8, 16), 256, 0, s>>>(p->off.get(), p->perm.get(), npix, nch,
+                                                                     sub.get());
+    BM_LAUNCH_CHECK();
+    DevBuf<uint32_t> seglen(ne), segpos(ne), segidx(ne + 1);
+    cm_seglen_kernel<<<grid_for(ctx, (ne + 255) / 256, 16), 256, 0, s>>>(sub.get(), pc->mask.get(), npix, nch,
+                                                                         seglen.get(), segidx.get());
+    BM_LAUNCH_CHECK();
+    BM_CUDA(cudaMemsetAsync(segidx.get() + ne, 0, sizeof(uint32_t), s));
+    exclusive_scan_u32(seglen.get(), segpos.get(), ne, s);
+    exclusive_scan_u32(segidx.get(), segidx.get(), ne + 1, s);  // [ne] = the number of segments
+    // chunk c's first segment is segidx[c * npix]; the kept samples are
+    // segpos[ne - 1] + seglen[ne - 1]
+    std::vector<uint32_t> h_first(nch + 1);
+    for (int c = 0; c <= nch; ++c)
+        BM_CUDA(cudaMemcpyAsync(&h_first[c], segidx.get() + (int64_t)c * npix, sizeof(uint32_t),
+                                cudaMemcpyDeviceToHost, s));
+    uint32_t last_pos = 0, last_len = 0;
+    BM_CUDA(cudaMemcpyAsync(&last_pos, segpos.get() + ne - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    BM_CUDA(cudaMemcpyAsync(&last_len, seglen.get() + ne - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    BM_CUDA(cudaStreamSynchronize(s));
+    const int64_t nkept = (int64_t)last_pos + last_len;
+    const int64_t nseg = h_first[nch];
+    pc->cseg.assign(h_first.begin(), h_first.end());
+    pc->cm_t.alloc(std::max<int64_t>(nkept, 1));
+    pc->cm_cs.alloc(std::max<int64_t>(nkept, 1));
+    pc->seg_pix.alloc(std::max<int64_t>(nseg, 1));
+    pc->seg_beg.alloc(std::max<int64_t>(nseg, 1));
+    pc->seg_len.alloc(std::max<int64_t>(nseg, 1));
+    cm_scatter_kernel<<<grid_for(ctx, (npix + 7) / 8, 16), 256, 0, s>>>(p->off.get(), sub.get(), segpos.get(),
+                                                                      pc->mask.get(), npix, p->perm.get(),
+                                                                      p->cs_hi_s.get(), pc->cm_t.get(),
+                                                                      pc->cm_cs.get());
+    BM_LAUNCH_CHECK();
+    cm_segments_kernel<<<grid_for(ctx, (ne + 255) / 256, 16), 256, 0, s>>>(seglen.get(), segpos.get(), segidx.get(),
+                                                                            npix, nch, pc->seg_pix.get(),
+                                                                            pc->seg_beg.get(), pc->seg_len.get());
+    BM_LAUNCH_CHECK();
+}
+
+// True when the chunk-major order is (or has now been) built.
+static bool ensure_chunk_major(bm_pointing* p, bm_inv_noise* n, bm_precond* pc) {
+    if (pc->pt_nch == 0) {
+        const int nch = (int)((p->nsamples + (int64_t(1) << kPtChunkBits) - 1) >> kPtChunkBits);
+        // temporaries: the bounds table and three [nch][npix] tables
+        if (n->fft_n32 == 0 || (size_t)p->npix * (size_t)(4 * nch + 2) * sizeof(int32_t) > kPtTableMaxBytes) {
+            pc->pt_nch = -1;
+        } else {
+            build_chunk_major(p, pc, nch);
+            pc->pt_nch = nch;
+        }
+    }
+    return pc->pt_nch > 0;
+}
+
+// q = P^T z for z in time order, by chunks of the chunk-major order.
 static void pt_chunked(bm_pointing* p, bm_precond* pc, const float* z, double* q) {
     bm_context* ctx = p->ctx;
     cudaStream_t s = ctx->stream;
     const int nc = p->ncomp;
     const int64_t npix = p->npix;
-    const int nch = (int)((p->nsamples + (int64_t(1) << kPtChunkBits) - 1) >> kPtChunkBits);
-    if (pc->pt_nch == 0) {  // first use: the table of sub-run bounds
-        if ((size_t)npix * (size_t)(nch + 1) * sizeof(int32_t) > kPtSubMaxBytes) {
-            pc->pt_nch = -1;
-        } else {
-            ScopedTimer timer(ctx, "toeplitz_pt_bounds");
-            pc->pt_sub.alloc((size_t)npix * (nch + 1));
-            pt_bounds_kernel<<<grid_for(ctx, (npix + 7) / 8, 16), 256, 0, s>>>(p->off.get(), p->perm.get(), npix, nch,
-                                                                             pc->pt_sub.get());
-            BM_LAUNCH_CHECK();
-            pc->pt_nch = nch;
-        }
-    }
-    if (pc->pt_nch < 0) {
-        gather_reduce_f32(p, kept_items(pc), z, q);
-        return;
-    }
+    const int nch = pc->pt_nch;
     float2* acc = workspace_as<float2>(ctx, "pt_acc", (size_t)npix * nc);
     BM_CUDA(cudaMemsetAsync(acc, 0, sizeof(float2) * (size_t)npix * nc, s));
-    const int64_t wunits = ((npix + 3) / 4 + kWarps - 1) / kWarps;
     for (int c = 0; c < nch; ++c) {
+        const int64_t seg0 = pc->cseg[c], nseg = pc->cseg[c + 1] - seg0;
+        if (nseg == 0) continue;
+        const int64_t wunits = ((nseg + 3) / 4 + kWarps - 1) / kWarps;
 #define BM_PT(NC)                                                                                                  \
     pt_chunk_kernel<NC><<<resident_grid(ctx, pt_chunk_kernel<NC>, kWarps * 32, wunits), kWarps * 32, 0, s>>>(       \
-        p->off.get(), pc->pt_sub.get(), pc->mask.get(), npix, nch, c, p->perm.get(), p->cs_hi_s.get(), z, acc)
+        pc->seg_pix.get(), pc->seg_beg.get(), pc->seg_len.get(), seg0, nseg, pc->cm_t.get(), pc->cm_cs.get(), z, acc)
         if (nc == 3) BM_PT(3); else if (nc == 2) BM_PT(2); else BM_PT(1);
 #undef BM_PT
         BM_LAUNCH_CHECK();
@@ -1523,12 +1601,22 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
                 float* x32 = workspace_as<float>(ctx, "x32", nvec);
                 masked_copy_kernel<float><<<vgrid, threads, 0, s>>>(xr, pc->mask.get(), p->npix, nc, x32);
                 BM_LAUNCH_CHECK();
-                if (pc->nitems > 0) {
+                if (pc->nitems > 0 && p->hwp && n->kind == 0 && nc > 1) {
+                    // the angle rebuilt from the half-wave-plate model
+                    ScopedTimer timer(ctx, "matvec_white_hwp");
+#define BM_WHWP(NC)                                                                                                 \
+    white_matvec_hwp_kernel<NC><<<resident_grid(ctx, white_matvec_hwp_kernel<NC>, kWarps * 32, wunits), kWarps * 32, \
+                                  0, s>>>(pc->item_pix.get(), pc->item_beg.get(), pc->item_len.get(), pc->nitems,   \
+                                          p->perm.get(), p->hwp_model, p->hwp_tab.get(), n->wdf.get(), x32, partial)
+                    if (nc == 3) BM_WHWP(3); else BM_WHWP(2);
+#undef BM_WHWP
+                    BM_LAUNCH_CHECK();
+                } else if (pc->nitems > 0) {
                     ScopedTimer timer(ctx, "matvec_white_f32");
 #define BM_WF32(NC)                                                                                     \
-    white_matvec_f32_kernel<NC><<<resident_grid(ctx, white_matvec_f32_kernel<NC>, kWarps * 32, wunits), kWarps * 32, 0, s>>>(pc->item_pix.get(), pc->item_beg.get(),     \
-                                                             pc->item_len.get(), pc->nitems, pc->wcs.get(), \
-                                                             pc->w1.get(), x32, partial)
+    white_matvec_f32_kernel<NC, float><<<resident_grid(ctx, white_matvec_f32_kernel<NC, float>, kWhiteWarps * 32, wunits), kWhiteWarps * 32, 0, s>>>( \
+        pc->item_pix.get(), pc->item_beg.get(), pc->item_len.get(), pc->nitems, pc->wcs.get(), pc->w1.get(), x32,    \
+        partial)
                     if (nc == 3) BM_WF32(3); else if (nc == 2) BM_WF32(2); else BM_WF32(1);
 #undef BM_WF32
                     BM_LAUNCH_CHECK();
@@ -1551,6 +1639,9 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
             offset_matvec_refine(p, n, pc, xr, qr);
         } else {
             if (prec == BM_PREC_MIXED) {
+                // the transpose by time chunks over the chunk-major order when
+                // it can be built (FFT form), else the pixel-sorted gather
+                const bool cm = ensure_chunk_major(p, n, pc);
                 float* z32 = workspace_as<float>(ctx, "z32", p->nsamples);
                 {
                     ScopedTimer timer(ctx, "toeplitz_f32");
@@ -1566,7 +1657,8 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
                 }
                 // scatter with the same FP32 trig the gather used (symmetric operator)
                 ScopedTimer timer(ctx, "toeplitz_pt");
-                pt_chunked(p, pc, z32, qr);
+                if (cm) pt_chunked(p, pc, z32, qr);
+                else gather_reduce_f32(p, kept_items(pc), z32, qr);
             } else {
                 // FP64, or the refinement operator: the same with a
                 // double-float filter and pixel sums
@@ -1587,6 +1679,7 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
                 gather_reduce<double>(p, kept_items(pc), z64, nullptr, p->cs_lo_s.get(), refine, qr);
             }
         }
+        shard_reduce(ctx, qr, nvec);  // a shard's partial A x, summed over the ranks
     }
 }
 
@@ -1599,9 +1692,10 @@ void rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dt
     for (int64_t r = 0; r < nrhs; ++r) {
         double* br = b + r * nvec;
         if (diagonal_noise(n)) {
-            if (!tod && df && pc->b_tod.get()) {  // assembled with the preconditioner's blocks
+            if (!tod && df && pc->b_tod.get()) {  // assembled (and summed over the ranks) with the blocks
                 BM_CUDA(cudaMemcpyAsync(br, pc->b_tod.get(), sizeof(double) * nvec, cudaMemcpyDeviceToDevice,
                                         ctx->stream));
+                continue;
             } else if (!tod) {  // the TOD sorted along with the pointing
                 gather_reduce<float>(p, kept_items(pc), nullptr, n, p->cs_lo_s.get(), df, br, p->tod_s.get(), pc);
             } else if (dt == BM_F32) {
@@ -1637,6 +1731,7 @@ void rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dt
             }
             gather_reduce<double>(p, kept_items(pc), z64, nullptr, p->cs_lo_s.get(), df, br);
         }
+        shard_reduce(ctx, br, nvec);  // a shard's partial b, summed over the ranks
     }
 }
 
@@ -1653,6 +1748,7 @@ void pointing_apply_transpose(bm_pointing* p, const double* y, double* x) {
     plan_items(p->ctx, p->off.get(), nullptr, p->npix, it);
     const ItemsView v{it.pix.get(), it.beg.get(), it.len.get(), it.n, it.pitem.get()};
     gather_reduce<double>(p, v, y, nullptr, p->cs_lo_s.get(), false, x);
+    shard_reduce(p->ctx, x, p->npix * p->ncomp);
     BM_CUDA(cudaStreamSynchronize(p->ctx->stream));
 }
 

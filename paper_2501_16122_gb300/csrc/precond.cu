@@ -299,6 +299,69 @@ __device__ __forceinline__ void eig_sym3(const double a[6], double& lmin, double
     lmax = fmax(m[0][0], fmax(m[1][1], m[2][2]));
 }
 
+// Eigenvalue extremes, condition number, mask, the block and its inverse of
+// pixel p from its block sums a (the NS upper-triangle entries) and its hit
+// count: Eq. 7 with the mask rule of the build's reading (hits < min_hits,
+// or, for QU and IQU, lambda_min <= 0 or cond > max_cond).
+template <int NC>
+__device__ __forceinline__ void decide_block(int64_t p, const double* a, int32_t hits, int32_t min_hits,
+                                             double max_cond, double* __restrict__ B, double* __restrict__ Minv,
+                                             double* __restrict__ cond, uint8_t* __restrict__ mask) {
+    double lmin, lmax;
+    if (NC == 3) {
+        eig_sym3(a, lmin, lmax);
+    } else if (NC == 2) {
+        const double m = 0.5 * (a[0] + a[2]);
+        const double h = 0.5 * (a[0] - a[2]);
+        const double rad = sqrt(h * h + a[1] * a[1]);
+        lmax = m + rad;
+        lmin = m - rad;
+    } else {
+        lmin = lmax = a[0];
+    }
+    const double c = lmin > 0.0 ? lmax / lmin : INFINITY;
+    bool bad = hits < min_hits;
+    if (NC > 1) bad = bad || !(lmin > 0.0) || c > max_cond;
+    else bad = bad || !(a[0] > 0.0);
+    cond[p] = c;
+    mask[p] = bad ? 1 : 0;
+    double* Bp = B + p * NC * NC;
+    double* Mp = Minv + p * NC * NC;
+    if (NC == 3) {
+        const double b[9] = {a[0], a[1], a[2], a[1], a[3], a[4], a[2], a[4], a[5]};
+#pragma unroll
+        for (int j = 0; j < 9; ++j) Bp[j] = b[j];
+        if (bad) {
+#pragma unroll
+            for (int j = 0; j < 9; ++j) Mp[j] = 0.0;
+        } else {
+            const double c00 = a[3] * a[5] - a[4] * a[4];
+            const double c01 = a[2] * a[4] - a[1] * a[5];
+            const double c02 = a[1] * a[4] - a[2] * a[3];
+            const double c11 = a[0] * a[5] - a[2] * a[2];
+            const double c12 = a[1] * a[2] - a[0] * a[4];
+            const double c22 = a[0] * a[3] - a[1] * a[1];
+            const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+            const double id = 1.0 / det;
+            const double m[9] = {c00 * id, c01 * id, c02 * id, c01 * id, c11 * id,
+                                 c12 * id, c02 * id, c12 * id, c22 * id};
+#pragma unroll
+            for (int j = 0; j < 9; ++j) Mp[j] = m[j];
+        }
+    } else if (NC == 2) {
+        Bp[0] = a[0]; Bp[1] = a[1]; Bp[2] = a[1]; Bp[3] = a[2];
+        if (bad) {
+            Mp[0] = Mp[1] = Mp[2] = Mp[3] = 0.0;
+        } else {
+            const double id = 1.0 / (a[0] * a[2] - a[1] * a[1]);
+            Mp[0] = a[2] * id; Mp[1] = -a[1] * id; Mp[2] = -a[1] * id; Mp[3] = a[0] * id;
+        }
+    } else {
+        Bp[0] = a[0];
+        Mp[0] = bad ? 0.0 : 1.0 / a[0];
+    }
+}
+
 template <int NC>
 __global__ void finalize_blocks_kernel(const int64_t* __restrict__ pitem, const double* __restrict__ partial,
                                        const int32_t* __restrict__ hits, int64_t npix, int32_t min_hits,
@@ -313,59 +376,47 @@ __global__ void finalize_blocks_kernel(const int64_t* __restrict__ pitem, const 
         for (int64_t k = pitem[p]; k < pitem[p + 1]; ++k)
 #pragma unroll
             for (int j = 0; j < NS; ++j) a[j] += partial[k * NS + j];
-        double lmin, lmax;
-        if (NC == 3) {
-            eig_sym3(a, lmin, lmax);
-        } else if (NC == 2) {
-            const double m = 0.5 * (a[0] + a[2]);
-            const double h = 0.5 * (a[0] - a[2]);
-            const double rad = sqrt(h * h + a[1] * a[1]);
-            lmax = m + rad;
-            lmin = m - rad;
-        } else {
-            lmin = lmax = a[0];
-        }
-        const double c = lmin > 0.0 ? lmax / lmin : INFINITY;
-        bool bad = hits[p] < min_hits;
-        if (NC > 1) bad = bad || !(lmin > 0.0) || c > max_cond;
-        else bad = bad || !(a[0] > 0.0);
-        cond[p] = c;
-        mask[p] = bad ? 1 : 0;
-        double* Bp = B + p * NC * NC;
-        double* Mp = Minv + p * NC * NC;
-        if (NC == 3) {
-            const double b[9] = {a[0], a[1], a[2], a[1], a[3], a[4], a[2], a[4], a[5]};
+        decide_block<NC>(p, a, hits[p], min_hits, max_cond, B, Minv, cond, mask);
+    }
+}
+
+// Sharded build, first half: this rank's block sums of every pixel and its
+// hit count, S[p] = (a_0 .. a_{NS-1}, hits), summed over the item partials in
+// the same order as finalize_blocks_kernel.
+template <int NC>
+__global__ void block_sums_kernel(const int64_t* __restrict__ pitem, const double* __restrict__ partial,
+                                  const int32_t* __restrict__ hits, int64_t npix, double* __restrict__ S) {
+    constexpr int NS = NC * (NC + 1) / 2;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double a[NS];
 #pragma unroll
-            for (int j = 0; j < 9; ++j) Bp[j] = b[j];
-            if (bad) {
+        for (int j = 0; j < NS; ++j) a[j] = 0.0;
+        for (int64_t k = pitem[p]; k < pitem[p + 1]; ++k)
 #pragma unroll
-                for (int j = 0; j < 9; ++j) Mp[j] = 0.0;
-            } else {
-                const double c00 = a[3] * a[5] - a[4] * a[4];
-                const double c01 = a[2] * a[4] - a[1] * a[5];
-                const double c02 = a[1] * a[4] - a[2] * a[3];
-                const double c11 = a[0] * a[5] - a[2] * a[2];
-                const double c12 = a[1] * a[2] - a[0] * a[4];
-                const double c22 = a[0] * a[3] - a[1] * a[1];
-                const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
-                const double id = 1.0 / det;
-                const double m[9] = {c00 * id, c01 * id, c02 * id, c01 * id, c11 * id,
-                                     c12 * id, c02 * id, c12 * id, c22 * id};
+            for (int j = 0; j < NS; ++j) a[j] += partial[k * NS + j];
 #pragma unroll
-                for (int j = 0; j < 9; ++j) Mp[j] = m[j];
-            }
-        } else if (NC == 2) {
-            Bp[0] = a[0]; Bp[1] = a[1]; Bp[2] = a[1]; Bp[3] = a[2];
-            if (bad) {
-                Mp[0] = Mp[1] = Mp[2] = Mp[3] = 0.0;
-            } else {
-                const double id = 1.0 / (a[0] * a[2] - a[1] * a[1]);
-                Mp[0] = a[2] * id; Mp[1] = -a[1] * id; Mp[2] = -a[1] * id; Mp[3] = a[0] * id;
-            }
-        } else {
-            Bp[0] = a[0];
-            Mp[0] = bad ? 0.0 : 1.0 / a[0];
-        }
+        for (int j = 0; j < NS; ++j) S[p * (NS + 1) + j] = a[j];
+        S[p * (NS + 1) + NS] = (double)hits[p];
+    }
+}
+
+// Sharded build, second half: the decision of every pixel from the block
+// sums and hit counts summed over the ranks; the global hit counts are kept.
+template <int NC>
+__global__ void finalize_block_sums_kernel(const double* __restrict__ S, int64_t npix, int32_t min_hits,
+                                           double max_cond, double* __restrict__ B, double* __restrict__ Minv,
+                                           double* __restrict__ cond, uint8_t* __restrict__ mask,
+                                           int32_t* __restrict__ hits_out) {
+    constexpr int NS = NC * (NC + 1) / 2;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double a[NS];
+#pragma unroll
+        for (int j = 0; j < NS; ++j) a[j] = S[p * (NS + 1) + j];
+        const int32_t h = (int32_t)S[p * (NS + 1) + NS];
+        hits_out[p] = h;
+        decide_block<NC>(p, a, h, min_hits, max_cond, B, Minv, cond, mask);
     }
 }
 
@@ -394,7 +445,10 @@ void build_precond(bm_precond* pc) {
         DevBuf<double> partial((all.n > 0 ? all.n : 1) * ns);
         // the weighted sorted stream: white noise, and the offset template's
         // mixed operator (its white part)
-        const bool white = (diagonal_noise(n) || n->kind == 3) && p->nvalid > 0;
+        // (not for a half-wave-plate pointing with per-detector white noise
+        // in QU or IQU: its FP32 matvec rebuilds the angle from the model)
+        const bool white = (diagonal_noise(n) || n->kind == 3) && p->nvalid > 0 &&
+                           !(p->hwp && n->kind == 0 && nc > 1);
         if (n->kind == 2 && p->nvalid > 0) {  // a weight per sample: gathered once into sorted order
             pc->ws_df.alloc(p->nvalid);
             pc->ws_sqrt.alloc(p->nvalid);
@@ -441,19 +495,45 @@ void build_precond(bm_precond* pc) {
             BM_LAUNCH_CHECK();
         }
         const int pgrid = grid_for(ctx, (npix + threads - 1) / threads, 16);
+        if (!ctx->allreduce) {
 #define BM_FIN(NC)                                                                                       \
     finalize_blocks_kernel<NC><<<pgrid, threads, 0, s>>>(all.pitem.get(), partial.get(), p->hits.get(),  \
                                                          npix, pc->min_hits, pc->max_cond, pc->B.get(), \
                                                          pc->Minv.get(), pc->cond.get(), pc->mask.get())
-        if (nc == 3) BM_FIN(3);
-        else if (nc == 2) BM_FIN(2);
-        else BM_FIN(1);
+            if (nc == 3) BM_FIN(3);
+            else if (nc == 2) BM_FIN(2);
+            else BM_FIN(1);
 #undef BM_FIN
-        BM_LAUNCH_CHECK();
+            BM_LAUNCH_CHECK();
+            pc->hits_global.release();
+        } else {
+            // a shard: this rank's block sums and hit counts, summed over
+            // the ranks, then the decisions (the same on every rank)
+            DevBuf<double> S(npix * (ns + 1));
+            pc->hits_global.alloc(npix);
+#define BM_SUMS(NC)                                                                                                   \
+    block_sums_kernel<NC><<<pgrid, threads, 0, s>>>(all.pitem.get(), partial.get(), p->hits.get(), npix, S.get())
+            if (nc == 3) BM_SUMS(3);
+            else if (nc == 2) BM_SUMS(2);
+            else BM_SUMS(1);
+#undef BM_SUMS
+            BM_LAUNCH_CHECK();
+            shard_reduce(ctx, S.get(), npix * (ns + 1));
+#define BM_FINS(NC)                                                                                                \
+    finalize_block_sums_kernel<NC><<<pgrid, threads, 0, s>>>(S.get(), npix, pc->min_hits, pc->max_cond,             \
+                                                             pc->B.get(), pc->Minv.get(), pc->cond.get(),         \
+                                                             pc->mask.get(), pc->hits_global.get())
+            if (nc == 3) BM_FINS(3);
+            else if (nc == 2) BM_FINS(2);
+            else BM_FINS(1);
+#undef BM_FINS
+            BM_LAUNCH_CHECK();
+        }
         if (with_rhs) {
             finalize_rhs_kernel<<<pgrid, threads, 0, s>>>(all.pitem.get(), rpartial.get(), pc->mask.get(), npix, nc,
                                                           pc->b_tod.get());
             BM_LAUNCH_CHECK();
+            shard_reduce(ctx, pc->b_tod.get(), npix * nc);
         }
         BM_CUDA(cudaStreamSynchronize(s));
     }

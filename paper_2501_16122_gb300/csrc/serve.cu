@@ -52,10 +52,14 @@ int64_t estimate_bytes(const bm_request& r) {
     const bool trig = r.cos2psi != nullptr;
     int64_t per_sample = 4 + 4 + (trig ? 16 : 32);  // pix, perm, trig (time + sorted; hi [+ lo])
     per_sample += 16;                               // radix-sort scratch during ingest
-    per_sample += (r.noise == BM_NOISE_WHITE) ? 8 : 12;  // weighted stream | filtered z (f32 + f64)
-    if (r.noise == BM_NOISE_TOEPLITZ) per_sample += 4;
+    // white: the weighted stream; Toeplitz: the filter's time-ordered y and
+    // z (FP32 and FP64) and the chunk-major order of the inner transpose
+    // (each sample's position and trig pair)
+    per_sample += (r.noise == BM_NOISE_WHITE) ? 8 : 24 + 12;
     const int64_t per_pixel = 12 + 2 * 8 * nc * nc + 9 + 8 + 16 + 12 * 8 * nc;
-    return ns * per_sample + np * per_pixel + (int64_t(64) << 20);
+    int64_t tmp = 0;  // the chunk-major order's build tables (at most 4 GiB, else not built)
+    if (r.noise == BM_NOISE_TOEPLITZ) tmp = std::min<int64_t>(((ns >> 24) + 1) * 16 * np + 8 * np, int64_t(1) << 32);
+    return ns * per_sample + np * per_pixel + tmp + (int64_t(64) << 20);
 }
 
 }  // namespace

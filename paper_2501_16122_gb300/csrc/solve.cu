@@ -458,7 +458,7 @@ bm_status pcg_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void*
     bm_context* ctx = p->ctx;
     const int nc = p->ncomp;
     const int64_t nvec = p->npix * nc;
-    if (nrhs > 1 && n->kind == 0 && prec == BM_PREC_MIXED) {
+    if (nrhs > 1 && n->kind == 0 && prec == BM_PREC_MIXED && !ctx->allreduce) {
         const bm_status st = batched_white_solve(p, n, pc, tod, dt, nrhs, map_out, tol, maxiter, info);
         if (st != BM_OK) set_error("at least one right-hand side did not converge (%s)", bm_status_string(st));
         return st;

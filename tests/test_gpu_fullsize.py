@@ -104,6 +104,31 @@ def test_config1_full_size(L, ctx):
         assert err < 1e-6, (k, err)
     for h, f in ((pc, L.bm_precond_destroy), (n, L.bm_inv_noise_destroy), (p, L.bm_pointing_destroy)):
         f(h)
+    del d_pix
+    gc.collect()
+    torch.cuda.empty_cache()
+
+    # The benchmarked path itself: pix, the trig pair and the TOD given as
+    # page-locked host buffers, the TOD carried through the pixel sort and
+    # read in sorted order by the RHS (the bench's end-to-end step).  Same
+    # values summed in the same order: the map must equal the one above bit
+    # for bit, and so meet the oracle on the sampled pixels.
+    h_pix = torch.from_numpy(pt["pix"]).pin_memory()
+    h_c, h_s = torch.from_numpy(c32).pin_memory(), torch.from_numpy(s32).pin_memory()
+    h_tod = torch.from_numpy(tod).pin_memory()
+    p2 = L.bm_pointing_create_with_tod(ctx, e.npix, h_pix, h_tod, cos2psi=h_c, sin2psi=h_s)
+    n2 = L.bm_inv_noise_create_diag(ctx, e.det_offsets, 1 / e.sigma ** 2)
+    pc2 = L.bm_blockdiag_precond_create(p2, n2, 3, 1e3)
+    out2 = torch.full_like(out, float("nan"))
+    st2, info2 = L.bm_pcg_solve(p2, n2, pc2, None, 1, out2, 1e-8, 200, L.BM_PREC_MIXED)
+    assert st2 == L.BM_OK and info2[0]["rel_residual"] <= 1e-8
+    a, b = out.cpu().numpy(), out2.cpu().numpy()
+    assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+    x2 = b.reshape(e.npix, 3)[pixels]
+    for k in range(3):
+        assert np.linalg.norm(x2[:, k] - ref[:, k]) / np.linalg.norm(ref[:, k]) < 1e-6
+    for h, f in ((pc2, L.bm_precond_destroy), (n2, L.bm_inv_noise_destroy), (p2, L.bm_pointing_destroy)):
+        f(h)
 
 
 def oracle_toeplitz_matvec_pixels(e, pix, c32, s32, coeffs, chunk, mask, x, pixels):

@@ -46,8 +46,10 @@ def _worker(rank, world, port, noise_kind, results):
         e, pt, S = _system(noise_kind)
         x = np.random.default_rng(7).normal(size=(e.npix, 3))
         d = np.random.default_rng(8).normal(size=e.nsamples)
-        # this rank's detectors and their samples
-        mine = [k for k in range(e.ndet) if k % world == rank]
+        # this rank's detectors and their samples: the library's partition
+        from paper_2501_16122_gb300.shard import detector_shard
+        d0, d1, _ = detector_shard(e.det_offsets, rank, world)
+        mine = list(range(d0, d1))
         off = np.asarray(e.det_offsets)
         idx = np.concatenate([np.arange(off[k], off[k + 1]) for k in mine])
         sub_off = np.concatenate([[0], np.cumsum([off[k + 1] - off[k] for k in mine])])
@@ -86,3 +88,25 @@ def test_detector_sharding_sums_to_the_full_operator(noise_kind):
         assert p.exitcode == 0
     eq, eb = results.get(timeout=5)
     assert eq < 1e-13 and eb < 1e-13, (eq, eb)
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 5, 8])
+def test_detector_shard_partition(world):
+    """Every detector belongs to exactly one rank, in order, each rank at
+    least one, about as many samples each; the local offsets start at 0."""
+    from paper_2501_16122_gb300.shard import detector_shard
+    rng = np.random.default_rng(world)
+    lens = rng.integers(1, 1000, 13)
+    off = np.concatenate([[0], np.cumsum(lens)])
+    prev = 0
+    sizes = []
+    for r in range(world):
+        d0, d1, sub = detector_shard(off, r, world)
+        assert d0 == prev and d1 > d0
+        assert sub[0] == 0 and np.array_equal(sub, off[d0:d1 + 1] - off[d0])
+        sizes.append(off[d1] - off[d0])
+        prev = d1
+    assert prev == 13
+    assert max(sizes) <= off[-1] / world + lens.max()
+    with pytest.raises(ValueError):
+        detector_shard(off, 0, 14)
