@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--horizon", type=float, default=20.0, help="config4: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=20.0, help="config4: mean arrivals per second")
     ap.add_argument("--nrhs", type=int, default=64, help="config3: right-hand sides")
+    ap.add_argument("--slots", type=int, default=8, help="config4: requests the server runs at once")
     ap.add_argument("--no-fp64-solve", action="store_true", help="config2: skip the timed plain FP64 solve")
     ap.add_argument("--rhs-path", choices=["carried", "gather"], default="carried",
                     help="config1: the TOD sorted along with the pointing (carried, default) or "
@@ -250,9 +251,9 @@ KERNELS = {"ingest_validate": "validate_kernel", "ingest_hist": "rs_hist_kernel"
            "ingest_scatter": "rs_scatter_kernel", "blocks": "blocks_kernel", "rhs": "gather_reduce_kernel",
            "matvec_white_f32": "white_matvec_f32_kernel"}
 TRAFFIC = {
-    # profiles/ingest_sort_nside256_256x262144.md: 42.4 and 44.0 DRAM bytes
-    # per sample for the two scatter passes (mean 43.2) on the 67M-sample
-    # case; the traffic grows in proportion to the samples
+    # ncu on the 67M-sample case of the same scan (256 detectors x 262,144
+    # samples): 42.4 and 44.0 DRAM bytes per sample for the two scatter
+    # passes (mean 43.2); the traffic grows in proportion to the samples
     "ingest_scatter": lambda n: 43.2 * n,
 }
 

@@ -214,7 +214,7 @@ def run_config2(args, noise="toeplitz"):
     clocks = sampler.stop()
     fam = {}
     for name in ("ingest", "blocks", "rhs", "toeplitz_f32", "toeplitz_refine", "toeplitz_f64", "toeplitz_pt",
-                 "toeplitz_pt_bounds", "offset_filter_f64", "offset_means_f32",
+                 "toeplitz_pt_df", "toeplitz_pt_bounds", "offset_filter_f64", "offset_means_f32",
                  "offset_matvec_f32", "offset_means_df", "offset_pt_df", "ingest_validate", "ingest_hist",
                  "ingest_scatter"):
         tot, cnt = L.bm_context_kernel_time(ctx, name)
@@ -357,6 +357,7 @@ def run_config3(args):
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
     ctx = L.bm_context_create(0)
+    fp32_tf, _ = measured_fma_tflops(L, ctx)
     inv_var = 1 / e.sigma ** 2
     out = torch.zeros(R * e.npix * 3, dtype=torch.float64, device="cuda")
     one = torch.zeros(e.npix * 3, dtype=torch.float64, device="cuda")
@@ -388,7 +389,18 @@ def run_config3(args):
     launches = (L.bm_kernel_launches() - l0) / args.steps
     clocks = sampler.stop()
     rhs_ms, _ = L.bm_context_kernel_time(ctx, "rhs_batched")
+    mv_ms, mv_n = L.bm_context_kernel_time(ctx, "matvec_batched")
     L.bm_context_set_timing(ctx, False)
+    # the batched matvec's algorithmic bytes: the weighted trig stream once
+    # (8 B a kept sample) for all R right-hand sides, and per kept pixel the
+    # R FP32 x values (12 B each) read and the R FP64 results (24 B) written
+    hits = torch.empty(e.npix, dtype=torch.int32, device="cuda")
+    mask = torch.empty(e.npix, dtype=torch.uint8, device="cuda")
+    L.bm_precond_get_mask(h[2], mask, hits)
+    kept = mask == 0
+    n_kept_s, n_kept_p = int(hits[kept].sum().item()), int(kept.sum().item())
+    mv_bytes = 8 * n_kept_s + n_kept_p * R * (12 + 24)
+    mv_ms_l = mv_ms / max(mv_n, 1)
     # one right-hand side at a time, mixed and FP64 (timed on two RHS, scaled to R)
     t1 = time.perf_counter()
     for r in range(2):
@@ -419,6 +431,18 @@ def run_config3(args):
         "solve": {"status": st, "max_iterations": max(i["iterations"] for i in infos),
                   "max_rel_residual": max(i["rel_residual"] for i in infos)},
         "rhs0_rel_diff_vs_fp64_solve": agree,
+        # the batched matvec streams little (one pointing read for all R) and
+        # does ~11 FP32 flops per kept sample and right-hand side: its bound
+        # is the FP32 pipe; the HBM fraction is given beside it
+        "roofline": {"bound": "alu", "kernel": "batched_matvec_kernel (one pointing read for all R)",
+                     "ms_per_launch": mv_ms_l, "flops_per_launch": 11.0 * n_kept_s * R,
+                     "achieved": 11.0 * n_kept_s * R / (mv_ms_l * 1e-3) / 1e12 if mv_n else None,
+                     "peak": fp32_tf, "unit": "TFLOP/s",
+                     "frac": 11.0 * n_kept_s * R / (mv_ms_l * 1e-3) / 1e12 / fp32_tf if mv_n else None,
+                     "peak_basis": "measured FP32 FMA rate (bm_measure_fma_peak)",
+                     "bytes_per_launch": mv_bytes,
+                     "hbm_frac": mv_bytes / (mv_ms_l * 1e-3) / 1e9 / hbm_peak() if mv_n else None,
+                     "traffic": None},
         "clocks": clocks, "input_generation_s": t_gen,
     }
     print(json.dumps(line), flush=True)
@@ -497,7 +521,7 @@ def run_config4(args):
         return req, (keep, pix, c, s, tod, out)
 
     ctx = L.bm_context_create(0)
-    srv = L.bm_serve_create(ctx, 120 * 2 ** 30, 8)
+    srv = L.bm_serve_create(ctx, 120 * 2 ** 30, args.slots)
     done = []
     tickets = []
     lock = threading.Lock()
@@ -548,6 +572,10 @@ def run_config4(args):
     clocks = sampler.stop()
     stats = L.bm_serve_get_stats(srv)
     L.bm_serve_destroy(srv)
+    for x in tickets:  # the requests' device buffers go back to the device
+        x["bufs"] = None
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
 
     # The plain alternative: the same kind of requests solved one at a time in
     # FP64 (pointing, noise, preconditioner, FP64 PCG), on a seeded sample.
@@ -594,7 +622,7 @@ def run_config4(args):
         "value": samples / wall, "unit": "TOD samples/s",
         "config": {"workload": f"Poisson arrivals {args.rate}/s for {args.horizon} s, nside U{{64..512}}, "
                                f"ndet log-U[8,512], Ns 2^U[18,22], white or Toeplitz (p=1/2, fknee log-U[0.05,0.5]), "
-                               f"tol 1e-6, budget 120 GB, 8 slots", "requests": len(reqs)},
+                               f"tol 1e-6, budget 120 GB, {args.slots} slots", "requests": len(reqs)},
         "completed_ok": ok, "wall_s": wall, "offered_samples_per_s": samples / args.horizon,
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "p50_white": float(np.percentile(lw, 50)) if lw.size else None,

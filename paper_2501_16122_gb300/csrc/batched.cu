@@ -674,6 +674,11 @@ bm_status batched_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const v
 
     const Variant var = (pc->nitems > 0) ? autotune<NC>(ctx, pc, R, bb) : Variant{2, 4};
     const int per = 32 * var.rpl;
+    if (ctx->timing && pc->nitems > 0) {  // one batched matvec timed on its own (its roofline)
+        ScopedTimer timer(ctx, "matvec_batched");
+        for (int r0 = 0; r0 < R; r0 += per)
+            launch_matvec<NC>(ctx, pc, var, bb.x32, r0, std::min(per, R - r0), R, bb.q, bb.partial);
+    }
 
     // The inner iteration as a graph (captured on first use).
     cudaGraphExec_t gexec = nullptr;

@@ -80,6 +80,17 @@ struct DevBuf {
         void* p = nullptr;
         stream = tl_stream;
         cudaError_t e = cudaMallocAsync(&p, count * sizeof(T), stream);
+        if (e == cudaErrorMemoryAllocation) {
+            // the pool may hold memory freed by finished work: release it to
+            // the device once and retry
+            (void)cudaGetLastError();
+            int dev = 0;
+            cudaMemPool_t pool = nullptr;
+            if (cudaStreamSynchronize(stream) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+                cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess)
+                cudaMemPoolTrimTo(pool, 0);
+            e = cudaMallocAsync(&p, count * sizeof(T), stream);
+        }
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
             set_error("device allocation of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));

@@ -125,7 +125,22 @@ void shard_reduce(bm_context* ctx, double* buf, int64_t count) {
 
 void* workspace(bm_context* ctx, const char* name, size_t bytes) {
     auto& b = ctx->ws[name];
-    if (b.n < bytes) b.alloc_from(ctx->ws_pool, bytes + bytes / 8);  // stream-ordered: old users finish first
+    if (b.n < bytes) {
+        try {
+            b.alloc_from(ctx->ws_pool, bytes + bytes / 8);  // stream-ordered: old users finish first
+        } catch (const Error& e) {
+            if (e.status != BM_ERR_OOM) throw;
+            // memory freed elsewhere in the process may still be held by the
+            // device's default pool (or this context's own): give it back to
+            // the device and try once more
+            BM_CUDA(cudaDeviceSynchronize());
+            cudaMemPool_t def = nullptr;
+            if (cudaDeviceGetDefaultMemPool(&def, ctx->device) == cudaSuccess) cudaMemPoolTrimTo(def, 0);
+            if (ctx->ws_pool) cudaMemPoolTrimTo(ctx->ws_pool, 0);
+            clear_error();
+            b.alloc_from(ctx->ws_pool, bytes + bytes / 8);
+        }
+    }
     return b.get();
 }
 

@@ -64,7 +64,7 @@ __device__ __forceinline__ df32 fnum<df32, float2>(float2 v) { return {v.x, v.y}
 // An element as the output type.
 __device__ __forceinline__ float fout(float v) { return v; }
 __device__ __forceinline__ double fout(double v) { return v; }
-__device__ __forceinline__ double fout(df32 v) { return df_to_double(v); }
+__device__ __forceinline__ float2 fout(df32 v) { return make_float2(v.hi, v.lo); }
 
 // Padded shared-memory index: one spare entry after every 16.
 __device__ __forceinline__ int fpad(int a) { return a + (a >> 4); }
@@ -257,9 +257,9 @@ template <typename T> constexpr int kFftRadix = sizeof(T) == 4 ? 16 : 4;
 template <typename T> constexpr int kFftMaxM = sizeof(T) == 4 ? 4096 : 2048;
 
 // Table, spectrum and output types per element type: FP32 runs on FP32
-// tables; FP64 reads the FP64 tables; double-float reads its spectrum as
-// (hi, lo) pairs and the FP64 twiddles (converted once per block); both write
-// FP64.
+// tables; FP64 reads the FP64 tables and writes FP64; double-float reads its
+// spectrum as (hi, lo) pairs and the FP64 twiddles (converted once per block)
+// and writes (hi, lo) pairs.
 template <typename T> struct FftIO {
     using spec_t = double;
     using tw_t = double;
@@ -268,7 +268,7 @@ template <typename T> struct FftIO {
 template <> struct FftIO<df32> {
     using spec_t = float2;
     using tw_t = double;
-    using out_t = double;
+    using out_t = float2;  // the (hi, lo) pair itself: no FP64 conversion per sample
 };
 template <> struct FftIO<float> {
     using spec_t = float;
@@ -314,8 +314,8 @@ toeplitz_fft_kernel(Src src, const typename FftIO<T>::spec_t* __restrict__ spec,
         for (int n = threadIdx.x; n < M; n += kFftThreads) {
             const int64_t ta = b0 + 2 * n, tb = ta + 1;
             using V = decltype(src(ta));
-            const T ya = fnum<T>((ta >= cs && ta < ce) ? src(ta) : V(0));
-            const T yb = fnum<T>((tb >= cs && tb < ce) ? src(tb) : V(0));
+            const T ya = fnum<T>((ta >= cs && ta < ce) ? src(ta) : V{});
+            const T yb = fnum<T>((tb >= cs && tb < ce) ? src(tb) : V{});
             buf[fpad(n)] = {ya, yb};
         }
         __syncthreads();

@@ -61,13 +61,15 @@ __global__ void masked_copy4_kernel(const double* __restrict__ x, const uint8_t*
 // ---------------------------------- white, FP32 form, half-wave-plate angle
 // The same operator for a pointing whose angle follows the half-wave-plate
 // model (bm_pointing_create_hwp): per sorted sample the kernel reads only its
-// time index t (4 bytes), finds the detector d (looked up only when t passes
-// the current detector's end: a lane's samples of one pixel are in time
-// order), rebuilds (cos 2 theta, sin 2 theta) in FP32 from the exactly
-// reduced phase (hwp_trig_f32: a table of kHwpTab entries in shared memory
-// and a short polynomial), and accumulates w_d y v with y = v . x_p:
-// FP32 products, FP32 group sums of 8 samples folded into double-float, warp
-// sums in double-float, an FP64 partial per item.
+// time index t (4 bytes), finds its detector d (t / ns for equal detectors,
+// else a search of the offsets), rebuilds (cos 2 theta, sin 2 theta) in FP32
+// from the exactly reduced phase (hwp_turns32, hwp_trig32: a table of
+// kHwpTab entries and a short polynomial) and accumulates w_d y v with
+// y = v . x_p: FP32 products, FP32 group sums of 8 samples folded into
+// double-float, warp sums in double-float, an FP64 partial per item.  The
+// eight samples of a lane in flight are independent (each looks its
+// detector up); the per-detector angle offsets and weights sit in shared
+// memory up to kMaxDetSmem detectors.
 template <int NC>
 __global__ void __launch_bounds__(kWarps * 32)
 white_matvec_hwp_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ item_beg,
@@ -76,7 +78,15 @@ white_matvec_hwp_kernel(const int32_t* __restrict__ item_pix, const int64_t* __r
                         const float* __restrict__ x32, double* __restrict__ partial) {
     static_assert(NC > 1, "I-only maps do not depend on the angle");
     __shared__ float2 tab[kHwpTab];
+    __shared__ uint32_t s_a0[kMaxDetSmem];
+    __shared__ float s_w[kMaxDetSmem];
     for (int j = threadIdx.x; j < kHwpTab; j += blockDim.x) tab[j] = tab_g[j];
+    const bool in_smem = m.ndet <= kMaxDetSmem;
+    if (in_smem)
+        for (int d = threadIdx.x; d < m.ndet; d += blockDim.x) {
+            s_a0[d] = (uint32_t)(m.turn0[d] >> 32);
+            s_w[d] = wdf[d].x;
+        }
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * kWarps;
@@ -89,17 +99,11 @@ white_matvec_hwp_kernel(const int32_t* __restrict__ item_pix, const int64_t* __r
         else { xQ = x32[2 * p]; xU = x32[2 * p + 1]; }
         float aI = 0.f, aQ = 0.f, aU = 0.f;
         df32 AI = {0.f, 0.f}, AQ = {0.f, 0.f}, AU = {0.f, 0.f};
-        // the current detector's end, first sample, angle offset and weight
-        uint32_t dend = 0, dbeg = 0, a0 = 0;
-        float w = 0.f;
         auto step = [&](uint32_t t) {
-            if (t >= dend) {
-                const int d = det_of(m.off, m.ndet, m.ns, m.inv_ns, t);
-                dbeg = m.ns ? (uint32_t)d * m.ns : m.off[d];
-                dend = m.ns ? dbeg + m.ns : m.off[d + 1];
-                a0 = (uint32_t)(__ldg(m.turn0 + d) >> 32);
-                w = __ldg(&wdf[d].x);
-            }
+            const int d = det_of(m.off, m.ndet, m.ns, m.inv_ns, t);
+            const uint32_t dbeg = m.ns ? (uint32_t)d * m.ns : m.off[d];
+            const uint32_t a0 = in_smem ? s_a0[d] : (uint32_t)(m.turn0[d] >> 32);
+            const float w = in_smem ? s_w[d] : wdf[d].x;
             const float2 cs = hwp_trig32(hwp_turns32(m.nu, a0, t - dbeg), tab);
             float y = fmaf(cs.x, xQ, cs.y * xU);
             if (NC == 3) y += xI;
@@ -118,12 +122,12 @@ white_matvec_hwp_kernel(const int32_t* __restrict__ item_pix, const int64_t* __r
         for (; i + 224 < len; i += 256) {  // eight samples a lane, their loads issued together
             uint32_t t[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) t[u] = __ldg(perm + b + i + 32 * u);
+            for (int u = 0; u < 8; ++u) t[u] = __ldcs(perm + b + i + 32 * u);
 #pragma unroll
             for (int u = 0; u < 8; ++u) step(t[u]);
             fold();
         }
-        for (; i < len; i += 32) step(__ldg(perm + b + i));
+        for (; i < len; i += 32) step(__ldcs(perm + b + i));
         fold();
         AQ = df_warp_sum(AQ);
         AU = df_warp_sum(AU);
@@ -604,6 +608,88 @@ pt_chunk_kernel(const int32_t* __restrict__ seg_pix, const uint32_t* __restrict_
     }
 }
 
+// The double-float form of the chunk transpose (the refinement operator's and
+// the RHS's pixel sums of z given as (hi, lo) pairs, for exact FP32 trig):
+// chunk c's samples with time index in [t_lo, t_hi) -- half a chunk, so that
+// the 64 MB of z pairs it gathers stay in L2 -- of each segment (a prefix or
+// a suffix of it: its samples are in time order, found by a binary search),
+// summed in the lazily renormalised double-float form of the gather-reduce
+// (rhs_term_lazy) by kPtLanes lanes per segment, then added to the pixel's
+// double-float accumulator (one writer per launch; launches in time order).
+template <int NC>
+__global__ void __launch_bounds__(kWarps * 32)
+pt_chunk_df_kernel(const int32_t* __restrict__ seg_pix, const uint32_t* __restrict__ seg_beg,
+                   const int32_t* __restrict__ seg_len, int64_t seg0, int64_t nseg, uint32_t t_lo, uint32_t t_hi,
+                   const uint32_t* __restrict__ cm_t, const float2* __restrict__ cm_cs,
+                   const float2* __restrict__ z, float2* __restrict__ acc) {
+    constexpr int G = 32 / kPtLanes;
+    constexpr int U = 4;
+    const int lane = threadIdx.x & 31, gl = lane % kPtLanes, grp = lane / kPtLanes;
+    const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+    for (int64_t kw = ((int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5)) * G; kw < nseg; kw += nwarps * G) {
+        const int64_t k = kw + grp;
+        int64_t p = 0, b = 0;
+        int32_t i_lo = 0, i_hi = 0;
+        if (k < nseg) {
+            p = seg_pix[seg0 + k];
+            b = seg_beg[seg0 + k];
+            const int32_t len = seg_len[seg0 + k];
+            // the segment's samples in [t_lo, t_hi): [first >= t_lo, first >= t_hi)
+            auto lower = [&](uint32_t tv) {
+                int32_t lo = 0, hi = len;
+                while (lo < hi) {
+                    const int32_t mid = (lo + hi) >> 1;
+                    if (__ldg(cm_t + b + mid) < tv) lo = mid + 1; else hi = mid;
+                }
+                return lo;
+            };
+            i_lo = lower(t_lo);
+            i_hi = lower(t_hi);
+        }
+        df32 A[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) A[c] = {0.f, 0.f};
+        int nadd = 0;
+        for (int32_t i0 = i_lo; i0 < i_hi; i0 += U * kPtLanes) {
+            uint32_t t[U];
+            float2 h[U], v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int32_t i = i0 + gl + u * kPtLanes;
+                t[u] = i < i_hi ? __ldcs(cm_t + b + i) : 0xFFFFFFFFu;
+                h[u] = (NC > 1 && i < i_hi) ? __ldcs(cm_cs + b + i) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = t[u] != 0xFFFFFFFFu ? z[t[u]] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (t[u] != 0xFFFFFFFFu) {
+                    rhs_term_lazy<NC>(A, v[u].x, v[u].y, false, make_float2(0.f, 0.f), h[u], make_float2(0.f, 0.f));
+                    if (++nadd == kLazyNorm) {
+                        nadd = 0;
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) acc_norm(A[c]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            acc_norm(A[c]);
+#pragma unroll
+            for (int o = kPtLanes / 2; o > 0; o >>= 1) A[c] = df_add(A[c], df_shfl_xor(A[c], o));
+        }
+        if (gl == 0 && i_hi > i_lo) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const float2 old = acc[p * NC + c];
+                const df32 s = df_add(df32{old.x, old.y}, A[c]);
+                acc[p * NC + c] = make_float2(s.hi, s.lo);
+            }
+        }
+    }
+}
+
 __global__ void pt_finalize_kernel(const float2* __restrict__ acc, const uint8_t* __restrict__ mask, int64_t npix,
                                    int nc, double* __restrict__ q) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x)
@@ -655,6 +741,40 @@ struct SrcPlainF32 {
     const float* y;
     __device__ float operator()(int64_t t) const { return y[t]; }
 };
+struct SrcPlainDF {  // a double-float (hi, lo) pair per sample
+    const float2* y;
+    __device__ float2 operator()(int64_t t) const { return y[t]; }
+};
+
+// y = P x over every sample in double-float on the FP32 pipes (the
+// refinement operator's input): the trig pair as (hi, lo) (lo absent: the
+// exact FP32 values), the map as masked_copy_df_kernel writes it (two float4
+// of (hi, lo) pairs per pixel: I, Q; U, 0); y written as
+// (hi, lo) pairs.  Flagged samples and masked pixels give 0.
+__global__ void pointing_apply_df_kernel(const int32_t* __restrict__ pix, const float2* __restrict__ hi,
+                                         const float2* __restrict__ lo, int64_t n, const float4* __restrict__ x2,
+                                         float2* __restrict__ y) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p = pix[t];
+        df32 v = {0.f, 0.f};
+        if (p >= 0) {
+            const float2 h = hi[t];
+            const float2 l = lo ? lo[t] : make_float2(0.f, 0.f);
+            const float4 u = x2[2 * (int64_t)p], w = x2[2 * (int64_t)p + 1];
+            const df32 c = {h.x, l.x}, s = {h.y, l.y};
+            v = df_add(df_add(df32{u.x, u.y}, df_mul(c, df32{u.z, u.w})), df_mul(s, df32{w.x, w.y}));
+        }
+        y[t] = make_float2(v.hi, v.lo);
+    }
+}
+
+// z (FP64) -> (hi, lo) pairs.
+__global__ void to_df_kernel(const double* __restrict__ z, int64_t n, float2* __restrict__ out) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const df32 v = df_from(z[t]);
+        out[t] = make_float2(v.hi, v.lo);
+    }
+}
 
 // y = P x over every sample in FP32, from the padded map x4 (zero on masked
 // pixels, so their samples give 0; flagged samples give 0): the filter's
@@ -910,14 +1030,33 @@ static void apply_toeplitz_f32(bm_inv_noise* n, const Src& src, float* z) {
 // df: the FFT in double-float on the FP32 pipes (~48-bit arithmetic, for the
 // refinement operator of the mixed solve) instead of FP64.
 template <class Src>
-static void apply_toeplitz_f64(bm_inv_noise* n, const Src& src, double* z, bool df = false) {
+static void apply_toeplitz_f64(bm_inv_noise* n, const Src& src, double* z) {
     const auto* tw = reinterpret_cast<const cpx<double>*>(n->tw64.get());
-    if (n->fft_n64 && df)
-        run_toeplitz_fft<df32>(n, src, n->fft_n64, n->spec_df.get(), tw, z);
-    else if (n->fft_n64)
+    if (n->fft_n64)
         run_toeplitz_fft<double>(n, src, n->fft_n64, n->spec64.get(), tw, z);
     else
         run_toeplitz<double, 4>(n, src, n->coeffs64.get(), z);
+}
+// A sample source read as FP64 (for the direct filter of short bands).
+template <class Src>
+struct SrcAsF64 {
+    Src src;
+    __device__ double operator()(int64_t t) const { return as_f64(src(t)); }
+};
+// The same in double-float, z as (hi, lo) pairs (the mixed path's RHS and
+// refinement operator): the FFT form in double-float on the FP32 pipes; the
+// direct filter (short bands) in FP64, converted.
+template <class Src>
+static void apply_toeplitz_df(bm_inv_noise* n, const Src& src, float2* z) {
+    if (n->fft_n64) {
+        const auto* tw = reinterpret_cast<const cpx<double>*>(n->tw64.get());
+        run_toeplitz_fft<df32>(n, src, n->fft_n64, n->spec_df.get(), tw, z);
+    } else {
+        double* z64 = workspace_as<double>(n->ctx, "z64_direct", n->nsamples);
+        run_toeplitz<double, 4>(n, SrcAsF64<Src>{src}, n->coeffs64.get(), z64);
+        to_df_kernel<<<grid_for(n->ctx, (n->nsamples + 255) / 256, 16), 256, 0, n->ctx->stream>>>(z64, n->nsamples, z);
+        BM_LAUNCH_CHECK();
+    }
 }
 
 // ----------------------------------------------------------- offset filter
@@ -1418,9 +1557,9 @@ static void apply_filter_f32(bm_inv_noise* n, const bm_precond*, const Src& src,
     apply_toeplitz_f32(n, src, z);  // the offset template's mixed operator is offset_matvec_mixed
 }
 template <class Src>
-static void apply_filter_f64(bm_inv_noise* n, const bm_precond* pc, const Src& src, double* z, bool df) {
+static void apply_filter_f64(bm_inv_noise* n, const bm_precond* pc, const Src& src, double* z) {
     if (n->kind == 3) run_offset_filter<double>(n, src, pc->ofs_inv.get(), z);
-    else apply_toeplitz_f64(n, src, z, df);
+    else apply_toeplitz_f64(n, src, z);
 }
 
 static void finalize(bm_context* ctx, const int64_t* pitem, const double* partial, int64_t npix, int nc,
@@ -1527,6 +1666,36 @@ static bool ensure_chunk_major(bm_pointing* p, bm_inv_noise* n, bm_precond* pc) 
         }
     }
     return pc->pt_nch > 0;
+}
+
+// q = P^T z for double-float z pairs in time order (exact FP32 trig), by
+// half chunks of the chunk-major order.
+static void pt_chunked_df(bm_pointing* p, bm_precond* pc, const float2* z, double* q) {
+    bm_context* ctx = p->ctx;
+    cudaStream_t s = ctx->stream;
+    const int nc = p->ncomp;
+    const int64_t npix = p->npix;
+    const int nch = pc->pt_nch;
+    float2* acc = workspace_as<float2>(ctx, "pt_acc", (size_t)npix * nc);
+    BM_CUDA(cudaMemsetAsync(acc, 0, sizeof(float2) * (size_t)npix * nc, s));
+    for (int c = 0; c < nch; ++c) {
+        const int64_t seg0 = pc->cseg[c], nseg = pc->cseg[c + 1] - seg0;
+        if (nseg == 0) continue;
+        const int64_t wunits = ((nseg + 3) / 4 + kWarps - 1) / kWarps;
+        for (int half = 0; half < 2; ++half) {
+            const uint64_t t0 = ((uint64_t)c << kPtChunkBits) + (uint64_t)half * (1u << (kPtChunkBits - 1));
+            const uint64_t t1 = std::min<uint64_t>(t0 + (1u << (kPtChunkBits - 1)), 0xFFFFFFFFull);
+#define BM_PTD(NC)                                                                                              \
+    pt_chunk_df_kernel<NC><<<resident_grid(ctx, pt_chunk_df_kernel<NC>, kWarps * 32, wunits), kWarps * 32, 0, s>>>( \
+        pc->seg_pix.get(), pc->seg_beg.get(), pc->seg_len.get(), seg0, nseg, (uint32_t)t0, (uint32_t)t1,          \
+        pc->cm_t.get(), pc->cm_cs.get(), z, acc)
+            if (nc == 3) BM_PTD(3); else if (nc == 2) BM_PTD(2); else BM_PTD(1);
+#undef BM_PTD
+            BM_LAUNCH_CHECK();
+        }
+    }
+    pt_finalize_kernel<<<grid_for(ctx, (npix + 255) / 256, 16), 256, 0, s>>>(acc, pc->mask.get(), npix, nc, q);
+    BM_LAUNCH_CHECK();
 }
 
 // q = P^T z for z in time order, by chunks of the chunk-major order.
@@ -1645,13 +1814,16 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
                 float* z32 = workspace_as<float>(ctx, "z32", p->nsamples);
                 {
                     ScopedTimer timer(ctx, "toeplitz_f32");
-                    float* y32 = workspace_as<float>(ctx, "y32", p->nsamples);
                     float4* x4 = workspace_as<float4>(ctx, "x4", p->npix);
                     masked_copy4_kernel<<<grid_for(ctx, (p->npix + threads - 1) / threads, 16), threads, 0, s>>>(
                         xr, pc->mask.get(), p->npix, nc, x4);
                     BM_LAUNCH_CHECK();
-                    pointing_apply_f32_kernel<<<grid_for(ctx, (p->nsamples + threads - 1) / threads, 16), threads, 0, s>>>(
-                        p->pix.get(), p->cs_hi_t.get(), p->nsamples, x4, y32);
+                    // y = P x in its own full-occupancy pass (formed inside the
+                    // FFT filter's load stage instead, its dependent map gather
+                    // left the filter latency-bound: 15.8 -> 23.7 ms at config 2)
+                    float* y32 = workspace_as<float>(ctx, "y32", p->nsamples);
+                    pointing_apply_f32_kernel<<<grid_for(ctx, (p->nsamples + threads - 1) / threads, 16), threads, 0,
+                                                s>>>(p->pix.get(), p->cs_hi_t.get(), p->nsamples, x4, y32);
                     BM_LAUNCH_CHECK();
                     apply_filter_f32(n, pc, SrcPlainF32{y32}, z32);
                 }
@@ -1659,24 +1831,41 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
                 ScopedTimer timer(ctx, "toeplitz_pt");
                 if (cm) pt_chunked(p, pc, z32, qr);
                 else gather_reduce_f32(p, kept_items(pc), z32, qr);
+            } else if (prec == kPrecRefine) {
+                // the refinement operator: P x, the filter and the pixel sums
+                // in double-float on the FP32 pipes, no FP64 per sample
+                float4* x2 = workspace_as<float4>(ctx, "x_df", 2 * p->npix);
+                float2* z2 = workspace_as<float2>(ctx, "z_df", p->nsamples);
+                masked_copy_df_kernel<<<grid_for(ctx, (p->npix + threads - 1) / threads, 16), threads, 0, s>>>(
+                    xr, pc->mask.get(), p->npix, nc, x2);
+                BM_LAUNCH_CHECK();
+                {
+                    ScopedTimer timer(ctx, "toeplitz_refine");
+                    float2* y2 = workspace_as<float2>(ctx, "y_df", p->nsamples);
+                    pointing_apply_df_kernel<<<grid_for(ctx, (p->nsamples + threads - 1) / threads, 16), threads, 0, s>>>(
+                        p->pix.get(), p->cs_hi_t.get(), p->cs_lo_t.get(), p->nsamples, x2, y2);
+                    BM_LAUNCH_CHECK();
+                    apply_toeplitz_df(n, SrcPlainDF{y2}, z2);
+                }
+                ScopedTimer timer(ctx, "toeplitz_pt_df");
+                if (p->cs_lo_s.get() == nullptr && ensure_chunk_major(p, n, pc)) pt_chunked_df(p, pc, z2, qr);
+                else gather_reduce<float2>(p, kept_items(pc), z2, nullptr, p->cs_lo_s.get(), true, qr);
             } else {
-                // FP64, or the refinement operator: the same with a
-                // double-float filter and pixel sums
-                const bool refine = prec == kPrecRefine;
+                // FP64: P x, the filter and the pixel sums in FP64
                 double* xm = workspace_as<double>(ctx, "xm", nvec);
                 double* z64 = workspace_as<double>(ctx, "z64", p->nsamples);
                 masked_copy_kernel<double><<<vgrid, threads, 0, s>>>(xr, pc->mask.get(), p->npix, nc, xm);
                 BM_LAUNCH_CHECK();
                 {
-                    ScopedTimer timer(ctx, refine ? "toeplitz_refine" : "toeplitz_f64");
+                    ScopedTimer timer(ctx, "toeplitz_f64");
                     double* y64 = workspace_as<double>(ctx, "y64", p->nsamples);
                     pointing_apply_kernel<<<grid_for(ctx, (p->nsamples + threads - 1) / threads, 16), threads, 0, s>>>(
                         p->pix.get(), p->cs_hi_t.get(), p->cs_lo_t.get(), p->nsamples, nc, xm, y64);
                     BM_LAUNCH_CHECK();
-                    apply_filter_f64(n, pc, SrcPlain{y64}, z64, refine);
+                    apply_filter_f64(n, pc, SrcPlain{y64}, z64);
                 }
                 ScopedTimer timer(ctx, "toeplitz_pt");
-                gather_reduce<double>(p, kept_items(pc), z64, nullptr, p->cs_lo_s.get(), refine, qr);
+                gather_reduce<double>(p, kept_items(pc), z64, nullptr, p->cs_lo_s.get(), false, qr);
             }
         }
         shard_reduce(ctx, qr, nvec);  // a shard's partial A x, summed over the ranks
@@ -1718,16 +1907,31 @@ void rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dt
                 run_offset_filter<double, SrcMaskedTod<double>, float2>(n, src, pc->ofs_inv.get(), z2);
             }
             gather_reduce<float2>(p, kept_items(pc), z2, nullptr, p->cs_lo_s.get(), true, br);
+        } else if (df && n->kind == 1) {
+            // the mixed path's Toeplitz RHS: filter and pixel sums in
+            // double-float, z as (hi, lo) pairs
+            float2* z2 = workspace_as<float2>(ctx, "z_df", p->nsamples);
+            if (dt == BM_F32) {
+                SrcMaskedTod<float> src{p->pix.get(), pc->mask.get(),
+                                        static_cast<const float*>(tod) + r * p->nsamples};
+                apply_toeplitz_df(n, src, z2);
+            } else {
+                SrcMaskedTod<double> src{p->pix.get(), pc->mask.get(),
+                                         static_cast<const double*>(tod) + r * p->nsamples};
+                apply_toeplitz_df(n, src, z2);
+            }
+            if (p->cs_lo_s.get() == nullptr && ensure_chunk_major(p, n, pc)) pt_chunked_df(p, pc, z2, br);
+            else gather_reduce<float2>(p, kept_items(pc), z2, nullptr, p->cs_lo_s.get(), true, br);
         } else {
             double* z64 = workspace_as<double>(ctx, "z64", p->nsamples);
             if (dt == BM_F32) {
                 SrcMaskedTod<float> src{p->pix.get(), pc->mask.get(),
                                         static_cast<const float*>(tod) + r * p->nsamples};
-                apply_filter_f64(n, pc, src, z64, df);
+                apply_filter_f64(n, pc, src, z64);
             } else {
                 SrcMaskedTod<double> src{p->pix.get(), pc->mask.get(),
                                          static_cast<const double*>(tod) + r * p->nsamples};
-                apply_filter_f64(n, pc, src, z64, df);
+                apply_filter_f64(n, pc, src, z64);
             }
             gather_reduce<double>(p, kept_items(pc), z64, nullptr, p->cs_lo_s.get(), df, br);
         }

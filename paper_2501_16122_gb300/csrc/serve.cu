@@ -337,6 +337,12 @@ void bm_serve_destroy(bm_server* s) {
     s->cv_work.notify_all();
     s->cv_done.notify_all();
     for (auto& w : s->workers) w.join();
+    // the workers' memory went back to the device's default pool, which
+    // keeps it cached: hand it back to the device
+    cudaMemPool_t pool = nullptr;
+    if (cudaSetDevice(s->device) == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess &&
+        cudaDeviceGetDefaultMemPool(&pool, s->device) == cudaSuccess)
+        cudaMemPoolTrimTo(pool, 0);
     delete s;
 }
 
