@@ -623,7 +623,12 @@ def run_config4(args):
         "config": {"workload": f"Poisson arrivals {args.rate}/s for {args.horizon} s, nside U{{64..512}}, "
                                f"ndet log-U[8,512], Ns 2^U[18,22], white or Toeplitz (p=1/2, fknee log-U[0.05,0.5]), "
                                f"tol 1e-6, budget 120 GB, {args.slots} slots", "requests": len(reqs)},
-        "completed_ok": ok, "wall_s": wall, "offered_samples_per_s": samples / args.horizon,
+        "completed_ok": ok,
+        "failed": [{"status": x["res"]["status"], "message": x["res"]["message"], "samples": x["samples"],
+                    "white": x["white"], "iterations": x["res"]["iterations"],
+                    "rel_residual": x["res"]["rel_residual"]}
+                   for x in tickets if x["res"]["status"] != L.BM_OK][:20],
+        "wall_s": wall, "offered_samples_per_s": samples / args.horizon,
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "p50_white": float(np.percentile(lw, 50)) if lw.size else None,
                        "p50_toeplitz": float(np.percentile(lt, 50)) if lt.size else None},

@@ -13,7 +13,8 @@
 // costs O(log N) flops instead of the 2L - 1 of the direct filter.
 //
 // The M-point transform runs in place in shared memory as Stockham passes of
-// radix 16 (8, 4 or 2 for the last one): a thread reads its R points, applies
+// radix 16 for FP32, 8 for double-float and 4 for FP64, then 8, 4 or 2 for
+// the last one: a thread reads its R points, applies
 // the pass twiddles, does the R-point DFT in registers, and after a barrier
 // writes the R results.  For radix R, current sub-transform size Ns and
 // j in [0, M/R), k = j mod Ns:
@@ -23,6 +24,8 @@
 // entry every 16 so that the first pass's stride-16 writes spread over the
 // banks.
 #pragma once
+
+#include <type_traits>
 
 #include "bm_internal.cuh"
 
@@ -162,7 +165,35 @@ __device__ __forceinline__ void fft_pass(cpx<T>* buf, int M, int Ns, const cpx<T
                 return x;
             };
             cpx<T>* w = v[bb];
-            if (R == 16) {
+            if (R == 16 && sizeof(T) == 4 && Ns > 1) {
+                // FP32: of the pass twiddles W^(r step) read only W^step,
+                // W^(2 step), W^(4 step), W^(8 step) from the table and form
+                // the others with at most two complex products (a few ulp;
+                // a quarter fewer shared-memory loads in this pass)
+                const cpx<T> t1 = twid<T>(tws, M, step, inv), t2 = twid<T>(tws, M, 2 * step, inv);
+                const cpx<T> t4 = twid<T>(tws, M, 4 * step, inv), t8 = twid<T>(tws, M, 8 * step, inv);
+                const cpx<T> t12 = cmul(t4, t8);
+#pragma unroll
+                for (int n2 = 0; n2 < 4; ++n2) {
+                    // the group's twiddles W^((4 n1 + n2) step), n1 = 0..3
+                    const cpx<T> base = n2 == 0 ? cpx<T>{fnum<T>(1.0f), fnum<T>(0.0f)}
+                                      : n2 == 1 ? t1 : n2 == 2 ? t2 : cmul(t1, t2);
+                    const cpx<T> g1 = n2 == 0 ? t4 : cmul(base, t4);
+                    const cpx<T> g2 = n2 == 0 ? t8 : cmul(base, t8);
+                    const cpx<T> g3 = n2 == 0 ? t12 : cmul(base, t12);
+                    w[n2] = buf[fpad(j + n2 * Q)];
+                    if (n2 > 0) w[n2] = cmul(w[n2], base);
+                    w[n2 + 4] = cmul(buf[fpad(j + (4 + n2) * Q)], g1);
+                    w[n2 + 8] = cmul(buf[fpad(j + (8 + n2) * Q)], g2);
+                    w[n2 + 12] = cmul(buf[fpad(j + (12 + n2) * Q)], g3);
+                    dft4<T, 4>(w + n2, inv);
+#pragma unroll
+                    for (int k1 = 1; k1 < 4; ++k1)
+                        if (n2 > 0) w[n2 + 4 * k1] = cmul(w[n2 + 4 * k1], w16<T>(n2 * k1, inv));
+                }
+#pragma unroll
+                for (int k1 = 0; k1 < 4; ++k1) dft4<T, 1>(w + 4 * k1, inv);
+            } else if (R == 16) {
                 // four groups x[4 n1 + n2] (n1 = 0..3): load, first DFT-4, inner twiddles
 #pragma unroll
                 for (int n2 = 0; n2 < 4; ++n2) {
@@ -205,13 +236,14 @@ constexpr int kFftThreads = 256;
 
 // M-point transform in place (M a power of two, M <= MMAX), forward or
 // inverse (unnormalised); ends with a barrier.  RMAX caps the radix: 16
-// (M <= 4096, one butterfly per thread and pass) or 4 (for FP64, whose
-// points take twice the registers; up to MMAX / (2 kFftThreads) butterflies
-// per thread).
+// (FP32; M <= 4096, one butterfly per thread and pass), 8 (double-float)
+// or 4 (FP64, whose radix-8 butterflies spill registers); up to
+// MMAX / (RMAX kFftThreads) butterflies per thread.
 template <typename T, int RMAX, int MMAX>
 __device__ __forceinline__ void fft_run(cpx<T>* buf, int M, const cpx<T>* tws, bool inv) {
-    static_assert(RMAX == 16 || RMAX == 4, "radix cap");
-    static_assert(RMAX == 4 || MMAX <= 16 * kFftThreads, "one radix-16 butterfly per thread");
+    static_assert(RMAX == 16 || RMAX == 8 || RMAX == 4, "radix cap");
+    static_assert(RMAX != 16 || MMAX <= 16 * kFftThreads, "one radix-16 butterfly per thread");
+    constexpr int NB8 = RMAX == 16 ? 1 : (MMAX / 8 + kFftThreads - 1) / kFftThreads;
     constexpr int NB4 = RMAX == 16 ? 1 : (MMAX / 4 + kFftThreads - 1) / kFftThreads;
     constexpr int NB2 = RMAX == 16 ? 1 : (MMAX / 2 + kFftThreads - 1) / kFftThreads;
     int Ns = 1;
@@ -220,8 +252,8 @@ __device__ __forceinline__ void fft_run(cpx<T>* buf, int M, const cpx<T>* tws, b
         if (RMAX == 16 && rem >= 16) {
             fft_pass<T, 16, 1>(buf, M, Ns, tws, inv);
             Ns *= 16;
-        } else if (RMAX == 16 && rem == 8) {
-            fft_pass<T, 8, 1>(buf, M, Ns, tws, inv);
+        } else if (RMAX >= 8 && rem >= 8) {
+            fft_pass<T, 8, NB8>(buf, M, Ns, tws, inv);
             Ns *= 8;
         } else if (rem >= 4) {
             fft_pass<T, 4, NB4>(buf, M, Ns, tws, inv);
@@ -253,7 +285,7 @@ __device__ __forceinline__ int fft_tile_det(const int64_t* ts, int ndet, int64_t
 
 // Radix cap and largest transform per element type (the host sizes the
 // FFT within these: N <= 8192 for FP32, N <= 4096 for FP64 and double-float).
-template <typename T> constexpr int kFftRadix = sizeof(T) == 4 ? 16 : 4;
+template <typename T> constexpr int kFftRadix = sizeof(T) == 4 ? 16 : (std::is_same<T, double>::value ? 4 : 8);
 template <typename T> constexpr int kFftMaxM = sizeof(T) == 4 ? 4096 : 2048;
 
 // Table, spectrum and output types per element type: FP32 runs on FP32
