@@ -150,7 +150,8 @@ __device__ __forceinline__ cpx<T> twid(const cpx<T>* tws, int M, int e, bool inv
 // butterflies (j = threadIdx.x + b blockDim.x), whose points it holds in
 // registers across the barrier between the reads and the writes.
 template <typename T, int R, int NB>
-__device__ __forceinline__ void fft_pass(cpx<T>* buf, int M, int Ns, const cpx<T>* tws, bool inv) {
+__device__ __forceinline__ void fft_pass(cpx<T>* buf, int M, int Ns, const cpx<T>* tws, bool inv,
+                                         const cpx<T>* ptw = nullptr) {
     const int Q = M / R;
     cpx<T> v[NB][R];
 #pragma unroll
@@ -170,8 +171,17 @@ __device__ __forceinline__ void fft_pass(cpx<T>* buf, int M, int Ns, const cpx<T
                 // W^(2 step), W^(4 step), W^(8 step) from the table and form
                 // the others with at most two complex products (a few ulp;
                 // a quarter fewer shared-memory loads in this pass)
-                const cpx<T> t1 = twid<T>(tws, M, step, inv), t2 = twid<T>(tws, M, 2 * step, inv);
-                const cpx<T> t4 = twid<T>(tws, M, 4 * step, inv), t8 = twid<T>(tws, M, 8 * step, inv);
+                // from the pass's own table ptw[e][k] = W^(2^e step(k)) (rows
+                // of Ns consecutive entries, so a warp's loads hit distinct
+                // banks), else from the shared table
+                cpx<T> t1, t2, t4, t8;
+                if (ptw) {
+                    t1 = ptw[k]; t2 = ptw[Ns + k]; t4 = ptw[2 * Ns + k]; t8 = ptw[3 * Ns + k];
+                    if (inv) { t1.y = -t1.y; t2.y = -t2.y; t4.y = -t4.y; t8.y = -t8.y; }
+                } else {
+                    t1 = twid<T>(tws, M, step, inv); t2 = twid<T>(tws, M, 2 * step, inv);
+                    t4 = twid<T>(tws, M, 4 * step, inv); t8 = twid<T>(tws, M, 8 * step, inv);
+                }
                 const cpx<T> t12 = cmul(t4, t8);
 #pragma unroll
                 for (int n2 = 0; n2 < 4; ++n2) {
@@ -240,7 +250,8 @@ constexpr int kFftThreads = 256;
 // or 4 (FP64, whose radix-8 butterflies spill registers); up to
 // MMAX / (RMAX kFftThreads) butterflies per thread.
 template <typename T, int RMAX, int MMAX>
-__device__ __forceinline__ void fft_run(cpx<T>* buf, int M, const cpx<T>* tws, bool inv) {
+__device__ __forceinline__ void fft_run(cpx<T>* buf, int M, const cpx<T>* tws, bool inv,
+                                        const cpx<T>* ptw = nullptr) {
     static_assert(RMAX == 16 || RMAX == 8 || RMAX == 4, "radix cap");
     static_assert(RMAX != 16 || MMAX <= 16 * kFftThreads, "one radix-16 butterfly per thread");
     constexpr int NB8 = RMAX == 16 ? 1 : (MMAX / 8 + kFftThreads - 1) / kFftThreads;
@@ -250,7 +261,8 @@ __device__ __forceinline__ void fft_run(cpx<T>* buf, int M, const cpx<T>* tws, b
     while (Ns < M) {
         const int rem = M / Ns;
         if (RMAX == 16 && rem >= 16) {
-            fft_pass<T, 16, 1>(buf, M, Ns, tws, inv);
+            fft_pass<T, 16, 1>(buf, M, Ns, tws, inv, (ptw && Ns > 1) ? ptw : nullptr);
+            if (ptw && Ns > 1) ptw += 4 * Ns;  // the next pass's table follows
             Ns *= 16;
         } else if (RMAX >= 8 && rem >= 8) {
             fft_pass<T, 8, NB8>(buf, M, Ns, tws, inv);
@@ -309,10 +321,18 @@ template <> struct FftIO<float> {
 };
 
 // Shared memory of the filter kernel: the padded buffer and the table.
+// Entries of the radix-16 passes' own twiddle tables (FP32): 4 Ns for every
+// radix-16 pass after the first.
+__host__ __device__ inline int fft_pass_tw_len(int M) {
+    int n = 0;
+    for (int Ns = 16; Ns * 16 <= M; Ns *= 16) n += 4 * Ns;
+    return n;
+}
 template <typename T>
 inline size_t fft_smem(int N) {
     const int M = N / 2;
-    return sizeof(cpx<T>) * ((size_t)fft_buf_len(M) + (size_t)M + 1);
+    const size_t ptw = sizeof(T) == 4 ? (size_t)fft_pass_tw_len(M) : 0;
+    return sizeof(cpx<T>) * ((size_t)fft_buf_len(M) + (size_t)M + 1 + ptw);
 }
 
 // One block of H = N - 2(L-1) outputs per iteration (grid-stride over blocks).
@@ -327,6 +347,22 @@ toeplitz_fft_kernel(Src src, const typename FftIO<T>::spec_t* __restrict__ spec,
     cpx<T>* buf = reinterpret_cast<cpx<T>*>(fft_smem_raw);
     cpx<T>* tws = buf + fft_buf_len(M);  // W_N^q, q = 0..M
     for (int q = threadIdx.x; q <= M; q += kFftThreads) tws[q] = {fnum<T>(tw[q].x), fnum<T>(tw[q].y)};
+    // FP32: each radix-16 pass after the first gets its own table of the
+    // twiddles W_M^(2^e step), e = 0..3, step = (M / (16 Ns)) k, for its
+    // Ns values of k (read by fft_pass without bank conflicts)
+    cpx<T>* ptw = nullptr;
+    if (sizeof(T) == 4) {
+        ptw = tws + M + 1;
+        __syncthreads();  // the shared table is complete
+        cpx<T>* t = ptw;
+        for (int Ns = 16; Ns * 16 <= M; Ns *= 16) {
+            for (int i = threadIdx.x; i < 4 * Ns; i += kFftThreads) {
+                const int e = i / Ns, k = i % Ns;
+                t[i] = twid<T>(tws, M, (1 << e) * (M / (16 * Ns)) * k, false);
+            }
+            t += 4 * Ns;
+        }
+    }
     const int H = N - 2 * (L - 1);
     const T inv_m = fnum<T>(typename FftIO<T>::tw_t(1) / typename FftIO<T>::tw_t(M));  // M = 2^k: exact
     const T half = fnum<T>(typename FftIO<T>::tw_t(0.5));
@@ -354,7 +390,7 @@ toeplitz_fft_kernel(Src src, const typename FftIO<T>::spec_t* __restrict__ spec,
         // forward transform, spectrum product, inverse transform: one copy of
         // the transform code serves both directions
         for (int dir = 0; dir < 2; ++dir) {
-            fft_run<T, kFftRadix<T>, kFftMaxM<T>>(buf, M, tws, dir == 1);
+            fft_run<T, kFftRadix<T>, kFftMaxM<T>>(buf, M, tws, dir == 1, ptw);
             if (dir == 1) break;
             const typename FftIO<T>::spec_t* K = spec + (int64_t)d * (M + 1);
             // Even/odd split, multiply by the real spectrum, re-pack for the
