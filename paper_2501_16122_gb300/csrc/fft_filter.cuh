@@ -162,7 +162,16 @@ __device__ __forceinline__ void fft_pass(cpx<T>* buf, int M, int Ns, const cpx<T
             const int step = (M / (Ns * R)) * k;  // W_{Ns R}^(r k) = W_M^(r step)
             auto load = [&](int r) {
                 cpx<T> x = buf[fpad(j + r * Q)];
-                if (r > 0 && Ns > 1) x = cmul(x, twid<T>(tws, M, r * step, inv));
+                if (r > 0 && Ns > 1) {
+                    cpx<T> t;
+                    if (ptw) {  // the pass's own table ptw[r - 1][k]
+                        t = ptw[(r - 1) * Ns + k];
+                        if (inv) t.y = -t.y;
+                    } else {
+                        t = twid<T>(tws, M, r * step, inv);
+                    }
+                    x = cmul(x, t);
+                }
                 return x;
             };
             cpx<T>* w = v[bb];
@@ -244,6 +253,39 @@ __device__ __forceinline__ void fft_pass(cpx<T>* buf, int M, int Ns, const cpx<T
 
 constexpr int kFftThreads = 256;
 
+// Radix cap and largest transform per element type (the host sizes the
+// FFT within these: N <= 8192 for FP32, N <= 4096 for FP64 and double-float).
+template <typename T> constexpr int kFftRadix = sizeof(T) == 4 ? 16 : (std::is_same<T, double>::value ? 4 : 8);
+template <typename T> constexpr int kFftMaxM = sizeof(T) == 4 ? 4096 : 2048;
+
+// The passes' own twiddle tables, one after another in pass order: FP32
+// (radix 16) has 4 Ns entries W^(2^e step), e = 0..3, for every radix-16
+// pass after the first (the other twiddles are products of these; a shorter
+// last pass reads the shared table); the 16-byte types have (R - 1) Ns
+// entries W^(r step), r = 1..R-1, for every pass after the first.  Ns
+// consecutive entries per row, so a warp's loads hit distinct banks.
+// fft_pass_tw_len gives their total length; the kernel and fft_run walk the
+// passes in the same order.
+template <typename T>
+__host__ __device__ inline int fft_next_radix(int rem) {
+    if (sizeof(T) == 4) return rem >= 16 ? 16 : rem >= 8 ? 8 : rem >= 4 ? 4 : 2;
+    if (kFftRadix<T> == 8 && rem >= 8) return 8;
+    return rem >= 4 ? 4 : 2;
+}
+template <typename T>
+__host__ __device__ inline int fft_pass_tw_rows(int R) {
+    return sizeof(T) == 4 ? (R == 16 ? 4 : 0) : R - 1;
+}
+template <typename T>
+__host__ __device__ inline int fft_pass_tw_len(int M) {
+    int n = 0;
+    for (int Ns = 1; Ns < M;) {
+        const int R = fft_next_radix<T>(M / Ns);
+        if (Ns > 1) n += fft_pass_tw_rows<T>(R) * Ns;
+        Ns *= R;
+    }
+    return n;
+}
 // M-point transform in place (M a power of two, M <= MMAX), forward or
 // inverse (unnormalised); ends with a barrier.  RMAX caps the radix: 16
 // (FP32; M <= 4096, one butterfly per thread and pass), 8 (double-float)
@@ -252,28 +294,22 @@ constexpr int kFftThreads = 256;
 template <typename T, int RMAX, int MMAX>
 __device__ __forceinline__ void fft_run(cpx<T>* buf, int M, const cpx<T>* tws, bool inv,
                                         const cpx<T>* ptw = nullptr) {
-    static_assert(RMAX == 16 || RMAX == 8 || RMAX == 4, "radix cap");
+    static_assert(RMAX == kFftRadix<T>, "the radix follows the element type");
     static_assert(RMAX != 16 || MMAX <= 16 * kFftThreads, "one radix-16 butterfly per thread");
     constexpr int NB8 = RMAX == 16 ? 1 : (MMAX / 8 + kFftThreads - 1) / kFftThreads;
     constexpr int NB4 = RMAX == 16 ? 1 : (MMAX / 4 + kFftThreads - 1) / kFftThreads;
     constexpr int NB2 = RMAX == 16 ? 1 : (MMAX / 2 + kFftThreads - 1) / kFftThreads;
     int Ns = 1;
     while (Ns < M) {
-        const int rem = M / Ns;
-        if (RMAX == 16 && rem >= 16) {
-            fft_pass<T, 16, 1>(buf, M, Ns, tws, inv, (ptw && Ns > 1) ? ptw : nullptr);
-            if (ptw && Ns > 1) ptw += 4 * Ns;  // the next pass's table follows
-            Ns *= 16;
-        } else if (RMAX >= 8 && rem >= 8) {
-            fft_pass<T, 8, NB8>(buf, M, Ns, tws, inv);
-            Ns *= 8;
-        } else if (rem >= 4) {
-            fft_pass<T, 4, NB4>(buf, M, Ns, tws, inv);
-            Ns *= 4;
-        } else {
-            fft_pass<T, 2, NB2>(buf, M, Ns, tws, inv);
-            Ns *= 2;
-        }
+        const int R = fft_next_radix<T>(M / Ns);
+        const int rows = fft_pass_tw_rows<T>(R);
+        const cpx<T>* pt = (ptw && Ns > 1 && rows) ? ptw : nullptr;
+        if (R == 16) fft_pass<T, 16, 1>(buf, M, Ns, tws, inv, pt);
+        else if (R == 8) fft_pass<T, 8, NB8>(buf, M, Ns, tws, inv, pt);
+        else if (R == 4) fft_pass<T, 4, NB4>(buf, M, Ns, tws, inv, pt);
+        else fft_pass<T, 2, NB2>(buf, M, Ns, tws, inv, pt);
+        if (pt) ptw += rows * Ns;
+        Ns *= R;
     }
 }
 
@@ -294,11 +330,6 @@ __device__ __forceinline__ int fft_tile_det(const int64_t* ts, int ndet, int64_t
     }
     return lo;
 }
-
-// Radix cap and largest transform per element type (the host sizes the
-// FFT within these: N <= 8192 for FP32, N <= 4096 for FP64 and double-float).
-template <typename T> constexpr int kFftRadix = sizeof(T) == 4 ? 16 : (std::is_same<T, double>::value ? 4 : 8);
-template <typename T> constexpr int kFftMaxM = sizeof(T) == 4 ? 4096 : 2048;
 
 // Table, spectrum and output types per element type: FP32 runs on FP32
 // tables; FP64 reads the FP64 tables and writes FP64; double-float reads its
@@ -321,18 +352,10 @@ template <> struct FftIO<float> {
 };
 
 // Shared memory of the filter kernel: the padded buffer and the table.
-// Entries of the radix-16 passes' own twiddle tables (FP32): 4 Ns for every
-// radix-16 pass after the first.
-__host__ __device__ inline int fft_pass_tw_len(int M) {
-    int n = 0;
-    for (int Ns = 16; Ns * 16 <= M; Ns *= 16) n += 4 * Ns;
-    return n;
-}
 template <typename T>
 inline size_t fft_smem(int N) {
     const int M = N / 2;
-    const size_t ptw = sizeof(T) == 4 ? (size_t)fft_pass_tw_len(M) : 0;
-    return sizeof(cpx<T>) * ((size_t)fft_buf_len(M) + (size_t)M + 1 + ptw);
+    return sizeof(cpx<T>) * ((size_t)fft_buf_len(M) + (size_t)M + 1 + (size_t)fft_pass_tw_len<T>(M));
 }
 
 // One block of H = N - 2(L-1) outputs per iteration (grid-stride over blocks).
@@ -347,20 +370,24 @@ toeplitz_fft_kernel(Src src, const typename FftIO<T>::spec_t* __restrict__ spec,
     cpx<T>* buf = reinterpret_cast<cpx<T>*>(fft_smem_raw);
     cpx<T>* tws = buf + fft_buf_len(M);  // W_N^q, q = 0..M
     for (int q = threadIdx.x; q <= M; q += kFftThreads) tws[q] = {fnum<T>(tw[q].x), fnum<T>(tw[q].y)};
-    // FP32: each radix-16 pass after the first gets its own table of the
-    // twiddles W_M^(2^e step), e = 0..3, step = (M / (16 Ns)) k, for its
-    // Ns values of k (read by fft_pass without bank conflicts)
-    cpx<T>* ptw = nullptr;
-    if (sizeof(T) == 4) {
-        ptw = tws + M + 1;
-        __syncthreads();  // the shared table is complete
+    // the passes' own twiddle tables (see fft_pass_tw_len), built once
+    cpx<T>* ptw = tws + M + 1;
+    __syncthreads();  // the shared table is complete
+    {
         cpx<T>* t = ptw;
-        for (int Ns = 16; Ns * 16 <= M; Ns *= 16) {
-            for (int i = threadIdx.x; i < 4 * Ns; i += kFftThreads) {
-                const int e = i / Ns, k = i % Ns;
-                t[i] = twid<T>(tws, M, (1 << e) * (M / (16 * Ns)) * k, false);
+        for (int Ns = 1; Ns < M;) {
+            const int R = fft_next_radix<T>(M / Ns);
+            const int rows = fft_pass_tw_rows<T>(R);
+            if (Ns > 1 && rows) {
+                const int stepk = M / (Ns * R);  // step = stepk k
+                for (int i = threadIdx.x; i < rows * Ns; i += kFftThreads) {
+                    const int e = i / Ns, k = i % Ns;
+                    const int r = sizeof(T) == 4 ? (1 << e) : e + 1;
+                    t[i] = twid<T>(tws, M, r * stepk * k, false);
+                }
+                t += rows * Ns;
             }
-            t += 4 * Ns;
+            Ns *= R;
         }
     }
     const int H = N - 2 * (L - 1);
