@@ -449,7 +449,7 @@ gather_reduce_f32_kernel(const int64_t* __restrict__ item_beg, const int32_t* __
 // contiguous.  Each pixel's double-float accumulator is updated chunk after
 // chunk by one group of lanes (a fixed order: deterministic).
 constexpr int kPtChunkBits = 24;
-constexpr int kPtLanes = 8;  // lanes per pixel
+constexpr int kPtLanes = 8;  // lanes per segment (4 measured slower)
 
 // sub[c * npix + p] = the first position of pixel p's run (counted from
 // off[p]) whose sample lies in chunk c or later, for c in [0, nch]; c = nch
@@ -1681,7 +1681,7 @@ static void pt_chunked_df(bm_pointing* p, bm_precond* pc, const float2* z, doubl
     for (int c = 0; c < nch; ++c) {
         const int64_t seg0 = pc->cseg[c], nseg = pc->cseg[c + 1] - seg0;
         if (nseg == 0) continue;
-        const int64_t wunits = ((nseg + 3) / 4 + kWarps - 1) / kWarps;
+        const int64_t wunits = ((nseg + 32 / kPtLanes - 1) / (32 / kPtLanes) + kWarps - 1) / kWarps;
         for (int half = 0; half < 2; ++half) {
             const uint64_t t0 = ((uint64_t)c << kPtChunkBits) + (uint64_t)half * (1u << (kPtChunkBits - 1));
             const uint64_t t1 = std::min<uint64_t>(t0 + (1u << (kPtChunkBits - 1)), 0xFFFFFFFFull);
@@ -1710,7 +1710,7 @@ static void pt_chunked(bm_pointing* p, bm_precond* pc, const float* z, double* q
     for (int c = 0; c < nch; ++c) {
         const int64_t seg0 = pc->cseg[c], nseg = pc->cseg[c + 1] - seg0;
         if (nseg == 0) continue;
-        const int64_t wunits = ((nseg + 3) / 4 + kWarps - 1) / kWarps;
+        const int64_t wunits = ((nseg + 32 / kPtLanes - 1) / (32 / kPtLanes) + kWarps - 1) / kWarps;
 #define BM_PT(NC)                                                                                                  \
     pt_chunk_kernel<NC><<<resident_grid(ctx, pt_chunk_kernel<NC>, kWarps * 32, wunits), kWarps * 32, 0, s>>>(       \
         pc->seg_pix.get(), pc->seg_beg.get(), pc->seg_len.get(), seg0, nseg, pc->cm_t.get(), pc->cm_cs.get(), z, acc)
