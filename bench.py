@@ -71,6 +71,15 @@ def parse():
     ap.add_argument("--rate", type=float, default=20.0, help="config4: mean arrivals per second")
     ap.add_argument("--nrhs", type=int, default=64, help="config3: right-hand sides")
     ap.add_argument("--slots", type=int, default=8, help="config4: requests the server runs at once")
+    ap.add_argument("--shared-frac", type=float, default=0.0,
+                    help="config4: fraction of requests that are white-noise realisations of a few shared "
+                         "observations (same pointing, pointing_key set)")
+    ap.add_argument("--observations", type=int, default=4, help="config4: shared observations")
+    ap.add_argument("--no-keys", action="store_true",
+                    help="config4: submit the shared observations' requests without pointing_key (each solved "
+                         "from scratch: the serial comparison for the same arrivals)")
+    ap.add_argument("--alone-sample", type=int, default=24,
+                    help="config4: requests re-solved one at a time for the serial comparison")
     ap.add_argument("--no-fp64-solve", action="store_true", help="config2: skip the timed plain FP64 solve")
     ap.add_argument("--rhs-path", choices=["carried", "gather"], default="carried",
                     help="config1: the TOD sorted along with the pointing (carried, default) or "
@@ -601,6 +610,11 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank)
         return
+    if args.workload == "config4":
+        # the caller's request buffers come and go in many sizes: expandable
+        # segments keep torch's cache from fragmenting next to the server's
+        # own allocations
+        os.environ.setdefault("PYTORCH_CUDA_ALLOC_CONF", "expandable_segments:True")
     if args.workload != "config1":
         import bench_workloads
         bench_workloads.run(args, rank, world, local_rank)

@@ -488,6 +488,22 @@ def run_config4(args):
         if t > args.horizon:
             break
         arrivals.append(t)
+    # Shared observations (--shared-frac > 0): a few fixed pointings, each
+    # drawn like a request but capped at 2^28 samples, whose requests are
+    # white-noise Monte Carlo realisations: the observation's TOD (signal
+    # plus white noise, gathered from the pool once) plus a fresh white-noise
+    # draw per request, submitted with the observation's pointing_key.
+    rng_obs = np.random.default_rng(args.seed + 5)
+    observations = []
+    for j in range(args.observations if args.shared_frac > 0 else 0):
+        while True:
+            nside = int(rng_obs.choice([64, 128, 256, 512]))
+            ndet = int(round(math.exp(rng_obs.uniform(math.log(8), math.log(512)))))
+            ns_ = int(2 ** rng_obs.uniform(18, 22)) // 1024 * 1024
+            if ndet * ns_ <= 2 ** 28:
+                break
+        observations.append(dict(nside=nside, ndet=ndet, ns=ns_, key=j + 1))
+
     reqs = []
     for ta in arrivals:
         nside = int(rng.choice([64, 128, 256, 512]))
@@ -495,9 +511,14 @@ def run_config4(args):
         ns_ = int(2 ** rng.uniform(18, 22)) // 1024 * 1024
         white = rng.random() < 0.5
         fknee = math.exp(rng.uniform(math.log(0.05), math.log(0.5)))
-        reqs.append(dict(t=ta, nside=nside, ndet=ndet, ns=ns_, white=white, fknee=fknee))
+        obs = int(rng.integers(len(observations))) if observations and rng.random() < args.shared_frac else -1
+        if obs >= 0:
+            o = observations[obs]
+            reqs.append(dict(t=ta, nside=o["nside"], ndet=o["ndet"], ns=o["ns"], white=True, fknee=fknee, obs=obs))
+        else:
+            reqs.append(dict(t=ta, nside=nside, ndet=ndet, ns=ns_, white=white, fknee=fknee, obs=-1))
 
-    def build(rq):
+    def gather_inputs(rq):
         e0, pix0, c0, s0, tw, t1f = pools[rq["nside"]]
         ndet, ns_ = rq["ndet"], rq["ns"]
         d = np.arange(ndet)
@@ -510,14 +531,31 @@ def run_config4(args):
         else:  # the pool realisation nearest in log f_knee; N^-1 uses the request's own f_knee
             tod_pool = t1f[min(fk_pool, key=lambda f: abs(math.log(f / rq["fknee"])))]
         pix, c, s, tod = (torch.index_select(a, 0, idx) for a in (pix0, c0, s0, tod_pool))
-        del idx
         sigma = np.asarray(e0.sigma)[src]
+        return e0, pix, c, s, tod, sigma
+
+    obs_bufs = []
+    for o in observations:
+        e0, pix, c, s, tod, sigma = gather_inputs(dict(o, white=True))
+        sig_t = torch.from_numpy(np.repeat(sigma, o["ns"]).astype(np.float32)).cuda()
+        obs_bufs.append((e0, pix, c, s, tod, sigma, sig_t))
+    obs_gen = torch.Generator(device="cuda").manual_seed(args.seed + 6)
+
+    def build(rq):
+        ndet, ns_ = rq["ndet"], rq["ns"]
+        key = 0
+        if rq["obs"] >= 0:
+            e0, pix, c, s, tod0, sigma, sig_t = obs_bufs[rq["obs"]]
+            tod = tod0 + sig_t * torch.randn(tod0.shape, generator=obs_gen, device="cuda", dtype=torch.float32)
+            key = 0 if args.no_keys else observations[rq["obs"]]["key"]
+        else:
+            e0, pix, c, s, tod, sigma = gather_inputs(rq)
         chunk = min(2 ** 20, ns_)
         coeffs = None if rq["white"] else synth.toeplitz_band(sigma, rq["fknee"], 1.0, 20.0, chunk, 512)
         out = torch.empty(e0.npix * 3, dtype=torch.float64, device="cuda")
         det_off = np.arange(ndet + 1, dtype=np.int64) * ns_
         req, keep = L.make_request(e0.npix, pix, tod, out, det_off, 1 / sigma ** 2, cos2psi=c, sin2psi=s,
-                                   coeffs=coeffs, chunk_len=chunk, tol=1e-6, maxiter=3000)
+                                   coeffs=coeffs, chunk_len=chunk, tol=1e-6, maxiter=3000, pointing_key=key)
         return req, (keep, pix, c, s, tod, out)
 
     ctx = L.bm_context_create(0)
@@ -554,7 +592,7 @@ def run_config4(args):
         now = time.perf_counter() - t_start
         if rq["t"] > now:
             time.sleep(rq["t"] - now)
-        nbytes = rq["ndet"] * rq["ns"] * 16
+        nbytes = rq["ndet"] * rq["ns"] * (4 if rq["obs"] >= 0 else 16)
         while True:
             with lock:
                 if inflight_bytes[0] + nbytes <= cap or inflight_bytes[0] == 0:
@@ -566,7 +604,7 @@ def run_config4(args):
         tk = L.bm_serve_submit(srv, req)
         with lock:
             tickets.append({"ticket": tk, "res": None, "t_arr": rq["t"], "bufs": bufs, "bytes": nbytes,
-                            "white": rq["white"], "samples": rq["ndet"] * rq["ns"]})
+                            "white": rq["white"], "samples": rq["ndet"] * rq["ns"], "shared": rq["obs"] >= 0})
     th.join()
     wall = time.perf_counter() - t_start
     clocks = sampler.stop()
@@ -604,7 +642,8 @@ def run_config4(args):
         L.bm_pointing_destroy(p)
         return dt, rq["ndet"] * rq["ns"], st
 
-    pick = np.random.default_rng(args.seed + 4).choice(len(reqs), size=min(8, len(reqs)), replace=False)
+    pick = np.random.default_rng(args.seed + 4).choice(len(reqs), size=min(args.alone_sample, len(reqs)),
+                                                         replace=False)
     alone = {"fp64": [0.0, 0], "mixed": [0.0, 0]}
     for i in pick:
         for name, prec in (("fp64", L.BM_PREC_FP64), ("mixed", L.BM_PREC_MIXED)):
@@ -617,12 +656,19 @@ def run_config4(args):
     samples = sum(x["samples"] for x in tickets)
     lw = np.array([x["t_done"] - x["t_arr"] for x in tickets if x["white"]]) * 1000
     lt = np.array([x["t_done"] - x["t_arr"] for x in tickets if not x["white"]]) * 1000
+    ls = np.array([x["t_done"] - x["t_arr"] for x in tickets if x["shared"]]) * 1000
     line = {
         "workload": "config4", "metric": "served map-making requests: latency from arrival and throughput",
         "value": samples / wall, "unit": "TOD samples/s",
         "config": {"workload": f"Poisson arrivals {args.rate}/s for {args.horizon} s, nside U{{64..512}}, "
                                f"ndet log-U[8,512], Ns 2^U[18,22], white or Toeplitz (p=1/2, fknee log-U[0.05,0.5]), "
-                               f"tol 1e-6, budget 120 GB, {args.slots} slots", "requests": len(reqs)},
+                               f"tol 1e-6, budget 120 GB, {args.slots} slots"
+                               + (f"; a fraction {args.shared_frac} of the requests are white-noise realisations "
+                                  f"of {len(observations)} shared observations"
+                                  + (" submitted without pointing_key" if args.no_keys else " (pointing_key)")
+                                  if observations else ""),
+                   "requests": len(reqs), "shared_frac": args.shared_frac,
+                   "observations": observations},
         "completed_ok": ok,
         "failed": [{"status": x["res"]["status"], "message": x["res"]["message"], "samples": x["samples"],
                     "white": x["white"], "iterations": x["res"]["iterations"],
@@ -631,11 +677,13 @@ def run_config4(args):
         "wall_s": wall, "offered_samples_per_s": samples / args.horizon,
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "p50_white": float(np.percentile(lw, 50)) if lw.size else None,
-                       "p50_toeplitz": float(np.percentile(lt, 50)) if lt.size else None},
+                       "p50_toeplitz": float(np.percentile(lt, 50)) if lt.size else None,
+                       "p50_shared": float(np.percentile(ls, 50)) if ls.size else None},
         "one_at_a_time": {"sample_requests": len(pick),
                           "fp64_samples_per_s": alone["fp64"][1] / alone["fp64"][0],
                           "mixed_samples_per_s": alone["mixed"][1] / alone["mixed"][0]},
         "served_vs_fp64_one_at_a_time": (samples / wall) / (alone["fp64"][1] / alone["fp64"][0]),
+        "served_vs_mixed_one_at_a_time": (samples / wall) / (alone["mixed"][1] / alone["mixed"][0]),
         "server_stats": stats, "clocks": clocks, "pool_generation_s": t_gen,
     }
     print(json.dumps(line), flush=True)

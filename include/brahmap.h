@@ -362,10 +362,31 @@ bm_status bm_pcg_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const vo
  * its own CUDA stream, so their device work overlaps; a request is admitted
  * when a slot is free and its estimated device memory fits in what is left of
  * hbm_budget_bytes (first come, first served; the head of the queue waits for
- * memory rather than being overtaken).  While a request runs, its pointing,
- * preconditioner and CG state stay resident on the device; they are released
- * when it completes.  Each request's solve is the same computation as
- * bm_pointing_create(_trig) + bm_inv_noise_create_* +
+ * memory rather than being overtaken, except by requests that wait for a
+ * resident pointing in use).  A request that fails to allocate while other
+ * requests hold memory is queued again (at most three times) and runs after
+ * one of them has finished.
+ *
+ * Resident pointings: requests that carry the same nonzero pointing_key
+ * share one pointing (the caller promises equal npix, nsamples, solver,
+ * det_offsets and pixel and angle values, in whatever buffers).  The first
+ * such request leaves the ingested pointing, its noise model and its
+ * preconditioner resident on the device after it completes; later requests
+ * with the key reuse them (the noise model and preconditioner are rebuilt
+ * when the noise levels, min_hits or max_cond differ), so their cost is the
+ * RHS and the PCG alone.  Resident pointings count against the budget and
+ * the least recently used one that no request is using is released when an
+ * admitted request needs its memory.
+ *
+ * Batching: when a slot takes a white-noise mixed-precision request with a
+ * pointing_key, every queued request with the same key, noise levels,
+ * min_hits, max_cond, tol, maxiter and TOD dtype joins it (as many as the
+ * memory left allows, at most 256), and they are solved together by the
+ * multi-RHS PCG of bm_pcg_solve (one pass over the pointing for all of
+ * them).  A request's map from a batch agrees with its map solved alone to
+ * the rounding of the per-RHS CG scalars (their reduction tree depends on the
+ * batch size); a request without a key, or that is not batched, is exactly
+ * the computation of bm_pointing_create(_trig) + bm_inv_noise_create_* +
  * bm_blockdiag_precond_create + bm_pcg_solve, so its map does not depend on
  * what else is running.  All bm_serve_* calls are thread-safe.  This loop has
  * no counterpart in the paper. */
@@ -398,6 +419,7 @@ typedef struct {
     int32_t maxiter;
     bm_precision precision;
     double* map_out;             /* device [npix][ncomp], written by the solve */
+    uint64_t pointing_key;       /* 0, or the caller's name of a shared pointing (see above) */
 } bm_request;
 
 typedef struct {
@@ -409,6 +431,8 @@ typedef struct {
     double latency_ms;           /* submit -> finish */
     int64_t device_bytes;        /* memory reserved for the request */
     char message[256];           /* bm_last_error() of a failed solve, else "" */
+    int32_t batch_size;          /* right-hand sides solved together with this one (1 = alone) */
+    int32_t resident;            /* 1 when the request reused a resident pointing */
 } bm_result;
 
 typedef struct {
@@ -416,6 +440,10 @@ typedef struct {
     double p50_ms, p99_ms, mean_ms;   /* latency over completed requests */
     double samples_per_s;             /* samples of completed requests / wall time since creation */
     int64_t budget_bytes, reserved_bytes, peak_reserved_bytes;
+    int64_t resident_bytes;           /* estimated memory of the resident pointings */
+    int64_t resident_hits;            /* requests that reused a resident pointing */
+    int64_t batches, batched_requests;/* multi-RHS solves run, and the requests in them */
+    int64_t evictions, oom_requeues;  /* resident pointings released; requests queued again */
 } bm_serve_stats;
 
 /* Server on ctx's device with max_slots in [1, 64] slots. */

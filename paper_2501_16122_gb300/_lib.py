@@ -51,14 +51,14 @@ class bm_request(ctypes.Structure):
                 ("chunk_len", ctypes.c_int64), ("nlags", ctypes.c_int32), ("coeffs", ctypes.c_void_p),
                 ("tod", ctypes.c_void_p), ("tod_dtype", ctypes.c_int), ("min_hits", ctypes.c_int32),
                 ("max_cond", ctypes.c_double), ("tol", ctypes.c_double), ("maxiter", ctypes.c_int32),
-                ("precision", ctypes.c_int), ("map_out", ctypes.c_void_p)]
+                ("precision", ctypes.c_int), ("map_out", ctypes.c_void_p), ("pointing_key", ctypes.c_uint64)]
 
 
 class bm_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("outer_iterations", ctypes.c_int32),
                 ("slot", ctypes.c_int32), ("rel_residual", ctypes.c_double), ("queue_ms", ctypes.c_double),
                 ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double), ("device_bytes", ctypes.c_int64),
-                ("message", ctypes.c_char * 256)]
+                ("message", ctypes.c_char * 256), ("batch_size", ctypes.c_int32), ("resident", ctypes.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -69,7 +69,9 @@ class bm_result(ctypes.Structure):
 class bm_serve_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "rejected", "cancelled", "running", "queued")] + \
                [(n, ctypes.c_double) for n in ("p50_ms", "p99_ms", "mean_ms", "samples_per_s")] + \
-               [(n, ctypes.c_int64) for n in ("budget_bytes", "reserved_bytes", "peak_reserved_bytes")]
+               [(n, ctypes.c_int64) for n in ("budget_bytes", "reserved_bytes", "peak_reserved_bytes",
+                                              "resident_bytes", "resident_hits", "batches", "batched_requests",
+                                              "evictions", "oom_requeues")]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -502,9 +504,11 @@ def bm_serve_create(ctx, hbm_budget_bytes: int, max_slots: int):
 
 def make_request(npix, pix, tod, map_out, det_offsets, inv_var, solver=BM_SOLVER_IQU, cos2psi=None, sin2psi=None,
                  psi=None, coeffs=None, chunk_len=0, min_hits=3, max_cond=1e3, tol=1e-6, maxiter=500,
-                 precision=BM_PREC_MIXED):
+                 precision=BM_PREC_MIXED, pointing_key=0):
     """Build a bm_request from torch device tensors and host arrays.  Returns
-    (request, keepalive) -- keep the second object alive until submitted."""
+    (request, keepalive) -- keep the second object alive until submitted.
+    pointing_key: 0, or the caller's name of a pointing shared by several
+    requests (kept resident by the server between them)."""
     import torch
     off, offp = _host(det_offsets, np.int64)
     iv, ivp = _host(inv_var, np.float64)
@@ -529,6 +533,7 @@ def make_request(npix, pix, tod, map_out, det_offsets, inv_var, solver=BM_SOLVER
     r.tod, r.tod_dtype = _dev(tod, None, "tod"), _dtype_code(tod)
     r.min_hits, r.max_cond, r.tol, r.maxiter, r.precision = int(min_hits), float(max_cond), float(tol), int(maxiter), int(precision)
     r.map_out = _dev(map_out, torch.float64, "map_out")
+    r.pointing_key = int(pointing_key)
     return r, keep
 
 

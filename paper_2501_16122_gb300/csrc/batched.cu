@@ -16,10 +16,13 @@
 // several items write item partials that a per-pixel pass sums in item order
 // (deterministic).
 //
-// PCG: per-RHS FP64 scalars on the device, per-RHS done flags; one inner
-// iteration (matvec + dots + updates) is captured once as a CUDA graph on the
-// context's side stream and replayed.  Mixed precision with iterative
-// refinement: outer residual r = b - B x per pixel in FP64 (for white noise
+// PCG: per-RHS FP64 scalars on the device, per-RHS done flags; the inner
+// loop is one CUDA graph with a WHILE node (one inner iteration per pass,
+// matvec + dots + updates, ended on the device when every RHS is done or an
+// iteration limit is reached), captured once per solve on the context's side
+// stream; the host reads the RHS states once per outer iteration.  Mixed
+// precision with iterative refinement: outer residual r = b - B x per pixel
+// in FP64 (for white noise
 // A equals the block-diagonal matrix B of Eq. 7).
 #include <algorithm>
 #include <cmath>
@@ -46,20 +49,69 @@ struct RhsState {
 
 // ---------------------------------------------------------------- transpose
 template <typename T>
-__global__ void transpose_group_kernel(const T* __restrict__ in, int64_t n, int r0, int G, T* __restrict__ out) {
+__global__ void transpose_group_kernel(const T* const* __restrict__ rows, int64_t n, int r0, int G,
+                                       T* __restrict__ out) {
     __shared__ T tile[32][33];
     const int rt = blockIdx.y * 32;
     for (int64_t t0 = (int64_t)blockIdx.x * 32; t0 < n; t0 += (int64_t)gridDim.x * 32) {
         for (int yy = threadIdx.y; yy < 32; yy += 8) {
             const int r = rt + yy;
             const int64_t t = t0 + threadIdx.x;
-            tile[yy][threadIdx.x] = (r < G && t < n) ? in[(int64_t)(r0 + r) * n + t] : T(0);
+            tile[yy][threadIdx.x] = (r < G && t < n) ? rows[r0 + r][t] : T(0);
         }
         __syncthreads();
         for (int yy = threadIdx.y; yy < 32; yy += 8) {
             const int64_t t = t0 + yy;
             const int r = rt + threadIdx.x;
             if (t < n && r < G) out[t * G + r] = tile[threadIdx.x][yy];
+        }
+        __syncthreads();
+    }
+}
+
+// FP32 rows -> [n][G] (G <= 32) by tiles of kTT samples x G rows staged in
+// shared memory: each row's samples are loaded as float4 runs (streaming,
+// read once), and the tile's output, one contiguous block of kTT G floats,
+// is stored as float4 runs.  Rows must start on 16-byte boundaries.
+constexpr int kTT = 128;
+
+__global__ void __launch_bounds__(256) transpose_f32x4_kernel(const float* const* __restrict__ rows, int64_t n, int r0,
+                                                              int G, float* __restrict__ out) {
+    __shared__ float tile[32][kTT + 1];
+    for (int64_t t0 = (int64_t)blockIdx.x * kTT; t0 < n; t0 += (int64_t)gridDim.x * kTT) {
+        const int cnt = (int)min((int64_t)kTT, n - t0);
+        for (int i = threadIdx.x; i < G * (kTT / 4); i += blockDim.x) {
+            const int r = i / (kTT / 4), c = (i % (kTT / 4)) * 4;
+            const float* src = rows[r0 + r] + t0 + c;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (c + 4 <= cnt) {
+                v = __ldcs(reinterpret_cast<const float4*>(src));
+            } else {
+                if (c < cnt) v.x = src[0];
+                if (c + 1 < cnt) v.y = src[1];
+                if (c + 2 < cnt) v.z = src[2];
+            }
+            tile[r][c] = v.x;
+            tile[r][c + 1] = v.y;
+            tile[r][c + 2] = v.z;
+            tile[r][c + 3] = v.w;
+        }
+        __syncthreads();
+        float* dst = out + t0 * G;
+        const int total = cnt * G;
+        for (int j = threadIdx.x * 4; j < total; j += blockDim.x * 4) {
+            float v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int e = j + k;
+                const int tt = G == 32 ? (e >> 5) : e / G;
+                v[k] = e < total ? tile[e - tt * G][tt] : 0.f;
+            }
+            if (j + 4 <= total) {
+                *reinterpret_cast<float4*>(dst + j) = make_float4(v[0], v[1], v[2], v[3]);
+            } else {
+                for (int k = 0; k < 4 && j + k < total; ++k) dst[j + k] = v[k];
+            }
         }
         __syncthreads();
     }
@@ -81,8 +133,10 @@ batched_rhs_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restri
                    const uint32_t* __restrict__ perm, const float2* __restrict__ hi, const float2* __restrict__ lo,
                    const T* __restrict__ dT, int G, int r0, int R, DetTables dt, int ndet,
                    double* __restrict__ out, double* __restrict__ partial) {
-    __shared__ uint32_t s_off[kMaxDetSmem + 1];
-    __shared__ float2 s_w[kMaxDetSmem];
+    // the detector tables, staged when they fit (sized by the launch)
+    extern __shared__ __align__(16) unsigned char rhs_smem[];
+    float2* s_w = reinterpret_cast<float2*>(rhs_smem);
+    uint32_t* s_off = reinterpret_cast<uint32_t*>(rhs_smem + sizeof(float2) * (size_t)ndet);
     const bool in_smem = ndet <= kMaxDetSmem;
     if (in_smem) {
         for (int d = threadIdx.x; d <= ndet; d += blockDim.x) s_off[d] = dt.off[d];
@@ -144,14 +198,14 @@ batched_rhs_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restri
                     dv[q] = r < G ? dT[(int64_t)t * G + r] : T(0);
                 }
             };
-            // four rows in flight, then their sums in sample order
+            // eight rows in flight, then their sums in sample order
             int kk = 0;
-            for (; kk + 4 <= cnt; kk += 4) {
-                T dv[4][RPL];
+            for (; kk + 8 <= cnt; kk += 8) {
+                T dv[8][RPL];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) row(kk + u, dv[u]);
+                for (int u = 0; u < 8; ++u) row(kk + u, dv[u]);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) add(kk + u, dv[u]);
+                for (int u = 0; u < 8; ++u) add(kk + u, dv[u]);
             }
             for (; kk < cnt; ++kk) {
                 T dv[RPL];
@@ -493,16 +547,30 @@ __global__ void b_sum2_kernel(const double* __restrict__ part, int nblk, int R, 
     out[R + r] = b;
 }
 
-// map_out[r][p][c] = x[p][r][c] (NaN on masked pixels)
+// maps[r][p][c] = x[p][r][c] (NaN on masked pixels)
 __global__ void b_write_map_kernel(const double* __restrict__ x, const uint8_t* __restrict__ mask, int64_t npix,
-                                   int R, int NC, double* __restrict__ out) {
+                                   int R, int NC, double* const* __restrict__ maps) {
     const int64_t n = npix * R * NC;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t p = i / ((int64_t)R * NC);
         const int64_t rem = i - p * R * NC;
         const int r = (int)(rem / NC), c = (int)(rem - (int64_t)r * NC);
-        out[((int64_t)r * npix + p) * NC + c] = mask[p] ? NAN : x[i];
+        maps[r][p * NC + c] = mask[p] ? NAN : x[i];
     }
+}
+
+// Inner-loop control for the WHILE node of the batched solve: loop[0]
+// counts the iterations run by the current graph launch (inc = 1 after an
+// iteration, 0 before the first), loop[1] is their limit; the node goes on
+// while any right-hand side is active and the limit is not reached.
+__global__ void b_loop_kernel(const RhsState* __restrict__ st, int R, int* __restrict__ loop, int inc,
+                              cudaGraphConditionalHandle h) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int it = loop[0] + inc;
+    loop[0] = it;
+    bool active = false;
+    for (int r = 0; r < R; ++r) active = active || st[r].done == 0;
+    cudaGraphSetConditional(h, (active && it < loop[1]) ? 1u : 0u);
 }
 
 // ------------------------------------------------------------------ launchers
@@ -539,9 +607,10 @@ template <int NC, typename T, int RPL>
 void launch_rhs_v(bm_context* ctx, bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const T* dT, int G, int r0,
                   int R, double* b, double* partial, bool exact_lo) {
     auto kern = batched_rhs_kernel<NC, T, RPL, 4>;
-    const int grid = resident_grid(ctx, kern, 4 * 32, (pc->nitems + 3) / 4);
+    const size_t smem = n->ndet <= kMaxDetSmem ? (sizeof(float2) + sizeof(uint32_t)) * (size_t)n->ndet + 4 : 0;
+    const int grid = resident_grid(ctx, kern, 4 * 32, (pc->nitems + 3) / 4, smem);
     const DetTables dt{n->det_off32.get(), n->wdf.get(), n->wsqrt.get(), n->ns_uniform, n->inv_ns};
-    kern<<<grid, 4 * 32, 0, ctx->stream>>>(pc->item_pix.get(), pc->item_beg.get(), pc->item_len.get(), pc->nitems,
+    kern<<<grid, 4 * 32, smem, ctx->stream>>>(pc->item_pix.get(), pc->item_beg.get(), pc->item_len.get(), pc->nitems,
                                           pc->pitem.get(), p->perm.get(), p->cs_hi_s.get(),
                                           exact_lo ? p->cs_lo_s.get() : nullptr, dT, G, r0, R, dt, n->ndet, b,
                                           partial);
@@ -557,6 +626,7 @@ struct BatchBufs {
     double *b, *x, *r, *e, *rcg, *z, *pv, *q, *partial, *part, *tolr, *sums;
     float* x32;
     RhsState* st;
+    int* loop;
 };
 
 template <int NC>
@@ -599,8 +669,8 @@ Variant autotune(bm_context* ctx, bm_precond* pc, int R, const BatchBufs& bb) {
 }
 
 template <int NC>
-bm_status batched_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dtype dt, int R,
-                        double* map_out, double tol, int32_t maxiter, bm_solve_info* info) {
+bm_status batched_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* const* rows, bm_dtype dt,
+                        int R, double* const* maps, double tol, int32_t maxiter, bm_solve_info* info) {
     bm_context* ctx = p->ctx;
     cudaStream_t s = ctx->stream;
     const int64_t npix = p->npix;
@@ -624,6 +694,22 @@ bm_status batched_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const v
     bb.sums = workspace_as<double>(ctx, "bt_sums", 2 * (size_t)R);
     bb.x32 = workspace_as<float>(ctx, "bt_x32", nv);
     bb.st = reinterpret_cast<RhsState*>(workspace_as<char>(ctx, "bt_state", sizeof(RhsState) * R));
+    bb.loop = workspace_as<int>(ctx, "bt_loop", 2);
+    // the caller's TOD rows and map outputs, as device arrays of pointers
+    char* ptrs = workspace_as<char>(ctx, "bt_ptrs", 2 * sizeof(void*) * (size_t)R);
+    {
+        std::vector<const void*> h(2 * (size_t)R);
+        for (int r = 0; r < R; ++r) {
+            h[r] = rows[r];
+            h[R + r] = maps[r];
+        }
+        BM_CUDA(cudaMemcpyAsync(ptrs, h.data(), 2 * sizeof(void*) * (size_t)R, cudaMemcpyHostToDevice, s));
+        BM_CUDA(cudaStreamSynchronize(s));
+    }
+    const void* const* d_rows = reinterpret_cast<const void* const*>(ptrs);
+    bool rows_aligned = true;
+    for (int r = 0; r < R; ++r) rows_aligned = rows_aligned && (reinterpret_cast<uintptr_t>(rows[r]) % 16 == 0);
+    double* const* d_maps = reinterpret_cast<double* const*>(ptrs + sizeof(void*) * (size_t)R);
 
     // --- batched RHS, TOD transposed group by group
     {
@@ -636,12 +722,16 @@ bm_status batched_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const v
             const dim3 tgrid((unsigned)std::min<int64_t>((p->nsamples + 31) / 32, (int64_t)ctx->num_sms * 16),
                              (unsigned)((g + 31) / 32));
             const dim3 tblk(32, 8);
-            if (dt == BM_F32)
-                transpose_group_kernel<float><<<tgrid, tblk, 0, s>>>(static_cast<const float*>(tod), p->nsamples, r0,
-                                                                     g, static_cast<float*>(dT));
+            if (dt == BM_F32 && rows_aligned)
+                transpose_f32x4_kernel<<<resident_grid(ctx, transpose_f32x4_kernel, 256, (p->nsamples + kTT - 1) / kTT),
+                                         256, 0, s>>>(reinterpret_cast<const float* const*>(d_rows), p->nsamples, r0,
+                                                      g, static_cast<float*>(dT));
+            else if (dt == BM_F32)
+                transpose_group_kernel<float><<<tgrid, tblk, 0, s>>>(reinterpret_cast<const float* const*>(d_rows),
+                                                                     p->nsamples, r0, g, static_cast<float*>(dT));
             else
-                transpose_group_kernel<double><<<tgrid, tblk, 0, s>>>(static_cast<const double*>(tod), p->nsamples,
-                                                                      r0, g, static_cast<double*>(dT));
+                transpose_group_kernel<double><<<tgrid, tblk, 0, s>>>(
+                    reinterpret_cast<const double* const*>(d_rows), p->nsamples, r0, g, static_cast<double*>(dT));
             BM_LAUNCH_CHECK();
             const bool lo = p->cs_lo_s.get() != nullptr;
             if (dt == BM_F32)
@@ -680,9 +770,6 @@ bm_status batched_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const v
             launch_matvec<NC>(ctx, pc, var, bb.x32, r0, std::min(per, R - r0), R, bb.q, bb.partial);
     }
 
-    // The inner iteration as a graph (captured on first use).
-    cudaGraphExec_t gexec = nullptr;
-    int64_t graph_kernels = 0;
     auto inner_iteration = [&](cudaStream_t st) {
         batched_masked_f32_kernel<<<vgrid, threads, 0, st>>>(bb.pv, pc->mask.get(), npix, RNC, bb.x32);
         BM_LAUNCH_CHECK();
@@ -703,6 +790,63 @@ bm_status batched_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const v
         BM_LAUNCH_CHECK();
         b_pupdate_kernel<<<rgrid, kRT, 0, st>>>(geo, NC, bb.pv, bb.z, bb.st);
         BM_LAUNCH_CHECK();
+    };
+
+    // The inner PCG loop as one graph, built on first use: b_loop_kernel
+    // decides whether to enter, then a WHILE node runs one inner iteration
+    // followed by b_loop_kernel again, for as long as any right-hand side is
+    // active and fewer iterations than the limit in loop[1] have run.  The
+    // limit bounds the loop whatever the states hold.  The host reads the
+    // states once per outer iteration, not after every inner one.
+    cudaGraphExec_t gexec = nullptr;
+    int64_t body_kernels = 0;
+    bool graph_ok = true;
+    auto build_loop_graph = [&]() {
+        cudaGraph_t graph = nullptr;
+        BM_CUDA(cudaGraphCreate(&graph, 0));
+        cudaGraphConditionalHandle h;
+        cudaError_t e = cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault);
+        if (e == cudaSuccess)
+            e = cudaStreamBeginCaptureToGraph(ctx->side, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            b_loop_kernel<<<1, 32, 0, ctx->side>>>(bb.st, R, bb.loop, 0, h);
+            e = cudaGetLastError();
+            const cudaError_t e2 = cudaStreamEndCapture(ctx->side, &graph);
+            if (e == cudaSuccess) e = e2;
+        }
+        cudaGraphNode_t first = nullptr;
+        size_t nn = 1;
+        if (e == cudaSuccess) e = cudaGraphGetNodes(graph, &first, &nn);
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t wnode = nullptr;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&wnode, graph, &first, nullptr, 1, &cp);
+        if (e == cudaSuccess) {
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            e = cudaStreamBeginCaptureToGraph(ctx->side, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                const int64_t before = bm_kernel_launches();
+                try {
+                    inner_iteration(ctx->side);
+                } catch (...) {
+                    cudaStreamEndCapture(ctx->side, &body);
+                    cudaGraphDestroy(graph);
+                    throw;
+                }
+                body_kernels = bm_kernel_launches() - before + 1;  // + the loop kernel
+                count_launches(-(body_kernels - 1));  // counted from the iterations that ran
+                b_loop_kernel<<<1, 32, 0, ctx->side>>>(bb.st, R, bb.loop, 1, h);
+                e = cudaGetLastError();
+                const cudaError_t e2 = cudaStreamEndCapture(ctx->side, &body);
+                if (e == cudaSuccess) e = e2;
+            }
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        BM_CUDA(e);
     };
 
     std::vector<bm_solve_info> inf(R);
@@ -728,39 +872,39 @@ bm_status batched_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const v
         BM_LAUNCH_CHECK();
         b_init_finalize<<<sgrid, 128, 0, s>>>(bb.part, rgrid, R, bb.tolr, bb.st);
         BM_LAUNCH_CHECK();
-        int it = 0;
-        for (; inner_total + it < maxiter; ++it) {
-            BM_CUDA(cudaMemcpyAsync(hst.data(), bb.st, sizeof(RhsState) * R, cudaMemcpyDeviceToHost, s));
-            BM_CUDA(cudaStreamSynchronize(s));
-            bool any = false;
-            for (int r = 0; r < R; ++r) any = any || !hst[r].done;
-            if (!any) break;
-            if (gexec == nullptr && ctx->side != nullptr) {
-                cudaGraph_t graph = nullptr;
-                BM_CUDA(cudaEventRecord(ctx->side_ev, s));
-                BM_CUDA(cudaStreamWaitEvent(ctx->side, ctx->side_ev, 0));
-                const int64_t before = bm_kernel_launches();
-                BM_CUDA(cudaStreamBeginCapture(ctx->side, cudaStreamCaptureModeThreadLocal));
-                inner_iteration(ctx->side);
-                BM_CUDA(cudaStreamEndCapture(ctx->side, &graph));
-                graph_kernels = bm_kernel_launches() - before;
-                count_launches(-graph_kernels);  // counted when the graph is replayed
-                BM_CUDA(cudaGraphInstantiate(&gexec, graph, 0));
-                BM_CUDA(cudaGraphDestroy(graph));
+        const int hloop[2] = {0, maxiter - inner_total};  // >= 1 here
+        BM_CUDA(cudaMemcpyAsync(bb.loop, hloop, sizeof(hloop), cudaMemcpyHostToDevice, s));
+        int loop_out[2] = {0, 0};
+        if (ctx->side != nullptr && gexec == nullptr && graph_ok) {
+            try {
+                build_loop_graph();
+            } catch (const Error&) {  // no conditional graph here: the host-driven loop below
+                graph_ok = false;
+                gexec = nullptr;
+                cudaGetLastError();
+                clear_error();
             }
-            if (gexec) {
-                BM_CUDA(cudaEventRecord(ctx->side_ev, s));
-                BM_CUDA(cudaStreamWaitEvent(ctx->side, ctx->side_ev, 0));
-                BM_CUDA(cudaGraphLaunch(gexec, ctx->side));
-                count_launches(graph_kernels);
-                BM_CUDA(cudaEventRecord(ctx->side_ev, ctx->side));
-                BM_CUDA(cudaStreamWaitEvent(s, ctx->side_ev, 0));
-            } else {
+        }
+        if (gexec != nullptr) {
+            BM_CUDA(cudaEventRecord(ctx->side_ev, s));
+            BM_CUDA(cudaStreamWaitEvent(ctx->side, ctx->side_ev, 0));
+            BM_CUDA(cudaGraphLaunch(gexec, ctx->side));
+            BM_CUDA(cudaEventRecord(ctx->side_ev, ctx->side));
+            BM_CUDA(cudaStreamWaitEvent(s, ctx->side_ev, 0));
+            BM_CUDA(cudaMemcpyAsync(loop_out, bb.loop, sizeof(loop_out), cudaMemcpyDeviceToHost, s));
+        } else {  // no side stream or no conditional graph: the same loop driven from the host
+            for (int it = 0; it < hloop[1]; ++it) {
+                BM_CUDA(cudaMemcpyAsync(hst.data(), bb.st, sizeof(RhsState) * R, cudaMemcpyDeviceToHost, s));
+                BM_CUDA(cudaStreamSynchronize(s));
+                bool any = false;
+                for (int r = 0; r < R; ++r) any = any || !hst[r].done;
+                if (!any) break;
                 inner_iteration(s);
             }
         }
         BM_CUDA(cudaMemcpyAsync(hst.data(), bb.st, sizeof(RhsState) * R, cudaMemcpyDeviceToHost, s));
         BM_CUDA(cudaStreamSynchronize(s));
+        if (gexec != nullptr) count_launches(1 + (int64_t)loop_out[0] * body_kernels);
         int itmax = 0;
         for (int r = 0; r < R; ++r) {
             inf[r].iterations += hst[r].iters;
@@ -785,7 +929,7 @@ bm_status batched_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const v
     }
     if (gexec) cudaGraphExecDestroy(gexec);
 
-    b_write_map_kernel<<<vgrid, threads, 0, s>>>(bb.x, pc->mask.get(), npix, R, NC, map_out);
+    b_write_map_kernel<<<vgrid, threads, 0, s>>>(bb.x, pc->mask.get(), npix, R, NC, d_maps);
     BM_LAUNCH_CHECK();
     BM_CUDA(cudaStreamSynchronize(s));
     bm_status first = BM_OK;
@@ -802,24 +946,35 @@ bm_status batched_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const v
 
 }  // namespace
 
-bm_status batched_white_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dtype dt,
-                              int32_t nrhs, double* map_out, double tol, int32_t maxiter, bm_solve_info* info) {
+bm_status batched_white_solve_rows(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* const* rows,
+                                   bm_dtype dt, int32_t nrhs, double* const* maps, double tol, int32_t maxiter,
+                                   bm_solve_info* info) {
     const int nc = p->ncomp;
-    const int64_t nvec = p->npix * nc;
     bm_status first = BM_OK;
     // Groups of at most kBatchMax right-hand sides per batched solve.
     for (int32_t r0 = 0; r0 < nrhs; r0 += kBatchMax) {
         const int R = std::min<int32_t>(kBatchMax, nrhs - r0);
-        const void* t = static_cast<const char*>(tod) + (size_t)r0 * p->nsamples * (dt == BM_F32 ? 4 : 8);
-        double* out = map_out + (int64_t)r0 * nvec;
         bm_solve_info* ir = info ? info + r0 : nullptr;
         bm_status st;
-        if (nc == 3) st = batched_solve<3>(p, n, pc, t, dt, R, out, tol, maxiter, ir);
-        else if (nc == 2) st = batched_solve<2>(p, n, pc, t, dt, R, out, tol, maxiter, ir);
-        else st = batched_solve<1>(p, n, pc, t, dt, R, out, tol, maxiter, ir);
+        if (nc == 3) st = batched_solve<3>(p, n, pc, rows + r0, dt, R, maps + r0, tol, maxiter, ir);
+        else if (nc == 2) st = batched_solve<2>(p, n, pc, rows + r0, dt, R, maps + r0, tol, maxiter, ir);
+        else st = batched_solve<1>(p, n, pc, rows + r0, dt, R, maps + r0, tol, maxiter, ir);
         if (first == BM_OK && st != BM_OK) first = st;
     }
     return first;
+}
+
+bm_status batched_white_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dtype dt,
+                              int32_t nrhs, double* map_out, double tol, int32_t maxiter, bm_solve_info* info) {
+    const int64_t nvec = p->npix * p->ncomp;
+    const size_t row_bytes = (size_t)p->nsamples * (dt == BM_F32 ? 4 : 8);
+    std::vector<const void*> rows(nrhs);
+    std::vector<double*> maps(nrhs);
+    for (int32_t r = 0; r < nrhs; ++r) {
+        rows[r] = static_cast<const char*>(tod) + (size_t)r * row_bytes;
+        maps[r] = map_out + (int64_t)r * nvec;
+    }
+    return batched_white_solve_rows(p, n, pc, rows.data(), dt, nrhs, maps.data(), tol, maxiter, info);
 }
 
 }  // namespace bm

@@ -305,6 +305,12 @@ constexpr int kBatchMax = 256;  // right-hand sides per batched solve
 // one pointing (groups of at most kBatchMax).
 bm_status batched_white_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dtype dt,
                               int32_t nrhs, double* map_out, double tol, int32_t maxiter, bm_solve_info* info);
+// The same from separate buffers: rows[r] is RHS r's device TOD
+// [nsamples], maps[r] its device map [npix][ncomp] (host arrays of nrhs
+// pointers).
+bm_status batched_white_solve_rows(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* const* rows,
+                                   bm_dtype dt, int32_t nrhs, double* const* maps, double tol, int32_t maxiter,
+                                   bm_solve_info* info);
 // Adds kernels launched by a CUDA-graph replay to the launch counter.
 void count_launches(int64_t n);
 
