@@ -567,7 +567,7 @@ def run_config4(args):
     sampler.start()
     t_start = time.perf_counter()
     inflight_bytes = [0]
-    cap = 60 * 2 ** 30  # caller-side input buffers outstanding at once
+    cap = 40 * 2 ** 30  # caller-side input buffers outstanding at once
 
     def poller():
         while True:

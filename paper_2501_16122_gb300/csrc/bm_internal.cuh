@@ -153,6 +153,7 @@ struct bm_context {
     // new memory.
     cudaMemPool_t ws_pool = nullptr;
     std::map<std::string, bm::DevBuf<char>> ws;
+    uint64_t ws_generation = 0;  // bumped when a workspace is (re)allocated: graphs holding its address are stale
     // Library-owned stream for CUDA-graph capture and replay (the caller's
     // stream may be the legacy default stream, which cannot be captured),
     // ordered against `stream` with side_ev.
@@ -289,6 +290,7 @@ struct bm_precond {
     bm::DevBuf<int32_t> seg_pix;   // [segments] pixel
     bm::DevBuf<uint32_t> seg_beg;  // [segments] first position in cm_t / cm_cs
     bm::DevBuf<int32_t> seg_len;   // [segments] samples
+    bm::DevBuf<int32_t> seg_mid;   // [segments] samples in the first half of the segment's chunk
     std::vector<int64_t> cseg;     // [pt_nch + 1] first segment of each chunk (host)
     // Offset filter: 1 / (the kept samples of each interval), 0 where none;
     // the interval of every sample in pixel-sorted order.

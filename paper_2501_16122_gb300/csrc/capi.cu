@@ -126,6 +126,7 @@ void shard_reduce(bm_context* ctx, double* buf, int64_t count) {
 void* workspace(bm_context* ctx, const char* name, size_t bytes) {
     auto& b = ctx->ws[name];
     if (b.n < bytes) {
+        ctx->ws_generation += 1;
         try {
             b.alloc_from(ctx->ws_pool, bytes + bytes / 8);  // stream-ordered: old users finish first
         } catch (const Error& e) {

@@ -404,14 +404,29 @@ toeplitz_fft_kernel(Src src, const typename FftIO<T>::spec_t* __restrict__ spec,
         const int64_t t1 = min(t0 + (int64_t)H, ce);
         const int64_t b0 = t0 - (L - 1);
         __syncthreads();  // previous block done with the buffer (and the table loaded)
-        // Gather the block's inputs: four sample pairs per thread in flight.
-#pragma unroll 4
-        for (int n = threadIdx.x; n < M; n += kFftThreads) {
-            const int64_t ta = b0 + 2 * n, tb = ta + 1;
-            using V = decltype(src(ta));
-            const T ya = fnum<T>((ta >= cs && ta < ce) ? src(ta) : V{});
-            const T yb = fnum<T>((tb >= cs && tb < ce) ? src(tb) : V{});
-            buf[fpad(n)] = {ya, yb};
+        // Gather the block's inputs: for FP32 all of a thread's sample pairs
+        // in flight at once (one memory latency per block of outputs; the
+        // transform is short next to it), for the 8-byte types four pairs at
+        // a time (their registers are taken by the transform).
+        {
+            constexpr int GP = sizeof(T) == 4 ? kFftMaxM<T> / kFftThreads : 4;
+            using V = decltype(src(b0));
+            V va[GP], vb[GP];
+            // (FP32: M <= GP kFftThreads, so the loop below runs once)
+            for (int n0 = 0; n0 < (sizeof(T) == 4 ? 1 : M); n0 += GP * kFftThreads) {
+#pragma unroll
+                for (int u = 0; u < GP; ++u) {
+                    const int n = n0 + threadIdx.x + u * kFftThreads;
+                    const int64_t ta = b0 + 2 * n, tb = ta + 1;
+                    va[u] = (n < M && ta >= cs && ta < ce) ? src(ta) : V{};
+                    vb[u] = (n < M && tb >= cs && tb < ce) ? src(tb) : V{};
+                }
+#pragma unroll
+                for (int u = 0; u < GP; ++u) {
+                    const int n = n0 + threadIdx.x + u * kFftThreads;
+                    if (n < M) buf[fpad(n)] = {fnum<T>(va[u]), fnum<T>(vb[u])};
+                }
+            }
         }
         __syncthreads();
         // forward transform, spectrum product, inverse transform: one copy of

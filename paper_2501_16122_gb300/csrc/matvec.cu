@@ -547,16 +547,33 @@ pt_chunk_kernel(const int32_t* __restrict__ seg_pix, const uint32_t* __restrict_
     constexpr int G = 32 / kPtLanes;
     constexpr int U = 8;
     const int lane = threadIdx.x & 31, gl = lane % kPtLanes, grp = lane / kPtLanes;
-    const int64_t nwarps = (int64_t)gridDim.x * kWarps;
-    for (int64_t kw = ((int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5)) * G; kw < nseg; kw += nwarps * G) {
-        const int64_t k = kw + grp;
-        int64_t p = 0, b = 0;
-        int32_t len = 0;
+    const int64_t stride = (int64_t)gridDim.x * kWarps * G;
+    // A group's segment metadata is loaded one iteration ahead, and its
+    // pixel's accumulator before the samples (this group is its only writer
+    // in the launch), so that the iteration waits on the sample streams and
+    // the gather of z only.
+    auto meta = [&](int64_t k, int64_t& p, int64_t& b, int32_t& len) {
+        p = 0;
+        b = 0;
+        len = 0;
         if (k < nseg) {
             p = seg_pix[seg0 + k];
             b = seg_beg[seg0 + k];
             len = seg_len[seg0 + k];
         }
+    };
+    int64_t kw = ((int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5)) * G;
+    int64_t p, b;
+    int32_t len;
+    meta(kw + grp, p, b, len);
+    for (; kw < nseg; kw += stride) {
+        int64_t pn, bn;
+        int32_t lenn;
+        meta(kw + stride + grp, pn, bn, lenn);
+        const bool writer = gl == 0 && len > 0;
+        float2 old[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) old[c] = writer ? acc[p * NC + c] : make_float2(0.f, 0.f);
         float a[NC];
         df32 A[NC];
 #pragma unroll
@@ -597,55 +614,64 @@ pt_chunk_kernel(const int32_t* __restrict__ seg_pix, const uint32_t* __restrict_
 #pragma unroll
             for (int o = kPtLanes / 2; o > 0; o >>= 1) A[c] = df_add(A[c], df_shfl_xor(A[c], o));
         }
-        if (gl == 0 && len > 0) {
+        if (writer) {
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                const float2 old = acc[p * NC + c];
-                const df32 s = df_add(df32{old.x, old.y}, A[c]);
+                const df32 s = df_add(df32{old[c].x, old[c].y}, A[c]);
                 acc[p * NC + c] = make_float2(s.hi, s.lo);
             }
         }
+        p = pn;
+        b = bn;
+        len = lenn;
     }
 }
 
 // The double-float form of the chunk transpose (the refinement operator's and
 // the RHS's pixel sums of z given as (hi, lo) pairs, for exact FP32 trig):
-// chunk c's samples with time index in [t_lo, t_hi) -- half a chunk, so that
-// the 64 MB of z pairs it gathers stay in L2 -- of each segment (a prefix or
-// a suffix of it: its samples are in time order, found by a binary search),
+// one half of chunk c's time range per launch -- so that the 64 MB of z
+// pairs it gathers stay in L2 -- i.e. of each segment the first seg_mid
+// samples (half 0) or the rest (half 1), its samples being in time order;
 // summed in the lazily renormalised double-float form of the gather-reduce
 // (rhs_term_lazy) by kPtLanes lanes per segment, then added to the pixel's
 // double-float accumulator (one writer per launch; launches in time order).
+// Metadata one iteration ahead and the accumulator read early, as in
+// pt_chunk_kernel.
 template <int NC>
 __global__ void __launch_bounds__(kWarps * 32)
 pt_chunk_df_kernel(const int32_t* __restrict__ seg_pix, const uint32_t* __restrict__ seg_beg,
-                   const int32_t* __restrict__ seg_len, int64_t seg0, int64_t nseg, uint32_t t_lo, uint32_t t_hi,
-                   const uint32_t* __restrict__ cm_t, const float2* __restrict__ cm_cs,
+                   const int32_t* __restrict__ seg_len, const int32_t* __restrict__ seg_mid, int64_t seg0,
+                   int64_t nseg, int half, const uint32_t* __restrict__ cm_t, const float2* __restrict__ cm_cs,
                    const float2* __restrict__ z, float2* __restrict__ acc) {
     constexpr int G = 32 / kPtLanes;
     constexpr int U = 4;
     const int lane = threadIdx.x & 31, gl = lane % kPtLanes, grp = lane / kPtLanes;
-    const int64_t nwarps = (int64_t)gridDim.x * kWarps;
-    for (int64_t kw = ((int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5)) * G; kw < nseg; kw += nwarps * G) {
-        const int64_t k = kw + grp;
-        int64_t p = 0, b = 0;
-        int32_t i_lo = 0, i_hi = 0;
+    const int64_t stride = (int64_t)gridDim.x * kWarps * G;
+    auto meta = [&](int64_t k, int64_t& p, int64_t& b, int32_t& i_lo, int32_t& i_hi) {
+        p = 0;
+        b = 0;
+        i_lo = 0;
+        i_hi = 0;
         if (k < nseg) {
             p = seg_pix[seg0 + k];
             b = seg_beg[seg0 + k];
-            const int32_t len = seg_len[seg0 + k];
-            // the segment's samples in [t_lo, t_hi): [first >= t_lo, first >= t_hi)
-            auto lower = [&](uint32_t tv) {
-                int32_t lo = 0, hi = len;
-                while (lo < hi) {
-                    const int32_t mid = (lo + hi) >> 1;
-                    if (__ldg(cm_t + b + mid) < tv) lo = mid + 1; else hi = mid;
-                }
-                return lo;
-            };
-            i_lo = lower(t_lo);
-            i_hi = lower(t_hi);
+            const int32_t mid = seg_mid[seg0 + k];
+            i_lo = half ? mid : 0;
+            i_hi = half ? seg_len[seg0 + k] : mid;
         }
+    };
+    int64_t kw = ((int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5)) * G;
+    int64_t p, b;
+    int32_t i_lo, i_hi;
+    meta(kw + grp, p, b, i_lo, i_hi);
+    for (; kw < nseg; kw += stride) {
+        int64_t pn, bn;
+        int32_t lon, hin;
+        meta(kw + stride + grp, pn, bn, lon, hin);
+        const bool writer = gl == 0 && i_hi > i_lo;
+        float2 old[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) old[c] = writer ? acc[p * NC + c] : make_float2(0.f, 0.f);
         df32 A[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) A[c] = {0.f, 0.f};
@@ -679,14 +705,34 @@ pt_chunk_df_kernel(const int32_t* __restrict__ seg_pix, const uint32_t* __restri
 #pragma unroll
             for (int o = kPtLanes / 2; o > 0; o >>= 1) A[c] = df_add(A[c], df_shfl_xor(A[c], o));
         }
-        if (gl == 0 && i_hi > i_lo) {
+        if (writer) {
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                const float2 old = acc[p * NC + c];
-                const df32 s = df_add(df32{old.x, old.y}, A[c]);
+                const df32 s = df_add(df32{old[c].x, old[c].y}, A[c]);
                 acc[p * NC + c] = make_float2(s.hi, s.lo);
             }
         }
+        p = pn;
+        b = bn;
+        i_lo = lon;
+        i_hi = hin;
+    }
+}
+
+// seg_mid[k] = the number of segment k's samples (in time order) before
+// t_mid, the middle of its chunk's time range: one binary search per segment
+// when the chunk-major order is built.
+__global__ void cm_seg_mid_kernel(const uint32_t* __restrict__ seg_beg, const int32_t* __restrict__ seg_len,
+                                  int64_t seg0, int64_t nseg, uint32_t t_mid, const uint32_t* __restrict__ cm_t,
+                                  int32_t* __restrict__ seg_mid) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nseg; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = seg_beg[seg0 + k];
+        int32_t lo = 0, hi = seg_len[seg0 + k];
+        while (lo < hi) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (cm_t[b + mid] < t_mid) lo = mid + 1; else hi = mid;
+        }
+        seg_mid[seg0 + k] = lo;
     }
 }
 
@@ -1651,6 +1697,18 @@ static void build_chunk_major(bm_pointing* p, bm_precond* pc, int nch) {
                                                                             npix, nch, pc->seg_pix.get(),
                                                                             pc->seg_beg.get(), pc->seg_len.get());
     BM_LAUNCH_CHECK();
+    // each segment's split at the middle of its chunk (the double-float
+    // transpose runs half a chunk per launch)
+    pc->seg_mid.alloc(std::max<int64_t>(nseg, 1));
+    for (int c = 0; c < nch; ++c) {
+        const int64_t seg0 = pc->cseg[c], n = pc->cseg[c + 1] - seg0;
+        if (n == 0) continue;
+        const uint64_t t_mid = ((uint64_t)c << kPtChunkBits) + (uint64_t(1) << (kPtChunkBits - 1));
+        cm_seg_mid_kernel<<<grid_for(ctx, (n + 255) / 256, 16), 256, 0, s>>>(
+            pc->seg_beg.get(), pc->seg_len.get(), seg0, n, (uint32_t)std::min<uint64_t>(t_mid, 0xFFFFFFFFull),
+            pc->cm_t.get(), pc->seg_mid.get());
+        BM_LAUNCH_CHECK();
+    }
 }
 
 // True when the chunk-major order is (or has now been) built.
@@ -1683,11 +1741,9 @@ static void pt_chunked_df(bm_pointing* p, bm_precond* pc, const float2* z, doubl
         if (nseg == 0) continue;
         const int64_t wunits = ((nseg + 32 / kPtLanes - 1) / (32 / kPtLanes) + kWarps - 1) / kWarps;
         for (int half = 0; half < 2; ++half) {
-            const uint64_t t0 = ((uint64_t)c << kPtChunkBits) + (uint64_t)half * (1u << (kPtChunkBits - 1));
-            const uint64_t t1 = std::min<uint64_t>(t0 + (1u << (kPtChunkBits - 1)), 0xFFFFFFFFull);
 #define BM_PTD(NC)                                                                                              \
     pt_chunk_df_kernel<NC><<<resident_grid(ctx, pt_chunk_df_kernel<NC>, kWarps * 32, wunits), kWarps * 32, 0, s>>>( \
-        pc->seg_pix.get(), pc->seg_beg.get(), pc->seg_len.get(), seg0, nseg, (uint32_t)t0, (uint32_t)t1,          \
+        pc->seg_pix.get(), pc->seg_beg.get(), pc->seg_len.get(), pc->seg_mid.get(), seg0, nseg, half,              \
         pc->cm_t.get(), pc->cm_cs.get(), z, acc)
             if (nc == 3) BM_PTD(3); else if (nc == 2) BM_PTD(2); else BM_PTD(1);
 #undef BM_PTD
@@ -1815,16 +1871,21 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
                 {
                     ScopedTimer timer(ctx, "toeplitz_f32");
                     float4* x4 = workspace_as<float4>(ctx, "x4", p->npix);
-                    masked_copy4_kernel<<<grid_for(ctx, (p->npix + threads - 1) / threads, 16), threads, 0, s>>>(
-                        xr, pc->mask.get(), p->npix, nc, x4);
-                    BM_LAUNCH_CHECK();
-                    // y = P x in its own full-occupancy pass (formed inside the
-                    // FFT filter's load stage instead, its dependent map gather
-                    // left the filter latency-bound: 15.8 -> 23.7 ms at config 2)
                     float* y32 = workspace_as<float>(ctx, "y32", p->nsamples);
-                    pointing_apply_f32_kernel<<<grid_for(ctx, (p->nsamples + threads - 1) / threads, 16), threads, 0,
-                                                s>>>(p->pix.get(), p->cs_hi_t.get(), p->nsamples, x4, y32);
-                    BM_LAUNCH_CHECK();
+                    {
+                        ScopedTimer timer_px(ctx, "toeplitz_px");
+                        masked_copy4_kernel<<<grid_for(ctx, (p->npix + threads - 1) / threads, 16), threads, 0,
+                                              s>>>(xr, pc->mask.get(), p->npix, nc, x4);
+                        BM_LAUNCH_CHECK();
+                        // y = P x in its own full-occupancy pass (formed inside
+                        // the FFT filter's load stage instead, its dependent map
+                        // gather left the filter latency-bound: 15.8 -> 23.7 ms
+                        // at config 2)
+                        pointing_apply_f32_kernel<<<grid_for(ctx, (p->nsamples + threads - 1) / threads, 16),
+                                                    threads, 0, s>>>(p->pix.get(), p->cs_hi_t.get(), p->nsamples,
+                                                                     x4, y32);
+                        BM_LAUNCH_CHECK();
+                    }
                     apply_filter_f32(n, pc, SrcPlainF32{y32}, z32);
                 }
                 // scatter with the same FP32 trig the gather used (symmetric operator)

@@ -331,6 +331,7 @@ bm_status run_request(bm_context* ctx, Job& job) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     ctx->ws.clear();
+    ctx->ws_generation += 1;
     return st;
 }
 
@@ -448,6 +449,7 @@ bm_status run_keyed(bm_server* s, Plan& plan, const std::vector<Job*>& js) {
         cudaSetDevice(e->ctx->device);
         cudaStreamSynchronize(e->ctx->stream);
         e->ctx->ws.clear();
+        e->ctx->ws_generation += 1;
     }
     return st;
 }

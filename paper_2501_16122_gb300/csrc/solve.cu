@@ -327,18 +327,147 @@ CgState read_state(bm_context* ctx, const CgState* st) {
     return h;
 }
 
+// Loop control of the WHILE node below: loop[0] counts the iterations of the
+// current graph launch (inc = 1 after an iteration, 0 before the first),
+// loop[1] is their limit; the node goes on while the solve is not done and
+// the limit is not reached.
+__global__ void cg_loop_kernel(const CgState* __restrict__ st, int* __restrict__ loop, int inc,
+                               cudaGraphConditionalHandle h) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int it = loop[0] + inc;
+    loop[0] = it;
+    cudaGraphSetConditional(h, (st->done == 0 && it < loop[1]) ? 1u : 0u);
+}
+
+// The PCG iterations of a solve as one CUDA graph: cg_loop_kernel decides
+// whether to enter, then a WHILE node runs one iteration (matvec and CG
+// updates) followed by cg_loop_kernel, until the state is done or the limit
+// is reached; the host reads the state once afterwards instead of after
+// every iteration.  Built on the context's side stream after one eager
+// iteration (which makes every lazily built table and scratch buffer), for
+// a solve on one process without kernel timing; rebuilt if a workspace has
+// moved since (the graph holds their addresses).
+struct CgLoop {
+    cudaGraphExec_t exec = nullptr;
+    uint64_t generation = 0;
+    int64_t body_kernels = 0;
+    bool ok = true;
+    int* loop = nullptr;
+    ~CgLoop() {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
+
+template <int NC>
+void build_cg_loop(CgLoop& gl, Cg& cg, bm_pointing* p, bm_inv_noise* n, bm_precision prec) {
+    bm_context* ctx = cg.pc->ctx;
+    if (gl.exec) {
+        cudaGraphExecDestroy(gl.exec);
+        gl.exec = nullptr;
+    }
+    gl.loop = workspace_as<int>(ctx, "cg_loop", 2);
+    gl.generation = ctx->ws_generation;
+    cudaGraph_t graph = nullptr;
+    BM_CUDA(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess)
+        e = cudaStreamBeginCaptureToGraph(ctx->side, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cg_loop_kernel<<<1, 32, 0, ctx->side>>>(cg.st, gl.loop, 0, h);
+        e = cudaGetLastError();
+        const cudaError_t e2 = cudaStreamEndCapture(ctx->side, &graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    cudaGraphNode_t first = nullptr;
+    size_t nn = 1;
+    if (e == cudaSuccess) e = cudaGraphGetNodes(graph, &first, &nn);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&wnode, graph, &first, nullptr, 1, &cp);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(ctx->side, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const int64_t before = bm_kernel_launches();
+            cudaStream_t saved = ctx->stream;
+            ctx->stream = ctx->side;  // the matvec launches on the context stream
+            try {
+                cg_iteration<NC>(cg, p, n, prec, ctx->side);
+            } catch (...) {
+                ctx->stream = saved;
+                cudaStreamEndCapture(ctx->side, &body);
+                cudaGraphDestroy(graph);
+                throw;
+            }
+            ctx->stream = saved;
+            gl.body_kernels = bm_kernel_launches() - before + 1;  // + the loop kernel
+            count_launches(-(gl.body_kernels - 1));  // counted from the iterations that ran
+            cg_loop_kernel<<<1, 32, 0, ctx->side>>>(cg.st, gl.loop, 1, h);
+            e = cudaGetLastError();
+            const cudaError_t e2 = cudaStreamEndCapture(ctx->side, &body);
+            if (e == cudaSuccess) e = e2;
+        }
+    }
+    // a workspace made while capturing would be a graph allocation: not usable
+    if (e == cudaSuccess && ctx->ws_generation != gl.generation) e = cudaErrorStreamCaptureUnsupported;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&gl.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    BM_CUDA(e);
+}
+
 // PCG on A x = b from x = 0 (x, r written into cg).  Returns iterations and the final state.
 template <int NC>
 CgState run_pcg(Cg& cg, bm_pointing* p, bm_inv_noise* n, const double* b, double tol, int maxiter,
-                bm_precision prec) {
-    cudaStream_t s = cg.pc->ctx->stream;
+                bm_precision prec, CgLoop* gl = nullptr) {
+    bm_context* ctx = cg.pc->ctx;
+    cudaStream_t s = ctx->stream;
     BM_CUDA(cudaMemsetAsync(cg.x, 0, sizeof(double) * cg.nvec, s));
     BM_CUDA(cudaMemcpyAsync(cg.r, b, sizeof(double) * cg.nvec, cudaMemcpyDeviceToDevice, s));
     cg_start<NC>(cg, b, cg.r, tol, s);
-    CgState h = read_state(cg.pc->ctx, cg.st);
-    for (int it = 0; it < maxiter && !h.done; ++it) {
+    CgState h = read_state(ctx, cg.st);
+    int it = 0;
+    if (!h.done && it < maxiter) {  // one iteration eagerly
         cg_iteration<NC>(cg, p, n, prec, s);
-        h = read_state(cg.pc->ctx, cg.st);
+        ++it;
+        h = read_state(ctx, cg.st);
+    }
+    const bool graph = gl && gl->ok && ctx->side && !ctx->allreduce && !ctx->timing;
+    if (graph && !h.done && it < maxiter) {
+        if (!gl->exec || gl->generation != ctx->ws_generation) {
+            try {
+                build_cg_loop<NC>(*gl, cg, p, n, prec);
+            } catch (const Error&) {  // no conditional graph here: the host-driven loop below
+                gl->ok = false;
+                if (gl->exec) cudaGraphExecDestroy(gl->exec);
+                gl->exec = nullptr;
+                cudaGetLastError();
+                clear_error();
+            }
+        }
+        if (gl->exec) {
+            const int hl[2] = {0, maxiter - it};
+            BM_CUDA(cudaMemcpyAsync(gl->loop, hl, sizeof(hl), cudaMemcpyHostToDevice, s));
+            BM_CUDA(cudaEventRecord(ctx->side_ev, s));
+            BM_CUDA(cudaStreamWaitEvent(ctx->side, ctx->side_ev, 0));
+            BM_CUDA(cudaGraphLaunch(gl->exec, ctx->side));
+            BM_CUDA(cudaEventRecord(ctx->side_ev, ctx->side));
+            BM_CUDA(cudaStreamWaitEvent(s, ctx->side_ev, 0));
+            BM_CUDA(cudaMemcpyAsync(ctx->h_pinned + 16, gl->loop, sizeof(int), cudaMemcpyDeviceToHost, s));
+            h = read_state(ctx, cg.st);  // synchronises the stream
+            int ran = 0;
+            memcpy(&ran, ctx->h_pinned + 16, sizeof(int));
+            count_launches(1 + (int64_t)ran * gl->body_kernels);
+            return h;
+        }
+    }
+    for (; it < maxiter && !h.done; ++it) {
+        cg_iteration<NC>(cg, p, n, prec, s);
+        h = read_state(ctx, cg.st);
     }
     return h;
 }
@@ -389,6 +518,7 @@ bm_status solve_one(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const doubl
     bm_solve_info inf{};
     bm_status status = BM_OK;
     double bb = 0.0;
+    CgLoop loop;
     {
         // ||b||^2 (as the residual of x = 0)
         BM_CUDA(cudaMemsetAsync(cg.x, 0, sizeof(double) * cg.nvec, s));
@@ -406,7 +536,7 @@ bm_status solve_one(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const doubl
     if (bb == 0.0) {
         inf.rel_residual = 0.0;
     } else if (prec == BM_PREC_FP64) {
-        CgState h = run_pcg<NC>(cg, p, n, b, tol, maxiter, BM_PREC_FP64);
+        CgState h = run_pcg<NC>(cg, p, n, b, tol, maxiter, BM_PREC_FP64, &loop);
         BM_CUDA(cudaMemcpyAsync(xs, cg.x, sizeof(double) * cg.nvec, cudaMemcpyDeviceToDevice, s));
         inf.iterations = h.iters;
         if (h.done == 2) status = BM_ERR_BREAKDOWN;
@@ -421,7 +551,8 @@ bm_status solve_one(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const doubl
         const int max_outer = 30;
         while (std::sqrt(rr) > tol * bnorm && inner_total < maxiter && outer < max_outer) {
             const double inner_tol = std::max(1e-6, 0.5 * tol * bnorm / std::sqrt(rr));
-            CgState h = run_pcg<NC>(cg, p, n, rs, std::min(inner_tol, 0.5), maxiter - inner_total, BM_PREC_MIXED);
+            CgState h = run_pcg<NC>(cg, p, n, rs, std::min(inner_tol, 0.5), maxiter - inner_total, BM_PREC_MIXED,
+                                    &loop);
             inner_total += h.iters;
             ++outer;
             if (h.done == 2 && h.iters == 0) { status = BM_ERR_BREAKDOWN; break; }
