@@ -213,8 +213,9 @@ def run_config2(args, noise="toeplitz"):
     ms = (time.perf_counter() - t0) * 1000 / args.steps
     clocks = sampler.stop()
     fam = {}
-    for name in ("ingest", "blocks", "rhs", "toeplitz_f32", "toeplitz_refine", "toeplitz_f64", "toeplitz_pt",
-                 "toeplitz_pt_df", "toeplitz_pt_bounds", "offset_filter_f64", "offset_means_f32",
+    for name in ("ingest", "blocks", "rhs", "toeplitz_f32", "toeplitz_px", "toeplitz_refine", "toeplitz_px_df",
+                 "toeplitz_f64", "toeplitz_pt", "toeplitz_pt_df", "toeplitz_pt_bounds", "offset_filter_f64",
+                 "offset_means_f32",
                  "offset_matvec_f32", "offset_means_df", "offset_pt_df", "ingest_validate", "ingest_hist",
                  "ingest_scatter"):
         tot, cnt = L.bm_context_kernel_time(ctx, name)
@@ -284,8 +285,12 @@ def run_config2(args, noise="toeplitz"):
         return
     # The band is applied by FFT overlap-save: per tile of H = N - 2(L-1)
     # outputs one real N-point transform pair (5 N log2 N flops) and the
-    # spectrum product (2N); its inputs are the window's pix + trig
-    # (12 B per input sample) and it writes z (4 B FP32 / 8 B FP64).
+    # spectrum product (2N); it reads the window of y = P x (4 B FP32, 8 B
+    # double-float or FP64 per input sample) and writes z (4 B / 8 B).  The
+    # FP32 and double-float families also hold the P x pass (timed on its
+    # own as toeplitz_px / toeplitz_px_df: pix + trig read, y written, 16 B
+    # a sample FP32 and 28 B double-float), which is taken out of the
+    # transform's time here.
     def fft_tiles(N):
         H = N - 2 * (nlags - 1)
         per_chunk = -(-chunk // H)
@@ -294,17 +299,22 @@ def run_config2(args, noise="toeplitz"):
     # (the refinement operator's double-float transform is counted in FP64
     #  flops against the FP32 pipes' rate / 20, about the cost of one
     #  double-float multiply-add)
-    for name, N, zb, peak, unit in (("toeplitz_f32", fft_size(nlags, chunk, 8192), 4, fp32_tf, "FP32"),
-                                    ("toeplitz_refine", fft_size(nlags, chunk, 4096), 8, fp32_tf / 20,
-                                     "FP32 double-float"),
-                                    ("toeplitz_f64", fft_size(nlags, chunk, 4096), 8, fp64_tf, "FP64")):
+    for name, px, N, zb, peak, unit in (("toeplitz_f32", "toeplitz_px", fft_size(nlags, chunk, 8192), 4, fp32_tf,
+                                         "FP32"),
+                                        ("toeplitz_refine", "toeplitz_px_df", fft_size(nlags, chunk, 4096), 8,
+                                         fp32_tf / 20, "FP32 double-float"),
+                                        ("toeplitz_f64", None, fft_size(nlags, chunk, 4096), 8, fp64_tf, "FP64")):
         ms_l = fam.get(name, {}).get("ms_per_launch")
         if not N or not ms_l:
             continue
+        px_ms = fam.get(px, {}).get("ms_per_launch", 0.0) if px else 0.0
+        ms_l = ms_l - px_ms
         tiles, H = fft_tiles(N)
         flops = tiles * (5.0 * N * math.log2(N) + 2.0 * N)
-        bytes_ = tiles * N * 12.0 + e.nsamples * zb
-        fam_fft[name] = {"fft_n": N, "tiles": tiles, "ms_per_launch": ms_l,
+        bytes_ = tiles * N * zb + e.nsamples * zb
+        fam_fft[name] = {"fft_n": N, "tiles": tiles, "ms_per_launch": ms_l, "px_ms": px_ms,
+                         "px_hbm_frac": (e.nsamples * (16 if zb == 4 else 28) / (px_ms * 1e-3) / 1e9 / hbm_peak()
+                                         if px_ms else None),
                          "tflops": flops / (ms_l * 1e-3) / 1e12, "peak_tflops": peak, "pipe": unit,
                          "flop_frac": flops / (ms_l * 1e-3) / 1e12 / peak,
                          "gbs": bytes_ / (ms_l * 1e-3) / 1e9, "hbm_frac": bytes_ / (ms_l * 1e-3) / 1e9 / hbm_peak()}

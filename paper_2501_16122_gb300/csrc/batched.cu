@@ -8,7 +8,8 @@
 // contiguous values.
 //
 // Kernels (one warp per work item, lanes over right-hand sides, RPL per lane):
-//   batched_rhs:    b_{p,r} = sum_{t in p} w_d d_r[t] v_t   (double-float)
+//   batched_rhs:    b_{p,r} = sum_{t in p} w_d d_r[t] v_t   (double-float,
+//                   lazily renormalised as the single-RHS gather-reduce)
 //   batched_matvec: q_{p,r} = sum_{t in p} u_t (u_t . x_{p,r}) with the FP32
 //                   weighted stream u_t = sqrt(w)(1?, cos, sin): FP32 products,
 //                   compensated (double-float) sums
@@ -38,7 +39,7 @@ namespace bm {
 
 namespace {
 
-constexpr int kRB = 256;   // reduction blocks for per-RHS dot products
+constexpr int kRB = 2048;  // most blocks of the per-pixel PCG kernels (a full wave: enough loads in flight for HBM)
 constexpr int kRT = 256;   // threads per reduction block
 
 struct RhsState {
@@ -156,6 +157,7 @@ batched_rhs_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restri
         for (int q = 0; q < RPL; ++q)
 #pragma unroll
             for (int c = 0; c < NC; ++c) acc[q][c] = {0.f, 0.f};
+        int nadd = 0;
         for (int base = 0; base < len; base += 32) {
             const int j = base + lane;
             const bool valid = j < len;
@@ -168,26 +170,27 @@ batched_rhs_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restri
                 wl = wp[det_of(offp, ndet, dt.ns, dt.inv_ns, tl)];
             }
             const int cnt = min(32, len - base);
-            // sample kk of the chunk: its row of the G right-hand sides, added in order
+            // sample kk of the chunk: its row of the G right-hand sides, added
+            // in order in the lazily renormalised form (rhs_term_lazy)
             auto add = [&](int kk, const T (&dv)[RPL]) {
-                const df32 w = {__shfl_sync(0xffffffffu, wl.x, kk), __shfl_sync(0xffffffffu, wl.y, kk)};
-                const df32 c = {__shfl_sync(0xffffffffu, h.x, kk), __shfl_sync(0xffffffffu, l.x, kk)};
-                const df32 s = {__shfl_sync(0xffffffffu, h.y, kk), __shfl_sync(0xffffffffu, l.y, kk)};
+                const float2 w = {__shfl_sync(0xffffffffu, wl.x, kk), __shfl_sync(0xffffffffu, wl.y, kk)};
+                const float2 hh = {__shfl_sync(0xffffffffu, h.x, kk), __shfl_sync(0xffffffffu, h.y, kk)};
+                const float2 ll = {__shfl_sync(0xffffffffu, l.x, kk), __shfl_sync(0xffffffffu, l.y, kk)};
 #pragma unroll
                 for (int q = 0; q < RPL; ++q) {
                     if (lane + 32 * q < G) {
                         df32 d;
                         if (sizeof(T) == 4) d = {(float)dv[q], 0.f};
                         else d = df_from((double)dv[q]);
-                        const df32 wd = df_mul(d, w);
-                        if (NC == 1) {
-                            acc[q][0] = df_add(acc[q][0], wd);
-                        } else {
-                            if (NC == 3) acc[q][0] = df_add(acc[q][0], wd);
-                            acc[q][NC - 2] = df_add(acc[q][NC - 2], df_mul(wd, c));
-                            acc[q][NC - 1] = df_add(acc[q][NC - 1], df_mul(wd, s));
-                        }
+                        rhs_term_lazy<NC>(acc[q], d.hi, d.lo, true, w, hh, ll);
                     }
+                }
+                if (++nadd == kLazyNorm) {
+                    nadd = 0;
+#pragma unroll
+                    for (int q = 0; q < RPL; ++q)
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) acc_norm(acc[q][c]);
                 }
             };
             auto row = [&](int kk, T (&dv)[RPL]) {
@@ -219,7 +222,10 @@ batched_rhs_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restri
             if (r < G) {
                 double* dst = item_dst(pitem, p, k, R, NC, r0 + r, out, partial);
 #pragma unroll
-                for (int c = 0; c < NC; ++c) dst[c] = df_to_double(acc[q][c]);
+                for (int c = 0; c < NC; ++c) {
+                    acc_norm(acc[q][c]);
+                    dst[c] = df_to_double(acc[q][c]);
+                }
             }
         }
     }
@@ -547,15 +553,27 @@ __global__ void b_sum2_kernel(const double* __restrict__ part, int nblk, int R, 
     out[R + r] = b;
 }
 
-// maps[r][p][c] = x[p][r][c] (NaN on masked pixels)
+// maps[r][p][c] = x[p][r][c] (NaN on masked pixels), by tiles of P pixels:
+// the tile's block of x (P R NC contiguous values) is staged in shared memory
+// and each map's P NC contiguous values are written as one run.
 __global__ void b_write_map_kernel(const double* __restrict__ x, const uint8_t* __restrict__ mask, int64_t npix,
-                                   int R, int NC, double* const* __restrict__ maps) {
-    const int64_t n = npix * R * NC;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = i / ((int64_t)R * NC);
-        const int64_t rem = i - p * R * NC;
-        const int r = (int)(rem / NC), c = (int)(rem - (int64_t)r * NC);
-        maps[r][p * NC + c] = mask[p] ? NAN : x[i];
+                                   int R, int NC, int P, double* const* __restrict__ maps) {
+    extern __shared__ double map_tile[];  // [P R NC]
+    const int per = R * NC;
+    const int64_t ntiles = (npix + P - 1) / P;
+    for (int64_t tb = blockIdx.x; tb < ntiles; tb += gridDim.x) {
+        const int64_t p0 = tb * P;
+        const int np = (int)(npix - p0 < P ? npix - p0 : P);
+        const double* src = x + p0 * per;
+        for (int i = threadIdx.x; i < np * per; i += blockDim.x) map_tile[i] = src[i];
+        __syncthreads();
+        const int run = np * NC;
+        for (int i = threadIdx.x; i < R * run; i += blockDim.x) {
+            const int r = i / run, j = i - r * run;
+            const int pl = j / NC, c = j - pl * NC;
+            maps[r][(p0 + pl) * NC + c] = mask[p0 + pl] ? NAN : map_tile[(pl * R + r) * NC + c];
+        }
+        __syncthreads();
     }
 }
 
@@ -747,7 +765,15 @@ bm_status batched_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const v
     int Rp = 1;
     while (Rp < R) Rp <<= 1;
     BGeo geo{R, Rp, kRT / Rp, npix};
-    const int rgrid = kRB;
+    // per-pixel PCG kernels: one wave of resident blocks (at most kRB)
+    int per_sm = 64;
+    for (const void* k : {reinterpret_cast<const void*>(b_residual_kernel<NC>),
+                          reinterpret_cast<const void*>(b_init_kernel<NC>),
+                          reinterpret_cast<const void*>(b_update_kernel<NC>),
+                          reinterpret_cast<const void*>(b_dot_kernel),
+                          reinterpret_cast<const void*>(b_pupdate_kernel)})
+        per_sm = std::min(per_sm, blocks_per_sm(k, kRT, 0));
+    const int rgrid = std::min(kRB, std::max(per_sm, 1) * ctx->num_sms);
     const int sgrid = (R + 127) / 128;
 
     // x = 0; r = b (masked), per-RHS ||b||
@@ -929,8 +955,14 @@ bm_status batched_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const v
     }
     if (gexec) cudaGraphExecDestroy(gexec);
 
-    b_write_map_kernel<<<vgrid, threads, 0, s>>>(bb.x, pc->mask.get(), npix, R, NC, d_maps);
-    BM_LAUNCH_CHECK();
+    {
+        const int P = std::max(1, 4096 / RNC);  // pixels a tile: at most 32 KB of x staged
+        const size_t smem = sizeof(double) * (size_t)P * RNC;
+        const int64_t ntiles = (npix + P - 1) / P;
+        b_write_map_kernel<<<resident_grid(ctx, b_write_map_kernel, threads, ntiles, smem), threads, smem, s>>>(
+            bb.x, pc->mask.get(), npix, R, NC, P, d_maps);
+        BM_LAUNCH_CHECK();
+    }
     BM_CUDA(cudaStreamSynchronize(s));
     bm_status first = BM_OK;
     for (int r = 0; r < R; ++r) {

@@ -476,23 +476,41 @@ toeplitz_fft_kernel(Src src, const typename FftIO<T>::spec_t* __restrict__ spec,
     }
 }
 
+// cost[e] = cos(2 pi e / N), e = 0..N-1, in FP64.
+__global__ void cos_table_kernel(int N, double* __restrict__ cost) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < N; e += gridDim.x * blockDim.x)
+        cost[e] = cospi(2.0 * (double)e / (double)N);
+}
+
 // K[d][k] = c_0 + 2 sum_{j=1}^{L-1} c_j cos(2 pi j k / N), k = 0..N/2, in FP64
-// (the argument reduced exactly with the integer j k mod N).
-__global__ void band_spectrum_kernel(const double* __restrict__ coeffs, int ndet, int L, int N,
-                                     double* __restrict__ spec64, float* __restrict__ spec32,
-                                     float2* __restrict__ spec_df) {
+// (the argument reduced exactly: the integer j k mod N, stepped by k, indexes
+// the table cost of cos(2 pi e / N), staged in shared memory with the
+// detector's band).  Block b handles detector b / kb_per_det and the
+// kBandK values of k from (b mod kb_per_det) kBandK.
+constexpr int kBandK = 1024;
+__global__ void band_spectrum_kernel(const double* __restrict__ coeffs, const double* __restrict__ cost, int ndet,
+                                     int L, int N, int kb_per_det, double* __restrict__ spec64,
+                                     float* __restrict__ spec32, float2* __restrict__ spec_df) {
+    extern __shared__ __align__(16) unsigned char band_smem[];
+    double* tab = reinterpret_cast<double*>(band_smem);  // [N]
+    double* c = tab + N;                                 // [L]
     const int M = N / 2;
-    const int64_t total = (int64_t)ndet * (M + 1);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int d = (int)(i / (M + 1));
-        const int k = (int)(i - (int64_t)d * (M + 1));
-        const double* c = coeffs + (int64_t)d * L;
+    const int d = blockIdx.x / kb_per_det;
+    const int k0 = (blockIdx.x % kb_per_det) * kBandK;
+    if (d >= ndet) return;
+    for (int e = threadIdx.x; e < N; e += blockDim.x) tab[e] = cost[e];
+    for (int j = threadIdx.x; j < L; j += blockDim.x) c[j] = coeffs[(int64_t)d * L + j];
+    __syncthreads();
+    for (int k = k0 + threadIdx.x; k < min(k0 + kBandK, M + 1); k += blockDim.x) {
         double s = 0.0;
+        int e = 0;  // j k mod N
         for (int j = 1; j < L; ++j) {
-            const int64_t e = ((int64_t)j * k) % N;
-            s += c[j] * cospi(2.0 * (double)e / (double)N);
+            e += k;
+            if (e >= N) e -= N;
+            s += c[j] * tab[e];
         }
         const double v = c[0] + 2.0 * s;
+        const int64_t i = (int64_t)d * (M + 1) + k;
         if (spec64) spec64[i] = v;
         if (spec32) spec32[i] = (float)v;
         if (spec_df) {

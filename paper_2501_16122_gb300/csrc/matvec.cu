@@ -547,33 +547,16 @@ pt_chunk_kernel(const int32_t* __restrict__ seg_pix, const uint32_t* __restrict_
     constexpr int G = 32 / kPtLanes;
     constexpr int U = 8;
     const int lane = threadIdx.x & 31, gl = lane % kPtLanes, grp = lane / kPtLanes;
-    const int64_t stride = (int64_t)gridDim.x * kWarps * G;
-    // A group's segment metadata is loaded one iteration ahead, and its
-    // pixel's accumulator before the samples (this group is its only writer
-    // in the launch), so that the iteration waits on the sample streams and
-    // the gather of z only.
-    auto meta = [&](int64_t k, int64_t& p, int64_t& b, int32_t& len) {
-        p = 0;
-        b = 0;
-        len = 0;
+    const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+    for (int64_t kw = ((int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5)) * G; kw < nseg; kw += nwarps * G) {
+        const int64_t k = kw + grp;
+        int64_t p = 0, b = 0;
+        int32_t len = 0;
         if (k < nseg) {
             p = seg_pix[seg0 + k];
             b = seg_beg[seg0 + k];
             len = seg_len[seg0 + k];
         }
-    };
-    int64_t kw = ((int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5)) * G;
-    int64_t p, b;
-    int32_t len;
-    meta(kw + grp, p, b, len);
-    for (; kw < nseg; kw += stride) {
-        int64_t pn, bn;
-        int32_t lenn;
-        meta(kw + stride + grp, pn, bn, lenn);
-        const bool writer = gl == 0 && len > 0;
-        float2 old[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) old[c] = writer ? acc[p * NC + c] : make_float2(0.f, 0.f);
         float a[NC];
         df32 A[NC];
 #pragma unroll
@@ -614,16 +597,14 @@ pt_chunk_kernel(const int32_t* __restrict__ seg_pix, const uint32_t* __restrict_
 #pragma unroll
             for (int o = kPtLanes / 2; o > 0; o >>= 1) A[c] = df_add(A[c], df_shfl_xor(A[c], o));
         }
-        if (writer) {
+        if (gl == 0 && len > 0) {
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                const df32 s = df_add(df32{old[c].x, old[c].y}, A[c]);
+                const float2 old = acc[p * NC + c];
+                const df32 s = df_add(df32{old.x, old.y}, A[c]);
                 acc[p * NC + c] = make_float2(s.hi, s.lo);
             }
         }
-        p = pn;
-        b = bn;
-        len = lenn;
     }
 }
 
@@ -635,8 +616,9 @@ pt_chunk_kernel(const int32_t* __restrict__ seg_pix, const uint32_t* __restrict_
 // summed in the lazily renormalised double-float form of the gather-reduce
 // (rhs_term_lazy) by kPtLanes lanes per segment, then added to the pixel's
 // double-float accumulator (one writer per launch; launches in time order).
-// Metadata one iteration ahead and the accumulator read early, as in
-// pt_chunk_kernel.
+// Metadata one iteration ahead and the accumulator read early (the FP32
+// pt_chunk_kernel measured slower with the same change: its extra registers
+// cut it from five resident blocks per SM to four).
 template <int NC>
 __global__ void __launch_bounds__(kWarps * 32)
 pt_chunk_df_kernel(const int32_t* __restrict__ seg_pix, const uint32_t* __restrict__ seg_beg,
@@ -998,6 +980,22 @@ static void run_toeplitz(bm_inv_noise* n, const Src& src, const T* coeffs, T* z)
     BM_LAUNCH_CHECK();  // tile_start is released stream-ordered after the kernel
 }
 
+// The band spectra of every detector for an N-point transform (see
+// band_spectrum_kernel), in the requested forms.
+static void band_spectrum(bm_inv_noise* n, int N, double* spec64, float* spec32, float2* spec_df) {
+    bm_context* ctx = n->ctx;
+    const int threads = 256;
+    DevBuf<double> cost(N);
+    cos_table_kernel<<<(N + threads - 1) / threads, threads, 0, ctx->stream>>>(N, cost.get());
+    BM_LAUNCH_CHECK();
+    const int kb = (N / 2 + 1 + kBandK - 1) / kBandK;
+    const size_t smem = sizeof(double) * ((size_t)N + (size_t)n->nlags);
+    ensure_smem_limit(reinterpret_cast<const void*>(band_spectrum_kernel), smem);
+    band_spectrum_kernel<<<(unsigned)((int64_t)n->ndet * kb), threads, smem, ctx->stream>>>(
+        n->coeffs64.get(), cost.get(), n->ndet, n->nlags, N, kb, spec64, spec32, spec_df);
+    BM_LAUNCH_CHECK();  // the table is released stream-ordered after the kernel
+}
+
 // FFT size for a band of L lags: the smallest power of two with at least half
 // of each transform producing outputs (H >= N/2), grown toward a whole chunk,
 // at most `cap`; 0 if the band is too long for `cap` (direct filter).
@@ -1025,10 +1023,7 @@ void prepare_toeplitz_fft(bm_inv_noise* n) {
         const int N = n->fft_n32;
         n->spec32.alloc((size_t)n->ndet * (N / 2 + 1));
         n->tw32.alloc(N);
-        band_spectrum_kernel<<<grid_for(ctx, ((int64_t)n->ndet * (N / 2 + 1) + threads - 1) / threads, 16), threads, 0,
-                               ctx->stream>>>(n->coeffs64.get(), n->ndet, n->nlags, N, nullptr, n->spec32.get(),
-                                              nullptr);
-        BM_LAUNCH_CHECK();
+        band_spectrum(n, N, nullptr, n->spec32.get(), nullptr);
         twiddle_kernel<<<(N + threads - 1) / threads, threads, 0, ctx->stream>>>(N, nullptr, n->tw32.get());
         BM_LAUNCH_CHECK();
     }
@@ -1037,10 +1032,7 @@ void prepare_toeplitz_fft(bm_inv_noise* n) {
         n->spec64.alloc((size_t)n->ndet * (N / 2 + 1));
         n->spec_df.alloc((size_t)n->ndet * (N / 2 + 1));
         n->tw64.alloc(N);
-        band_spectrum_kernel<<<grid_for(ctx, ((int64_t)n->ndet * (N / 2 + 1) + threads - 1) / threads, 16), threads, 0,
-                               ctx->stream>>>(n->coeffs64.get(), n->ndet, n->nlags, N, n->spec64.get(), nullptr,
-                                              n->spec_df.get());
-        BM_LAUNCH_CHECK();
+        band_spectrum(n, N, n->spec64.get(), nullptr, n->spec_df.get());
         twiddle_kernel<<<(N + threads - 1) / threads, threads, 0, ctx->stream>>>(N, n->tw64.get(), nullptr);
         BM_LAUNCH_CHECK();
     }
@@ -1903,9 +1895,13 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
                 {
                     ScopedTimer timer(ctx, "toeplitz_refine");
                     float2* y2 = workspace_as<float2>(ctx, "y_df", p->nsamples);
-                    pointing_apply_df_kernel<<<grid_for(ctx, (p->nsamples + threads - 1) / threads, 16), threads, 0, s>>>(
-                        p->pix.get(), p->cs_hi_t.get(), p->cs_lo_t.get(), p->nsamples, x2, y2);
-                    BM_LAUNCH_CHECK();
+                    {
+                        ScopedTimer timer_px(ctx, "toeplitz_px_df");
+                        pointing_apply_df_kernel<<<grid_for(ctx, (p->nsamples + threads - 1) / threads, 16),
+                                                   threads, 0, s>>>(p->pix.get(), p->cs_hi_t.get(),
+                                                                    p->cs_lo_t.get(), p->nsamples, x2, y2);
+                        BM_LAUNCH_CHECK();
+                    }
                     apply_toeplitz_df(n, SrcPlainDF{y2}, z2);
                 }
                 ScopedTimer timer(ctx, "toeplitz_pt_df");
