@@ -2,7 +2,9 @@
 // pointing (noise or signal realisations), solved together so that every
 // pass over the pointing serves all R of them.
 //
-// Layout: vectors are RHS-interleaved, [npix][R][ncomp].  The caller's TOD
+// Layout: vectors are RHS-interleaved, [npix][ncomp][R] (per pixel and
+// Stokes component the R right-hand sides are contiguous, so a warp over
+// right-hand sides reads and writes whole lines).  The caller's TOD
 // [R][nsamples] is transposed group by group (G <= 32 * RPL right-hand sides)
 // into [nsamples][G], so that the pixel-sorted gather of one sample reads G
 // contiguous values.
@@ -122,8 +124,8 @@ __global__ void __launch_bounds__(256) transpose_f32x4_kernel(const float* const
 // is its pixel's only item, else the item's partial slot.
 __device__ __forceinline__ double* item_dst(const int64_t* pitem, int64_t p, int64_t k, int R, int NC, int r,
                                             double* out, double* partial) {
-    if (pitem[p + 1] - pitem[p] == 1) return out + ((int64_t)p * R + r) * NC;
-    return partial + ((int64_t)k * R + r) * NC;
+    if (pitem[p + 1] - pitem[p] == 1) return out + (int64_t)p * NC * R + r;
+    return partial + (int64_t)k * NC * R + r;
 }
 
 // ---------------------------------------------------------------- batched RHS
@@ -201,14 +203,21 @@ batched_rhs_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restri
                     dv[q] = r < G ? dT[(int64_t)t * G + r] : T(0);
                 }
             };
-            // eight rows in flight, then their sums in sample order
+            // sixteen rows in flight, then their sums in sample order
             int kk = 0;
-            for (; kk + 8 <= cnt; kk += 8) {
-                T dv[8][RPL];
+            for (; kk + 16 <= cnt; kk += 16) {
+                T dv[16][RPL];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) row(kk + u, dv[u]);
+                for (int u = 0; u < 16; ++u) row(kk + u, dv[u]);
 #pragma unroll
-                for (int u = 0; u < 8; ++u) add(kk + u, dv[u]);
+                for (int u = 0; u < 16; ++u) add(kk + u, dv[u]);
+            }
+            for (; kk + 4 <= cnt; kk += 4) {
+                T dv[4][RPL];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) row(kk + u, dv[u]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) add(kk + u, dv[u]);
             }
             for (; kk < cnt; ++kk) {
                 T dv[RPL];
@@ -224,7 +233,7 @@ batched_rhs_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restri
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
                     acc_norm(acc[q][c]);
-                    dst[c] = df_to_double(acc[q][c]);
+                    dst[(int64_t)c * R] = df_to_double(acc[q][c]);
                 }
             }
         }
@@ -253,7 +262,7 @@ batched_matvec_kernel(const int32_t* __restrict__ item_pix, const int64_t* __res
             const int r = lane + 32 * q;
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                xv[q][c] = r < G ? x32[((int64_t)p * R + r0 + r) * NC + c] : 0.f;
+                xv[q][c] = r < G ? x32[((int64_t)p * NC + c) * R + r0 + r] : 0.f;
                 g[q][c] = 0.f;
                 A[q][c] = {0.f, 0.f};
             }
@@ -305,7 +314,7 @@ batched_matvec_kernel(const int32_t* __restrict__ item_pix, const int64_t* __res
             if (r < G) {
                 double* dst = item_dst(pitem, p, k, R, NC, r0 + r, out, partial);
 #pragma unroll
-                for (int c = 0; c < NC; ++c) dst[c] = df_to_double(df_add(A[q][c], g[q][c]));
+                for (int c = 0; c < NC; ++c) dst[(int64_t)c * R] = df_to_double(df_add(A[q][c], g[q][c]));
             }
         }
     }
@@ -327,7 +336,7 @@ __global__ void batched_finalize_kernel(const int64_t* __restrict__ pitem, const
     }
 }
 
-// [npix][R][NC] FP64 -> FP32 with masked pixels zeroed.
+// [npix][NC][R] FP64 -> FP32 with masked pixels zeroed.
 __global__ void batched_masked_f32_kernel(const double* __restrict__ x, const uint8_t* __restrict__ mask,
                                           int64_t npix, int RNC, float* __restrict__ out) {
     const int64_t n = npix * RNC;
@@ -380,17 +389,20 @@ __global__ void __launch_bounds__(kRT) b_residual_kernel(BGeo g, const double* _
     double s_rr = 0.0, s_bb = 0.0;
     if (rr_ < g.R) {
         for (int64_t p = (int64_t)blockIdx.x * g.ppb + sub; p < g.npix; p += (int64_t)gridDim.x * g.ppb) {
-            const int64_t o = (p * g.R + rr_) * NC;
+            const int64_t o = p * NC * g.R + rr_;
             double xv[NC], bx[NC];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) xv[c] = x[o + c];
+            for (int c = 0; c < NC; ++c) xv[c] = x[o + c * g.R];
             apply_block<NC>(B, p, xv, bx);
             const bool keep = mask[p] == 0;
+            double bl[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) bl[c] = b[o + c * g.R];  // not behind the mask load
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                const double bv = keep ? b[o + c] : 0.0;
+                const double bv = keep ? bl[c] : 0.0;
                 const double v = keep ? bv - bx[c] : 0.0;
-                r[o + c] = v;
+                r[o + c * g.R] = v;
                 s_rr += v * v;
                 s_bb += bv * bv;
             }
@@ -411,17 +423,17 @@ __global__ void __launch_bounds__(kRT) b_init_kernel(BGeo g, const double* __res
     double s_rz = 0.0, s_rr = 0.0;
     if (rr_ < g.R) {
         for (int64_t p = (int64_t)blockIdx.x * g.ppb + sub; p < g.npix; p += (int64_t)gridDim.x * g.ppb) {
-            const int64_t o = (p * g.R + rr_) * NC;
+            const int64_t o = p * NC * g.R + rr_;
             double rv[NC], zv[NC];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) rv[c] = rin[o + c];
+            for (int c = 0; c < NC; ++c) rv[c] = rin[o + c * g.R];
             apply_block<NC>(M, p, rv, zv);
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                e[o + c] = 0.0;
-                rcg[o + c] = rv[c];
-                z[o + c] = zv[c];
-                pv[o + c] = zv[c];
+                e[o + c * g.R] = 0.0;
+                rcg[o + c * g.R] = rv[c];
+                z[o + c * g.R] = zv[c];
+                pv[o + c * g.R] = zv[c];
                 s_rz += rv[c] * zv[c];
                 s_rr += rv[c] * rv[c];
             }
@@ -457,8 +469,8 @@ __global__ void __launch_bounds__(kRT) b_dot_kernel(BGeo g, int NCr, const doubl
     double s = 0.0;
     if (rr_ < g.R) {
         for (int64_t p = (int64_t)blockIdx.x * g.ppb + sub; p < g.npix; p += (int64_t)gridDim.x * g.ppb) {
-            const int64_t o = (p * g.R + rr_) * NCr;
-            for (int c = 0; c < NCr; ++c) s += a[o + c] * b[o + c];
+            const int64_t o = p * NCr * g.R + rr_;
+            for (int c = 0; c < NCr; ++c) s += a[o + c * g.R] * b[o + c * g.R];
         }
     }
     block_rhs_reduce(s, sh, g, part, 0);
@@ -486,18 +498,18 @@ __global__ void __launch_bounds__(kRT) b_update_kernel(BGeo g, const double* __r
     if (rr_ < g.R && !st[rr_].done) {
         const double alpha = st[rr_].alpha;
         for (int64_t p = (int64_t)blockIdx.x * g.ppb + sub; p < g.npix; p += (int64_t)gridDim.x * g.ppb) {
-            const int64_t o = (p * g.R + rr_) * NC;
+            const int64_t o = p * NC * g.R + rr_;
             double rv[NC], zv[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                e[o + c] += alpha * pv[o + c];
-                rv[c] = rcg[o + c] - alpha * q[o + c];
-                rcg[o + c] = rv[c];
+                e[o + c * g.R] += alpha * pv[o + c * g.R];
+                rv[c] = rcg[o + c * g.R] - alpha * q[o + c * g.R];
+                rcg[o + c * g.R] = rv[c];
             }
             apply_block<NC>(M, p, rv, zv);
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                z[o + c] = zv[c];
+                z[o + c * g.R] = zv[c];
                 s_rr += rv[c] * rv[c];
                 s_rz += rv[c] * zv[c];
             }
@@ -530,8 +542,8 @@ __global__ void __launch_bounds__(kRT) b_pupdate_kernel(BGeo g, int NCr, double*
     if (rr_ >= g.R || st[rr_].done) return;
     const double beta = st[rr_].beta;
     for (int64_t p = (int64_t)blockIdx.x * g.ppb + sub; p < g.npix; p += (int64_t)gridDim.x * g.ppb) {
-        const int64_t o = (p * g.R + rr_) * NCr;
-        for (int c = 0; c < NCr; ++c) pv[o + c] = z[o + c] + beta * pv[o + c];
+        const int64_t o = p * NCr * g.R + rr_;
+        for (int c = 0; c < NCr; ++c) pv[o + c * g.R] = z[o + c * g.R] + beta * pv[o + c * g.R];
     }
 }
 
@@ -571,7 +583,7 @@ __global__ void b_write_map_kernel(const double* __restrict__ x, const uint8_t* 
         for (int i = threadIdx.x; i < R * run; i += blockDim.x) {
             const int r = i / run, j = i - r * run;
             const int pl = j / NC, c = j - pl * NC;
-            maps[r][(p0 + pl) * NC + c] = mask[p0 + pl] ? NAN : map_tile[(pl * R + r) * NC + c];
+            maps[r][(p0 + pl) * NC + c] = mask[p0 + pl] ? NAN : map_tile[(pl * NC + c) * R + r];
         }
         __syncthreads();
     }
@@ -639,7 +651,7 @@ void launch_rhs_v(bm_context* ctx, bm_pointing* p, bm_inv_noise* n, bm_precond* 
 // the transposed copy holds nsamples x 32 values at most.
 int rhs_group(int R) { return R < 32 ? R : 32; }
 
-// The batched solver's device buffers, all RHS-interleaved [npix][R][NC].
+// The batched solver's device buffers, all RHS-interleaved [npix][NC][R].
 struct BatchBufs {
     double *b, *x, *r, *e, *rcg, *z, *pv, *q, *partial, *part, *tolr, *sums;
     float* x32;

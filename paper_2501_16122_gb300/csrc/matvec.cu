@@ -819,9 +819,9 @@ __global__ void pointing_apply_f32_kernel(const int32_t* __restrict__ pix, const
     const int4* pix4 = reinterpret_cast<const int4*>(pix);
     const float4* hi4 = reinterpret_cast<const float4*>(hi);
     float4* y4 = reinterpret_cast<float4*>(y);
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += stride) {
-        const int4 p = __ldcs(pix4 + q);
-        const float4 ha = __ldcs(hi4 + 2 * q), hb = __ldcs(hi4 + 2 * q + 1);
+    // two groups of four per iteration, all their loads issued first (more
+    // memory requests in flight per thread)
+    auto group = [&](const int4 p, const float4 ha, const float4 hb, int64_t q) {
         const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 x0 = p.x >= 0 ? x4[p.x] : z, x1 = p.y >= 0 ? x4[p.y] : z;
         const float4 x2 = p.z >= 0 ? x4[p.z] : z, x3 = p.w >= 0 ? x4[p.w] : z;
@@ -831,7 +831,17 @@ __global__ void pointing_apply_f32_kernel(const int32_t* __restrict__ pix, const
         out.z = fmaf(hb.x, x2.y, fmaf(hb.y, x2.z, x2.x));
         out.w = fmaf(hb.z, x3.y, fmaf(hb.w, x3.z, x3.x));
         y4[q] = out;
+    };
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; q + stride < nq; q += 2 * stride) {
+        const int64_t q2 = q + stride;
+        const int4 pa = __ldcs(pix4 + q), pb = __ldcs(pix4 + q2);
+        const float4 ha = __ldcs(hi4 + 2 * q), hb = __ldcs(hi4 + 2 * q + 1);
+        const float4 hc = __ldcs(hi4 + 2 * q2), hd = __ldcs(hi4 + 2 * q2 + 1);
+        group(pa, ha, hb, q);
+        group(pb, hc, hd, q2);
     }
+    if (q < nq) group(__ldcs(pix4 + q), __ldcs(hi4 + 2 * q), __ldcs(hi4 + 2 * q + 1), q);
     // the last n mod 4 samples
     for (int64_t t = 4 * nq + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
         const int32_t pp = pix[t];
