@@ -559,6 +559,9 @@ def run_gb300(args, rank, world, local_rank):
         last = infos[-1][1]
         line = {
             "metric": METRIC, "value": nt_total / (ms_max * 1e-3), "unit": "TOD samples/s",
+            "value_basis": ("the step's TOD samples / the whole step's time (ingest + preconditioner + RHS + "
+                            "PCG to tol); the PᵀN⁻¹P matvec alone is under 'matvec', the time-to-map without "
+                            "the ingest under 'time_to_map_ms'"),
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
             "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
             "dtype": "f32",

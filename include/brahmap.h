@@ -335,10 +335,12 @@ bm_status bm_matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const doubl
  * until the process exits.  The array holds one FP64 value per work item and
  * Stokes component; a problem needing more than 2^21 values is rejected
  * with BM_ERR_INVALID (use bm_matvec).  x, q device FP64 [npix][ncomp]; n
- * must be the diagonal noise pc was built from.  The first call on a device
- * looks the array's address up (cudaGetSymbolAddress); make it before any
- * stream capture.  All calls share the array: calls that overlap on the GPU
- * race, so serialise them. */
+ * must be the diagonal noise pc was built from (a weight per detector or
+ * per sample).  bm_context_create looks the array's address up and loads
+ * the kernels' code, so no call maps memory, not even the first.  The call
+ * synchronises the context stream before it returns (so it cannot be
+ * captured into a CUDA graph).  All calls share the array: calls that
+ * overlap on the GPU race, so serialise them. */
 bm_status bm_matvec_white_static(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x,
                                  double* q);
 

@@ -72,7 +72,7 @@ __global__ void transpose_group_kernel(const T* const* __restrict__ rows, int64_
     }
 }
 
-// FP32 rows -> [n][G] (G <= 32) by tiles of kTT samples x G rows staged in
+// FP32 rows -> [n][G] (G <= 64) by tiles of kTT samples x G rows staged in
 // shared memory: each row's samples are loaded as float4 runs (streaming,
 // read once), and the tile's output, one contiguous block of kTT G floats,
 // is stored as float4 runs.  Rows must start on 16-byte boundaries.
@@ -80,7 +80,7 @@ constexpr int kTT = 128;
 
 __global__ void __launch_bounds__(256) transpose_f32x4_kernel(const float* const* __restrict__ rows, int64_t n, int r0,
                                                               int G, float* __restrict__ out) {
-    __shared__ float tile[32][kTT + 1];
+    __shared__ float tile[64][kTT + 1];
     for (int64_t t0 = (int64_t)blockIdx.x * kTT; t0 < n; t0 += (int64_t)gridDim.x * kTT) {
         const int cnt = (int)min((int64_t)kTT, n - t0);
         for (int i = threadIdx.x; i < G * (kTT / 4); i += blockDim.x) {
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(256) transpose_f32x4_kernel(const float* const
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int e = j + k;
-                const int tt = G == 32 ? (e >> 5) : e / G;
+                const int tt = G == 32 ? (e >> 5) : (G == 64 ? (e >> 6) : e / G);
                 v[k] = e < total ? tile[e - tt * G][tt] : 0.f;
             }
             if (j + 4 <= total) {
@@ -203,14 +203,16 @@ batched_rhs_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restri
                     dv[q] = r < G ? dT[(int64_t)t * G + r] : T(0);
                 }
             };
-            // sixteen rows in flight, then their sums in sample order
+            // sixteen (one RHS a lane) or eight rows in flight, then their
+            // sums in sample order
+            constexpr int U = 16 / RPL;
             int kk = 0;
-            for (; kk + 16 <= cnt; kk += 16) {
-                T dv[16][RPL];
+            for (; kk + U <= cnt; kk += U) {
+                T dv[U][RPL];
 #pragma unroll
-                for (int u = 0; u < 16; ++u) row(kk + u, dv[u]);
+                for (int u = 0; u < U; ++u) row(kk + u, dv[u]);
 #pragma unroll
-                for (int u = 0; u < 16; ++u) add(kk + u, dv[u]);
+                for (int u = 0; u < U; ++u) add(kk + u, dv[u]);
             }
             for (; kk + 4 <= cnt; kk += 4) {
                 T dv[4][RPL];
@@ -647,9 +649,10 @@ void launch_rhs_v(bm_context* ctx, bm_pointing* p, bm_inv_noise* n, bm_precond* 
     BM_LAUNCH_CHECK();
 }
 
-// Right-hand sides per transposed TOD group (one per lane of the RHS kernel);
-// the transposed copy holds nsamples x 32 values at most.
-int rhs_group(int R) { return R < 32 ? R : 32; }
+// Right-hand sides per transposed TOD group (one or two per lane of the RHS
+// kernel: two halve the per-sample work of the warp that is shared by its
+// right-hand sides); the transposed copy holds nsamples x 64 values at most.
+int rhs_group(int R) { return R <= 32 ? R : std::min(R, 64); }
 
 // The batched solver's device buffers, all RHS-interleaved [npix][NC][R].
 struct BatchBufs {
@@ -765,9 +768,11 @@ bm_status batched_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const v
             BM_LAUNCH_CHECK();
             const bool lo = p->cs_lo_s.get() != nullptr;
             if (dt == BM_F32)
-                launch_rhs_v<NC, float, 1>(ctx, p, n, pc, static_cast<float*>(dT), g, r0, R, bb.b, bb.partial, lo);
+                (g > 32 ? launch_rhs_v<NC, float, 2> : launch_rhs_v<NC, float, 1>)(
+                    ctx, p, n, pc, static_cast<float*>(dT), g, r0, R, bb.b, bb.partial, lo);
             else
-                launch_rhs_v<NC, double, 1>(ctx, p, n, pc, static_cast<double*>(dT), g, r0, R, bb.b, bb.partial, lo);
+                (g > 32 ? launch_rhs_v<NC, double, 2> : launch_rhs_v<NC, double, 1>)(
+                    ctx, p, n, pc, static_cast<double*>(dT), g, r0, R, bb.b, bb.partial, lo);
         }
         batched_finalize_kernel<<<vgrid, threads, 0, s>>>(pc->pitem.get(), bb.partial, npix, RNC, bb.b);
         BM_LAUNCH_CHECK();

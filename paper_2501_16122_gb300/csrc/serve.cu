@@ -74,7 +74,8 @@ struct Job {
 //            transpose; per pixel the blocks, their inverses, mask, hits)
 //  create:   scratch of building them (the radix sort's records; the
 //            chunk-major order's build tables, at most 4 GiB)
-//  solve(R): scratch of a solve of R right-hand sides on them
+//  solve(R): scratch of a solve of R right-hand sides on them (for R > 1 the
+//            TOD group transposed for the batched RHS, up to 64 rows)
 int64_t est_resident(const bm_request& r) {
     const int64_t ns = r.nsamples, np = r.npix, nc = (int64_t)r.solver;
     const int64_t trig = r.cos2psi != nullptr ? 16 : 32;
@@ -94,7 +95,7 @@ int64_t est_solve(const bm_request& r, int R) {
     if (R <= 1) return ns * (r.noise == BM_NOISE_WHITE ? 0 : 24) + np * 96 * nc;
     const int64_t esz = r.tod_dtype == BM_F64 ? 8 : 4;
     const int64_t items = np + ns / bm::kItemMax + 1;
-    return ns * std::min(R, 32) * esz + (int64_t)R * nc * (np * (11 * 8 + 4) + items * 8);
+    return ns * std::min(R, 64) * esz + (int64_t)R * nc * (np * (11 * 8 + 4) + items * 8);
 }
 
 // Everything the noise model and preconditioner of a request depend on.
