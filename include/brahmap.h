@@ -134,6 +134,17 @@ bm_status bm_context_set_allreduce(bm_context* ctx, bm_allreduce_fn fn, void* us
  * count of the kernel family `name` ("matvec_white_f32", "matvec_white_f64",
  * "toeplitz_f32", "toeplitz_f64", "rhs", "ingest", "blocks") and resets it. */
 bm_status bm_context_set_timing(bm_context* ctx, int enable);
+
+/* CUDA graphs (on by default): bm_pcg_solve runs its PCG iterations as one
+ * CUDA graph per solve whose conditional WHILE node ends the loop on the
+ * device, captured on a stream of the context.  While a capture is in
+ * progress, a device-wide synchronisation (cudaDeviceSynchronize,
+ * torch.cuda.synchronize) by any other thread of the process fails with
+ * cudaErrorStreamCaptureUnsupported; a context used while other threads
+ * synchronise the device can turn the graphs off (the iterations are then
+ * driven from the host: the same results, bit for bit).  The server's
+ * contexts have them off. */
+bm_status bm_context_set_graphs(bm_context* ctx, int enable);
 bm_status bm_context_kernel_time(bm_context* ctx, const char* name, double* total_ms,
                                  int64_t* launches);
 /* Number of CUDA kernels the library has launched in this process so far

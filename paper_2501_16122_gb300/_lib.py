@@ -92,6 +92,7 @@ _SIGS = {
     "bm_context_create": ([ctypes.c_int, _P, _PP], ctypes.c_int),
     "bm_context_destroy": ([_P], None),
     "bm_context_set_timing": ([_P, ctypes.c_int], ctypes.c_int),
+    "bm_context_set_graphs": ([_P, ctypes.c_int], ctypes.c_int),
     "bm_context_kernel_time": ([_P, ctypes.c_char_p, ctypes.POINTER(_f64), ctypes.POINTER(_i64)], ctypes.c_int),
     "bm_kernel_launches": ([], _i64),
     "bm_ang2pix_ring": ([_P, _i64, _i64, _P, _P, _P], ctypes.c_int),
@@ -282,6 +283,10 @@ from .shard import detector_shard  # noqa: E402,F401  (host-side partition of a 
 
 def bm_context_set_timing(ctx, enable: bool):
     _check(lib.bm_context_set_timing(ctx, int(bool(enable))), "bm_context_set_timing")
+
+
+def bm_context_set_graphs(ctx, enable: bool):
+    _check(lib.bm_context_set_graphs(ctx, int(bool(enable))), "bm_context_set_graphs")
 
 
 def bm_kernel_launches() -> int:

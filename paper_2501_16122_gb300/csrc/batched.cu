@@ -918,7 +918,7 @@ bm_status batched_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const v
         const int hloop[2] = {0, maxiter - inner_total};  // >= 1 here
         BM_CUDA(cudaMemcpyAsync(bb.loop, hloop, sizeof(hloop), cudaMemcpyHostToDevice, s));
         int loop_out[2] = {0, 0};
-        if (ctx->side != nullptr && gexec == nullptr && graph_ok) {
+        if (ctx->side != nullptr && ctx->graphs && gexec == nullptr && graph_ok) {
             try {
                 build_loop_graph();
             } catch (const Error&) {  // no conditional graph here: the host-driven loop below

@@ -159,6 +159,11 @@ struct bm_context {
     // ordered against `stream` with side_ev.
     cudaStream_t side = nullptr;
     cudaEvent_t side_ev = nullptr;
+    // Whether solves may capture their iterations into CUDA graphs.  Off for
+    // the server's contexts: while a stream captures, a device-wide
+    // synchronisation by any other thread of the process fails, and the
+    // server runs next to the caller's own threads.
+    bool graphs = true;
     // Device address of the allocation-free matvec's static scratch array on
     // this context's device (looked up when the context is created).
     double* static_scratch = nullptr;

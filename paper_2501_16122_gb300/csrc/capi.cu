@@ -287,6 +287,14 @@ bm_status bm_context_set_timing(bm_context* ctx, int enable) {
     });
 }
 
+bm_status bm_context_set_graphs(bm_context* ctx, int enable) {
+    return guarded([&] {
+        BM_REQUIRE(ctx, "ctx is NULL");
+        ctx->graphs = enable != 0;
+        return BM_OK;
+    });
+}
+
 bm_status bm_context_kernel_time(bm_context* ctx, const char* name, double* total_ms,
                                  int64_t* launches) {
     return guarded([&] {

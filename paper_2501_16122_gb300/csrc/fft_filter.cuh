@@ -46,14 +46,34 @@ template <typename T>
 __device__ __forceinline__ cpx<T> csub(cpx<T> a, cpx<T> b) { return {a.x - b.x, a.y - b.y}; }
 template <typename T>
 __device__ __forceinline__ cpx<T> cconj(cpx<T> a) { return {a.x, -a.y}; }
+// A value as it is stored between passes: normalised for double-float.
+template <typename T>
+__device__ __forceinline__ cpx<T> fnorm(cpx<T> a) { return a; }
 
 // Double-float (a pair of FP32 numbers carrying ~48 bits) as an FFT element:
 // the refinement operator of the mixed solve transforms in this type on the
 // FP32 pipes instead of FP64, which runs at 1/64 of the FP32 rate here.
-__device__ __forceinline__ df32 operator+(df32 a, df32 b) { return df_add(a, b); }
+// Inside a pass the sums and products are left unnormalised (the leading
+// part from an exact two_sum / two_prod, the rounding errors and cross terms
+// added into the trailing part), and every value is renormalised once when
+// the pass stores it (fnorm): the trailing part stays within a few units of
+// the leading part's last place over a butterfly, at about 40% fewer FP32
+// operations than normalising after each operation.
+__device__ __forceinline__ df32 operator+(df32 a, df32 b) {
+    const df32 s = df_two_sum(a.hi, b.hi);
+    return {s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo))};
+}
 __device__ __forceinline__ df32 operator-(df32 a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ df32 operator-(df32 a, df32 b) { return df_add(a, -b); }
-__device__ __forceinline__ df32 operator*(df32 a, df32 b) { return df_mul(a, b); }
+__device__ __forceinline__ df32 operator-(df32 a, df32 b) { return a + (-b); }
+__device__ __forceinline__ df32 operator*(df32 a, df32 b) {
+    const df32 p = df_two_prod(a.hi, b.hi);
+    return {p.hi, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo))};
+}
+
+template <>
+__device__ __forceinline__ cpx<df32> fnorm(cpx<df32> a) {
+    return {df_quick_two_sum(a.x.hi, a.x.lo), df_quick_two_sum(a.y.hi, a.y.lo)};
+}
 
 // A number of type V as element type T (no detour through FP64 for FP32).
 template <typename T, typename V>
@@ -67,7 +87,10 @@ __device__ __forceinline__ df32 fnum<df32, float2>(float2 v) { return {v.x, v.y}
 // An element as the output type.
 __device__ __forceinline__ float fout(float v) { return v; }
 __device__ __forceinline__ double fout(double v) { return v; }
-__device__ __forceinline__ float2 fout(df32 v) { return make_float2(v.hi, v.lo); }
+__device__ __forceinline__ float2 fout(df32 v) {
+    const df32 n = df_quick_two_sum(v.hi, v.lo);
+    return make_float2(n.hi, n.lo);
+}
 
 // Padded shared-memory index: one spare entry after every 16.
 __device__ __forceinline__ int fpad(int a) { return a + (a >> 4); }
@@ -244,7 +267,7 @@ __device__ __forceinline__ void fft_pass(cpx<T>* buf, int M, int Ns, const cpx<T
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int sl = R == 16 ? slot16(r) : (R == 8 ? slot8(r) : r);
-                buf[fpad(base + r * Ns)] = v[bb][sl];
+                buf[fpad(base + r * Ns)] = fnorm(v[bb][sl]);
             }
         }
     }
@@ -462,8 +485,8 @@ toeplitz_fft_kernel(Src src, const typename FftIO<T>::spec_t* __restrict__ spec,
                 };
                 const cpx<T> zo = zval(Yk, Yk2, wk);
                 const cpx<T> zo2 = zval(Yk2, Yk, wk2);
-                buf[fpad(k)] = zo;
-                if (k2 < M && k2 != k) buf[fpad(k2)] = zo2;
+                buf[fpad(k)] = fnorm(zo);
+                if (k2 < M && k2 != k) buf[fpad(k2)] = fnorm(zo2);
             }
             __syncthreads();
         }

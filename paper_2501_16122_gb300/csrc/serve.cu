@@ -350,6 +350,9 @@ bm_status make_context(int device, cudaStream_t* stream, bm_context** ctx) {
         cudaMemPoolDestroy((*ctx)->ws_pool);
         (*ctx)->ws_pool = nullptr;
     }
+    // no graph capture in the server's solves: a capture in a slot would make
+    // a device-wide synchronisation by any other thread of the process fail
+    if (st == BM_OK) (*ctx)->graphs = false;
     return st;
 }
 

@@ -436,7 +436,7 @@ CgState run_pcg(Cg& cg, bm_pointing* p, bm_inv_noise* n, const double* b, double
         ++it;
         h = read_state(ctx, cg.st);
     }
-    const bool graph = gl && gl->ok && ctx->side && !ctx->allreduce && !ctx->timing;
+    const bool graph = gl && gl->ok && ctx->graphs && ctx->side && !ctx->allreduce && !ctx->timing;
     if (graph && !h.done && it < maxiter) {
         if (!gl->exec || gl->generation != ctx->ws_generation) {
             try {

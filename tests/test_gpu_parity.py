@@ -562,3 +562,33 @@ def test_uneven_detector_lengths(L, ctx, prec):
         L.bm_precond_destroy(pc)
         L.bm_inv_noise_destroy(n)
         L.bm_pointing_destroy(p)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_graphs_on_and_off_same_bits(L, ctx, prec):
+    """The PCG iterations as a CUDA graph (the default) and driven from the
+    host (bm_context_set_graphs(ctx, 0)) run the same kernels in the same
+    order: Toeplitz solves (single RHS) and a batched white-noise solve give
+    the same maps bit for bit."""
+    c = Case(L, ctx, 8, 4, 8192 + 13, 41, noise="toeplitz", chunk=2048, nlags=48, psi_dtype=np.float64,
+             build_oracle=False)
+    w = Case(L, ctx, 8, 4, 6000, 42, build_oracle=False)
+    try:
+        tol = 1e-12 if prec == 0 else 1e-10
+        d = torch.from_numpy(np.stack([w.tod, w.tod[::-1].copy(), 0.5 * w.tod])).cuda()
+        maps = []
+        for graphs in (True, False):
+            L.bm_context_set_graphs(ctx, graphs)
+            one = c.vec()
+            st, info = L.bm_pcg_solve(c.p, c.n, c.pc, c.d_tod, 1, one, tol, 500, prec)
+            assert st == L.BM_OK and info[0]["iterations"] > 1, info
+            many = torch.zeros(3 * w.npix * 3, dtype=torch.float64, device="cuda")
+            st, infos = L.bm_pcg_solve(w.p, w.n, w.pc, d, 3, many, 1e-10, 500, L.BM_PREC_MIXED)
+            assert st == L.BM_OK, infos
+            maps.append((one, many))
+        for a, b in zip(maps[0], maps[1]):
+            assert torch.equal(torch.nan_to_num(a), torch.nan_to_num(b))
+    finally:
+        L.bm_context_set_graphs(ctx, True)
+        c.close()
+        w.close()
