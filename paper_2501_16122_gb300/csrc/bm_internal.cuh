@@ -185,7 +185,8 @@ struct HwpModel {
     int ndet = 0;
     uint32_t ns = 0;                          // samples per detector when all are equal, else 0
     float inv_ns = 0.f;
-    const double2* tab64 = nullptr;           // [kHwpTab] (cos, sin)(2 pi j / kHwpTab) in FP64
+    const float4* tabdf = nullptr;            // [kHwpTab] (cos, sin)(2 pi j / kHwpTab) as double-float
+                                              // pairs: (cos hi, sin hi, cos lo, sin lo)
 };
 }  // namespace bm
 
@@ -208,7 +209,7 @@ struct bm_pointing {
     bm::DevBuf<uint32_t> hwp_off;           // [ndet + 1]
     bm::DevBuf<unsigned long long> hwp_turn0;  // [ndet]
     bm::DevBuf<float2> hwp_tab;             // [kHwpTab] (cos, sin)(2 pi j / kHwpTab) in FP32
-    bm::DevBuf<double2> hwp_tab64;          // [kHwpTab] the same in FP64
+    bm::DevBuf<float4> hwp_tab_df;          // [kHwpTab] the same as double-float pairs
 };
 
 struct bm_inv_noise {
@@ -521,19 +522,6 @@ __device__ __forceinline__ float2 hwp_trig32(uint32_t a32, const float2* tab) {
     const float sd = dl * fmaf(-0.16666667f, d2, 1.0f);
     return make_float2(fmaf(cs.x, cd, -cs.y * sd), fmaf(cs.y, cd, cs.x * sd));
 }
-// (cos, sin) of 2 pi a for a 64-bit turn fraction a in FP64: the table entry
-// of the top kHwpTabBits bits rotated by the remainder delta (< 2 pi /
-// kHwpTab = 0.0062), cos delta = 1 - delta^2/2 + delta^4/24, sin delta =
-// delta - delta^3/6 + delta^5/120 (truncation errors below 8e-17).
-__device__ __forceinline__ void hwp_trig64(unsigned long long a, const double2* tab, double& c, double& s) {
-    const double2 cs = tab[a >> (64 - kHwpTabBits)];
-    const double dl = (double)(a & ((1ull << (64 - kHwpTabBits)) - 1ull)) * 3.4061215800865545e-19;  // 2 pi / 2^64
-    const double d2 = dl * dl;
-    const double cd = fma(fma(d2, 1.0 / 24.0, -0.5), d2, 1.0);
-    const double sd = dl * fma(fma(d2, 1.0 / 120.0, -1.0 / 6.0), d2, 1.0);
-    c = fma(cs.x, cd, -cs.y * sd);
-    s = fma(cs.y, cd, cs.x * sd);
-}
 // (cos, sin) of 2 pi a for a 64-bit turn fraction a, in FP32 (hwp_trig32 of
 // its top 32 bits).
 __device__ __forceinline__ float2 hwp_trig_f32(unsigned long long a, const float2* tab) {
@@ -638,6 +626,34 @@ __device__ __forceinline__ void acc_add(df32& a, float p, float e) {
     a.lo = __fadd_rn(a.lo, __fadd_rn(s.lo, e));
 }
 __device__ __forceinline__ void acc_norm(df32& a) { a = df_two_sum(a.hi, a.lo); }
+
+// (cos, sin) of 2 pi a for a 64-bit turn fraction a as double-float pairs,
+// on the FP32 pipes (FP64 runs at 1/74 of their rate here): the table entry
+// of the top kHwpTabBits bits rotated by the remainder delta (< 2 pi /
+// kHwpTab = 0.0062), cos delta = 1 - delta^2/2 + delta^4/24, sin delta =
+// delta - delta^3/6 + delta^5/120 (truncation below 8e-17); the remainder
+// keeps its top 48 bits (2^-58 of a turn dropped), the rest is double-float
+// arithmetic (~2^-46 relative).  Returns (cos hi, sin hi, cos lo, sin lo).
+__device__ __forceinline__ float4 hwp_trig_df(unsigned long long a, const float4* tab) {
+    const float4 t = tab[a >> (64 - kHwpTabBits)];
+    const unsigned long long r = a & ((1ull << (64 - kHwpTabBits)) - 1ull);  // < 2^54
+    // r 2^-64 as a double-float: (r >> 30) 2^-34 exactly, then the low 30 bits
+    const df32 rt = df_quick_two_sum(__ull2float_rz(r >> 30) * 5.820766091346741e-11f,        // 2^-34
+                                     __ull2float_rn(r & 0x3FFFFFFFull) * 5.421010862427522e-20f);  // 2^-64
+    const df32 two_pi = {6.28318548202514648f, -1.74845553e-7f};
+    const df32 dl = df_mul(rt, two_pi);
+    const df32 d2 = df_mul(dl, dl);
+    const df32 third = {-0.166666672f, 4.96705388e-9f};   // -1/6
+    const df32 cdt = df_add(df32{-0.5f, 0.f}, d2.hi * 0.0416666679f);  // -1/2 + d2/24
+    const df32 cd = df_add(df_mul(d2, cdt), 1.0f);
+    const df32 sdt = df_add(third, d2.hi * 0.00833333377f);          // -1/6 + d2/120
+    const df32 sd = df_mul(dl, df_add(df_mul(d2, sdt), 1.0f));
+    const df32 c0 = {t.x, t.z}, s0 = {t.y, t.w};
+    const df32 ssd = df_mul(s0, sd);
+    const df32 c = df_add(df_mul(c0, cd), df32{-ssd.hi, -ssd.lo});
+    const df32 s = df_add(df_mul(s0, cd), df_mul(c0, sd));
+    return make_float4(c.hi, s.hi, c.lo, s.lo);
+}
 
 // One sample's terms of b = P^T N^-1 d (and of the weighted transposes) in
 // the lazy form: val = d w (d a float: `dh`, dl = 0; or a double-float), then

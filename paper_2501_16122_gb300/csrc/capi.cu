@@ -424,12 +424,13 @@ static void check_det_offsets(int32_t ndet, const int64_t* det_offsets);
 namespace bm {
 namespace {
 // tab[j] = (cos, sin)(2 pi j / kHwpTab) in FP64, and rounded to FP32.
-__global__ void hwp_table_kernel(float2* __restrict__ tab, double2* __restrict__ tab64) {
+__global__ void hwp_table_kernel(float2* __restrict__ tab, float4* __restrict__ tabdf) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < kHwpTab; j += gridDim.x * blockDim.x) {
         double sn, cs;
         sincospi(2.0 * (double)j / (double)kHwpTab, &sn, &cs);
-        tab[j] = make_float2((float)cs, (float)sn);
-        tab64[j] = make_double2(cs, sn);
+        const float ch = (float)cs, sh = (float)sn;
+        tab[j] = make_float2(ch, sh);
+        tabdf[j] = make_float4(ch, sh, (float)(cs - (double)ch), (float)(sn - (double)sh));
     }
 }
 
@@ -483,17 +484,17 @@ bm_status bm_pointing_create_hwp(bm_context* ctx, int64_t npix, int64_t nsamples
             p->hwp_off.alloc(ndet + 1);
             p->hwp_turn0.alloc(ndet);
             p->hwp_tab.alloc(kHwpTab);
-            p->hwp_tab64.alloc(kHwpTab);
+            p->hwp_tab_df.alloc(kHwpTab);
             BM_CUDA(cudaMemcpyAsync(p->hwp_off.get(), off.data(), sizeof(uint32_t) * (ndet + 1),
                                     cudaMemcpyHostToDevice, ctx->stream));
             BM_CUDA(cudaMemcpyAsync(p->hwp_turn0.get(), turn0.data(), sizeof(unsigned long long) * ndet,
                                     cudaMemcpyHostToDevice, ctx->stream));
-            hwp_table_kernel<<<(kHwpTab + 255) / 256, 256, 0, ctx->stream>>>(p->hwp_tab.get(), p->hwp_tab64.get());
+            hwp_table_kernel<<<(kHwpTab + 255) / 256, 256, 0, ctx->stream>>>(p->hwp_tab.get(), p->hwp_tab_df.get());
             BM_LAUNCH_CHECK();
             HwpModel& m = p->hwp_model;
             m.off = p->hwp_off.get();
             m.turn0 = p->hwp_turn0.get();
-            m.tab64 = p->hwp_tab64.get();
+            m.tabdf = p->hwp_tab_df.get();
             m.nu = turn_fixed(hwp_turns_per_sample);
             m.ndet = ndet;
             // t / ns for uniform detectors (as the noise handles do; fewer than 2^20 detectors)

@@ -124,15 +124,14 @@ validate_kernel(const int32_t* __restrict__ pix, const void* __restrict__ psi,
             hi[i] = make_float2(c, s);
         } else if constexpr (MODE == kHwp) {
             // 2 theta of the half-wave-plate model in turns, reduced exactly,
-            // and its cos and sin in FP64 (table and short polynomials)
+            // and its cos and sin as double-float pairs (table and short
+            // polynomials on the FP32 pipes)
             ok_a = true;
             const int d = det_of(hwp.off, hwp.ndet, hwp.ns, hwp.inv_ns, (uint32_t)i);
             const unsigned long long a2 = hwp_turns(hwp, d, (uint32_t)i);
-            double sn, cs;
-            hwp_trig64(a2, hwp.tab64, cs, sn);
-            const float ch = (float)cs, sh = (float)sn;
-            hi[i] = make_float2(ch, sh);
-            lo[i] = make_float2((float)(cs - (double)ch), (float)(sn - (double)sh));
+            const float4 t = hwp_trig_df(a2, hwp.tabdf);
+            hi[i] = make_float2(t.x, t.y);
+            lo[i] = make_float2(t.z, t.w);
         } else {
             ok_a = isfinite(a);
             double sn, cs;
