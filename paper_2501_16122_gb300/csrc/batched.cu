@@ -381,8 +381,10 @@ __device__ __forceinline__ void apply_block(const double* __restrict__ M, int64_
     }
 }
 
-// r = b - B x (masked pixels 0); part slot 0: r.r, slot 1: b.b
-template <int NC>
+// r = b - B x (masked pixels 0); XZ: x = 0 (the start: r = b, no block
+// products, which cost GB300's FP64 pipe most of this kernel's time);
+// part slot 0: r.r, slot 1: b.b
+template <int NC, bool XZ>
 __global__ void __launch_bounds__(kRT) b_residual_kernel(BGeo g, const double* __restrict__ B, const uint8_t* __restrict__ mask,
                                                         const double* __restrict__ b, const double* __restrict__ x,
                                                         double* __restrict__ r, double* __restrict__ part) {
@@ -392,10 +394,16 @@ __global__ void __launch_bounds__(kRT) b_residual_kernel(BGeo g, const double* _
     if (rr_ < g.R) {
         for (int64_t p = (int64_t)blockIdx.x * g.ppb + sub; p < g.npix; p += (int64_t)gridDim.x * g.ppb) {
             const int64_t o = p * NC * g.R + rr_;
-            double xv[NC], bx[NC];
+            double bx[NC];
+            if (XZ) {
 #pragma unroll
-            for (int c = 0; c < NC; ++c) xv[c] = x[o + c * g.R];
-            apply_block<NC>(B, p, xv, bx);
+                for (int c = 0; c < NC; ++c) bx[c] = 0.0;
+            } else {
+                double xv[NC];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) xv[c] = x[o + c * g.R];
+                apply_block<NC>(B, p, xv, bx);
+            }
             const bool keep = mask[p] == 0;
             double bl[NC];
 #pragma unroll
@@ -784,7 +792,7 @@ bm_status batched_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const v
     BGeo geo{R, Rp, kRT / Rp, npix};
     // per-pixel PCG kernels: one wave of resident blocks (at most kRB)
     int per_sm = 64;
-    for (const void* k : {reinterpret_cast<const void*>(b_residual_kernel<NC>),
+    for (const void* k : {reinterpret_cast<const void*>(b_residual_kernel<NC, false>),
                           reinterpret_cast<const void*>(b_init_kernel<NC>),
                           reinterpret_cast<const void*>(b_update_kernel<NC>),
                           reinterpret_cast<const void*>(b_dot_kernel),
@@ -795,7 +803,7 @@ bm_status batched_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const v
 
     // x = 0; r = b (masked), per-RHS ||b||
     BM_CUDA(cudaMemsetAsync(bb.x, 0, sizeof(double) * nv, s));
-    b_residual_kernel<NC><<<rgrid, kRT, 0, s>>>(geo, pc->B.get(), pc->mask.get(), bb.b, bb.x, bb.r, bb.part);
+    b_residual_kernel<NC, true><<<rgrid, kRT, 0, s>>>(geo, pc->B.get(), pc->mask.get(), bb.b, bb.x, bb.r, bb.part);
     BM_LAUNCH_CHECK();
     b_sum2_kernel<<<sgrid, 128, 0, s>>>(bb.part, rgrid, R, bb.sums);
     BM_LAUNCH_CHECK();
@@ -957,7 +965,8 @@ bm_status batched_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const v
         ++outer;
         b_axpy_kernel<<<vgrid, threads, 0, s>>>(bb.x, bb.e, nv);
         BM_LAUNCH_CHECK();
-        b_residual_kernel<NC><<<rgrid, kRT, 0, s>>>(geo, pc->B.get(), pc->mask.get(), bb.b, bb.x, bb.r, bb.part);
+        b_residual_kernel<NC, false><<<rgrid, kRT, 0, s>>>(geo, pc->B.get(), pc->mask.get(), bb.b, bb.x, bb.r,
+                                                          bb.part);
         BM_LAUNCH_CHECK();
         b_sum2_kernel<<<sgrid, 128, 0, s>>>(bb.part, rgrid, R, bb.sums);
         BM_LAUNCH_CHECK();
