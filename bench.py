@@ -70,7 +70,7 @@ def parse():
     ap.add_argument("--horizon", type=float, default=20.0, help="config4: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=20.0, help="config4: mean arrivals per second")
     ap.add_argument("--nrhs", type=int, default=64, help="config3: right-hand sides")
-    ap.add_argument("--slots", type=int, default=8, help="config4: requests the server runs at once")
+    ap.add_argument("--slots", type=int, default=2, help="config4: requests the server runs at once")
     ap.add_argument("--shared-frac", type=float, default=0.0,
                     help="config4: fraction of requests that are white-noise realisations of a few shared "
                          "observations (same pointing, pointing_key set)")
