@@ -5,8 +5,9 @@
 // Layout: vectors are RHS-interleaved, [npix][ncomp][R] (per pixel and
 // Stokes component the R right-hand sides are contiguous, so a warp over
 // right-hand sides reads and writes whole lines).  The caller's TOD
-// [R][nsamples] is transposed group by group (G <= 32 * RPL right-hand sides)
-// into [nsamples][G], so that the pixel-sorted gather of one sample reads G
+// [R][nsamples] is transposed group by group (G <= 32 * RPL right-hand sides,
+// RPL = 1 or 2 a lane, the group size timed once per problem shape) into
+// [nsamples][G], so that the pixel-sorted gather of one sample reads G
 // contiguous values.
 //
 // Kernels (one warp per work item, lanes over right-hand sides, RPL per lane):
@@ -657,10 +658,54 @@ void launch_rhs_v(bm_context* ctx, bm_pointing* p, bm_inv_noise* n, bm_precond* 
     BM_LAUNCH_CHECK();
 }
 
-// Right-hand sides per transposed TOD group (one or two per lane of the RHS
-// kernel: two halve the per-sample work of the warp that is shared by its
-// right-hand sides); the transposed copy holds nsamples x 64 values at most.
-int rhs_group(int R) { return R <= 32 ? R : std::min(R, 64); }
+// Group size of the batched RHS for a problem shape: for more than 32
+// right-hand sides, groups of 32 (one a lane) and of 64 (two a lane) are
+// both run once per shape (pixels, kept samples, R, components, TOD type)
+// and timed, and the faster is kept for the process; both give the same
+// bits (each right-hand side's sums run in the same order either way).
+// Returns the group size; b holds the RHS on return.
+template <class F>
+int rhs_autotune(bm_context* ctx, bm_pointing* p, int R, bm_dtype dt, F&& run) {
+    static std::mutex mu;
+    static std::map<std::tuple<int64_t, int64_t, int, int, int>, int> cache;
+    if (R <= 32) {
+        run(R);
+        return R;
+    }
+    const auto key = std::make_tuple(p->npix, p->nvalid, R, p->ncomp, (int)dt);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            run(it->second);
+            return it->second;
+        }
+    }
+    cudaEvent_t a, b;
+    BM_CUDA(cudaEventCreate(&a));
+    BM_CUDA(cudaEventCreate(&b));
+    float best_ms = 1e30f;
+    int best = 32;
+    for (int G : {32, std::min(R, 64)}) {
+        BM_CUDA(cudaEventRecord(a, ctx->stream));
+        run(G);
+        BM_CUDA(cudaEventRecord(b, ctx->stream));
+        BM_CUDA(cudaEventSynchronize(b));
+        float ms = 0.f;
+        BM_CUDA(cudaEventElapsedTime(&ms, a, b));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = G;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = best;
+    return best;
+}
+
+
 
 // The batched solver's device buffers, all RHS-interleaved [npix][NC][R].
 struct BatchBufs {
@@ -752,10 +797,8 @@ bm_status batched_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const v
     for (int r = 0; r < R; ++r) rows_aligned = rows_aligned && (reinterpret_cast<uintptr_t>(rows[r]) % 16 == 0);
     double* const* d_maps = reinterpret_cast<double* const*>(ptrs + sizeof(void*) * (size_t)R);
 
-    // --- batched RHS, TOD transposed group by group
-    {
-        ScopedTimer timer(ctx, "rhs_batched");
-        const int G = rhs_group(R);
+    // --- batched RHS, TOD transposed group by group (groups of G <= 64 rows)
+    auto batched_rhs = [&](int G) {
         const size_t esz = dt == BM_F32 ? 4 : 8;
         void* dT = workspace(ctx, "bt_todT", (size_t)p->nsamples * G * esz);
         for (int r0 = 0; r0 < R; r0 += G) {
@@ -784,6 +827,11 @@ bm_status batched_solve(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const v
         }
         batched_finalize_kernel<<<vgrid, threads, 0, s>>>(pc->pitem.get(), bb.partial, npix, RNC, bb.b);
         BM_LAUNCH_CHECK();
+    };
+    {
+        const int G = rhs_autotune(ctx, p, R, dt, batched_rhs);  // runs the RHS at least once
+        ScopedTimer timer(ctx, "rhs_batched");
+        if (ctx->timing) batched_rhs(G);  // (timed on its own when kernel timing is on)
     }
 
     // --- geometry of the per-pixel PCG kernels

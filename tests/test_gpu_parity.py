@@ -328,7 +328,7 @@ def test_noiseless_recovery_fp32_inputs(L, ctx):
         c.close()
 
 
-@pytest.mark.parametrize("solver,R", [(3, 5), (3, 40), (2, 3), (1, 3)])
+@pytest.mark.parametrize("solver,R", [(3, 5), (3, 40), (3, 70), (2, 3), (1, 3)])
 def test_batched_multi_rhs(L, ctx, solver, R):
     # R realisations (sky + white noise) sharing one pointing, solved as one
     # batched mixed-precision PCG: every map matches the oracle and the
