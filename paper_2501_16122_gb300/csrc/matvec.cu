@@ -774,6 +774,28 @@ struct SrcPlainDF {  // a double-float (hi, lo) pair per sample
     __device__ float2 operator()(int64_t t) const { return y[t]; }
 };
 
+// The masked TOD as double-float pairs (SrcMaskedTod's values, written once
+// before the double-float filter so that its loads are plain streams rather
+// than a pixel-then-mask gather per sample).
+template <typename D>
+__global__ void masked_tod_df_kernel(const int32_t* __restrict__ pix, const uint8_t* __restrict__ mask,
+                                     const D* __restrict__ d, int64_t n, float2* __restrict__ out) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p = __ldcs(pix + t);
+        const D v = __ldcs(d + t);
+        float2 o = make_float2(0.f, 0.f);
+        if (p >= 0 && !mask[p]) {
+            if (sizeof(D) == 4) {
+                o.x = (float)v;
+            } else {
+                const df32 f = df_from((double)v);
+                o = make_float2(f.hi, f.lo);
+            }
+        }
+        out[t] = o;
+    }
+}
+
 // y = P x over every sample in double-float on the FP32 pipes (the
 // refinement operator's input): the trig pair as (hi, lo) (lo absent: the
 // exact FP32 values), the map as masked_copy_df_kernel writes it (two float4
@@ -1978,15 +2000,17 @@ void rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dt
             // the mixed path's Toeplitz RHS: filter and pixel sums in
             // double-float, z as (hi, lo) pairs
             float2* z2 = workspace_as<float2>(ctx, "z_df", p->nsamples);
-            if (dt == BM_F32) {
-                SrcMaskedTod<float> src{p->pix.get(), pc->mask.get(),
-                                        static_cast<const float*>(tod) + r * p->nsamples};
-                apply_toeplitz_df(n, src, z2);
-            } else {
-                SrcMaskedTod<double> src{p->pix.get(), pc->mask.get(),
-                                         static_cast<const double*>(tod) + r * p->nsamples};
-                apply_toeplitz_df(n, src, z2);
-            }
+            float2* y2 = workspace_as<float2>(ctx, "y_df", p->nsamples);
+            const int tthreads = 256;
+            const int tgrid = grid_for(ctx, (p->nsamples + tthreads - 1) / tthreads, 16);
+            if (dt == BM_F32)
+                masked_tod_df_kernel<float><<<tgrid, tthreads, 0, ctx->stream>>>(
+                    p->pix.get(), pc->mask.get(), static_cast<const float*>(tod) + r * p->nsamples, p->nsamples, y2);
+            else
+                masked_tod_df_kernel<double><<<tgrid, tthreads, 0, ctx->stream>>>(
+                    p->pix.get(), pc->mask.get(), static_cast<const double*>(tod) + r * p->nsamples, p->nsamples, y2);
+            BM_LAUNCH_CHECK();
+            apply_toeplitz_df(n, SrcPlainDF{y2}, z2);
             if (p->cs_lo_s.get() == nullptr && ensure_chunk_major(p, n, pc)) pt_chunked_df(p, pc, z2, br);
             else gather_reduce<float2>(p, kept_items(pc), z2, nullptr, p->cs_lo_s.get(), true, br);
         } else {
