@@ -469,9 +469,17 @@ __global__ void pt_bounds_kernel(const int64_t* __restrict__ off, const uint32_t
             if (c <= f) s[(int64_t)c * npix] = 0;
             else if (c > l) s[(int64_t)c * npix] = len;
         }
-        for (int32_t i = lane + 1; i < len; i += 32) {
-            const int c0 = (int)(perm[b + i - 1] >> kPtChunkBits), c1 = (int)(perm[b + i] >> kPtChunkBits);
-            for (int c = c0 + 1; c <= c1; ++c) s[(int64_t)c * npix] = i;
+        // each sample's chunk read once; the previous sample's from the
+        // neighbouring lane (lane 0: the last lane of the previous round)
+        int carry = f;
+        for (int32_t i0 = 0; i0 < len; i0 += 32) {
+            const int32_t i = i0 + lane;
+            const int c1 = i < len ? (int)(perm[b + i] >> kPtChunkBits) : l;
+            int c0 = __shfl_up_sync(0xffffffffu, c1, 1);
+            if (lane == 0) c0 = carry;
+            carry = __shfl_sync(0xffffffffu, c1, 31);
+            if (i >= 1 && i < len)
+                for (int c = c0 + 1; c <= c1; ++c) s[(int64_t)c * npix] = i;
         }
     }
 }
