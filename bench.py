@@ -260,10 +260,7 @@ KERNELS = {"ingest_validate": "validate_kernel", "ingest_hist": "rs_hist_kernel"
            "ingest_scatter": "rs_scatter_kernel", "blocks": "blocks_kernel", "rhs": "gather_reduce_kernel",
            "matvec_white_f32": "white_matvec_f32_kernel"}
 TRAFFIC = {
-    # ncu on the 67M-sample case of the same scan (256 detectors x 262,144
-    # samples): 42.4 and 44.0 DRAM bytes per sample for the two scatter
-    # passes (mean 43.2); the traffic grows in proportion to the samples
-    "ingest_scatter": lambda n: 43.2 * n,
+    "ingest_scatter": None,
 }
 
 
@@ -456,18 +453,20 @@ def run_gb300(args, rank, world, local_rank):
     while (1 << nbits) <= e.npix:
         nbits += 1
     passes = -(-nbits // 10)
+    bits = -(-nbits // passes)
+    kb = 2 if nbits - bits <= 16 else 4  # bytes of a key stored between passes
     n_valid = int(hits.sum().item())
     scatter_bytes = 0
     hist_bytes = 0
     for ps in range(passes):
         last = ps == passes - 1
-        # keys + records, or keys + trig pair (+ TOD) in time order
-        rd = 4 + (16 if ps > 0 else (12 if carried else 8))
+        # keys + records, or pixel keys + trig pair (+ TOD) in time order
+        rd = (kb + 16) if ps > 0 else (4 + (12 if carried else 8))
         # perm + trig (+ TOD) of kept samples, or records + keys
-        wr = ((16 if carried else 12) * n_valid / nt) if last else 20
+        wr = ((16 if carried else 12) * n_valid / nt) if last else 16 + kb
         scatter_bytes += (rd + wr) * nt
         if ps > 0:                                         # (the first pass's counts come from validation)
-            hist_bytes += 4 * nt                           # keys
+            hist_bytes += kb * nt                          # keys
     step_bytes = {
         "ingest_validate": 24 * nt,                       # pix + cos + sin in; pix, trig pair out
         "ingest_hist": hist_bytes,
@@ -579,7 +578,7 @@ def run_gb300(args, rank, world, local_rank):
             "solve": {"status_ok": st_ok, "iterations": last["iterations"],
                       "outer_iterations": last["outer_iterations"], "rel_residual": last["rel_residual"]},
             "roofline": ({"bound": "hbm", "achieved": rooflines[dom]["achieved_gbs"], "peak": hbm, "unit": "GB/s",
-                          "frac": rooflines[dom]["frac"], "traffic": TRAFFIC.get(dom, lambda n: None)(nt),
+                          "frac": rooflines[dom]["frac"], "traffic": (TRAFFIC.get(dom) or (lambda n: None))(nt),
                           "kernel": KERNELS[dom], "family": dom, "peak_kind": peak_kind,
                           "launches_per_step": fam[dom]["launches"] / args.steps,
                           "bytes_per_launch": rooflines[dom]["bytes_per_step"] / (fam[dom]["launches"] / args.steps),

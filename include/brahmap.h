@@ -239,6 +239,14 @@ bm_status bm_pointing_create_hwp(bm_context* ctx, int64_t npix, int64_t nsamples
 void bm_pointing_destroy(bm_pointing* p);
 /* hits device int32 [npix]: samples per pixel (flagged samples excluded). */
 bm_status bm_pointing_get_hits(const bm_pointing* p, int32_t* hits);
+/* The pixel-sorted sample order the operators run in (the precomputation
+ * of Sec. III-A item 1, which groups the samples of each pixel for P^T):
+ * *nvalid (host, may be NULL) receives the number of non-flagged samples,
+ * and order (device uint32 [nvalid], caller-owned; may be NULL to ask for
+ * the count alone) their time indices in increasing pixel, samples of one
+ * pixel in time order (the stable sort by pixel).  Synchronous.
+ * BM_ERR_INVALID for a NULL handle. */
+bm_status bm_pointing_get_order(const bm_pointing* p, uint32_t* order, int64_t* nvalid);
 /* y = P x (the paper's PointingLO): x device FP64 [npix][ncomp], y device
  * FP64 [nsamples]; every non-flagged sample, no mask.  FP64 arithmetic. */
 bm_status bm_pointing_apply(bm_pointing* p, const double* x, double* y);

@@ -103,6 +103,7 @@ _SIGS = {
                                     ctypes.c_int),
     "bm_pointing_destroy": ([_P], None),
     "bm_pointing_get_hits": ([_P, _P], ctypes.c_int),
+    "bm_pointing_get_order": ([_P, _P, _P], ctypes.c_int),
     "bm_pointing_apply": ([_P, _P, _P], ctypes.c_int),
     "bm_pointing_apply_transpose": ([_P, _P, _P], ctypes.c_int),
     "bm_inv_noise_create_diag": ([_P, _i32, _P, _P, _PP], ctypes.c_int),
@@ -365,6 +366,17 @@ def bm_pointing_destroy(p):
 def bm_pointing_get_hits(p, hits):
     import torch
     _check(lib.bm_pointing_get_hits(p, _dev(hits, torch.int32, "hits")), "bm_pointing_get_hits")
+
+
+def bm_pointing_get_order(p):
+    """The time indices of the non-flagged samples in pixel order, ties in
+    time order (a device int32 tensor holding the uint32 indices)."""
+    import torch
+    nv = ctypes.c_int64(0)
+    _check(lib.bm_pointing_get_order(p, None, ctypes.byref(nv)), "bm_pointing_get_order")
+    order = torch.zeros(max(nv.value, 1), dtype=torch.int32, device="cuda")
+    _check(lib.bm_pointing_get_order(p, ctypes.c_void_p(order.data_ptr()), None), "bm_pointing_get_order")
+    return order[: nv.value]
 
 
 def bm_pointing_apply(p, x, y):

@@ -529,6 +529,20 @@ bm_status bm_pointing_get_hits(const bm_pointing* p, int32_t* hits) {
     });
 }
 
+bm_status bm_pointing_get_order(const bm_pointing* p, uint32_t* order, int64_t* nvalid) {
+    return guarded([&] {
+        BM_REQUIRE(p, "NULL argument");
+        if (nvalid) *nvalid = p->nvalid;
+        if (order && p->nvalid > 0) {
+            use_device(p->ctx);
+            BM_CUDA(cudaMemcpyAsync(order, p->perm.get(), sizeof(uint32_t) * p->nvalid, cudaMemcpyDeviceToDevice,
+                                    p->ctx->stream));
+            BM_CUDA(cudaStreamSynchronize(p->ctx->stream));
+        }
+        return BM_OK;
+    });
+}
+
 bm_status bm_pointing_apply(bm_pointing* p, const double* x, double* y) {
     return guarded([&] {
         BM_REQUIRE(p && x && y, "NULL argument");

@@ -32,6 +32,7 @@
 // pairs (and TOD), and the CSR offsets come from a binary search per pixel
 // over pix[perm[i]].
 #include <algorithm>
+#include <type_traits>
 
 #include "bm_internal.cuh"
 
@@ -57,6 +58,7 @@ constexpr uint32_t kNoDigit = 0xFFFFFFFFu;
 struct SortPlan {
     int bits = 1, passes = 1, bins = 2, grid = 1;
     int64_t range = SC_TILE;  // samples per block, a multiple of SC_TILE
+    bool key16 = true;        // the keys between passes (the digits not yet consumed) fit in 16 bits
 };
 
 __device__ __forceinline__ int64_t range_begin(int64_t range) { return (int64_t)blockIdx.x * range; }
@@ -64,7 +66,7 @@ __device__ __forceinline__ int64_t range_begin(int64_t range) { return (int64_t)
 // Stores that ask L2 to keep their lines (evict_last): a scatter pass writes
 // each digit's output run a few samples per tile, so a 32-byte sector is
 // completed by later tiles of the same block; evicting it half written would
-// cost a read-modify-write in DRAM.
+// cost a read-modify-write in DRAM (plain stores measured slower).
 __device__ __forceinline__ uint64_t l2_keep_policy() {
     uint64_t pol;
     asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
@@ -73,14 +75,15 @@ __device__ __forceinline__ uint64_t l2_keep_policy() {
 __device__ __forceinline__ void st_keep(uint32_t* p, uint32_t v, uint64_t pol) {
     asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
 }
+__device__ __forceinline__ void st_keep(uint16_t* p, uint16_t v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.b16 [%0], %1, %2;" ::"l"(p), "h"(v), "l"(pol) : "memory");
+}
 __device__ __forceinline__ void st_keep(uint4* p, uint4 v, uint64_t pol) {
     asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y),
-                 "r"(v.z), "r"(v.w), "l"(pol)
-                 : "memory");
+                 "r"(v.z), "r"(v.w), "l"(pol) : "memory");
 }
 __device__ __forceinline__ void st_keep(float2* p, float2 v, uint64_t pol) {
-    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y), "l"(pol)
-                 : "memory");
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y), "l"(pol) : "memory");
 }
 
 // ----------------------------------------------------------------- validate
@@ -211,13 +214,15 @@ __device__ __forceinline__ uint32_t pixel_key(uint32_t raw, uint32_t flag_key) {
     return (flag_key && (int32_t)raw < 0) ? flag_key : raw;
 }
 
-// Digit counts of the block's range for one pass: hist[d * G + block].
-// Each thread counts 16 consecutive keys (vector loads), adding runs of equal
-// digits at once into its warp's own histogram; the warp histograms are
-// summed at the end.
+// Digit counts of the block's range for a pass after the first:
+// hist[d * G + block], the digit being the low bits of the stored key (each
+// pass stores the key shifted past the digit it sorted on).  Each thread
+// counts 16 consecutive keys (vector loads), adding runs of equal digits at
+// once into its warp's own histogram; the warp histograms are summed at the
+// end.
+template <typename KT>
 __global__ void __launch_bounds__(IG_THREADS)
-rs_hist_kernel(const uint32_t* __restrict__ keys, int64_t n, int64_t range, int shift, int bins, int G,
-               uint32_t flag_key, uint32_t* __restrict__ hist) {
+rs_hist_kernel(const KT* __restrict__ keys, int64_t n, int64_t range, int bins, int G, uint32_t* __restrict__ hist) {
     extern __shared__ __align__(16) uint32_t hh[];  // [IG_WARPS][bins]
     for (int d = threadIdx.x; d < IG_WARPS * bins; d += IG_THREADS) hh[d] = 0;
     __syncthreads();
@@ -225,27 +230,28 @@ rs_hist_kernel(const uint32_t* __restrict__ keys, int64_t n, int64_t range, int 
     const uint32_t dmask = (uint32_t)bins - 1u;
     const int64_t begin = range_begin(range);
     const int64_t end = begin + range < n ? begin + range : n;
+    constexpr int kPerVec = 16 / sizeof(KT);
     for (int64_t base = begin; base < end; base += IG_TILE) {
         const int64_t i0 = base + (int64_t)threadIdx.x * IG_PER_THREAD;
         uint32_t k[IG_PER_THREAD];
         if (i0 + IG_PER_THREAD <= end) {
             const uint4* v = reinterpret_cast<const uint4*>(keys + i0);  // i0 is a multiple of 16
 #pragma unroll
-            for (int q = 0; q < IG_PER_THREAD / 4; ++q) {
+            for (int q = 0; q < IG_PER_THREAD / kPerVec; ++q) {
                 const uint4 x = __ldcs(v + q);
-                k[4 * q] = pixel_key(x.x, flag_key);
-                k[4 * q + 1] = pixel_key(x.y, flag_key);
-                k[4 * q + 2] = pixel_key(x.z, flag_key);
-                k[4 * q + 3] = pixel_key(x.w, flag_key);
+                const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int e = 0; e < kPerVec; ++e)
+                    k[kPerVec * q + e] = sizeof(KT) == 4 ? w4[e] : (w4[e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
             }
         } else {
 #pragma unroll
-            for (int r = 0; r < IG_PER_THREAD; ++r) k[r] = i0 + r < end ? pixel_key(keys[i0 + r], flag_key) : kNoDigit;
+            for (int r = 0; r < IG_PER_THREAD; ++r) k[r] = i0 + r < end ? (uint32_t)keys[i0 + r] : kNoDigit;
         }
         uint32_t cur = kNoDigit, run = 0;
 #pragma unroll
         for (int r = 0; r < IG_PER_THREAD; ++r) {
-            const uint32_t d = k[r] == kNoDigit ? kNoDigit : ((k[r] >> shift) & dmask);
+            const uint32_t d = k[r] == kNoDigit ? kNoDigit : (k[r] & dmask);
             if (d == cur) {
                 ++run;
             } else {
@@ -306,25 +312,31 @@ __device__ void scan_bins(const T* cnt, T* start, int bins, uint32_t* wtot) {
 // cos, sin} (one store stream instead of three: the scatter's short digit
 // runs then fill whole lines, which measured twice as fast).  The keys travel
 // as their own stream, so the first word of the record is free for the TOD
-// sample when one is sorted along (else it is unused).
+// sample when one is sorted along (else it is unused).  A pass sorts on the
+// low `bits` bits of its key and stores the key shifted past them, so every
+// pass reads its digit from the low bits, and the stored keys are 16-bit
+// when what is left of the pixel index fits (2 bytes a sample instead of 4,
+// written once and read once).
 struct ScatterArgs {
     const uint4* rec_in;      // records of the previous pass, or null on the first pass:
                               //   then the sample index itself, the trig pairs and the TOD in time order
-    const uint32_t* keys_in;  // keys in this pass's input order
+    const void* keys_in;      // keys in this pass's input order: the validated pixel indices (int32) on
+                              //   the first pass, else the stored keys (KT)
     const float2* hi_in;
     const float* tod_in;      // first pass: the TOD in time order, or null
     const float2* lo_in;      // lo halves of the trig pairs in this pass's input order, or null
     int64_t n;
     int64_t range;
-    int shift, bins, G;
+    int bits, bins, G;
     const uint32_t* offs;  // [bins][G] exclusive digit-major scan of the counts
     uint4* rec_out;        // intermediate passes: records, and the keys alone for the next pass
-    uint32_t* keys_out;
+    void* keys_out;        //   (KT, shifted right by bits)
     uint32_t* perm_out;    // last pass: sample indices (perm) and trig pairs of the kept samples
     float2* hi_out;
     float* tod_out;        // last pass: the TOD of the kept samples in sorted order, or null
     float2* lo_out;        // every pass with lo_in: the lo halves in this pass's output order
-    uint32_t key_limit;    // last pass: samples with keys >= key_limit (flagged) get no entry
+    uint32_t nvalid;       // last pass: the kept samples; flagged ones (key npix, the largest) sort to
+                           //   positions >= nvalid and get no entry
     uint32_t flag_key;     // first pass: keys_in are pixel indices, -1 maps to flag_key (= npix)
     unsigned long long* err;  // set to 1 if a wait for a bulk copy gave up
 };
@@ -382,13 +394,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 // and tile position are then staged in digit order, and the write-out reads
 // the payload of a staged sample from the window in shared memory and
 // stores the digit runs at their running global offsets.
-template <bool LAST, bool FIRST>
+template <bool LAST, bool FIRST, typename KT>
 __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(ScatterArgs a) {
+    using KI = typename std::conditional<FIRST, uint32_t, KT>::type;  // the input keys' type
+    constexpr int kKeysPer16 = 16 / (int)sizeof(KI);
     extern __shared__ __align__(128) unsigned char smem[];
     uint4* s_rec = reinterpret_cast<uint4*>(smem);                          // window: records
     float2* s_hi = reinterpret_cast<float2*>(smem);                         // window, first pass: trig pairs
     float* s_tod = reinterpret_cast<float*>(smem + 8 * SC_TILE);            //   and TOD values
-    uint32_t* s_keys = reinterpret_cast<uint32_t*>(smem + 16 * SC_TILE);    // keys
+    KI* s_keys = reinterpret_cast<KI*>(smem + 16 * SC_TILE);                // keys
     uint16_t* s_src = reinterpret_cast<uint16_t*>(smem + 20 * SC_TILE);     // tile position of a staged sample
     uint16_t* wcnt = reinterpret_cast<uint16_t*>(smem + 22 * SC_TILE);      // [warp][digit]
     uint32_t* s_stk = reinterpret_cast<uint32_t*>(wcnt);                   // staged keys (after the counters' use)
@@ -398,10 +412,13 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
     uint16_t* tstart = tcnt + a.bins;                                       // tile-local start per digit
     __shared__ uint32_t wtot[SC_WARPS];
     __shared__ __align__(8) uint64_t bar[3];  // [0] keys, [1] window: first part, [2] window: second part
-    // lane-mask tables of the ranking, one per warp (2^10 entries): in the
-    // window's second half (records of the tile's second half, or the TOD
-    // values), which is copied in after the ranking
-    uint32_t* s_tbl = reinterpret_cast<uint32_t*>(smem + 8 * SC_TILE);
+    // lane-mask tables of the ranking, 4 KB a warp: in the window's second
+    // half (records of the tile's second half), which is copied in after the
+    // ranking; on the first pass, whose window (trig pairs and TOD values)
+    // leaves the last quarter free, in that quarter and the keys' buffer
+    // (the keys are in registers by then), so the whole window is copied in
+    // while the previous tile is written out
+    uint32_t* s_tbl = reinterpret_cast<uint32_t*>(smem + (FIRST ? 12 : 8) * SC_TILE);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     const int bins = a.bins;
@@ -430,11 +447,12 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
     // separately: whole 16-byte units (the rest of a ragged last tile is
     // loaded by the threads).  The fence orders the block's earlier accesses
     // of the buffer (made visible by a barrier) before the copy's writes.
+    const KI* keys_in = static_cast<const KI*>(a.keys_in);
     auto issue_keys = [&](int64_t base, int cnt) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        const uint32_t kbytes = (uint32_t)(cnt & ~3) * 4u;
+        const uint32_t kbytes = (uint32_t)(cnt & ~(kKeysPer16 - 1)) * (uint32_t)sizeof(KI);
         mbar_arrive_expect(&bar[0], kbytes);
-        if (kbytes) bulk_g2s(s_keys, a.keys_in + base, kbytes, &bar[0]);
+        if (kbytes) bulk_g2s(s_keys, keys_in + base, kbytes, &bar[0]);
     };
     // the window's first part: records of the tile's first half, or the
     // trig pairs
@@ -481,88 +499,129 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
     if (threadIdx.x == 0 && begin < end) {
         issue_keys(begin, (int)(end - begin < SC_TILE ? end - begin : SC_TILE));
         issue_win1(begin, (int)(end - begin < SC_TILE ? end - begin : SC_TILE));
+        if (FIRST) issue_win2(begin, (int)(end - begin < SC_TILE ? end - begin : SC_TILE));
     }
     uint32_t parity = 0;
     for (int64_t base = begin; base < end; base += SC_TILE, parity ^= 1u) {
         const int cnt = (int)(end - base < SC_TILE ? end - base : SC_TILE);
         // the ragged end of the last tile, with plain loads
-        for (int j = (cnt & ~3) + threadIdx.x; j < cnt; j += SC_THREADS) s_keys[j] = a.keys_in[base + j];
+        for (int j = (cnt & ~(kKeysPer16 - 1)) + threadIdx.x; j < cnt; j += SC_THREADS) s_keys[j] = keys_in[base + j];
         if (FIRST && (cnt & 1) && threadIdx.x == 0) s_hi[cnt - 1] = a.hi_in[base + cnt - 1];
-        if (give_up(!mbar_wait(&bar[0], parity), parity, parity, false)) return;
+        if (give_up(!mbar_wait(&bar[0], parity), parity, parity, FIRST)) return;
         __syncthreads();  // the plain-loaded keys too
         uint32_t key[IG_PER_THREAD], rank[IG_PER_THREAD];
         // 1. the warp's 512 consecutive keys, 32 per round
 #pragma unroll
         for (int r = 0; r < IG_PER_THREAD; ++r) {
             const int j = w * IG_WARP_SPAN + r * 32 + lane;
-            key[r] = j < cnt ? (FIRST ? pixel_key(s_keys[j], a.flag_key) : s_keys[j]) : 0u;
+            key[r] = j < cnt ? (FIRST ? pixel_key(s_keys[j], a.flag_key) : (uint32_t)s_keys[j]) : 0u;
         }
-        // 2. stable rank within the warp, round by round.  The lanes of a
-        //    round that hold the same digit are found through a table of
+        // 2. stable rank within the warp, two rounds at a time.  The lanes
+        //    of a round that hold the same digit are found through a table of
         //    lane masks in shared memory (each lane ORs its bit into its
-        //    digit's entry and reads the entry back; the lowest lane of the
-        //    group clears it): a warp-wide match instruction costs ~60 cycles
-        //    of the SM here, these shared-memory operations ~2.  The group's
-        //    leader adds the group size to the warp's digit counter and
-        //    broadcasts the count before it; rounds add in program order, so
-        //    ranks follow the input order (a stable sort).  One table of 2^10
-        //    entries per warp, in the window's second half.  Two 16-bit digit
-        //    counters share a 32-bit word (a warp counts at most 512 samples
-        //    a digit), so an add never carries into the neighbour.
+        //    digit's entry and reads the entry back; the lanes clear it
+        //    afterwards): a warp-wide match instruction costs ~60 cycles of
+        //    the SM here, these shared-memory operations ~2.  Rounds A and B
+        //    (B's samples after A's) have a table each, 512 entries, so both
+        //    fit in 4 KB a warp (the window's second half holds the 16
+        //    warps' tables); with 10-bit digits the tables take the low 9
+        //    bits and a vote on the top bit splits each entry.  Every lane
+        //    reads its digit's warp counter c before the pair: a sample of A
+        //    ranks at c + (A lanes below it with its digit), one of B at c +
+        //    (A lanes with its digit, read from A's table at B's digit) + (B
+        //    lanes below it); the lowest lane of each digit adds the pair's
+        //    count.  Ranks follow the input order (a stable sort), and the
+        //    pair takes three shared-memory round trips where two single
+        //    rounds took six.  The 16-bit counters are stored as halves (a
+        //    warp counts at most 512 samples a digit); two leaders never
+        //    store the same counter in one pair.
+        if (FIRST) __syncthreads();  // every warp has its keys before the tables overwrite them
         {
             uint4* z = reinterpret_cast<uint4*>(s_tbl);
             for (int i = threadIdx.x; i < SC_TILE / 2; i += SC_THREADS) z[i] = make_uint4(0u, 0u, 0u, 0u);
         }
         __syncthreads();
         {
-            uint32_t* wcnt32 = reinterpret_cast<uint32_t*>(wcnt);
-            uint32_t* tbl = s_tbl + w * 1024;
+            uint16_t* wc = wcnt + w * bins;
+            uint32_t* tA = s_tbl + w * 1024;
+            uint32_t* tB = tA + 512;
+            const bool split = bins > 512;
+            const uint32_t tmask = split ? 511u : dmask;
+            const unsigned me = 1u << lane;
 #pragma unroll
-            for (int r = 0; r < IG_PER_THREAD; ++r) {
-                const int j = w * IG_WARP_SPAN + r * 32 + lane;
-                const bool valid = j < cnt;
-                const uint32_t d = (key[r] >> a.shift) & dmask;
-                if (valid) atomicOr(tbl + d, 1u << lane);
+            for (int r = 0; r < IG_PER_THREAD; r += 2) {
+                const int jA = w * IG_WARP_SPAN + r * 32 + lane;
+                const bool vA = jA < cnt, vB = jA + 32 < cnt;
+                const uint32_t dA = key[r] & dmask, dB = key[r + 1] & dmask;
+                const uint32_t iA = dA & tmask, iB = dB & tmask;
+                if (vA) atomicOr(tA + iA, me);
+                if (vB) atomicOr(tB + iB, me);
+                const unsigned hA = split ? __ballot_sync(0xffffffffu, vA && (dA & 512u)) : 0u;
+                const unsigned hB = split ? __ballot_sync(0xffffffffu, vB && (dB & 512u)) : 0u;
                 __syncwarp();
-                const unsigned peers = valid ? tbl[d] : (1u << lane);
+                unsigned pA = tA[iA], pB = tB[iB];
+                unsigned xAB = tA[iB], xBA = tB[iA];  // A lanes on B's entry, B lanes on A's entry
+                const uint32_t cA = wc[dA], cB = wc[dB];
                 __syncwarp();
-                const int leader = __ffs(peers) - 1;
-                uint32_t old = 0;
-                if (valid && lane == leader) {
-                    const uint32_t sh = 16u * (d & 1u);
-                    old = (atomicAdd(wcnt32 + ((w * bins + d) >> 1), (uint32_t)__popc(peers) << sh) >> sh) & 0xFFFFu;
-                    tbl[d] = 0u;
+                if (split) {
+                    pA &= (dA & 512u) ? hA : ~hA;
+                    xAB &= (dB & 512u) ? hA : ~hA;
+                    pB &= (dB & 512u) ? hB : ~hB;
+                    xBA &= (dA & 512u) ? hB : ~hB;
                 }
-                rank[r] = __shfl_sync(0xffffffffu, old, leader) + __popc(peers & lt_mask);
-                __syncwarp();  // the entry is clear before the next round's ORs
+                if (vA) tA[iA] = 0u;
+                if (vB) tB[iB] = 0u;
+                const uint32_t nAB = (uint32_t)__popc(xAB), nBA = (uint32_t)__popc(xBA);
+                rank[r] = cA + (uint32_t)__popc(pA & lt_mask);
+                rank[r + 1] = cB + nAB + (uint32_t)__popc(pB & lt_mask);
+                if (vA && lane == __ffs(pA) - 1) wc[dA] = (uint16_t)(cA + (uint32_t)__popc(pA) + nBA);
+                if (vB && nAB == 0u && lane == __ffs(pB) - 1) wc[dB] = (uint16_t)(cB + (uint32_t)__popc(pB));
+                __syncwarp();  // entries clear and counters stored before the next pair
             }
         }
         __syncthreads();
         // the tables are done with: the window's second part can come in
-        if (threadIdx.x == 0) issue_win2(base, cnt);
-        // 3. per digit: exclusive prefix over warps, tile count; then over digits
-        for (int d = threadIdx.x; d < bins; d += SC_THREADS) {
-            uint32_t t = 0;
+        if (!FIRST && threadIdx.x == 0) issue_win2(base, cnt);
+        // 3. per digit: the tile count (the warps' counts summed), the scan
+        //    over digits, then each warp's start of each digit in the tile
+        //    (the digit's start + the counts of the warps before it) written
+        //    over its counter.  Two 16-bit digits a 32-bit word: every value
+        //    is below 2^13, so the halves add without carries.  run_base
+        //    becomes the offset of the tile's digit-ordered position j to its
+        //    global position: g = run_base[d] + j.
+        {
+            uint32_t* wc32 = reinterpret_cast<uint32_t*>(wcnt);
+            uint32_t* tcnt32 = reinterpret_cast<uint32_t*>(tcnt);
+            const uint32_t* tstart32 = reinterpret_cast<const uint32_t*>(tstart);
+            const int hb = bins >> 1;
+            for (int t = threadIdx.x; t < hb; t += SC_THREADS) {
+                uint32_t sum = 0;
 #pragma unroll
-            for (int q = 0; q < SC_WARPS; ++q) {
-                const uint32_t c = wcnt[q * bins + d];
-                wcnt[q * bins + d] = (uint16_t)t;
-                t += c;
+                for (int q = 0; q < SC_WARPS; ++q) sum += wc32[q * hb + t];
+                tcnt32[t] = sum;
             }
-            tcnt[d] = (uint16_t)t;
+            __syncthreads();
+            scan_bins<SC_THREADS>(tcnt, tstart, bins, wtot);
+            __syncthreads();
+            for (int t = threadIdx.x; t < hb; t += SC_THREADS) {
+                uint32_t run = tstart32[t];
+#pragma unroll
+                for (int q = 0; q < SC_WARPS; ++q) {
+                    const uint32_t c = wc32[q * hb + t];
+                    wc32[q * hb + t] = run;
+                    run += c;
+                }
+                run_base[2 * t] -= tstart[2 * t];
+                run_base[2 * t + 1] -= tstart[2 * t + 1];
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        scan_bins<SC_THREADS>(tcnt, tstart, bins, wtot);
-        __syncthreads();
         // 4. stage keys and tile positions in digit order: the positions
         //    first (they read the counters), then the keys into the
         //    counters' region; the keys' buffer is free from here on, so the
         //    next tile's keys start arriving during the write-out
 #pragma unroll
-        for (int r = 0; r < IG_PER_THREAD; ++r) {
-            const uint32_t d = (key[r] >> a.shift) & dmask;
-            rank[r] += tstart[d] + wcnt[w * bins + d];
-        }
+        for (int r = 0; r < IG_PER_THREAD; ++r) rank[r] += wcnt[w * bins + (key[r] & dmask)];
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < IG_PER_THREAD; ++r) {
@@ -590,8 +649,8 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
         for (int j = threadIdx.x; j < cnt; j += SC_THREADS) {
             const uint32_t k = s_stk[j];
             const uint32_t src = s_src[j];
-            const uint32_t d = (k >> a.shift) & dmask;
-            const uint32_t g = run_base[d] + (uint32_t)j - tstart[d];
+            const uint32_t d = k & dmask;
+            const uint32_t g = run_base[d] + (uint32_t)j;
             uint4 rr;
             if (!FIRST) {
                 rr = s_rec[src];
@@ -602,9 +661,9 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
             }
             if (!LAST) {
                 st_keep(a.rec_out + g, rr, pol);
-                st_keep(a.keys_out + g, k, pol);
+                st_keep(static_cast<KT*>(a.keys_out) + g, (KT)(k >> a.bits), pol);
                 if (a.lo_in) st_keep(a.lo_out + g, a.lo_in[base + src], pol);
-            } else if (k < a.key_limit) {
+            } else if (g < a.nvalid) {
                 st_keep(a.perm_out + g, rr.y, pol);
                 st_keep(a.hi_out + g, make_float2(__uint_as_float(rr.z), __uint_as_float(rr.w)), pol);
                 if (a.tod_out) st_keep(reinterpret_cast<uint32_t*>(a.tod_out) + g, rr.x, pol);
@@ -614,13 +673,15 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
         __syncthreads();
         // 6. advance the running offsets, clear the warp counters, start the
         //    next tile's window
-        for (int d = threadIdx.x; d < bins; d += SC_THREADS) {
-            run_base[d] += tcnt[d];
-#pragma unroll
-            for (int q = 0; q < SC_WARPS; ++q) wcnt[q * bins + d] = 0;
+        for (int d = threadIdx.x; d < bins; d += SC_THREADS) run_base[d] += tstart[d] + tcnt[d];
+        {
+            uint4* z = reinterpret_cast<uint4*>(wcnt);
+            for (int i = threadIdx.x; i < SC_WARPS * bins / 8; i += SC_THREADS) z[i] = make_uint4(0u, 0u, 0u, 0u);
         }
-        if (threadIdx.x == 0 && base + SC_TILE < end)
+        if (threadIdx.x == 0 && base + SC_TILE < end) {
             issue_win1(base + SC_TILE, (int)(end - base - SC_TILE < SC_TILE ? end - base - SC_TILE : SC_TILE));
+            if (FIRST) issue_win2(base + SC_TILE, (int)(end - base - SC_TILE < SC_TILE ? end - base - SC_TILE : SC_TILE));
+        }
         __syncthreads();
     }
 }
@@ -648,6 +709,15 @@ __global__ void hits_kernel(const int64_t* __restrict__ off, int64_t npix, int32
 }
 
 
+using ScatterFn = void (*)(ScatterArgs);
+ScatterFn scatter_fn(bool last, bool first, bool key16) {
+    if (first)
+        return last ? rs_scatter_kernel<true, true, uint32_t>
+                    : (key16 ? rs_scatter_kernel<false, true, uint16_t> : rs_scatter_kernel<false, true, uint32_t>);
+    if (last) return key16 ? rs_scatter_kernel<true, false, uint16_t> : rs_scatter_kernel<true, false, uint32_t>;
+    return key16 ? rs_scatter_kernel<false, false, uint16_t> : rs_scatter_kernel<false, false, uint32_t>;
+}
+
 SortPlan plan_sort(const bm_context* ctx, int64_t n, int64_t npix) {
     SortPlan sp;
     int nbits = 1;
@@ -655,18 +725,18 @@ SortPlan plan_sort(const bm_context* ctx, int64_t n, int64_t npix) {
     sp.passes = (nbits + RS_MAX_BITS - 1) / RS_MAX_BITS;
     sp.bits = (nbits + sp.passes - 1) / sp.passes;
     sp.bins = 1 << sp.bits;
+    sp.key16 = nbits - sp.bits <= 16;
     const size_t smem = scatter_smem(sp.bins);
-    ensure_smem_limit(reinterpret_cast<const void*>(rs_scatter_kernel<false, true>), smem);
-    ensure_smem_limit(reinterpret_cast<const void*>(rs_scatter_kernel<false, false>), smem);
-    ensure_smem_limit(reinterpret_cast<const void*>(rs_scatter_kernel<true, true>), smem);
-    ensure_smem_limit(reinterpret_cast<const void*>(rs_scatter_kernel<true, false>), smem);
-    ensure_smem_limit(reinterpret_cast<const void*>(rs_hist_kernel), sizeof(uint32_t) * IG_WARPS * sp.bins);
+    for (int pass = 0; pass < sp.passes; ++pass)
+        ensure_smem_limit(reinterpret_cast<const void*>(scatter_fn(pass + 1 == sp.passes, pass == 0, sp.key16)), smem);
+    ensure_smem_limit(reinterpret_cast<const void*>(rs_hist_kernel<uint16_t>), sizeof(uint32_t) * IG_WARPS * sp.bins);
+    ensure_smem_limit(reinterpret_cast<const void*>(rs_hist_kernel<uint32_t>), sizeof(uint32_t) * IG_WARPS * sp.bins);
     for (const void* k : {reinterpret_cast<const void*>(validate_kernel<kTrigIn, true>),
                           reinterpret_cast<const void*>(validate_kernel<kPsi64, true>),
                           reinterpret_cast<const void*>(validate_kernel<kPsi32, true>),
                           reinterpret_cast<const void*>(validate_kernel<kHwp, true>)})
         ensure_smem_limit(k, sizeof(uint32_t) * kVHist * sp.bins);
-    int per_sm = blocks_per_sm(reinterpret_cast<const void*>(rs_scatter_kernel<true, false>), SC_THREADS, smem);
+    int per_sm = blocks_per_sm(reinterpret_cast<const void*>(scatter_fn(true, sp.passes == 1, sp.key16)), SC_THREADS, smem);
     if (per_sm < 1) per_sm = 1;
     // four waves of equal ranges keep the tail short
     const int64_t want = (int64_t)ctx->num_sms * per_sm * 4;
@@ -731,33 +801,37 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
     // for the next ingest, so that these large transient buffers do not
     // fragment the device memory pool the handles allocate from.
     uint4 *rec_a = nullptr, *rec_b = nullptr;
-    uint32_t *keys_a = nullptr, *keys_b = nullptr;
+    void *keys_a = nullptr, *keys_b = nullptr;
     float2 *lo_a = nullptr, *lo_b = nullptr;
+    const size_t key_bytes = sp.key16 ? 2 : 4;
     if (sp.passes > 1) {
         rec_a = workspace_as<uint4>(ctx, "ingest_rec_a", n);
-        keys_a = workspace_as<uint32_t>(ctx, "ingest_keys_a", n);
+        keys_a = workspace(ctx, "ingest_keys_a", key_bytes * n);
         if (has_lo) lo_a = workspace_as<float2>(ctx, "ingest_lo_a", n);
     }
     if (sp.passes > 2) {
         rec_b = workspace_as<uint4>(ctx, "ingest_rec_b", n);
-        keys_b = workspace_as<uint32_t>(ctx, "ingest_keys_b", n);
+        keys_b = workspace(ctx, "ingest_keys_b", key_bytes * n);
         if (has_lo) lo_b = workspace_as<float2>(ctx, "ingest_lo_b", n);
     }
     // the first pass reads its keys from the validated pixel indices
-    const uint32_t* kin = reinterpret_cast<const uint32_t*>(p->pix.get());
-    uint32_t* kout = keys_a;
+    const void* kin = p->pix.get();
+    void* kout = keys_a;
     const size_t smem = scatter_smem(sp.bins);
     const uint4* rin = nullptr;  // the first pass reads keys, indices and trig in time order
     uint4* rout = rec_a;
     const float2* lin = has_lo ? p->cs_lo_t.get() : nullptr;
     float2* lout = lo_a;
     for (int pass = 0; pass < sp.passes; ++pass) {
-        const int shift = pass * sp.bits;
         if (pass > 0) {
             ScopedTimer ht(ctx, "ingest_hist");
             const size_t hsm = sizeof(uint32_t) * IG_WARPS * sp.bins;
-            rs_hist_kernel<<<sp.grid, IG_THREADS, hsm, s>>>(kin, n, sp.range, shift, sp.bins, sp.grid,
-                                                            pass == 0 ? (uint32_t)npix : 0u, hist.get());
+            if (sp.key16)
+                rs_hist_kernel<uint16_t><<<sp.grid, IG_THREADS, hsm, s>>>(static_cast<const uint16_t*>(kin), n,
+                                                                          sp.range, sp.bins, sp.grid, hist.get());
+            else
+                rs_hist_kernel<uint32_t><<<sp.grid, IG_THREADS, hsm, s>>>(static_cast<const uint32_t*>(kin), n,
+                                                                          sp.range, sp.bins, sp.grid, hist.get());
             BM_LAUNCH_CHECK();
         }
         exclusive_scan_u32(hist.get(), hist.get(), (int64_t)sp.bins * sp.grid, s);
@@ -769,7 +843,7 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
         a.lo_in = lin;
         a.n = n;
         a.range = sp.range;
-        a.shift = shift;
+        a.bits = sp.bits;
         a.bins = sp.bins;
         a.G = sp.grid;
         a.offs = hist.get();
@@ -780,8 +854,7 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
             a.rec_out = rout;
             a.keys_out = kout;
             a.lo_out = lout;
-            if (pass == 0) rs_scatter_kernel<false, true><<<sp.grid, SC_THREADS, smem, s>>>(a);
-            else rs_scatter_kernel<false, false><<<sp.grid, SC_THREADS, smem, s>>>(a);
+            scatter_fn(false, pass == 0, sp.key16)<<<sp.grid, SC_THREADS, smem, s>>>(a);
             BM_LAUNCH_CHECK();
             kin = kout;
             kout = (kout == keys_a) ? keys_b : keys_a;
@@ -794,9 +867,8 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
             a.hi_out = p->cs_hi_s.get();
             a.tod_out = tod ? p->tod_s.get() : nullptr;
             a.lo_out = has_lo ? p->cs_lo_s.get() : nullptr;
-            a.key_limit = (uint32_t)npix;
-            if (pass == 0) rs_scatter_kernel<true, true><<<sp.grid, SC_THREADS, smem, s>>>(a);
-            else rs_scatter_kernel<true, false><<<sp.grid, SC_THREADS, smem, s>>>(a);
+            a.nvalid = (uint32_t)nvalid;
+            scatter_fn(true, pass == 0, sp.key16)<<<sp.grid, SC_THREADS, smem, s>>>(a);
             BM_LAUNCH_CHECK();
         }
     }

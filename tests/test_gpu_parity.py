@@ -87,6 +87,38 @@ def test_pointing_operators_and_hits(L, ctx, solver):
         c.close()
 
 
+def stable_order(pix):
+    """The kept samples' time indices sorted by pixel, ties in time order."""
+    kept = np.flatnonzero(pix >= 0)
+    return kept[np.argsort(pix[kept], kind="stable")]
+
+
+@pytest.mark.parametrize("nside,n", [(256, 2_000_003),   # 20 bits: two 10-bit passes, 16-bit keys between
+                                     (2048, 1_000_003),  # 26 bits: three 9-bit passes, 32-bit keys between
+                                     (4096, 300_007)])   # 28 bits: three 10-bit passes, 32-bit keys between
+def test_sort_order_is_the_stable_sort(L, ctx, nside, n):
+    """The order every operator runs in is, exactly, the stable sort of the
+    kept samples by pixel: ties (runs of one pixel, and hot pixels hit from
+    many tiles and ranges) in time order, and pixels just below npix, whose
+    high digits the flagged samples' key npix shares."""
+    npix = 12 * nside * nside
+    rng = np.random.default_rng(nside + 1)
+    pix = rng.integers(0, npix, size=n).astype(np.int32)
+    pix[1::3] = pix[0::3][: pix[1::3].size]
+    hot = rng.random(n) < 0.2
+    pix[hot] = rng.integers(0, 100, size=hot.sum()) * (npix // 100)
+    top = rng.random(n) < 0.05
+    pix[top] = npix - 1 - rng.integers(0, 64, size=top.sum())
+    pix[rng.random(n) < 0.1] = -1
+    psi = rng.uniform(0, np.pi, size=n)
+    p = L.bm_pointing_create(ctx, npix, torch.from_numpy(pix).cuda(), torch.from_numpy(psi).cuda(), 3)
+    try:
+        order = L.bm_pointing_get_order(p).cpu().numpy().astype(np.int64)
+        assert np.array_equal(order, stable_order(pix))
+    finally:
+        L.bm_pointing_destroy(p)
+
+
 @pytest.mark.parametrize("nside,n,trig", [(8, 200_003, False),       # 10-bit keys: one sort pass
                                           (64, 3_000_001, True),     # 16 bits: two passes, many ranges
                                           (1024, 500_009, False)])   # 24 bits: three passes
@@ -113,6 +145,7 @@ def test_sort_plans_random_pixels(L, ctx, nside, n, trig):
         hits = torch.zeros(npix, dtype=torch.int32, device="cuda")
         L.bm_pointing_get_hits(p, hits)
         assert np.array_equal(hits.cpu().numpy(), gls.hits(pix, npix))
+        assert np.array_equal(L.bm_pointing_get_order(p).cpu().numpy().astype(np.int64), stable_order(pix))
         y = rng.normal(size=n)
         xt = torch.zeros(npix * 3, dtype=torch.float64, device="cuda")
         L.bm_pointing_apply_transpose(p, torch.from_numpy(y).cuda(), xt)
