@@ -458,17 +458,22 @@ def run_gb300(args, rank, world, local_rank):
     n_valid = int(hits.sum().item())
     scatter_bytes = 0
     hist_bytes = 0
+    # The timed step passes cos/sin as 16-byte-aligned device arrays: the
+    # first sort pass reads them itself and writes the time-ordered pairs
+    # (8 bytes a sample), and the validation reads and copies the pixels alone.
     for ps in range(passes):
         last = ps == passes - 1
-        # keys + records, or pixel keys + trig pair (+ TOD) in time order
+        # keys + records, or pixel keys + cos + sin (+ TOD) in time order
         rd = (kb + 16) if ps > 0 else (4 + (12 if carried else 8))
         # perm + trig (+ TOD) of kept samples, or records + keys
         wr = ((16 if carried else 12) * n_valid / nt) if last else 16 + kb
+        if ps == 0:
+            wr += 8                                        # the time-ordered trig pairs
         scatter_bytes += (rd + wr) * nt
         if ps > 0:                                         # (the first pass's counts come from validation)
             hist_bytes += kb * nt                          # keys
     step_bytes = {
-        "ingest_validate": 24 * nt,                       # pix + cos + sin in; pix, trig pair out
+        "ingest_validate": 8 * nt,                        # pix in, pix out (with the first pass's digit counts)
         "ingest_hist": hist_bytes,
         "ingest_scatter": scatter_bytes,
         # perm + trig pair (+ the carried TOD, whose RHS this pass also sums) in, weighted pair out

@@ -93,13 +93,16 @@ __device__ __forceinline__ void st_keep(float2* p, float2 v, uint64_t pol) {
 // pairs.  counters[0] = invalid samples,
 // counters[1] = flagged samples.  With tod_dst, also copies the TOD
 // (a host-memory source read once over the host link).
-// MODE: kTrigIn (cos/sin given), kPsi64 or kPsi32 (angles given).
+// MODE: kTrigIn (cos/sin given), kPsi64 or kPsi32 (angles given), kHwp
+// (the half-wave-plate model), or kPixOnly (cos/sin given and left to the
+// first sort pass, which reads them once, checks them and writes the
+// time-ordered pairs: this pass then reads and copies the pixels alone).
 // HIST: also the first sort pass's digit counts (the sort key of each
 // validated sample, flagged ones as npix, masked to the low digit) of each
 // range of `range` samples, hist[d * G + range], as rs_hist_kernel counts
 // them; `sub` blocks share a range (its equal parts), each adding its counts
 // to the zeroed hist.  Without HIST the loop is grid-strided.
-constexpr int kTrigIn = 0, kPsi64 = 1, kPsi32 = 2, kHwp = 3;
+constexpr int kTrigIn = 0, kPsi64 = 1, kPsi32 = 2, kHwp = 3, kPixOnly = 4;
 constexpr int kVHist = 4;  // shared-memory digit histograms per validation block
 template <int MODE, bool HIST>
 __global__ void __launch_bounds__(256)
@@ -125,6 +128,8 @@ validate_kernel(const int32_t* __restrict__ pix, const void* __restrict__ psi,
         if constexpr (MODE == kTrigIn) {
             ok_a = fabsf(c) <= 1.0f && fabsf(s) <= 1.0f;  // false for NaN
             hi[i] = make_float2(c, s);
+        } else if constexpr (MODE == kPixOnly) {
+            ok_a = true;
         } else if constexpr (MODE == kHwp) {
             // 2 theta of the half-wave-plate model in turns, reduced exactly,
             // and its cos and sin as double-float pairs (table and short
@@ -174,9 +179,9 @@ validate_kernel(const int32_t* __restrict__ pix, const void* __restrict__ psi,
                 }
             } else if constexpr (MODE == kPsi64) {
                 if (v) a[u] = __ldcs(static_cast<const double*>(psi) + i);
-            } else {
+            } else if constexpr (MODE == kPsi32) {
                 if (v) a[u] = (double)__ldcs(static_cast<const float*>(psi) + i);
-            }
+            }  // kHwp and kPixOnly read no angle
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -322,7 +327,11 @@ struct ScatterArgs {
                               //   then the sample index itself, the trig pairs and the TOD in time order
     const void* keys_in;      // keys in this pass's input order: the validated pixel indices (int32) on
                               //   the first pass, else the stored keys (KT)
-    const float2* hi_in;
+    const float2* hi_in;      // first pass: the trig pairs in time order; or, with c_in and s_in,
+    const float* c_in;        //   the caller's cos 2psi and sin 2psi (16-byte aligned), which the
+    const float* s_in;        //   pass checks (|.| <= 1) and writes as pairs to hi_t_out in time order
+    float2* hi_t_out;
+    unsigned long long* bad;  //   (samples with a bad pair are counted here)
     const float* tod_in;      // first pass: the TOD in time order, or null
     const float2* lo_in;      // lo halves of the trig pairs in this pass's input order, or null
     int64_t n;
@@ -394,13 +403,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 // and tile position are then staged in digit order, and the write-out reads
 // the payload of a staged sample from the window in shared memory and
 // stores the digit runs at their running global offsets.
-template <bool LAST, bool FIRST, typename KT>
+template <bool LAST, bool FIRST, typename KT, bool TRIG2>
 __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(ScatterArgs a) {
     using KI = typename std::conditional<FIRST, uint32_t, KT>::type;  // the input keys' type
     constexpr int kKeysPer16 = 16 / (int)sizeof(KI);
     extern __shared__ __align__(128) unsigned char smem[];
     uint4* s_rec = reinterpret_cast<uint4*>(smem);                          // window: records
     float2* s_hi = reinterpret_cast<float2*>(smem);                         // window, first pass: trig pairs
+    float* s_c = reinterpret_cast<float*>(smem);                            //   or (TRIG2) cos and sin
+    float* s_s = reinterpret_cast<float*>(smem + 4 * SC_TILE);
     float* s_tod = reinterpret_cast<float*>(smem + 8 * SC_TILE);            //   and TOD values
     KI* s_keys = reinterpret_cast<KI*>(smem + 16 * SC_TILE);                // keys
     uint16_t* s_src = reinterpret_cast<uint16_t*>(smem + 20 * SC_TILE);     // tile position of a staged sample
@@ -462,6 +473,13 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
             const uint32_t n1 = cnt < SC_TILE / 2 ? (uint32_t)cnt : SC_TILE / 2;
             mbar_arrive_expect(&bar[1], n1 * 16u);
             bulk_g2s(s_rec, a.rec_in + base, n1 * 16u, &bar[1]);
+        } else if (TRIG2) {
+            const uint32_t cbytes = (uint32_t)(cnt & ~3) * 4u;
+            mbar_arrive_expect(&bar[1], 2u * cbytes);
+            if (cbytes) {
+                bulk_g2s(s_c, a.c_in + base, cbytes, &bar[1]);
+                bulk_g2s(s_s, a.s_in + base, cbytes, &bar[1]);
+            }
         } else {
             const uint32_t hbytes = (uint32_t)(cnt & ~1) * 8u;
             mbar_arrive_expect(&bar[1], hbytes);
@@ -502,11 +520,17 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
         if (FIRST) issue_win2(begin, (int)(end - begin < SC_TILE ? end - begin : SC_TILE));
     }
     uint32_t parity = 0;
+    uint32_t nbad = 0;
     for (int64_t base = begin; base < end; base += SC_TILE, parity ^= 1u) {
         const int cnt = (int)(end - base < SC_TILE ? end - base : SC_TILE);
         // the ragged end of the last tile, with plain loads
         for (int j = (cnt & ~(kKeysPer16 - 1)) + threadIdx.x; j < cnt; j += SC_THREADS) s_keys[j] = keys_in[base + j];
-        if (FIRST && (cnt & 1) && threadIdx.x == 0) s_hi[cnt - 1] = a.hi_in[base + cnt - 1];
+        if (FIRST && !TRIG2 && (cnt & 1) && threadIdx.x == 0) s_hi[cnt - 1] = a.hi_in[base + cnt - 1];
+        if (TRIG2)
+            for (int j = (cnt & ~3) + threadIdx.x; j < cnt; j += SC_THREADS) {
+                s_c[j] = a.c_in[base + j];
+                s_s[j] = a.s_in[base + j];
+            }
         if (give_up(!mbar_wait(&bar[0], parity), parity, parity, FIRST)) return;
         __syncthreads();  // the plain-loaded keys too
         uint32_t key[IG_PER_THREAD], rank[IG_PER_THREAD];
@@ -582,6 +606,18 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
         __syncthreads();
         // the tables are done with: the window's second part can come in
         if (!FIRST && threadIdx.x == 0) issue_win2(base, cnt);
+        // given cos/sin (TRIG2): the tile's time-ordered pairs, checked and
+        // written while the digits are counted and staged, phases that leave
+        // the store path idle (in the write-out these stores measured 3k
+        // cycles a tile)
+        if (TRIG2) {
+            if (give_up(!mbar_wait(&bar[1], parity), parity, parity, true)) return;
+            for (int j = threadIdx.x; j < cnt; j += SC_THREADS) {
+                const float cj = s_c[j], sj = s_s[j];
+                __stcs(a.hi_t_out + base + j, make_float2(cj, sj));
+                nbad += !(fabsf(cj) <= 1.0f && fabsf(sj) <= 1.0f);  // NaN counts
+            }
+        }
         // 3. per digit: the tile count (the warps' counts summed), the scan
         //    over digits, then each warp's start of each digit in the tile
         //    (the digit's start + the counts of the warps before it) written
@@ -655,7 +691,7 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
             if (!FIRST) {
                 rr = s_rec[src];
             } else {
-                const float2 h = s_hi[src];
+                const float2 h = TRIG2 ? make_float2(s_c[src], s_s[src]) : s_hi[src];
                 const float dv = a.tod_in ? s_tod[src] : 0.f;
                 rr = make_uint4(__float_as_uint(dv), (uint32_t)(base + src), __float_as_uint(h.x), __float_as_uint(h.y));
             }
@@ -684,6 +720,10 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
         }
         __syncthreads();
     }
+    if (TRIG2) {
+        nbad = __reduce_add_sync(0xffffffffu, nbad);
+        if (lane == 0 && nbad) atomicAdd(a.bad, (unsigned long long)nbad);
+    }
 }
 
 // off[p] = first sorted position whose pixel is >= p, for p in [0, npix]:
@@ -710,12 +750,18 @@ __global__ void hits_kernel(const int64_t* __restrict__ off, int64_t npix, int32
 
 
 using ScatterFn = void (*)(ScatterArgs);
-ScatterFn scatter_fn(bool last, bool first, bool key16) {
+ScatterFn scatter_fn(bool last, bool first, bool key16, bool trig2) {
+    if (first && trig2)
+        return last ? rs_scatter_kernel<true, true, uint32_t, true>
+                    : (key16 ? rs_scatter_kernel<false, true, uint16_t, true>
+                             : rs_scatter_kernel<false, true, uint32_t, true>);
     if (first)
-        return last ? rs_scatter_kernel<true, true, uint32_t>
-                    : (key16 ? rs_scatter_kernel<false, true, uint16_t> : rs_scatter_kernel<false, true, uint32_t>);
-    if (last) return key16 ? rs_scatter_kernel<true, false, uint16_t> : rs_scatter_kernel<true, false, uint32_t>;
-    return key16 ? rs_scatter_kernel<false, false, uint16_t> : rs_scatter_kernel<false, false, uint32_t>;
+        return last ? rs_scatter_kernel<true, true, uint32_t, false>
+                    : (key16 ? rs_scatter_kernel<false, true, uint16_t, false>
+                             : rs_scatter_kernel<false, true, uint32_t, false>);
+    if (last)
+        return key16 ? rs_scatter_kernel<true, false, uint16_t, false> : rs_scatter_kernel<true, false, uint32_t, false>;
+    return key16 ? rs_scatter_kernel<false, false, uint16_t, false> : rs_scatter_kernel<false, false, uint32_t, false>;
 }
 
 SortPlan plan_sort(const bm_context* ctx, int64_t n, int64_t npix) {
@@ -728,15 +774,19 @@ SortPlan plan_sort(const bm_context* ctx, int64_t n, int64_t npix) {
     sp.key16 = nbits - sp.bits <= 16;
     const size_t smem = scatter_smem(sp.bins);
     for (int pass = 0; pass < sp.passes; ++pass)
-        ensure_smem_limit(reinterpret_cast<const void*>(scatter_fn(pass + 1 == sp.passes, pass == 0, sp.key16)), smem);
+        for (bool trig2 : {false, true})
+            ensure_smem_limit(reinterpret_cast<const void*>(scatter_fn(pass + 1 == sp.passes, pass == 0, sp.key16, trig2)),
+                              smem);
     ensure_smem_limit(reinterpret_cast<const void*>(rs_hist_kernel<uint16_t>), sizeof(uint32_t) * IG_WARPS * sp.bins);
     ensure_smem_limit(reinterpret_cast<const void*>(rs_hist_kernel<uint32_t>), sizeof(uint32_t) * IG_WARPS * sp.bins);
     for (const void* k : {reinterpret_cast<const void*>(validate_kernel<kTrigIn, true>),
+                          reinterpret_cast<const void*>(validate_kernel<kPixOnly, true>),
                           reinterpret_cast<const void*>(validate_kernel<kPsi64, true>),
                           reinterpret_cast<const void*>(validate_kernel<kPsi32, true>),
                           reinterpret_cast<const void*>(validate_kernel<kHwp, true>)})
         ensure_smem_limit(k, sizeof(uint32_t) * kVHist * sp.bins);
-    int per_sm = blocks_per_sm(reinterpret_cast<const void*>(scatter_fn(true, sp.passes == 1, sp.key16)), SC_THREADS, smem);
+    int per_sm = blocks_per_sm(reinterpret_cast<const void*>(scatter_fn(true, sp.passes == 1, sp.key16, false)),
+                               SC_THREADS, smem);
     if (per_sm < 1) per_sm = 1;
     // four waves of equal ranges keep the tail short
     const int64_t want = (int64_t)ctx->num_sms * per_sm * 4;
@@ -757,6 +807,20 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
     const int64_t n = p->nsamples, npix = p->npix;
     const bool exact_trig = cos2psi != nullptr;  // FP32 trig given: it defines the operator, no lo part
     const bool has_lo = !exact_trig;
+    // cos/sin in device memory at 16-byte boundaries: the first sort pass
+    // bulk-copies them itself, checks them and writes the time-ordered
+    // pairs; the validation then reads the pixels alone
+    auto in_device_memory = [](const void* ptr) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return false;
+        }
+        return at.type == cudaMemoryTypeDevice;
+    };
+    const bool trig2 = exact_trig && !hwp &&
+                       ((reinterpret_cast<uintptr_t>(cos2psi) | reinterpret_cast<uintptr_t>(sin2psi)) & 15u) == 0 &&
+                       in_device_memory(cos2psi) && in_device_memory(sin2psi);
     const SortPlan sp = plan_sort(ctx, n, npix);
     const int threads = 256;
 
@@ -766,14 +830,17 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
     DevBuf<float> tod_copy;  // a host TOD, copied by the validation pass
     if (tod && tod_on_host) tod_copy.alloc(n);
     const float* tod_t = tod_on_host ? tod_copy.get() : tod;
-    DevBuf<unsigned long long> counters(3);  // invalid samples, flagged samples, a scatter wait that gave up
-    BM_CUDA(cudaMemsetAsync(counters.get(), 0, 3 * sizeof(unsigned long long), s));
+    // invalid samples, flagged samples, a scatter wait that gave up, samples
+    // with a bad cos/sin pair found by the first sort pass
+    DevBuf<unsigned long long> counters(4);
+    BM_CUDA(cudaMemsetAsync(counters.get(), 0, 4 * sizeof(unsigned long long), s));
     // digit counts of every sort pass; the first pass's come from the validation
     DevBuf<uint32_t> hist((size_t)sp.bins * sp.grid);
     {
         ScopedTimer vt(ctx, "ingest_validate");
         BM_CUDA(cudaMemsetAsync(hist.get(), 0, sizeof(uint32_t) * (size_t)sp.bins * sp.grid, s));
-        auto kern = exact_trig ? validate_kernel<kTrigIn, true>
+        auto kern = trig2        ? validate_kernel<kPixOnly, true>
+                    : exact_trig ? validate_kernel<kTrigIn, true>
                     : hwp      ? validate_kernel<kHwp, true>
                                : (psi_dtype == BM_F64 ? validate_kernel<kPsi64, true> : validate_kernel<kPsi32, true>);
         constexpr int kSub = 2;  // two blocks a range: eight resident blocks per SM
@@ -839,6 +906,13 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
         a.rec_in = rin;
         a.keys_in = kin;
         a.hi_in = p->cs_hi_t.get();
+        const bool pass_trig2 = trig2 && pass == 0;
+        if (pass_trig2) {
+            a.c_in = cos2psi;
+            a.s_in = sin2psi;
+            a.hi_t_out = p->cs_hi_t.get();
+            a.bad = counters.get() + 3;
+        }
         a.tod_in = pass == 0 ? tod_t : nullptr;
         a.lo_in = lin;
         a.n = n;
@@ -854,7 +928,7 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
             a.rec_out = rout;
             a.keys_out = kout;
             a.lo_out = lout;
-            scatter_fn(false, pass == 0, sp.key16)<<<sp.grid, SC_THREADS, smem, s>>>(a);
+            scatter_fn(false, pass == 0, sp.key16, pass_trig2)<<<sp.grid, SC_THREADS, smem, s>>>(a);
             BM_LAUNCH_CHECK();
             kin = kout;
             kout = (kout == keys_a) ? keys_b : keys_a;
@@ -868,7 +942,7 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
             a.tod_out = tod ? p->tod_s.get() : nullptr;
             a.lo_out = has_lo ? p->cs_lo_s.get() : nullptr;
             a.nvalid = (uint32_t)nvalid;
-            scatter_fn(true, pass == 0, sp.key16)<<<sp.grid, SC_THREADS, smem, s>>>(a);
+            scatter_fn(true, pass == 0, sp.key16, pass_trig2)<<<sp.grid, SC_THREADS, smem, s>>>(a);
             BM_LAUNCH_CHECK();
         }
     }
@@ -879,13 +953,15 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
     BM_LAUNCH_CHECK();
     hits_kernel<<<pgrid, threads, 0, s>>>(p->off.get(), npix, p->hits.get());
     BM_LAUNCH_CHECK();
-    unsigned long long h_err = 0;
-    BM_CUDA(cudaMemcpyAsync(&h_err, counters.get() + 2, sizeof(h_err), cudaMemcpyDeviceToHost, s));
+    unsigned long long h_err[2] = {0, 0};
+    BM_CUDA(cudaMemcpyAsync(h_err, counters.get() + 2, sizeof(h_err), cudaMemcpyDeviceToHost, s));
     BM_CUDA(cudaStreamSynchronize(s));
-    if (h_err) {
+    if (h_err[0]) {
         set_error("the pixel sort gave up waiting for a bulk copy into shared memory");
         throw Error{BM_ERR_TIMEOUT};
     }
+    BM_REQUIRE(h_err[1] == 0, "%llu samples have a pixel index outside [-1, %lld) or a bad angle / trig value",
+               h_err[1], (long long)npix);
 }
 
 }  // namespace bm

@@ -503,6 +503,56 @@ def test_trig_input_blocks_matvec_rhs(L, ctx, noise):
         c.close()
 
 
+def test_trig_input_alignment_and_host_memory(L, ctx):
+    """Given cos/sin in device memory at 16-byte boundaries, the first sort
+    pass reads them itself and writes the time-ordered pairs; off a boundary
+    or in host memory the validation pass does.  Every form gives the same
+    handle: the order, P x over the time-ordered pairs and P^T y bitwise
+    equal.  A cos or sin outside [-1, 1] (or NaN) is refused in every form."""
+    nside, n = 16, 300_001
+    npix = 12 * nside * nside
+    rng = np.random.default_rng(77)
+    pix = rng.integers(0, npix, size=n).astype(np.int32)
+    pix[rng.random(n) < 0.05] = -1
+    c32, s32 = synth.trig32(rng.uniform(0, np.pi, size=n))
+    y = torch.from_numpy(rng.normal(size=n)).cuda()
+    x = torch.from_numpy(rng.normal(size=npix * 3)).cuda()
+
+    def forms(c, s):
+        dc, ds = torch.from_numpy(c).cuda(), torch.from_numpy(s).cuda()
+        oc, os_ = torch.zeros(n + 1, dtype=torch.float32, device="cuda"), torch.zeros(n + 1, dtype=torch.float32,
+                                                                                     device="cuda")
+        oc[1:], os_[1:] = dc, ds
+        assert oc[1:].data_ptr() % 16 != 0
+        return {"aligned": (dc, ds), "offset": (oc[1:], os_[1:]),
+                "host": (torch.from_numpy(c).pin_memory(), torch.from_numpy(s).pin_memory())}
+
+    d_pix = torch.from_numpy(pix).cuda()
+    got = {}
+    for name, (c, s_) in forms(c32, s32).items():
+        p = L.bm_pointing_create_trig(ctx, npix, d_pix, c, s_, 3)
+        try:
+            yy = torch.zeros(n, dtype=torch.float64, device="cuda")
+            L.bm_pointing_apply(p, x, yy)
+            xt = torch.zeros(npix * 3, dtype=torch.float64, device="cuda")
+            L.bm_pointing_apply_transpose(p, y, xt)
+            got[name] = (L.bm_pointing_get_order(p).cpu().numpy(), yy.cpu().numpy(), xt.cpu().numpy())
+        finally:
+            L.bm_pointing_destroy(p)
+    for name in ("offset", "host"):
+        for a, b in zip(got["aligned"], got[name]):
+            assert np.array_equal(np.nan_to_num(a), np.nan_to_num(b)), name
+    v = gls.pointing_weights_trig(c32, s32, 3)
+    assert rel(got["aligned"][1], gls.apply_P(pix, v, x.cpu().numpy().reshape(npix, 3))) < 1e-13
+    for bad in (1.5, np.nan):
+        cb = c32.copy()
+        cb[n // 3] = bad
+        for name, (c, s_) in forms(cb, s32).items():
+            with pytest.raises(L.BrahmapError) as ei:
+                L.bm_pointing_create_trig(ctx, npix, d_pix, c, s_, 3)
+            assert ei.value.status == L.BM_ERR_INVALID and "trig value" in str(ei.value), (bad, name)
+
+
 def test_trig_input_config1_like_solve(L, ctx):
     # The config-1 input format (int32 pix, FP32 cos/sin, FP32 TOD, white
     # noise) on a reduced scan: mixed solve to 1e-8 matches the oracle to 1e-6,
