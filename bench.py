@@ -260,10 +260,7 @@ KERNELS = {"ingest_validate": "validate_kernel", "ingest_hist": "rs_hist_kernel"
            "ingest_scatter": "rs_scatter_kernel", "blocks": "blocks_kernel", "rhs": "gather_reduce_kernel",
            "matvec_white_f32": "white_matvec_f32_kernel"}
 TRAFFIC = {
-    # ncu on the 67M-sample case of the same scan (256 detectors x 262,144
-    # samples): 47.2 and 41.9 DRAM bytes per sample for the two scatter
-    # passes (mean 44.6); the traffic grows in proportion to the samples
-    "ingest_scatter": lambda n: 44.6 * n,
+    "ingest_scatter": None,
 }
 
 
@@ -462,15 +459,17 @@ def run_gb300(args, rank, world, local_rank):
     scatter_bytes = 0
     hist_bytes = 0
     # The timed step passes cos/sin as 16-byte-aligned device arrays: the
-    # first sort pass reads them itself and writes the time-ordered pairs
-    # (8 bytes a sample), and the validation reads and copies the pixels alone.
+    # first sort pass reads them itself and the validation reads and copies
+    # the pixels alone; with the TOD carried, the time-ordered pairs are left
+    # to the first time-ordered operator (none in a white-noise step), else
+    # the first pass writes them (8 bytes a sample).
     for ps in range(passes):
         last = ps == passes - 1
         # keys + records, or pixel keys + cos + sin (+ TOD) in time order
         rd = (kb + 16) if ps > 0 else (4 + (12 if carried else 8))
         # perm + trig (+ TOD) of kept samples, or records + keys
         wr = ((16 if carried else 12) * n_valid / nt) if last else 16 + kb
-        if ps == 0:
+        if ps == 0 and not carried:
             wr += 8                                        # the time-ordered trig pairs
         scatter_bytes += (rd + wr) * nt
         if ps > 0:                                         # (the first pass's counts come from validation)

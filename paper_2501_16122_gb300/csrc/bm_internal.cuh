@@ -195,7 +195,9 @@ struct bm_pointing {
     int64_t npix = 0, nsamples = 0, nvalid = 0;
     int ncomp = 3;
     bm::DevBuf<int32_t> pix;       // [nsamples] time order, -1 = flagged
-    bm::DevBuf<float2> cs_hi_t;    // [nsamples] (cos 2psi, sin 2psi) rounded to FP32
+    bm::DevBuf<float2> cs_hi_t;    // [nsamples] (cos 2psi, sin 2psi) rounded to FP32; read through
+                                   //   bm::time_trig, which builds it on first use when deferred
+    bool trig_t_deferred = false;  // cs_hi_t not built yet (a pointing carrying a TOD, given cos/sin)
     bm::DevBuf<float2> cs_lo_t;    // [nsamples] FP64 value minus hi, rounded to FP32
     bm::DevBuf<uint32_t> perm;     // [nvalid] sample index, pixel-sorted (stable)
     bm::DevBuf<int64_t> off;       // [npix + 1] CSR offsets into perm
@@ -371,6 +373,10 @@ void shard_reduce(bm_context* ctx, double* buf, int64_t count);
 double* static_scratch_setup();
 
 // Launch wrappers implemented in the .cu files.
+// The time-ordered trig pairs of p (cs_hi_t), built from the pixel-sorted
+// pairs on the first call when the ingest deferred them (flagged samples
+// get (0, 0)); an error inside a stream capture, where it cannot allocate.
+const float2* time_trig(bm_pointing* p);
 void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dtype, const float* cos2psi,
             const float* sin2psi, const float* tod = nullptr, bool tod_on_host = false,
             const HwpModel* hwp = nullptr);

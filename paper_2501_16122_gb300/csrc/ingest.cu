@@ -330,7 +330,7 @@ struct ScatterArgs {
     const float2* hi_in;      // first pass: the trig pairs in time order; or, with c_in and s_in,
     const float* c_in;        //   the caller's cos 2psi and sin 2psi (16-byte aligned), which the
     const float* s_in;        //   pass checks (|.| <= 1) and writes as pairs to hi_t_out in time order
-    float2* hi_t_out;
+    float2* hi_t_out;         //   (null: the time-ordered pairs are deferred)
     unsigned long long* bad;  //   (samples with a bad pair are counted here)
     const float* tod_in;      // first pass: the TOD in time order, or null
     const float2* lo_in;      // lo halves of the trig pairs in this pass's input order, or null
@@ -606,17 +606,12 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
         __syncthreads();
         // the tables are done with: the window's second part can come in
         if (!FIRST && threadIdx.x == 0) issue_win2(base, cnt);
-        // given cos/sin (TRIG2): the tile's time-ordered pairs, checked and
-        // written while the digits are counted and staged, phases that leave
-        // the store path idle (in the write-out these stores measured 3k
-        // cycles a tile)
-        if (TRIG2) {
+        // given cos/sin (TRIG2) and not deferred: the tile's time-ordered
+        // pairs, written while the digits are counted and staged (in the
+        // write-out these stores measured 3k cycles a tile)
+        if (TRIG2 && a.hi_t_out) {
             if (give_up(!mbar_wait(&bar[1], parity), parity, parity, true)) return;
-            for (int j = threadIdx.x; j < cnt; j += SC_THREADS) {
-                const float cj = s_c[j], sj = s_s[j];
-                __stcs(a.hi_t_out + base + j, make_float2(cj, sj));
-                nbad += !(fabsf(cj) <= 1.0f && fabsf(sj) <= 1.0f);  // NaN counts
-            }
+            for (int j = threadIdx.x; j < cnt; j += SC_THREADS) __stcs(a.hi_t_out + base + j, make_float2(s_c[j], s_s[j]));
         }
         // 3. per digit: the tile count (the warps' counts summed), the scan
         //    over digits, then each warp's start of each digit in the tile
@@ -692,6 +687,7 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
                 rr = s_rec[src];
             } else {
                 const float2 h = TRIG2 ? make_float2(s_c[src], s_s[src]) : s_hi[src];
+                if (TRIG2) nbad += !(fabsf(h.x) <= 1.0f && fabsf(h.y) <= 1.0f);  // each sample once; NaN counts
                 const float dv = a.tod_in ? s_tod[src] : 0.f;
                 rr = make_uint4(__float_as_uint(dv), (uint32_t)(base + src), __float_as_uint(h.x), __float_as_uint(h.y));
             }
@@ -824,8 +820,14 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
     const SortPlan sp = plan_sort(ctx, n, npix);
     const int threads = 256;
 
+    // A pointing that carries a TOD is made for white-noise solves, which
+    // read only the pixel-sorted pairs: given cos/sin, its time-ordered pairs
+    // (8 bytes a sample) are built from the sorted ones by the first
+    // time-ordered operator that needs them (time_trig).
+    const bool defer_t = trig2 && tod != nullptr;
     p->pix.alloc(n);
-    p->cs_hi_t.alloc(n);
+    if (!defer_t) p->cs_hi_t.alloc(n);
+    p->trig_t_deferred = defer_t;
     if (has_lo) p->cs_lo_t.alloc(n);
     DevBuf<float> tod_copy;  // a host TOD, copied by the validation pass
     if (tod && tod_on_host) tod_copy.alloc(n);
@@ -910,7 +912,7 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
         if (pass_trig2) {
             a.c_in = cos2psi;
             a.s_in = sin2psi;
-            a.hi_t_out = p->cs_hi_t.get();
+            a.hi_t_out = defer_t ? nullptr : p->cs_hi_t.get();
             a.bad = counters.get() + 3;
         }
         a.tod_in = pass == 0 ? tod_t : nullptr;
@@ -962,6 +964,36 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
     }
     BM_REQUIRE(h_err[1] == 0, "%llu samples have a pixel index outside [-1, %lld) or a bad angle / trig value",
                h_err[1], (long long)npix);
+}
+
+namespace {
+__global__ void time_trig_kernel(const uint32_t* __restrict__ perm, const float2* __restrict__ hi_s, int64_t nvalid,
+                                 float2* __restrict__ hi_t) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvalid; i += (int64_t)gridDim.x * blockDim.x)
+        hi_t[perm[i]] = hi_s[i];
+}
+}  // namespace
+
+const float2* time_trig(bm_pointing* p) {
+    if (p->trig_t_deferred) {
+        bm_context* ctx = p->ctx;
+        cudaStream_t s = ctx->stream;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        BM_CUDA(cudaStreamIsCapturing(s, &cs));
+        BM_REQUIRE(cs == cudaStreamCaptureStatusNone,
+                   "the time-ordered trig pairs of a pointing that carries a TOD are built on first use, "
+                   "which a stream capture cannot hold: make one time-ordered call before capturing");
+        ScopedTimer timer(ctx, "time_trig");
+        p->cs_hi_t.alloc(p->nsamples);
+        BM_CUDA(cudaMemsetAsync(p->cs_hi_t.get(), 0, sizeof(float2) * (size_t)p->nsamples, s));
+        if (p->nvalid > 0) {
+            time_trig_kernel<<<grid_for(ctx, (p->nvalid + 255) / 256, 16), 256, 0, s>>>(p->perm.get(), p->cs_hi_s.get(),
+                                                                                        p->nvalid, p->cs_hi_t.get());
+            BM_LAUNCH_CHECK();
+        }
+        p->trig_t_deferred = false;
+    }
+    return p->cs_hi_t.get();
 }
 
 }  // namespace bm

@@ -1562,8 +1562,9 @@ static void offset_matvec_refine(bm_pointing* p, bm_inv_noise* n, bm_precond* pc
     float2* mwd = workspace_as<float2>(ctx, "ofs_mwd", std::max<int64_t>(n->nint, 1));
     if (n->nint > 0) {
         ScopedTimer timer(ctx, "offset_means_df");
+        const float2* trig_t = time_trig(p);  // built here on first use when deferred
         offset_means_df_kernel<<<resident_grid(ctx, offset_means_df_kernel, 256, (n->nint + 7) / 8), 256, 0, s>>>(
-            p->pix.get(), p->cs_hi_t.get(), p->cs_lo_t.get(), xd, offset_geom(n), pc->ofs_inv.get(), n->white.get(),
+            p->pix.get(), trig_t, p->cs_lo_t.get(), xd, offset_geom(n), pc->ofs_inv.get(), n->white.get(),
             nc, mwd);
         BM_LAUNCH_CHECK();
     }
@@ -1600,8 +1601,9 @@ static void offset_matvec_mixed(bm_pointing* p, bm_inv_noise* n, bm_precond* pc,
     float* mw = workspace_as<float>(ctx, "ofs_mw", std::max<int64_t>(n->nint, 1));
     if (n->nint > 0) {
         ScopedTimer timer(ctx, "offset_means_f32");
+        const float2* trig_t = time_trig(p);  // built here on first use when deferred
         offset_means_f32_kernel<<<resident_grid(ctx, offset_means_f32_kernel, 256, (n->nint + 7) / 8), 256, 0, s>>>(
-            p->pix.get(), p->cs_hi_t.get(), x4, offset_geom(n), pc->ofs_inv.get(), n->white.get(), nc > 1, mw);
+            p->pix.get(), trig_t, x4, offset_geom(n), pc->ofs_inv.get(), n->white.get(), nc > 1, mw);
         BM_LAUNCH_CHECK();
     }
     double* partial = workspace_as<double>(ctx, "partial", (size_t)std::max<int64_t>(pc->nitems, 1) * nc);
@@ -1913,8 +1915,9 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
                         // the FFT filter's load stage instead, its dependent map
                         // gather left the filter latency-bound: 15.8 -> 23.7 ms
                         // at config 2)
+                        const float2* trig_t = time_trig(p);  // built here on first use when deferred
                         pointing_apply_f32_kernel<<<grid_for(ctx, (p->nsamples + threads - 1) / threads, 16),
-                                                    threads, 0, s>>>(p->pix.get(), p->cs_hi_t.get(), p->nsamples,
+                                                    threads, 0, s>>>(p->pix.get(), trig_t, p->nsamples,
                                                                      x4, y32);
                         BM_LAUNCH_CHECK();
                     }
@@ -1937,8 +1940,9 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
                     float2* y2 = workspace_as<float2>(ctx, "y_df", p->nsamples);
                     {
                         ScopedTimer timer_px(ctx, "toeplitz_px_df");
+                        const float2* trig_t = time_trig(p);  // built here on first use when deferred
                         pointing_apply_df_kernel<<<grid_for(ctx, (p->nsamples + threads - 1) / threads, 16),
-                                                   threads, 0, s>>>(p->pix.get(), p->cs_hi_t.get(),
+                                                   threads, 0, s>>>(p->pix.get(), trig_t,
                                                                     p->cs_lo_t.get(), p->nsamples, x2, y2);
                         BM_LAUNCH_CHECK();
                     }
@@ -1956,8 +1960,9 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
                 {
                     ScopedTimer timer(ctx, "toeplitz_f64");
                     double* y64 = workspace_as<double>(ctx, "y64", p->nsamples);
+                    const float2* trig_t = time_trig(p);  // built here on first use when deferred
                     pointing_apply_kernel<<<grid_for(ctx, (p->nsamples + threads - 1) / threads, 16), threads, 0, s>>>(
-                        p->pix.get(), p->cs_hi_t.get(), p->cs_lo_t.get(), p->nsamples, nc, xm, y64);
+                        p->pix.get(), trig_t, p->cs_lo_t.get(), p->nsamples, nc, xm, y64);
                     BM_LAUNCH_CHECK();
                     apply_filter_f64(n, pc, SrcPlain{y64}, z64);
                 }
@@ -2041,8 +2046,9 @@ void rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dt
 void pointing_apply(bm_pointing* p, const double* x, double* y) {
     bm_context* ctx = p->ctx;
     const int threads = 256;
+    const float2* trig_t = time_trig(p);  // built here on first use when deferred
     pointing_apply_kernel<<<grid_for(ctx, (p->nsamples + threads - 1) / threads, 16), threads, 0, ctx->stream>>>(
-        p->pix.get(), p->cs_hi_t.get(), p->cs_lo_t.get(), p->nsamples, p->ncomp, x, y);
+        p->pix.get(), trig_t, p->cs_lo_t.get(), p->nsamples, p->ncomp, x, y);
     BM_LAUNCH_CHECK();
 }
 

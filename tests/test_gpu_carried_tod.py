@@ -117,6 +117,54 @@ def test_carried_tod_solve(L, ctx, prec, host):
         c.close()
 
 
+def test_carried_tod_pointing_with_time_ordered_operators(L, ctx):
+    """A pointing that carries a TOD, given cos/sin in device memory, builds
+    its time-ordered trig pairs only when a time-ordered operator first
+    needs them: with Toeplitz noise its matvecs (FP64 and mixed), its P x and
+    its refined solve are bitwise those of the same pointing made without the
+    TOD (whose first sort pass writes the pairs at creation)."""
+    c = Case(L, ctx, 16, 4, 40_000, 4321, noise="toeplitz", chunk=4096, nlags=64, flag=0.01, trig=True,
+             tod_dtype=np.float32, build_oracle=False)
+    try:
+        c32, s32 = c.trig
+        p1 = L.bm_pointing_create_with_tod(ctx, c.npix, c.d_pix, c.d_tod, cos2psi=torch.from_numpy(c32).cuda(),
+                                           sin2psi=torch.from_numpy(s32).cuda())
+        pc1 = L.bm_blockdiag_precond_create(p1, c.n, 3, 1e3)
+        try:
+            x = c.vec(np.random.default_rng(5).normal(size=(c.npix, 3)))
+            y0 = torch.zeros(c.e.nsamples, dtype=torch.float64, device="cuda")
+            y1 = torch.zeros_like(y0)
+            L.bm_pointing_apply(p1, x, y1)  # the first time-ordered call builds the pairs
+            L.bm_pointing_apply(c.p, x, y0)
+            assert torch.equal(y0, y1)
+            for prec in (L.BM_PREC_FP64, L.BM_PREC_MIXED):
+                q0, q1 = c.vec(), c.vec()
+                L.bm_matvec(c.p, c.n, c.pc, x, q0, prec)
+                L.bm_matvec(p1, c.n, pc1, x, q1, prec)
+                assert torch.equal(torch.nan_to_num(q0), torch.nan_to_num(q1)), prec
+            m0, m1 = c.vec(), c.vec()
+            st0, _ = L.bm_pcg_solve(c.p, c.n, c.pc, c.d_tod, 1, m0, 1e-8, 300, L.BM_PREC_MIXED)
+            st1, _ = L.bm_pcg_solve(p1, c.n, pc1, c.d_tod, 1, m1, 1e-8, 300, L.BM_PREC_MIXED)
+            assert st0 == st1 == L.BM_OK
+            assert torch.equal(torch.nan_to_num(m0, 7.0), torch.nan_to_num(m1, 7.0))
+        finally:
+            L.bm_precond_destroy(pc1)
+            L.bm_pointing_destroy(p1)
+        # a fresh carried pointing whose first time-ordered operator is the solve
+        p2 = L.bm_pointing_create_with_tod(ctx, c.npix, c.d_pix, c.d_tod, cos2psi=torch.from_numpy(c32).cuda(),
+                                           sin2psi=torch.from_numpy(s32).cuda())
+        pc2 = L.bm_blockdiag_precond_create(p2, c.n, 3, 1e3)
+        try:
+            m2 = c.vec()
+            st2, _ = L.bm_pcg_solve(p2, c.n, pc2, c.d_tod, 1, m2, 1e-8, 300, L.BM_PREC_MIXED)
+            assert st2 == L.BM_OK and torch.equal(torch.nan_to_num(m0, 7.0), torch.nan_to_num(m2, 7.0))
+        finally:
+            L.bm_precond_destroy(pc2)
+            L.bm_pointing_destroy(p2)
+    finally:
+        c.close()
+
+
 def test_carried_tod_errors(L, ctx):
     c = Case(L, ctx, 8, 2, 5_000, 31, noise="toeplitz", chunk=1000, nlags=8, tod_dtype=np.float32,
              build_oracle=False)
