@@ -613,11 +613,11 @@ __device__ __forceinline__ df32 df_warp_sum(df32 a) {
 // error plus the cross terms.  acc_add adds p to the accumulator's leading
 // part exactly (two_sum) and the rounding error and e to its trailing part;
 // acc_norm (every kLazyNorm terms of a lane, and before the lanes are
-// combined) renormalises the pair.  The trailing part then stays within a
-// few units of the leading part's last place: about a third fewer
-// instructions than a normalised double-float product and sum per term, at
-// an error of a few 2^-48 per term.
-constexpr int kLazyNorm = 4;
+// combined) renormalises the pair.  The trailing part then stays within
+// about kLazyNorm units of the leading part's last place: about a third
+// fewer instructions than a normalised double-float product and sum per
+// term, at an error of a few 2^-48 per term.
+constexpr int kLazyNorm = 8;
 __device__ __forceinline__ void prod_u(float hi, float lo, float b, float& p, float& e) {
     p = __fmul_rn(hi, b);
     e = __fmaf_rn(lo, b, __fmaf_rn(hi, b, -p));

@@ -50,6 +50,7 @@ constexpr int IG_TILE = IG_THREADS * IG_PER_THREAD;  // 4096 samples
 constexpr int SC_THREADS = 512;
 constexpr int SC_WARPS = SC_THREADS / 32;
 constexpr int SC_TILE = SC_THREADS * IG_PER_THREAD;
+static_assert(SC_TILE <= 8192, "the last pass packs a tile position into 13 bits");
 constexpr int SC_MIN_BLOCKS = SC_THREADS == 256 ? 2 : 1;  // blocks per SM the shared memory allows
 constexpr int IG_WARP_SPAN = 512;                          // consecutive samples per warp in a tile
 constexpr int RS_MAX_BITS = 10;
@@ -96,7 +97,8 @@ __device__ __forceinline__ void st_keep(float2* p, float2 v, uint64_t pol) {
 // MODE: kTrigIn (cos/sin given), kPsi64 or kPsi32 (angles given), kHwp
 // (the half-wave-plate model), or kPixOnly (cos/sin given and left to the
 // first sort pass, which reads them once, checks them and writes the
-// time-ordered pairs: this pass then reads and copies the pixels alone).
+// time-ordered pairs or leaves them to time_trig: this pass then reads and
+// copies the pixels alone).
 // HIST: also the first sort pass's digit counts (the sort key of each
 // validated sample, flagged ones as npix, masked to the low digit) of each
 // range of `range` samples, hist[d * G + range], as rs_hist_kernel counts
@@ -658,8 +660,12 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
         for (int r = 0; r < IG_PER_THREAD; ++r) {
             const int j = w * IG_WARP_SPAN + r * 32 + lane;
             if (j < cnt) {
-                s_stk[rank[r]] = key[r];
-                s_src[rank[r]] = (uint16_t)j;
+                if (LAST) {  // the last pass needs only the digit: digit and position in one word
+                    s_stk[rank[r]] = ((key[r] & dmask) << 13) | (uint32_t)j;
+                } else {
+                    s_stk[rank[r]] = key[r];
+                    s_src[rank[r]] = (uint16_t)j;
+                }
             }
         }
         // a TOD that is not bulk-copied (off a 16-byte boundary, or the
@@ -679,8 +685,8 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
         //    each sample from the window in shared memory
         for (int j = threadIdx.x; j < cnt; j += SC_THREADS) {
             const uint32_t k = s_stk[j];
-            const uint32_t src = s_src[j];
-            const uint32_t d = k & dmask;
+            const uint32_t src = LAST ? (k & 8191u) : s_src[j];
+            const uint32_t d = LAST ? (k >> 13) : (k & dmask);
             const uint32_t g = run_base[d] + (uint32_t)j;
             uint4 rr;
             if (!FIRST) {

@@ -179,7 +179,7 @@ blocks_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ 
         // the lane's samples are still added in order
         constexpr int kUnroll = 4;
         // the lazy sums are renormalised after every kLazyNorm samples of the
-        // lane (kUnroll == kLazyNorm: at the end of each group) and at the end
+        // lane (at the end of every kLazyNorm / kUnroll groups) and at the end
         auto norm = [&]() {
             if (EXACT) {
 #pragma unroll
@@ -190,7 +190,7 @@ blocks_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ 
                 for (int j = 0; j < NC; ++j) acc_norm(racc[j]);
             }
         };
-        static_assert(kUnroll == kLazyNorm, "groups end on renormalisation points");
+        static_assert(kLazyNorm % kUnroll == 0, "renormalisation points fall at group ends");
         int nadd = 0;
         int i = lane;
         for (; i + 32 * (kUnroll - 1) < len; i += 32 * kUnroll) {
@@ -207,7 +207,11 @@ blocks_kernel(const int32_t* __restrict__ item_pix, const int64_t* __restrict__ 
             }
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) add(b + i + 32 * u, t[u], h[u], l[u], dv[u]);
-            norm();
+            nadd += kUnroll;
+            if (nadd == kLazyNorm) {
+                nadd = 0;
+                norm();
+            }
         }
         for (; i < len; i += 32) {
             const int64_t si = b + i;
