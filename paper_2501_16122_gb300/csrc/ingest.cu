@@ -425,13 +425,14 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
     uint16_t* tstart = tcnt + a.bins;                                       // tile-local start per digit
     __shared__ uint32_t wtot[SC_WARPS];
     __shared__ __align__(8) uint64_t bar[3];  // [0] keys, [1] window: first part, [2] window: second part
-    // lane-mask tables of the ranking, 4 KB a warp: in the window's second
-    // half (records of the tile's second half), which is copied in after the
-    // ranking; on the first pass, whose window (trig pairs and TOD values)
-    // leaves the last quarter free, in that quarter and the keys' buffer
-    // (the keys are in registers by then), so the whole window is copied in
-    // while the previous tile is written out
-    uint32_t* s_tbl = reinterpret_cast<uint32_t*>(smem + (FIRST ? 12 : 8) * SC_TILE);
+    // lane-mask tables of the ranking, outside the payload window, so that
+    // the whole window of the next tile is copied in while the current one
+    // is written out: on the first pass, whose window (trig pairs and TOD
+    // values) leaves its last quarter free, 4 KB a warp in that quarter and
+    // the keys' buffer (the keys are in registers by then); on later passes,
+    // whose records fill the window, 2 KB a warp in the keys' buffer alone
+    constexpr int kTblEntries = FIRST ? 512 : 256;  // entries of each of a warp's two tables
+    uint32_t* s_tbl = reinterpret_cast<uint32_t*>(smem + (FIRST ? 12 : 16) * SC_TILE);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     const int bins = a.bins;
@@ -468,7 +469,7 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
         if (kbytes) bulk_g2s(s_keys, keys_in + base, kbytes, &bar[0]);
     };
     // the window's first part: records of the tile's first half, or the
-    // trig pairs
+    // trig pairs (or cos and sin)
     auto issue_win1 = [&](int64_t base, int cnt) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         if (!FIRST) {
@@ -488,8 +489,7 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
             if (hbytes) bulk_g2s(s_hi, a.hi_in + base, hbytes, &bar[1]);
         }
     };
-    // the second part, over the ranking tables: records of the second half,
-    // or the TOD values
+    // the second part: records of the second half, or the TOD values
     auto issue_win2 = [&](int64_t base, int cnt) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         if (!FIRST) {
@@ -519,7 +519,7 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
     if (threadIdx.x == 0 && begin < end) {
         issue_keys(begin, (int)(end - begin < SC_TILE ? end - begin : SC_TILE));
         issue_win1(begin, (int)(end - begin < SC_TILE ? end - begin : SC_TILE));
-        if (FIRST) issue_win2(begin, (int)(end - begin < SC_TILE ? end - begin : SC_TILE));
+        issue_win2(begin, (int)(end - begin < SC_TILE ? end - begin : SC_TILE));
     }
     uint32_t parity = 0;
     uint32_t nbad = 0;
@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
                 s_c[j] = a.c_in[base + j];
                 s_s[j] = a.s_in[base + j];
             }
-        if (give_up(!mbar_wait(&bar[0], parity), parity, parity, FIRST)) return;
+        if (give_up(!mbar_wait(&bar[0], parity), parity, parity, true)) return;
         __syncthreads();  // the plain-loaded keys too
         uint32_t key[IG_PER_THREAD], rank[IG_PER_THREAD];
         // 1. the warp's 512 consecutive keys, 32 per round
@@ -548,10 +548,10 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
         //    digit's entry and reads the entry back; the lanes clear it
         //    afterwards): a warp-wide match instruction costs ~60 cycles of
         //    the SM here, these shared-memory operations ~2.  Rounds A and B
-        //    (B's samples after A's) have a table each, 512 entries, so both
-        //    fit in 4 KB a warp (the window's second half holds the 16
-        //    warps' tables); with 10-bit digits the tables take the low 9
-        //    bits and a vote on the top bit splits each entry.  Every lane
+        //    (B's samples after A's) have a table each (512 entries on the
+        //    first pass, 256 later: 4 or 2 KB a warp); digits wider than a
+        //    table index it with their low bits and a vote on each higher
+        //    bit splits the entries.  Every lane
         //    reads its digit's warp counter c before the pair: a sample of A
         //    ranks at c + (A lanes below it with its digit), one of B at c +
         //    (A lanes with its digit, read from A's table at B's digit) + (B
@@ -561,18 +561,22 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
         //    rounds took six.  The 16-bit counters are stored as halves (a
         //    warp counts at most 512 samples a digit); two leaders never
         //    store the same counter in one pair.
-        if (FIRST) __syncthreads();  // every warp has its keys before the tables overwrite them
+        __syncthreads();  // every warp has its keys before the tables overwrite them
         {
             uint4* z = reinterpret_cast<uint4*>(s_tbl);
-            for (int i = threadIdx.x; i < SC_TILE / 2; i += SC_THREADS) z[i] = make_uint4(0u, 0u, 0u, 0u);
+            for (int i = threadIdx.x; i < SC_WARPS * 2 * kTblEntries / 4; i += SC_THREADS)
+                z[i] = make_uint4(0u, 0u, 0u, 0u);
         }
         __syncthreads();
         {
             uint16_t* wc = wcnt + w * bins;
-            uint32_t* tA = s_tbl + w * 1024;
-            uint32_t* tB = tA + 512;
-            const bool split = bins > 512;
-            const uint32_t tmask = split ? 511u : dmask;
+            uint32_t* tA = s_tbl + w * 2 * kTblEntries;
+            uint32_t* tB = tA + kTblEntries;
+            // digits wider than a table: a vote on each bit above it splits
+            // the entries (one bit on the first pass, up to two later)
+            constexpr int kB0 = FIRST ? 9 : 8;
+            const int nvote = bins <= kTblEntries ? 0 : (bins <= 2 * kTblEntries ? 1 : 2);
+            const uint32_t tmask = (uint32_t)(bins < kTblEntries ? bins : kTblEntries) - 1u;
             const unsigned me = 1u << lane;
 #pragma unroll
             for (int r = 0; r < IG_PER_THREAD; r += 2) {
@@ -582,18 +586,25 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
                 const uint32_t iA = dA & tmask, iB = dB & tmask;
                 if (vA) atomicOr(tA + iA, me);
                 if (vB) atomicOr(tB + iB, me);
-                const unsigned hA = split ? __ballot_sync(0xffffffffu, vA && (dA & 512u)) : 0u;
-                const unsigned hB = split ? __ballot_sync(0xffffffffu, vB && (dB & 512u)) : 0u;
+                const unsigned hA0 = nvote > 0 ? __ballot_sync(0xffffffffu, vA && ((dA >> kB0) & 1u)) : 0u;
+                const unsigned hB0 = nvote > 0 ? __ballot_sync(0xffffffffu, vB && ((dB >> kB0) & 1u)) : 0u;
+                const unsigned hA1 = nvote > 1 ? __ballot_sync(0xffffffffu, vA && ((dA >> (kB0 + 1)) & 1u)) : 0u;
+                const unsigned hB1 = nvote > 1 ? __ballot_sync(0xffffffffu, vB && ((dB >> (kB0 + 1)) & 1u)) : 0u;
                 __syncwarp();
                 unsigned pA = tA[iA], pB = tB[iB];
                 unsigned xAB = tA[iB], xBA = tB[iA];  // A lanes on B's entry, B lanes on A's entry
                 const uint32_t cA = wc[dA], cB = wc[dB];
                 __syncwarp();
-                if (split) {
-                    pA &= (dA & 512u) ? hA : ~hA;
-                    xAB &= (dB & 512u) ? hA : ~hA;
-                    pB &= (dB & 512u) ? hB : ~hB;
-                    xBA &= (dA & 512u) ? hB : ~hB;
+                if (nvote > 0) {  // keep the lanes whose bits above the table match the digit's
+                    auto filt = [&](uint32_t d, unsigned h0, unsigned h1) {
+                        unsigned f = ((d >> kB0) & 1u) ? h0 : ~h0;
+                        if (nvote > 1) f &= ((d >> (kB0 + 1)) & 1u) ? h1 : ~h1;
+                        return f;
+                    };
+                    pA &= filt(dA, hA0, hA1);
+                    xAB &= filt(dB, hA0, hA1);
+                    pB &= filt(dB, hB0, hB1);
+                    xBA &= filt(dA, hB0, hB1);
                 }
                 if (vA) tA[iA] = 0u;
                 if (vB) tB[iB] = 0u;
@@ -606,8 +617,6 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
             }
         }
         __syncthreads();
-        // the tables are done with: the window's second part can come in
-        if (!FIRST && threadIdx.x == 0) issue_win2(base, cnt);
         // given cos/sin (TRIG2) and not deferred: the tile's time-ordered
         // pairs, written while the digits are counted and staged (in the
         // write-out these stores measured 3k cycles a tile)
@@ -718,7 +727,7 @@ __global__ void __launch_bounds__(SC_THREADS, SC_MIN_BLOCKS) rs_scatter_kernel(S
         }
         if (threadIdx.x == 0 && base + SC_TILE < end) {
             issue_win1(base + SC_TILE, (int)(end - base - SC_TILE < SC_TILE ? end - base - SC_TILE : SC_TILE));
-            if (FIRST) issue_win2(base + SC_TILE, (int)(end - base - SC_TILE < SC_TILE ? end - base - SC_TILE : SC_TILE));
+            issue_win2(base + SC_TILE, (int)(end - base - SC_TILE < SC_TILE ? end - base - SC_TILE : SC_TILE));
         }
         __syncthreads();
     }
