@@ -478,7 +478,9 @@ def run_gb300(args, rank, world, local_rank):
         if ps > 0:                                         # (the first pass's counts come from validation)
             hist_bytes += kb * nt                          # keys
     step_bytes = {
-        "ingest_validate": 8 * nt,                        # pix in, pix out (with the first pass's digit counts)
+        # pix in (with the first pass's digit counts); pix out unless the TOD is
+        # carried (then the time-ordered copy waits for a time-ordered operator)
+        "ingest_validate": (4 if carried else 8) * nt,
         "ingest_hist": hist_bytes,
         "ingest_scatter": scatter_bytes,
         # perm + trig pair (+ the carried TOD, whose RHS this pass also sums) in, weighted pair out

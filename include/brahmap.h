@@ -205,9 +205,10 @@ bm_status bm_pointing_create_trig(bm_context* ctx, int64_t npix, int64_t nsample
  * caller's array may be freed on return.  The carried TOD serves one
  * right-hand side of a white-noise system (a Toeplitz N^-1 filters in time
  * order).  With the trig pair in 16-byte-aligned device memory the handle
- * keeps only the pixel-sorted pairs at first; the first time-ordered
- * operator (bm_pointing_apply, a Toeplitz or offset-template matvec or
- * solve) builds the time-ordered ones from them (8 bytes a sample, memory
+ * keeps only the pixel-sorted pairs at first (and, with pix there too, no
+ * time-ordered pixel copy); the first time-ordered operator
+ * (bm_pointing_apply, a Toeplitz or offset-template matvec or solve) builds
+ * the time-ordered ones from the sorted order (8 + 4 bytes a sample, memory
  * allocated then; that call must not be inside a stream capture, else
  * BM_ERR_INVALID).  This entry point has no counterpart in the paper.  Errors as
  * bm_pointing_create; BM_ERR_INVALID when both or neither of psi and the trig

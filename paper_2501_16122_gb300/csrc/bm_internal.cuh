@@ -194,7 +194,9 @@ struct bm_pointing {
     bm_context* ctx = nullptr;
     int64_t npix = 0, nsamples = 0, nvalid = 0;
     int ncomp = 3;
-    bm::DevBuf<int32_t> pix;       // [nsamples] time order, -1 = flagged
+    bm::DevBuf<int32_t> pix;       // [nsamples] time order, -1 = flagged; read through bm::time_pix,
+                                   //   which builds it on first use when deferred
+    bool pix_deferred = false;     // pix not built yet (a pointing carrying a TOD, pixels in device memory)
     bm::DevBuf<float2> cs_hi_t;    // [nsamples] (cos 2psi, sin 2psi) rounded to FP32; read through
                                    //   bm::time_trig, which builds it on first use when deferred
     bool trig_t_deferred = false;  // cs_hi_t not built yet (a pointing carrying a TOD, given cos/sin)
@@ -377,6 +379,11 @@ double* static_scratch_setup();
 // pairs on the first call when the ingest deferred them (flagged samples
 // get (0, 0)); an error inside a stream capture, where it cannot allocate.
 const float2* time_trig(bm_pointing* p);
+// The time-ordered pixel indices of p (-1 = flagged), built from the CSR
+// offsets and perm on the first call when the ingest deferred them (a lazily
+// filled part of the handle, hence the const argument); an error inside a
+// stream capture.
+const int32_t* time_pix(const bm_pointing* p);
 void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dtype, const float* cos2psi,
             const float* sin2psi, const float* tod = nullptr, bool tod_on_host = false,
             const HwpModel* hwp = nullptr);

@@ -153,7 +153,7 @@ validate_kernel(const int32_t* __restrict__ pix, const void* __restrict__ psi,
         const bool kept = ok_p && p >= 0;
         nbad += (!ok_p) + (!ok_a);
         nflag += !kept;
-        pix_out[i] = ok_p ? p : -1;
+        if (pix_out) pix_out[i] = ok_p ? p : -1;  // (null: the copy is deferred)
         if (HIST) atomicAdd(&mine[(kept ? (uint32_t)p : (uint32_t)npix) & dmask], 1u);
     };
     // four samples per thread and pass, their loads issued together
@@ -840,9 +840,14 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
     // (8 bytes a sample) are built from the sorted ones by the first
     // time-ordered operator that needs them (time_trig).
     const bool defer_t = trig2 && tod != nullptr;
-    p->pix.alloc(n);
+    // likewise its time-ordered pixel copy, when the caller's pixels are in
+    // device memory at a 16-byte boundary: the first sort pass and the CSR
+    // offsets read them there, and time_pix builds the copy on first use
+    const bool defer_pix = defer_t && (reinterpret_cast<uintptr_t>(pix) & 15u) == 0 && in_device_memory(pix);
+    if (!defer_pix) p->pix.alloc(n);
     if (!defer_t) p->cs_hi_t.alloc(n);
     p->trig_t_deferred = defer_t;
+    p->pix_deferred = defer_pix;
     if (has_lo) p->cs_lo_t.alloc(n);
     DevBuf<float> tod_copy;  // a host TOD, copied by the validation pass
     if (tod && tod_on_host) tod_copy.alloc(n);
@@ -862,7 +867,7 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
                                : (psi_dtype == BM_F64 ? validate_kernel<kPsi64, true> : validate_kernel<kPsi32, true>);
         constexpr int kSub = 2;  // two blocks a range: eight resident blocks per SM
         kern<<<sp.grid * kSub, IG_THREADS, sizeof(uint32_t) * kVHist * sp.bins, s>>>(
-            pix, psi, cos2psi, sin2psi, n, npix, p->pix.get(), p->cs_hi_t.get(), p->cs_lo_t.get(),
+            pix, psi, cos2psi, sin2psi, n, npix, defer_pix ? nullptr : p->pix.get(), p->cs_hi_t.get(), p->cs_lo_t.get(),
             tod_on_host ? tod : nullptr, tod_copy.get(), counters.get(), sp.range, kSub, sp.bins, sp.grid,
             hist.get(), hwp ? *hwp : HwpModel{});
         BM_LAUNCH_CHECK();
@@ -899,7 +904,8 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
         if (has_lo) lo_b = workspace_as<float2>(ctx, "ingest_lo_b", n);
     }
     // the first pass reads its keys from the validated pixel indices
-    const void* kin = p->pix.get();
+    const int32_t* pix_keys = defer_pix ? pix : p->pix.get();  // validated: every index in [-1, npix)
+    const void* kin = pix_keys;
     void* kout = keys_a;
     const size_t smem = scatter_smem(sp.bins);
     const uint4* rin = nullptr;  // the first pass reads keys, indices and trig in time order
@@ -966,7 +972,7 @@ void ingest(bm_pointing* p, const int32_t* pix, const void* psi, bm_dtype psi_dt
     p->off.alloc(npix + 1);
     p->hits.alloc(npix);
     const int pgrid = grid_for(ctx, (npix + 1 + threads - 1) / threads, 16);
-    lower_bound_kernel<<<pgrid, threads, 0, s>>>(p->perm.get(), p->pix.get(), nvalid, npix, p->off.get());
+    lower_bound_kernel<<<pgrid, threads, 0, s>>>(p->perm.get(), pix_keys, nvalid, npix, p->off.get());
     BM_LAUNCH_CHECK();
     hits_kernel<<<pgrid, threads, 0, s>>>(p->off.get(), npix, p->hits.get());
     BM_LAUNCH_CHECK();
@@ -988,6 +994,36 @@ __global__ void time_trig_kernel(const uint32_t* __restrict__ perm, const float2
         hi_t[perm[i]] = hi_s[i];
 }
 }  // namespace
+
+namespace {
+// pix_t[perm[i]] = q for every sorted position i of pixel q (one thread a pixel)
+__global__ void time_pix_kernel(const int64_t* __restrict__ off, const uint32_t* __restrict__ perm, int64_t npix,
+                                int32_t* __restrict__ pix_t) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < npix; q += (int64_t)gridDim.x * blockDim.x)
+        for (int64_t i = off[q]; i < off[q + 1]; ++i) pix_t[perm[i]] = (int32_t)q;
+}
+}  // namespace
+
+const int32_t* time_pix(const bm_pointing* pc) {
+    bm_pointing* p = const_cast<bm_pointing*>(pc);  // a lazily filled part of the handle
+    if (p->pix_deferred) {
+        bm_context* ctx = p->ctx;
+        cudaStream_t s = ctx->stream;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        BM_CUDA(cudaStreamIsCapturing(s, &cs));
+        BM_REQUIRE(cs == cudaStreamCaptureStatusNone,
+                   "the time-ordered pixels of a pointing that carries a TOD are built on first use, "
+                   "which a stream capture cannot hold: make one time-ordered call before capturing");
+        ScopedTimer timer(ctx, "time_pix");
+        p->pix.alloc(p->nsamples);
+        BM_CUDA(cudaMemsetAsync(p->pix.get(), 0xFF, sizeof(int32_t) * (size_t)p->nsamples, s));  // -1: flagged
+        time_pix_kernel<<<grid_for(ctx, (p->npix + 255) / 256, 16), 256, 0, s>>>(p->off.get(), p->perm.get(), p->npix,
+                                                                                 p->pix.get());
+        BM_LAUNCH_CHECK();
+        p->pix_deferred = false;
+    }
+    return p->pix.get();
+}
 
 const float2* time_trig(bm_pointing* p) {
     if (p->trig_t_deferred) {

@@ -1538,8 +1538,9 @@ void build_offset_counts(bm_precond* pc) {
     pc->ofs_inv.alloc(std::max<int64_t>(n->nint, 1));
     pc->ofs_isort.alloc(std::max<int64_t>(p->nvalid, 1));
     if (n->nint == 0) return;
+    const int32_t* pix_t = time_pix(p);  // built here on first use when deferred
     offset_counts_kernel<<<resident_grid(ctx, offset_counts_kernel, 256, (n->nint + 7) / 8), 256, 0, ctx->stream>>>(
-        p->pix.get(), pc->mask.get(), offset_geom(n), pc->ofs_inv.get());
+        pix_t, pc->mask.get(), offset_geom(n), pc->ofs_inv.get());
     BM_LAUNCH_CHECK();
     if (p->nvalid > 0) {
         offset_isort_kernel<<<grid_for(ctx, (p->nvalid + 255) / 256, 16), 256, 0, ctx->stream>>>(
@@ -1563,8 +1564,9 @@ static void offset_matvec_refine(bm_pointing* p, bm_inv_noise* n, bm_precond* pc
     if (n->nint > 0) {
         ScopedTimer timer(ctx, "offset_means_df");
         const float2* trig_t = time_trig(p);  // built here on first use when deferred
+        const int32_t* pix_t = time_pix(p);  // built here on first use when deferred
         offset_means_df_kernel<<<resident_grid(ctx, offset_means_df_kernel, 256, (n->nint + 7) / 8), 256, 0, s>>>(
-            p->pix.get(), trig_t, p->cs_lo_t.get(), xd, offset_geom(n), pc->ofs_inv.get(), n->white.get(),
+            pix_t, trig_t, p->cs_lo_t.get(), xd, offset_geom(n), pc->ofs_inv.get(), n->white.get(),
             nc, mwd);
         BM_LAUNCH_CHECK();
     }
@@ -1602,8 +1604,9 @@ static void offset_matvec_mixed(bm_pointing* p, bm_inv_noise* n, bm_precond* pc,
     if (n->nint > 0) {
         ScopedTimer timer(ctx, "offset_means_f32");
         const float2* trig_t = time_trig(p);  // built here on first use when deferred
+        const int32_t* pix_t = time_pix(p);  // built here on first use when deferred
         offset_means_f32_kernel<<<resident_grid(ctx, offset_means_f32_kernel, 256, (n->nint + 7) / 8), 256, 0, s>>>(
-            p->pix.get(), trig_t, x4, offset_geom(n), pc->ofs_inv.get(), n->white.get(), nc > 1, mw);
+            pix_t, trig_t, x4, offset_geom(n), pc->ofs_inv.get(), n->white.get(), nc > 1, mw);
         BM_LAUNCH_CHECK();
     }
     double* partial = workspace_as<double>(ctx, "partial", (size_t)std::max<int64_t>(pc->nitems, 1) * nc);
@@ -1916,8 +1919,9 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
                         // gather left the filter latency-bound: 15.8 -> 23.7 ms
                         // at config 2)
                         const float2* trig_t = time_trig(p);  // built here on first use when deferred
+                        const int32_t* pix_t = time_pix(p);  // built here on first use when deferred
                         pointing_apply_f32_kernel<<<grid_for(ctx, (p->nsamples + threads - 1) / threads, 16),
-                                                    threads, 0, s>>>(p->pix.get(), trig_t, p->nsamples,
+                                                    threads, 0, s>>>(pix_t, trig_t, p->nsamples,
                                                                      x4, y32);
                         BM_LAUNCH_CHECK();
                     }
@@ -1941,8 +1945,9 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
                     {
                         ScopedTimer timer_px(ctx, "toeplitz_px_df");
                         const float2* trig_t = time_trig(p);  // built here on first use when deferred
+                        const int32_t* pix_t = time_pix(p);  // built here on first use when deferred
                         pointing_apply_df_kernel<<<grid_for(ctx, (p->nsamples + threads - 1) / threads, 16),
-                                                   threads, 0, s>>>(p->pix.get(), trig_t,
+                                                   threads, 0, s>>>(pix_t, trig_t,
                                                                     p->cs_lo_t.get(), p->nsamples, x2, y2);
                         BM_LAUNCH_CHECK();
                     }
@@ -1961,8 +1966,9 @@ void matvec(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const double* x, do
                     ScopedTimer timer(ctx, "toeplitz_f64");
                     double* y64 = workspace_as<double>(ctx, "y64", p->nsamples);
                     const float2* trig_t = time_trig(p);  // built here on first use when deferred
+                    const int32_t* pix_t = time_pix(p);  // built here on first use when deferred
                     pointing_apply_kernel<<<grid_for(ctx, (p->nsamples + threads - 1) / threads, 16), threads, 0, s>>>(
-                        p->pix.get(), trig_t, p->cs_lo_t.get(), p->nsamples, nc, xm, y64);
+                        pix_t, trig_t, p->cs_lo_t.get(), p->nsamples, nc, xm, y64);
                     BM_LAUNCH_CHECK();
                     apply_filter_f64(n, pc, SrcPlain{y64}, z64);
                 }
@@ -2000,11 +2006,11 @@ void rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dt
             // the offset template's double-float RHS: z as double-float pairs
             float2* z2 = workspace_as<float2>(ctx, "z2", p->nsamples);
             if (dt == BM_F32) {
-                SrcMaskedTod<float> src{p->pix.get(), pc->mask.get(),
+                SrcMaskedTod<float> src{time_pix(p), pc->mask.get(),
                                         static_cast<const float*>(tod) + r * p->nsamples};
                 run_offset_filter<double, SrcMaskedTod<float>, float2>(n, src, pc->ofs_inv.get(), z2);
             } else {
-                SrcMaskedTod<double> src{p->pix.get(), pc->mask.get(),
+                SrcMaskedTod<double> src{time_pix(p), pc->mask.get(),
                                          static_cast<const double*>(tod) + r * p->nsamples};
                 run_offset_filter<double, SrcMaskedTod<double>, float2>(n, src, pc->ofs_inv.get(), z2);
             }
@@ -2016,12 +2022,13 @@ void rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dt
             float2* y2 = workspace_as<float2>(ctx, "y_df", p->nsamples);
             const int tthreads = 256;
             const int tgrid = grid_for(ctx, (p->nsamples + tthreads - 1) / tthreads, 16);
+            const int32_t* pix_t = time_pix(p);  // built here on first use when deferred
             if (dt == BM_F32)
                 masked_tod_df_kernel<float><<<tgrid, tthreads, 0, ctx->stream>>>(
-                    p->pix.get(), pc->mask.get(), static_cast<const float*>(tod) + r * p->nsamples, p->nsamples, y2);
+                    pix_t, pc->mask.get(), static_cast<const float*>(tod) + r * p->nsamples, p->nsamples, y2);
             else
                 masked_tod_df_kernel<double><<<tgrid, tthreads, 0, ctx->stream>>>(
-                    p->pix.get(), pc->mask.get(), static_cast<const double*>(tod) + r * p->nsamples, p->nsamples, y2);
+                    pix_t, pc->mask.get(), static_cast<const double*>(tod) + r * p->nsamples, p->nsamples, y2);
             BM_LAUNCH_CHECK();
             apply_toeplitz_df(n, SrcPlainDF{y2}, z2);
             if (p->cs_lo_s.get() == nullptr && ensure_chunk_major(p, n, pc)) pt_chunked_df(p, pc, z2, br);
@@ -2029,11 +2036,11 @@ void rhs(bm_pointing* p, bm_inv_noise* n, bm_precond* pc, const void* tod, bm_dt
         } else {
             double* z64 = workspace_as<double>(ctx, "z64", p->nsamples);
             if (dt == BM_F32) {
-                SrcMaskedTod<float> src{p->pix.get(), pc->mask.get(),
+                SrcMaskedTod<float> src{time_pix(p), pc->mask.get(),
                                         static_cast<const float*>(tod) + r * p->nsamples};
                 apply_filter_f64(n, pc, src, z64);
             } else {
-                SrcMaskedTod<double> src{p->pix.get(), pc->mask.get(),
+                SrcMaskedTod<double> src{time_pix(p), pc->mask.get(),
                                          static_cast<const double*>(tod) + r * p->nsamples};
                 apply_filter_f64(n, pc, src, z64);
             }
@@ -2047,8 +2054,9 @@ void pointing_apply(bm_pointing* p, const double* x, double* y) {
     bm_context* ctx = p->ctx;
     const int threads = 256;
     const float2* trig_t = time_trig(p);  // built here on first use when deferred
+    const int32_t* pix_t = time_pix(p);  // built here on first use when deferred
     pointing_apply_kernel<<<grid_for(ctx, (p->nsamples + threads - 1) / threads, 16), threads, 0, ctx->stream>>>(
-        p->pix.get(), trig_t, p->cs_lo_t.get(), p->nsamples, p->ncomp, x, y);
+        pix_t, trig_t, p->cs_lo_t.get(), p->nsamples, p->ncomp, x, y);
     BM_LAUNCH_CHECK();
 }
 

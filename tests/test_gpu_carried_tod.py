@@ -118,11 +118,12 @@ def test_carried_tod_solve(L, ctx, prec, host):
 
 
 def test_carried_tod_pointing_with_time_ordered_operators(L, ctx):
-    """A pointing that carries a TOD, given cos/sin in device memory, builds
-    its time-ordered trig pairs only when a time-ordered operator first
-    needs them: with Toeplitz noise its matvecs (FP64 and mixed), its P x and
-    its refined solve are bitwise those of the same pointing made without the
-    TOD (whose first sort pass writes the pairs at creation)."""
+    """A pointing that carries a TOD, given pixels and cos/sin in device
+    memory, builds its time-ordered pixels and trig pairs only when a
+    time-ordered operator first needs them: with Toeplitz noise its matvecs
+    (FP64 and mixed), its P x and its refined solve, and with the offset
+    template its matvecs, are bitwise those of the same pointing made
+    without the TOD (which keeps both at creation)."""
     c = Case(L, ctx, 16, 4, 40_000, 4321, noise="toeplitz", chunk=4096, nlags=64, flag=0.01, trig=True,
              tod_dtype=np.float32, build_oracle=False)
     try:
@@ -150,6 +151,26 @@ def test_carried_tod_pointing_with_time_ordered_operators(L, ctx):
         finally:
             L.bm_precond_destroy(pc1)
             L.bm_pointing_destroy(p1)
+        # the offset template's operators (time-ordered interval means) on a
+        # fresh carried pointing: bitwise those of the plain pointing
+        inv_var = 1.0 / c.e.sigma ** 2
+        n_o = L.bm_inv_noise_create_offset_filter(ctx, c.e.det_offsets, inv_var, 700)
+        p3 = L.bm_pointing_create_with_tod(ctx, c.npix, c.d_pix, c.d_tod, cos2psi=torch.from_numpy(c32).cuda(),
+                                           sin2psi=torch.from_numpy(s32).cuda())
+        pc_o0 = L.bm_blockdiag_precond_create(c.p, n_o, 3, 1e3)
+        pc_o3 = L.bm_blockdiag_precond_create(p3, n_o, 3, 1e3)
+        try:
+            x = c.vec(np.random.default_rng(6).normal(size=(c.npix, 3)))
+            for prec in (L.BM_PREC_FP64, L.BM_PREC_MIXED):
+                q0, q3 = c.vec(), c.vec()
+                L.bm_matvec(c.p, n_o, pc_o0, x, q0, prec)
+                L.bm_matvec(p3, n_o, pc_o3, x, q3, prec)
+                assert torch.equal(torch.nan_to_num(q0), torch.nan_to_num(q3)), prec
+        finally:
+            L.bm_precond_destroy(pc_o3)
+            L.bm_precond_destroy(pc_o0)
+            L.bm_pointing_destroy(p3)
+            L.bm_inv_noise_destroy(n_o)
         # a fresh carried pointing whose first time-ordered operator is the solve
         p2 = L.bm_pointing_create_with_tod(ctx, c.npix, c.d_pix, c.d_tod, cos2psi=torch.from_numpy(c32).cuda(),
                                            sin2psi=torch.from_numpy(s32).cuda())
